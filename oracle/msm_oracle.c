@@ -1,0 +1,1097 @@
+/*
+ * msm_oracle.c -- plain, slow, FP64 CPU oracle of the B-spline multilevel
+ * summation method (MSM) described in arXiv 2510.05961 (msmJAX).
+ *
+ * TEST INFRASTRUCTURE ONLY. The product library never links, loads or calls
+ * this file and shares no header, helper, table or constant with it. Only the
+ * test-suite, the smoke check and the CPU-baseline leg of the benchmark use it.
+ *
+ * Each function names the passage of the paper it restates. The arithmetic is
+ * FP64 with plain ordered loops (build with -ffp-contract=off, no fast-math);
+ * OpenMP only splits loops whose iterations write disjoint outputs, so every
+ * output is summed in the same order with or without threads. The one FP32
+ * routine is the cell binning, which follows the FP32 cell-index contract bit
+ * for bit (see or_bin).
+ *
+ * Parity status: every function below is pinned by a CPU test against values
+ * that do not come from this file (closed forms, direct sums, Ewald sums, the
+ * rock-salt Madelung constant, finite differences, exact invariants).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXLEV 20
+
+/* status bits of or_bin */
+#define OR_ST_OUTSIDE 1
+#define OR_ST_NONFINITE 2
+
+typedef struct {
+  /* inputs */
+  double L[3];          /* orthorhombic cell edge lengths */
+  int pbc[3];           /* 1 periodic, 0 open */
+  double h;             /* target level-1 spacing */
+  int grid_override[3]; /* >0: level-1 interval count along that axis */
+  double a;             /* level-zero cutoff r_cut^(0) */
+  int p;                /* B-spline order (even) */
+  int levels;           /* L, 0 = rule below */
+  /* derived by or_plan_init */
+  int nlev;             /* number of grid levels L (top level included) */
+  int ncomp;            /* levels whose grids are evaluated (nlev, or nlev-1 when the top is dropped) */
+  int top_kept;         /* 1 when the top level's stencil is applied (all axes open) */
+  int M[3];             /* level-1 interval counts */
+  double h1[3];         /* level-1 spacings L/M */
+  int lo[OR_MAXLEV][3]; /* first grid index per level (index 0 = level 1) */
+  int n[OR_MAXLEV][3];  /* grid points per level */
+  int S[3];             /* kernel-sample radius of the level stencils */
+  int R[3];             /* stencil radius S + p/2 - 1 */
+  int C[3];             /* binning cells per axis */
+  double edge[3];       /* binning cell edges */
+  int nnbr[3];          /* neighbour-cell reach ceil(a/edge) */
+  float invLf[3];       /* (float)(1/L): binning contract */
+} or_plan;
+
+/* ------------------------------------------------------------------------ */
+/* Softening and splitting, Sec. 3.4, Eq. coulomb_splitting_with_softener.   */
+/* ------------------------------------------------------------------------ */
+
+/* c_k = binom(2k,k)/4^k, the magnitude of the k-th Taylor coefficient of
+ * s^(-1/2) about s = 1: binom(-1/2,k)(s-1)^k = c_k (1-s)^k. */
+static double coef_ck(int k) {
+  double c = 1.0;
+  for (int j = 1; j <= k; j++) c *= (2.0 * j - 1.0) / (2.0 * j);
+  return c;
+}
+
+/* gamma(rho): 1/rho for rho >= 1; for rho < 1 the degree p-1 Taylor
+ * polynomial of s^(-1/2) about s = 1, evaluated at s = rho^2 (Sec. 3.4). */
+double or_gamma(int p, double rho) {
+  if (rho >= 1.0) return 1.0 / rho;
+  double s = 1.0 - rho * rho, acc = 0.0, pw = 1.0;
+  for (int k = 0; k <= p - 1; k++) {
+    acc += coef_ck(k) * pw;
+    pw *= s;
+  }
+  return acc;
+}
+
+/* d gamma / d rho. */
+double or_dgamma(int p, double rho) {
+  if (rho >= 1.0) return -1.0 / (rho * rho);
+  double s = 1.0 - rho * rho, acc = 0.0, pw = 1.0;
+  for (int k = 1; k <= p - 1; k++) {
+    acc += coef_ck(k) * k * pw;
+    pw *= s;
+  }
+  return acc * (-2.0 * rho);
+}
+
+/* Partial kernel k_l(r), l = 0 .. nlev (Eq. coulomb_splitting_with_softener):
+ *   k_0 = 1/r - gamma(r/a)/a,
+ *   k_l = gamma(r/(2^(l-1) a))/(2^(l-1) a) - gamma(r/(2^l a))/(2^l a), 1 <= l <= L-1,
+ *   k_L = gamma(r/(2^(L-1) a))/(2^(L-1) a).
+ * Where gamma = 1/rho in both terms the difference is exactly zero, so
+ * k_l(r) = 0 for r >= 2^l a (l < L); that zero is returned as such. */
+double or_kl(int p, double a, int nlev, int l, double r) {
+  if (l == 0) {
+    if (r >= a) return 0.0;
+    return 1.0 / r - or_gamma(p, r / a) / a;
+  }
+  double s1 = ldexp(a, l - 1);
+  if (l == nlev) return or_gamma(p, r / s1) / s1;
+  double s2 = ldexp(a, l);
+  if (r >= s2) return 0.0;
+  return or_gamma(p, r / s1) / s1 - or_gamma(p, r / s2) / s2;
+}
+
+/* d k_l / d r. */
+double or_dkl(int p, double a, int nlev, int l, double r) {
+  if (l == 0) {
+    if (r >= a) return 0.0;
+    return -1.0 / (r * r) - or_dgamma(p, r / a) / (a * a);
+  }
+  double s1 = ldexp(a, l - 1);
+  if (l == nlev) return or_dgamma(p, r / s1) / (s1 * s1);
+  double s2 = ldexp(a, l);
+  if (r >= s2) return 0.0;
+  return or_dgamma(p, r / s1) / (s1 * s1) - or_dgamma(p, r / s2) / (s2 * s2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* B-spline basis, Sec. 3.3 (cardinal B-spline of order p, support p cells). */
+/* ------------------------------------------------------------------------ */
+
+/* Centred cardinal B-spline of order q, support (-q/2, q/2), written as the
+ * truncated-power sum Phi_q(t) = 1/(q-1)! sum_k (-1)^k C(q,k) (t+q/2-k)_+^(q-1).
+ * It is evaluated at -|t| (Phi_q is even), where only the small leading terms
+ * of the sum are non-zero. */
+double or_bspline(int q, double t) {
+  t = -fabs(t);
+  double half = 0.5 * q;
+  if (t <= -half) return 0.0;
+  double fact = 1.0;
+  for (int j = 2; j <= q - 1; j++) fact *= j;
+  double sum = 0.0, binom = 1.0;
+  for (int k = 0; k <= q; k++) {
+    double x = t + half - k;
+    if (x > 0.0) {
+      double pw = 1.0;
+      for (int e = 0; e < q - 1; e++) pw *= x;
+      sum += (k & 1) ? -binom * pw : binom * pw;
+    }
+    binom = binom * (q - k) / (k + 1);
+  }
+  return sum / fact;
+}
+
+/* Phi_q'(t) = Phi_{q-1}(t + 1/2) - Phi_{q-1}(t - 1/2). */
+double or_dbspline(int q, double t) {
+  return or_bspline(q - 1, t + 0.5) - or_bspline(q - 1, t - 0.5);
+}
+
+/* Restriction coefficients J_k, k = -p/2 .. p/2 (Eq.
+ * restriction_prolongation_explicit_formulas). The paper defers the formula to
+ * its Ref. HWX+16; this is the B-spline two-scale relation
+ * Phi_p(x/2) = sum_k 2^(1-p) C(p, k+p/2) Phi_p(x-k). Output index k + p/2. */
+void or_J(int p, double* J) {
+  double binom = 1.0;
+  for (int k = 0; k <= p; k++) {
+    J[k] = ldexp(binom, 1 - p);
+    binom = binom * (p - k) / (k + 1);
+  }
+}
+
+/* Quasi-interpolation coefficients omega'_j, j = -(p/2-1) .. p/2-1 (output
+ * index j + p/2 - 1), of Eq. kernel_stencil_by_conv_with_universal_coeff.
+ * The paper does not print them. Reading used: the shortest symmetric sequence
+ * whose symbol times the squared B-spline sampling symbol
+ * b(theta) = sum_n Phi_p(n) cos(n theta) equals 1 + O(theta^p); i.e. the
+ * Taylor coefficients of theta^0 .. theta^(p-2) of omega(theta) b(theta)^2 are
+ * 1, 0, ..., 0. This is p/2 linear equations for the p/2 unknowns
+ * omega'_0 .. omega'_(p/2-1), solved by Gaussian elimination. */
+int or_omega(int p, double* w) {
+  int K = p / 2;
+  double beta[8], gam[8], fac[20];
+  fac[0] = 1.0;
+  for (int i = 1; i < 20; i++) fac[i] = fac[i - 1] * i;
+  for (int k = 0; k < K; k++) {
+    double s = 0.0;
+    for (int m = -p / 2; m <= p / 2; m++) s += or_bspline(p, (double)m) * pow((double)m, 2.0 * k);
+    beta[k] = ((k & 1) ? -1.0 : 1.0) * s / fac[2 * k];
+  }
+  for (int k = 0; k < K; k++) {
+    gam[k] = 0.0;
+    for (int i = 0; i <= k; i++) gam[k] += beta[i] * beta[k - i];
+  }
+  /* coefficient of theta^(2i) in omega(theta) = w_0 + 2 sum_j w_j cos(j theta):
+   * A[i][j] w_j with A[i][0] = [i==0], A[i][j] = 2 (-1)^i j^(2i) / (2i)!. */
+  double A[8][8], Mx[8][9];
+  for (int i = 0; i < K; i++)
+    for (int j = 0; j < K; j++)
+      A[i][j] = (j == 0) ? (i == 0 ? 1.0 : 0.0)
+                         : 2.0 * ((i & 1) ? -1.0 : 1.0) * pow((double)j, 2.0 * i) / fac[2 * i];
+  for (int k = 0; k < K; k++) {
+    for (int j = 0; j < K; j++) {
+      double s = 0.0;
+      for (int i = 0; i <= k; i++) s += A[i][j] * gam[k - i];
+      Mx[k][j] = s;
+    }
+    Mx[k][K] = (k == 0) ? 1.0 : 0.0;
+  }
+  for (int c = 0; c < K; c++) {
+    int piv = c;
+    for (int r = c + 1; r < K; r++)
+      if (fabs(Mx[r][c]) > fabs(Mx[piv][c])) piv = r;
+    if (Mx[piv][c] == 0.0) return -1;
+    for (int j = 0; j <= K; j++) {
+      double t = Mx[c][j];
+      Mx[c][j] = Mx[piv][j];
+      Mx[piv][j] = t;
+    }
+    for (int r = 0; r < K; r++) {
+      if (r == c) continue;
+      double f = Mx[r][c] / Mx[c][c];
+      for (int j = c; j <= K; j++) Mx[r][j] -= f * Mx[c][j];
+    }
+  }
+  for (int j = 0; j < K; j++) {
+    double v = Mx[j][K] / Mx[j][j];
+    w[(K - 1) + j] = v;
+    w[(K - 1) - j] = v;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid set-up (Sec. 4.1 for periodic axes; readings for open axes).         */
+/* ------------------------------------------------------------------------ */
+
+static int floordiv(int a, int b) { int q = a / b; if ((a % b != 0) && ((a < 0) != (b < 0))) q--; return q; }
+static int ceildiv(int a, int b) { return -floordiv(-a, b); }
+
+/* Fills the derived fields. Returns 0, 1 (invalid argument) or 2 (unsupported).
+ * Periodic axes: M = 2^round(log2(L/h)) (or the override, a power of two), all
+ * periodic axes equal, spacing doubled until one point remains (Sec. 4.1), so
+ * L = log2(M) + 1 and the one-point top level is not evaluated. Open axes:
+ * M = ceil(L/h), level-1 indices [-p/2, M+p/2], each coarser level keeping the
+ * indices that restriction can reach; with every axis open the top level is
+ * evaluated with its full-range stencil. */
+int or_plan_init(or_plan* P) {
+  int p = P->p;
+  if (p != 4 && p != 6 && p != 8) return 1;
+  if (!(P->a > 0.0)) return 1;
+  int anyper = 0, Mper = 0;
+  for (int d = 0; d < 3; d++) {
+    if (!(P->L[d] > 0.0)) return 1;
+    int M;
+    if (P->grid_override[d] > 0) {
+      M = P->grid_override[d];
+    } else {
+      if (!(P->h > 0.0)) return 1;
+      if (P->pbc[d]) {
+        int e = (int)floor(log2(P->L[d] / P->h) + 0.5);
+        if (e < 1) e = 1;
+        if (e > 16) return 2;
+        M = 1 << e;
+      } else {
+        M = (int)ceil(P->L[d] / P->h);
+        if (M < 1) M = 1;
+      }
+    }
+    if (P->pbc[d]) {
+      if (M < 2 || (M & (M - 1)) != 0) return 2;
+      if (anyper && M != Mper) return 2;
+      anyper = 1;
+      Mper = M;
+    }
+    P->M[d] = M;
+    P->h1[d] = P->L[d] / M;
+  }
+  int hp = p / 2;
+  if (anyper) {
+    int nl = 1;
+    while ((1 << (nl - 1)) < Mper) nl++;
+    if (P->levels > 0 && P->levels != nl) return 2;
+    P->nlev = nl;
+    P->top_kept = 0;
+    P->ncomp = nl - 1;
+  } else {
+    P->top_kept = 1;
+    P->nlev = P->levels;
+  }
+  /* level index ranges */
+  for (int d = 0; d < 3; d++) {
+    if (P->pbc[d]) continue;
+    P->lo[0][d] = -hp;
+    P->n[0][d] = P->M[d] + p + 1;
+  }
+  int maxlev = OR_MAXLEV;
+  for (int l = 1; l < maxlev; l++) {
+    for (int d = 0; d < 3; d++) {
+      if (P->pbc[d]) continue;
+      int lo = P->lo[l - 1][d], hi = lo + P->n[l - 1][d] - 1;
+      int nlo = ceildiv(lo - hp, 2), nhi = floordiv(hi + hp, 2);
+      P->lo[l][d] = nlo;
+      P->n[l][d] = nhi - nlo + 1;
+    }
+  }
+  if (!anyper && P->nlev <= 0) {
+    int cap = (p + 1 > 8) ? p + 1 : 8;
+    int l = 1;
+    for (;; l++) {
+      int ok = 1;
+      for (int d = 0; d < 3; d++) if (P->n[l - 1][d] > cap) ok = 0;
+      if (ok || l == OR_MAXLEV) break;
+    }
+    P->nlev = l;
+  }
+  if (P->nlev < 1 || P->nlev > OR_MAXLEV) return 2;
+  if (!anyper) P->ncomp = P->nlev;
+  for (int l = 0; l < OR_MAXLEV; l++)
+    for (int d = 0; d < 3; d++)
+      if (P->pbc[d]) {
+        P->lo[l][d] = 0;
+        P->n[l][d] = (l < P->nlev) ? (P->M[d] >> l) : 1;
+        if (P->n[l][d] < 1) P->n[l][d] = 1;
+      }
+  for (int d = 0; d < 3; d++) {
+    P->S[d] = (int)ceil(2.0 * P->a / P->h1[d]) - 1;
+    if (P->S[d] < 0) P->S[d] = 0;
+    P->R[d] = P->S[d] + hp - 1;
+    int C = (int)floor(2.0 * P->L[d] / P->a);
+    if (C < 1) C = 1;
+    if (C > 256) C = 256;
+    P->C[d] = C;
+    P->edge[d] = P->L[d] / C;
+    P->nnbr[d] = (int)ceil(P->a / P->edge[d]);
+    P->invLf[d] = (float)(1.0 / P->L[d]);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell binning: the FP32 cell-index contract (bit-exact with the GPU).      */
+/* ------------------------------------------------------------------------ */
+
+/* Cell of each atom and the stable counting sort by cell. Per axis, in FP32
+ * with round-to-nearest and no contraction:
+ *   s = x * (float)(1/L);  periodic: s = s - floorf(s), s >= 1 -> 0;
+ *   open: s outside [0,1] -> status OUTSIDE (axis cell 0);
+ *   c = min((int)(s * (float)C), C - 1);  cell = (cx*Cy + cy)*Cz + cz.
+ * Non-finite coordinates or charges set status NONFINITE (axis cell 0).
+ * Within a cell, atoms keep ascending original index. */
+int or_bin(const or_plan* P, int n, const float* pos, const float* q, int* cell_id, int* cell_start,
+           int* perm) {
+  int status = 0;
+  int ncell = P->C[0] * P->C[1] * P->C[2];
+  for (int i = 0; i < n; i++) {
+    int c[3];
+    if (!isfinite(q[i])) status |= OR_ST_NONFINITE;
+    for (int d = 0; d < 3; d++) {
+      float x = pos[3 * i + d];
+      c[d] = 0;
+      if (!isfinite(x)) { status |= OR_ST_NONFINITE; continue; }
+      float s = x * P->invLf[d];
+      if (P->pbc[d]) {
+        s = s - floorf(s);
+        if (s >= 1.0f) s = 0.0f;
+      } else if (!(s >= 0.0f && s <= 1.0f)) {
+        status |= OR_ST_OUTSIDE;
+        continue;
+      }
+      float t = s * (float)P->C[d];
+      int ci = (int)t;
+      if (ci > P->C[d] - 1) ci = P->C[d] - 1;
+      c[d] = ci;
+    }
+    cell_id[i] = (c[0] * P->C[1] + c[1]) * P->C[2] + c[2];
+  }
+  for (int c = 0; c <= ncell; c++) cell_start[c] = 0;
+  for (int i = 0; i < n; i++) cell_start[cell_id[i] + 1]++;
+  for (int c = 0; c < ncell; c++) cell_start[c + 1] += cell_start[c];
+  int* cursor = (int*)malloc(sizeof(int) * (ncell > 0 ? ncell : 1));
+  for (int c = 0; c < ncell; c++) cursor[c] = cell_start[c];
+  for (int i = 0; i < n; i++) perm[cursor[cell_id[i]]++] = i;
+  free(cursor);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid helpers                                                              */
+/* ------------------------------------------------------------------------ */
+
+static int lev_size(const or_plan* P, int l) { /* l is 1-based */
+  return P->n[l - 1][0] * P->n[l - 1][1] * P->n[l - 1][2];
+}
+
+/* storage index of grid point m on axis d of level l, or -1 when an open axis
+ * has no such point. Periodic axes wrap. */
+static int gidx(const or_plan* P, int l, int d, int m) {
+  int nn = P->n[l - 1][d];
+  if (P->pbc[d]) {
+    int r = m % nn;
+    return r < 0 ? r + nn : r;
+  }
+  int i = m - P->lo[l - 1][d];
+  return (i >= 0 && i < nn) ? i : -1;
+}
+
+/* level-1 grid coordinate u = x / h_1 of a Cartesian coordinate (periodic axes
+ * wrapped into the cell first). */
+static double to_u(const or_plan* P, int d, double x) {
+  if (P->pbc[d]) x = x - P->L[d] * floor(x / P->L[d]);
+  return x / P->h1[d];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Anterpolation, interpolation (Sec. 3.2.2, Alg. anterpolation_double_loop,  */
+/* Eqs. grid_charge, uoneplus_interpolation_with_index_set,                  */
+/* analytic_uoneplus_position_grad / _charge_grad).                           */
+/* ------------------------------------------------------------------------ */
+
+/* q~^1_m = sum_i q_i phi^1_m(r_i), phi^1_m(r) = prod_d Phi_p(u_d - m_d),
+ * summed over the index set m_d in {floor(u_d)-p/2+1 .. floor(u_d)+p/2}. */
+void or_anterp(const or_plan* P, int n, const double* pos, const double* q, double* grid) {
+  int p = P->p, nsz = lev_size(P, 1);
+  int ny = P->n[0][1], nz = P->n[0][2];
+  for (int k = 0; k < nsz; k++) grid[k] = 0.0;
+  for (int i = 0; i < n; i++) {
+    int base[3], idx[3][8];
+    double w[3][8];
+    for (int d = 0; d < 3; d++) {
+      double u = to_u(P, d, pos[3 * i + d]);
+      base[d] = (int)floor(u) - p / 2 + 1;
+      for (int j = 0; j < p; j++) {
+        w[d][j] = or_bspline(p, u - (base[d] + j));
+        idx[d][j] = gidx(P, 1, d, base[d] + j);
+      }
+    }
+    for (int jx = 0; jx < p; jx++)
+      for (int jy = 0; jy < p; jy++)
+        for (int jz = 0; jz < p; jz++) {
+          if (idx[0][jx] < 0 || idx[1][jy] < 0 || idx[2][jz] < 0) continue;
+          grid[(idx[0][jx] * ny + idx[1][jy]) * nz + idx[2][jz]] += q[i] * w[0][jx] * w[1][jy] * w[2][jz];
+        }
+  }
+}
+
+/* phi1_i = sum_m e_m phi^1_m(r_i); grad_i = q_i sum_m e_m grad phi^1_m(r_i);
+ * F1_i = -grad_i. d phi_m / d x_d = Phi_p'(u_d - m_d) / h_1d times the other two
+ * factors. F1 may be NULL. */
+void or_interp(const or_plan* P, int n, const double* pos, const double* q, const double* e,
+               double* phi1, double* F1) {
+  int p = P->p;
+  int ny = P->n[0][1], nz = P->n[0][2];
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; i++) {
+    int base[3], idx[3][8];
+    double w[3][8], dw[3][8];
+    for (int d = 0; d < 3; d++) {
+      double u = to_u(P, d, pos[3 * i + d]);
+      base[d] = (int)floor(u) - p / 2 + 1;
+      for (int j = 0; j < p; j++) {
+        w[d][j] = or_bspline(p, u - (base[d] + j));
+        dw[d][j] = or_dbspline(p, u - (base[d] + j)) / P->h1[d];
+        idx[d][j] = gidx(P, 1, d, base[d] + j);
+      }
+    }
+    double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int jx = 0; jx < p; jx++)
+      for (int jy = 0; jy < p; jy++)
+        for (int jz = 0; jz < p; jz++) {
+          if (idx[0][jx] < 0 || idx[1][jy] < 0 || idx[2][jz] < 0) continue;
+          double ev = e[(idx[0][jx] * ny + idx[1][jy]) * nz + idx[2][jz]];
+          ph += ev * w[0][jx] * w[1][jy] * w[2][jz];
+          gx += ev * dw[0][jx] * w[1][jy] * w[2][jz];
+          gy += ev * w[0][jx] * dw[1][jy] * w[2][jz];
+          gz += ev * w[0][jx] * w[1][jy] * dw[2][jz];
+        }
+    phi1[i] = ph;
+    if (F1) {
+      F1[3 * i + 0] = -q[i] * gx;
+      F1[3 * i + 1] = -q[i] * gy;
+      F1[3 * i + 2] = -q[i] * gz;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restriction and prolongation, Eq. restriction_prolongation_explicit_formulas */
+/* ------------------------------------------------------------------------ */
+
+/* q~^(l+1)_m = sum_n J_(n - 2m) q~^l_n, with J_n = J_nx J_ny J_nz (l 1-based).
+ * Periodic axes wrap the fine index; open axes drop indices outside the grid. */
+void or_restrict(const or_plan* P, int l, const double* fine, double* coarse) {
+  int p = P->p, hp = p / 2;
+  double J[9];
+  or_J(p, J);
+  int* nc = (int*)P->n[l];
+  int* nf = (int*)P->n[l - 1];
+#pragma omp parallel for schedule(static)
+  for (int cx = 0; cx < nc[0]; cx++)
+    for (int cy = 0; cy < nc[1]; cy++)
+      for (int cz = 0; cz < nc[2]; cz++) {
+        int m[3] = {cx + P->lo[l][0], cy + P->lo[l][1], cz + P->lo[l][2]};
+        double acc = 0.0;
+        for (int kx = -hp; kx <= hp; kx++) {
+          int fx = gidx(P, l, 0, 2 * m[0] + kx);
+          if (fx < 0) continue;
+          for (int ky = -hp; ky <= hp; ky++) {
+            int fy = gidx(P, l, 1, 2 * m[1] + ky);
+            if (fy < 0) continue;
+            for (int kz = -hp; kz <= hp; kz++) {
+              int fz = gidx(P, l, 2, 2 * m[2] + kz);
+              if (fz < 0) continue;
+              acc += J[kx + hp] * J[ky + hp] * J[kz + hp] * fine[(fx * nf[1] + fy) * nf[2] + fz];
+            }
+          }
+        }
+        coarse[(cx * nc[1] + cy) * nc[2] + cz] = acc;
+      }
+}
+
+/* fine += I^T coarse, the transpose of or_restrict: (I^T e)_m = sum_n J_(m-2n) e_n.
+ * Written as the scatter of each coarse value to the fine points it came from,
+ * which is the transpose on periodic (wrapped) and open grids alike. */
+void or_prolong_add(const or_plan* P, int l, const double* coarse, double* fine) {
+  int p = P->p, hp = p / 2;
+  double J[9];
+  or_J(p, J);
+  int* nc = (int*)P->n[l];
+  int* nf = (int*)P->n[l - 1];
+  for (int cx = 0; cx < nc[0]; cx++)
+    for (int cy = 0; cy < nc[1]; cy++)
+      for (int cz = 0; cz < nc[2]; cz++) {
+        int m[3] = {cx + P->lo[l][0], cy + P->lo[l][1], cz + P->lo[l][2]};
+        double ev = coarse[(cx * nc[1] + cy) * nc[2] + cz];
+        for (int kx = -hp; kx <= hp; kx++) {
+          int fx = gidx(P, l, 0, 2 * m[0] + kx);
+          if (fx < 0) continue;
+          for (int ky = -hp; ky <= hp; ky++) {
+            int fy = gidx(P, l, 1, 2 * m[1] + ky);
+            if (fy < 0) continue;
+            for (int kz = -hp; kz <= hp; kz++) {
+              int fz = gidx(P, l, 2, 2 * m[2] + kz);
+              if (fz < 0) continue;
+              fine[(fx * nf[1] + fy) * nf[2] + fz] += J[kx + hp] * J[ky + hp] * J[kz + hp] * ev;
+            }
+          }
+        }
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stencils K^l, Eq. kernel_stencil_by_conv_with_universal_coeff, and their  */
+/* strain derivatives.                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Offset box of the stencil applied on level l (1-based): d in [lo, lo+sz).
+ * Levels below the top: [-R, R] per axis. Top level kept (all axes open): the
+ * full range of grid displacements. Periodic axes are folded onto [0, n_l):
+ * on a periodic grid the operator sums every image of an offset. */
+void or_stencil_box(const or_plan* P, int l, int* lo, int* sz) {
+  for (int d = 0; d < 3; d++) {
+    if (P->pbc[d]) {
+      lo[d] = 0;
+      sz[d] = P->n[l - 1][d];
+    } else if (l == P->nlev) {
+      lo[d] = -(P->n[l - 1][d] - 1);
+      sz[d] = 2 * P->n[l - 1][d] - 1;
+    } else {
+      lo[d] = -P->R[d];
+      sz[d] = 2 * P->R[d] + 1;
+    }
+  }
+}
+
+/* Stencil of level l (1-based) on its box (or_stencil_box), which = 0 for K^l,
+ * 1..6 for dK^l/d eps_ab with ab = xx, yy, zz, xy, xz, yz. G (row-major 3x3,
+ * NULL = identity) maps the grid displacement h_l o n to the sample vector
+ * v = G (h_l o n), so a strained cell can be evaluated for finite differences.
+ * Sample values: which 0: k_l(|v|); which > 0: k_l'(|v|) v_a v_b / |v| (0 at v = 0).
+ * K_m = sum_n omega'_(mx-nx) omega'_(my-ny) omega'_(mz-nz) sample(n), applied
+ * one axis at a time; periodic axes then folded onto [0, n_l). */
+void or_stencil_build(const or_plan* P, int l, int which, const double* G, double* out) {
+  int p = P->p, r = p / 2 - 1;
+  double om[8];
+  or_omega(p, om);
+  /* unfolded output box */
+  int olo[3], osz[3], slo[3], ssz[3];
+  for (int d = 0; d < 3; d++) {
+    if (l == P->nlev) {
+      olo[d] = -(P->n[l - 1][d] - 1);
+      osz[d] = 2 * P->n[l - 1][d] - 1;
+    } else {
+      olo[d] = -P->R[d];
+      osz[d] = 2 * P->R[d] + 1;
+    }
+    slo[d] = olo[d] - r;
+    ssz[d] = osz[d] + 2 * r;
+  }
+  double hl[3];
+  for (int d = 0; d < 3; d++) hl[d] = ldexp(P->h1[d], l - 1);
+  int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  size_t ns = (size_t)ssz[0] * ssz[1] * ssz[2];
+  double* smp = (double*)malloc(sizeof(double) * ns);
+#pragma omp parallel for schedule(static)
+  for (int ix = 0; ix < ssz[0]; ix++)
+    for (int iy = 0; iy < ssz[1]; iy++)
+      for (int iz = 0; iz < ssz[2]; iz++) {
+        double g[3] = {hl[0] * (ix + slo[0]), hl[1] * (iy + slo[1]), hl[2] * (iz + slo[2])};
+        double v[3];
+        for (int a = 0; a < 3; a++)
+          v[a] = G ? G[3 * a + 0] * g[0] + G[3 * a + 1] * g[1] + G[3 * a + 2] * g[2] : g[a];
+        double rr = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double val;
+        if (which == 0) {
+          val = or_kl(p, P->a, P->nlev, l, rr);
+        } else {
+          int a = ab[which - 1][0], b = ab[which - 1][1];
+          val = (rr > 0.0) ? or_dkl(p, P->a, P->nlev, l, rr) * v[a] * v[b] / rr : 0.0;
+        }
+        smp[((size_t)ix * ssz[1] + iy) * ssz[2] + iz] = val;
+      }
+  /* z pass: A[nx][ny][mz] = sum_t omega'_t smp[nx][ny][mz - t] */
+  size_t nA = (size_t)ssz[0] * ssz[1] * osz[2];
+  double* A = (double*)malloc(sizeof(double) * nA);
+  for (int ix = 0; ix < ssz[0]; ix++)
+    for (int iy = 0; iy < ssz[1]; iy++)
+      for (int mz = 0; mz < osz[2]; mz++) {
+        double acc = 0.0;
+        for (int t = -r; t <= r; t++)
+          acc += om[t + r] * smp[((size_t)ix * ssz[1] + iy) * ssz[2] + (mz + r - t)];
+        A[((size_t)ix * ssz[1] + iy) * osz[2] + mz] = acc;
+      }
+  size_t nB = (size_t)ssz[0] * osz[1] * osz[2];
+  double* B = (double*)malloc(sizeof(double) * nB);
+  for (int ix = 0; ix < ssz[0]; ix++)
+    for (int my = 0; my < osz[1]; my++)
+      for (int mz = 0; mz < osz[2]; mz++) {
+        double acc = 0.0;
+        for (int t = -r; t <= r; t++)
+          acc += om[t + r] * A[((size_t)ix * ssz[1] + (my + r - t)) * osz[2] + mz];
+        B[((size_t)ix * osz[1] + my) * osz[2] + mz] = acc;
+      }
+  size_t nK = (size_t)osz[0] * osz[1] * osz[2];
+  double* Kb = (double*)malloc(sizeof(double) * nK);
+  for (int mx = 0; mx < osz[0]; mx++)
+    for (int my = 0; my < osz[1]; my++)
+      for (int mz = 0; mz < osz[2]; mz++) {
+        double acc = 0.0;
+        for (int t = -r; t <= r; t++)
+          acc += om[t + r] * B[((size_t)(mx + r - t) * osz[1] + my) * osz[2] + mz];
+        Kb[((size_t)mx * osz[1] + my) * osz[2] + mz] = acc;
+      }
+  /* fold periodic axes */
+  int flo[3], fsz[3];
+  or_stencil_box(P, l, flo, fsz);
+  size_t nF = (size_t)fsz[0] * fsz[1] * fsz[2];
+  for (size_t k = 0; k < nF; k++) out[k] = 0.0;
+  for (int mx = 0; mx < osz[0]; mx++)
+    for (int my = 0; my < osz[1]; my++)
+      for (int mz = 0; mz < osz[2]; mz++) {
+        int m[3] = {mx + olo[0], my + olo[1], mz + olo[2]}, f[3];
+        for (int d = 0; d < 3; d++) {
+          if (P->pbc[d]) {
+            int r2 = m[d] % fsz[d];
+            f[d] = r2 < 0 ? r2 + fsz[d] : r2;
+          } else {
+            f[d] = m[d] - flo[d];
+          }
+        }
+        out[((size_t)f[0] * fsz[1] + f[1]) * fsz[2] + f[2]] += Kb[((size_t)mx * osz[1] + my) * osz[2] + mz];
+      }
+  free(smp);
+  free(A);
+  free(B);
+  free(Kb);
+}
+
+/* e_m = sum_d K_d q_(m-d) (Eq. action_of_K_as_convolution) on level l; periodic
+ * axes wrap, open axes drop indices outside the grid. Zero stencil entries are
+ * skipped. */
+void or_stencil_apply(const or_plan* P, int l, const double* K, const double* qg, double* eg) {
+  int klo[3], ksz[3];
+  or_stencil_box(P, l, klo, ksz);
+  int* nn = (int*)P->n[l - 1];
+  int* lo = (int*)P->lo[l - 1];
+  size_t nK = (size_t)ksz[0] * ksz[1] * ksz[2];
+  int* nzl = (int*)malloc(sizeof(int) * (nK > 0 ? nK : 1));
+  size_t nnz = 0;
+  for (size_t k = 0; k < nK; k++) if (K[k] != 0.0) nzl[nnz++] = (int)k;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int ix = 0; ix < nn[0]; ix++)
+    for (int iy = 0; iy < nn[1]; iy++)
+      for (int iz = 0; iz < nn[2]; iz++) {
+        int m[3] = {ix + lo[0], iy + lo[1], iz + lo[2]};
+        double acc = 0.0;
+        for (size_t t = 0; t < nnz; t++) {
+          int k = nzl[t];
+          int d[3] = {k / (ksz[1] * ksz[2]) + klo[0], (k / ksz[2]) % ksz[1] + klo[1], k % ksz[2] + klo[2]};
+          int sx = gidx(P, l, 0, m[0] - d[0]);
+          if (sx < 0) continue;
+          int sy = gidx(P, l, 1, m[1] - d[1]);
+          if (sy < 0) continue;
+          int sz2 = gidx(P, l, 2, m[2] - d[2]);
+          if (sz2 < 0) continue;
+          acc += K[k] * qg[((size_t)sx * nn[1] + sy) * nn[2] + sz2];
+        }
+        eg[((size_t)ix * nn[1] + iy) * nn[2] + iz] = acc;
+      }
+  free(nzl);
+}
+
+/* Grid part of the virial on level l: -1/2 q~^T (dK/d eps_ab) q~ for the six
+ * components, computed as -1/2 sum_d dK_d C_d with the autocorrelation
+ * C_d = sum_m q~_m q~_(m-d) (the same double sum, grouped by offset). */
+void or_grid_virial_level(const or_plan* P, int l, const double* qg, double W6[6]) {
+  int klo[3], ksz[3];
+  or_stencil_box(P, l, klo, ksz);
+  size_t nK = (size_t)ksz[0] * ksz[1] * ksz[2];
+  double* dK = (double*)malloc(sizeof(double) * nK * 6);
+  for (int c = 0; c < 6; c++) or_stencil_build(P, l, c + 1, NULL, dK + c * nK);
+  double* Cd = (double*)malloc(sizeof(double) * nK);
+  int* nn = (int*)P->n[l - 1];
+  int* lo = (int*)P->lo[l - 1];
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long k = 0; k < (long)nK; k++) {
+    int any = 0;
+    for (int c = 0; c < 6; c++) if (dK[c * nK + k] != 0.0) any = 1;
+    if (!any) { Cd[k] = 0.0; continue; }
+    int d[3] = {(int)(k / (ksz[1] * ksz[2])) + klo[0], (int)((k / ksz[2]) % ksz[1]) + klo[1],
+                (int)(k % ksz[2]) + klo[2]};
+    double acc = 0.0;
+    for (int ix = 0; ix < nn[0]; ix++) {
+      int sx = gidx(P, l, 0, ix + lo[0] - d[0]);
+      if (sx < 0) continue;
+      for (int iy = 0; iy < nn[1]; iy++) {
+        int sy = gidx(P, l, 1, iy + lo[1] - d[1]);
+        if (sy < 0) continue;
+        for (int iz = 0; iz < nn[2]; iz++) {
+          int sz2 = gidx(P, l, 2, iz + lo[2] - d[2]);
+          if (sz2 < 0) continue;
+          acc += qg[((size_t)ix * nn[1] + iy) * nn[2] + iz] * qg[((size_t)sx * nn[1] + sy) * nn[2] + sz2];
+        }
+      }
+    }
+    Cd[k] = acc;
+  }
+  for (int c = 0; c < 6; c++) {
+    double acc = 0.0;
+    for (size_t k = 0; k < nK; k++) acc += dK[c * nK + k] * Cd[k];
+    W6[c] = -0.5 * acc;
+  }
+  free(dK);
+  free(Cd);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Short-range part, Eq. U_zero.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* phi0_i = sum over (j, image n) != (i, 0) with |d| < a of q_j k_0(|d|),
+ * d = r_j + A n - r_i, minus the self term q_i gamma(0)/a (the sum over l >= 1
+ * of k_l(0), which telescopes). Every periodic image within the cutoff counts,
+ * self images included. F0_i = sum q_i q_j k_0'(|d|) d/|d|;
+ * W0 = -1/2 sum_i sum_(j,n) q_i q_j k_0'(|d|) d d^T / |d| (row-major 3x3).
+ * E0 = 1/2 sum_i q_i phi0_i. Candidates come from a cell list with cells of
+ * edge >= a. F0, W0 may be NULL. */
+void or_short_range(const or_plan* P, int n, const double* pos, const double* q, double* phi0, double* F0,
+                    double* W0) {
+  int p = P->p;
+  double a = P->a;
+  int C[3];
+  double e[3];
+  double* w = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+  for (int d = 0; d < 3; d++) {
+    C[d] = (int)floor(P->L[d] / a);
+    if (C[d] < 1) C[d] = 1;
+    if (C[d] > 512) C[d] = 512;
+    e[d] = P->L[d] / C[d];
+  }
+  for (int i = 0; i < n; i++)
+    for (int d = 0; d < 3; d++) {
+      double x = pos[3 * i + d];
+      if (P->pbc[d]) {
+        x = x - P->L[d] * floor(x / P->L[d]);
+        if (x >= P->L[d]) x -= P->L[d];
+      }
+      w[3 * i + d] = x;
+    }
+  int ncell = C[0] * C[1] * C[2];
+  int* head = (int*)malloc(sizeof(int) * (ncell + 1));
+  int* list = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  int* cid = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int c = 0; c <= ncell; c++) head[c] = 0;
+  for (int i = 0; i < n; i++) {
+    int c[3];
+    for (int d = 0; d < 3; d++) {
+      int ci = (int)floor(w[3 * i + d] / e[d]);
+      if (ci < 0) ci = 0;
+      if (ci > C[d] - 1) ci = C[d] - 1;
+      c[d] = ci;
+    }
+    cid[i] = (c[0] * C[1] + c[1]) * C[2] + c[2];
+    head[cid[i] + 1]++;
+  }
+  for (int c = 0; c < ncell; c++) head[c + 1] += head[c];
+  {
+    int* cur = (int*)malloc(sizeof(int) * (ncell > 0 ? ncell : 1));
+    for (int c = 0; c < ncell; c++) cur[c] = head[c];
+    for (int i = 0; i < n; i++) list[cur[cid[i]]++] = i;
+    free(cur);
+  }
+  double self = or_gamma(p, 0.0) / a;
+  double* Wi = W0 ? (double*)malloc(sizeof(double) * 9 * (n > 0 ? n : 1)) : NULL;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int i = 0; i < n; i++) {
+    double xi[3] = {w[3 * i], w[3 * i + 1], w[3 * i + 2]};
+    int clo[3], chi[3];
+    for (int d = 0; d < 3; d++) {
+      clo[d] = (int)floor((xi[d] - a) / e[d]);
+      chi[d] = (int)floor((xi[d] + a) / e[d]);
+      if (!P->pbc[d]) {
+        if (clo[d] < 0) clo[d] = 0;
+        if (chi[d] > C[d] - 1) chi[d] = C[d] - 1;
+      }
+    }
+    double ph = 0.0, f[3] = {0, 0, 0}, wv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int ux = clo[0]; ux <= chi[0]; ux++)
+      for (int uy = clo[1]; uy <= chi[1]; uy++)
+        for (int uz = clo[2]; uz <= chi[2]; uz++) {
+          int u[3] = {ux, uy, uz}, cw[3];
+          double sh[3];
+          int zero_shift = 1;
+          for (int d = 0; d < 3; d++) {
+            int k = floordiv(u[d], C[d]);
+            cw[d] = u[d] - k * C[d];
+            sh[d] = k * P->L[d];
+            if (k != 0) zero_shift = 0;
+          }
+          int c = (cw[0] * C[1] + cw[1]) * C[2] + cw[2];
+          for (int t = head[c]; t < head[c + 1]; t++) {
+            int j = list[t];
+            if (j == i && zero_shift) continue;
+            double d[3];
+            for (int dd = 0; dd < 3; dd++) d[dd] = w[3 * j + dd] + sh[dd] - xi[dd];
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= a * a) continue;
+            double r = sqrt(r2);
+            ph += q[j] * or_kl(p, a, P->nlev, 0, r);
+            double dk = or_dkl(p, a, P->nlev, 0, r);
+            for (int dd = 0; dd < 3; dd++) f[dd] += q[i] * q[j] * dk * d[dd] / r;
+            if (Wi)
+              for (int aa = 0; aa < 3; aa++)
+                for (int bb = 0; bb < 3; bb++) wv[3 * aa + bb] += -0.5 * q[i] * q[j] * dk * d[aa] * d[bb] / r;
+          }
+        }
+    phi0[i] = ph - q[i] * self;
+    if (F0)
+      for (int dd = 0; dd < 3; dd++) F0[3 * i + dd] = f[dd];
+    if (Wi)
+      for (int k = 0; k < 9; k++) Wi[9 * i + k] = wv[k];
+  }
+  if (W0) {
+    for (int k = 0; k < 9; k++) {
+      double acc = 0.0;
+      for (int i = 0; i < n; i++) acc += Wi[9 * i + k];
+      W0[k] = acc;
+    }
+    free(Wi);
+  }
+  free(w);
+  free(head);
+  free(list);
+  free(cid);
+}
+
+/* Kahan sum of 1/2 sum_i q_i phi_i. */
+double or_energy(int n, const double* q, const double* phi) {
+  double s = 0.0, c = 0.0;
+  for (int i = 0; i < n; i++) {
+    double y = 0.5 * q[i] * phi[i] - c;
+    double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Whole method: Sec. 2 / Eq. u_oneplus_nested_eval and the derivatives of   */
+/* Sec. 3.2.2.                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Grid pass: q~^1 -> restrictions -> e^l = K^l q~^l on every evaluated level
+ * -> prolongation from the top down, e^l += I^T e^(l+1). qlev / elev hold the
+ * grids of all evaluated levels back to back (level 1 first). */
+void or_grid_pass(const or_plan* P, double* qlev, double* elev) {
+  size_t off[OR_MAXLEV + 1];
+  off[0] = 0;
+  for (int l = 1; l <= P->ncomp; l++) off[l] = off[l - 1] + (size_t)lev_size(P, l);
+  for (int l = 1; l < P->ncomp; l++) or_restrict(P, l, qlev + off[l - 1], qlev + off[l]);
+  for (int l = 1; l <= P->ncomp; l++) {
+    int klo[3], ksz[3];
+    or_stencil_box(P, l, klo, ksz);
+    size_t nK = (size_t)ksz[0] * ksz[1] * ksz[2];
+    double* K = (double*)malloc(sizeof(double) * nK);
+    or_stencil_build(P, l, 0, NULL, K);
+    or_stencil_apply(P, l, K, qlev + off[l - 1], elev + off[l - 1]);
+    free(K);
+  }
+  for (int l = P->ncomp - 1; l >= 1; l--) or_prolong_add(P, l, elev + off[l], elev + off[l - 1]);
+}
+
+size_t or_grid_total(const or_plan* P) {
+  size_t s = 0;
+  for (int l = 1; l <= P->ncomp; l++) s += (size_t)lev_size(P, l);
+  return s;
+}
+
+/* Full evaluation. Outputs (any may be NULL except E): phi (n), F (n x 3),
+ * W (3x3), and the level grids qlev / elev (or_grid_total doubles each). */
+void or_msm(const or_plan* P, int n, const double* pos, const double* q, double* E, double* phi, double* F,
+            double* W, double* qlev_out, double* elev_out) {
+  size_t tot = or_grid_total(P);
+  double* qlev = qlev_out ? qlev_out : (double*)malloc(sizeof(double) * (tot > 0 ? tot : 1));
+  double* elev = elev_out ? elev_out : (double*)malloc(sizeof(double) * (tot > 0 ? tot : 1));
+  double* phi0 = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double* phi1 = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double* F0 = (F || W) ? (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1)) : NULL;
+  double* F1 = F ? (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1)) : NULL;
+  double W0[9];
+  or_short_range(P, n, pos, q, phi0, F0, W ? W0 : NULL);
+  if (P->ncomp >= 1) {
+    or_anterp(P, n, pos, q, qlev);
+    or_grid_pass(P, qlev, elev);
+    or_interp(P, n, pos, q, elev, phi1, F1);
+  } else {
+    for (int i = 0; i < n; i++) phi1[i] = 0.0;
+    if (F1) for (int i = 0; i < 3 * n; i++) F1[i] = 0.0;
+  }
+  double* ph = phi ? phi : (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  for (int i = 0; i < n; i++) ph[i] = phi0[i] + phi1[i];
+  *E = or_energy(n, q, ph);
+  if (F)
+    for (int i = 0; i < 3 * n; i++) F[i] = F0[i] + F1[i];
+  if (W) {
+    double Wg[6] = {0, 0, 0, 0, 0, 0};
+    size_t off = 0;
+    for (int l = 1; l <= P->ncomp; l++) {
+      double w6[6];
+      or_grid_virial_level(P, l, qlev + off, w6);
+      for (int c = 0; c < 6; c++) Wg[c] += w6[c];
+      off += (size_t)lev_size(P, l);
+    }
+    int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+    for (int k = 0; k < 9; k++) W[k] = W0[k] + Wg[map[k]];
+  }
+  if (!phi) free(ph);
+  if (!qlev_out) free(qlev);
+  if (!elev_out) free(elev);
+  free(phi0);
+  free(phi1);
+  free(F0);
+  free(F1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact sums used as pins (not the method).                                */
+/* ------------------------------------------------------------------------ */
+
+/* Direct open-boundary Coulomb sum, Eq. generic_pair_potential_sum with k = 1/r:
+ * phi_i = sum_(j != i) q_j / r_ij, F_i = q_i sum_j q_j (r_i - r_j)/r^3,
+ * E = 1/2 sum q_i phi_i. */
+void or_direct_open(int n, const double* pos, const double* q, double* E, double* phi, double* F) {
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0, f[3] = {0, 0, 0};
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      double d[3] = {pos[3 * i] - pos[3 * j], pos[3 * i + 1] - pos[3 * j + 1], pos[3 * i + 2] - pos[3 * j + 2]};
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      ph += q[j] / r;
+      for (int k = 0; k < 3; k++) f[k] += q[i] * q[j] * d[k] / (r * r * r);
+    }
+    phi[i] = ph;
+    if (F)
+      for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
+  }
+  *E = or_energy(n, q, phi);
+}
+
+/* Direct sum of one smooth kernel over all ordered pairs including i == j
+ * (open boundaries): phi_i = sum_j q_j k_l(r_ij) for level l of a plan with
+ * nlev levels. Used to pin the grid part level by level. */
+void or_direct_level(int p, double a, int nlev, int l, int n, const double* pos, const double* q, double* E,
+                     double* phi) {
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0;
+    for (int j = 0; j < n; j++) {
+      double d[3] = {pos[3 * i] - pos[3 * j], pos[3 * i + 1] - pos[3 * j + 1], pos[3 * i + 2] - pos[3 * j + 2]};
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      ph += q[j] * or_kl(p, a, nlev, l, r);
+    }
+    phi[i] = ph;
+  }
+  *E = or_energy(n, q, phi);
+}
+
+/* Ewald sum for an orthorhombic periodic cell with tin-foil boundary
+ * conditions (textbook form): real-space erfc(alpha r)/r over all images with
+ * r < rcut, reciprocal sum over |k| <= kmax of (4 pi / V) exp(-k^2/4alpha^2)/k^2,
+ * self term -2 alpha/sqrt(pi) q_i. phi, F per atom; E = 1/2 sum q phi. */
+void or_ewald(const double* L, int n, const double* pos, const double* q, double alpha, double rcut,
+              double kmax, double* E, double* phi, double* F) {
+  double V = L[0] * L[1] * L[2];
+  int im[3];
+  for (int d = 0; d < 3; d++) im[d] = (int)ceil(rcut / L[d]) + 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0, f[3] = {0, 0, 0};
+    for (int j = 0; j < n; j++) {
+      double d0[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
+      for (int d = 0; d < 3; d++) d0[d] -= L[d] * floor(d0[d] / L[d] + 0.5);
+      for (int nx = -im[0]; nx <= im[0]; nx++)
+        for (int ny = -im[1]; ny <= im[1]; ny++)
+          for (int nz = -im[2]; nz <= im[2]; nz++) {
+            if (j == i && nx == 0 && ny == 0 && nz == 0) continue;
+            double d[3] = {d0[0] + nx * L[0], d0[1] + ny * L[1], d0[2] + nz * L[2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rcut * rcut) continue;
+            double r = sqrt(r2);
+            double er = erfc(alpha * r);
+            ph += q[j] * er / r;
+            double dpot = -er / r2 - 2.0 * alpha / sqrt(M_PI) * exp(-alpha * alpha * r2) / r; /* d/dr erfc(ar)/r */
+            for (int k = 0; k < 3; k++) f[k] += q[i] * q[j] * dpot * d[k] / r;
+          }
+    }
+    phi[i] = ph - 2.0 * alpha / sqrt(M_PI) * q[i];
+    if (F)
+      for (int k = 0; k < 3; k++) F[3 * i + k] = f[k];
+  }
+  /* reciprocal space: k = 2 pi (mx/Lx, my/Ly, mz/Lz) */
+  int mm[3];
+  for (int d = 0; d < 3; d++) mm[d] = (int)floor(kmax * L[d] / (2.0 * M_PI));
+  double* ph_r = (double*)calloc((size_t)n, sizeof(double));
+  double* f_r = (double*)calloc((size_t)3 * n, sizeof(double));
+  long nkx = 2L * mm[0] + 1, nky = 2L * mm[1] + 1, nkz = 2L * mm[2] + 1;
+  long nk = nkx * nky * nkz;
+  /* per-k loop with per-atom work; the per-atom accumulations are done
+   * afterwards in fixed k order to stay deterministic */
+  double* Sre = (double*)malloc(sizeof(double) * nk);
+  double* Sim = (double*)malloc(sizeof(double) * nk);
+  double* Ak = (double*)malloc(sizeof(double) * nk);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (long t = 0; t < nk; t++) {
+    int mx = (int)(t / (nky * nkz)) - mm[0], my = (int)((t / nkz) % nky) - mm[1], mz = (int)(t % nkz) - mm[2];
+    double k[3] = {2 * M_PI * mx / L[0], 2 * M_PI * my / L[1], 2 * M_PI * mz / L[2]};
+    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    if ((mx == 0 && my == 0 && mz == 0) || k2 > kmax * kmax) {
+      Ak[t] = 0.0;
+      Sre[t] = Sim[t] = 0.0;
+      continue;
+    }
+    Ak[t] = 4.0 * M_PI / V * exp(-k2 / (4.0 * alpha * alpha)) / k2;
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < n; j++) {
+      double kr = k[0] * pos[3 * j] + k[1] * pos[3 * j + 1] + k[2] * pos[3 * j + 2];
+      sr += q[j] * cos(kr);
+      si += q[j] * sin(kr);
+    }
+    Sre[t] = sr;
+    Sim[t] = si;
+  }
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0, f[3] = {0, 0, 0};
+    for (long t = 0; t < nk; t++) {
+      if (Ak[t] == 0.0) continue;
+      int mx = (int)(t / (nky * nkz)) - mm[0], my = (int)((t / nkz) % nky) - mm[1], mz = (int)(t % nkz) - mm[2];
+      double k[3] = {2 * M_PI * mx / L[0], 2 * M_PI * my / L[1], 2 * M_PI * mz / L[2]};
+      double kr = k[0] * pos[3 * i] + k[1] * pos[3 * i + 1] + k[2] * pos[3 * i + 2];
+      double c = cos(kr), s = sin(kr);
+      /* Re(S(k) e^{-ik r_i}) and Im(S*(k) e^{ik r_i}) */
+      double re = Sre[t] * c + Sim[t] * s;
+      double imv = Sre[t] * s - Sim[t] * c;
+      ph += Ak[t] * re;
+      for (int d = 0; d < 3; d++) f[d] += Ak[t] * q[i] * k[d] * imv;
+    }
+    ph_r[i] = ph;
+    for (int d = 0; d < 3; d++) f_r[3 * i + d] = f[d];
+  }
+  for (int i = 0; i < n; i++) {
+    phi[i] += ph_r[i];
+    if (F)
+      for (int d = 0; d < 3; d++) F[3 * i + d] += f_r[3 * i + d];
+  }
+  *E = or_energy(n, q, phi);
+  free(ph_r);
+  free(f_r);
+  free(Sre);
+  free(Sim);
+  free(Ak);
+}

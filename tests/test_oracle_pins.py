@@ -1,0 +1,454 @@
+"""Pins of the FP64 oracle against values that do not come from the oracle.
+
+Each test checks one part of the oracle against a closed form, a textbook
+value, a mathematical identity of the method, an exact direct sum, an Ewald
+sum, the rock-salt Madelung constant or finite differences. A plausible slip
+(a dropped term, a wrong sign or index, a transposed operand) in any oracle
+function fails at least one of them.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2510_05961_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ----------------------------------------------------------------- softening / splitting
+def test_gamma_closed_forms(oracle):
+    # gamma(0) = sum_k binom(2k,k)/4^k, k < p: 35/16, 693/256, 6435/2048
+    assert oracle.gamma(4, 0.0) == pytest.approx(35 / 16, rel=1e-15)
+    assert oracle.gamma(6, 0.0) == pytest.approx(693 / 256, rel=1e-15)
+    assert oracle.gamma(8, 0.0) == pytest.approx(6435 / 2048, rel=1e-15)
+    # order 3 is the classic C^2 softening 15/8 - 5/4 rho^2 + 3/8 rho^4
+    for rho in np.linspace(0, 0.999, 17):
+        assert oracle.gamma(3, rho) == pytest.approx(15 / 8 - 5 / 4 * rho ** 2 + 3 / 8 * rho ** 4, rel=1e-14)
+    for p in (4, 6, 8):
+        for rho in (1.0, 1.3, 7.0):
+            assert oracle.gamma(p, rho) == pytest.approx(1 / rho, rel=1e-15)
+            assert oracle.dgamma(p, rho) == pytest.approx(-1 / rho ** 2, rel=1e-15)
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_gamma_smooth_join(oracle, p):
+    # gamma is C^(p-1) at rho = 1: on [0,1) it is a polynomial of degree 2p-2;
+    # recover it from samples and compare its derivatives at 1 with those of
+    # 1/rho, (-1)^k k!. Orders 0..p-1 agree, order p does not.
+    deg = 2 * p - 2
+    xs = 0.5 - 0.5 * np.cos(np.pi * (np.arange(deg + 1) + 0.5) / (deg + 1))
+    ys = np.array([oracle.gamma(p, x) for x in xs])
+    poly = np.polynomial.Polynomial.fit(xs, ys, deg).convert()
+    for k in range(p + 1):
+        dk = poly.deriv(k)(1.0) if k else poly(1.0)
+        ref = (-1) ** k * math.factorial(k)
+        if k < p:
+            assert dk == pytest.approx(ref, rel=1e-7, abs=1e-7), (k, dk, ref)
+        else:
+            assert abs(dk - ref) > 1e-3 * abs(ref)
+    # derivative function against a central difference
+    for rho in (0.1, 0.5, 0.9):
+        fd = (oracle.gamma(p, rho + 1e-6) - oracle.gamma(p, rho - 1e-6)) / 2e-6
+        assert oracle.dgamma(p, rho) == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+@pytest.mark.parametrize("nlev", [1, 3, 6])
+def test_splitting_telescopes_to_coulomb(oracle, p, nlev):
+    # Eq. kernel_splitting: sum_l k_l(r) = 1/r, and sum_(l>=1) k_l(0) = gamma(0)/a
+    a = 3.7
+    for r in np.geomspace(0.05, 400.0, 37):
+        s = sum(oracle.kl(p, a, nlev, l, r) for l in range(nlev + 1))
+        assert s == pytest.approx(1.0 / r, rel=1e-13)
+        ds = sum(oracle.dkl(p, a, nlev, l, r) for l in range(nlev + 1))
+        assert ds == pytest.approx(-1.0 / r ** 2, rel=1e-11)
+    self_sum = sum(oracle.kl(p, a, nlev, l, 0.0) for l in range(1, nlev + 1))
+    assert self_sum == pytest.approx(oracle.gamma(p, 0.0) / a, rel=1e-14)
+    # finite ranges: k_0 vanishes from a, k_l from 2^l a (l < L)
+    assert oracle.kl(p, a, nlev, 0, a) == 0.0
+    for l in range(1, nlev):
+        assert oracle.kl(p, a, nlev, l, 2 ** l * a * 1.0000001) == 0.0
+        assert oracle.kl(p, a, nlev, l, 2 ** l * a * 0.99) != 0.0
+
+
+# ----------------------------------------------------------------- B-splines, J
+@pytest.mark.parametrize("row", _golden_lines("bspline_integer_values.txt"))
+def test_bspline_integer_values(oracle, row):
+    p = int(row[0])
+    for t, v in enumerate(row[1:]):
+        assert oracle.bspline(p, t) == pytest.approx(float(Fraction(v)), rel=1e-14, abs=1e-16)
+        assert oracle.bspline(p, -t) == pytest.approx(float(Fraction(v)), rel=1e-14, abs=1e-16)
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_bspline_partition_of_unity_and_derivative(oracle, p):
+    rng = np.random.default_rng(p)
+    for u in rng.uniform(-5, 5, 25):
+        s = sum(oracle.bspline(p, u - m) for m in range(-12, 13))
+        assert s == pytest.approx(1.0, abs=1e-14)
+        ds = sum(oracle.dbspline(p, u - m) for m in range(-12, 13))
+        assert abs(ds) < 1e-13
+        fd = (oracle.bspline(p, u + 1e-6) - oracle.bspline(p, u - 1e-6)) / 2e-6
+        assert oracle.dbspline(p, u) == pytest.approx(fd, abs=1e-8)
+    # unit integral and support (-p/2, p/2)
+    xs = np.linspace(-p / 2, p / 2, 4001)
+    vals = np.array([oracle.bspline(p, x) for x in xs])
+    assert np.trapezoid(vals, xs) == pytest.approx(1.0, abs=1e-6)
+    assert oracle.bspline(p, p / 2) == 0.0 and oracle.bspline(p, p / 2 + 0.3) == 0.0
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_two_scale_relation(oracle, p):
+    # Phi_p(x/2) = sum_k J_k Phi_p(x - k): the relation restriction rests on
+    J = oracle.J(p)
+    assert J[0::2].sum() == pytest.approx(1.0, abs=1e-15)
+    assert J[1::2].sum() == pytest.approx(1.0, abs=1e-15)
+    for x in np.linspace(-p, p, 41):
+        rhs = sum(J[k + p // 2] * oracle.bspline(p, x - k) for k in range(-p // 2, p // 2 + 1))
+        assert oracle.bspline(p, x / 2) == pytest.approx(rhs, abs=1e-14)
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_omega_polynomial_reproduction(oracle, p):
+    """1-D kernel interpolation of a polynomial f(x - y) of degree < p is exact.
+
+    S(x,y) = sum_m sum_n Phi(x-m) K_(m-n) Phi(y-n) with K_k = sum_t omega'_t f(k-t)
+    (Eq. kernel_stencil_by_conv_with_universal_coeff in one dimension). Exactness
+    for degree < p is the approximation order the quasi-interpolation must keep;
+    degree p is not reproduced, so the sequence is no longer than it needs to be.
+    """
+    om = oracle.omega(p)
+    r = p // 2 - 1
+    rng = np.random.default_rng(10 + p)
+    pts = rng.uniform(-3, 3, size=(12, 2))
+
+    def S(f, x, y):
+        mx = np.arange(math.floor(x) - p // 2 + 1, math.floor(x) + p // 2 + 1)
+        ny = np.arange(math.floor(y) - p // 2 + 1, math.floor(y) + p // 2 + 1)
+        tot = 0.0
+        for m in mx:
+            for n in ny:
+                K = sum(om[t + r] * f(m - n - t) for t in range(-r, r + 1))
+                tot += oracle.bspline(p, x - m) * K * oracle.bspline(p, y - n)
+        return tot
+
+    for j in range(p):
+        f = lambda t, j=j: float(t) ** j
+        for x, y in pts:
+            assert S(f, x, y) == pytest.approx((x - y) ** j, abs=1e-10 * (1 + abs(x - y) ** j))
+    f = lambda t: float(t) ** p
+    errs = [abs(S(f, x, y) - (x - y) ** p) for x, y in pts]
+    assert max(errs) > 1e-6
+
+
+# ----------------------------------------------------------------- grids
+def _random_atoms(n, side, seed, neutral=True):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0, side, size=(n, 3))
+    q = rng.normal(size=n)
+    if neutral:
+        q -= q.mean()
+    return pos, q
+
+
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0), (1, 1, 0)])
+@pytest.mark.parametrize("p", [4, 6])
+def test_restriction_is_exact_anterpolation(oracle, pbc, p):
+    # anterpolating with the level-2 basis (spacing 2h) equals restricting the
+    # level-1 grid charge: the translation operator of Sec. 2 is exact for B-splines
+    side = 17.0
+    pos, q = _random_atoms(60, side, 3)
+    P1 = oracle.make_plan((side,) * 3, pbc, 0, 4.0, p, grid_override=(16, 16, 16))
+    P2 = oracle.make_plan((side,) * 3, pbc, 0, 4.0, p, grid_override=(8, 8, 8))
+    assert P1.level_shape(2) == P2.level_shape(1) and P1.level_lo(2) == P2.level_lo(1)
+    g1 = oracle.anterp(P1, pos, q)
+    g2 = oracle.restrict(P1, 1, g1)
+    d = oracle.anterp(P2, pos, q)
+    assert np.abs(g2 - d).max() <= 1e-13 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0), (0, 1, 1)])
+def test_charge_conservation_and_adjoint(oracle, pbc):
+    side = 23.0
+    pos, q = _random_atoms(80, side, 4, neutral=False)
+    P = oracle.make_plan((side,) * 3, pbc, 2.0, 5.0, 4)
+    g = oracle.anterp(P, pos, q)
+    levels = [g]
+    for l in range(1, P.ncomp):
+        levels.append(oracle.restrict(P, l, levels[-1]))
+    for g in levels:
+        assert g.sum() == pytest.approx(q.sum(), rel=1e-12, abs=1e-12)
+    rng = np.random.default_rng(5)
+    for l in range(1, P.ncomp):
+        f = rng.normal(size=P.level_shape(l))
+        c = rng.normal(size=P.level_shape(l + 1))
+        lhs = (oracle.restrict(P, l, f) * c).sum()
+        rhs = (f * oracle.prolong_add(P, l, c, np.zeros_like(f))).sum()
+        assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_plan_rules(oracle):
+    P = oracle.plan_for(W.open_cluster())
+    s = oracle.plan_summary(P)
+    assert s["nlev"] == 3 and s["M"] == [12, 12, 12]
+    assert s["lo"] == [[-2] * 3, [-2] * 3, [-2] * 3] and s["n"] == [[17] * 3, [11] * 3, [8] * 3]
+    assert s["R"] == [8] * 3
+    # 1M-atom sweep point: M = 128, 8 levels, top dropped
+    L = (1024000 / 0.1) ** (1 / 3)
+    P = oracle.make_plan((L,) * 3, (1, 1, 1), 2.0, 8.0, 4)
+    assert (P.M[0], P.nlev, P.ncomp, P.R[0]) == (128, 8, 7, 10)
+    with pytest.raises(ValueError):
+        oracle.make_plan((10, 20, 10), (1, 1, 1), 1.0, 3.0, 4)  # unequal periodic grids
+    with pytest.raises(ValueError):
+        oracle.make_plan((10, 10, 10), (0, 0, 0), 1.0, 3.0, 5)  # odd order
+
+
+@pytest.mark.parametrize("pbc", [(0, 0, 0), (1, 1, 1)])
+def test_stencil_symmetry_and_level_scaling(oracle, pbc):
+    side = 19.0
+    P = oracle.make_plan((side,) * 3, pbc, 1.2, 3.0, 4)
+    K1, lo1 = oracle.stencil(P, 1)
+    if not any(pbc):
+        assert np.allclose(K1, K1[::-1, ::-1, ::-1], rtol=1e-14, atol=0)
+        assert np.allclose(K1, np.transpose(K1, (1, 0, 2)), rtol=1e-14, atol=0)
+    for l in range(2, P.ncomp if not any(pbc) else P.ncomp + 1):
+        if l == P.nlev:
+            continue
+        Kl, _ = oracle.stencil(P, l)
+        if not any(pbc):
+            assert np.abs(Kl - K1 / 2 ** (l - 1)).max() <= 1e-14 * np.abs(K1).max()
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_level_interpolation_converges_at_order_p(oracle, p):
+    # level-1 grid energy 1/2 q~^T K^1 q~ against the direct sum of k_1 over all
+    # pairs (i == j included, Eq. U_oneplus): the error falls by ~2^p per halving of h
+    side, a = 12.0, 5.0
+    pos, q = _random_atoms(70, side, 6)
+    Ue, _ = oracle.direct_level(p, a, 3, 1, pos, q)
+    errs = []
+    for h in (1.25, 0.625):
+        P = oracle.make_plan((side,) * 3, (0, 0, 0), h, a, p, 3)
+        g = oracle.anterp(P, pos, q)
+        K, _ = oracle.stencil(P, 1)
+        e = oracle.stencil_apply(P, 1, K, g)
+        errs.append(abs(0.5 * (g * e).sum() - Ue) / abs(Ue))
+    assert errs[0] / errs[1] > 0.6 * 2 ** p, errs
+
+
+# ----------------------------------------------------------------- short range
+def test_short_range_against_brute_force_images(oracle):
+    # cell > a and cell < a (self images, a > L/2): brute force over images
+    for side, a in ((9.0, 4.0), (5.0, 6.5)):
+        pos, q = _random_atoms(40, side, 8)
+        P = oracle.make_plan((side,) * 3, (1, 1, 1), 1.0, a, 4)
+        phi0, F0, W0 = oracle.short_range(P, pos, q)
+        nimg = int(math.ceil(a / side)) + 1
+        phi = np.zeros(40)
+        F = np.zeros((40, 3))
+        Wb = np.zeros((3, 3))
+        for i in range(40):
+            for j in range(40):
+                for n in np.ndindex(*(2 * nimg + 1,) * 3):
+                    sh = (np.array(n) - nimg) * side
+                    if i == j and not sh.any():
+                        continue
+                    d = pos[j] + sh - pos[i]
+                    r = np.linalg.norm(d)
+                    if r >= a:
+                        continue
+                    phi[i] += q[j] * oracle.kl(4, a, P.nlev, 0, r)
+                    dk = oracle.dkl(4, a, P.nlev, 0, r)
+                    F[i] += q[i] * q[j] * dk * d / r
+                    Wb += -0.5 * q[i] * q[j] * dk * np.outer(d, d) / r
+            phi[i] -= q[i] * oracle.gamma(4, 0.0) / a
+        assert np.allclose(phi0, phi, rtol=1e-12, atol=1e-12)
+        assert np.allclose(F0, F, rtol=1e-11, atol=1e-11)
+        assert np.allclose(W0, Wb, rtol=1e-11, atol=1e-11)
+        assert np.abs(F0.sum(0)).max() < 1e-10 * np.abs(F0).max()  # Newton's third law
+
+
+def test_binning_contract(oracle):
+    # the FP32 cell-index contract written out independently in numpy float32
+    for w in (W.random_box(3000, seed=11), W.open_cluster(n=500, seed=12)):
+        P = oracle.plan_for(w)
+        cid, start, perm, st = oracle.bin_atoms(P, w.pos, w.q)
+        assert st == 0
+        C = np.array([P.C[d] for d in range(3)])
+        c = np.zeros((w.n, 3), np.int64)
+        for d in range(3):
+            inv = np.float32(1.0 / w.cell[d])
+            s = w.pos[:, d].astype(np.float32) * inv
+            if w.pbc[d]:
+                s = (s - np.floor(s)).astype(np.float32)
+                s[s >= np.float32(1.0)] = np.float32(0.0)
+            t = (s * np.float32(C[d])).astype(np.float32)
+            c[:, d] = np.minimum(t.astype(np.int64), C[d] - 1)
+        ref = (c[:, 0] * C[1] + c[:, 1]) * C[2] + c[:, 2]
+        assert np.array_equal(cid, ref)
+        assert np.array_equal(perm, np.lexsort((np.arange(w.n), ref)))
+        assert np.array_equal(start, np.concatenate([[0], np.cumsum(np.bincount(ref, minlength=C.prod()))]))
+    # out-of-cell and non-finite inputs are flagged
+    w = W.open_cluster(n=50)
+    pos = w.pos.copy()
+    pos[3, 1] = -1.0
+    P = oracle.plan_for(w)
+    assert oracle.bin_atoms(P, pos, w.q)[3] & oracle.ST_OUTSIDE
+    pos[3, 1] = np.nan
+    assert oracle.bin_atoms(P, pos, w.q)[3] & oracle.ST_NONFINITE
+
+
+# ----------------------------------------------------------------- whole method
+def test_open_cluster_against_direct_coulomb(oracle):
+    w = W.open_cluster()
+    pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+    E0, phi0, F0 = oracle.direct_open(pos, q)
+    errs = {}
+    for h, p in ((2.5, 4), (1.25, 4), (1.25, 6)):
+        P = oracle.make_plan(w.cell, w.pbc, h, w.a, p)
+        r = oracle.msm(P, pos, q, virial=False)
+        ferr = np.sqrt(((r["F"] - F0) ** 2).sum(1).mean() / (F0 ** 2).sum(1).mean())
+        perr = np.sqrt(((r["phi"] - phi0) ** 2).mean() / (phi0 ** 2).mean())
+        errs[(h, p)] = (abs(r["E"] - E0) / abs(E0), ferr, perr)
+    assert errs[(2.5, 4)][1] < 5e-3
+    assert errs[(1.25, 4)][1] < errs[(2.5, 4)][1] / 5
+    assert errs[(1.25, 4)][0] < errs[(2.5, 4)][0] / 5
+    assert errs[(1.25, 6)][1] < errs[(1.25, 4)][1]
+    assert errs[(1.25, 4)][1] < 5e-4
+
+
+def test_periodic_against_ewald(oracle):
+    pos, q = _random_atoms(300, 14.0, 9)
+    cell = (14.0,) * 3
+    Ee, phie, Fe = oracle.ewald_auto(cell, pos, q)
+    # the error falls as h halves (M = 8, 16, 32) and, once the grid resolves
+    # the kernels, as p rises
+    errs = {}
+    for M, p in ((8, 4), (16, 4), (32, 4), (32, 6)):
+        P = oracle.make_plan(cell, (1, 1, 1), 0, 6.0, p, grid_override=(M, M, M))
+        r = oracle.msm(P, pos, q, virial=False)
+        ferr = np.sqrt(((r["F"] - Fe) ** 2).sum(1).mean() / (Fe ** 2).sum(1).mean())
+        errs[(M, p)] = (abs(r["E"] - Ee) / abs(Ee), ferr)
+    for a, b in (((8, 4), (16, 4)), ((16, 4), (32, 4)), ((32, 4), (32, 6))):
+        assert errs[b][0] < errs[a][0] / 3 and errs[b][1] < errs[a][1] / 3, errs
+    assert errs[(32, 6)][1] < 1e-4
+
+
+def test_ewald_madelung(oracle):
+    ref = float(_golden_lines("madelung_nacl.txt")[0][0])
+    pos, q, L = W.nacl_crystal(1)
+    E, phi, F = oracle.ewald_auto((L,) * 3, pos, q, rcut=0.5)
+    assert -E * 0.5 / 4 == pytest.approx(ref, abs=1e-6)
+
+
+def test_msm_madelung(oracle):
+    # Sec. 4.1: p = 6 in FP64 reaches 7-8 decimals of the Madelung constant
+    ref = float(_golden_lines("madelung_nacl.txt")[0][0])
+    pos, q, L = W.nacl_crystal(1)
+    P = oracle.make_plan((L,) * 3, (1, 1, 1), 0, 4.0 * 0.5 * L, 6, grid_override=(16, 16, 16))  # a = 4 d_min, h = d_min / 8
+    r = oracle.msm(P, pos, q, virial=True)
+    M = -r["E"] * 0.5 / 4
+    assert M == pytest.approx(ref, abs=1e-6)
+    assert np.abs(r["F"]).max() < 1e-12
+    # cubic symmetry and Coulomb homogeneity: W = E/3 * identity (a not scaled: approx)
+    assert np.allclose(r["W"], np.eye(3) * r["E"] / 3, rtol=5e-5, atol=5e-5 * abs(r["E"]))
+
+
+def _small_periodic():
+    pos, q = _random_atoms(40, 9.0, 13)
+    return pos, q, (9.0, 9.0, 9.0)
+
+
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0), (1, 1, 0)])
+def test_exact_invariants(oracle, pbc):
+    rng = np.random.default_rng(14)
+    pos, q, cell = _small_periodic()
+    if not any(pbc) or pbc == (1, 1, 0):
+        pos = np.clip(pos, 0.5, 8.5)
+    P = oracle.make_plan(cell, pbc, 1.2, 3.5, 4)
+    r = oracle.msm(P, pos, q)
+    assert r["E"] == pytest.approx(0.5 * (q * r["phi"]).sum(), rel=1e-14)
+    # E(lambda q) = lambda^2 E
+    assert oracle.msm(P, pos, 2.5 * q, forces=False, virial=False)["E"] == pytest.approx(6.25 * r["E"], rel=1e-13)
+    # dE/dq = phi and F = -dE/dr (central differences of the MSM energy)
+    for i in rng.choice(40, 5, replace=False):
+        dq = 1e-5
+        qp, qm = q.copy(), q.copy()
+        qp[i] += dq
+        qm[i] -= dq
+        fd = (oracle.msm(P, pos, qp, False, False)["E"] - oracle.msm(P, pos, qm, False, False)["E"]) / (2 * dq)
+        assert fd == pytest.approx(r["phi"][i], rel=1e-7, abs=1e-8)
+        for d in range(3):
+            dx = 1e-5
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += dx
+            pm[i, d] -= dx
+            fd = (oracle.msm(P, pp, q, False, False)["E"] - oracle.msm(P, pm, q, False, False)["E"]) / (2 * dx)
+            assert -fd == pytest.approx(r["F"][i, d], rel=1e-5, abs=1e-6)
+    # a permutation of atoms permutes the outputs
+    perm = rng.permutation(40)
+    rp = oracle.msm(P, pos[perm], q[perm])
+    assert rp["E"] == pytest.approx(r["E"], rel=1e-13)
+    assert np.allclose(rp["phi"], r["phi"][perm], rtol=1e-12, atol=1e-12)
+    assert np.allclose(rp["F"], r["F"][perm], rtol=1e-11, atol=1e-11)
+
+
+def test_half_cell_translation_invariance(oracle):
+    # shifting a periodic system by L/2 moves every evaluated level by whole points
+    pos, q, cell = _small_periodic()
+    P = oracle.make_plan(cell, (1, 1, 1), 1.2, 3.5, 4)
+    r = oracle.msm(P, pos, q)
+    for d in range(3):
+        sh = pos.copy()
+        sh[:, d] += 4.5
+        rs = oracle.msm(P, sh, q)
+        assert rs["E"] == pytest.approx(r["E"], rel=1e-12)
+        assert np.allclose(rs["F"], r["F"], rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0)])
+def test_virial_against_strain_differences(oracle, pbc):
+    """W = -dE/d eps under r -> (1+eps) r, A -> (1+eps) A (grid coordinates fixed)."""
+    pos, q, cell = _small_periodic()
+    if not any(pbc):
+        pos = np.clip(pos, 0.5, 8.5)
+    P = oracle.make_plan(cell, pbc, 0, 3.5, 4, grid_override=(8, 8, 8))
+    r = oracle.msm(P, pos, q)
+    for d in range(3):
+        es = []
+        for s in (+1, -1):
+            eps = 1e-6 * s
+            c2 = list(cell)
+            c2[d] *= 1 + eps
+            p2 = pos.copy()
+            p2[:, d] *= 1 + eps
+            P2 = oracle.make_plan(c2, pbc, 0, 3.5, 4, grid_override=(8, 8, 8))
+            es.append(oracle.msm(P2, p2, q, False, False)["E"])
+        assert -(es[0] - es[1]) / 2e-6 == pytest.approx(r["W"][d, d], rel=1e-5, abs=1e-7)
+    assert np.allclose(r["W"], r["W"].T, rtol=1e-12, atol=1e-12)
+
+
+def test_strain_derivative_stencils(oracle):
+    # off-diagonal dK/d eps against sheared stencils: dK_xy = d K(G) / d eps at G = 1 + eps (xy + yx)/2
+    P = oracle.make_plan((11.0,) * 3, (0, 0, 0), 1.1, 2.5, 4, levels=3)
+    for which, (a, b) in zip(range(1, 7), [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        dK, _ = oracle.stencil(P, 1, which)
+        eps = 1e-6
+        G = np.eye(3)
+        G[a, b] += eps / (2 if a != b else 1)
+        G[b, a] += eps / 2 if a != b else 0
+        Kp, _ = oracle.stencil(P, 1, 0, G)
+        G = np.eye(3)
+        G[a, b] -= eps / (2 if a != b else 1)
+        G[b, a] -= eps / 2 if a != b else 0
+        Km, _ = oracle.stencil(P, 1, 0, G)
+        fd = (Kp - Km) / (2 * eps)
+        assert np.abs(fd - dK).max() <= 1e-6 * np.abs(dK).max()
