@@ -1,0 +1,361 @@
+"""Benchmark: MSM forward + backward (energy, forces, dE/dq, virial) throughput.
+
+Workload (default): the 1M-atom point of the linear-scaling sweep: a periodic
+cube at 0.1 atoms/A^3 with N = 1,024,000 uniform random +/-1 charges
+(L = 217.15 A), B-spline order p = 4, h = 2 A, cutoff a = 8 A (M = 128,
+8 levels). One step = one msm_forward (forces + virial bookkeeping) and one
+msm_backward (dE/dr, dE/dq, virial) on that system, inputs resident in HBM.
+L2 (129 MB) is flushed before every timed step by writing a 256 MB buffer.
+
+Multi-GPU: replicas only -- every rank evaluates its own 1M-atom system (the
+single-system path has no exchange step); value = all ranks' atoms / max time.
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on
+the host cores, on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MSM fwd+bwd atoms/s at 1M atoms (FP32 vs FP64 oracle), % roofline, batch speedup"
+N_HEADLINE = 1_024_000
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--atoms", type=int, default=N_HEADLINE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-atoms", type=int, default=128_000)
+    return ap.parse_args()
+
+
+def workload_desc(n):
+    L = (n / 0.1) ** (1 / 3)
+    return ("periodic cube, %d atoms at 0.1/A^3 (L=%.2f A), uniform positions, +/-1 charges; p=4, h=2, a=8; "
+            "fwd+bwd: E, F, dE/dq, virial" % (n, L))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline helpers
+def stencil_flops(plan_params, info):
+    """Algorithmic FLOPs of one stencil launch: 2 x sum over levels of points x stencil nonzeros."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2510_05961_gb300 import _lib
+    lib = _lib.load()
+    total = 0.0
+    for l in range(1, info["ncomp"] + 1):
+        lo = (C.c_int * 3)()
+        sz = (C.c_int * 3)()
+        _lib.check(lib.msm_plan_stencil(C.byref(plan_params), l, 0, None, 0, lo, sz))
+        out = np.zeros(sz[0] * sz[1] * sz[2], np.float32)
+        _lib.check(lib.msm_plan_stencil(C.byref(plan_params), l, 0, out.ctypes.data_as(C.c_void_p), out.size, lo, sz))
+        n = info["n"][l - 1]
+        total += 2.0 * n[0] * n[1] * n[2] * np.count_nonzero(out)
+    return total
+
+
+def short_flops(n, density, a):
+    """Algorithmic FLOPs of the short-range kernel with forces and virial: in-cutoff
+    ordered pairs of uniform random positions (n * density * 4/3 pi a^3) times
+    54 FLOPs per pair (FMA = 2)."""
+    return n * density * 4.0 / 3.0 * math.pi * a ** 3 * 54.0
+
+
+def stencil_source_sha():
+    p = os.path.join(ROOT, "paper_2510_05961_gb300", "csrc", "k_stencil.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def read_traffic(kernel_key):
+    """DRAM bytes per launch recorded from an ncu capture, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel_key)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for ln in open(path):
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != stencil_source_sha():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(n_sample):
+    """Time the FP64 oracle's forward+backward on a sample of the workload; atoms/s."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2510_05961_gb300 import workloads as W
+    O.build()
+    w = W.random_box(n_sample)
+    P = O.plan_for(w)
+    pos = w.pos.astype(np.float64)
+    q = w.q.astype(np.float64)
+    t0 = time.perf_counter()
+    O.msm(P, pos, q, forces=True, virial=True)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n_sample / dt, dt, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample = 16_000  # same density, h_1 = 1.70 A and stencil radius as the 1M-atom point
+    for _ in range(args.warmup):
+        oracle_sample(n_sample)
+    tot = 0.0
+    for _ in range(args.steps):
+        _, dt, cores = oracle_sample(n_sample)
+        tot += dt
+    ms = tot / args.steps * 1e3
+    val = n_sample / (ms / 1e3)
+    sample = ("oracle fwd+bwd on %d atoms of the same workload (0.1/A^3, p=4, h=2 -> h_1=1.70 A, a=8), "
+              "one evaluation per step" % n_sample)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "atoms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(N_HEADLINE), "sample_atoms": n_sample},
+        "cpu_baseline": {"value": val, "unit": "atoms/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2510_05961_gb300 import Plan
+    from paper_2510_05961_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2510_05961_gb300 import build
+    build.build()
+
+    n = args.atoms
+    w = W.random_box(n, seed=3010 + rank)
+    plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, 0, max_atoms=n, device=dev)
+    info = plan.info()
+    pos = torch.from_numpy(w.pos).to(dev)
+    q = torch.from_numpy(w.q).to(dev)
+    g = torch.ones(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gp = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gq = torch.empty(n, dtype=torch.float32, device=dev)
+    Wv = torch.empty(9, dtype=torch.float64, device=dev)
+    import ctypes as C
+
+    from paper_2510_05961_gb300 import _lib
+    lib = _lib.load()
+    stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream)
+    ws = C.c_void_p(plan.workspace.data_ptr())
+
+    def step():
+        _lib.check(lib.msm_forward(plan.handle, ws, plan.workspace.numel(), n, C.c_void_p(pos.data_ptr()),
+                                   C.c_void_p(q.data_ptr()), C.c_void_p(E.data_ptr()), None, C.c_void_p(F.data_ptr()),
+                                   _lib.MSM_WANT_FORCES | _lib.MSM_WANT_VIRIAL, sp))
+        _lib.check(lib.msm_backward(plan.handle, ws, C.c_void_p(g.data_ptr()), C.c_void_p(gp.data_ptr()),
+                                    C.c_void_p(gq.data_ptr()), C.c_void_p(Wv.data_ptr()), sp))
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert plan.status() == 0, "device status flags set"
+
+    plan.profile(True)
+    phase_tot = {}
+    launches = 0
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+        ph, nl = plan.profile_read() if i < args.steps else ({}, 0)
+        for k, v in ph.items():
+            phase_tot[k] = phase_tot.get(k, 0.0) + v
+        launches += nl
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    plan.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1e3)
+
+    # end-to-end through the public API with host buffers (copies in the timed region)
+    pos_h = torch.from_numpy(w.pos).pin_memory()
+    q_h = torch.from_numpy(w.q).pin_memory()
+    outs = (torch.empty(1, dtype=torch.float64, pin_memory=True), torch.empty((n, 3), dtype=torch.float32,
+                                                                              pin_memory=True),
+            torch.empty(n, dtype=torch.float32, pin_memory=True), torch.empty((3, 3), dtype=torch.float64,
+                                                                              pin_memory=True))
+    for _ in range(2):
+        plan.evaluate_host(pos_h, q_h, pinned_out=outs)
+    e2e_steps = max(3, min(args.steps, 10))
+    t_e2e = 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.evaluate_host(pos_h, q_h, pinned_out=outs)
+        t_e2e += time.perf_counter() - t0
+    ms_e2e = t_e2e / e2e_steps * 1e3
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_val = world * n / (ms_e2e / 1e3)
+
+    # roofline of the dominant kernel (by measured phase time)
+    ph_ms = {k: v / args.steps for k, v in phase_tot.items()}
+    peak_fp32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    st_flops = stencil_flops(plan.params, info)
+    sr_flops = short_flops(n, 0.1, w.a)
+    cand = {"stencil": (st_flops, ph_ms.get("stencil", 0.0)), "short": (sr_flops, ph_ms.get("short", 0.0))}
+    dom = max(cand, key=lambda k: cand[k][1])
+    fl, tms = cand[dom]
+    achieved = fl / (tms / 1e3) / 1e12 if tms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": {"stencil": "k_stencil_ball (level stencils)",
+                                        "short": "k_short (short-range pairs)"}[dom],
+            "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+            "traffic": read_traffic("stencil_ball_1M") if dom == "stencil" else None,
+            "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (no FP32 peak in MEASURED_PEAKS.json)",
+            "phase_ms": {k: round(v, 4) for k, v in ph_ms.items()},
+            "algorithmic_flops": {"stencil": st_flops, "short": sr_flops}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        val, dt, cores = oracle_sample(args.cpu_sample_atoms)
+        cpu = {"value": val, "unit": "atoms/s", "cores": cores, "kind": "oracle",
+               "sample": "one oracle fwd+bwd (E, F, dE/dq, virial) on %d atoms of the same workload (same density, "
+                         "p, h, a; h_1 = 1.70 A as at 1M), %.1f s" % (args.cpu_sample_atoms, dt)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(n), "atoms_per_gpu": n, "parallelism": "replicas",
+                       "l2": "flushed (256 MB write) before every step", "levels": info["nlev"],
+                       "M": info["M"][0]},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": e2e_val, "unit": "atoms/s", "h2d_bytes_per_step": n * 16,
+                    "d2h_bytes_per_step": n * 16 + 8 + 72, "ms_per_step": ms_e2e},
+            "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

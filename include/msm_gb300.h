@@ -1,0 +1,211 @@
+/*
+ * msm_gb300.h -- C ABI of the GB300 (sm_103a) multilevel summation method.
+ *
+ * The method is the B-spline multilevel summation method (MSM) of arXiv
+ * 2510.05961 (msmJAX), Sec. 2 and 3: the Coulomb energy of N point charges,
+ * U = 1/2 sum_i sum_(j != i) q_i q_j / r_ij (Eq. generic_pair_potential_sum),
+ * split into a short-range part U^0 evaluated pair by pair (Eq. U_zero) and a
+ * long-range part U^(1+) evaluated on a hierarchy of grids (Eqs. grid_charge,
+ * u_oneplus_nested_eval, uoneplus_interpolation). Units are those of the
+ * inputs; the Coulomb constant is 1 (Sec. 3.6).
+ *
+ * Conventions shared by every call:
+ *  - Plain C types only. Device pointers point to CUDA device memory of the
+ *    current device; host pointers are marked "host".
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call is stream-ordered and returns without waiting for the GPU,
+ *    except msm_status, which synchronises the stream.
+ *  - The caller owns and allocates every input, output and workspace buffer.
+ *    A plan owns only its host settings and its device constant tables
+ *    (stencils, work lists), allocated by msm_plan_create and freed by
+ *    msm_plan_destroy.
+ *  - Return value: MSM_OK (0) or an MSM_ERR_* code; msm_last_error() then
+ *    holds a message (per thread). Problems found on the GPU while running
+ *    (an atom outside an open cell, a non-finite input) do not fail the call:
+ *    they set bits in a device status word that msm_status reads; the
+ *    outputs of such a call are unspecified.
+ *  - Positions are Cartesian, row-major n x 3 (x,y,z per atom), float32.
+ *    Along a periodic axis any value is allowed (it is wrapped); along an open
+ *    axis 0 <= x <= L is required.
+ *  - All arithmetic on the GPU is float32 with float64 final sums of the
+ *    energy and the virial.
+ */
+#ifndef MSM_GB300_H
+#define MSM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define MSM_OK 0
+#define MSM_ERR_INVALID_ARG 1  /* a NULL pointer, a size out of range, bad settings */
+#define MSM_ERR_UNSUPPORTED 2  /* settings outside what this build implements */
+#define MSM_ERR_CUDA 3         /* a CUDA runtime call failed */
+#define MSM_ERR_NO_FORWARD 4   /* msm_backward without a prior msm_forward on the workspace */
+#define MSM_ERR_CAPACITY 5     /* n above the plan's max_atoms, or a workspace too small */
+
+/* bits of the device status word (msm_status) */
+#define MSM_DEV_OUT_OF_CELL 1  /* an atom outside [0, L] along an open axis */
+#define MSM_DEV_NONFINITE 2    /* a NaN or infinite position or charge */
+
+/* msm_forward flags */
+#define MSM_WANT_FORCES 1      /* compute forces in the forward pass */
+#define MSM_WANT_VIRIAL 2      /* keep what msm_backward needs for the virial */
+
+typedef struct msm_plan_s* msm_plan;
+typedef struct msm_batch_s* msm_batch;
+
+/* Settings of one system; the arguments of the paper's set_up_msm_params
+ * (Sec. 3.5): cell, periodicity, level-one spacing, level-zero cutoff, order.
+ *  cell[9]        row-major 3x3 cell matrix, rows = cell vectors a, b, c. This
+ *                 build accepts diagonal matrices only (orthorhombic cells).
+ *  pbc[3]         1 = periodic along that axis, 0 = open.
+ *  h              target level-1 grid spacing h_1 (> 0 unless overridden).
+ *                 Periodic axes use M = 2^round(log2(L/h)) intervals (all
+ *                 periodic axes must give the same M); open axes M = ceil(L/h).
+ *  grid_override  > 0: use exactly this many level-1 intervals on that axis
+ *                 (a power of two on periodic axes).
+ *  cutoff         level-zero cutoff a = r_cut^(0) (> 0).
+ *  order          B-spline order p: 4, 6 or 8.
+ *  levels         number of grid levels L; 0 = automatic. With any periodic
+ *                 axis L = log2(M) + 1 is fixed (spacing doubles until one
+ *                 point remains, Sec. 4.1) and any other value is rejected.
+ *  max_atoms      largest n a forward call may pass (sizes the workspace). */
+typedef struct {
+  double cell[9];
+  int pbc[3];
+  double h;
+  int grid_override[3];
+  double cutoff;
+  int order;
+  int levels;
+  int max_atoms;
+} msm_params;
+
+/* Derived sizes of a plan (msm_plan_get_info), for inspection and tests. */
+typedef struct {
+  int nlev;          /* grid levels L, top level included */
+  int ncomp;         /* levels whose grids are evaluated (L, or L-1 when the
+                        one-point top level of a periodic system is dropped) */
+  int M[3];          /* level-1 interval counts */
+  double h1[3];      /* level-1 spacings */
+  int lo[20][3];     /* first grid index of each evaluated level */
+  int n[20][3];      /* grid points of each evaluated level */
+  int R[3];          /* stencil radius of the levels below the top */
+  int C[3];          /* binning cells per axis */
+  int nnbr[3];       /* neighbour-cell reach per axis */
+  int stencil_kind[20]; /* 0 = ball stencil with wrap/zero, 1 = dense folded box */
+} msm_plan_info;
+
+/* Create a plan: validates the settings synchronously, builds the level
+ * stencils K^l (Eq. kernel_stencil_by_conv_with_universal_coeff) and their
+ * strain derivatives in FP64 on the host, and uploads them to the current
+ * device. *out receives the plan; free it with msm_plan_destroy. */
+int msm_plan_create(const msm_params* params, msm_plan* out);
+int msm_plan_destroy(msm_plan plan);
+int msm_plan_get_info(msm_plan plan, msm_plan_info* info);
+
+/* Host-only (no device needed): the plan msm_plan_create would build from
+ * params, described in *info. Same validation and return codes. */
+int msm_plan_describe(const msm_params* params, msm_plan_info* info);
+
+/* Host-only: the stencil a plan applies on level `level` (1-based), as float
+ * values on the offset box [lo, lo + sz) (z fastest), which = 0 for K^l
+ * (Eq. kernel_stencil_by_conv_with_universal_coeff), 1..6 for the strain
+ * derivatives dK^l/d eps_ab, ab = xx, yy, zz, xy, xz, yz. Ball levels are
+ * returned unfolded on [-R, R] (the kernel wraps indices), box levels folded
+ * along periodic axes onto [0, n). out (host, capacity `cap` floats) may be
+ * NULL to query lo and sz only. MSM_ERR_CAPACITY if cap is too small. */
+int msm_plan_stencil(const msm_params* params, int level, int which, float* out, size_t cap, int lo[3], int sz[3]);
+
+/* Bytes of device workspace a plan needs (for max_atoms atoms). The caller
+ * allocates it (any device allocator; 256-byte alignment or better) and passes
+ * it, unchanged between msm_forward and msm_backward, to every call. */
+int msm_workspace_bytes(msm_plan plan, size_t* bytes);
+
+/* Forward pass: energy, potentials and (optionally) forces of n atoms.
+ *  pos     device, n x 3 float32 Cartesian positions (row-major).
+ *  q       device, n float32 charges.
+ *  energy  device, 1 double: E = 1/2 sum_i q_i phi_i.
+ *  phi     device, n float32 or NULL: phi_i = dE/dq_i (Eq.
+ *          analytic_uoneplus_charge_grad plus the short-range part and the
+ *          self term).
+ *  forces  device, n x 3 float32 or NULL: F_i = -dE/dr_i (Eq.
+ *          analytic_uoneplus_position_grad plus the short-range part).
+ *          Needs MSM_WANT_FORCES.
+ *  flags   MSM_WANT_FORCES | MSM_WANT_VIRIAL.
+ * Returns MSM_ERR_CAPACITY if n > max_atoms or workspace_bytes is too small. */
+int msm_forward(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos,
+                const float* q, double* energy, float* phi, float* forces, int flags, void* stream);
+
+/* Backward pass for an upstream gradient g = dL/dE (device, 1 double),
+ * reusing the sorted bins, the level grids and the per-atom results the last
+ * msm_forward left in the workspace. Outputs (any may be NULL):
+ *  dE_dpos device, n x 3 float32: g * dE/dr_i = -g F_i.
+ *  dE_dq   device, n float32: g * phi_i.
+ *  virial  device, 9 doubles (row-major): g * W with W = -dE/d(eps) for the
+ *          homogeneous strain r -> (1+eps) r, cell -> (1+eps) cell.
+ * What the forward did not compute (forces, the short-range virial) is
+ * computed here. Returns MSM_ERR_NO_FORWARD without a prior forward. */
+int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,
+                 double* virial, void* stream);
+
+/* Synchronises stream and returns the device status word (MSM_DEV_* bits)
+ * of the last call on workspace in *device_status (host). */
+int msm_status(msm_plan plan, void* workspace, void* stream, int* device_status);
+
+/* Byte offset and element count, inside the workspace, of an internal array
+ * (for tests): which = 0 cell_start (int32, cells+1), 1 perm (int32, sorted
+ * slot -> atom), 2 grid charge of level `level` (float32, z fastest),
+ * 3 grid potential e of level `level` (after prolongation: e^(l+)),
+ * 4 sorted cell id of each sorted slot (int32). */
+int msm_debug_offset(msm_plan plan, int which, int level, size_t* offset_bytes, size_t* count);
+
+/* Phase timing. With profiling enabled, msm_forward / msm_backward record a
+ * CUDA event pair on the call's stream around each phase; msm_profile_read
+ * synchronises those events and returns, per phase, the milliseconds of the
+ * most recent forward and backward (host, ms[MSM_NPHASE]) and the number of
+ * kernels those two calls launched (host, *launches). Phases: */
+#define MSM_PH_BIN 0        /* binning (counting sort) */
+#define MSM_PH_SHORT 1      /* short-range pair sum */
+#define MSM_PH_ANTERP 2     /* anterpolation */
+#define MSM_PH_RESTRICT 3   /* restrictions, all levels */
+#define MSM_PH_STENCIL 4    /* level stencils, all levels */
+#define MSM_PH_PROLONG 5    /* prolongations, all levels */
+#define MSM_PH_INTERP 6     /* interpolation */
+#define MSM_PH_FINAL 7      /* outputs and energy */
+#define MSM_PH_VIRIAL 8     /* grid virial (backward) */
+#define MSM_PH_BSCALE 9     /* backward outputs */
+#define MSM_NPHASE 10
+int msm_profile(msm_plan plan, int enable);
+int msm_profile_read(msm_plan plan, double* ms, int* launches);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* msm_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent systems of uneven size and mixed periodicity in
+ * one set of launches (one launch per MSM phase for all systems), for the
+ * paper's vmap use (Sec. 4.1, batched Madelung evaluation).
+ *  per_sys    host, nsys settings (max_atoms ignored).
+ *  n_per_sys  host, nsys atom counts (fixed for the batch).
+ * Atoms of all systems are packed back to back in system order: positions
+ * (sum n) x 3, charges sum n; energy has nsys entries, virial 9 * nsys.
+ * ------------------------------------------------------------------------- */
+int msm_batch_create(const msm_params* per_sys, const int* n_per_sys, int nsys, msm_batch* out);
+int msm_batch_destroy(msm_batch batch);
+int msm_batch_workspace_bytes(msm_batch batch, size_t* bytes);
+int msm_batch_forward(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,
+                      double* energy, float* phi, float* forces, int flags, void* stream);
+int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_energy, float* dE_dpos,
+                       float* dE_dq, double* virial, void* stream);
+int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSM_GB300_H */

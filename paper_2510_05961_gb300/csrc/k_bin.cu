@@ -1,0 +1,207 @@
+// k_bin.cu -- cell-list binning by a stable counting sort (all systems of a
+// batch in one set of launches).
+//
+// Cell-index contract (bit-exact, FP32, round-to-nearest, no contraction):
+//   s = x * (float)(1/L); periodic: s -= floorf(s), s >= 1 -> 0;
+//   open: s outside [0,1] -> MSM_DEV_OUT_OF_CELL (axis cell 0);
+//   c = min((int)(s * (float)C), C-1); cell = (cx*Cy + cy)*Cz + cz.
+// Within a cell the sorted order is ascending atom index (stable), so the
+// sorted arrays are identical from run to run.
+//
+// Pipeline: count (atomic slot per atom) -> exclusive scan of the packed cell
+// counts of all systems -> scatter atom ids into buckets -> rank each atom in
+// its bucket by original index and write the sorted arrays.
+#include "msm_internal.h"
+
+namespace msm {
+
+__global__ void k_prologue(int* __restrict__ cell_count, int total_cells, int* __restrict__ status,
+                           SysDev* __restrict__ sys, int n_single) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = t; c < total_cells; c += gridDim.x * blockDim.x) cell_count[c] = 0;
+  if (t == 0) {
+    *status = 0;
+    if (n_single >= 0) sys[0].n = n_single;
+  }
+}
+
+// FP32 reduced coordinate s of one axis (the contract above); returns the
+// status bits it raises.
+__device__ __forceinline__ int reduced_coord(const SysDev& S, int d, float x, float& s) {
+  s = 0.0f;
+  if (!isfinite(x)) return kDevNonFinite;
+  float v = __fmul_rn(x, S.invL[d]);
+  if (S.pbc[d]) {
+    v = __fsub_rn(v, floorf(v));
+    if (v >= 1.0f) v = 0.0f;
+  } else if (!(v >= 0.0f && v <= 1.0f)) {
+    return kDevOutOfCell;
+  }
+  s = v;
+  return 0;
+}
+
+__device__ __forceinline__ int axis_cell(const SysDev& S, int d, float s, float& t) {
+  t = __fmul_rn(s, (float)S.C[d]);
+  int c = (int)t;
+  return c > S.C[d] - 1 ? S.C[d] - 1 : c;
+}
+
+__global__ void k_bin_count(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                            const float* __restrict__ pos, const float* __restrict__ q, int* __restrict__ cell_id,
+                            int* __restrict__ slot, int* __restrict__ cell_count, int* __restrict__ status) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int g = S.atom_off + local;
+  int bad = isfinite(q[g]) ? 0 : kDevNonFinite;
+  int c[3];
+  for (int d = 0; d < 3; d++) {
+    float s, t;
+    int b = reduced_coord(S, d, pos[3 * g + d], s);
+    bad |= b;
+    c[d] = b ? 0 : axis_cell(S, d, s, t);
+  }
+  int cell = (c[0] * S.C[1] + c[1]) * S.C[2] + c[2];
+  cell_id[g] = cell;
+  slot[g] = atomicAdd(&cell_count[S.cell_off + cell], 1);
+  if (bad) atomicOr(status, bad);
+}
+
+// exclusive scan of cell_count over tiles of 4096 cells
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  int pre = (wid > 0 ? sh[wid - 1] : 0) + x - v;
+  total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return pre;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int* __restrict__ cnt, int total_cells,
+                                                              int* __restrict__ start, int* __restrict__ tiles) {
+  __shared__ int sh[32];
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  int v[kScanPer], sum = 0;
+  for (int k = 0; k < kScanPer; k++) {
+    v[k] = (base + k < total_cells) ? cnt[base + k] : 0;
+    sum += v[k];
+  }
+  int total;
+  int pre = block_exclusive_scan(sum, sh, total);
+  for (int k = 0; k < kScanPer; k++) {
+    if (base + k < total_cells) start[base + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_fix(int* __restrict__ start, int total_cells,
+                                                            const int* __restrict__ tiles, int ntiles) {
+  __shared__ int sh[32];
+  __shared__ int s_off;
+  // offset of this tile = sum of the totals of the tiles before it
+  int acc = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) acc += tiles[t];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w];
+    s_off = s;
+  }
+  __syncthreads();
+  int off = s_off;
+  int base = blockIdx.x * kScanTile;
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x)
+    if (base + k < total_cells) start[base + k] += off;
+  if (blockIdx.x == (unsigned)(ntiles - 1) && threadIdx.x == 0) start[total_cells] = off + tiles[ntiles - 1];
+}
+
+__global__ void k_bin_scatter(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                              const int* __restrict__ cell_id, const int* __restrict__ slot,
+                              const int* __restrict__ cell_start, int* __restrict__ bucket) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int g = S.atom_off + local;
+  bucket[cell_start[S.cell_off + cell_id[g]] + slot[g]] = g;
+}
+
+__global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                           const float* __restrict__ pos, const float* __restrict__ q,
+                           const int* __restrict__ cell_id, const int* __restrict__ cell_start,
+                           const int* __restrict__ bucket, int* __restrict__ perm, int* __restrict__ scell,
+                           float4* __restrict__ xq, float4* __restrict__ uq) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int g = S.atom_off + local;
+  int cell = cell_id[g];
+  int b = cell_start[S.cell_off + cell], e = cell_start[S.cell_off + cell + 1];
+  int rank = 0;
+  for (int t = b; t < e; t++) rank += (bucket[t] < g);
+  int dst = b + rank;
+  perm[dst] = g;
+  scell[dst] = cell;
+  float qq = q[g];
+  float loc[3], u[3];
+  int c[3] = {cell / (S.C[1] * S.C[2]), (cell / S.C[2]) % S.C[1], cell % S.C[2]};
+  for (int d = 0; d < 3; d++) {
+    float s, t;
+    if (reduced_coord(S, d, pos[3 * g + d], s)) {
+      loc[d] = 0.0f;
+      u[d] = 0.0f;
+      continue;
+    }
+    axis_cell(S, d, s, t);
+    loc[d] = (t - (float)c[d]) * S.edge[d];
+    u[d] = s * S.Mf[d];
+  }
+  xq[dst] = make_float4(loc[0], loc[1], loc[2], qq);
+  uq[dst] = make_float4(u[0], u[1], u[2], qq);
+}
+
+void launch_prologue(const Work& w, int total_cells, SysDev* sys, int n_single, cudaStream_t s) {
+  int blocks = (total_cells + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  k_prologue<<<blocks, 256, 0, s>>>(w.cell_count, total_cells, w.status, sys, n_single);
+}
+
+void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitems, int total_cells,
+                int total_atoms, const float* pos, const float* q, cudaStream_t s) {
+  (void)total_atoms;
+  k_bin_count<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.slot, w.cell_count, w.status);
+  int ntiles = (total_cells + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(w.cell_count, total_cells, w.cell_start, w.scan_tiles);
+  k_scan_fix<<<ntiles, kScanThreads, 0, s>>>(w.cell_start, total_cells, w.scan_tiles, ntiles);
+  k_bin_scatter<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_id, w.slot, w.cell_start, w.bucket);
+  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.cell_start, w.bucket, w.perm, w.scell,
+                                       w.xq, w.uq);
+}
+
+}  // namespace msm

@@ -1,0 +1,146 @@
+// k_final.cu -- outputs of the MSM evaluation (Sec. 2, Eq. U_contributions;
+// Sec. 3.2.2 for the derivatives):
+//   phi_i = phi0_i + phi^(1+)_i  (= dE/dq_i),   F_i = F0_i + F^(1+)_i,
+//   E = 1/2 sum_i q_i phi_i   (FP64, fixed-order block sums),
+//   W = W0 + W^(1+)           (FP64, fixed-order sums of the block partials),
+// written back in the caller's atom order through the sort permutation.
+#include "msm_internal.h"
+
+namespace msm {
+
+__global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ sys,
+                                                     const AtomItem* __restrict__ items,
+                                                     const int* __restrict__ perm, const float4* __restrict__ xq,
+                                                     const float* __restrict__ phi_sr, const float* __restrict__ phi_lr,
+                                                     const float4* __restrict__ f_sr, const float4* __restrict__ f_lr,
+                                                     float* __restrict__ phi, float* __restrict__ forces,
+                                                     double* __restrict__ part_e) {
+  __shared__ double red[kChunk / 32];
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  double e = 0.0;
+  if ((int)threadIdx.x < it.count && local < S.n) {
+    int k = S.atom_off + local;
+    int g = perm[k];
+    float ph = phi_sr[k] + phi_lr[k];
+    e = 0.5 * (double)xq[k].w * (double)ph;
+    if (phi) phi[g] = ph;
+    if (forces) {
+      float4 a = f_sr[k], b = f_lr[k];
+      forces[3 * (long long)g + 0] = a.x + b.x;
+      forces[3 * (long long)g + 1] = a.y + b.y;
+      forces[3 * (long long)g + 2] = a.z + b.z;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kChunk / 32; w++) s += red[w];
+    part_e[blockIdx.x] = s;
+  }
+}
+
+// one block per system: energy = sum of the system's item partials in order
+__global__ void k_energy(const SysDev* __restrict__ sys, const double* __restrict__ part_e,
+                         double* __restrict__ energy) {
+  __shared__ double red[32];
+  const SysDev& S = sys[blockIdx.x];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < S.nitem; i += blockDim.x) acc += part_e[S.item0 + i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    energy[blockIdx.x] = s;
+  }
+}
+
+// one block per system: W = (sum of short-range partials + grid partials) * g
+__global__ void k_virial_out(const SysDev* __restrict__ sys, const double* __restrict__ part_w0,
+                             const double* __restrict__ part_wg, const int* __restrict__ vitem_off,
+                             const double* __restrict__ grad, double* __restrict__ virial) {
+  __shared__ double red[32][6];
+  const SysDev& S = sys[blockIdx.x];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < S.nitem; i += blockDim.x)
+    for (int c = 0; c < 6; c++) acc[c] += part_w0[6 * (long long)(S.item0 + i) + c];
+  // grid partials of this system: its ball items, then its box items
+  const int ns = gridDim.x;
+  for (int r = 0; r < 2; r++) {
+    int v0 = vitem_off[r * (ns + 1) + blockIdx.x], v1 = vitem_off[r * (ns + 1) + blockIdx.x + 1];
+    for (int i = v0 + threadIdx.x; i < v1; i += blockDim.x)
+      for (int c = 0; c < 6; c++) acc[c] += part_wg[6 * (long long)i + c];
+  }
+  for (int c = 0; c < 6; c++) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double w[6];
+    for (int c = 0; c < 6; c++) {
+      double s = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += red[k][c];
+      w[c] = s;
+    }
+    double g = grad ? grad[blockIdx.x] : 1.0;
+    double* V = virial + 9 * (long long)blockIdx.x;
+    V[0] = g * w[0]; V[1] = g * w[3]; V[2] = g * w[4];
+    V[3] = g * w[3]; V[4] = g * w[1]; V[5] = g * w[5];
+    V[6] = g * w[4]; V[7] = g * w[5]; V[8] = g * w[2];
+  }
+}
+
+__global__ void __launch_bounds__(kChunk) k_backward_scale(const SysDev* __restrict__ sys,
+                                                           const AtomItem* __restrict__ items,
+                                                           const int* __restrict__ perm,
+                                                           const float* __restrict__ phi_sr,
+                                                           const float* __restrict__ phi_lr,
+                                                           const float4* __restrict__ f_sr,
+                                                           const float4* __restrict__ f_lr,
+                                                           const double* __restrict__ grad,
+                                                           float* __restrict__ dE_dpos, float* __restrict__ dE_dq) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  int g = perm[k];
+  float gr = (float)grad[it.sys];
+  if (dE_dq) dE_dq[g] = gr * (phi_sr[k] + phi_lr[k]);
+  if (dE_dpos) {
+    float4 a = f_sr[k], b = f_lr[k];
+    dE_dpos[3 * (long long)g + 0] = -gr * (a.x + b.x);
+    dE_dpos[3 * (long long)g + 1] = -gr * (a.y + b.y);
+    dE_dpos[3 * (long long)g + 2] = -gr * (a.z + b.z);
+  }
+}
+
+void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
+                     float* forces, cudaStream_t s) {
+  k_finalize<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, phi, forces,
+                                       w.part_e);
+}
+
+void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s) {
+  k_energy<<<nsys, 256, 0, s>>>(t.sys, w.part_e, energy);
+}
+
+void launch_virial_out(const Work& w, const Tables& t, int nsys, const int* vitem_off, const double* grad,
+                       double* virial, cudaStream_t s) {
+  k_virial_out<<<nsys, 256, 0, s>>>(t.sys, w.part_w0, w.part_wg, vitem_off, grad, virial);
+}
+
+void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
+                           const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s) {
+  k_backward_scale<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, grad, dE_dpos,
+                                             dE_dq);
+}
+
+}  // namespace msm

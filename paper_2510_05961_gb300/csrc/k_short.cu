@@ -1,0 +1,135 @@
+// k_short.cu -- short-range part U^0 of the MSM (Eq. U_zero) over the cell
+// list: for every sorted atom i, every atom j of the neighbour cells and every
+// periodic image with |d| < a, (j, image) != (i, 0):
+//   phi0_i += q_j k_0(|d|),  k_0(r) = 1/r - gamma(r/a)/a   (Sec. 3.4),
+//   F0_i   += q_i q_j k_0'(r) d / r,
+//   W0     += -1/2 q_i q_j k_0'(r) d d^T / r,
+// and phi0_i -= q_i gamma(0)/a (the self term, sum_(l>=1) k_l(0)).
+// Positions are cell-local, so the displacement to an atom in the cell at
+// offset o is o * edge + (x_j - x_i) whether or not o wraps around a periodic
+// boundary; small periodic cells simply visit the same cell at several
+// offsets (every image within the cutoff, self images included).
+// One thread per sorted atom; the sum over j is the thread's own, so the
+// result does not depend on scheduling.
+#include "msm_internal.h"
+
+namespace msm {
+
+template <int P>
+__global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                                                  const int* __restrict__ cell_start, const int* __restrict__ scell,
+                                                  const float4* __restrict__ xq, float* __restrict__ phi_sr,
+                                                  float4* __restrict__ f_sr, double* __restrict__ part_w0,
+                                                  int want_f, int want_w) {
+  __shared__ double red[kChunk / 32][6];
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  bool active = (int)threadIdx.x < it.count && local < S.n;
+  float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (active) {
+    int k = S.atom_off + local;
+    float4 xi = xq[k];
+    int cell = scell[k];
+    int Cy = S.C[1], Cz = S.C[2];
+    int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
+    float gc[P], gdc[P - 1];
+#pragma unroll
+    for (int t = 0; t < P; t++) gc[t] = S.gc[t];
+#pragma unroll
+    for (int t = 0; t < P - 1; t++) gdc[t] = S.gdc[t];
+    const float a2 = S.a2, inv_a = S.inv_a, inv_a2 = S.inv_a2, two_inv_a3 = 2.0f * S.inv_a3;
+    float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
+      int ux = ci[0] + ox;
+      if (!S.pbc[0] && (ux < 0 || ux >= S.C[0])) continue;
+      int wx = ((ux % S.C[0]) + S.C[0]) % S.C[0];
+      float dxo = (float)ox * S.edge[0] - xi.x;
+      for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
+        int uy = ci[1] + oy;
+        if (!S.pbc[1] && (uy < 0 || uy >= Cy)) continue;
+        int wy = ((uy % Cy) + Cy) % Cy;
+        float dyo = (float)oy * S.edge[1] - xi.y;
+        for (int oz = -S.nnbr[2]; oz <= S.nnbr[2]; oz++) {
+          int uz = ci[2] + oz;
+          if (!S.pbc[2] && (uz < 0 || uz >= Cz)) continue;
+          int wz = ((uz % Cz) + Cz) % Cz;
+          float dzo = (float)oz * S.edge[2] - xi.z;
+          int c = S.cell_off + (wx * Cy + wy) * Cz + wz;
+          int jb = cell_start[c], je = cell_start[c + 1];
+          bool home = (ox | oy | oz) == 0;
+          for (int j = jb; j < je; j++) {
+            float4 xj = xq[j];
+            float dx = dxo + xj.x, dy = dyo + xj.y, dz = dzo + xj.z;
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < a2 && !(home && j == k)) {
+              float rinv = rsqrtf(r2);
+              float s = 1.0f - r2 * inv_a2;
+              float g = gc[P - 1];
+#pragma unroll
+              for (int t = P - 2; t >= 0; t--) g = fmaf(g, s, gc[t]);
+              float dg = gdc[P - 2];
+#pragma unroll
+              for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, s, gdc[t]);
+              ph = fmaf(xj.w, rinv - g * inv_a, ph);
+              if (want_f | want_w) {
+                // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
+                float fr = xj.w * fmaf(-rinv * rinv, rinv, two_inv_a3 * dg);
+                fx = fmaf(fr, dx, fx);
+                fy = fmaf(fr, dy, fy);
+                fz = fmaf(fr, dz, fz);
+                if (want_w) {
+                  w6[0] = fmaf(fr * dx, dx, w6[0]);
+                  w6[1] = fmaf(fr * dy, dy, w6[1]);
+                  w6[2] = fmaf(fr * dz, dz, w6[2]);
+                  w6[3] = fmaf(fr * dx, dy, w6[3]);
+                  w6[4] = fmaf(fr * dx, dz, w6[4]);
+                  w6[5] = fmaf(fr * dy, dz, w6[5]);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    phi_sr[k] = ph - xi.w * S.self_coef;
+    if (want_f) f_sr[k] = make_float4(xi.w * fx, xi.w * fy, xi.w * fz, 0.f);
+#pragma unroll
+    for (int c = 0; c < 6; c++) w6[c] *= -0.5f * xi.w;
+  }
+  if (!want_w) return;
+  // deterministic block reduction of the six virial components in FP64
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    double v = (double)w6[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < kChunk / 32; w++) v += red[w][threadIdx.x];
+    part_w0[6 * blockIdx.x + threadIdx.x] = v;
+  }
+}
+
+void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
+                  cudaStream_t s, int p) {
+  switch (p) {
+    case 4:
+      k_short<4><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0,
+                                           forces, virial);
+      break;
+    case 6:
+      k_short<6><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0,
+                                           forces, virial);
+      break;
+    default:
+      k_short<8><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0,
+                                           forces, virial);
+      break;
+  }
+}
+
+}  // namespace msm

@@ -1,0 +1,403 @@
+// msm_api.cu -- the C ABI (include/msm_gb300.h): plans, batches, forward and
+// backward passes. Each call validates its arguments on the host, resolves
+// the caller's workspace into arrays and enqueues the kernels on the caller's
+// stream; nothing here waits for the GPU except msm_status.
+#include <cstring>
+#include <string>
+
+#include "msm_plan.h"
+
+using namespace msm;
+
+struct msm_plan_s {
+  Engine eng;
+};
+struct msm_batch_s {
+  Engine eng;
+};
+
+static thread_local std::string g_err;
+
+static int set_err(int code, const std::string& m) {
+  g_err = m;
+  return code;
+}
+
+static int check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(MSM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return MSM_OK;
+}
+
+// phase timing: an event pair around each phase when profiling is on
+struct Phase {
+  Engine& E;
+  int ph;
+  cudaStream_t s;
+  Phase(Engine& e, int p, cudaStream_t st) : E(e), ph(p), s(st) {
+    if (E.profiling) {
+      cudaEventRecord(E.ev[2 * ph], s);
+      E.ev_used[ph] = true;
+    }
+  }
+  ~Phase() {
+    if (E.profiling) cudaEventRecord(E.ev[2 * ph + 1], s);
+  }
+};
+
+// kernels each phase launches (for the launch count)
+static int count_forward(const Engine& E, bool) {
+  int n = 1 + 5 + 1;                                   // prologue, binning, short range
+  n += E.anterp_items.empty() ? 0 : 1;
+  for (int l = 1; l < E.maxcomp; l++) n += 2;          // restriction + prolongation per level step
+  n += E.ball_items.empty() ? 0 : 1;
+  n += E.box_items.empty() ? 0 : 1;
+  n += 1 + 1 + 1;                                      // interp, finalize, energy
+  return n;
+}
+
+// forward pass of an engine; n_single >= 0 sets the atom count of a single-system plan
+static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const float* pos, const float* q,
+                       double* energy, float* phi, float* forces, int flags, cudaStream_t s) {
+  if (!ws || !energy) return set_err(MSM_ERR_INVALID_ARG, "workspace and energy must not be NULL");
+  if (ws_bytes < E.ws_bytes) return set_err(MSM_ERR_CAPACITY, "workspace smaller than msm_workspace_bytes");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return set_err(MSM_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  int n_total = E.single ? n_single : E.total_atoms;
+  if (n_total > 0 && (!pos || !q)) return set_err(MSM_ERR_INVALID_ARG, "positions and charges must not be NULL");
+  if ((flags & MSM_WANT_FORCES) == 0 && forces) return set_err(MSM_ERR_INVALID_ARG, "forces requested without MSM_WANT_FORCES");
+  const bool want_f = (flags & MSM_WANT_FORCES) != 0;
+  const bool want_w = (flags & MSM_WANT_VIRIAL) != 0;
+  Work w = E.resolve(ws);
+  Tables t = E.tables();
+  for (bool& u : E.ev_used) u = false;
+  const int nai = (int)E.atom_items.size();
+  {
+    Phase ph(E, MSM_PH_BIN, s);
+    launch_prologue(w, E.total_cells, E.d_sys, E.single ? n_single : -1, s);
+    launch_bin(w, t, E.d_atom_items, nai, E.total_cells, n_total, pos, q, s);
+  }
+  {
+    Phase ph(E, MSM_PH_SHORT, s);
+    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, s, E.p);
+  }
+  {
+    Phase ph(E, MSM_PH_ANTERP, s);
+    launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p);
+  }
+  {
+    Phase ph(E, MSM_PH_RESTRICT, s);
+    for (int l = 1; l < E.maxcomp; l++) {
+      int a = E.restrict_off[l - 1], b = E.restrict_off[l];
+      launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
+    }
+  }
+  {
+    Phase ph(E, MSM_PH_STENCIL, s);
+    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, s);
+    launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
+  }
+  {
+    Phase ph(E, MSM_PH_PROLONG, s);
+    for (int l = E.maxcomp - 1; l >= 1; l--) {
+      int a = E.prolong_off[l - 1], b = E.prolong_off[l];
+      launch_prolong(w, t, E.d_range_items + a, b - a, s, E.p);
+    }
+  }
+  {
+    Phase ph(E, MSM_PH_INTERP, s);
+    launch_interp(w, t, E.d_atom_items, nai, want_f, s, E.p);
+  }
+  {
+    Phase ph(E, MSM_PH_FINAL, s);
+    launch_finalize(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, s);
+    launch_energy(w, t, E.nsys, energy, s);
+  }
+  E.launches_fwd = count_forward(E, want_f);
+  E.launches_bwd = 0;
+  int rc = check_launch("msm_forward");
+  if (rc) return rc;
+  E.have_fwd = true;
+  E.last_flags = flags;
+  E.last_ws = ws;
+  E.last_n = n_total;
+  return MSM_OK;
+}
+
+static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos, float* dE_dq, double* virial,
+                        cudaStream_t s) {
+  if (!E.have_fwd || ws != E.last_ws) return set_err(MSM_ERR_NO_FORWARD, "msm_backward needs a prior msm_forward on this workspace");
+  if (!grad) return set_err(MSM_ERR_INVALID_ARG, "grad_energy must not be NULL");
+  Work w = E.resolve(ws);
+  Tables t = E.tables();
+  const int nai = (int)E.atom_items.size();
+  const bool had_f = (E.last_flags & MSM_WANT_FORCES) != 0;
+  const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
+  const bool need_f = dE_dpos != nullptr;
+  const bool need_w = virial != nullptr;
+  int nl = 0;
+  if ((need_f && !had_f) || (need_w && !had_w)) {
+    // the forward skipped these parts; the short-range kernel rewrites its
+    // potential with identical values, so running it again is safe
+    Phase ph(E, MSM_PH_SHORT, s);
+    launch_short(w, t, E.d_atom_items, nai, need_f || had_f, need_w || had_w, s, E.p);
+    nl++;
+    if (need_f && !had_f) {
+      launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
+      nl++;
+    }
+    E.last_flags |= (need_f ? MSM_WANT_FORCES : 0) | (need_w ? MSM_WANT_VIRIAL : 0);
+  }
+  if (need_w) {
+    Phase ph(E, MSM_PH_VIRIAL, s);
+    const int nb = (int)E.ball_items.size();
+    launch_virial_ball(w, t, E.d_ball_items, nb, E.rmax, E.ryz, 0, s);
+    launch_virial_box(w, t, E.d_box_items, (int)E.box_items.size(), nb, s);
+    launch_virial_out(w, t, E.nsys, E.d_voff, grad, virial, s);
+    nl += (nb ? 1 : 0) + (E.box_items.empty() ? 0 : 1) + 1;
+  }
+  if (dE_dpos || dE_dq) {
+    Phase ph(E, MSM_PH_BSCALE, s);
+    launch_backward_scale(w, t, E.d_atom_items, nai, grad, dE_dpos, dE_dq, s);
+    nl++;
+  }
+  E.launches_bwd = nl;
+  return check_launch("msm_backward");
+}
+
+static int read_status(Engine& E, void* ws, cudaStream_t s, int* out) {
+  if (!ws || !out) return set_err(MSM_ERR_INVALID_ARG, "workspace and device_status must not be NULL");
+  Work w = E.resolve(ws);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, w.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return set_err(MSM_ERR_CUDA, std::string("msm_status: ") + cudaGetErrorString(cudaGetLastError()));
+  *out = v;
+  return MSM_OK;
+}
+
+static void fill_info(const SysHost& S, msm_plan_info* info) {
+  std::memset(info, 0, sizeof(*info));
+  info->nlev = S.nlev;
+  info->ncomp = S.ncomp;
+  for (int d = 0; d < 3; d++) {
+    info->M[d] = S.M[d];
+    info->h1[d] = S.h1[d];
+    info->R[d] = S.R[d];
+    info->C[d] = S.C[d];
+    info->nnbr[d] = S.nnbr[d];
+  }
+  for (int l = 0; l < S.ncomp && l < 20; l++) {
+    for (int d = 0; d < 3; d++) {
+      info->lo[l][d] = S.lev[l].lo[d];
+      info->n[l][d] = S.lev[l].n[d];
+    }
+    info->stencil_kind[l] = S.lev[l].kind;
+  }
+}
+
+extern "C" {
+
+const char* msm_last_error(void) { return g_err.c_str(); }
+
+int msm_profile(msm_plan plan, int enable) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  Engine& E = plan->eng;
+  if (enable && !E.ev[0])
+    for (auto& e : E.ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return set_err(MSM_ERR_CUDA, "cudaEventCreate failed");
+  E.profiling = enable != 0;
+  return MSM_OK;
+}
+
+int msm_profile_read(msm_plan plan, double* ms, int* launches) {
+  if (!plan || !ms) return set_err(MSM_ERR_INVALID_ARG, "NULL argument");
+  Engine& E = plan->eng;
+  for (int p = 0; p < MSM_NPHASE; p++) {
+    ms[p] = 0.0;
+    if (!E.profiling || !E.ev_used[p]) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(E.ev[2 * p + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, E.ev[2 * p], E.ev[2 * p + 1]) != cudaSuccess)
+      return set_err(MSM_ERR_CUDA, "profile events not readable");
+    ms[p] = t;
+  }
+  if (launches) *launches = E.launches_fwd + E.launches_bwd;
+  return MSM_OK;
+}
+
+int msm_plan_create(const msm_params* params, msm_plan* out) {
+  if (!params || !out) return set_err(MSM_ERR_INVALID_ARG, "params and out must not be NULL");
+  if (params->max_atoms < 0) return set_err(MSM_ERR_INVALID_ARG, "max_atoms must be >= 0");
+  msm_plan p = new (std::nothrow) msm_plan_s;
+  if (!p) return set_err(MSM_ERR_CUDA, "out of host memory");
+  std::string err;
+  int rc = p->eng.build(params, &params->max_atoms, 1, true, &err);
+  if (rc) {
+    delete p;
+    return set_err(rc, err);
+  }
+  *out = p;
+  g_err.clear();
+  return MSM_OK;
+}
+
+int msm_plan_destroy(msm_plan plan) {
+  delete plan;
+  return MSM_OK;
+}
+
+int msm_plan_get_info(msm_plan plan, msm_plan_info* info) {
+  if (!plan || !info) return set_err(MSM_ERR_INVALID_ARG, "plan and info must not be NULL");
+  fill_info(plan->eng.sys[0], info);
+  return MSM_OK;
+}
+
+int msm_plan_describe(const msm_params* params, msm_plan_info* info) {
+  if (!params || !info) return set_err(MSM_ERR_INVALID_ARG, "params and info must not be NULL");
+  SysHost S;
+  std::string err;
+  int rc = plan_system(*params, S, &err);
+  if (rc) return set_err(rc, err);
+  fill_info(S, info);
+  return MSM_OK;
+}
+
+int msm_plan_stencil(const msm_params* params, int level, int which, float* out, size_t cap, int lo[3], int sz[3]) {
+  if (!params || !lo || !sz) return set_err(MSM_ERR_INVALID_ARG, "NULL argument");
+  if (which < 0 || which > 6) return set_err(MSM_ERR_INVALID_ARG, "which must be 0..6");
+  SysHost S;
+  std::string err;
+  int rc = plan_system(*params, S, &err);
+  if (rc) return set_err(rc, err);
+  if (level < 1 || level > S.ncomp) return set_err(MSM_ERR_INVALID_ARG, "level out of range");
+  const LevelHost& Lv = S.lev[level - 1];
+  size_t count;
+  const float* src;
+  std::vector<float> tmp;
+  if (Lv.kind == 0) {
+    for (int d = 0; d < 3; d++) {
+      lo[d] = -S.R[d];
+      sz[d] = 2 * S.R[d] + 1;
+    }
+    count = (size_t)sz[0] * sz[1] * sz[2];
+    if (which == 0) {
+      tmp.assign(S.kball.begin(), S.kball.end());
+    } else {
+      // the kernel stores half-space weights; undo that for the caller
+      tmp.assign(S.dkh.begin() + (which - 1) * count, S.dkh.begin() + which * count);
+      for (int x = -S.R[0]; x <= S.R[0]; x++)
+        for (int y = -S.R[1]; y <= S.R[1]; y++)
+          for (int z = -S.R[2]; z <= S.R[2]; z++) {
+            size_t at = ((size_t)(x + S.R[0]) * sz[1] + (y + S.R[1])) * sz[2] + (z + S.R[2]);
+            size_t mir = ((size_t)(-x + S.R[0]) * sz[1] + (-y + S.R[1])) * sz[2] + (-z + S.R[2]);
+            bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
+            if (half) tmp[at] *= 0.5f;
+            else if (!(x == 0 && y == 0 && z == 0)) tmp[at] = 0.5f * S.dkh[(which - 1) * count + mir];
+          }
+    }
+    for (auto& v : tmp) v *= Lv.scale;
+    src = tmp.data();
+  } else {
+    for (int d = 0; d < 3; d++) {
+      lo[d] = Lv.blo[d];
+      sz[d] = Lv.bsz[d];
+    }
+    count = (size_t)sz[0] * sz[1] * sz[2];
+    src = which == 0 ? Lv.kbox.data() : Lv.dkbox.data() + (which - 1) * count;
+  }
+  if (!out) return MSM_OK;
+  if (cap < count) return set_err(MSM_ERR_CAPACITY, "output buffer too small");
+  std::memcpy(out, src, sizeof(float) * count);
+  return MSM_OK;
+}
+
+int msm_workspace_bytes(msm_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return set_err(MSM_ERR_INVALID_ARG, "plan and bytes must not be NULL");
+  *bytes = plan->eng.ws_bytes;
+  return MSM_OK;
+}
+
+int msm_forward(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos, const float* q,
+                double* energy, float* phi, float* forces, int flags, void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  if (n < 0 || n > plan->eng.total_atoms) return set_err(MSM_ERR_CAPACITY, "n outside [0, max_atoms]");
+  return run_forward(plan->eng, workspace, workspace_bytes, n, pos, q, energy, phi, forces, flags,
+                     (cudaStream_t)stream);
+}
+
+int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,
+                 double* virial, void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  return run_backward(plan->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
+}
+
+int msm_status(msm_plan plan, void* workspace, void* stream, int* device_status) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  return read_status(plan->eng, workspace, (cudaStream_t)stream, device_status);
+}
+
+int msm_debug_offset(msm_plan plan, int which, int level, size_t* offset_bytes, size_t* count) {
+  if (!plan || !offset_bytes || !count) return set_err(MSM_ERR_INVALID_ARG, "NULL argument");
+  const Engine& E = plan->eng;
+  switch (which) {
+    case 0: *offset_bytes = E.L_cell_start; *count = (size_t)E.total_cells + 1; return MSM_OK;
+    case 1: *offset_bytes = E.L_perm; *count = (size_t)E.total_atoms; return MSM_OK;
+    case 4: *offset_bytes = E.L_scell; *count = (size_t)E.total_atoms; return MSM_OK;
+    case 2:
+    case 3: {
+      const SysHost& S = E.sys[0];
+      if (level < 1 || level > S.ncomp) return set_err(MSM_ERR_INVALID_ARG, "level out of range");
+      const LevDev& L = E.hlev[level - 1];
+      *offset_bytes = E.L_grid + sizeof(float) * (size_t)(which == 2 ? L.q_off : L.e_off);
+      *count = (size_t)L.n[0] * L.n[1] * L.n[2];
+      return MSM_OK;
+    }
+    default: return set_err(MSM_ERR_INVALID_ARG, "unknown array");
+  }
+}
+
+int msm_batch_create(const msm_params* per_sys, const int* n_per_sys, int nsys, msm_batch* out) {
+  if (!per_sys || !n_per_sys || !out || nsys <= 0) return set_err(MSM_ERR_INVALID_ARG, "bad batch arguments");
+  msm_batch b = new (std::nothrow) msm_batch_s;
+  if (!b) return set_err(MSM_ERR_CUDA, "out of host memory");
+  std::string err;
+  int rc = b->eng.build(per_sys, n_per_sys, nsys, false, &err);
+  if (rc) {
+    delete b;
+    return set_err(rc, err);
+  }
+  *out = b;
+  g_err.clear();
+  return MSM_OK;
+}
+
+int msm_batch_destroy(msm_batch batch) {
+  delete batch;
+  return MSM_OK;
+}
+
+int msm_batch_workspace_bytes(msm_batch batch, size_t* bytes) {
+  if (!batch || !bytes) return set_err(MSM_ERR_INVALID_ARG, "batch and bytes must not be NULL");
+  *bytes = batch->eng.ws_bytes;
+  return MSM_OK;
+}
+
+int msm_batch_forward(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,
+                      double* energy, float* phi, float* forces, int flags, void* stream) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return run_forward(batch->eng, workspace, workspace_bytes, -1, pos, q, energy, phi, forces, flags,
+                     (cudaStream_t)stream);
+}
+
+int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,
+                       double* virial, void* stream) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return run_backward(batch->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
+}
+
+int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return read_status(batch->eng, workspace, (cudaStream_t)stream, device_status);
+}
+
+}  // extern "C"

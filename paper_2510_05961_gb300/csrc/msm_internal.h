@@ -1,0 +1,133 @@
+// msm_internal.h -- device-side descriptors and kernel launchers of the
+// GB300 MSM library. Everything here is private to the library; the public
+// boundary is include/msm_gb300.h.
+//
+// Every kernel is batch-native: it reads per-system descriptors (SysDev),
+// per-level descriptors (LevDev) and a list of work items built on the host at
+// plan time, so one launch serves one system or hundreds of systems alike.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msm {
+
+constexpr int kMaxLev = 20;
+constexpr int kChunk = 256;        // atoms per per-atom work item
+constexpr int kAnterpT = 8;        // anterpolation tile edge (grid points)
+constexpr int kBallTY = 32;        // stencil tile rows (y)
+constexpr int kBallBZ = 16;        // outputs per thread along z
+constexpr int kBallTZ = 32;        // stencil tile depth (z)
+constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
+constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
+constexpr int kBoxChunk = 128;     // outputs per box-stencil work item
+constexpr int kGridChunk = 256;    // points per restriction/prolongation item
+
+// device status bits (mirrors MSM_DEV_* of the public header)
+constexpr int kDevOutOfCell = 1;
+constexpr int kDevNonFinite = 2;
+
+struct SysDev {
+  int n;            // atoms of this system
+  int atom_off;     // first packed (user-order and sorted) atom index
+  int C[3];         // binning cells per axis
+  int cell_off;     // first packed cell index
+  int nnbr[3];      // neighbour-cell reach ceil(a / edge)
+  int pbc[3];
+  int M[3];         // level-1 interval counts (u = s * M)
+  int p;            // B-spline order
+  int ncomp;        // evaluated grid levels
+  int lev0;         // index of level 1 in the LevDev table
+  int item0, nitem; // per-atom work items of this system
+  float edge[3];    // binning cell edges
+  float invL[3];    // (float)(1/L): binning contract
+  float Mf[3];      // M as float
+  float inv_h1[3];  // 1/h_1 per axis
+  float a2, inv_a, inv_a2, inv_a3;
+  float self_coef;  // gamma(0)/a (self term of Eq. U_zero)
+  float gc[8];      // softening polynomial in s = 1 - rho^2: gamma = sum_k gc[k] s^k
+  float gdc[8];     // gdc[k] = (k+1) gc[k+1]: d gamma / d s = sum_k gdc[k] s^k
+  float jc[9];      // restriction coefficients J_k, k = -p/2 .. p/2 (index k + p/2)
+};
+
+struct LevDev {
+  int sys, level;           // owning system, level number (1-based)
+  int n[3], lo[3], per[3];  // grid points, first grid index, periodic flags
+  long long q_off, e_off;   // float offsets of q~^l and e^l in the grid pool
+  int kind;                 // 0 = ball stencil (radius R, wrap/zero), 1 = dense box (folded)
+  int R[3];                 // ball radius per axis
+  int blo[3], bsz[3];       // box: offsets d in [blo, blo + bsz)
+  float scale;              // stencil scale 2^-(l-1) relative to the stored values
+  long long k_off;          // stencil values (ball: dense (2R+1)^3; box: bsz product)
+  long long dk_off;         // virial weights: 6 consecutive arrays of the same layout
+  long long w_off;          // ball: column half-widths of K (int pool, (2Rx+1)(2Ry+1))
+  long long wh_off;         // ball: column half-widths of the virial weights
+};
+
+struct AtomItem { int sys, start, count; };
+struct TileItem { int lev, x0, y0, z0; };
+struct RangeItem { int lev, start, count; };
+
+// workspace arrays of one call (device pointers resolved by the host)
+struct Work {
+  int* status;
+  int* cell_count;
+  int* cell_start;
+  int* scan_tiles;
+  int* cell_id;
+  int* slot;
+  int* bucket;
+  int* perm;
+  int* scell;
+  float4* xq;      // cell-local Cartesian position and charge, sorted order
+  float4* uq;      // level-1 grid coordinates and charge, sorted order
+  float* phi_sr;   // short-range potential incl. self term, sorted
+  float4* f_sr;    // short-range force, sorted
+  float* phi_lr;   // long-range potential, sorted
+  float4* f_lr;    // long-range force, sorted
+  double* part_e;  // per atom item: 1/2 sum q phi
+  double* part_w0; // per atom item: 6 short-range virial components
+  double* part_wg; // per virial item: 6 grid virial components
+  float* grid;     // grid pool
+};
+
+struct Tables {
+  const SysDev* sys;
+  const LevDev* lev;
+  const float* kpool;
+  const int* wpool;
+};
+
+// ---------------------------------------------------------------- launchers
+// binning (k_bin.cu)
+void launch_prologue(const Work& w, int total_cells, SysDev* sys, int n_single, cudaStream_t s);
+void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitems, int total_cells,
+                int total_atoms, const float* pos, const float* q, cudaStream_t s);
+// short range (k_short.cu)
+void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
+                  cudaStream_t s, int p);
+// anterpolation / interpolation (k_interp.cu)
+void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p);
+void launch_interp(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces,
+                   cudaStream_t s, int p);
+// restriction / prolongation (k_grid.cu)
+void launch_restrict(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
+void launch_prolong(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
+// stencils and grid virial (k_stencil.cu)
+void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
+                         int ryz_max[2], cudaStream_t s);
+void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);
+void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
+                        int ryz_max[2], int part_off, cudaStream_t s);
+void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, int part_off,
+                       cudaStream_t s);
+// outputs (k_final.cu)
+void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
+                     float* forces, cudaStream_t s);
+void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);
+void launch_virial_out(const Work& w, const Tables& t, int nsys, const int* vitem_off, const double* grad,
+                       double* virial, cudaStream_t s);
+void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
+                           const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
+
+}  // namespace msm

@@ -1,0 +1,657 @@
+// msm_plan.cu -- host planner of the GB300 MSM library (FP64): grid counts
+// and level ranges, softening coefficients, restriction coefficients,
+// quasi-interpolation coefficients, the level stencils K^l and their strain
+// derivatives, the work lists of every kernel and the workspace layout.
+//
+// Paper passages: level set-up of periodic cells (Sec. 4.1: spacing doubles
+// until one point remains), splitting and softening (Sec. 3.4, Eq.
+// coulomb_splitting_with_softener), restriction coefficients (Eq.
+// restriction_prolongation_explicit_formulas), stencils (Eq.
+// kernel_stencil_by_conv_with_universal_coeff; K^l = K^1 / 2^(l-1) for the
+// intermediate levels, Sec. 3.4).
+#include "msm_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace msm {
+
+// ------------------------------------------------------------------ math
+// Softening gamma(rho) (Sec. 3.4): 1/rho for rho >= 1, else the Taylor
+// polynomial of s^-1/2 about s = 1 to degree p-1, at s = rho^2. In the
+// variable t = 1 - rho^2 it reads sum_k c_k t^k with c_0 = 1,
+// c_k = c_(k-1) (2k - 1) / (2k).
+static void softening_coeffs(int p, double* c) {
+  c[0] = 1.0;
+  for (int k = 1; k < p; k++) c[k] = c[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
+}
+
+static double soft(int p, double rho) {
+  if (rho >= 1.0) return 1.0 / rho;
+  double c[8];
+  softening_coeffs(p, c);
+  double t = 1.0 - rho * rho, v = c[p - 1];
+  for (int k = p - 2; k >= 0; k--) v = v * t + c[k];
+  return v;
+}
+
+static double soft_d(int p, double rho) {  // d gamma / d rho
+  if (rho >= 1.0) return -1.0 / (rho * rho);
+  double c[8];
+  softening_coeffs(p, c);
+  double t = 1.0 - rho * rho, v = (p - 1) * c[p - 1];
+  for (int k = p - 2; k >= 1; k--) v = v * t + k * c[k];
+  return -2.0 * rho * v;
+}
+
+// grid-level partial kernel k_l (l >= 1) and its r-derivative
+static double klev(const SysHost& S, int l, double r, bool deriv) {
+  double s1 = S.a * std::ldexp(1.0, l - 1);
+  if (l == S.nlev) return deriv ? soft_d(S.p, r / s1) / (s1 * s1) : soft(S.p, r / s1) / s1;
+  double s2 = 2.0 * s1;
+  if (r >= s2) return 0.0;
+  if (deriv) return soft_d(S.p, r / s1) / (s1 * s1) - soft_d(S.p, r / s2) / (s2 * s2);
+  return soft(S.p, r / s1) / s1 - soft(S.p, r / s2) / s2;
+}
+
+// omega'_0 .. omega'_(p/2-1) (symmetric), exact rationals: the shortest
+// symmetric sequence whose symbol times the squared B-spline sampling symbol
+// is 1 + O(theta^p) (equivalently, 1-D kernel interpolation reproduces
+// polynomials of degree < p).
+static void omega_half(int p, double* w) {
+  switch (p) {
+    case 4: w[0] = 5.0 / 3.0; w[1] = -1.0 / 3.0; break;
+    case 6: w[0] = 121.0 / 40.0; w[1] = -71.0 / 60.0; w[2] = 41.0 / 240.0; break;
+    default:
+      w[0] = 5674.0 / 945.0; w[1] = -8261.0 / 2520.0; w[2] = 551.0 / 630.0; w[3] = -149.0 / 1512.0; break;
+  }
+}
+
+// ------------------------------------------------------------------ stencils
+// Dense 3-D array with an index origin: value at offset (x,y,z) stored at
+// ((x-o0)*s1 + (y-o1))*s2 + (z-o2).
+struct Box3 {
+  int o[3], s[3];
+  std::vector<double> v;
+  void init(const int lo[3], const int sz[3]) {
+    for (int d = 0; d < 3; d++) { o[d] = lo[d]; s[d] = sz[d]; }
+    v.assign((size_t)s[0] * s[1] * s[2], 0.0);
+  }
+  double& at(int x, int y, int z) { return v[((size_t)(x - o[0]) * s[1] + (y - o[1])) * s[2] + (z - o[2])]; }
+};
+
+// K_m = sum_t omega'_tx omega'_ty omega'_tz sample(m - t) on the output box
+// [-E, E] (per axis), sample(n) = f(h o n) for the level spacing hl. comp = 0:
+// k_l(|v|); comp 1..6: k_l'(|v|) v_a v_b / |v| with ab = xx,yy,zz,xy,xz,yz.
+static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box3& out) {
+  const int r = S.p / 2 - 1;
+  double wh[4];
+  omega_half(S.p, wh);
+  double hl[3];
+  for (int d = 0; d < 3; d++) hl[d] = S.h1[d] * std::ldexp(1.0, l - 1);
+  static const int AB[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  int slo[3], ssz[3], olo[3], osz[3];
+  for (int d = 0; d < 3; d++) {
+    slo[d] = -E[d] - r;
+    ssz[d] = 2 * (E[d] + r) + 1;
+    olo[d] = -E[d];
+    osz[d] = 2 * E[d] + 1;
+  }
+  Box3 smp;
+  smp.init(slo, ssz);
+  for (int x = slo[0]; x < slo[0] + ssz[0]; x++)
+    for (int y = slo[1]; y < slo[1] + ssz[1]; y++)
+      for (int z = slo[2]; z < slo[2] + ssz[2]; z++) {
+        double v[3] = {hl[0] * x, hl[1] * y, hl[2] * z};
+        double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double val;
+        if (comp == 0) {
+          val = klev(S, l, rr, false);
+        } else {
+          int a = AB[comp - 1][0], b = AB[comp - 1][1];
+          val = rr > 0.0 ? klev(S, l, rr, true) * v[a] * v[b] / rr : 0.0;
+        }
+        smp.at(x, y, z) = val;
+      }
+  auto om = [&](int t) { return wh[t < 0 ? -t : t]; };
+  // separable passes: z, then y, then x
+  int alo[3] = {slo[0], slo[1], olo[2]}, asz[3] = {ssz[0], ssz[1], osz[2]};
+  Box3 A;
+  A.init(alo, asz);
+  for (int x = slo[0]; x < slo[0] + ssz[0]; x++)
+    for (int y = slo[1]; y < slo[1] + ssz[1]; y++)
+      for (int z = olo[2]; z < olo[2] + osz[2]; z++) {
+        double acc = 0.0;
+        for (int t = -r; t <= r; t++) acc += om(t) * smp.at(x, y, z - t);
+        A.at(x, y, z) = acc;
+      }
+  int blo[3] = {slo[0], olo[1], olo[2]}, bsz[3] = {ssz[0], osz[1], osz[2]};
+  Box3 B;
+  B.init(blo, bsz);
+  for (int x = slo[0]; x < slo[0] + ssz[0]; x++)
+    for (int y = olo[1]; y < olo[1] + osz[1]; y++)
+      for (int z = olo[2]; z < olo[2] + osz[2]; z++) {
+        double acc = 0.0;
+        for (int t = -r; t <= r; t++) acc += om(t) * A.at(x, y - t, z);
+        B.at(x, y, z) = acc;
+      }
+  out.init(olo, osz);
+  for (int x = olo[0]; x < olo[0] + osz[0]; x++)
+    for (int y = olo[1]; y < olo[1] + osz[1]; y++)
+      for (int z = olo[2]; z < olo[2] + osz[2]; z++) {
+        double acc = 0.0;
+        for (int t = -r; t <= r; t++) acc += om(t) * B.at(x - t, y, z);
+        out.at(x, y, z) = acc;
+      }
+}
+
+// fold the periodic axes of an unfolded box onto [0, n) and scale
+static void fold(const Box3& in, const int n[3], const int per[3], double scale, Box3& out) {
+  int lo[3], sz[3];
+  for (int d = 0; d < 3; d++) {
+    lo[d] = per[d] ? 0 : in.o[d];
+    sz[d] = per[d] ? n[d] : in.s[d];
+  }
+  out.init(lo, sz);
+  for (int x = 0; x < in.s[0]; x++)
+    for (int y = 0; y < in.s[1]; y++)
+      for (int z = 0; z < in.s[2]; z++) {
+        int m[3] = {x + in.o[0], y + in.o[1], z + in.o[2]}, f[3];
+        for (int d = 0; d < 3; d++) {
+          if (per[d]) {
+            int rr = m[d] % n[d];
+            f[d] = rr < 0 ? rr + n[d] : rr;
+          } else {
+            f[d] = m[d];
+          }
+        }
+        out.at(f[0], f[1], f[2]) += scale * in.v[((size_t)x * in.s[1] + y) * in.s[2] + z];
+      }
+}
+
+// ------------------------------------------------------------------ planning
+static int fail(std::string* err, int code, const char* msg) {
+  if (err) *err = msg;
+  return code;
+}
+
+int plan_system(const msm_params& P, SysHost& S, std::string* err) {
+  for (int i = 0; i < 9; i++) {
+    if (!std::isfinite(P.cell[i])) return fail(err, MSM_ERR_INVALID_ARG, "cell has a non-finite entry");
+    if (i % 4 != 0 && P.cell[i] != 0.0)
+      return fail(err, MSM_ERR_UNSUPPORTED, "only orthorhombic (diagonal) cells are supported");
+  }
+  if (P.order != 4 && P.order != 6 && P.order != 8) return fail(err, MSM_ERR_INVALID_ARG, "order must be 4, 6 or 8");
+  if (!(P.cutoff > 0.0) || !std::isfinite(P.cutoff)) return fail(err, MSM_ERR_INVALID_ARG, "cutoff must be > 0");
+  S.p = P.order;
+  S.a = P.cutoff;
+  int Mper = 0;
+  for (int d = 0; d < 3; d++) {
+    S.L[d] = P.cell[4 * d];
+    if (!(S.L[d] > 0.0)) return fail(err, MSM_ERR_INVALID_ARG, "cell lengths must be > 0");
+    if (P.pbc[d] != 0 && P.pbc[d] != 1) return fail(err, MSM_ERR_INVALID_ARG, "pbc entries must be 0 or 1");
+    S.pbc[d] = P.pbc[d];
+    int M;
+    if (P.grid_override[d] > 0) {
+      M = P.grid_override[d];
+    } else {
+      if (!(P.h > 0.0) || !std::isfinite(P.h)) return fail(err, MSM_ERR_INVALID_ARG, "h must be > 0");
+      double ratio = S.L[d] / P.h;
+      if (S.pbc[d]) {
+        int e = (int)std::floor(std::log2(ratio) + 0.5);
+        e = std::max(e, 1);
+        if (e > 16) return fail(err, MSM_ERR_UNSUPPORTED, "periodic grid above 65536 points per axis");
+        M = 1 << e;
+      } else {
+        M = std::max(1, (int)std::ceil(ratio));
+      }
+    }
+    if (M > 65536) return fail(err, MSM_ERR_UNSUPPORTED, "grid above 65536 intervals per axis");
+    if (S.pbc[d]) {
+      if (M < 2 || (M & (M - 1))) return fail(err, MSM_ERR_UNSUPPORTED, "periodic grid counts must be powers of two >= 2");
+      if (Mper && Mper != M) return fail(err, MSM_ERR_UNSUPPORTED, "periodic axes must have equal grid counts");
+      Mper = M;
+    }
+    S.M[d] = M;
+    S.h1[d] = S.L[d] / M;
+  }
+  const int H = S.p / 2;
+  // level ranges: open axes keep the indices restriction can reach
+  int olo[kMaxLev][3], on[kMaxLev][3];
+  for (int d = 0; d < 3; d++) {
+    olo[0][d] = -H;
+    on[0][d] = S.M[d] + 2 * H + 1;
+    for (int l = 1; l < kMaxLev; l++) {
+      int lo = olo[l - 1][d], hi = lo + on[l - 1][d] - 1;
+      int a = lo - H, b = hi + H;
+      int nlo = (a >= 0) ? (a + 1) / 2 : -((-a) / 2);  // ceil(a/2)
+      int nhi = (b >= 0) ? b / 2 : -((-b + 1) / 2);    // floor(b/2)
+      olo[l][d] = nlo;
+      on[l][d] = nhi - nlo + 1;
+    }
+  }
+  if (Mper) {
+    int L = 1;
+    while ((1 << (L - 1)) < Mper) L++;
+    if (P.levels > 0 && P.levels != L)
+      return fail(err, MSM_ERR_UNSUPPORTED, "levels is fixed by the periodic grid (log2(M) + 1)");
+    S.nlev = L;
+    S.ncomp = L - 1;
+  } else {
+    if (P.levels > 0) {
+      S.nlev = P.levels;
+    } else {
+      int cap = std::max(8, S.p + 1), L = 1;
+      while (L < kMaxLev && (on[L - 1][0] > cap || on[L - 1][1] > cap || on[L - 1][2] > cap)) L++;
+      S.nlev = L;
+    }
+    if (S.nlev > kMaxLev) return fail(err, MSM_ERR_UNSUPPORTED, "too many levels");
+    S.ncomp = S.nlev;
+  }
+  S.lev.assign(S.ncomp, LevelHost());
+  for (int l = 1; l <= S.ncomp; l++) {
+    LevelHost& Lv = S.lev[l - 1];
+    for (int d = 0; d < 3; d++) {
+      Lv.per[d] = S.pbc[d];
+      if (S.pbc[d]) {
+        Lv.lo[d] = 0;
+        Lv.n[d] = S.M[d] >> (l - 1);
+      } else {
+        Lv.lo[d] = olo[l - 1][d];
+        Lv.n[d] = on[l - 1][d];
+      }
+    }
+  }
+  // stencil radius, binning cells
+  for (int d = 0; d < 3; d++) {
+    S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a / S.h1[d]) - 1);
+    S.R[d] = S.S[d] + H - 1;
+    int C = (int)std::floor(2.0 * S.L[d] / S.a);
+    S.C[d] = std::min(std::max(C, 1), 256);
+    S.edge[d] = S.L[d] / S.C[d];
+    S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
+  }
+  // level-1 shape stencil (intermediate levels are K^1 / 2^(l-1)) and virial weights
+  const bool any_mid = S.ncomp >= 1 && S.nlev > 1;
+  S.has_ball = false;
+  Box3 K1, dK1[6];
+  if (any_mid) {
+    build_stencil(S, 1, S.R, 0, K1);
+    for (int c = 0; c < 6; c++) build_stencil(S, 1, S.R, c + 1, dK1[c]);
+  }
+  for (int l = 1; l <= S.ncomp; l++) {
+    LevelHost& Lv = S.lev[l - 1];
+    Lv.scale = (float)std::ldexp(1.0, -(l - 1));
+    bool top = (l == S.nlev);
+    // ball kernels are compiled for radii up to kBallRmax; larger stencils
+    // (and stencils that overlap themselves on a periodic grid) use the box kernel
+    bool ball = !top;
+    for (int d = 0; d < 3; d++)
+      if ((Lv.per[d] && 2 * S.R[d] + 1 > Lv.n[d]) || S.R[d] > kBallRmax) ball = false;
+    for (int d = 0; d < 3; d++) Lv.R[d] = S.R[d];
+    if (ball) {
+      Lv.kind = 0;
+      S.has_ball = true;
+      continue;
+    }
+    Lv.kind = 1;
+    Box3 Kf, dKf[6];
+    if (top) {
+      int E[3];
+      for (int d = 0; d < 3; d++) E[d] = Lv.n[d] - 1;
+      Box3 Kt, dKt[6];
+      build_stencil(S, l, E, 0, Kt);
+      for (int c = 0; c < 6; c++) build_stencil(S, l, E, c + 1, dKt[c]);
+      fold(Kt, Lv.n, Lv.per, 1.0, Kf);
+      for (int c = 0; c < 6; c++) fold(dKt[c], Lv.n, Lv.per, 1.0, dKf[c]);
+    } else {
+      double sc = std::ldexp(1.0, -(l - 1));
+      fold(K1, Lv.n, Lv.per, sc, Kf);
+      for (int c = 0; c < 6; c++) fold(dK1[c], Lv.n, Lv.per, sc, dKf[c]);
+    }
+    Lv.scale = 1.0f;
+    for (int d = 0; d < 3; d++) {
+      Lv.blo[d] = Kf.o[d];
+      Lv.bsz[d] = Kf.s[d];
+    }
+    Lv.kbox.assign(Kf.v.begin(), Kf.v.end());
+    Lv.dkbox.clear();
+    for (int c = 0; c < 6; c++) Lv.dkbox.insert(Lv.dkbox.end(), dKf[c].v.begin(), dKf[c].v.end());
+  }
+  if (S.has_ball) {
+    const int nx = 2 * S.R[0] + 1, ny = 2 * S.R[1] + 1, nz = 2 * S.R[2] + 1;
+    S.kball.assign(K1.v.begin(), K1.v.end());
+    S.dkh.assign((size_t)6 * nx * ny * nz, 0.0f);
+    S.wball.assign((size_t)nx * ny, -1);
+    S.whalf.assign((size_t)nx * ny, -1);
+    for (int x = -S.R[0]; x <= S.R[0]; x++)
+      for (int y = -S.R[1]; y <= S.R[1]; y++)
+        for (int z = -S.R[2]; z <= S.R[2]; z++) {
+          size_t at = ((size_t)(x + S.R[0]) * ny + (y + S.R[1])) * nz + (z + S.R[2]);
+          size_t col = (size_t)(x + S.R[0]) * ny + (y + S.R[1]);
+          if ((float)K1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z));
+          // half-space weights: C_d = C_-d, so sum_d dK_d C_d = dK_0 C_0 + 2 sum_(d in half) dK_d C_d
+          bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
+          bool zero = x == 0 && y == 0 && z == 0;
+          double f = half ? 2.0 : (zero ? 1.0 : 0.0);
+          bool any = false;
+          for (int c = 0; c < 6; c++) {
+            float v = (float)(f * dK1[c].v[at]);
+            S.dkh[(size_t)c * nx * ny * nz + at] = v;
+            if (v != 0.0f) any = true;
+          }
+          if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z));
+        }
+  }
+  // scalar coefficients
+  softening_coeffs(S.p, S.gc);
+  {
+    double binom = 1.0;
+    for (int k = 0; k <= S.p; k++) {
+      S.jc[k] = std::ldexp(binom, 1 - S.p);
+      binom = binom * (S.p - k) / (k + 1);
+    }
+  }
+  return MSM_OK;
+}
+
+// ------------------------------------------------------------------ engine
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool single_, std::string* err) {
+  nsys = nsys_;
+  single = single_;
+  sys.assign(nsys, SysHost());
+  for (int s = 0; s < nsys; s++) {
+    int rc = plan_system(prm[s], sys[s], err);
+    if (rc) return rc;
+    if (counts[s] < 0) return fail(err, MSM_ERR_INVALID_ARG, "atom counts must be >= 0");
+    if (sys[s].p != sys[0].p) return fail(err, MSM_ERR_UNSUPPORTED, "all systems of a batch need the same order");
+  }
+  p = sys[0].p;
+  // systems, atoms, cells, levels, grid pool
+  std::vector<SysDev> hs(nsys);
+  hlev.clear();
+  atom_items.clear();
+  long long grid_off = 0;
+  int atom_off = 0, cell_off = 0;
+  maxcomp = 0;
+  for (int s = 0; s < nsys; s++) {
+    SysHost& S = sys[s];
+    SysDev& D = hs[s];
+    std::memset(&D, 0, sizeof(D));
+    D.n = counts[s];
+    D.atom_off = atom_off;
+    D.cell_off = cell_off;
+    D.p = S.p;
+    D.ncomp = S.ncomp;
+    D.lev0 = (int)hlev.size();
+    D.item0 = (int)atom_items.size();
+    for (int d = 0; d < 3; d++) {
+      D.C[d] = S.C[d];
+      D.nnbr[d] = S.nnbr[d];
+      D.pbc[d] = S.pbc[d];
+      D.M[d] = S.M[d];
+      D.edge[d] = (float)S.edge[d];
+      D.invL[d] = (float)(1.0 / S.L[d]);
+      D.Mf[d] = (float)S.M[d];
+      D.inv_h1[d] = (float)(1.0 / S.h1[d]);
+    }
+    D.a2 = (float)(S.a * S.a);
+    D.inv_a = (float)(1.0 / S.a);
+    D.inv_a2 = (float)(1.0 / (S.a * S.a));
+    D.inv_a3 = (float)(1.0 / (S.a * S.a * S.a));
+    D.self_coef = (float)(soft(S.p, 0.0) / S.a);
+    for (int k = 0; k < S.p; k++) D.gc[k] = (float)S.gc[k];
+    for (int k = 0; k + 1 < S.p; k++) D.gdc[k] = (float)((k + 1) * S.gc[k + 1]);
+    for (int k = 0; k <= S.p; k++) D.jc[k] = (float)S.jc[k];
+    for (int st = 0; st < counts[s]; st += kChunk) atom_items.push_back({s, st, std::min(kChunk, counts[s] - st)});
+    if (counts[s] == 0) atom_items.push_back({s, 0, 0});
+    D.nitem = (int)atom_items.size() - D.item0;
+    atom_off += counts[s];
+    cell_off += S.C[0] * S.C[1] * S.C[2];
+    maxcomp = std::max(maxcomp, S.ncomp);
+    for (int l = 1; l <= S.ncomp; l++) {
+      LevDev L;
+      std::memset(&L, 0, sizeof(L));
+      const LevelHost& Lv = S.lev[l - 1];
+      L.sys = s;
+      L.level = l;
+      for (int d = 0; d < 3; d++) {
+        L.n[d] = Lv.n[d];
+        L.lo[d] = Lv.lo[d];
+        L.per[d] = Lv.per[d];
+        L.R[d] = Lv.R[d];
+        L.blo[d] = Lv.blo[d];
+        L.bsz[d] = Lv.bsz[d];
+      }
+      L.kind = Lv.kind;
+      L.scale = Lv.scale;
+      long long npts = (long long)Lv.n[0] * Lv.n[1] * Lv.n[2];
+      L.q_off = grid_off;
+      grid_off += align_up(npts, 64);
+      L.e_off = grid_off;
+      grid_off += align_up(npts, 64);
+      hlev.push_back(L);
+    }
+  }
+  total_atoms = atom_off;
+  total_cells = cell_off;
+  grid_floats = grid_off;
+  // stencil pools
+  std::vector<float> kp;
+  std::vector<int> wp;
+  for (int s = 0; s < nsys; s++) {
+    SysHost& S = sys[s];
+    long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1;
+    if (S.has_ball) {
+      kball_off = (long long)kp.size();
+      kp.insert(kp.end(), S.kball.begin(), S.kball.end());
+      dkh_off = (long long)kp.size();
+      kp.insert(kp.end(), S.dkh.begin(), S.dkh.end());
+      wb_off = (long long)wp.size();
+      wp.insert(wp.end(), S.wball.begin(), S.wball.end());
+      wh_off = (long long)wp.size();
+      wp.insert(wp.end(), S.whalf.begin(), S.whalf.end());
+    }
+    for (int l = 1; l <= S.ncomp; l++) {
+      LevDev& L = hlev[hs[s].lev0 + l - 1];
+      const LevelHost& Lv = S.lev[l - 1];
+      if (L.kind == 0) {
+        L.k_off = kball_off;
+        L.dk_off = dkh_off;
+        L.w_off = wb_off;
+        L.wh_off = wh_off;
+      } else {
+        while (kp.size() % 4) kp.push_back(0.f);
+        L.k_off = (long long)kp.size();
+        kp.insert(kp.end(), Lv.kbox.begin(), Lv.kbox.end());
+        L.dk_off = (long long)kp.size();
+        kp.insert(kp.end(), Lv.dkbox.begin(), Lv.dkbox.end());
+      }
+    }
+    while (kp.size() % 4) kp.push_back(0.f);
+  }
+  if (kp.empty()) kp.push_back(0.f);
+  if (wp.empty()) wp.push_back(0);
+  // work lists
+  anterp_items.clear();
+  ball_items.clear();
+  box_items.clear();
+  vb_off.assign(nsys + 1, 0);
+  vx_off.assign(nsys + 1, 0);
+  rmax = 0;
+  ryz[0] = ryz[1] = 0;
+  for (int s = 0; s < nsys; s++) {
+    const SysHost& S = sys[s];
+    vb_off[s] = (int)ball_items.size();
+    vx_off[s] = (int)box_items.size();
+    for (int l = 1; l <= S.ncomp; l++) {
+      int li = hs[s].lev0 + l - 1;
+      const LevDev& L = hlev[li];
+      if (l == 1)
+        for (int x = 0; x < L.n[0]; x += kAnterpT)
+          for (int y = 0; y < L.n[1]; y += kAnterpT)
+            for (int z = 0; z < L.n[2]; z += kAnterpT) anterp_items.push_back({li, x, y, z});
+      if (L.kind == 0) {
+        for (int x = 0; x < L.n[0]; x++)
+          for (int y = 0; y < L.n[1]; y += kBallTY)
+            for (int z = 0; z < L.n[2]; z += kBallTZ) ball_items.push_back({li, x, y, z});
+        rmax = std::max(rmax, L.R[2]);
+        ryz[0] = std::max(ryz[0], L.R[1]);
+        ryz[1] = std::max(ryz[1], L.R[2]);
+      } else {
+        long long npts = (long long)L.n[0] * L.n[1] * L.n[2];
+        for (long long st = 0; st < npts; st += kBoxChunk)
+          box_items.push_back({li, (int)st, (int)std::min<long long>(kBoxChunk, npts - st)});
+      }
+    }
+  }
+  vb_off[nsys] = (int)ball_items.size();
+  vx_off[nsys] = (int)box_items.size();
+  restrict_steps.assign(std::max(0, maxcomp - 1), std::vector<RangeItem>());
+  prolong_steps.assign(std::max(0, maxcomp - 1), std::vector<RangeItem>());
+  for (int l = 1; l < maxcomp; l++) {
+    for (int s = 0; s < nsys; s++) {
+      if (sys[s].ncomp <= l) continue;
+      int fi = hs[s].lev0 + l - 1, ci = fi + 1;
+      const LevDev& F = hlev[fi];
+      const LevDev& Cc = hlev[ci];
+      long long nc = (long long)Cc.n[0] * Cc.n[1] * Cc.n[2];
+      for (long long st = 0; st < nc; st += kGridChunk)
+        restrict_steps[l - 1].push_back({ci, (int)st, (int)std::min<long long>(kGridChunk, nc - st)});
+      long long nf = (long long)F.n[0] * F.n[1] * F.n[2];
+      for (long long st = 0; st < nf; st += kGridChunk)
+        prolong_steps[l - 1].push_back({fi, (int)st, (int)std::min<long long>(kGridChunk, nf - st)});
+    }
+  }
+  // device tables
+  std::vector<int> voff(2 * (nsys + 1));
+  for (int s = 0; s <= nsys; s++) {
+    voff[s] = vb_off[s];
+    voff[nsys + 1 + s] = (int)ball_items.size() + vx_off[s];
+  }
+  hsys = hs;
+  int rc = upload(kp, wp, voff, err);
+  if (rc) return rc;
+  // workspace layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return o;
+  };
+  const size_t N = (size_t)std::max(total_atoms, 1);
+  const int ntiles = (total_cells + 4095) / 4096;
+  L_status = take(256);
+  L_cell_count = take(sizeof(int) * total_cells);
+  L_cell_start = take(sizeof(int) * (total_cells + 1));
+  L_scan_tiles = take(sizeof(int) * std::max(ntiles, 1));
+  L_cell_id = take(sizeof(int) * N);
+  L_slot = take(sizeof(int) * N);
+  L_bucket = take(sizeof(int) * N);
+  L_perm = take(sizeof(int) * N);
+  L_scell = take(sizeof(int) * N);
+  L_xq = take(sizeof(float4) * N);
+  L_uq = take(sizeof(float4) * N);
+  L_phi_sr = take(sizeof(float) * N);
+  L_phi_lr = take(sizeof(float) * N);
+  L_f_sr = take(sizeof(float4) * N);
+  L_f_lr = take(sizeof(float4) * N);
+  L_part_e = take(sizeof(double) * atom_items.size());
+  L_part_w0 = take(sizeof(double) * 6 * atom_items.size());
+  L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(ball_items.size() + box_items.size(), 1));
+  L_grid = take(sizeof(float) * std::max<long long>(grid_floats, 1));
+  ws_bytes = off;
+  return MSM_OK;
+}
+
+template <class T>
+static int up(const std::vector<T>& h, T** d, std::string* err) {
+  size_t b = sizeof(T) * std::max<size_t>(h.size(), 1);
+  if (cudaMalloc((void**)d, b) != cudaSuccess) return fail(err, MSM_ERR_CUDA, "cudaMalloc of plan tables failed");
+  if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(err, MSM_ERR_CUDA, "cudaMemcpy of plan tables failed");
+  return MSM_OK;
+}
+
+int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, const std::vector<int>& voff,
+                   std::string* err) {
+  int rc;
+  if ((rc = up(hsys, &d_sys, err))) return rc;
+  if ((rc = up(hlev, &d_lev, err))) return rc;
+  if ((rc = up(kp, &d_kpool, err))) return rc;
+  if ((rc = up(wp, &d_wpool, err))) return rc;
+  if ((rc = up(atom_items, &d_atom_items, err))) return rc;
+  if ((rc = up(anterp_items, &d_anterp_items, err))) return rc;
+  if ((rc = up(ball_items, &d_ball_items, err))) return rc;
+  if ((rc = up(box_items, &d_box_items, err))) return rc;
+  if ((rc = up(voff, &d_voff, err))) return rc;
+  std::vector<RangeItem> all;
+  restrict_off.assign(restrict_steps.size() + 1, 0);
+  for (size_t i = 0; i < restrict_steps.size(); i++) {
+    restrict_off[i] = (int)all.size();
+    all.insert(all.end(), restrict_steps[i].begin(), restrict_steps[i].end());
+  }
+  restrict_off[restrict_steps.size()] = (int)all.size();
+  prolong_off.assign(prolong_steps.size() + 1, 0);
+  for (size_t i = 0; i < prolong_steps.size(); i++) {
+    prolong_off[i] = (int)all.size();
+    all.insert(all.end(), prolong_steps[i].begin(), prolong_steps[i].end());
+  }
+  prolong_off[prolong_steps.size()] = (int)all.size();
+  if ((rc = up(all, &d_range_items, err))) return rc;
+  return MSM_OK;
+}
+
+Engine::~Engine() {
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(d_sys);
+  cudaFree(d_lev);
+  cudaFree(d_kpool);
+  cudaFree(d_wpool);
+  cudaFree(d_atom_items);
+  cudaFree(d_anterp_items);
+  cudaFree(d_ball_items);
+  cudaFree(d_box_items);
+  cudaFree(d_voff);
+  cudaFree(d_range_items);
+}
+
+Work Engine::resolve(void* ws) const {
+  char* b = (char*)ws;
+  Work w;
+  w.status = (int*)(b + L_status);
+  w.cell_count = (int*)(b + L_cell_count);
+  w.cell_start = (int*)(b + L_cell_start);
+  w.scan_tiles = (int*)(b + L_scan_tiles);
+  w.cell_id = (int*)(b + L_cell_id);
+  w.slot = (int*)(b + L_slot);
+  w.bucket = (int*)(b + L_bucket);
+  w.perm = (int*)(b + L_perm);
+  w.scell = (int*)(b + L_scell);
+  w.xq = (float4*)(b + L_xq);
+  w.uq = (float4*)(b + L_uq);
+  w.phi_sr = (float*)(b + L_phi_sr);
+  w.phi_lr = (float*)(b + L_phi_lr);
+  w.f_sr = (float4*)(b + L_f_sr);
+  w.f_lr = (float4*)(b + L_f_lr);
+  w.part_e = (double*)(b + L_part_e);
+  w.part_w0 = (double*)(b + L_part_w0);
+  w.part_wg = (double*)(b + L_part_wg);
+  w.grid = (float*)(b + L_grid);
+  return w;
+}
+
+Tables Engine::tables() const {
+  Tables t;
+  t.sys = d_sys;
+  t.lev = d_lev;
+  t.kpool = d_kpool;
+  t.wpool = d_wpool;
+  return t;
+}
+
+}  // namespace msm

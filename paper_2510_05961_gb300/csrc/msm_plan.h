@@ -1,0 +1,97 @@
+// msm_plan.h -- host-side plan and engine of the GB300 MSM library (private).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/msm_gb300.h"
+#include "msm_internal.h"
+
+namespace msm {
+
+struct LevelHost {
+  int n[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, per[3] = {0, 0, 0};
+  int kind = 0;                      // 0 ball, 1 box
+  int R[3] = {0, 0, 0};
+  int blo[3] = {0, 0, 0}, bsz[3] = {0, 0, 0};
+  float scale = 1.0f;
+  std::vector<float> kbox, dkbox;    // box kind: folded stencil and 6 derivative arrays
+};
+
+struct SysHost {
+  double L[3];
+  int pbc[3];
+  double a;
+  int p;
+  int M[3];
+  double h1[3];
+  int nlev = 0, ncomp = 0;
+  int S[3], R[3];
+  int C[3];
+  double edge[3];
+  int nnbr[3];
+  double gc[8];
+  double jc[9];
+  std::vector<LevelHost> lev;
+  bool has_ball = false;
+  std::vector<float> kball, dkh;     // level-1 shape stencil (dense (2R+1)^3), half-space virial weights (6x)
+  std::vector<int> wball, whalf;     // column half-widths, -1 = empty column
+};
+
+int plan_system(const msm_params& P, SysHost& S, std::string* err);
+
+struct Engine {
+  int nsys = 0;
+  bool single = true;
+  int p = 4;
+  int maxcomp = 0;
+  int total_atoms = 0, total_cells = 0;
+  long long grid_floats = 0;
+  int rmax = 0, ryz[2] = {0, 0};
+  std::vector<SysHost> sys;
+  std::vector<SysDev> hsys;
+  std::vector<LevDev> hlev;
+  std::vector<AtomItem> atom_items;
+  std::vector<TileItem> anterp_items, ball_items;
+  std::vector<RangeItem> box_items;
+  std::vector<std::vector<RangeItem>> restrict_steps, prolong_steps;
+  std::vector<int> restrict_off, prolong_off;
+  std::vector<int> vb_off, vx_off;
+  // device tables (owned)
+  SysDev* d_sys = nullptr;
+  LevDev* d_lev = nullptr;
+  float* d_kpool = nullptr;
+  int* d_wpool = nullptr;
+  AtomItem* d_atom_items = nullptr;
+  TileItem* d_anterp_items = nullptr;
+  TileItem* d_ball_items = nullptr;
+  RangeItem* d_box_items = nullptr;
+  RangeItem* d_range_items = nullptr;
+  int* d_voff = nullptr;
+  // workspace layout (byte offsets)
+  size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
+      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_w0, L_part_wg, L_grid;
+  size_t ws_bytes = 0;
+  // state of the last forward pass
+  bool have_fwd = false;
+  int last_flags = 0;
+  void* last_ws = nullptr;
+  int last_n = 0;
+  // phase timing (msm_profile) and launch counts
+  bool profiling = false;
+  cudaEvent_t ev[2 * 10] = {};
+  bool ev_used[10] = {};
+  int launches_fwd = 0, launches_bwd = 0;
+
+  Engine() = default;
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
+  ~Engine();
+  int build(const msm_params* prm, const int* counts, int nsys, bool single, std::string* err);
+  int upload(const std::vector<float>& kp, const std::vector<int>& wp, const std::vector<int>& voff,
+             std::string* err);
+  Work resolve(void* ws) const;
+  Tables tables() const;
+};
+
+}  // namespace msm

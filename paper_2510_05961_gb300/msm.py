@@ -1,0 +1,244 @@
+"""Python front end of the GB300 MSM library.
+
+PyTorch provides device memory and streams; every step of the method runs in
+the library's CUDA kernels, called through the C ABI. ``MSMFunction`` is the
+autograd wrapper: its backward reuses the sorted bins, level grids and
+per-atom results the forward left in the plan's workspace (the hand-written
+adjoint of Sec. 3.2.2, Eqs. analytic_uoneplus_position_grad /
+analytic_uoneplus_charge_grad) and also yields the virial.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Plan:
+    """One system: cell, periodicity, level-one spacing h, cutoff a, order p, levels.
+
+    Holds the library plan (device stencil tables) and a workspace tensor
+    sized for ``max_atoms``. Not thread-safe; one forward/backward at a time.
+    """
+
+    def __init__(self, cell, pbc, h, cutoff, order=4, levels=0, grid_override=(0, 0, 0), max_atoms=1,
+                 device=None):
+        self.lib = L.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.params = L.make_params(cell, pbc, h, cutoff, order, levels, grid_override, max_atoms)
+            h_ = C.c_void_p()
+            L.check(self.lib.msm_plan_create(C.byref(self.params), C.byref(h_)))
+            self.handle = h_
+            nb = C.c_size_t()
+            L.check(self.lib.msm_workspace_bytes(self.handle, C.byref(nb)))
+            self.workspace = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        self.max_atoms = int(max_atoms)
+        self.last_virial = None
+        self._n = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and self.lib is not None:
+                self.lib.msm_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ info
+    def info(self):
+        I = L.PlanInfo()
+        L.check(self.lib.msm_plan_get_info(self.handle, C.byref(I)))
+        return {
+            "nlev": I.nlev, "ncomp": I.ncomp, "M": list(I.M), "h1": list(I.h1),
+            "lo": [list(I.lo[l]) for l in range(I.ncomp)], "n": [list(I.n[l]) for l in range(I.ncomp)],
+            "R": list(I.R), "C": list(I.C), "nnbr": list(I.nnbr),
+            "stencil_kind": [I.stencil_kind[l] for l in range(I.ncomp)],
+        }
+
+    def debug_array(self, which, level=1):
+        """View of an internal workspace array (0 cell_start, 1 perm, 2 grid charge, 3 grid potential, 4 sorted cell)."""
+        off = C.c_size_t()
+        cnt = C.c_size_t()
+        L.check(self.lib.msm_debug_offset(self.handle, which, level, C.byref(off), C.byref(cnt)))
+        dt = torch.float32 if which in (2, 3) else torch.int32
+        nbytes = int(cnt.value) * 4
+        return self.workspace[int(off.value):int(off.value) + nbytes].view(dt)
+
+    # ------------------------------------------------------------------ calls
+    def forward(self, pos, q, forces=True, virial=False, phi=True):
+        """Energy (float64, shape (1,)), potentials (n,) and forces (n, 3) of float32 device inputs."""
+        n = int(pos.shape[0])
+        assert pos.dtype == torch.float32 and q.dtype == torch.float32 and pos.is_contiguous() and q.is_contiguous()
+        assert pos.device == self.device and q.device == self.device
+        E = torch.empty(1, dtype=torch.float64, device=self.device)
+        ph = torch.empty(n, dtype=torch.float32, device=self.device) if phi else None
+        F = torch.empty((n, 3), dtype=torch.float32, device=self.device) if forces else None
+        flags = (L.MSM_WANT_FORCES if forces else 0) | (L.MSM_WANT_VIRIAL if virial else 0)
+        L.check(self.lib.msm_forward(self.handle, _ptr(self.workspace), self.workspace.numel(), n, _ptr(pos), _ptr(q),
+                                     _ptr(E), _ptr(ph), _ptr(F), flags, _stream(self.device)))
+        self._n = n
+        return E, ph, F
+
+    def backward(self, grad_E, dpos=True, dq=True, virial=True):
+        """dE/dpos, dE/dq (scaled by grad_E) and the virial (3x3 float64) from the last forward."""
+        n = self._n
+        g = grad_E.to(device=self.device, dtype=torch.float64).reshape(1).contiguous()
+        gp = torch.empty((n, 3), dtype=torch.float32, device=self.device) if dpos else None
+        gq = torch.empty(n, dtype=torch.float32, device=self.device) if dq else None
+        W = torch.empty(9, dtype=torch.float64, device=self.device) if virial else None
+        L.check(self.lib.msm_backward(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gp), _ptr(gq), _ptr(W),
+                                      _stream(self.device)))
+        if W is not None:
+            W = W.view(3, 3)
+            self.last_virial = W
+        return gp, gq, W
+
+    def status(self):
+        st = C.c_int()
+        L.check(self.lib.msm_status(self.handle, _ptr(self.workspace), _stream(self.device), C.byref(st)))
+        return st.value
+
+    def evaluate_host(self, pos, q, virial=True, pinned_out=None):
+        """End-to-end call on host tensors: copy in, forward + backward, copy out.
+
+        pos (n, 3) and q (n,) are float32 CPU tensors (pinned for asynchronous
+        copies). Returns host (E, dE/dpos, dE/dq, virial) after synchronising.
+        """
+        n = int(pos.shape[0])
+        dpos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
+        dq = torch.empty(n, dtype=torch.float32, device=self.device)
+        dpos.copy_(pos, non_blocking=True)
+        dq.copy_(q, non_blocking=True)
+        E, _, _ = self.forward(dpos, dq, forces=True, virial=virial, phi=False)
+        g = torch.ones(1, dtype=torch.float64, device=self.device)
+        gp, gq, W = self.backward(g, dpos=True, dq=True, virial=virial)
+        if pinned_out is None:
+            pinned_out = (torch.empty(1, dtype=torch.float64, pin_memory=True),
+                          torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
+                          torch.empty(n, dtype=torch.float32, pin_memory=True),
+                          torch.empty((3, 3), dtype=torch.float64, pin_memory=True))
+        oE, op, oq, oW = pinned_out
+        oE.copy_(E, non_blocking=True)
+        op.copy_(gp, non_blocking=True)
+        oq.copy_(gq, non_blocking=True)
+        if W is not None:
+            oW.copy_(W, non_blocking=True)
+        torch.cuda.current_stream(self.device).synchronize()
+        return oE, op, oq, oW
+
+    def profile(self, enable=True):
+        """Record CUDA-event times per phase of every forward/backward."""
+        L.check(self.lib.msm_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """(dict phase -> ms of the last forward + backward, kernels launched by them)."""
+        ms = (C.c_double * len(L.PHASES))()
+        nl = C.c_int()
+        L.check(self.lib.msm_profile_read(self.handle, ms, C.byref(nl)))
+        return {p: ms[i] for i, p in enumerate(L.PHASES)}, nl.value
+
+
+class MSMFunction(torch.autograd.Function):
+    """E = MSM energy of (pos, q); backward gives dE/dpos, dE/dq; plan.last_virial holds W * dL/dE."""
+
+    @staticmethod
+    def forward(ctx, pos, q, plan):
+        need_f = pos.requires_grad
+        E, _, _ = plan.forward(pos.detach().contiguous(), q.detach().contiguous(), forces=need_f, virial=True,
+                               phi=False)
+        ctx.plan = plan
+        ctx.need = (pos.requires_grad, q.requires_grad)
+        return E.reshape(())
+
+    @staticmethod
+    def backward(ctx, gE):
+        if gE is None:
+            return None, None, None
+        plan = ctx.plan
+        gp, gq, _ = plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
+        return gp, gq, None
+
+
+def msm_energy(pos, q, plan):
+    """Differentiable MSM energy (autograd through the library's adjoint kernels)."""
+    return MSMFunction.apply(pos, q, plan)
+
+
+class Batch:
+    """Many independent systems in one set of launches (one launch per MSM phase).
+
+    systems: list of dicts/objects with cell, pbc, h, a (cutoff), p (order), levels, n.
+    Atoms are packed back to back in system order.
+    """
+
+    def __init__(self, systems, device=None):
+        self.lib = L.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        ns = len(systems)
+        arr = (L.Params * ns)()
+        counts = (C.c_int * ns)()
+        self.counts = []
+        for i, s in enumerate(systems):
+            arr[i] = L.make_params(s.cell, s.pbc, s.h, s.a, s.p, getattr(s, "levels", 0),
+                                   getattr(s, "grid_override", (0, 0, 0)), 0)
+            counts[i] = int(s.n)
+            self.counts.append(int(s.n))
+        with torch.cuda.device(self.device):
+            h_ = C.c_void_p()
+            L.check(self.lib.msm_batch_create(arr, counts, ns, C.byref(h_)))
+            self.handle = h_
+            nb = C.c_size_t()
+            L.check(self.lib.msm_batch_workspace_bytes(self.handle, C.byref(nb)))
+            self.workspace = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        self.nsys = ns
+        self.ntot = sum(self.counts)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and self.lib is not None:
+                self.lib.msm_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def forward(self, pos, q, forces=True, virial=False, phi=True, out=None):
+        n = self.ntot
+        if out is None:
+            E = torch.empty(self.nsys, dtype=torch.float64, device=self.device)
+            ph = torch.empty(n, dtype=torch.float32, device=self.device) if phi else None
+            F = torch.empty((n, 3), dtype=torch.float32, device=self.device) if forces else None
+        else:
+            E, ph, F = out
+        flags = (L.MSM_WANT_FORCES if forces else 0) | (L.MSM_WANT_VIRIAL if virial else 0)
+        L.check(self.lib.msm_batch_forward(self.handle, _ptr(self.workspace), self.workspace.numel(), _ptr(pos),
+                                           _ptr(q), _ptr(E), _ptr(ph), _ptr(F), flags, _stream(self.device)))
+        return E, ph, F
+
+    def backward(self, grad_E, dpos=True, dq=True, virial=True, out=None):
+        n = self.ntot
+        g = grad_E.to(device=self.device, dtype=torch.float64).reshape(self.nsys).contiguous()
+        if out is None:
+            gp = torch.empty((n, 3), dtype=torch.float32, device=self.device) if dpos else None
+            gq = torch.empty(n, dtype=torch.float32, device=self.device) if dq else None
+            W = torch.empty(9 * self.nsys, dtype=torch.float64, device=self.device) if virial else None
+        else:
+            gp, gq, W = out
+        L.check(self.lib.msm_batch_backward(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gp), _ptr(gq), _ptr(W),
+                                            _stream(self.device)))
+        return gp, gq, (None if W is None else W.view(self.nsys, 3, 3))
+
+    def status(self):
+        st = C.c_int()
+        L.check(self.lib.msm_batch_status(self.handle, _ptr(self.workspace), _stream(self.device), C.byref(st)))
+        return st.value

@@ -1,0 +1,147 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol,
+and its host planner (grids, levels, stencils) agrees with the oracle's.
+
+No compute call runs here (there is no GPU); the planner queries are
+host-only entry points of the library.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2510_05961_gb300 import _lib, build
+from paper_2510_05961_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "msm_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(msm_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    decl = _declared()
+    assert len(decl) >= 15
+    assert sorted(_lib.EXPORTS) == decl
+    for name in decl:
+        assert hasattr(lib, name), name
+
+
+def _describe(lib, w=None, **kw):
+    if w is not None:
+        kw = dict(cell=w.cell, pbc=w.pbc, h=w.h, cutoff=w.a, order=w.p, levels=w.levels,
+                  grid_override=w.grid_override)
+    P = _lib.make_params(kw["cell"], kw["pbc"], kw["h"], kw["cutoff"], kw["order"], kw.get("levels", 0),
+                         kw.get("grid_override", (0, 0, 0)), 1)
+    I = _lib.PlanInfo()
+    rc = lib.msm_plan_describe(C.byref(P), C.byref(I))
+    return rc, I, P
+
+
+CASES = [
+    dict(cell=(30, 30, 30), pbc=(0, 0, 0), h=2.5, cutoff=10.0, order=4, levels=3),
+    dict(cell=(49.6,) * 3, pbc=(1, 1, 1), h=1.5, cutoff=9.0, order=6),
+    dict(cell=((1024000 / 0.1) ** (1 / 3),) * 3, pbc=(1, 1, 1), h=2.0, cutoff=8.0, order=4),
+    dict(cell=((16384000 / 0.1) ** (1 / 3),) * 3, pbc=(1, 1, 1), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(180.48,) * 3, pbc=(1, 1, 1), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(6.3, 6.3, 6.3), pbc=(1, 1, 1), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(6.3, 6.3, 6.3), pbc=(0, 0, 0), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(20.0, 20.0, 20.0), pbc=(1, 1, 0), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(36.8, 36.8, 36.8), pbc=(1, 1, 0), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(17.0, 23.0, 29.0), pbc=(0, 0, 0), h=1.3, cutoff=4.5, order=8),
+    dict(cell=(1.0, 1.0, 1.0), pbc=(1, 1, 1), h=0.0, cutoff=2.0, order=6, grid_override=(16, 16, 16)),
+    dict(cell=(12.0, 12.0, 12.0), pbc=(0, 0, 0), h=1.0, cutoff=3.0, order=4, levels=1),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s_%s_p%d" % (c["pbc"], c["cell"][0], c["order"]))
+def test_planner_matches_oracle(lib, oracle, case):
+    rc, I, _ = _describe(lib, **case)
+    assert rc == 0, lib.msm_last_error()
+    P = oracle.make_plan(case["cell"], case["pbc"], case["h"], case["cutoff"], case["order"], case.get("levels", 0),
+                         case.get("grid_override", (0, 0, 0)))
+    s = oracle.plan_summary(P)
+    assert I.nlev == s["nlev"] and I.ncomp == s["ncomp"]
+    assert list(I.M) == s["M"]
+    assert np.allclose(list(I.h1), s["h1"], rtol=1e-15)
+    for l in range(I.ncomp):
+        assert list(I.lo[l]) == s["lo"][l] and list(I.n[l]) == s["n"][l]
+    assert list(I.R) == s["R"] and list(I.C) == s["C"] and list(I.nnbr) == s["nnbr"]
+
+
+def _lib_stencil(lib, P, level, which):
+    lo = (C.c_int * 3)()
+    sz = (C.c_int * 3)()
+    assert lib.msm_plan_stencil(C.byref(P), level, which, None, 0, lo, sz) == 0
+    out = np.zeros(sz[0] * sz[1] * sz[2], np.float32)
+    rc = lib.msm_plan_stencil(C.byref(P), level, which, out.ctypes.data_as(C.c_void_p), out.size, lo, sz)
+    assert rc == 0
+    return out.reshape(tuple(sz)).astype(np.float64), tuple(lo)
+
+
+def _fold(K, lo, n, pbc):
+    """fold an offset box onto [0, n) along periodic axes (open axes unchanged)."""
+    out_sz = [n[d] if pbc[d] else K.shape[d] for d in range(3)]
+    out = np.zeros(out_sz)
+    idx = [np.arange(K.shape[d]) + lo[d] for d in range(3)]
+    idx = [(idx[d] % n[d]) if pbc[d] else np.arange(K.shape[d]) for d in range(3)]
+    np.add.at(out, np.ix_(*idx), K)
+    return out
+
+
+@pytest.mark.parametrize("case", CASES[:2] + CASES[4:9] + CASES[10:], ids=lambda c: "%s_%s" % (c["pbc"], c["cell"][0]))
+def test_stencils_match_oracle(lib, oracle, case):
+    rc, I, Pl = _describe(lib, **case)
+    P = oracle.make_plan(case["cell"], case["pbc"], case["h"], case["cutoff"], case["order"], case.get("levels", 0),
+                         case.get("grid_override", (0, 0, 0)))
+    for l in range(1, I.ncomp + 1):
+        ref = [oracle.stencil(P, l, which)[0] for which in range(7)]
+        # tolerance: float32 rounding of the stored values, relative to the
+        # largest entry of the stencil (which 0) or of the six derivatives
+        scale_k = np.abs(ref[0]).max()
+        scale_d = max(np.abs(r).max() for r in ref[1:])
+        for which in range(7):
+            K, lo = _lib_stencil(lib, Pl, l, which)
+            Kf = _fold(K, lo, P.level_shape(l), case["pbc"])
+            assert Kf.shape == ref[which].shape, (l, which)
+            scale = scale_k if which == 0 else scale_d
+            err = np.abs(Kf - ref[which]).max()
+            assert err <= 2e-6 * scale + 1e-30, (l, which, err, scale)
+
+
+def test_planner_rejects_bad_settings(lib):
+    bad = [
+        (dict(cell=(10, 10, 10), pbc=(0, 0, 0), h=1.0, cutoff=3.0, order=5), _lib.MSM_ERR_INVALID_ARG),
+        (dict(cell=(10, 10, 10), pbc=(0, 0, 0), h=1.0, cutoff=0.0, order=4), _lib.MSM_ERR_INVALID_ARG),
+        (dict(cell=(10, 20, 10), pbc=(1, 1, 1), h=1.0, cutoff=3.0, order=4), _lib.MSM_ERR_UNSUPPORTED),
+        (dict(cell=(10, 10, 10), pbc=(1, 1, 1), h=1.0, cutoff=3.0, order=4, levels=2), _lib.MSM_ERR_UNSUPPORTED),
+        (dict(cell=(10, 10, 10), pbc=(1, 1, 1), h=0.0, cutoff=3.0, order=4, grid_override=(12, 12, 12)),
+         _lib.MSM_ERR_UNSUPPORTED),
+        (dict(cell=(10, 10, -1), pbc=(0, 0, 0), h=1.0, cutoff=3.0, order=4), _lib.MSM_ERR_INVALID_ARG),
+    ]
+    for kw, code in bad:
+        rc, _, _ = _describe(lib, **kw)
+        assert rc == code, (kw, rc)
+        assert lib.msm_last_error()
+    # a sheared cell is outside this build
+    P = _lib.make_params([10, 1, 0, 0, 10, 0, 0, 0, 10], (1, 1, 1), 1.0, 3.0, 4)
+    I = _lib.PlanInfo()
+    assert lib.msm_plan_describe(C.byref(P), C.byref(I)) == _lib.MSM_ERR_UNSUPPORTED
+
+
+def test_batch_systems_plan(lib, oracle):
+    for w in W.batch_systems(nsys=30, seed=77):
+        rc, I, _ = _describe(lib, w)
+        assert rc == 0, lib.msm_last_error()
+        s = oracle.plan_summary(oracle.plan_for(w))
+        assert I.nlev == s["nlev"] and list(I.M) == s["M"] and list(I.C) == s["C"]

@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element.
+
+Tolerances (stated by the task for the FP32 path): relative energy error
+<= 1e-5, relative RMS error of forces, potentials (dE/dq) and virial
+<= 1e-4; the binning (cell_start, permutation, sorted cells) bit-exact.
+Intermediate grids are compared to the oracle's to 1e-4 of their largest
+entry (FP32 sums of up to a few thousand cancelling terms).
+"""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2510_05961_gb300 import Batch, Plan, build, msm_energy  # noqa: E402
+from paper_2510_05961_gb300 import workloads as W  # noqa: E402
+
+E_TOL = 1e-5
+F_TOL = 1e-4
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def rel_rms(a, b):
+    a = np.asarray(a, np.float64).reshape(len(a), -1)
+    b = np.asarray(b, np.float64).reshape(len(b), -1)
+    return float(np.sqrt(((a - b) ** 2).sum(1).mean() / max((b ** 2).sum(1).mean(), 1e-300)))
+
+
+def make_plan(w, n=None):
+    return Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=n or w.n, device=DEV)
+
+
+def gpu_run(w, plan=None, forces=True, virial=True):
+    plan = plan or make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    E, phi, F = plan.forward(pos, q, forces=forces, virial=virial)
+    out = {"plan": plan, "E": float(E.cpu()[0]), "phi": phi.cpu().numpy(), "F": F.cpu().numpy() if forces else None}
+    if virial:
+        g = torch.ones(1, dtype=torch.float64, device=DEV)
+        gp, gq, Wv = plan.backward(g)
+        out.update(W=Wv.cpu().numpy(), dpos=gp.cpu().numpy(), dq=gq.cpu().numpy())
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return out
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(key):
+    import oracle as O
+    w = WORKLOADS[key]()
+    P = O.plan_for(w)
+    return P, O.msm(P, w.pos.astype(np.float64), w.q.astype(np.float64), forces=True, virial=True, grids=True)
+
+
+WORKLOADS = {
+    "open_c1": lambda: W.open_cluster(),
+    "periodic_20001": lambda: W.random_box(20001, seed=31),
+    "water_600": lambda: W.water_box(nmol=600, L=26.2, seed=32),
+    "slab_3000": lambda: W.random_box(3000, seed=33, pbc=(1, 1, 0)),
+    "tiny_periodic_40": lambda: W.random_box(40, density=0.08, seed=34),
+    "tiny_open_25": lambda: W.random_box(25, density=0.08, seed=35, pbc=(0, 0, 0)),
+    "rocksalt_6": lambda: W.rocksalt(ncell=6, seed=36),
+    "open_p8": lambda: W.open_cluster(n=700, side=24.0, seed=37, h=1.6, a=6.0, p=8, levels=0),
+}
+
+
+def _oracle(key):
+    import oracle as O  # noqa: F401
+    O.build()
+    return oracle_run(key)
+
+
+# ---------------------------------------------------------------- binning
+@pytest.mark.parametrize("key", ["open_c1", "periodic_20001", "slab_3000", "tiny_periodic_40", "water_600"])
+def test_binning_bit_exact(key):
+    import oracle as O
+    O.build()
+    w = WORKLOADS[key]()
+    r = gpu_run(w, virial=False)
+    P = O.plan_for(w)
+    cid, start, perm, st = O.bin_atoms(P, w.pos, w.q)
+    plan = r["plan"]
+    assert np.array_equal(plan.debug_array(0).cpu().numpy(), start)
+    assert np.array_equal(plan.debug_array(1).cpu().numpy(), perm)
+    assert np.array_equal(plan.debug_array(4).cpu().numpy(), cid[perm])
+
+
+# ---------------------------------------------------------------- grids
+@pytest.mark.parametrize("key", ["open_c1", "periodic_20001", "slab_3000", "tiny_periodic_40", "open_p8"])
+def test_level_grids(key):
+    w = WORKLOADS[key]()
+    r = gpu_run(w, virial=False)
+    P, ref = _oracle(key)
+    for l in range(1, P.ncomp + 1):
+        qg = r["plan"].debug_array(2, l).cpu().numpy().reshape(P.level_shape(l))
+        eg = r["plan"].debug_array(3, l).cpu().numpy().reshape(P.level_shape(l))
+        qo, eo = ref["qlev"][l - 1], ref["elev"][l - 1]
+        assert np.abs(qg - qo).max() <= 1e-4 * np.abs(qo).max() + 1e-12, ("q", l)
+        assert np.abs(eg - eo).max() <= 1e-4 * np.abs(eo).max() + 1e-12, ("e", l)
+
+
+# ---------------------------------------------------------------- end to end
+@pytest.mark.parametrize("key", list(WORKLOADS))
+def test_forward_backward_parity(key):
+    w = WORKLOADS[key]()
+    r = gpu_run(w)
+    P, ref = _oracle(key)
+    assert abs(r["E"] - ref["E"]) <= E_TOL * abs(ref["E"]), (r["E"], ref["E"])
+    assert rel_rms(r["F"], ref["F"]) <= F_TOL
+    assert rel_rms(r["phi"], ref["phi"]) <= F_TOL
+    # backward with g = 1: dE/dq = phi, dE/dr = -F, virial
+    assert rel_rms(r["dq"], ref["phi"]) <= F_TOL
+    assert rel_rms(r["dpos"], -ref["F"]) <= F_TOL
+    Wo = ref["W"]
+    assert np.abs(r["W"] - Wo).max() <= F_TOL * np.abs(Wo).max(), (r["W"], Wo)
+
+
+def test_forward_without_forces_then_backward():
+    key = "periodic_20001"
+    w = WORKLOADS[key]()
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    E, phi, F = plan.forward(pos, q, forces=False, virial=False)
+    assert F is None
+    g = torch.full((1,), 2.0, dtype=torch.float64, device=DEV)
+    gp, gq, Wv = plan.backward(g)
+    P, ref = _oracle(key)
+    assert rel_rms(gp.cpu().numpy(), -2.0 * ref["F"]) <= F_TOL
+    assert rel_rms(gq.cpu().numpy(), 2.0 * ref["phi"]) <= F_TOL
+    assert np.abs(Wv.cpu().numpy() - 2.0 * ref["W"]).max() <= F_TOL * 2.0 * np.abs(ref["W"]).max()
+
+
+def test_autograd_function():
+    key = "rocksalt_6"
+    w = WORKLOADS[key]()
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV).requires_grad_(True)
+    q = torch.from_numpy(w.q).to(DEV).requires_grad_(True)
+    E = msm_energy(pos, q, plan)
+    (3.0 * E).backward()
+    P, ref = _oracle(key)
+    assert abs(E.item() - ref["E"]) <= E_TOL * abs(ref["E"])
+    assert rel_rms(pos.grad.cpu().numpy(), -3.0 * ref["F"]) <= F_TOL
+    assert rel_rms(q.grad.cpu().numpy(), 3.0 * ref["phi"]) <= F_TOL
+    Wv = plan.last_virial.cpu().numpy()
+    assert np.abs(Wv - 3.0 * ref["W"]).max() <= F_TOL * 3.0 * np.abs(ref["W"]).max()
+
+
+def test_finite_differences_on_gpu():
+    # central differences of the GPU energy (FP32 inputs, FP64 energy) for a few atoms
+    w = W.rocksalt(ncell=4, seed=40)
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    E, phi, F = plan.forward(pos, q)
+    F = F.cpu().numpy()
+    phi = phi.cpu().numpy()
+    rng = np.random.default_rng(41)
+    errs_f, errs_q = [], []
+    for i in rng.choice(w.n, 8, replace=False):
+        for d in range(3):
+            dx = 1e-2
+            pp = pos.clone()
+            pp[i, d] += dx
+            pm = pos.clone()
+            pm[i, d] -= dx
+            Ep = plan.forward(pp, q, forces=False)[0].item()
+            Em = plan.forward(pm, q, forces=False)[0].item()
+            errs_f.append(abs(-(Ep - Em) / (2 * dx) - F[i, d]) / (np.abs(F).max()))
+        dq = 1e-2
+        qp = q.clone()
+        qp[i] += dq
+        qm = q.clone()
+        qm[i] -= dq
+        Ep = plan.forward(pos, qp, forces=False)[0].item()
+        Em = plan.forward(pos, qm, forces=False)[0].item()
+        errs_q.append(abs((Ep - Em) / (2 * dq) - phi[i]) / np.abs(phi).max())
+    assert max(errs_f) < 2e-3 and max(errs_q) < 2e-3
+
+
+def test_determinism_and_ragged_counts():
+    w = WORKLOADS["periodic_20001"]()
+    plan = make_plan(w, n=w.n + 777)  # capacity above n: ragged tail of work items
+    a = gpu_run(w, plan)
+    b = gpu_run(w, plan)
+    assert a["E"] == b["E"]
+    assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F"], b["F"]) and np.array_equal(a["W"], b["W"])
+    P, ref = _oracle("periodic_20001")
+    assert abs(a["E"] - ref["E"]) <= E_TOL * abs(ref["E"])
+
+
+def test_empty_and_single_atom():
+    w = W.random_box(100, seed=42)
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    E, phi, F = plan.forward(pos[:0].contiguous(), q[:0].contiguous())
+    assert E.item() == 0.0
+    # one charge in a periodic box: E = -1/2 q^2 (self term) + image terms, compared with the oracle
+    import oracle as O
+    O.build()
+    P = O.plan_for(w)
+    r1 = O.msm(P, w.pos[:1].astype(np.float64), w.q[:1].astype(np.float64))
+    E1, phi1, F1 = plan.forward(pos[:1].contiguous(), q[:1].contiguous())
+    assert abs(E1.item() - r1["E"]) <= E_TOL * abs(r1["E"])
+
+
+def test_device_status_flags():
+    w = W.open_cluster(n=300, seed=43)
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    bad = pos.clone()
+    bad[5, 2] = -3.0  # outside the open cell
+    plan.forward(bad, q)
+    assert plan.status() & 1
+    bad = pos.clone()
+    bad[7, 0] = float("nan")
+    plan.forward(bad, q)
+    assert plan.status() & 2
+    plan.forward(pos, q)
+    assert plan.status() == 0
+
+
+# ---------------------------------------------------------------- batch
+def test_batch_matches_single_and_oracle():
+    import oracle as O
+    O.build()
+    systems = W.batch_systems(nsys=24, seed=44, nmax=600)
+    batch = Batch(systems, device=DEV)
+    pos = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(DEV)
+    q = torch.from_numpy(np.concatenate([s.q for s in systems])).to(DEV)
+    E, phi, F = batch.forward(pos, q, forces=True, virial=True)
+    g = torch.ones(len(systems), dtype=torch.float64, device=DEV)
+    gp, gq, Wb = batch.backward(g)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    E = E.cpu().numpy()
+    phi = phi.cpu().numpy()
+    F = F.cpu().numpy()
+    Wb = Wb.cpu().numpy()
+    off = 0
+    for s, sysw in enumerate(systems):
+        n = sysw.n
+        P = O.plan_for(sysw)
+        ref = O.msm(P, sysw.pos.astype(np.float64), sysw.q.astype(np.float64))
+        assert abs(E[s] - ref["E"]) <= E_TOL * abs(ref["E"]) + 1e-9, (s, E[s], ref["E"])
+        assert rel_rms(F[off:off + n], ref["F"]) <= F_TOL, s
+        assert rel_rms(phi[off:off + n], ref["phi"]) <= F_TOL, s
+        assert np.abs(Wb[s] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), s
+        single = gpu_run(sysw)
+        assert abs(single["E"] - E[s]) <= 1e-6 * abs(E[s]) + 1e-12
+        off += n
