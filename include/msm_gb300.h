@@ -183,6 +183,26 @@ int msm_debug_offset(msm_plan plan, int which, int level, size_t* offset_bytes, 
 int msm_profile(msm_plan plan, int enable);
 int msm_profile_read(msm_plan plan, double* ms, int* launches);
 
+/* Forward pass without a caller-allocated workspace. The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory themselves (a host application whose allocator owns all
+ * device memory, a real-time loop that must not allocate). It behaves as
+ * msm_forward but keeps its workspace in a fixed device array inside the
+ * library, MSM_NOALLOC_SCRATCH_BYTES large, which every GPU that loads the
+ * library holds until the process exits. It allocates nothing.
+ *  - Plans whose msm_workspace_bytes exceeds MSM_NOALLOC_SCRATCH_BYTES are
+ *    rejected with MSM_ERR_CAPACITY (about 250,000 atoms with modest grids fit).
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other threads) race and give wrong results; serialise them.
+ *  - There is no matching backward pass (msm_backward needs a workspace the
+ *    caller owns). Arguments and results are those of msm_forward. */
+#define MSM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int msm_forward_noalloc(msm_plan plan, int n, const float* pos, const float* q, double* energy, float* phi,
+                        float* forces, int flags, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* msm_last_error(void);
 

@@ -23,6 +23,8 @@ static int set_err(int code, const std::string& m) {
   return code;
 }
 
+int msm::api_error(int code, const std::string& msg) { return set_err(code, msg); }
+
 static int check_launch(const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(MSM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));

@@ -40,6 +40,9 @@ struct SysHost {
 
 int plan_system(const msm_params& P, SysHost& S, std::string* err);
 
+// records the thread's last-error message of the C ABI and returns code
+int api_error(int code, const std::string& msg);
+
 struct Engine {
   int nsys = 0;
   bool single = true;
