@@ -168,7 +168,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   perm[dst] = g;
   scell[dst] = cell;
   float qq = q[g];
-  float loc[3], u[3];
+  float loc[3], u[3];  // x, y relative to the cell corner, z relative to the column (cell z index 0)
   int c[3] = {cell / (S.C[1] * S.C[2]), (cell / S.C[2]) % S.C[1], cell % S.C[2]};
   for (int d = 0; d < 3; d++) {
     float s, t;
@@ -178,7 +178,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
       continue;
     }
     axis_cell(S, d, s, t);
-    loc[d] = (t - (float)c[d]) * S.edge[d];
+    loc[d] = (d < 2 ? (t - (float)c[d]) : t) * S.edge[d];
     u[d] = s * S.Mf[d];
   }
   xq[dst] = make_float4(loc[0], loc[1], loc[2], qq);

@@ -1,19 +1,30 @@
 // k_short.cu -- short-range part U^0 of the MSM (Eq. U_zero) over the cell
-// list: for every sorted atom i, every atom j of the neighbour cells and every
-// periodic image with |d| < a, (j, image) != (i, 0):
+// list: for every sorted atom i, every atom j and every periodic image with
+// |d| < a, (j, image) != (i, 0):
 //   phi0_i += q_j k_0(|d|),  k_0(r) = 1/r - gamma(r/a)/a   (Sec. 3.4),
 //   F0_i   += q_i q_j k_0'(r) d / r,
 //   W0     += -1/2 q_i q_j k_0'(r) d d^T / r,
 // and phi0_i -= q_i gamma(0)/a (the self term, sum_(l>=1) k_l(0)).
-// Positions are cell-local, so the displacement to an atom in the cell at
-// offset o is o * edge + (x_j - x_i) whether or not o wraps around a periodic
-// boundary; small periodic cells simply visit the same cell at several
-// offsets (every image within the cutoff, self images included).
-// One thread per sorted atom; the sum over j is the thread's own, so the
-// result does not depend on scheduling.
+//
+// Candidates: for each (dx, dy) column of cells around i's cell whose xy
+// distance to i is below a, the cells of that column along z within
+// sqrt(a^2 - dxy^2) of i. Cells of one column are consecutive in the sorted
+// order, so each column contributes one contiguous range of atoms per
+// periodic image along z. Sorted positions keep x, y relative to the cell
+// corner and z relative to the column base, so the displacement to a
+// candidate is (ox * edge_x + x_j - x_i, oy * edge_y + y_j - y_i,
+// z_j + kz * L_z - z_i) with no wrap arithmetic per pair. Small periodic
+// cells visit the same cells at several offsets: every image within the
+// cutoff counts, self images included. One thread per sorted atom; each
+// thread sums its own pairs, so the result does not depend on scheduling.
 #include "msm_internal.h"
 
 namespace msm {
+
+__device__ __forceinline__ int floordiv_s(int a, int b) {
+  int q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
 
 template <int P>
 __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
@@ -28,43 +39,56 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
   bool active = (int)threadIdx.x < it.count && local < S.n;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (active) {
-    int k = S.atom_off + local;
-    float4 xi = xq[k];
-    int cell = scell[k];
-    int Cy = S.C[1], Cz = S.C[2];
-    int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
+    const int k = S.atom_off + local;
+    const float4 xi = xq[k];
+    const int cell = scell[k];
+    const int Cx = S.C[0], Cy = S.C[1], Cz = S.C[2];
+    const int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
     float gc[P], gdc[P - 1];
 #pragma unroll
     for (int t = 0; t < P; t++) gc[t] = S.gc[t];
 #pragma unroll
     for (int t = 0; t < P - 1; t++) gdc[t] = S.gdc[t];
     const float a2 = S.a2, inv_a = S.inv_a, inv_a2 = S.inv_a2, two_inv_a3 = 2.0f * S.inv_a3;
+    const float ex = S.edge[0], ey = S.edge[1], ez = S.edge[2], inv_ez = 1.0f / ez;
     float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
-      int ux = ci[0] + ox;
-      if (!S.pbc[0] && (ux < 0 || ux >= S.C[0])) continue;
-      int wx = ((ux % S.C[0]) + S.C[0]) % S.C[0];
-      float dxo = (float)ox * S.edge[0] - xi.x;
+      const int ux = ci[0] + ox;
+      if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
+      const int wx = ux - floordiv_s(ux, Cx) * Cx;
+      const float bx = (float)ox * ex - xi.x;  // d_x = bx + x_j
+      const float mx = ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f);
       for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
-        int uy = ci[1] + oy;
+        const int uy = ci[1] + oy;
         if (!S.pbc[1] && (uy < 0 || uy >= Cy)) continue;
-        int wy = ((uy % Cy) + Cy) % Cy;
-        float dyo = (float)oy * S.edge[1] - xi.y;
-        for (int oz = -S.nnbr[2]; oz <= S.nnbr[2]; oz++) {
-          int uz = ci[2] + oz;
-          if (!S.pbc[2] && (uz < 0 || uz >= Cz)) continue;
-          int wz = ((uz % Cz) + Cz) % Cz;
-          float dzo = (float)oz * S.edge[2] - xi.z;
-          int c = S.cell_off + (wx * Cy + wy) * Cz + wz;
-          int jb = cell_start[c], je = cell_start[c + 1];
-          bool home = (ox | oy | oz) == 0;
+        const float by = (float)oy * ey - xi.y;
+        const float my = oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f);
+        const float rxy2 = mx * mx + my * my;
+        if (rxy2 >= a2) continue;
+        const int wy = uy - floordiv_s(uy, Cy) * Cy;
+        const float zr = sqrtf(a2 - rxy2);
+        int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
+        if (!S.pbc[2]) {
+          zlo = max(zlo, 0);
+          zhi = min(zhi, Cz - 1);
+        }
+        const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
+        const bool home_xy = (ox | oy) == 0;
+        int uz = zlo;
+        while (uz <= zhi) {
+          const int kz = floordiv_s(uz, Cz);
+          const int wz = uz - kz * Cz;
+          const int wend = min(Cz - 1, wz + (zhi - uz));
+          const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+          const float bz = (float)kz * S.Lf[2] - xi.z;
+          const bool home = home_xy && kz == 0;
           for (int j = jb; j < je; j++) {
-            float4 xj = xq[j];
-            float dx = dxo + xj.x, dy = dyo + xj.y, dz = dzo + xj.z;
-            float r2 = dx * dx + dy * dy + dz * dz;
+            const float4 xj = xq[j];
+            const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < a2 && !(home && j == k)) {
-              float rinv = rsqrtf(r2);
-              float s = 1.0f - r2 * inv_a2;
+              const float rinv = rsqrtf(r2);
+              const float s = 1.0f - r2 * inv_a2;
               float g = gc[P - 1];
 #pragma unroll
               for (int t = P - 2; t >= 0; t--) g = fmaf(g, s, gc[t]);
@@ -74,7 +98,7 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
               ph = fmaf(xj.w, rinv - g * inv_a, ph);
               if (want_f | want_w) {
                 // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
-                float fr = xj.w * fmaf(-rinv * rinv, rinv, two_inv_a3 * dg);
+                const float fr = xj.w * fmaf(-rinv * rinv, rinv, two_inv_a3 * dg);
                 fx = fmaf(fr, dx, fx);
                 fy = fmaf(fr, dy, fy);
                 fz = fmaf(fr, dz, fz);
@@ -89,6 +113,7 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
               }
             }
           }
+          uz += wend - wz + 1;
         }
       }
     }

@@ -3,25 +3,30 @@
 // grid part of the virial, W = -1/2 sum_l sum_d (dK^l/d eps)_d C^l_d with the
 // autocorrelation C^l_d = sum_m q~^l_m q~^l_(m-d).
 //
-// Ball kernels (levels whose stencil support is a ball of radius R that does
-// not overlap itself under the periodic wrap): one block per output tile of
-// 1 x 32 x 32 points; the block streams the 2R+1 input x-planes of the tile's
-// halo through shared memory (cp.async, double buffered, periodic wrap or
-// zero fill done by the copy addresses) together with the matching x-slab of
-// the stencil. Each thread owns 16 consecutive z outputs in registers and,
-// per (dx, dy) stencil column of half-width w, loads 16 + 2w plane values and
-// 2w + 1 stencil values and issues 16 (2w + 1) FFMA from registers; w picks
-// an unrolled variant, so the ball shape costs nothing for empty columns.
-// The arithmetic is FP32 on the CUDA cores: the contraction has no dense
+// Ball levels (stencil support a ball of radius R that does not overlap
+// itself under the periodic wrap). A pad kernel first writes a halo-padded
+// copy of q~^l (periodic images or zeros in the halo), so every tile's input
+// box is a plain rectangle. One block per output tile of 1 x 32 x 32 points
+// streams the 2R+1 input x-planes of the tile's halo through shared memory
+// (16-byte cp.async rows, double buffered) together with the matching x-slab
+// of the stencil, stored column by column with dz aligned to 16 bytes. Each
+// thread owns 16 consecutive z outputs in registers; per (dx, dy) stencil
+// column of half-width w it loads its 16 + 2w window and the 2w + 1 stencil
+// values with 128-bit shared loads and issues 16 (2w + 1) FFMA from registers.
+// w selects an unrolled variant, so the ball shape costs nothing for empty
+// columns. The arithmetic is FP32 on the CUDA cores: the sum has no dense
 // reduction axis, and a Toeplitz recast for the tensor cores would multiply
 // the work by (16 + 2R)/(2R + 1) per axis while TF32 loses the accuracy the
 // method needs.
 //
-// The virial kernel is the same loop with the roles swapped: per column a
-// thread forms its partial C_(dx,dy,dz) for the 2w + 1 dz values and
-// contracts it at once with the six strain-derivative weights (stored with
-// the half-space symmetry C_d = C_-d folded in). Box kernels serve the small
-// levels with folded (dense) stencils and the top level of open systems.
+// The ball virial kernel is the same loop with the roles swapped: per column a
+// thread forms its partial C_(dx,dy,dz) for the 2w + 1 dz values and at once
+// contracts it with the six strain-derivative weights (stored with the
+// half-space symmetry C_d = C_-d folded in).
+//
+// Box levels (small periodic levels whose stencil wraps onto itself, folded
+// onto the grid, and the top level of open systems): one warp per output, the
+// lanes splitting the stencil entries, then a shuffle reduction.
 #include "msm_internal.h"
 
 namespace msm {
@@ -30,49 +35,94 @@ constexpr int BZ = kBallBZ;
 constexpr int TY = kBallTY;
 constexpr int TZ = kBallTZ;
 constexpr int NT = kBallThreads;
+constexpr int kWslMax = 64;  // column table entries per stage buffer (2 R_y + 1 <= 49)
 
 __device__ __forceinline__ int wrap_s(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool valid) {
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-  int bytes = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(bytes));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ------------------------------------------------------------------ halo padding
+__global__ void __launch_bounds__(kGridChunk) k_pad(const LevDev* __restrict__ levs,
+                                                    const RangeItem* __restrict__ items, float* __restrict__ grid) {
+  RangeItem it = items[blockIdx.x];
+  if ((int)threadIdx.x >= it.count) return;
+  const LevDev& L = levs[it.lev];
+  int idx = it.start + threadIdx.x;
+  int pz = idx % L.pn[2], py = (idx / L.pn[2]) % L.pn[1], px = idx / (L.pn[2] * L.pn[1]);
+  int c[3] = {px - L.R[0], py - L.R[1], pz - L.hz};
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (L.per[d]) c[d] = wrap_s(c[d], L.n[d]);
+    else ok = ok && c[d] >= 0 && c[d] < L.n[d];
+  }
+  grid[L.p_off + idx] = ok ? grid[L.q_off + ((long long)c[0] * L.n[1] + c[1]) * L.n[2] + c[2]] : 0.0f;
+}
 
 // ------------------------------------------------------------------ columns
 template <int W>
 __device__ __forceinline__ void ball_column(float (&acc)[BZ], const float* __restrict__ qrow,
                                             const float* __restrict__ kc) {
-  float qv[BZ + 2 * W];
+  constexpr int A = (W + 3) & ~3;
+  constexpr int NQ = BZ + 2 * A;
+  constexpr int NK = 2 * A + 4;
+  float qv[NQ], kv[NK];
 #pragma unroll
-  for (int t = 0; t < BZ + 2 * W; t++) qv[t] = qrow[t - W];
+  for (int t = 0; t < NQ; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(qrow - A + t);
+    qv[t] = v.x; qv[t + 1] = v.y; qv[t + 2] = v.z; qv[t + 3] = v.w;
+  }
 #pragma unroll
-  for (int j = 0; j <= 2 * W; j++) {
-    const float kv = kc[j - W];
+  for (int t = 0; t < 2 * A + 1; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(kc - A + t);
+    kv[t] = v.x; kv[t + 1] = v.y; kv[t + 2] = v.z; kv[t + 3] = v.w;
+  }
 #pragma unroll
-    for (int o = 0; o < BZ; o++) acc[o] = fmaf(kv, qv[o - j + 2 * W], acc[o]);
+  for (int dz = -W; dz <= W; dz++) {
+    const float k = kv[dz + A];
+#pragma unroll
+    for (int o = 0; o < BZ; o++) acc[o] = fmaf(k, qv[o - dz + A], acc[o]);
   }
 }
 
 template <int W>
 __device__ __forceinline__ void virial_column(float (&w6)[6], const float (&qown)[BZ],
-                                              const float* __restrict__ qrow, const float* __restrict__ kc,
+                                              const float* __restrict__ qrow, const float* __restrict__ kd,
                                               int kstride) {
-  float qv[BZ + 2 * W];
+  constexpr int A = (W + 3) & ~3;
+  constexpr int NQ = BZ + 2 * A;
+  float qv[NQ];
 #pragma unroll
-  for (int t = 0; t < BZ + 2 * W; t++) qv[t] = qrow[t - W];
+  for (int t = 0; t < NQ; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(qrow - A + t);
+    qv[t] = v.x; qv[t + 1] = v.y; qv[t + 2] = v.z; qv[t + 3] = v.w;
+  }
+  float c[2 * W + 1];
 #pragma unroll
-  for (int j = 0; j <= 2 * W; j++) {
-    float c = 0.f;
+  for (int dz = -W; dz <= W; dz++) {
+    float s = 0.f;
 #pragma unroll
-    for (int o = 0; o < BZ; o++) c = fmaf(qown[o], qv[o - j + 2 * W], c);
+    for (int o = 0; o < BZ; o++) s = fmaf(qown[o], qv[o - dz + A], s);
+    c[dz + W] = s;
+  }
 #pragma unroll
-    for (int k = 0; k < 6; k++) w6[k] = fmaf(kc[k * kstride + j - W], c, w6[k]);
+  for (int k = 0; k < 6; k++) {
+    float kv[2 * A + 4];
+#pragma unroll
+    for (int t = 0; t < 2 * A + 1; t += 4) {
+      float4 v = *reinterpret_cast<const float4*>(kd + k * kstride - A + t);
+      kv[t] = v.x; kv[t + 1] = v.y; kv[t + 2] = v.z; kv[t + 3] = v.w;
+    }
+#pragma unroll
+    for (int dz = -W; dz <= W; dz++) w6[k] = fmaf(kv[dz + A], c[dz + W], w6[k]);
   }
 }
 
@@ -104,47 +154,24 @@ struct Col<WMAX, WMAX> {
 };
 
 // ------------------------------------------------------------------ staging
-// shared-memory carve-up: two plane buffers, two stencil slabs, two column tables
-__device__ __forceinline__ float* sm_plane(float* smem, int plane_sz, int b) { return smem + b * plane_sz; }
-__device__ __forceinline__ float* sm_kslab(float* smem, int plane_sz, int kslab_sz, int b) {
-  return smem + 2 * plane_sz + b * kslab_sz;
-}
-__device__ __forceinline__ int* sm_wsl(float* smem, int plane_sz, int kslab_sz, int wsl_sz, int b) {
-  return reinterpret_cast<int*>(smem + 2 * plane_sz + 2 * kslab_sz) + b * wsl_sz;
-}
-
-// Issue the copies of input plane x = x0 - dx (rows y0-Ry .. y0+TY-1+Ry,
-// columns z0-Rz .. z0+TZ-1+Rz) and of the stencil x-slab of this dx.
-__device__ __forceinline__ void stage(const LevDev& L, const TileItem& it, int step, const float* __restrict__ src,
-                                      const float* __restrict__ kpool, long long kslab_off, int nkcomp,
-                                      long long kcomp_stride, const int* __restrict__ wpool, long long w_off,
-                                      float* plane, float* kslab, int* wsl, int stride) {
-  const int Rx = L.R[0], Ry = L.R[1], Rz = L.R[2];
-  const int rows = TY + 2 * Ry, cols = TZ + 2 * Rz;
-  const int dx = step - Rx;
-  int xs = it.x0 - dx;
-  bool xok = true;
-  if (L.per[0]) xs = wrap_s(xs, L.n[0]);
-  else xok = (xs >= 0 && xs < L.n[0]);
-  const int n1 = L.n[1], n2 = L.n[2];
-  for (int e = threadIdx.x; e < rows * cols; e += NT) {
-    int r = e / cols, c = e - r * cols;
-    int ys = it.y0 - Ry + r, zs = it.z0 - Rz + c;
-    bool ok = xok;
-    if (L.per[1]) ys = wrap_s(ys, n1);
-    else ok = ok && ys >= 0 && ys < n1;
-    if (L.per[2]) zs = wrap_s(zs, n2);
-    else ok = ok && zs >= 0 && zs < n2;
-    const float* g = ok ? src + ((long long)xs * n1 + ys) * n2 + zs : src;
-    cp_async4(plane + r * stride + c, g, ok);
-  }
-  const int ksz = (2 * Ry + 1) * (2 * Rz + 1);
-  for (int k = 0; k < nkcomp; k++) {
-    const float* ks = kpool + kslab_off + k * kcomp_stride + (long long)step * ksz;
-    for (int e = threadIdx.x; e < ksz; e += NT) cp_async4(kslab + k * ksz + e, ks + e, true);
-  }
-  for (int e = threadIdx.x; e < 2 * Ry + 1; e += NT)
-    cp_async4(wsl + e, wpool + w_off + (long long)step * (2 * Ry + 1) + e, true);
+// Copies of input plane x = x0 - dx of the padded grid (rows y0-Ry .. y0+TY-1+Ry,
+// columns z0-hz .. z0+TZ-1+hz), of the nk stencil slabs of this dx and of its
+// column table, into stage buffer b.
+__device__ __forceinline__ void stage_ball(const LevDev& L, const TileItem& it, int step,
+                                           const float* __restrict__ grid, const float* __restrict__ kpool,
+                                           long long koff, int nk, const int* __restrict__ wpool, long long woff,
+                                           float* plane, float* kslab, int* wsl, int stride) {
+  const int Rx = L.R[0], Ry = L.R[1], hz = L.hz;
+  const int rows = TY + 2 * Ry, cpr = (TZ + 2 * hz) / 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int px = it.x0 + 2 * Rx - step;  // padded index of x0 - dx, dx = step - Rx
+  const float* src = grid + L.p_off + ((long long)px * L.pn[1] + it.y0) * L.pn[2] + it.z0;
+  for (int r = warp; r < rows; r += NT / 32)
+    if (lane < cpr) cp_async16(plane + r * stride + 4 * lane, src + (long long)r * L.pn[2] + 4 * lane);
+  const int kchunks = nk * (2 * Ry + 1) * kSK(hz) / 4;
+  const float* ks = kpool + koff + (long long)step * nk * (2 * Ry + 1) * kSK(hz);
+  for (int e = threadIdx.x; e < kchunks; e += NT) cp_async16(kslab + 4 * e, ks + 4 * e);
+  for (int e = threadIdx.x; e < 2 * Ry + 1; e += NT) wsl[e] = wpool[woff + (long long)step * (2 * Ry + 1) + e];
   cp_async_commit();
 }
 
@@ -152,38 +179,37 @@ template <int WMAX>
 __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ levs,
                                                      const TileItem* __restrict__ items,
                                                      const float* __restrict__ kpool, const int* __restrict__ wpool,
-                                                     float* __restrict__ grid, int plane_sz, int kslab_sz,
-                                                     int wsl_sz, int stride) {
-  extern __shared__ float smem[];
+                                                     float* __restrict__ grid, int stride, int plane_sz, int kslab_sz) {
+  extern __shared__ __align__(16) float smem[];
+  float* planes = smem;
+  float* kslabs = smem + 2 * plane_sz;
+  int* wsl = reinterpret_cast<int*>(kslabs + 2 * kslab_sz);
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
-  const int Rx = L.R[0], Ry = L.R[1], Rz = L.R[2];
+  const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
   const int ty = threadIdx.x % TY, zb = threadIdx.x / TY;
-  const float* src = grid + L.q_off;
   float acc[BZ];
 #pragma unroll
   for (int o = 0; o < BZ; o++) acc[o] = 0.f;
   const int nsteps = 2 * Rx + 1;
-  const int ksz = (2 * Ry + 1) * (2 * Rz + 1);
-  stage(L, it, 0, src, kpool, L.k_off, 1, 0, wpool, L.w_off, sm_plane(smem, plane_sz, 0), sm_kslab(smem, plane_sz, kslab_sz, 0), sm_wsl(smem, plane_sz, kslab_sz, wsl_sz, 0), stride);
+  stage_ball(L, it, 0, grid, kpool, L.k_off, 1, wpool, L.w_off, planes, kslabs, wsl, stride);
   for (int step = 0; step < nsteps; step++) {
     cp_async_wait_all();
     __syncthreads();
     const int b = step & 1;
     if (step + 1 < nsteps)
-      stage(L, it, step + 1, src, kpool, L.k_off, 1, 0, wpool, L.w_off, sm_plane(smem, plane_sz, b ^ 1),
-            sm_kslab(smem, plane_sz, kslab_sz, b ^ 1), sm_wsl(smem, plane_sz, kslab_sz, wsl_sz, b ^ 1), stride);
-    const float* plane = sm_plane(smem, plane_sz, b);
-    const float* kslab = sm_kslab(smem, plane_sz, kslab_sz, b);
-    const int* wsl = sm_wsl(smem, plane_sz, kslab_sz, wsl_sz, b);
+      stage_ball(L, it, step + 1, grid, kpool, L.k_off, 1, wpool, L.w_off, planes + (b ^ 1) * plane_sz,
+                 kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax, stride);
+    const float* plane = planes + b * plane_sz;
+    const float* kslab = kslabs + b * kslab_sz;
+    const int* wc = wsl + b * kWslMax;
     for (int dy = -Ry; dy <= Ry; dy++) {
-      const int w = wsl[dy + Ry];
+      const int w = wc[dy + Ry];
       if (w < 0) continue;
-      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + Rz;
-      const float* kc = kslab + (dy + Ry) * (2 * Rz + 1) + Rz;
+      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz;
+      const float* kc = kslab + (dy + Ry) * SK + hz;
       Col<0, WMAX>::stencil(w, acc, qrow, kc);
     }
-    (void)ksz;
   }
   const int y = it.y0 + ty;
   if (y < L.n[1]) {
@@ -200,42 +226,43 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const LevDev* __restrict__ l
                                                     const TileItem* __restrict__ items,
                                                     const float* __restrict__ kpool, const int* __restrict__ wpool,
                                                     const float* __restrict__ grid, double* __restrict__ part,
-                                                    int plane_sz, int kslab_sz, int wsl_sz, int stride) {
-  extern __shared__ float smem[];
+                                                    int stride, int plane_sz, int kslab_sz) {
+  extern __shared__ __align__(16) float smem[];
   __shared__ double red[NT / 32][6];
+  float* planes = smem;
+  float* kslabs = smem + 2 * plane_sz;
+  int* wsl = reinterpret_cast<int*>(kslabs + 2 * kslab_sz);
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
-  const int Rx = L.R[0], Ry = L.R[1], Rz = L.R[2];
+  const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
   const int ty = threadIdx.x % TY, zb = threadIdx.x / TY;
-  const float* src = grid + L.q_off;
-  const int ksz = (2 * Ry + 1) * (2 * Rz + 1);
-  const long long kcs = (long long)(2 * Rx + 1) * ksz;  // one component of the dense box
+  const int kstride = (2 * Ry + 1) * SK;
   float qown[BZ];
   {
     const int y = it.y0 + ty, z0 = it.z0 + zb * BZ;
+    const float* row = grid + L.p_off + ((long long)(it.x0 + Rx) * L.pn[1] + (y + Ry)) * L.pn[2] + hz;
 #pragma unroll
-    for (int o = 0; o < BZ; o++)
-      qown[o] = (y < L.n[1] && z0 + o < L.n[2]) ? src[((long long)it.x0 * L.n[1] + y) * L.n[2] + z0 + o] : 0.f;
+    for (int o = 0; o < BZ; o++) qown[o] = (y < L.n[1] && z0 + o < L.n[2]) ? row[z0 + o] : 0.f;
   }
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int nsteps = 2 * Rx + 1;
-  stage(L, it, 0, src, kpool, L.dk_off, 6, kcs, wpool, L.wh_off, sm_plane(smem, plane_sz, 0), sm_kslab(smem, plane_sz, kslab_sz, 0), sm_wsl(smem, plane_sz, kslab_sz, wsl_sz, 0), stride);
+  stage_ball(L, it, 0, grid, kpool, L.dk_off, 6, wpool, L.wh_off, planes, kslabs, wsl, stride);
   for (int step = 0; step < nsteps; step++) {
     cp_async_wait_all();
     __syncthreads();
     const int b = step & 1;
     if (step + 1 < nsteps)
-      stage(L, it, step + 1, src, kpool, L.dk_off, 6, kcs, wpool, L.wh_off, sm_plane(smem, plane_sz, b ^ 1),
-            sm_kslab(smem, plane_sz, kslab_sz, b ^ 1), sm_wsl(smem, plane_sz, kslab_sz, wsl_sz, b ^ 1), stride);
-    const float* plane = sm_plane(smem, plane_sz, b);
-    const float* kslab = sm_kslab(smem, plane_sz, kslab_sz, b);
-    const int* wsl = sm_wsl(smem, plane_sz, kslab_sz, wsl_sz, b);
+      stage_ball(L, it, step + 1, grid, kpool, L.dk_off, 6, wpool, L.wh_off, planes + (b ^ 1) * plane_sz,
+                 kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax, stride);
+    const float* plane = planes + b * plane_sz;
+    const float* kslab = kslabs + b * kslab_sz;
+    const int* wc = wsl + b * kWslMax;
     for (int dy = -Ry; dy <= Ry; dy++) {
-      const int w = wsl[dy + Ry];
+      const int w = wc[dy + Ry];
       if (w < 0) continue;
-      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + Rz;
-      const float* kc = kslab + (dy + Ry) * (2 * Rz + 1) + Rz;
-      Col<0, WMAX>::virial(w, w6, qown, qrow, kc, ksz);
+      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz;
+      const float* kd = kslab + (dy + Ry) * SK + hz;
+      Col<0, WMAX>::virial(w, w6, qown, qrow, kd, kstride);
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -254,125 +281,147 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const LevDev* __restrict__ l
 }
 
 // ------------------------------------------------------------------ boxes
-__global__ void __launch_bounds__(kBoxChunk) k_stencil_box(const LevDev* __restrict__ levs,
-                                                           const RangeItem* __restrict__ items,
-                                                           const float* __restrict__ kpool,
-                                                           float* __restrict__ grid) {
-  RangeItem it = items[blockIdx.x];
-  if ((int)threadIdx.x >= it.count) return;
-  const LevDev& L = levs[it.lev];
-  int idx = it.start + threadIdx.x;
-  int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
-  const float* q = grid + L.q_off;
-  const float* K = kpool + L.k_off;
-  float acc = 0.f;
-  for (int a = 0; a < L.bsz[0]; a++) {
-    int sx = m[0] - (a + L.blo[0]);
-    if (L.per[0]) sx = wrap_s(sx, L.n[0]);
-    else if (sx < 0 || sx >= L.n[0]) continue;
-    for (int b = 0; b < L.bsz[1]; b++) {
-      int sy = m[1] - (b + L.blo[1]);
-      if (L.per[1]) sy = wrap_s(sy, L.n[1]);
-      else if (sy < 0 || sy >= L.n[1]) continue;
-      const float* krow = K + ((long long)a * L.bsz[1] + b) * L.bsz[2];
-      const float* qrow = q + ((long long)sx * L.n[1] + sy) * L.n[2];
-      for (int c = 0; c < L.bsz[2]; c++) {
-        int sz = m[2] - (c + L.blo[2]);
-        if (L.per[2]) sz = wrap_s(sz, L.n[2]);
-        else if (sz < 0 || sz >= L.n[2]) continue;
-        acc = fmaf(__ldg(krow + c), qrow[sz], acc);
+// One warp per output point; the lanes split the box entries t (coalesced
+// stencil loads), then a shuffle reduction.
+constexpr int kBoxThreads = 256;
+
+struct BoxIter {
+  int a, b, c;
+  __device__ __forceinline__ void init(int t, const LevDev& L) {
+    c = t % L.bsz[2];
+    b = (t / L.bsz[2]) % L.bsz[1];
+    a = t / (L.bsz[2] * L.bsz[1]);
+  }
+  __device__ __forceinline__ void advance32(const LevDev& L) {
+    c += 32;
+    while (c >= L.bsz[2]) {
+      c -= L.bsz[2];
+      if (++b >= L.bsz[1]) {
+        b = 0;
+        ++a;
       }
     }
   }
-  grid[L.e_off + idx] = acc * L.scale;
+};
+
+// storage index of q_(m - d) or -1 (open axis, outside)
+__device__ __forceinline__ int box_src(const LevDev& L, const int m[3], const BoxIter& t) {
+  int s[3] = {m[0] - (t.a + L.blo[0]), m[1] - (t.b + L.blo[1]), m[2] - (t.c + L.blo[2])};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (L.per[d]) s[d] &= (L.n[d] - 1);  // periodic level sizes are powers of two
+    else if (s[d] < 0 || s[d] >= L.n[d]) return -1;
+  }
+  return (s[0] * L.n[1] + s[1]) * L.n[2] + s[2];
 }
 
-__global__ void __launch_bounds__(kBoxChunk) k_virial_box(const LevDev* __restrict__ levs,
-                                                          const RangeItem* __restrict__ items,
-                                                          const float* __restrict__ kpool,
-                                                          const float* __restrict__ grid,
-                                                          double* __restrict__ part) {
-  __shared__ double red[kBoxChunk / 32][6];
-  RangeItem it = items[blockIdx.x];
+__global__ void __launch_bounds__(kBoxThreads) k_stencil_box(const LevDev* __restrict__ levs,
+                                                             const RangeItem* __restrict__ items,
+                                                             const float* __restrict__ kpool,
+                                                             float* __restrict__ grid) {
+  const RangeItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nt = L.bsz[0] * L.bsz[1] * L.bsz[2];
+  const float* q = grid + L.q_off;
+  const float* K = kpool + L.k_off;
+  for (int o = warp; o < it.count; o += kBoxThreads / 32) {
+    const int idx = it.start + o;
+    const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
+    float acc = 0.f;
+    BoxIter ti;
+    ti.init(lane, L);
+    for (int t = lane; t < nt; t += 32) {
+      int s = box_src(L, m, ti);
+      if (s >= 0) acc = fmaf(__ldg(K + t), q[s], acc);
+      ti.advance32(L);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) grid[L.e_off + idx] = acc * L.scale;
+  }
+}
+
+__global__ void __launch_bounds__(kBoxThreads) k_virial_box(const LevDev* __restrict__ levs,
+                                                            const RangeItem* __restrict__ items,
+                                                            const float* __restrict__ kpool,
+                                                            const float* __restrict__ grid,
+                                                            double* __restrict__ part) {
+  __shared__ double red[kBoxThreads / 32][6];
+  const RangeItem it = items[blockIdx.x];
+  const LevDev& L = levs[it.lev];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nt = L.bsz[0] * L.bsz[1] * L.bsz[2];
+  const float* q = grid + L.q_off;
+  const float* K = kpool + L.dk_off;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if ((int)threadIdx.x < it.count) {
-    int idx = it.start + threadIdx.x;
-    int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
-    const float* q = grid + L.q_off;
+  for (int o = warp; o < it.count; o += kBoxThreads / 32) {
+    const int idx = it.start + o;
+    const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
     const float qm = q[idx];
-    const long long cs = (long long)L.bsz[0] * L.bsz[1] * L.bsz[2];
-    const float* K = kpool + L.dk_off;
-    for (int a = 0; a < L.bsz[0]; a++) {
-      int sx = m[0] - (a + L.blo[0]);
-      if (L.per[0]) sx = wrap_s(sx, L.n[0]);
-      else if (sx < 0 || sx >= L.n[0]) continue;
-      for (int b = 0; b < L.bsz[1]; b++) {
-        int sy = m[1] - (b + L.blo[1]);
-        if (L.per[1]) sy = wrap_s(sy, L.n[1]);
-        else if (sy < 0 || sy >= L.n[1]) continue;
-        const long long kr = ((long long)a * L.bsz[1] + b) * L.bsz[2];
-        const float* qrow = q + ((long long)sx * L.n[1] + sy) * L.n[2];
-        for (int c = 0; c < L.bsz[2]; c++) {
-          int sz = m[2] - (c + L.blo[2]);
-          if (L.per[2]) sz = wrap_s(sz, L.n[2]);
-          else if (sz < 0 || sz >= L.n[2]) continue;
-          float cq = qm * qrow[sz];
+    BoxIter ti;
+    ti.init(lane, L);
+    for (int t = lane; t < nt; t += 32) {
+      int s = box_src(L, m, ti);
+      if (s >= 0) {
+        const float cq = qm * q[s];
 #pragma unroll
-          for (int k = 0; k < 6; k++) w6[k] = fmaf(__ldg(K + k * cs + kr + c), cq, w6[k]);
-        }
+        for (int k = 0; k < 6; k++) w6[k] = fmaf(__ldg(K + (long long)k * nt + t), cq, w6[k]);
       }
+      ti.advance32(L);
     }
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < 6; c++) {
     double v = -0.5 * (double)L.scale * (double)w6[c];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid][c] = v;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][c] = v;
   }
   __syncthreads();
   if (threadIdx.x < 6) {
     double v = 0.0;
-    for (int w = 0; w < kBoxChunk / 32; w++) v += red[w][threadIdx.x];
+    for (int w = 0; w < kBoxThreads / 32; w++) v += red[w][threadIdx.x];
     part[6 * (long long)blockIdx.x + threadIdx.x] = v;
   }
 }
 
 // ------------------------------------------------------------------ launchers
-static void ball_smem(int ryz_max[2], int ncomp, int& plane_sz, int& kslab_sz, int& wsl_sz, int& stride,
-                      size_t& bytes) {
-  const int Ry = ryz_max[0], Rz = ryz_max[1];
-  stride = (TZ + 2 * Rz) | 1;
+static void ball_smem(const int ryz_max[2], int nk, int& stride, int& plane_sz, int& kslab_sz, size_t& bytes) {
+  const int Ry = ryz_max[0], hz = ryz_max[1];
+  stride = TZ + 2 * hz;
+  if ((stride / 4) % 2 == 0) stride += 4;  // 4 x odd floats: conflict-free 128-bit row loads
   plane_sz = (TY + 2 * Ry) * stride;
-  kslab_sz = ncomp * (2 * Ry + 1) * (2 * Rz + 1);
-  wsl_sz = 2 * Ry + 1;
-  bytes = sizeof(float) * (2 * (size_t)plane_sz + 2 * (size_t)kslab_sz) + sizeof(int) * 2 * (size_t)wsl_sz;
+  kslab_sz = nk * (2 * Ry + 1) * kSK(hz);
+  bytes = sizeof(float) * (2 * (size_t)plane_sz + 2 * (size_t)kslab_sz) + sizeof(int) * 2 * kWslMax;
 }
 
 template <int WMAX>
 static void run_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int ryz_max[2],
                      cudaStream_t s) {
-  int plane_sz, kslab_sz, wsl_sz, stride;
+  int stride, plane_sz, kslab_sz;
   size_t bytes;
-  ball_smem(ryz_max, 1, plane_sz, kslab_sz, wsl_sz, stride, bytes);
+  ball_smem(ryz_max, 1, stride, plane_sz, kslab_sz, bytes);
   cudaFuncSetAttribute(k_stencil_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_stencil_ball<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid, plane_sz, kslab_sz, wsl_sz,
-                                                 stride);
+  k_stencil_ball<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid, stride, plane_sz,
+                                                 kslab_sz);
 }
 
 template <int WMAX>
 static void run_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int ryz_max[2],
                             int part_off, cudaStream_t s) {
-  int plane_sz, kslab_sz, wsl_sz, stride;
+  int stride, plane_sz, kslab_sz;
   size_t bytes;
-  ball_smem(ryz_max, 6, plane_sz, kslab_sz, wsl_sz, stride, bytes);
+  ball_smem(ryz_max, 6, stride, plane_sz, kslab_sz, bytes);
   cudaFuncSetAttribute(k_virial_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_virial_ball<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid,
-                                                w.part_wg + 6 * (long long)part_off, plane_sz, kslab_sz, wsl_sz,
-                                                stride);
+                                                w.part_wg + 6 * (long long)part_off, stride, plane_sz, kslab_sz);
 }
 
+void launch_pad(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return;
+  k_pad<<<nitems, kGridChunk, 0, s>>>(t.lev, items, w.grid);
+}
+
+// ryz_max = {largest R_y, largest halo hz} over the ball levels; rmax = largest R_z
 void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
                          int ryz_max[2], cudaStream_t s) {
   if (nitems <= 0) return;
@@ -393,13 +442,13 @@ void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, i
 
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {
   if (nitems <= 0) return;
-  k_stencil_box<<<nitems, kBoxChunk, 0, s>>>(t.lev, items, t.kpool, w.grid);
+  k_stencil_box<<<nitems, kBoxThreads, 0, s>>>(t.lev, items, t.kpool, w.grid);
 }
 
 void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, int part_off,
                        cudaStream_t s) {
   if (nitems <= 0) return;
-  k_virial_box<<<nitems, kBoxChunk, 0, s>>>(t.lev, items, t.kpool, w.grid, w.part_wg + 6 * (long long)part_off);
+  k_virial_box<<<nitems, kBoxThreads, 0, s>>>(t.lev, items, t.kpool, w.grid, w.part_wg + 6 * (long long)part_off);
 }
 
 }  // namespace msm

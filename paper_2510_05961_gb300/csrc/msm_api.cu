@@ -52,7 +52,7 @@ static int count_forward(const Engine& E, bool) {
   int n = 1 + 5 + 1;                                   // prologue, binning, short range
   n += E.anterp_items.empty() ? 0 : 1;
   for (int l = 1; l < E.maxcomp; l++) n += 2;          // restriction + prolongation per level step
-  n += E.ball_items.empty() ? 0 : 1;
+  n += E.ball_items.empty() ? 0 : 2;                   // halo padding + ball stencil
   n += E.box_items.empty() ? 0 : 1;
   n += 1 + 1 + 1;                                      // interp, finalize, energy
   return n;
@@ -95,6 +95,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   }
   {
     Phase ph(E, MSM_PH_STENCIL, s);
+    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), s);
     launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, s);
     launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
   }

@@ -20,7 +20,7 @@ constexpr int kBallBZ = 16;        // outputs per thread along z
 constexpr int kBallTZ = 32;        // stencil tile depth (z)
 constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
-constexpr int kBoxChunk = 128;     // outputs per box-stencil work item
+constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
 constexpr int kGridChunk = 256;    // points per restriction/prolongation item
 
 // device status bits (mirrors MSM_DEV_* of the public header)
@@ -43,6 +43,7 @@ struct SysDev {
   float invL[3];    // (float)(1/L): binning contract
   float Mf[3];      // M as float
   float inv_h1[3];  // 1/h_1 per axis
+  float Lf[3];      // cell lengths
   float a2, inv_a, inv_a2, inv_a3;
   float self_coef;  // gamma(0)/a (self term of Eq. U_zero)
   float gc[8];      // softening polynomial in s = 1 - rho^2: gamma = sum_k gc[k] s^k
@@ -58,11 +59,18 @@ struct LevDev {
   int R[3];                 // ball radius per axis
   int blo[3], bsz[3];       // box: offsets d in [blo, blo + bsz)
   float scale;              // stencil scale 2^-(l-1) relative to the stored values
-  long long k_off;          // stencil values (ball: dense (2R+1)^3; box: bsz product)
-  long long dk_off;         // virial weights: 6 consecutive arrays of the same layout
-  long long w_off;          // ball: column half-widths of K (int pool, (2Rx+1)(2Ry+1))
+  long long k_off;          // stencil values. box: dense bsz product; ball: per (dx, dy)
+                            // column, dz = -hz .. hz at [0, 2hz] of a row of kSK(hz) floats
+  long long dk_off;         // virial weights. box: 6 arrays like k; ball: [dx][6][dy][row]
+  long long w_off;          // ball: column half-widths of K (int pool, (2Rx+1)(2Ry+1), -1 = empty)
   long long wh_off;         // ball: column half-widths of the virial weights
+  int hz;                   // ball: z halo of the padded grid (>= R[2], multiple of 4)
+  int pn[3];                // ball: padded grid dims
+  long long p_off;          // ball: float offset of the halo-padded copy of q~^l in the grid pool
 };
+
+// row length (floats) of one stored ball-stencil column with halo hz
+__host__ __device__ constexpr int kSK(int hz) { return 2 * hz + 4; }
 
 struct AtomItem { int sys, start, count; };
 struct TileItem { int lev, x0, y0, z0; };
@@ -79,7 +87,7 @@ struct Work {
   int* bucket;
   int* perm;
   int* scell;
-  float4* xq;      // cell-local Cartesian position and charge, sorted order
+  float4* xq;      // position (x, y from the cell corner, z from the cell column's base) and charge, sorted
   float4* uq;      // level-1 grid coordinates and charge, sorted order
   float* phi_sr;   // short-range potential incl. self term, sorted
   float4* f_sr;    // short-range force, sorted
@@ -114,6 +122,7 @@ void launch_interp(const Work& w, const Tables& t, const AtomItem* items, int ni
 void launch_restrict(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
 void launch_prolong(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
 // stencils and grid virial (k_stencil.cu)
+void launch_pad(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);
 void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
                          int ryz_max[2], cudaStream_t s);
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);

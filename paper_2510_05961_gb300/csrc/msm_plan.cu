@@ -397,6 +397,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       D.invL[d] = (float)(1.0 / S.L[d]);
       D.Mf[d] = (float)S.M[d];
       D.inv_h1[d] = (float)(1.0 / S.h1[d]);
+      D.Lf[d] = (float)S.L[d];
     }
     D.a2 = (float)(S.a * S.a);
     D.inv_a = (float)(1.0 / S.a);
@@ -433,6 +434,17 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       grid_off += align_up(npts, 64);
       L.e_off = grid_off;
       grid_off += align_up(npts, 64);
+      L.p_off = -1;
+      if (L.kind == 0) {
+        // halo-padded copy of q~^l read by the ball kernels: halos R_x, R_y and
+        // hz = R_z rounded up to 4 floats; y and z extents rounded up to whole tiles
+        L.hz = (L.R[2] + 3) & ~3;
+        L.pn[0] = L.n[0] + 2 * L.R[0];
+        L.pn[1] = (int)align_up(L.n[1], kBallTY) + 2 * L.R[1];
+        L.pn[2] = (int)align_up(L.n[2], kBallTZ) + 2 * L.hz;
+        L.p_off = grid_off;
+        grid_off += align_up((long long)L.pn[0] * L.pn[1] * L.pn[2], 64);
+      }
       hlev.push_back(L);
     }
   }
@@ -446,10 +458,25 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     SysHost& S = sys[s];
     long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1;
     if (S.has_ball) {
+      // column layout read by the ball kernels: for each (dx, dy) a row of
+      // kSK(hz) floats with dz = -hz .. hz at [0, 2hz]; virial weights [dx][6][dy][row]
+      const int nx = 2 * S.R[0] + 1, ny = 2 * S.R[1] + 1, nz = 2 * S.R[2] + 1;
+      const int hz = (S.R[2] + 3) & ~3, SK = kSK(hz);
+      while (kp.size() % 4) kp.push_back(0.f);
       kball_off = (long long)kp.size();
-      kp.insert(kp.end(), S.kball.begin(), S.kball.end());
+      kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
+      for (int x = 0; x < nx; x++)
+        for (int y = 0; y < ny; y++)
+          for (int z = 0; z < nz; z++)
+            kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.R[2] + hz)] = S.kball[((size_t)x * ny + y) * nz + z];
       dkh_off = (long long)kp.size();
-      kp.insert(kp.end(), S.dkh.begin(), S.dkh.end());
+      kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
+      for (int x = 0; x < nx; x++)
+        for (int c = 0; c < 6; c++)
+          for (int y = 0; y < ny; y++)
+            for (int z = 0; z < nz; z++)
+              kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.R[2] + hz)] =
+                  S.dkh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
       wb_off = (long long)wp.size();
       wp.insert(wp.end(), S.wball.begin(), S.wball.end());
       wh_off = (long long)wp.size();
@@ -478,6 +505,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   // work lists
   anterp_items.clear();
   ball_items.clear();
+  pad_items.clear();
   box_items.clear();
   vb_off.assign(nsys + 1, 0);
   vx_off.assign(nsys + 1, 0);
@@ -500,7 +528,10 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
             for (int z = 0; z < L.n[2]; z += kBallTZ) ball_items.push_back({li, x, y, z});
         rmax = std::max(rmax, L.R[2]);
         ryz[0] = std::max(ryz[0], L.R[1]);
-        ryz[1] = std::max(ryz[1], L.R[2]);
+        ryz[1] = std::max(ryz[1], L.hz);
+        long long npad = (long long)L.pn[0] * L.pn[1] * L.pn[2];
+        for (long long st = 0; st < npad; st += kGridChunk)
+          pad_items.push_back({li, (int)st, (int)std::min<long long>(kGridChunk, npad - st)});
       } else {
         long long npts = (long long)L.n[0] * L.n[1] * L.n[2];
         for (long long st = 0; st < npts; st += kBoxChunk)
@@ -587,6 +618,7 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   if ((rc = up(anterp_items, &d_anterp_items, err))) return rc;
   if ((rc = up(ball_items, &d_ball_items, err))) return rc;
   if ((rc = up(box_items, &d_box_items, err))) return rc;
+  if ((rc = up(pad_items, &d_pad_items, err))) return rc;
   if ((rc = up(voff, &d_voff, err))) return rc;
   std::vector<RangeItem> all;
   restrict_off.assign(restrict_steps.size() + 1, 0);
@@ -616,6 +648,7 @@ Engine::~Engine() {
   cudaFree(d_anterp_items);
   cudaFree(d_ball_items);
   cudaFree(d_box_items);
+  cudaFree(d_pad_items);
   cudaFree(d_voff);
   cudaFree(d_range_items);
 }

@@ -3,8 +3,9 @@
 Tolerances (stated by the task for the FP32 path): relative energy error
 <= 1e-5, relative RMS error of forces, potentials (dE/dq) and virial
 <= 1e-4; the binning (cell_start, permutation, sorted cells) bit-exact.
-Intermediate grids are compared to the oracle's to 1e-4 of their largest
-entry (FP32 sums of up to a few thousand cancelling terms).
+Intermediate grids are compared to the oracle's to 1e-4 of the largest
+entry of the level-1 grid (each level's potential is prolonged onto level 1
+with weights <= 1, so that is the scale its FP32 rounding matters on).
 """
 import functools
 
@@ -102,12 +103,14 @@ def test_level_grids(key):
     w = WORKLOADS[key]()
     r = gpu_run(w, virial=False)
     P, ref = _oracle(key)
+    qscale = np.abs(ref["qlev"][0]).max()
+    escale = np.abs(ref["elev"][0]).max()
     for l in range(1, P.ncomp + 1):
         qg = r["plan"].debug_array(2, l).cpu().numpy().reshape(P.level_shape(l))
         eg = r["plan"].debug_array(3, l).cpu().numpy().reshape(P.level_shape(l))
         qo, eo = ref["qlev"][l - 1], ref["elev"][l - 1]
-        assert np.abs(qg - qo).max() <= 1e-4 * np.abs(qo).max() + 1e-12, ("q", l)
-        assert np.abs(eg - eo).max() <= 1e-4 * np.abs(eo).max() + 1e-12, ("e", l)
+        assert np.abs(qg - qo).max() <= 1e-4 * qscale, ("q", l)
+        assert np.abs(eg - eo).max() <= 1e-4 * escale, ("e", l)
 
 
 # ---------------------------------------------------------------- end to end
