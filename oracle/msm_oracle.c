@@ -47,7 +47,7 @@ typedef struct {
   int n[OR_MAXLEV][3];  /* grid points per level */
   int S[3];             /* kernel-sample radius of the level stencils */
   int R[3];             /* stencil radius S + p/2 - 1 */
-  int C[3];             /* binning cells per axis */
+  int C[3];             /* binning cells per axis (periodic: M / 2^k, edge <= a/2; open: floor(2L/a)) */
   double edge[3];       /* binning cell edges */
   int nnbr[3];          /* neighbour-cell reach ceil(a/edge) */
   float invLf[3];       /* (float)(1/L): binning contract */
@@ -320,9 +320,19 @@ int or_plan_init(or_plan* P) {
     P->S[d] = (int)ceil(2.0 * P->a / P->h1[d]) - 1;
     if (P->S[d] < 0) P->S[d] = 0;
     P->R[d] = P->S[d] + hp - 1;
-    int C = (int)floor(2.0 * P->L[d] / P->a);
-    if (C < 1) C = 1;
-    if (C > 256) C = 256;
+    int C;
+    if (P->pbc[d]) {
+      /* periodic axis: cells of k level-1 intervals, k the largest power of
+       * two with k h_1 <= a/2 (at least 1), at most 512 cells */
+      int k = 1;
+      while (2 * k <= P->M[d] && 2 * k * P->h1[d] <= 0.5 * P->a) k *= 2;
+      while (P->M[d] / k > 512) k *= 2;
+      C = P->M[d] / k;
+    } else {
+      C = (int)floor(2.0 * P->L[d] / P->a);
+      if (C < 1) C = 1;
+      if (C > 256) C = 256;
+    }
     P->C[d] = C;
     P->edge[d] = P->L[d] / C;
     P->nnbr[d] = (int)ceil(P->a / P->edge[d]);

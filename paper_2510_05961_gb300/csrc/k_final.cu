@@ -67,8 +67,8 @@ __global__ void k_virial_out(const SysDev* __restrict__ sys, const double* __res
   __shared__ double red[32][6];
   const SysDev& S = sys[blockIdx.x];
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < S.nitem; i += blockDim.x)
-    for (int c = 0; c < 6; c++) acc[c] += part_w0[6 * (long long)(S.item0 + i) + c];
+  for (int i = threadIdx.x; i < S.nitem * kChunkWarps; i += blockDim.x)
+    for (int c = 0; c < 6; c++) acc[c] += part_w0[6 * ((long long)S.item0 * kChunkWarps + i) + c];
   // grid partials of this system: its ball items, then its box items
   const int ns = gridDim.x;
   for (int r = 0; r < 2; r++) {

@@ -81,8 +81,16 @@ __global__ void __launch_bounds__(64) k_anterp(const SysDev* __restrict__ sys, c
     if (e > L.n[d]) e = L.n[d];
     m0[d] = st0[d] + L.lo[d];
     m1[d] = e - 1 + L.lo[d];
-    cl[d] = floordiv_i((m0[d] - H) * S.C[d], S.M[d]) - 1;
-    ch[d] = floordiv_i((m1[d] + H) * S.C[d], S.M[d]) + 1;
+    if (S.pbc[d] && S.M[d] % S.C[d] == 0) {
+      // cells aligned with the grid (k intervals per cell, powers of two): the
+      // cell of an atom is floor(u / k) exactly, so the range is exact
+      const int k = S.M[d] / S.C[d];
+      cl[d] = floordiv_i(m0[d] - H, k);
+      ch[d] = floordiv_i(m1[d] + H - 1, k);
+    } else {
+      cl[d] = floordiv_i((m0[d] - H) * S.C[d], S.M[d]) - 1;
+      ch[d] = floordiv_i((m1[d] + H) * S.C[d], S.M[d]) + 1;
+    }
     if (!S.pbc[d]) {
       if (cl[d] < 0) cl[d] = 0;
       if (ch[d] > S.C[d] - 1) ch[d] = S.C[d] - 1;

@@ -32,7 +32,6 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
                                                   const float4* __restrict__ xq, float* __restrict__ phi_sr,
                                                   float4* __restrict__ f_sr, double* __restrict__ part_w0,
                                                   int want_f, int want_w) {
-  __shared__ double red[kChunk / 32][6];
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   int local = it.start + threadIdx.x;
@@ -46,10 +45,10 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
     const int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
     float gc[P], gdc[P - 1];
 #pragma unroll
-    for (int t = 0; t < P; t++) gc[t] = S.gc[t];
+    for (int t = 0; t < P; t++) gc[t] = S.gca[t];
 #pragma unroll
-    for (int t = 0; t < P - 1; t++) gdc[t] = S.gdc[t];
-    const float a2 = S.a2, inv_a = S.inv_a, inv_a2 = S.inv_a2, two_inv_a3 = 2.0f * S.inv_a3;
+    for (int t = 0; t < P - 1; t++) gdc[t] = S.gdca[t];
+    const float a2 = S.a2, inv_a2 = S.inv_a2;
     const float ex = S.edge[0], ey = S.edge[1], ez = S.edge[2], inv_ez = 1.0f / ez;
     float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
@@ -95,20 +94,21 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
               float dg = gdc[P - 2];
 #pragma unroll
               for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, s, gdc[t]);
-              ph = fmaf(xj.w, rinv - g * inv_a, ph);
+              ph = fmaf(xj.w, rinv - g, ph);  // k_0 = 1/r - gamma(r/a)/a
               if (want_f | want_w) {
                 // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
-                const float fr = xj.w * fmaf(-rinv * rinv, rinv, two_inv_a3 * dg);
-                fx = fmaf(fr, dx, fx);
-                fy = fmaf(fr, dy, fy);
-                fz = fmaf(fr, dz, fz);
+                const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
+                const float frx = fr * dx, fry = fr * dy, frz = fr * dz;
+                fx += frx;
+                fy += fry;
+                fz += frz;
                 if (want_w) {
-                  w6[0] = fmaf(fr * dx, dx, w6[0]);
-                  w6[1] = fmaf(fr * dy, dy, w6[1]);
-                  w6[2] = fmaf(fr * dz, dz, w6[2]);
-                  w6[3] = fmaf(fr * dx, dy, w6[3]);
-                  w6[4] = fmaf(fr * dx, dz, w6[4]);
-                  w6[5] = fmaf(fr * dy, dz, w6[5]);
+                  w6[0] = fmaf(frx, dx, w6[0]);
+                  w6[1] = fmaf(fry, dy, w6[1]);
+                  w6[2] = fmaf(frz, dz, w6[2]);
+                  w6[3] = fmaf(frx, dy, w6[3]);
+                  w6[4] = fmaf(frx, dz, w6[4]);
+                  w6[5] = fmaf(fry, dz, w6[5]);
                 }
               }
             }
@@ -123,19 +123,13 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
     for (int c = 0; c < 6; c++) w6[c] *= -0.5f * xi.w;
   }
   if (!want_w) return;
-  // deterministic block reduction of the six virial components in FP64
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // per-warp FP64 partials of the six virial components (fixed order, no block barrier)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < 6; c++) {
     double v = (double)w6[c];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid][c] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double v = 0.0;
-    for (int w = 0; w < kChunk / 32; w++) v += red[w][threadIdx.x];
-    part_w0[6 * blockIdx.x + threadIdx.x] = v;
+    if (lane == 0) part_w0[6 * ((long long)blockIdx.x * kChunkWarps + wid) + c] = v;
   }
 }
 

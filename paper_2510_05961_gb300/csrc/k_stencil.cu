@@ -13,8 +13,8 @@
 // thread owns 16 consecutive z outputs in registers; per (dx, dy) stencil
 // column of half-width w it loads its 16 + 2w window and the 2w + 1 stencil
 // values with 128-bit shared loads and issues 16 (2w + 1) FFMA from registers.
-// w selects an unrolled variant, so the ball shape costs nothing for empty
-// columns. The arithmetic is FP32 on the CUDA cores: the sum has no dense
+// w (rounded up to an even value by the planner) selects an unrolled variant,
+// so the ball shape costs little for short columns and nothing for empty ones. The arithmetic is FP32 on the CUDA cores: the sum has no dense
 // reduction axis, and a Toeplitz recast for the tensor cores would multiply
 // the work by (16 + 2R)/(2R + 1) per axis while TF32 loses the accuracy the
 // method needs.
@@ -126,20 +126,21 @@ __device__ __forceinline__ void virial_column(float (&w6)[6], const float (&qown
   }
 }
 
+// dispatch on the (even) column half-width w
 template <int W, int WMAX>
 struct Col {
   static __device__ __forceinline__ void stencil(int w, float (&acc)[BZ], const float* q, const float* k) {
     if (w == W)
       ball_column<W>(acc, q, k);
     else
-      Col<W + 1, WMAX>::stencil(w, acc, q, k);
+      Col<W + 2, WMAX>::stencil(w, acc, q, k);
   }
   static __device__ __forceinline__ void virial(int w, float (&w6)[6], const float (&qown)[BZ], const float* q,
                                                 const float* k, int ks) {
     if (w == W)
       virial_column<W>(w6, qown, q, k, ks);
     else
-      Col<W + 1, WMAX>::virial(w, w6, qown, q, k, ks);
+      Col<W + 2, WMAX>::virial(w, w6, qown, q, k, ks);
   }
 };
 template <int WMAX>

@@ -14,6 +14,7 @@ namespace msm {
 
 constexpr int kMaxLev = 20;
 constexpr int kChunk = 256;        // atoms per per-atom work item
+constexpr int kChunkWarps = kChunk / 32;
 constexpr int kAnterpT = 8;        // anterpolation tile edge (grid points)
 constexpr int kBallTY = 32;        // stencil tile rows (y)
 constexpr int kBallBZ = 16;        // outputs per thread along z
@@ -46,8 +47,8 @@ struct SysDev {
   float Lf[3];      // cell lengths
   float a2, inv_a, inv_a2, inv_a3;
   float self_coef;  // gamma(0)/a (self term of Eq. U_zero)
-  float gc[8];      // softening polynomial in s = 1 - rho^2: gamma = sum_k gc[k] s^k
-  float gdc[8];     // gdc[k] = (k+1) gc[k+1]: d gamma / d s = sum_k gdc[k] s^k
+  float gca[8];     // softening polynomial over a, in s = 1 - (r/a)^2: gamma(r/a)/a = sum_k gca[k] s^k
+  float gdca[8];    // (2/a^3) d gamma / d s = sum_k gdca[k] s^k, so k_0'(r)/r = -1/r^3 + sum_k gdca[k] s^k
   float jc[9];      // restriction coefficients J_k, k = -p/2 .. p/2 (index k + p/2)
 };
 
@@ -94,7 +95,7 @@ struct Work {
   float* phi_lr;   // long-range potential, sorted
   float4* f_lr;    // long-range force, sorted
   double* part_e;  // per atom item: 1/2 sum q phi
-  double* part_w0; // per atom item: 6 short-range virial components
+  double* part_w0; // per warp of each atom item: 6 short-range virial components
   double* part_wg; // per virial item: 6 grid virial components
   float* grid;     // grid pool
 };

@@ -267,8 +267,17 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
   for (int d = 0; d < 3; d++) {
     S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a / S.h1[d]) - 1);
     S.R[d] = S.S[d] + H - 1;
-    int C = (int)std::floor(2.0 * S.L[d] / S.a);
-    S.C[d] = std::min(std::max(C, 1), 256);
+    if (S.pbc[d]) {
+      // periodic axis: cells aligned with the grid, k = 2^j level-1 intervals
+      // per cell, the largest with k h_1 <= a/2 (k >= 1), at most 512 cells
+      int k = 1;
+      while (2 * k <= S.M[d] && 2 * k * S.h1[d] <= 0.5 * S.a) k *= 2;
+      while (S.M[d] / k > 512) k *= 2;
+      S.C[d] = S.M[d] / k;
+    } else {
+      int C = (int)std::floor(2.0 * S.L[d] / S.a);
+      S.C[d] = std::min(std::max(C, 1), 256);
+    }
     S.edge[d] = S.L[d] / S.C[d];
     S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
   }
@@ -323,6 +332,8 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     const int nx = 2 * S.R[0] + 1, ny = 2 * S.R[1] + 1, nz = 2 * S.R[2] + 1;
     S.kball.assign(K1.v.begin(), K1.v.end());
     S.dkh.assign((size_t)6 * nx * ny * nz, 0.0f);
+    // column half-widths, rounded up to even values (the stored rows are zero
+    // beyond the support): half as many unrolled column variants
     S.wball.assign((size_t)nx * ny, -1);
     S.whalf.assign((size_t)nx * ny, -1);
     for (int x = -S.R[0]; x <= S.R[0]; x++)
@@ -330,7 +341,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
         for (int z = -S.R[2]; z <= S.R[2]; z++) {
           size_t at = ((size_t)(x + S.R[0]) * ny + (y + S.R[1])) * nz + (z + S.R[2]);
           size_t col = (size_t)(x + S.R[0]) * ny + (y + S.R[1]);
-          if ((float)K1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z));
+          if ((float)K1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z) + (std::abs(z) & 1));
           // half-space weights: C_d = C_-d, so sum_d dK_d C_d = dK_0 C_0 + 2 sum_(d in half) dK_d C_d
           bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
           bool zero = x == 0 && y == 0 && z == 0;
@@ -341,7 +352,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
             S.dkh[(size_t)c * nx * ny * nz + at] = v;
             if (v != 0.0f) any = true;
           }
-          if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z));
+          if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z) + (std::abs(z) & 1));
         }
   }
   // scalar coefficients
@@ -404,8 +415,8 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     D.inv_a2 = (float)(1.0 / (S.a * S.a));
     D.inv_a3 = (float)(1.0 / (S.a * S.a * S.a));
     D.self_coef = (float)(soft(S.p, 0.0) / S.a);
-    for (int k = 0; k < S.p; k++) D.gc[k] = (float)S.gc[k];
-    for (int k = 0; k + 1 < S.p; k++) D.gdc[k] = (float)((k + 1) * S.gc[k + 1]);
+    for (int k = 0; k < S.p; k++) D.gca[k] = (float)(S.gc[k] / S.a);
+    for (int k = 0; k + 1 < S.p; k++) D.gdca[k] = (float)(2.0 * (k + 1) * S.gc[k + 1] / (S.a * S.a * S.a));
     for (int k = 0; k <= S.p; k++) D.jc[k] = (float)S.jc[k];
     for (int st = 0; st < counts[s]; st += kChunk) atom_items.push_back({s, st, std::min(kChunk, counts[s] - st)});
     if (counts[s] == 0) atom_items.push_back({s, 0, 0});
@@ -526,7 +537,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
         for (int x = 0; x < L.n[0]; x++)
           for (int y = 0; y < L.n[1]; y += kBallTY)
             for (int z = 0; z < L.n[2]; z += kBallTZ) ball_items.push_back({li, x, y, z});
-        rmax = std::max(rmax, L.R[2]);
+        rmax = std::max(rmax, L.R[2] + (L.R[2] & 1));  // column half-widths are even
         ryz[0] = std::max(ryz[0], L.R[1]);
         ryz[1] = std::max(ryz[1], L.hz);
         long long npad = (long long)L.pn[0] * L.pn[1] * L.pn[2];
@@ -591,7 +602,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_f_sr = take(sizeof(float4) * N);
   L_f_lr = take(sizeof(float4) * N);
   L_part_e = take(sizeof(double) * atom_items.size());
-  L_part_w0 = take(sizeof(double) * 6 * atom_items.size());
+  L_part_w0 = take(sizeof(double) * 6 * kChunkWarps * atom_items.size());
   L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(ball_items.size() + box_items.size(), 1));
   L_grid = take(sizeof(float) * std::max<long long>(grid_floats, 1));
   ws_bytes = off;
