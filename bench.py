@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--atoms", type=int, default=N_HEADLINE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-atoms", type=int, default=128_000)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-systems", type=int, default=512)
     return ap.parse_args()
 
 
@@ -201,6 +203,79 @@ def run_reference(args):
     }))
 
 
+# --------------------------------------------------------------------------- batched systems
+def batch_bench(dev, nsys, steps, warmup):
+    """512 independent systems (log-uniform 20-4000 atoms, open / slab / periodic):
+    forward + backward of the whole batch as one captured CUDA graph, against a
+    loop of single-system forward + backward calls on the same systems."""
+    import torch
+
+    from paper_2510_05961_gb300 import Batch, Plan
+    from paper_2510_05961_gb300 import workloads as W
+
+    systems = W.batch_systems(nsys=nsys)
+    ntot = sum(s.n for s in systems)
+    batch = Batch(systems, device=dev)
+    pos = torch.from_numpy(__import__("numpy").concatenate([s.pos for s in systems])).to(dev)
+    q = torch.from_numpy(__import__("numpy").concatenate([s.q for s in systems])).to(dev)
+    g = torch.ones(nsys, dtype=torch.float64, device=dev)
+    out_f = (torch.empty(nsys, dtype=torch.float64, device=dev), None,
+             torch.empty((ntot, 3), dtype=torch.float32, device=dev))
+    out_b = (torch.empty((ntot, 3), dtype=torch.float32, device=dev), torch.empty(ntot, dtype=torch.float32, device=dev),
+             torch.empty(9 * nsys, dtype=torch.float64, device=dev))
+
+    def bstep():
+        batch.forward(pos, q, forces=True, virial=True, phi=False, out=out_f)
+        batch.backward(g, out=out_b)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            bstep()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    assert batch.status() == 0
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        bstep()
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_batch = e0.elapsed_time(e1) / steps
+
+    plans = [Plan(s.cell, s.pbc, s.h, s.a, s.p, s.levels, max_atoms=s.n, device=dev) for s in systems]
+    pos_s = [torch.from_numpy(s.pos).to(dev) for s in systems]
+    q_s = [torch.from_numpy(s.q).to(dev) for s in systems]
+    g1 = torch.ones(1, dtype=torch.float64, device=dev)
+
+    def lstep():
+        for pl, p_, q_ in zip(plans, pos_s, q_s):
+            pl.forward(p_, q_, forces=True, virial=True, phi=False)
+            pl.backward(g1)
+
+    lstep()
+    torch.cuda.synchronize(dev)
+    nl = max(1, min(steps, 5))
+    e0.record(st)
+    for _ in range(nl):
+        lstep()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_loop = e0.elapsed_time(e1) / nl
+    return {"systems": nsys, "atoms": ntot, "ms_batched_graph": ms_batch, "ms_loop_single_calls": ms_loop,
+            "speedup": ms_loop / ms_batch, "atoms_per_s_batched": ntot / (ms_batch / 1e3),
+            "workload": "log-uniform 20-4000 atoms, 1/3 open, 1/3 slab (x,y periodic), 1/3 periodic, 0.08/A^3, "
+                        "N(0,0.5) charges; p=4, h=2, a=8; fwd+bwd (E, F, dE/dq, virial)"}
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -324,6 +399,10 @@ def run_gpu(args):
             "phase_ms": {k: round(v, 4) for k, v in ph_ms.items()},
             "algorithmic_flops": {"stencil": st_flops, "short": sr_flops}}
 
+    batch_res = None
+    if rank == 0 and not args.no_batch:
+        batch_res = batch_bench(dev, args.batch_systems, max(args.steps, 5), args.warmup)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         val, dt, cores = oracle_sample(args.cpu_sample_atoms)
@@ -341,7 +420,7 @@ def run_gpu(args):
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_val, "unit": "atoms/s", "h2d_bytes_per_step": n * 16,
                     "d2h_bytes_per_step": n * 16 + 8 + 72, "ms_per_step": ms_e2e},
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "batch": batch_res,
         }
         print(json.dumps(line))
     if world > 1:

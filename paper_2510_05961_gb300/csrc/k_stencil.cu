@@ -401,7 +401,10 @@ static void run_ball(const Work& w, const Tables& t, const TileItem* items, int 
   int stride, plane_sz, kslab_sz;
   size_t bytes;
   ball_smem(ryz_max, 1, stride, plane_sz, kslab_sz, bytes);
-  cudaFuncSetAttribute(k_stencil_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static size_t attr = 0;  // raise the dynamic shared-memory limit once per size
+  if (bytes > attr && cudaFuncSetAttribute(k_stencil_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bytes) == cudaSuccess)
+    attr = bytes;
   k_stencil_ball<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid, stride, plane_sz,
                                                  kslab_sz);
 }
@@ -412,7 +415,10 @@ static void run_virial_ball(const Work& w, const Tables& t, const TileItem* item
   int stride, plane_sz, kslab_sz;
   size_t bytes;
   ball_smem(ryz_max, 6, stride, plane_sz, kslab_sz, bytes);
-  cudaFuncSetAttribute(k_virial_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static size_t attr = 0;
+  if (bytes > attr && cudaFuncSetAttribute(k_virial_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bytes) == cudaSuccess)
+    attr = bytes;
   k_virial_ball<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid,
                                                 w.part_wg + 6 * (long long)part_off, stride, plane_sz, kslab_sz);
 }
