@@ -109,23 +109,40 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- roofline helpers
-def stencil_flops(plan_params, info):
-    """Algorithmic FLOPs of one stencil launch: 2 x sum over levels of points x stencil nonzeros."""
+def stencil_flops(plan_params, info, cell, a, p):
+    """Algorithmic FLOPs of one stencil phase.
+
+    Ball levels apply the raw kernel samples s (nonzero for |h_1 o n| < 2a) to
+    the omega'-prefiltered grid: 2 x points x nnz(s), plus the prefilter,
+    2 x (p-1)^3 per padded point. Box levels apply the folded stencil:
+    2 x points x its nonzeros."""
     import ctypes as C
 
     import numpy as np
 
     from paper_2510_05961_gb300 import _lib
     lib = _lib.load()
+    h1 = np.array(info["h1"])
+    S = [int(math.ceil(2 * a / h1[d])) - 1 for d in range(3)]
+    assert p == 4, "ball levels apply raw samples (and prefilter) for p = 4 only"
+    g = [np.arange(-S[d], S[d] + 1) * h1[d] for d in range(3)]
+    r2 = g[0][:, None, None] ** 2 + g[1][None, :, None] ** 2 + g[2][None, None, :] ** 2
+    nnz_s = int(np.count_nonzero(r2 < (2 * a) ** 2))
     total = 0.0
     for l in range(1, info["ncomp"] + 1):
-        lo = (C.c_int * 3)()
-        sz = (C.c_int * 3)()
-        _lib.check(lib.msm_plan_stencil(C.byref(plan_params), l, 0, None, 0, lo, sz))
-        out = np.zeros(sz[0] * sz[1] * sz[2], np.float32)
-        _lib.check(lib.msm_plan_stencil(C.byref(plan_params), l, 0, out.ctypes.data_as(C.c_void_p), out.size, lo, sz))
         n = info["n"][l - 1]
-        total += 2.0 * n[0] * n[1] * n[2] * np.count_nonzero(out)
+        pts = n[0] * n[1] * n[2]
+        if info["stencil_kind"][l - 1] == 0:
+            padded = (n[0] + 2 * S[0]) * (n[1] + 2 * S[1]) * (n[2] + 2 * S[2])
+            total += 2.0 * pts * nnz_s + 2.0 * padded * (p - 1) ** 3
+        else:
+            lo = (C.c_int * 3)()
+            sz = (C.c_int * 3)()
+            _lib.check(lib.msm_plan_stencil(C.byref(plan_params), l, 0, None, 0, lo, sz))
+            out = np.zeros(sz[0] * sz[1] * sz[2], np.float32)
+            _lib.check(lib.msm_plan_stencil(C.byref(plan_params), l, 0, out.ctypes.data_as(C.c_void_p), out.size,
+                                            lo, sz))
+            total += 2.0 * pts * np.count_nonzero(out)
     return total
 
 
@@ -385,7 +402,7 @@ def run_gpu(args):
     # roofline of the dominant kernel (by measured phase time)
     ph_ms = {k: v / args.steps for k, v in phase_tot.items()}
     peak_fp32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    st_flops = stencil_flops(plan.params, info)
+    st_flops = stencil_flops(plan.params, info, w.cell, w.a, w.p)
     sr_flops = short_flops(n, 0.1, w.a)
     cand = {"stencil": (st_flops, ph_ms.get("stencil", 0.0)), "short": (sr_flops, ph_ms.get("short", 0.0))}
     dom = max(cand, key=lambda k: cand[k][1])

@@ -3,10 +3,14 @@
 // grid part of the virial, W = -1/2 sum_l sum_d (dK^l/d eps)_d C^l_d with the
 // autocorrelation C^l_d = sum_m q~^l_m q~^l_(m-d).
 //
-// Ball levels (stencil support a ball of radius R that does not overlap
-// itself under the periodic wrap). A pad kernel first writes a halo-padded
-// copy of q~^l (periodic images or zeros in the halo), so every tile's input
-// box is a plain rectangle. One block per output tile of 1 x 32 x 32 points
+// Ball levels (support a ball of radius R that does not overlap itself under
+// the periodic wrap). Since K^l = omega'^3 * s^l with s^l the raw samples of
+// k_l on the grid (Eq. kernel_stencil_by_conv_with_universal_coeff), the ball
+// kernels compute e^l = s^l * (omega'^3 * q~^l): the samples have a smaller
+// ball (|h o n| < 2a, about two thirds of K's nonzeros) and the 3-tap-per-axis
+// prefilter is fused into a pad kernel that writes a halo-padded copy of the
+// prefiltered grid (periodic images or zeros in the halo), so every tile's
+// input box is a plain rectangle. One block per output tile of 1 x 32 x 32 points
 // streams the 2R+1 input x-planes of the tile's halo through shared memory
 // (16-byte cp.async rows, double buffered) together with the matching x-slab
 // of the stencil, stored column by column with dz aligned to 16 bytes. Each
@@ -20,9 +24,10 @@
 // method needs.
 //
 // The ball virial kernel is the same loop with the roles swapped: per column a
-// thread forms its partial C_(dx,dy,dz) for the 2w + 1 dz values and at once
-// contracts it with the six strain-derivative weights (stored with the
-// half-space symmetry C_d = C_-d folded in).
+// thread forms its partial C'_(dx,dy,dz) = sum_m q~_m q'_(m-d) for the 2w + 1 dz
+// values and at once contracts it with the six strain-derivative samples
+// (q~^T dK q~ = sum_d ds_d C'_d for dK = omega'^3 * ds; stored with the
+// half-space symmetry C'_d = C'_-d folded in).
 //
 // Box levels (small periodic levels whose stencil wraps onto itself, folded
 // onto the grid, and the top level of open systems): one warp per output, the
@@ -50,21 +55,54 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ halo padding
-__global__ void __launch_bounds__(kGridChunk) k_pad(const LevDev* __restrict__ levs,
+// Halo-padded copy of the omega'-prefiltered grid, q'_m = sum_t omega'_tx
+// omega'_ty omega'_tz q~_(m-t) (periodic axes wrap, open axes read zeros outside
+// the grid). The ball kernels apply the raw kernel samples s to q', which equals
+// K * q~ since K = omega'^3 * s (Eq. kernel_stencil_by_conv_with_universal_coeff)
+// and convolution is associative.
+// index of grid point c along an axis of n points: periodic axes wrap (the
+// halo may reach past one period on small grids), open axes give -1 outside
+__device__ __forceinline__ int pad_axis(int c, int n, int per) {
+  if (per) {
+    while (c < 0) c += n;
+    while (c >= n) c -= n;
+    return c;
+  }
+  return (c >= 0 && c < n) ? c : -1;
+}
+
+__global__ void __launch_bounds__(kGridChunk) k_pad(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                     const RangeItem* __restrict__ items, float* __restrict__ grid) {
   RangeItem it = items[blockIdx.x];
   if ((int)threadIdx.x >= it.count) return;
   const LevDev& L = levs[it.lev];
-  int idx = it.start + threadIdx.x;
-  int pz = idx % L.pn[2], py = (idx / L.pn[2]) % L.pn[1], px = idx / (L.pn[2] * L.pn[1]);
-  int c[3] = {px - L.R[0], py - L.R[1], pz - L.hz};
-  bool ok = true;
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    if (L.per[d]) c[d] = wrap_s(c[d], L.n[d]);
-    else ok = ok && c[d] >= 0 && c[d] < L.n[d];
+  const SysDev& S = sys[L.sys];
+  const int r = S.pre_r;
+  const int idx = it.start + threadIdx.x;
+  const int pz = idx % L.pn[2], py = (idx / L.pn[2]) % L.pn[1], px = idx / (L.pn[2] * L.pn[1]);
+  const int c[3] = {px - L.R[0], py - L.R[1], pz - L.hz};
+  // wrapped source index of each tap, once per axis
+  int ix[7], iy[7], iz[7];
+  for (int t = -r; t <= r; t++) {
+    ix[t + r] = pad_axis(c[0] - t, L.n[0], L.per[0]);
+    iy[t + r] = pad_axis(c[1] - t, L.n[1], L.per[1]);
+    iz[t + r] = pad_axis(c[2] - t, L.n[2], L.per[2]);
   }
-  grid[L.p_off + idx] = ok ? grid[L.q_off + ((long long)c[0] * L.n[1] + c[1]) * L.n[2] + c[2]] : 0.0f;
+  const float* q = grid + L.q_off;
+  float acc = 0.f;
+  for (int tx = 0; tx <= 2 * r; tx++) {
+    if (ix[tx] < 0) continue;
+    const float wx = S.om[tx < r ? r - tx : tx - r];
+    for (int ty = 0; ty <= 2 * r; ty++) {
+      if (iy[ty] < 0) continue;
+      const float* row = q + ((long long)ix[tx] * L.n[1] + iy[ty]) * L.n[2];
+      float az = 0.f;
+      for (int tz = 0; tz <= 2 * r; tz++)
+        if (iz[tz] >= 0) az = fmaf(S.om[tz < r ? r - tz : tz - r], __ldg(row + iz[tz]), az);
+      acc = fmaf(wx * S.om[ty < r ? r - ty : ty - r], az, acc);
+    }
+  }
+  grid[L.p_off + idx] = acc;
 }
 
 // ------------------------------------------------------------------ columns
@@ -238,10 +276,10 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const LevDev* __restrict__ l
   const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
   const int ty = threadIdx.x % TY, zb = threadIdx.x / TY;
   const int kstride = (2 * Ry + 1) * SK;
-  float qown[BZ];
+  float qown[BZ];  // raw q~ at this thread's points (the window below reads the prefiltered q')
   {
     const int y = it.y0 + ty, z0 = it.z0 + zb * BZ;
-    const float* row = grid + L.p_off + ((long long)(it.x0 + Rx) * L.pn[1] + (y + Ry)) * L.pn[2] + hz;
+    const float* row = grid + L.q_off + ((long long)it.x0 * L.n[1] + y) * L.n[2];
 #pragma unroll
     for (int o = 0; o < BZ; o++) qown[o] = (y < L.n[1] && z0 + o < L.n[2]) ? row[z0 + o] : 0.f;
   }
@@ -425,7 +463,7 @@ static void run_virial_ball(const Work& w, const Tables& t, const TileItem* item
 
 void launch_pad(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {
   if (nitems <= 0) return;
-  k_pad<<<nitems, kGridChunk, 0, s>>>(t.lev, items, w.grid);
+  k_pad<<<nitems, kGridChunk, 0, s>>>(t.sys, t.lev, items, w.grid);
 }
 
 // ryz_max = {largest R_y, largest halo hz} over the ball levels; rmax = largest R_z

@@ -283,22 +283,9 @@ int msm_plan_stencil(const msm_params* params, int level, int which, float* out,
       sz[d] = 2 * S.R[d] + 1;
     }
     count = (size_t)sz[0] * sz[1] * sz[2];
-    if (which == 0) {
-      tmp.assign(S.kball.begin(), S.kball.end());
-    } else {
-      // the kernel stores half-space weights; undo that for the caller
-      tmp.assign(S.dkh.begin() + (which - 1) * count, S.dkh.begin() + which * count);
-      for (int x = -S.R[0]; x <= S.R[0]; x++)
-        for (int y = -S.R[1]; y <= S.R[1]; y++)
-          for (int z = -S.R[2]; z <= S.R[2]; z++) {
-            size_t at = ((size_t)(x + S.R[0]) * sz[1] + (y + S.R[1])) * sz[2] + (z + S.R[2]);
-            size_t mir = ((size_t)(-x + S.R[0]) * sz[1] + (-y + S.R[1])) * sz[2] + (-z + S.R[2]);
-            bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
-            if (half) tmp[at] *= 0.5f;
-            else if (!(x == 0 && y == 0 && z == 0)) tmp[at] = 0.5f * S.dkh[(which - 1) * count + mir];
-          }
-    }
-    for (auto& v : tmp) v *= Lv.scale;
+    const double* v = which == 0 ? S.kball.data() : S.dk1.data() + (which - 1) * count;
+    tmp.resize(count);
+    for (size_t i = 0; i < count; i++) tmp[i] = (float)(v[i] * Lv.scale);
     src = tmp.data();
   } else {
     for (int d = 0; d < 3; d++) {

@@ -50,6 +50,8 @@ struct SysDev {
   float gca[8];     // softening polynomial over a, in s = 1 - (r/a)^2: gamma(r/a)/a = sum_k gca[k] s^k
   float gdca[8];    // (2/a^3) d gamma / d s = sum_k gdca[k] s^k, so k_0'(r)/r = -1/r^3 + sum_k gdca[k] s^k
   float jc[9];      // restriction coefficients J_k, k = -p/2 .. p/2 (index k + p/2)
+  float om[4];      // prefilter of the ball levels: omega'_0 .. omega'_(pre_r) (symmetric), or identity
+  int pre_r;        // prefilter half-width (p/2 - 1 when the ball kernels apply raw samples, else 0)
 };
 
 struct LevDev {
@@ -67,7 +69,8 @@ struct LevDev {
   long long wh_off;         // ball: column half-widths of the virial weights
   int hz;                   // ball: z halo of the padded grid (>= R[2], multiple of 4)
   int pn[3];                // ball: padded grid dims
-  long long p_off;          // ball: float offset of the halo-padded copy of q~^l in the grid pool
+  long long p_off;          // ball: float offset of the halo-padded, omega'-prefiltered copy of q~^l
+                            // (ball levels apply raw kernel samples; R is the sample radius)
 };
 
 // row length (floats) of one stored ball-stencil column with halo hz

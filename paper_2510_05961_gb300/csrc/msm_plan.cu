@@ -146,6 +146,34 @@ static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box
       }
 }
 
+// Raw kernel samples on [-E, E] (per axis), without the omega' convolution:
+// comp 0: k_l(|v|); comp 1..6: k_l'(|v|) v_a v_b / |v|, v = h_l o n.
+static void build_samples(const SysHost& S, int l, const int E[3], int comp, Box3& out) {
+  double hl[3];
+  for (int d = 0; d < 3; d++) hl[d] = S.h1[d] * std::ldexp(1.0, l - 1);
+  static const int AB[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  int lo[3], sz[3];
+  for (int d = 0; d < 3; d++) {
+    lo[d] = -E[d];
+    sz[d] = 2 * E[d] + 1;
+  }
+  out.init(lo, sz);
+  for (int x = -E[0]; x <= E[0]; x++)
+    for (int y = -E[1]; y <= E[1]; y++)
+      for (int z = -E[2]; z <= E[2]; z++) {
+        double v[3] = {hl[0] * x, hl[1] * y, hl[2] * z};
+        double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double val;
+        if (comp == 0) {
+          val = klev(S, l, rr, false);
+        } else {
+          int a = AB[comp - 1][0], b = AB[comp - 1][1];
+          val = rr > 0.0 ? klev(S, l, rr, true) * v[a] * v[b] / rr : 0.0;
+        }
+        out.at(x, y, z) = val;
+      }
+}
+
 // fold the periodic axes of an unfolded box onto [0, n) and scale
 static void fold(const Box3& in, const int n[3], const int per[3], double scale, Box3& out) {
   int lo[3], sz[3];
@@ -267,6 +295,8 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
   for (int d = 0; d < 3; d++) {
     S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a / S.h1[d]) - 1);
     S.R[d] = S.S[d] + H - 1;
+    S.prefilter = (S.p == 4);
+    S.B[d] = S.prefilter ? S.S[d] : S.R[d];
     if (S.pbc[d]) {
       // periodic axis: cells aligned with the grid, k = 2^j level-1 intervals
       // per cell, the largest with k h_1 <= a/2 (k >= 1), at most 512 cells
@@ -281,7 +311,9 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     S.edge[d] = S.L[d] / S.C[d];
     S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
   }
-  // level-1 shape stencil (intermediate levels are K^1 / 2^(l-1)) and virial weights
+  // level-1 shape stencil K^1 (intermediate levels are K^1 / 2^(l-1)) and its
+  // strain derivatives; the ball kernels apply the raw samples s^1 instead,
+  // to the omega'-prefiltered grid: K * q = (omega'^3 * s) * q = s * (omega'^3 * q)
   const bool any_mid = S.ncomp >= 1 && S.nlev > 1;
   S.has_ball = false;
   Box3 K1, dK1[6];
@@ -297,14 +329,15 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     // (and stencils that overlap themselves on a periodic grid) use the box kernel
     bool ball = !top;
     for (int d = 0; d < 3; d++)
-      if ((Lv.per[d] && 2 * S.R[d] + 1 > Lv.n[d]) || S.R[d] > kBallRmax) ball = false;
-    for (int d = 0; d < 3; d++) Lv.R[d] = S.R[d];
+      if ((Lv.per[d] && 2 * S.B[d] + 1 > Lv.n[d]) || S.B[d] > kBallRmax) ball = false;
+    for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
     if (ball) {
       Lv.kind = 0;
       S.has_ball = true;
       continue;
     }
     Lv.kind = 1;
+    for (int d = 0; d < 3; d++) Lv.R[d] = S.R[d];
     Box3 Kf, dKf[6];
     if (top) {
       int E[3];
@@ -328,28 +361,41 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     Lv.dkbox.clear();
     for (int c = 0; c < 6; c++) Lv.dkbox.insert(Lv.dkbox.end(), dKf[c].v.begin(), dKf[c].v.end());
   }
-  if (S.has_ball) {
-    const int nx = 2 * S.R[0] + 1, ny = 2 * S.R[1] + 1, nz = 2 * S.R[2] + 1;
+  if (any_mid) {
     S.kball.assign(K1.v.begin(), K1.v.end());
-    S.dkh.assign((size_t)6 * nx * ny * nz, 0.0f);
+    S.dk1.clear();
+    for (int c = 0; c < 6; c++) S.dk1.insert(S.dk1.end(), dK1[c].v.begin(), dK1[c].v.end());
+  }
+  if (S.has_ball) {
+    Box3 s1, ds1[6];
+    if (S.prefilter) {
+      build_samples(S, 1, S.B, 0, s1);
+      for (int c = 0; c < 6; c++) build_samples(S, 1, S.B, c + 1, ds1[c]);
+    } else {
+      s1 = K1;
+      for (int c = 0; c < 6; c++) ds1[c] = dK1[c];
+    }
+    const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
+    S.sball.assign(s1.v.begin(), s1.v.end());
+    S.dsh.assign((size_t)6 * nx * ny * nz, 0.0f);
     // column half-widths, rounded up to even values (the stored rows are zero
     // beyond the support): half as many unrolled column variants
     S.wball.assign((size_t)nx * ny, -1);
     S.whalf.assign((size_t)nx * ny, -1);
-    for (int x = -S.R[0]; x <= S.R[0]; x++)
-      for (int y = -S.R[1]; y <= S.R[1]; y++)
-        for (int z = -S.R[2]; z <= S.R[2]; z++) {
-          size_t at = ((size_t)(x + S.R[0]) * ny + (y + S.R[1])) * nz + (z + S.R[2]);
-          size_t col = (size_t)(x + S.R[0]) * ny + (y + S.R[1]);
-          if ((float)K1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z) + (std::abs(z) & 1));
-          // half-space weights: C_d = C_-d, so sum_d dK_d C_d = dK_0 C_0 + 2 sum_(d in half) dK_d C_d
+    for (int x = -S.B[0]; x <= S.B[0]; x++)
+      for (int y = -S.B[1]; y <= S.B[1]; y++)
+        for (int z = -S.B[2]; z <= S.B[2]; z++) {
+          size_t at = ((size_t)(x + S.B[0]) * ny + (y + S.B[1])) * nz + (z + S.B[2]);
+          size_t col = (size_t)(x + S.B[0]) * ny + (y + S.B[1]);
+          if ((float)s1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z) + (std::abs(z) & 1));
+          // half-space weights: C'_d = C'_-d, so sum_d ds_d C'_d = ds_0 C'_0 + 2 sum_(d in half) ds_d C'_d
           bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
           bool zero = x == 0 && y == 0 && z == 0;
           double f = half ? 2.0 : (zero ? 1.0 : 0.0);
           bool any = false;
           for (int c = 0; c < 6; c++) {
-            float v = (float)(f * dK1[c].v[at]);
-            S.dkh[(size_t)c * nx * ny * nz + at] = v;
+            float v = (float)(f * ds1[c].v[at]);
+            S.dsh[(size_t)c * nx * ny * nz + at] = v;
             if (v != 0.0f) any = true;
           }
           if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z) + (std::abs(z) & 1));
@@ -418,6 +464,15 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     for (int k = 0; k < S.p; k++) D.gca[k] = (float)(S.gc[k] / S.a);
     for (int k = 0; k + 1 < S.p; k++) D.gdca[k] = (float)(2.0 * (k + 1) * S.gc[k + 1] / (S.a * S.a * S.a));
     for (int k = 0; k <= S.p; k++) D.jc[k] = (float)S.jc[k];
+    {
+      double om[4];
+      omega_half(S.p, om);
+      // the ball kernels prefilter the grid with omega' (and apply the raw
+      // samples) for p = 4 only; for p = 6, 8 the large omega' (omega'_0 = 3.0,
+      // 6.0) would cost FP32 digits, so they apply K itself (identity prefilter)
+      D.pre_r = S.prefilter ? S.p / 2 - 1 : 0;
+      for (int k = 0; k < 4; k++) D.om[k] = S.prefilter ? (k < S.p / 2 ? (float)om[k] : 0.f) : (k == 0 ? 1.f : 0.f);
+    }
     for (int st = 0; st < counts[s]; st += kChunk) atom_items.push_back({s, st, std::min(kChunk, counts[s] - st)});
     if (counts[s] == 0) atom_items.push_back({s, 0, 0});
     D.nitem = (int)atom_items.size() - D.item0;
@@ -471,23 +526,23 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     if (S.has_ball) {
       // column layout read by the ball kernels: for each (dx, dy) a row of
       // kSK(hz) floats with dz = -hz .. hz at [0, 2hz]; virial weights [dx][6][dy][row]
-      const int nx = 2 * S.R[0] + 1, ny = 2 * S.R[1] + 1, nz = 2 * S.R[2] + 1;
-      const int hz = (S.R[2] + 3) & ~3, SK = kSK(hz);
+      const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
+      const int hz = (S.B[2] + 3) & ~3, SK = kSK(hz);
       while (kp.size() % 4) kp.push_back(0.f);
       kball_off = (long long)kp.size();
       kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
       for (int x = 0; x < nx; x++)
         for (int y = 0; y < ny; y++)
           for (int z = 0; z < nz; z++)
-            kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.R[2] + hz)] = S.kball[((size_t)x * ny + y) * nz + z];
+            kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.sball[((size_t)x * ny + y) * nz + z];
       dkh_off = (long long)kp.size();
       kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
       for (int x = 0; x < nx; x++)
         for (int c = 0; c < 6; c++)
           for (int y = 0; y < ny; y++)
             for (int z = 0; z < nz; z++)
-              kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.R[2] + hz)] =
-                  S.dkh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
+              kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.B[2] + hz)] =
+                  S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
       wb_off = (long long)wp.size();
       wp.insert(wp.end(), S.wball.begin(), S.wball.end());
       wh_off = (long long)wp.size();

@@ -27,6 +27,8 @@ struct SysHost {
   double h1[3];
   int nlev = 0, ncomp = 0;
   int S[3], R[3];
+  int B[3];                          // radius of the ball-kernel stencil: S (raw samples, p = 4) or R (K)
+  bool prefilter = false;            // ball kernels apply raw samples to the omega'-prefiltered grid
   int C[3];
   double edge[3];
   int nnbr[3];
@@ -34,8 +36,9 @@ struct SysHost {
   double jc[9];
   std::vector<LevelHost> lev;
   bool has_ball = false;
-  std::vector<float> kball, dkh;     // level-1 shape stencil (dense (2R+1)^3), half-space virial weights (6x)
-  std::vector<int> wball, whalf;     // column half-widths, -1 = empty column
+  std::vector<double> kball, dk1;    // K^1 and its 6 strain derivatives, dense on [-R, R]^3 (host queries)
+  std::vector<float> sball, dsh;     // raw samples s^1 on [-S, S]^3 and half-space virial weights (6x), ball kernels
+  std::vector<int> wball, whalf;     // column half-widths of sball / dsh, -1 = empty column
 };
 
 int plan_system(const msm_params& P, SysHost& S, std::string* err);
