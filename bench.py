@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--atoms", type=int, default=N_HEADLINE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-atoms", type=int, default=128_000)
+    ap.add_argument("--cpu-sample-atoms", type=int, default=N_HEADLINE)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-systems", type=int, default=512)
     return ap.parse_args()
@@ -69,7 +69,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -153,12 +153,12 @@ def short_flops(n, density, a):
     return n * density * 4.0 / 3.0 * math.pi * a ** 3 * 54.0
 
 
-def stencil_source_sha():
-    p = os.path.join(ROOT, "paper_2510_05961_gb300", "csrc", "k_stencil.cu")
+def source_sha(src):
+    p = os.path.join(ROOT, "paper_2510_05961_gb300", "csrc", src)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def read_traffic(kernel_key):
+def read_traffic(kernel_key, src):
     """DRAM bytes per launch recorded from an ncu capture, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel_key)
     if not os.path.exists(path):
@@ -168,7 +168,7 @@ def read_traffic(kernel_key):
         if ":" in ln and not ln.startswith("#"):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_sha256_16") != stencil_source_sha():
+    if kv.get("source_sha256_16") != source_sha(src):
         return None
     try:
         return float(kv["dram_bytes_per_launch"])
@@ -411,7 +411,8 @@ def run_gpu(args):
     roof = {"bound": "alu", "kernel": {"stencil": "k_stencil_ball (level stencils)",
                                         "short": "k_short (short-range pairs)"}[dom],
             "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
-            "traffic": read_traffic("stencil_ball_1M") if dom == "stencil" else None,
+            "traffic": (read_traffic("stencil_ball_1M", "k_stencil.cu") if dom == "stencil"
+                        else read_traffic("short_1M", "k_short.cu")),
             "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (no FP32 peak in MEASURED_PEAKS.json)",
             "phase_ms": {k: round(v, 4) for k, v in ph_ms.items()},
             "algorithmic_flops": {"stencil": st_flops, "short": sr_flops}}
@@ -424,8 +425,8 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         val, dt, cores = oracle_sample(args.cpu_sample_atoms)
         cpu = {"value": val, "unit": "atoms/s", "cores": cores, "kind": "oracle",
-               "sample": "one oracle fwd+bwd (E, F, dE/dq, virial) on %d atoms of the same workload (same density, "
-                         "p, h, a; h_1 = 1.70 A as at 1M), %.1f s" % (args.cpu_sample_atoms, dt)}
+               "sample": "one oracle fwd+bwd (E, F, dE/dq, virial) of a %d-atom system of the same workload (same "
+                         "density, p, h, a), %.1f s" % (args.cpu_sample_atoms, dt)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
