@@ -60,36 +60,62 @@ __global__ void k_energy(const SysDev* __restrict__ sys, const double* __restric
   }
 }
 
-// one block per system: W = (sum of short-range partials + grid partials) * g
-__global__ void k_virial_out(const SysDev* __restrict__ sys, const double* __restrict__ part_w0,
-                             const double* __restrict__ part_wg, const int* __restrict__ vitem_off,
-                             const double* __restrict__ grad, double* __restrict__ virial) {
-  __shared__ double red[32][6];
-  const SysDev& S = sys[blockIdx.x];
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < S.nitem * kChunkWarps; i += blockDim.x)
-    for (int c = 0; c < 6; c++) acc[c] += part_w0[6 * ((long long)S.item0 * kChunkWarps + i) + c];
-  // grid partials of this system: its ball items, then its box items
-  const int ns = gridDim.x;
-  for (int r = 0; r < 2; r++) {
-    int v0 = vitem_off[r * (ns + 1) + blockIdx.x], v1 = vitem_off[r * (ns + 1) + blockIdx.x + 1];
-    for (int i = v0 + threadIdx.x; i < v1; i += blockDim.x)
-      for (int c = 0; c < 6; c++) acc[c] += part_wg[6 * (long long)i + c];
-  }
+// Virial reduction, stage 1: block (s, b) of a (nsys x kVirialSlices) grid sums
+// slice b of system s's partials (short-range per warp, then grid per tile)
+// in a fixed order; stage 2: one block per system sums its slices and scales
+// by g. Deterministic; the FP64 additions are spread over the whole GPU.
+constexpr int kVirialSlices = 64;
+
+__device__ __forceinline__ void block_sum6(double (&acc)[6], double (*red)[6], double* out) {
   for (int c = 0; c < 6; c++) {
     double v = acc[c];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
   }
   __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += red[k][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_virial_slices(const SysDev* __restrict__ sys,
+                                                       const double* __restrict__ part_w0,
+                                                       const double* __restrict__ part_wg,
+                                                       const int* __restrict__ vitem_off, double* __restrict__ slices) {
+  __shared__ double red[8][6];
+  const int s = blockIdx.x, b = blockIdx.y, ns = gridDim.x;
+  const SysDev& S = sys[s];
+  const int n0 = S.nitem * kChunkWarps;
+  const int nb = vitem_off[s + 1] - vitem_off[s];
+  const int nx = vitem_off[ns + 1 + s + 1] - vitem_off[ns + 1 + s];
+  const int total = n0 + nb + nx;
+  const int per = (total + kVirialSlices - 1) / kVirialSlices;
+  const int lo = b * per, hi = min(total, lo + per);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double* src;
+    if (i < n0) src = part_w0 + 6 * ((long long)S.item0 * kChunkWarps + i);
+    else if (i < n0 + nb) src = part_wg + 6 * (long long)(vitem_off[s] + (i - n0));
+    else src = part_wg + 6 * (long long)(vitem_off[ns + 1 + s] + (i - n0 - nb));
+    for (int c = 0; c < 6; c++) acc[c] += src[c];
+  }
+  block_sum6(acc, red, slices + 6 * ((long long)s * kVirialSlices + b));
+}
+
+__global__ void __launch_bounds__(64) k_virial_out(const double* __restrict__ slices,
+                                                   const double* __restrict__ grad, double* __restrict__ virial) {
+  __shared__ double red[2][6];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double* src = slices + 6 * (long long)blockIdx.x * kVirialSlices;
+  for (int i = threadIdx.x; i < kVirialSlices; i += blockDim.x)
+    for (int c = 0; c < 6; c++) acc[c] += src[6 * i + c];
+  __shared__ double w[6];
+  block_sum6(acc, red, w);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double w[6];
-    for (int c = 0; c < 6; c++) {
-      double s = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) s += red[k][c];
-      w[c] = s;
-    }
-    double g = grad ? grad[blockIdx.x] : 1.0;
+    const double g = grad ? grad[blockIdx.x] : 1.0;
     double* V = virial + 9 * (long long)blockIdx.x;
     V[0] = g * w[0]; V[1] = g * w[3]; V[2] = g * w[4];
     V[3] = g * w[3]; V[4] = g * w[1]; V[5] = g * w[5];
@@ -134,7 +160,8 @@ void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cud
 
 void launch_virial_out(const Work& w, const Tables& t, int nsys, const int* vitem_off, const double* grad,
                        double* virial, cudaStream_t s) {
-  k_virial_out<<<nsys, 256, 0, s>>>(t.sys, w.part_w0, w.part_wg, vitem_off, grad, virial);
+  k_virial_slices<<<dim3(nsys, kVirialSlices), 256, 0, s>>>(t.sys, w.part_w0, w.part_wg, vitem_off, w.part_vs);
+  k_virial_out<<<nsys, 64, 0, s>>>(w.part_vs, grad, virial);
 }
 
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,

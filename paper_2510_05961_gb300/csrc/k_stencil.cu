@@ -27,7 +27,9 @@
 // thread forms its partial C'_(dx,dy,dz) = sum_m q~_m q'_(m-d) for the 2w + 1 dz
 // values and at once contracts it with the six strain-derivative samples
 // (q~^T dK q~ = sum_d ds_d C'_d for dK = omega'^3 * ds; stored with the
-// half-space symmetry C'_d = C'_-d folded in).
+// half-space symmetry C'_d = C'_-d folded in). With raw samples the six
+// factor through one weight column (ds_ab = g v_a v_b, v = h o d), so the
+// contraction takes three dz moments of g C' per column.
 //
 // Box levels (small periodic levels whose stencil wraps onto itself, folded
 // onto the grid, and the top level of open systems): one warp per output, the
@@ -164,6 +166,46 @@ __device__ __forceinline__ void virial_column(float (&w6)[6], const float (&qown
   }
 }
 
+// p = 4 (raw samples): ds_ab(n) = g(n) (h_1 o n)_a (h_1 o n)_b, so one weight
+// column g replaces the six and the contraction needs only the moments
+// sum g C', sum g C' dz, sum g C' dz^2 of the column. cx = h_x dx, cy = h_y dy;
+// w6[2], w6[4], w6[5] collect the dz moments without their h_z factors.
+template <int W>
+__device__ __forceinline__ void virial_column_fact(float (&w6)[6], const float (&qown)[BZ],
+                                                   const float* __restrict__ qrow, const float* __restrict__ gd,
+                                                   float cx, float cy) {
+  constexpr int A = (W + 3) & ~3;
+  constexpr int NQ = BZ + 2 * A;
+  float qv[NQ], gv[2 * A + 4];
+#pragma unroll
+  for (int t = 0; t < NQ; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(qrow - A + t);
+    qv[t] = v.x; qv[t + 1] = v.y; qv[t + 2] = v.z; qv[t + 3] = v.w;
+  }
+#pragma unroll
+  for (int t = 0; t < 2 * A + 1; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(gd - A + t);
+    gv[t] = v.x; gv[t + 1] = v.y; gv[t + 2] = v.z; gv[t + 3] = v.w;
+  }
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int dz = -W; dz <= W; dz++) {
+    float c = 0.f;
+#pragma unroll
+    for (int o = 0; o < BZ; o++) c = fmaf(qown[o], qv[o - dz + A], c);
+    const float t = gv[dz + A] * c;
+    s0 += t;
+    s1 = fmaf(t, (float)dz, s1);
+    s2 = fmaf(t, (float)(dz * dz), s2);
+  }
+  w6[0] = fmaf(cx * cx, s0, w6[0]);
+  w6[1] = fmaf(cy * cy, s0, w6[1]);
+  w6[2] += s2;
+  w6[3] = fmaf(cx * cy, s0, w6[3]);
+  w6[4] = fmaf(cx, s1, w6[4]);
+  w6[5] = fmaf(cy, s1, w6[5]);
+}
+
 // dispatch on the (even) column half-width w
 template <int W, int WMAX>
 struct Col {
@@ -180,6 +222,13 @@ struct Col {
     else
       Col<W + 2, WMAX>::virial(w, w6, qown, q, k, ks);
   }
+  static __device__ __forceinline__ void virial_fact(int w, float (&w6)[6], const float (&qown)[BZ], const float* q,
+                                                     const float* g, float cx, float cy) {
+    if (w == W)
+      virial_column_fact<W>(w6, qown, q, g, cx, cy);
+    else
+      Col<W + 2, WMAX>::virial_fact(w, w6, qown, q, g, cx, cy);
+  }
 };
 template <int WMAX>
 struct Col<WMAX, WMAX> {
@@ -189,6 +238,10 @@ struct Col<WMAX, WMAX> {
   static __device__ __forceinline__ void virial(int, float (&w6)[6], const float (&qown)[BZ], const float* q,
                                                 const float* k, int ks) {
     virial_column<WMAX>(w6, qown, q, k, ks);
+  }
+  static __device__ __forceinline__ void virial_fact(int, float (&w6)[6], const float (&qown)[BZ], const float* q,
+                                                     const float* g, float cx, float cy) {
+    virial_column_fact<WMAX>(w6, qown, q, g, cx, cy);
   }
 };
 
@@ -260,8 +313,8 @@ __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ 
   }
 }
 
-template <int WMAX>
-__global__ void __launch_bounds__(NT) k_virial_ball(const LevDev* __restrict__ levs,
+template <int WMAX, bool FACT>
+__global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                     const TileItem* __restrict__ items,
                                                     const float* __restrict__ kpool, const int* __restrict__ wpool,
                                                     const float* __restrict__ grid, double* __restrict__ part,
@@ -276,6 +329,14 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const LevDev* __restrict__ l
   const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
   const int ty = threadIdx.x % TY, zb = threadIdx.x / TY;
   const int kstride = (2 * Ry + 1) * SK;
+  constexpr int NK = FACT ? 1 : 6;
+  float hx = 0.f, hy = 0.f, hzs = 0.f;
+  if (FACT) {
+    const SysDev& S = sys[L.sys];
+    hx = S.h1f[0];
+    hy = S.h1f[1];
+    hzs = S.h1f[2];
+  }
   float qown[BZ];  // raw q~ at this thread's points (the window below reads the prefiltered q')
   {
     const int y = it.y0 + ty, z0 = it.z0 + zb * BZ;
@@ -285,24 +346,33 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const LevDev* __restrict__ l
   }
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int nsteps = 2 * Rx + 1;
-  stage_ball(L, it, 0, grid, kpool, L.dk_off, 6, wpool, L.wh_off, planes, kslabs, wsl, stride);
+  stage_ball(L, it, 0, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes, kslabs, wsl, stride);
   for (int step = 0; step < nsteps; step++) {
     cp_async_wait_all();
     __syncthreads();
     const int b = step & 1;
     if (step + 1 < nsteps)
-      stage_ball(L, it, step + 1, grid, kpool, L.dk_off, 6, wpool, L.wh_off, planes + (b ^ 1) * plane_sz,
+      stage_ball(L, it, step + 1, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes + (b ^ 1) * plane_sz,
                  kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax, stride);
     const float* plane = planes + b * plane_sz;
     const float* kslab = kslabs + b * kslab_sz;
     const int* wc = wsl + b * kWslMax;
+    const float cx = hx * (float)(step - Rx);
     for (int dy = -Ry; dy <= Ry; dy++) {
       const int w = wc[dy + Ry];
       if (w < 0) continue;
       const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz;
       const float* kd = kslab + (dy + Ry) * SK + hz;
-      Col<0, WMAX>::virial(w, w6, qown, qrow, kd, kstride);
+      if (FACT)
+        Col<0, WMAX>::virial_fact(w, w6, qown, qrow, kd, cx, hy * (float)dy);
+      else
+        Col<0, WMAX>::virial(w, w6, qown, qrow, kd, kstride);
     }
+  }
+  if (FACT) {
+    w6[2] *= hzs * hzs;
+    w6[4] *= hzs;
+    w6[5] *= hzs;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -447,18 +517,28 @@ static void run_ball(const Work& w, const Tables& t, const TileItem* items, int 
                                                  kslab_sz);
 }
 
-template <int WMAX>
+template <int WMAX, bool FACT>
 static void run_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int ryz_max[2],
                             int part_off, cudaStream_t s) {
   int stride, plane_sz, kslab_sz;
   size_t bytes;
-  ball_smem(ryz_max, 6, stride, plane_sz, kslab_sz, bytes);
+  ball_smem(ryz_max, FACT ? 1 : 6, stride, plane_sz, kslab_sz, bytes);
   static size_t attr = 0;
-  if (bytes > attr && cudaFuncSetAttribute(k_virial_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (bytes > attr && cudaFuncSetAttribute(k_virial_ball<WMAX, FACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)bytes) == cudaSuccess)
     attr = bytes;
-  k_virial_ball<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid,
-                                                w.part_wg + 6 * (long long)part_off, stride, plane_sz, kslab_sz);
+  k_virial_ball<WMAX, FACT><<<nitems, NT, bytes, s>>>(t.sys, t.lev, items, t.kpool, t.wpool, w.grid,
+                                                      w.part_wg + 6 * (long long)part_off, stride, plane_sz,
+                                                      kslab_sz);
+}
+
+template <bool FACT>
+static void dispatch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
+                                 int ryz_max[2], int part_off, cudaStream_t s) {
+  if (rmax <= 8) run_virial_ball<8, FACT>(w, t, items, nitems, ryz_max, part_off, s);
+  else if (rmax <= 12) run_virial_ball<12, FACT>(w, t, items, nitems, ryz_max, part_off, s);
+  else if (rmax <= 16) run_virial_ball<16, FACT>(w, t, items, nitems, ryz_max, part_off, s);
+  else run_virial_ball<24, FACT>(w, t, items, nitems, ryz_max, part_off, s);
 }
 
 void launch_pad(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {
@@ -476,13 +556,13 @@ void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, 
   else run_ball<24>(w, t, items, nitems, ryz_max, s);
 }
 
+// factorized: the ball tables hold raw samples (p = 4) with the one-column
+// virial weights g
 void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
-                        int ryz_max[2], int part_off, cudaStream_t s) {
+                        int ryz_max[2], int part_off, bool factorized, cudaStream_t s) {
   if (nitems <= 0) return;
-  if (rmax <= 8) run_virial_ball<8>(w, t, items, nitems, ryz_max, part_off, s);
-  else if (rmax <= 12) run_virial_ball<12>(w, t, items, nitems, ryz_max, part_off, s);
-  else if (rmax <= 16) run_virial_ball<16>(w, t, items, nitems, ryz_max, part_off, s);
-  else run_virial_ball<24>(w, t, items, nitems, ryz_max, part_off, s);
+  if (factorized) dispatch_virial_ball<true>(w, t, items, nitems, rmax, ryz_max, part_off, s);
+  else dispatch_virial_ball<false>(w, t, items, nitems, rmax, ryz_max, part_off, s);
 }
 
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {

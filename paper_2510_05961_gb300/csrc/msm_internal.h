@@ -45,6 +45,7 @@ struct SysDev {
   float Mf[3];      // M as float
   float inv_h1[3];  // 1/h_1 per axis
   float Lf[3];      // cell lengths
+  float h1f[3];     // level-1 spacings
   float a2, inv_a, inv_a2, inv_a3;
   float self_coef;  // gamma(0)/a (self term of Eq. U_zero)
   float gca[8];     // softening polynomial over a, in s = 1 - (r/a)^2: gamma(r/a)/a = sum_k gca[k] s^k
@@ -100,6 +101,7 @@ struct Work {
   double* part_e;  // per atom item: 1/2 sum q phi
   double* part_w0; // per warp of each atom item: 6 short-range virial components
   double* part_wg; // per virial item: 6 grid virial components
+  double* part_vs; // per system and reduction slice: 6 virial components
   float* grid;     // grid pool
 };
 
@@ -131,7 +133,7 @@ void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, 
                          int ryz_max[2], cudaStream_t s);
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);
 void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
-                        int ryz_max[2], int part_off, cudaStream_t s);
+                        int ryz_max[2], int part_off, bool factorized, cudaStream_t s);
 void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, int part_off,
                        cudaStream_t s);
 // outputs (k_final.cu)

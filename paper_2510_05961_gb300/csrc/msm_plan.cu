@@ -378,6 +378,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
     S.sball.assign(s1.v.begin(), s1.v.end());
     S.dsh.assign((size_t)6 * nx * ny * nz, 0.0f);
+    S.fsh.assign(S.prefilter ? (size_t)nx * ny * nz : 0, 0.0f);
     // column half-widths, rounded up to even values (the stored rows are zero
     // beyond the support): half as many unrolled column variants
     S.wball.assign((size_t)nx * ny, -1);
@@ -397,6 +398,14 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
             float v = (float)(f * ds1[c].v[at]);
             S.dsh[(size_t)c * nx * ny * nz + at] = v;
             if (v != 0.0f) any = true;
+          }
+          if (S.prefilter) {
+            // raw samples factor: ds_ab(n) = g(n) v_a v_b with g = k_1'(|v|)/|v|, v = h_1 o n
+            const double vx = S.h1[0] * x, vy = S.h1[1] * y, vz = S.h1[2] * z;
+            const double rr = std::sqrt(vx * vx + vy * vy + vz * vz);
+            const float g = rr > 0.0 ? (float)(f * klev(S, 1, rr, true) / rr) : 0.0f;
+            S.fsh[at] = g;
+            any = g != 0.0f;
           }
           if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z) + (std::abs(z) & 1));
         }
@@ -455,6 +464,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       D.Mf[d] = (float)S.M[d];
       D.inv_h1[d] = (float)(1.0 / S.h1[d]);
       D.Lf[d] = (float)S.L[d];
+      D.h1f[d] = (float)S.h1[d];
     }
     D.a2 = (float)(S.a * S.a);
     D.inv_a = (float)(1.0 / S.a);
@@ -536,13 +546,22 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
           for (int z = 0; z < nz; z++)
             kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.sball[((size_t)x * ny + y) * nz + z];
       dkh_off = (long long)kp.size();
-      kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
-      for (int x = 0; x < nx; x++)
-        for (int c = 0; c < 6; c++)
+      if (S.prefilter) {
+        // factorized virial weights g(n), one array [dx][dy][row]
+        kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
+        for (int x = 0; x < nx; x++)
           for (int y = 0; y < ny; y++)
             for (int z = 0; z < nz; z++)
-              kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.B[2] + hz)] =
-                  S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
+              kp[dkh_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.fsh[((size_t)x * ny + y) * nz + z];
+      } else {
+        kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
+        for (int x = 0; x < nx; x++)
+          for (int c = 0; c < 6; c++)
+            for (int y = 0; y < ny; y++)
+              for (int z = 0; z < nz; z++)
+                kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.B[2] + hz)] =
+                    S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
+      }
       wb_off = (long long)wp.size();
       wp.insert(wp.end(), S.wball.begin(), S.wball.end());
       wh_off = (long long)wp.size();
@@ -659,6 +678,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_part_e = take(sizeof(double) * atom_items.size());
   L_part_w0 = take(sizeof(double) * 6 * kChunkWarps * atom_items.size());
   L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(ball_items.size() + box_items.size(), 1));
+  L_part_vs = take(sizeof(double) * 6 * 64 * (size_t)nsys);
   L_grid = take(sizeof(float) * std::max<long long>(grid_floats, 1));
   ws_bytes = off;
   return MSM_OK;
@@ -740,6 +760,7 @@ Work Engine::resolve(void* ws) const {
   w.part_e = (double*)(b + L_part_e);
   w.part_w0 = (double*)(b + L_part_w0);
   w.part_wg = (double*)(b + L_part_wg);
+  w.part_vs = (double*)(b + L_part_vs);
   w.grid = (float*)(b + L_grid);
   return w;
 }

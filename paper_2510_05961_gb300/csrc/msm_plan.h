@@ -37,7 +37,8 @@ struct SysHost {
   std::vector<LevelHost> lev;
   bool has_ball = false;
   std::vector<double> kball, dk1;    // K^1 and its 6 strain derivatives, dense on [-R, R]^3 (host queries)
-  std::vector<float> sball, dsh;     // raw samples s^1 on [-S, S]^3 and half-space virial weights (6x), ball kernels
+  std::vector<float> sball, dsh;     // ball-kernel stencil on [-B, B]^3 and half-space virial weights (6x)
+  std::vector<float> fsh;            // p = 4: factorized half-space virial weights g = k_1'(|v|)/|v|
   std::vector<int> wball, whalf;     // column half-widths of sball / dsh, -1 = empty column
 };
 
@@ -77,7 +78,7 @@ struct Engine {
   int* d_voff = nullptr;
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
-      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_w0, L_part_wg, L_grid;
+      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_w0, L_part_wg, L_part_vs, L_grid;
   size_t ws_bytes = 0;
   // state of the last forward pass
   bool have_fwd = false;
