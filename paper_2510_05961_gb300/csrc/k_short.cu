@@ -1,6 +1,6 @@
 // k_short.cu -- short-range part U^0 of the MSM (Eq. U_zero) over the cell
 // list: for every sorted atom i, every atom j and every periodic image with
-// |d| < a, (j, image) != (i, 0):
+// 0 < |d| < a,
 //   phi0_i += q_j k_0(|d|),  k_0(r) = 1/r - gamma(r/a)/a   (Sec. 3.4),
 //   F0_i   += q_i q_j k_0'(r) d / r,
 //   W0     += -1/2 q_i q_j k_0'(r) d d^T / r,
@@ -13,10 +13,15 @@
 // periodic image along z. Sorted positions keep x, y relative to the cell
 // corner and z relative to the column base, so the displacement to a
 // candidate is (ox * edge_x + x_j - x_i, oy * edge_y + y_j - y_i,
-// z_j + kz * L_z - z_i) with no wrap arithmetic per pair. Small periodic
-// cells visit the same cells at several offsets: every image within the
-// cutoff counts, self images included. One thread per sorted atom; each
-// thread sums its own pairs, so the result does not depend on scheduling.
+// z_j + kz * L_z - z_i) with no wrap arithmetic per pair. The self pair
+// gives exactly d = 0 and every other image of i lies a period away, so the
+// pair test 0 < r^2 < a^2 excludes exactly (j, image) = (i, 0) (distinct
+// atoms at one point have infinite Coulomb energy and are outside the
+// method's domain). Small periodic cells visit the same cells at several
+// offsets: every image within the cutoff counts. One thread per sorted atom;
+// each thread sums its own pairs, so the result does not depend on
+// scheduling. Whether forces and the virial are wanted are template
+// parameters, so the pair loop carries no runtime flags.
 #include "msm_internal.h"
 
 namespace msm {
@@ -26,12 +31,11 @@ __device__ __forceinline__ int floordiv_s(int a, int b) {
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
-template <int P>
+template <int P, bool WF, bool WW>
 __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                                                   const int* __restrict__ cell_start, const int* __restrict__ scell,
                                                   const float4* __restrict__ xq, float* __restrict__ phi_sr,
-                                                  float4* __restrict__ f_sr, double* __restrict__ part_w0,
-                                                  int want_f, int want_w) {
+                                                  float4* __restrict__ f_sr, double* __restrict__ part_w0) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   int local = it.start + threadIdx.x;
@@ -48,8 +52,8 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
     for (int t = 0; t < P; t++) gc[t] = S.gca[t];
 #pragma unroll
     for (int t = 0; t < P - 1; t++) gdc[t] = S.gdca[t];
-    const float a2 = S.a2, inv_a2 = S.inv_a2;
-    const float ex = S.edge[0], ey = S.edge[1], ez = S.edge[2], inv_ez = 1.0f / ez;
+    const float a2 = S.a2, inv_a2 = S.inv_a2, Lz = S.Lf[2];
+    const float ex = S.edge[0], ey = S.edge[1], inv_ez = 1.0f / S.edge[2];
     float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
       const int ux = ci[0] + ox;
@@ -72,57 +76,55 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
           zhi = min(zhi, Cz - 1);
         }
         const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
-        const bool home_xy = (ox | oy) == 0;
         int uz = zlo;
         while (uz <= zhi) {
           const int kz = floordiv_s(uz, Cz);
           const int wz = uz - kz * Cz;
           const int wend = min(Cz - 1, wz + (zhi - uz));
           const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
-          const float bz = (float)kz * S.Lf[2] - xi.z;
-          const bool home = home_xy && kz == 0;
+          const float bz = (float)kz * Lz - xi.z;
           for (int j = jb; j < je; j++) {
             const float4 xj = xq[j];
             const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < a2 && !(home && j == k)) {
-              const float rinv = rsqrtf(r2);
-              const float s = 1.0f - r2 * inv_a2;
-              float g = gc[P - 1];
+          if (r2 < a2 && r2 > 0.f) {
+            const float rinv = rsqrtf(r2);
+            const float s = 1.0f - r2 * inv_a2;
+            float g = gc[P - 1];
 #pragma unroll
-              for (int t = P - 2; t >= 0; t--) g = fmaf(g, s, gc[t]);
+            for (int t = P - 2; t >= 0; t--) g = fmaf(g, s, gc[t]);
+            ph = fmaf(xj.w, rinv - g, ph);  // k_0 = 1/r - gamma(r/a)/a
+            if (WF || WW) {
               float dg = gdc[P - 2];
 #pragma unroll
               for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, s, gdc[t]);
-              ph = fmaf(xj.w, rinv - g, ph);  // k_0 = 1/r - gamma(r/a)/a
-              if (want_f | want_w) {
-                // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
-                const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
-                const float frx = fr * dx, fry = fr * dy, frz = fr * dz;
-                fx += frx;
-                fy += fry;
-                fz += frz;
-                if (want_w) {
-                  w6[0] = fmaf(frx, dx, w6[0]);
-                  w6[1] = fmaf(fry, dy, w6[1]);
-                  w6[2] = fmaf(frz, dz, w6[2]);
-                  w6[3] = fmaf(frx, dy, w6[3]);
-                  w6[4] = fmaf(frx, dz, w6[4]);
-                  w6[5] = fmaf(fry, dz, w6[5]);
-                }
+              // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
+              const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
+              const float frx = fr * dx, fry = fr * dy, frz = fr * dz;
+              fx += frx;
+              fy += fry;
+              fz += frz;
+              if (WW) {
+                w6[0] = fmaf(frx, dx, w6[0]);
+                w6[1] = fmaf(fry, dy, w6[1]);
+                w6[2] = fmaf(frz, dz, w6[2]);
+                w6[3] = fmaf(frx, dy, w6[3]);
+                w6[4] = fmaf(frx, dz, w6[4]);
+                w6[5] = fmaf(fry, dz, w6[5]);
               }
             }
           }
+        }
           uz += wend - wz + 1;
         }
       }
     }
     phi_sr[k] = ph - xi.w * S.self_coef;
-    if (want_f) f_sr[k] = make_float4(xi.w * fx, xi.w * fy, xi.w * fz, 0.f);
+    if (WF) f_sr[k] = make_float4(xi.w * fx, xi.w * fy, xi.w * fz, 0.f);
 #pragma unroll
     for (int c = 0; c < 6; c++) w6[c] *= -0.5f * xi.w;
   }
-  if (!want_w) return;
+  if (!WW) return;
   // per-warp FP64 partials of the six virial components (fixed order, no block barrier)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -133,21 +135,20 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
   }
 }
 
+template <int P>
+static void run_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
+                      cudaStream_t s) {
+  auto kern = virial ? (forces ? k_short<P, true, true> : k_short<P, false, true>)
+                     : (forces ? k_short<P, true, false> : k_short<P, false, false>);
+  kern<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0);
+}
+
 void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                   cudaStream_t s, int p) {
   switch (p) {
-    case 4:
-      k_short<4><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0,
-                                           forces, virial);
-      break;
-    case 6:
-      k_short<6><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0,
-                                           forces, virial);
-      break;
-    default:
-      k_short<8><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0,
-                                           forces, virial);
-      break;
+    case 4: run_short<4>(w, t, items, nitems, forces, virial, s); break;
+    case 6: run_short<6>(w, t, items, nitems, forces, virial, s); break;
+    default: run_short<8>(w, t, items, nitems, forces, virial, s); break;
   }
 }
 
