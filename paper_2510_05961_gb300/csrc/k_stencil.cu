@@ -73,38 +73,77 @@ __device__ __forceinline__ int pad_axis(int c, int n, int per) {
   return (c >= 0 && c < n) ? c : -1;
 }
 
-__global__ void __launch_bounds__(kGridChunk) k_pad(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
-                                                    const RangeItem* __restrict__ items, float* __restrict__ grid) {
-  RangeItem it = items[blockIdx.x];
-  if ((int)threadIdx.x >= it.count) return;
+// One block per tile of kPadTX x-planes x kPadTY rows x kPadTZ columns of
+// the padded grid, one thread per (row, column). The block walks the source
+// x-planes the tile needs: it stages the plane's (rows +- r) x (columns +- r)
+// patch in shared memory (wrapped or zero source indices, fixed per tile),
+// applies the (2r+1)^2 y-z taps, and keeps the last 2r+1 filtered planes in
+// registers for the x taps. r = 0 (no prefilter) makes it a halo copy.
+template <int PR>
+__global__ void __launch_bounds__(kPadTY * kPadTZ) k_pad(const SysDev* __restrict__ sys,
+                                                         const LevDev* __restrict__ levs,
+                                                         const TileItem* __restrict__ items, float* __restrict__ grid) {
+  constexpr int NT = kPadTY * kPadTZ;
+  constexpr int PW = kPadTZ + 2 * PR;
+  constexpr int NE = (kPadTY + 2 * PR) * PW;
+  constexpr int NL = (NE + NT - 1) / NT;
+  __shared__ float patch[NE];
+  const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const SysDev& S = sys[L.sys];
-  const int r = S.pre_r;
-  const int idx = it.start + threadIdx.x;
-  const int pz = idx % L.pn[2], py = (idx / L.pn[2]) % L.pn[1], px = idx / (L.pn[2] * L.pn[1]);
-  const int c[3] = {px - L.R[0], py - L.R[1], pz - L.hz};
-  // wrapped source index of each tap, once per axis
-  int ix[7], iy[7], iz[7];
-  for (int t = -r; t <= r; t++) {
-    ix[t + r] = pad_axis(c[0] - t, L.n[0], L.per[0]);
-    iy[t + r] = pad_axis(c[1] - t, L.n[1], L.per[1]);
-    iz[t + r] = pad_axis(c[2] - t, L.n[2], L.per[2]);
-  }
-  const float* q = grid + L.q_off;
-  float acc = 0.f;
-  for (int tx = 0; tx <= 2 * r; tx++) {
-    if (ix[tx] < 0) continue;
-    const float wx = S.om[tx < r ? r - tx : tx - r];
-    for (int ty = 0; ty <= 2 * r; ty++) {
-      if (iy[ty] < 0) continue;
-      const float* row = q + ((long long)ix[tx] * L.n[1] + iy[ty]) * L.n[2];
-      float az = 0.f;
-      for (int tz = 0; tz <= 2 * r; tz++)
-        if (iz[tz] >= 0) az = fmaf(S.om[tz < r ? r - tz : tz - r], __ldg(row + iz[tz]), az);
-      acc = fmaf(wx * S.om[ty < r ? r - ty : ty - r], az, acc);
+  const int tz = threadIdx.x % kPadTZ, ty = threadIdx.x / kPadTZ;
+  const int py = it.y0 + ty, pz = it.z0 + tz;
+  const bool own = py < L.pn[1] && pz < L.pn[2];
+  float om[PR + 1];
+#pragma unroll
+  for (int k = 0; k <= PR; k++) om[k] = S.om[k];
+  // in-plane source offset of each patch element this thread stages (-1: zero)
+  int soff[NL];
+#pragma unroll
+  for (int u = 0; u < NL; u++) {
+    const int e = threadIdx.x + u * NT;
+    soff[u] = -1;
+    if (e < NE) {
+      const int sy = pad_axis(it.y0 + e / PW - PR - L.R[1], L.n[1], L.per[1]);
+      const int sz = pad_axis(it.z0 + e % PW - PR - L.hz, L.n[2], L.per[2]);
+      if (sy >= 0 && sz >= 0) soff[u] = sy * L.n[2] + sz;
     }
   }
-  grid[L.p_off + idx] = acc;
+  const float* q = grid + L.q_off;
+  const long long plane = (long long)L.n[1] * L.n[2];
+  float g[2 * PR + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * PR; k++) g[k] = 0.f;
+  const int xend = min(it.x0 + kPadTX, L.pn[0]);
+  // source plane xs feeds outputs px = xs + Rx - PR .. xs + Rx + PR
+  for (int xs = it.x0 - L.R[0] - PR, step = 0; xs <= xend - 1 - L.R[0] + PR; xs++, step++) {
+    const int sx = pad_axis(xs, L.n[0], L.per[0]);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NL; u++) {
+      const int e = threadIdx.x + u * NT;
+      if (e < NE) patch[e] = (sx >= 0 && soff[u] >= 0) ? __ldg(q + sx * plane + soff[u]) : 0.f;
+    }
+    __syncthreads();
+    float v = 0.f;
+#pragma unroll
+    for (int a = 0; a <= 2 * PR; a++) {
+      float row = 0.f;
+#pragma unroll
+      for (int b = 0; b <= 2 * PR; b++) row = fmaf(om[b < PR ? PR - b : b - PR], patch[(ty + a) * PW + tz + b], row);
+      v = fmaf(om[a < PR ? PR - a : a - PR], row, v);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * PR; k++) g[k] = g[k + 1];
+    g[2 * PR] = v;
+    if (step >= 2 * PR && own) {
+      float o = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * PR; k++) o = fmaf(om[k < PR ? PR - k : k - PR], g[k], o);
+      const int px = xs + L.R[0] - PR;
+      grid[L.p_off + ((long long)px * L.pn[1] + py) * L.pn[2] + pz] = o;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ columns
@@ -541,9 +580,10 @@ static void dispatch_virial_ball(const Work& w, const Tables& t, const TileItem*
   else run_virial_ball<24, FACT>(w, t, items, nitems, ryz_max, part_off, s);
 }
 
-void launch_pad(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {
+void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitems, int pre_r, cudaStream_t s) {
   if (nitems <= 0) return;
-  k_pad<<<nitems, kGridChunk, 0, s>>>(t.sys, t.lev, items, w.grid);
+  if (pre_r == 1) k_pad<1><<<nitems, kPadTY * kPadTZ, 0, s>>>(t.sys, t.lev, items, w.grid);
+  else k_pad<0><<<nitems, kPadTY * kPadTZ, 0, s>>>(t.sys, t.lev, items, w.grid);
 }
 
 // ryz_max = {largest R_y, largest halo hz} over the ball levels; rmax = largest R_z

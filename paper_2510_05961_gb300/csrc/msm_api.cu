@@ -95,7 +95,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   }
   {
     Phase ph(E, MSM_PH_STENCIL, s);
-    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), s);
+    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
     launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, s);
     launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
   }

@@ -22,7 +22,8 @@ constexpr int kBallTZ = 32;        // stencil tile depth (z)
 constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
 constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
-constexpr int kGridChunk = 256;    // points per restriction/prolongation item
+constexpr int kGridChunk = 256;
+constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)    // points per restriction/prolongation item
 
 // device status bits (mirrors MSM_DEV_* of the public header)
 constexpr int kDevOutOfCell = 1;
@@ -128,7 +129,7 @@ void launch_interp(const Work& w, const Tables& t, const AtomItem* items, int ni
 void launch_restrict(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
 void launch_prolong(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
 // stencils and grid virial (k_stencil.cu)
-void launch_pad(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);
+void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitems, int pre_r, cudaStream_t s);
 void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
                          int ryz_max[2], cudaStream_t s);
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);

@@ -614,9 +614,9 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
         rmax = std::max(rmax, L.R[2] + (L.R[2] & 1));  // column half-widths are even
         ryz[0] = std::max(ryz[0], L.R[1]);
         ryz[1] = std::max(ryz[1], L.hz);
-        long long npad = (long long)L.pn[0] * L.pn[1] * L.pn[2];
-        for (long long st = 0; st < npad; st += kGridChunk)
-          pad_items.push_back({li, (int)st, (int)std::min<long long>(kGridChunk, npad - st)});
+        for (int x = 0; x < L.pn[0]; x += kPadTX)
+          for (int y = 0; y < L.pn[1]; y += kPadTY)
+            for (int z = 0; z < L.pn[2]; z += kPadTZ) pad_items.push_back({li, x, y, z});
       } else {
         long long npts = (long long)L.n[0] * L.n[1] * L.n[2];
         for (long long st = 0; st < npts; st += kBoxChunk)

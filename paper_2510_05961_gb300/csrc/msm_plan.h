@@ -60,7 +60,8 @@ struct Engine {
   std::vector<LevDev> hlev;
   std::vector<AtomItem> atom_items;
   std::vector<TileItem> anterp_items, ball_items;
-  std::vector<RangeItem> box_items, pad_items;
+  std::vector<RangeItem> box_items;
+  std::vector<TileItem> pad_items;
   std::vector<std::vector<RangeItem>> restrict_steps, prolong_steps;
   std::vector<int> restrict_off, prolong_off;
   std::vector<int> vb_off, vx_off;
@@ -73,7 +74,7 @@ struct Engine {
   TileItem* d_anterp_items = nullptr;
   TileItem* d_ball_items = nullptr;
   RangeItem* d_box_items = nullptr;
-  RangeItem* d_pad_items = nullptr;
+  TileItem* d_pad_items = nullptr;
   RangeItem* d_range_items = nullptr;
   int* d_voff = nullptr;
   // workspace layout (byte offsets)
