@@ -7,10 +7,10 @@
 // centred cardinal B-splines of order p (Sec. 3.3), evaluated in FP32 by the
 // uniform Cox-de Boor recursion on the fractional grid coordinate.
 //
-// Anterpolation is tile-owned: each block owns an 8^3 tile of the level-1
-// grid, gathers the atoms of the cells whose B-spline support reaches the
-// tile, and each thread sums one z-column of the tile over those atoms in a
-// fixed order. No global atomics; the result is the same on every run.
+// Anterpolation reads the cell-sorted atoms: each thread owns one level-1 grid
+// column of a tile and sums, in a fixed order, the atoms of the cells whose
+// B-spline support reaches it. No atomics; the result is the same on every
+// run.
 #include "msm_internal.h"
 
 namespace msm {
@@ -58,138 +58,121 @@ __device__ __forceinline__ void bspline_weights(float f, float (&w)[P], float (&
   }
 }
 
+// Centred B-spline Phi_P(t): zero for |t| >= P/2; on |t| in [i, i+1) the
+// polynomial S.bsp[i][.] (ascending powers) of the local variable |t| - i.
 template <int P>
-__global__ void __launch_bounds__(64) k_anterp(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
-                                               const TileItem* __restrict__ items,
-                                               const int* __restrict__ cell_start, const float4* __restrict__ uq,
-                                               float* __restrict__ grid) {
-  constexpr int T = kAnterpT;
-  constexpr int CAP = 128;
+__device__ __forceinline__ float bspline_value(float t, const float (&cf)[P / 2][P]) {
+  const float a = fabsf(t);
+  const int i = (int)a;
+  float w = 0.f;
+#pragma unroll
+  for (int piece = 0; piece < P / 2; piece++) {
+    const float s = a - (float)piece;
+    float v = cf[piece][P - 1];
+#pragma unroll
+    for (int k = P - 2; k >= 0; k--) v = fmaf(v, s, cf[piece][k]);
+    w = (i == piece) ? v : w;
+  }
+  return w;
+}
+
+// Anterpolation by grid columns. A block owns a tile of 16 x 8 grid columns
+// (x, y) and kAnterpTZ points along z; each thread owns one column and sums,
+// over the atoms of the cells whose B-spline support reaches that column,
+// q_i Phi(m_x - u_x) Phi(m_y - u_y) times the p weights of the atom's z-base
+// into a private z-array in shared memory (u: atom position in level-1 grid
+// units, shifted by the period for cells visited across a periodic
+// boundary). Warp w holds the columns of one parity class (x mod 2, y mod 2),
+// so its lanes visit the same number of cell columns; each lane keeps four
+// atom loads in flight. No atomics, no block barriers; every column sums its
+// atoms in a fixed order.
+constexpr int kAntNT = kAnterpTX * kAnterpTY;
+static_assert(kAnterpTX == 16 && kAnterpTY == 8, "one parity class of 8 x 4 columns per warp");
+
+template <int P>
+__global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
+                                                  const TileItem* __restrict__ items,
+                                                  const int* __restrict__ cell_start,
+                                                  const float4* __restrict__ uq, float* __restrict__ grid) {
   constexpr int H = P / 2;
-  __shared__ float sw[CAP][3 * T];
-  __shared__ int s_wtot[2];
+  constexpr int PAD = P - 1;
+  constexpr int NZ = kAnterpTZ + 2 * PAD;
+  __shared__ float col[NZ][kAntNT];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const SysDev& S = sys[L.sys];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tx = tid / T, ty = tid % T;
-  int st0[3] = {it.x0, it.y0, it.z0};
-  int m0[3], m1[3], cl[3], ch[3];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int gx = it.x0 + 2 * (lane & 7) + (warp & 1), gy = it.y0 + 2 * (lane >> 3) + (warp >> 1);
+  if (gx >= L.n[0] || gy >= L.n[1]) return;
+#pragma unroll
+  for (int r = 0; r < NZ; r++) col[r][t] = 0.f;
+  float cf[H][P];
+#pragma unroll
+  for (int i = 0; i < H; i++)
+#pragma unroll
+    for (int k = 0; k < P; k++) cf[i][k] = S.bsp[i][k];
+  const int zlen = min(kAnterpTZ, L.n[2] - it.z0);
+  // grid indices of this column and of the tile's z-range; atom cell ranges
+  const int m[3] = {gx + L.lo[0], gy + L.lo[1], it.z0 + L.lo[2]};
+  const int mhi[3] = {m[0], m[1], m[2] + zlen - 1};
+  int cl[3], ch[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    int e = st0[d] + T;
-    if (e > L.n[d]) e = L.n[d];
-    m0[d] = st0[d] + L.lo[d];
-    m1[d] = e - 1 + L.lo[d];
     if (S.pbc[d] && S.M[d] % S.C[d] == 0) {
-      // cells aligned with the grid (k intervals per cell, powers of two): the
-      // cell of an atom is floor(u / k) exactly, so the range is exact
+      // cells aligned with the grid (k intervals per cell): the cell of an
+      // atom is floor(u / k) exactly, so the range is exact
       const int k = S.M[d] / S.C[d];
-      cl[d] = floordiv_i(m0[d] - H, k);
-      ch[d] = floordiv_i(m1[d] + H - 1, k);
+      cl[d] = floordiv_i(m[d] - H, k);
+      ch[d] = floordiv_i(mhi[d] + H - 1, k);
     } else {
-      cl[d] = floordiv_i((m0[d] - H) * S.C[d], S.M[d]) - 1;
-      ch[d] = floordiv_i((m1[d] + H) * S.C[d], S.M[d]) + 1;
+      cl[d] = floordiv_i((m[d] - H) * S.C[d], S.M[d]) - 1;
+      ch[d] = floordiv_i((mhi[d] + H) * S.C[d], S.M[d]) + 1;
     }
     if (!S.pbc[d]) {
-      if (cl[d] < 0) cl[d] = 0;
-      if (ch[d] > S.C[d] - 1) ch[d] = S.C[d] - 1;
+      cl[d] = max(cl[d], 0);
+      ch[d] = min(ch[d], S.C[d] - 1);
     }
   }
-  float acc[T];
-#pragma unroll
-  for (int z = 0; z < T; z++) acc[z] = 0.0f;
-  int batch = 0;
-
-  auto accumulate = [&](int nb) {
-    for (int a = 0; a < nb; a++) {
-      float wxy = sw[a][tx] * sw[a][T + ty];
-      if (wxy != 0.0f) {
-#pragma unroll
-        for (int z = 0; z < T; z++) acc[z] = fmaf(wxy, sw[a][2 * T + z], acc[z]);
-      }
-    }
-  };
-
-  const int Cy = S.C[1], Cz = S.C[2];
+  const int Cx = S.C[0], Cy = S.C[1], Cz = S.C[2];
   for (int ux = cl[0]; ux <= ch[0]; ux++) {
-    int wx = wrap_i(ux, S.C[0]);
-    int shx = floordiv_i(ux, S.C[0]) * S.M[0];
+    const int wx = wrap_i(ux, Cx);
+    const float mx = (float)(m[0] - floordiv_i(ux, Cx) * S.M[0]);  // m_x minus the image shift
     for (int uy = cl[1]; uy <= ch[1]; uy++) {
-      int wy = wrap_i(uy, Cy);
-      int shy = floordiv_i(uy, Cy) * S.M[1];
+      const int wy = wrap_i(uy, Cy);
+      const float my = (float)(m[1] - floordiv_i(uy, Cy) * S.M[1]);
+      const int* cs = cell_start + S.cell_off + (wx * Cy + wy) * Cz;
       int uz = cl[2];
       while (uz <= ch[2]) {
-        int wz = wrap_i(uz, Cz);
-        int kz = floordiv_i(uz, Cz);
-        int run = Cz - 1 - wz;
-        if (uz + run > ch[2]) run = ch[2] - uz;
-        int shz = kz * S.M[2];
-        int cfirst = S.cell_off + (wx * Cy + wy) * Cz + wz;
-        int ab = cell_start[cfirst], ae = cell_start[cfirst + run + 1];
-        for (int base = ab; base < ae; base += 64) {
-          int idx = base + tid;
-          bool keep = false;
-          float wv[3][P], dummy[P];
-          int bb[3];
-          if (idx < ae) {
-            float4 u4 = uq[idx];
-            float uu[3] = {u4.x, u4.y, u4.z};
-            int sh[3] = {shx, shy, shz};
-            keep = true;
+        const int kz = floordiv_i(uz, Cz), wz = uz - kz * Cz;
+        const int wend = min(Cz - 1, wz + (ch[2] - uz));
+        const int zsh = kz * S.M[2] - m[2];  // z-base relative to the tile's first point
+        auto add = [&](const float4 u) {
+          const float wxy = u.w * bspline_value<P>(mx - u.x, cf) * bspline_value<P>(my - u.y, cf);
+          const float fl = floorf(u.z);
+          const int r = (int)fl + zsh - H + 1;  // first of the p z-points, tile-relative
+          if (wxy != 0.f && r >= -PAD && r < zlen) {
+            float wz[P], dummy[P];
+            bspline_weights<P, false>(u.z - fl, wz, dummy);
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-              float fl = floorf(uu[d]);
-              int b = (int)fl + sh[d];
-              bb[d] = b;
-              if (b < m0[d] - H || b > m1[d] + H - 1) keep = false;
-              bspline_weights<P, false>(uu[d] - fl, wv[d], dummy);
-            }
-            if (keep) {
-#pragma unroll
-              for (int j = 0; j < P; j++) wv[0][j] *= u4.w;
-            }
+            for (int jz = 0; jz < P; jz++) col[r + PAD + jz][t] = fmaf(wxy, wz[jz], col[r + PAD + jz][t]);
           }
-          unsigned bal = __ballot_sync(0xffffffffu, keep);
-          int rank = __popc(bal & ((1u << lane) - 1u));
-          if (lane == 0) s_wtot[warp] = __popc(bal);
-          __syncthreads();
-          int tot = s_wtot[0] + s_wtot[1];
-          int before = (warp == 1) ? s_wtot[0] : 0;
-          if (batch + tot > CAP) {
-            accumulate(batch);
-            __syncthreads();
-            batch = 0;
-          }
-          if (keep) {
-            int slotp = batch + before + rank;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-#pragma unroll
-              for (int t = 0; t < T; t++) {
-                int j = m0[d] + t - bb[d] + H - 1;
-                float v = 0.0f;
-#pragma unroll
-                for (int jj = 0; jj < P; jj++) v = (j == jj) ? wv[d][jj] : v;
-                sw[slotp][d * T + t] = v;
-              }
-            }
-          }
-          batch += tot;
-          __syncthreads();
+        };
+        const int je = cs[wend + 1];
+        int j = cs[wz];
+        for (; j + 3 < je; j += 4) {  // four loads in flight
+          const float4 u0 = uq[j], u1 = uq[j + 1], u2 = uq[j + 2], u3 = uq[j + 3];
+          add(u0);
+          add(u1);
+          add(u2);
+          add(u3);
         }
-        uz += run + 1;
+        for (; j < je; j++) add(uq[j]);
+        uz += wend - wz + 1;
       }
     }
   }
-  accumulate(batch);
-  int gx = it.x0 + tx, gy = it.y0 + ty;
-  if (gx < L.n[0] && gy < L.n[1]) {
-    float* out = grid + L.q_off + ((long long)gx * L.n[1] + gy) * L.n[2] + it.z0;
-#pragma unroll
-    for (int z = 0; z < T; z++)
-      if (it.z0 + z < L.n[2]) out[z] = acc[z];
-  }
+  float* out = grid + L.q_off + ((long long)gx * L.n[1] + gy) * L.n[2] + it.z0;
+  for (int z = 0; z < zlen; z++) out[z] = col[z + PAD][t];
 }
 
 template <int P>
@@ -255,9 +238,9 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
 void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p) {
   if (nitems <= 0) return;
   switch (p) {
-    case 4: k_anterp<4><<<nitems, 64, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
-    case 6: k_anterp<6><<<nitems, 64, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
-    default: k_anterp<8><<<nitems, 64, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
+    case 4: k_anterp<4><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
+    case 6: k_anterp<6><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
+    default: k_anterp<8><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
   }
 }
 

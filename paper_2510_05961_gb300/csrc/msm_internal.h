@@ -15,7 +15,7 @@ namespace msm {
 constexpr int kMaxLev = 20;
 constexpr int kChunk = 256;        // atoms per per-atom work item
 constexpr int kChunkWarps = kChunk / 32;
-constexpr int kAnterpT = 8;        // anterpolation tile edge (grid points)
+constexpr int kAnterpTX = 16, kAnterpTY = 8, kAnterpTZ = 32;  // anterpolation tile (grid points)
 constexpr int kBallTY = 32;        // stencil tile rows (y)
 constexpr int kBallBZ = 16;        // outputs per thread along z
 constexpr int kBallTZ = 32;        // stencil tile depth (z)
@@ -52,6 +52,7 @@ struct SysDev {
   float gca[8];     // softening polynomial over a, in s = 1 - (r/a)^2: gamma(r/a)/a = sum_k gca[k] s^k
   float gdca[8];    // (2/a^3) d gamma / d s = sum_k gdca[k] s^k, so k_0'(r)/r = -1/r^3 + sum_k gdca[k] s^k
   float jc[9];      // restriction coefficients J_k, k = -p/2 .. p/2 (index k + p/2)
+  float bsp[4][8];  // centred B-spline Phi_p on |t| in [i, i+1): sum_k bsp[i][k] (|t| - i)^k
   float om[4];      // prefilter of the ball levels: omega'_0 .. omega'_(pre_r) (symmetric), or identity
   int pre_r;        // prefilter half-width (p/2 - 1 when the ball kernels apply raw samples, else 0)
 };

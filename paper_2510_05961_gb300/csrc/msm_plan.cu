@@ -55,6 +55,32 @@ static double klev(const SysHost& S, int l, double r, bool deriv) {
   return soft(S.p, r / s1) / s1 - soft(S.p, r / s2) / s2;
 }
 
+// Pieces of the centred B-spline Phi_p(t) = N_p(t + p/2), N_p the cardinal
+// B-spline on [0, p): out[i][k] is the coefficient of s^k of Phi_p(i + s),
+// s in [0, 1), i = 0 .. p/2 - 1. Built from N_1 = 1 on [0, 1) by the
+// recursion N_m(x) = (x N_(m-1)(x) + (m - x) N_(m-1)(x - 1)) / (m - 1) applied
+// to the polynomial of each unit interval in its local variable.
+static void bspline_pieces(int p, double out[4][8]) {
+  double cur[8][8] = {{1.0}}, nxt[8][8];
+  for (int m = 2; m <= p; m++) {
+    for (int j = 0; j < m; j++) {
+      for (int k = 0; k < 8; k++) nxt[j][k] = 0.0;
+      // (j + s) N_(m-1) on interval j, plus (m - j - s) N_(m-1) on interval j - 1
+      for (int k = 0; k + 1 < m; k++) {
+        const double a = (j < m - 1) ? cur[j][k] : 0.0;
+        const double b = (j >= 1) ? cur[j - 1][k] : 0.0;
+        nxt[j][k] += j * a + (m - j) * b;
+        nxt[j][k + 1] += a - b;
+      }
+      for (int k = 0; k < m; k++) nxt[j][k] /= (m - 1);
+    }
+    for (int j = 0; j < m; j++)
+      for (int k = 0; k < 8; k++) cur[j][k] = nxt[j][k];
+  }
+  for (int i = 0; i < 4; i++)
+    for (int k = 0; k < 8; k++) out[i][k] = (i < p / 2 && k < p) ? cur[p / 2 + i][k] : 0.0;
+}
+
 // omega'_0 .. omega'_(p/2-1) (symmetric), exact rationals: the shortest
 // symmetric sequence whose symbol times the squared B-spline sampling symbol
 // is 1 + O(theta^p) (equivalently, 1-D kernel interpolation reproduces
@@ -475,6 +501,12 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     for (int k = 0; k + 1 < S.p; k++) D.gdca[k] = (float)(2.0 * (k + 1) * S.gc[k + 1] / (S.a * S.a * S.a));
     for (int k = 0; k <= S.p; k++) D.jc[k] = (float)S.jc[k];
     {
+      double bp[4][8];
+      bspline_pieces(S.p, bp);
+      for (int i = 0; i < 4; i++)
+        for (int k = 0; k < 8; k++) D.bsp[i][k] = (float)bp[i][k];
+    }
+    {
       double om[4];
       omega_half(S.p, om);
       // the ball kernels prefilter the grid with omega' (and apply the raw
@@ -604,9 +636,9 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       int li = hs[s].lev0 + l - 1;
       const LevDev& L = hlev[li];
       if (l == 1)
-        for (int x = 0; x < L.n[0]; x += kAnterpT)
-          for (int y = 0; y < L.n[1]; y += kAnterpT)
-            for (int z = 0; z < L.n[2]; z += kAnterpT) anterp_items.push_back({li, x, y, z});
+        for (int x = 0; x < L.n[0]; x += kAnterpTX)
+          for (int y = 0; y < L.n[1]; y += kAnterpTY)
+            for (int z = 0; z < L.n[2]; z += kAnterpTZ) anterp_items.push_back({li, x, y, z});
       if (L.kind == 0) {
         for (int x = 0; x < L.n[0]; x++)
           for (int y = 0; y < L.n[1]; y += kBallTY)
