@@ -351,11 +351,14 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     LevelHost& Lv = S.lev[l - 1];
     Lv.scale = (float)std::ldexp(1.0, -(l - 1));
     bool top = (l == S.nlev);
-    // ball kernels are compiled for radii up to kBallRmax; larger stencils
-    // (and stencils that overlap themselves on a periodic grid) use the box kernel
+    // ball kernels are compiled for radii up to kBallRmax; larger stencils use
+    // the box kernel. A ball that overlaps itself on a small periodic grid is
+    // still applied as a ball: its halo holds the periodic images (wrapped
+    // more than once where the grid is shorter than the halo), which sums
+    // every image of each offset exactly as the folded stencil does.
     bool ball = !top;
     for (int d = 0; d < 3; d++)
-      if ((Lv.per[d] && 2 * S.B[d] + 1 > Lv.n[d]) || S.B[d] > kBallRmax) ball = false;
+      if (S.B[d] > kBallRmax) ball = false;
     for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
     if (ball) {
       Lv.kind = 0;
