@@ -168,17 +168,26 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   perm[dst] = g;
   scell[dst] = cell;
   float qq = q[g];
-  float loc[3], u[3];  // x, y relative to the cell corner, z relative to the column (cell z index 0)
+  // x, y relative to the cell's lower faces, z relative to the column base
+  // (the Cartesian z of the image next to the cell), formed in FP64 from the
+  // FP32 input so that displacements between nearby atoms are exact to FP32
+  float loc[3], u[3];
   int c[3] = {cell / (S.C[1] * S.C[2]), (cell / S.C[2]) % S.C[1], cell % S.C[2]};
   for (int d = 0; d < 3; d++) {
     float s, t;
-    if (reduced_coord(S, d, pos[3 * g + d], s)) {
+    const float x = pos[3 * g + d];
+    if (reduced_coord(S, d, x, s)) {
       loc[d] = 0.0f;
       u[d] = 0.0f;
       continue;
     }
     axis_cell(S, d, s, t);
-    loc[d] = (d < 2 ? (t - (float)c[d]) : t) * S.edge[d];
+    double xd = x;
+    if (S.pbc[d]) {
+      if (!(xd >= 0.0 && xd < S.Ld[d])) xd -= S.Ld[d] * floor(xd / S.Ld[d]);
+      if (c[d] == 0 && xd > 0.5 * S.Ld[d]) xd -= S.Ld[d];  // s rounded up to 1 wraps to cell 0
+    }
+    loc[d] = d < 2 ? (float)(xd - c[d] * S.edged[d]) : (float)xd;
     u[d] = s * S.Mf[d];
   }
   xq[dst] = make_float4(loc[0], loc[1], loc[2], qq);

@@ -31,6 +31,12 @@ __device__ __forceinline__ int floordiv_s(int a, int b) {
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
+// k L - z, rounded once (FP64 only for the z-runs across a periodic face)
+__device__ __forceinline__ float image_shift(int k, double L, float z) {
+  if (k == 0) return -z;
+  return (float)(k * L - (double)z);
+}
+
 template <int P, bool WF, bool WW>
 __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                                                   const int* __restrict__ cell_start, const int* __restrict__ scell,
@@ -52,24 +58,27 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
     for (int t = 0; t < P; t++) gc[t] = S.gca[t];
 #pragma unroll
     for (int t = 0; t < P - 1; t++) gdc[t] = S.gdca[t];
-    const float a2 = S.a2, inv_a2 = S.inv_a2, Lz = S.Lf[2];
+    const float a2 = S.a2, inv_a2 = S.inv_a2;
     const float ex = S.edge[0], ey = S.edge[1], inv_ez = 1.0f / S.edge[2];
+    // the binning contract may place an atom a rounding step outside its cell's
+    // faces; culling keeps a margin of 2e-4 cell edges (enough for C <= 512)
+    constexpr float mg = 2e-4f;
     float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
       const int ux = ci[0] + ox;
       if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
       const int wx = ux - floordiv_s(ux, Cx) * Cx;
       const float bx = (float)ox * ex - xi.x;  // d_x = bx + x_j
-      const float mx = ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f);
+      const float mx = fmaxf((ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f)) - mg * ex, 0.f);
       for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
         const int uy = ci[1] + oy;
         if (!S.pbc[1] && (uy < 0 || uy >= Cy)) continue;
         const float by = (float)oy * ey - xi.y;
-        const float my = oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f);
+        const float my = fmaxf((oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f)) - mg * ey, 0.f);
         const float rxy2 = mx * mx + my * my;
         if (rxy2 >= a2) continue;
         const int wy = uy - floordiv_s(uy, Cy) * Cy;
-        const float zr = sqrtf(a2 - rxy2);
+        const float zr = sqrtf(a2 - rxy2) + mg * S.edge[2];
         int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
         if (!S.pbc[2]) {
           zlo = max(zlo, 0);
@@ -82,7 +91,7 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
           const int wz = uz - kz * Cz;
           const int wend = min(Cz - 1, wz + (zhi - uz));
           const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
-          const float bz = (float)kz * Lz - xi.z;
+          const float bz = image_shift(kz, S.Ld[2], xi.z);
           for (int j = jb; j < je; j++) {
             const float4 xj = xq[j];
             const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;

@@ -22,14 +22,16 @@ constexpr int kBallTZ = 32;        // stencil tile depth (z)
 constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
 constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
-constexpr int kGridChunk = 256;
-constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)    // points per restriction/prolongation item
+constexpr int kGridChunk = 256;    // points per restriction/prolongation item
+constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)
 
 // device status bits (mirrors MSM_DEV_* of the public header)
 constexpr int kDevOutOfCell = 1;
 constexpr int kDevNonFinite = 2;
 
 struct SysDev {
+  double Ld[3];     // cell lengths (FP64: periodic image shifts of the pair displacements)
+  double edged[3];  // binning cell edges (FP64)
   int n;            // atoms of this system
   int atom_off;     // first packed (user-order and sorted) atom index
   int C[3];         // binning cells per axis
@@ -94,7 +96,7 @@ struct Work {
   int* bucket;
   int* perm;
   int* scell;
-  float4* xq;      // position (x, y from the cell corner, z from the cell column's base) and charge, sorted
+  float4* xq;      // Cartesian position (the periodic image next to its cell) and charge, sorted
   float4* uq;      // level-1 grid coordinates and charge, sorted order
   float* phi_sr;   // short-range potential incl. self term, sorted
   float4* f_sr;    // short-range force, sorted

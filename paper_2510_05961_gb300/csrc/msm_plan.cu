@@ -489,6 +489,8 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       D.pbc[d] = S.pbc[d];
       D.M[d] = S.M[d];
       D.edge[d] = (float)S.edge[d];
+      D.edged[d] = S.edge[d];
+      D.Ld[d] = S.L[d];
       D.invL[d] = (float)(1.0 / S.L[d]);
       D.Mf[d] = (float)S.M[d];
       D.inv_h1[d] = (float)(1.0 / S.h1[d]);

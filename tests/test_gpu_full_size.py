@@ -1,0 +1,104 @@
+"""GPU parity at the full sizes of the benchmark workloads.
+
+Each test runs the CUDA path in the configuration the benchmark times
+(one plan sized to the system, forward with forces and virial, backward with
+dE = 1) and compares every output with the FP64 oracle run on the same seeded
+input: the 1,024,000-atom periodic box (p = 4, h = 2, a = 8), the
+4096-molecule water box (p = 6, h = 1.5, a = 9), the 32^3 rock-salt supercell
+(262,144 atoms) and the 512-system batch. Tolerances: relative energy error
+<= 1e-5 (plus an FP32 rounding floor of 1e-7 sum_i |q_i phi_i| / 2 for the
+few small systems whose energy nearly cancels); relative RMS error of
+forces, potentials, dE/dq and dE/dr <= 1e-4; virial to 1e-4 of its largest
+entry.
+The oracle takes about a minute for the 1M-atom box.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2510_05961_gb300 import Batch, Plan, build  # noqa: E402
+from paper_2510_05961_gb300 import workloads as W  # noqa: E402
+
+E_TOL = 1e-5
+F_TOL = 1e-4
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    import oracle as O
+    O.build()
+
+
+def rel_rms(a, b):
+    a = np.asarray(a, np.float64).reshape(len(a), -1)
+    b = np.asarray(b, np.float64).reshape(len(b), -1)
+    return float(np.sqrt(((a - b) ** 2).sum(1).mean() / max((b ** 2).sum(1).mean(), 1e-300)))
+
+
+def fwd_bwd(w):
+    plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=w.n, device=DEV)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    E, phi, F = plan.forward(pos, q, forces=True, virial=True)
+    gp, gq, Wv = plan.backward(torch.ones(1, dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return dict(E=float(E.cpu()[0]), phi=phi.cpu().numpy(), F=F.cpu().numpy(), W=Wv.cpu().numpy(),
+                dpos=gp.cpu().numpy(), dq=gq.cpu().numpy())
+
+
+def check(r, ref, q):
+    # 1e-5 relative, with an FP32 rounding floor for energies that cancel:
+    # 1e-7 of the sum of the magnitudes of the terms 1/2 q_i phi_i
+    floor = 1e-7 * 0.5 * float(np.abs(np.asarray(q, np.float64) * ref["phi"]).sum())
+    assert abs(r["E"] - ref["E"]) <= E_TOL * abs(ref["E"]) + floor, (r["E"], ref["E"], floor)
+    assert rel_rms(r["F"], ref["F"]) <= F_TOL
+    assert rel_rms(r["phi"], ref["phi"]) <= F_TOL
+    assert rel_rms(r["dq"], ref["phi"]) <= F_TOL
+    assert rel_rms(r["dpos"], -ref["F"]) <= F_TOL
+    assert np.abs(r["W"] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), (r["W"], ref["W"])
+
+
+def oracle_msm(w):
+    import oracle as O
+    P = O.plan_for(w)
+    return O.msm(P, w.pos.astype(np.float64), w.q.astype(np.float64), forces=True, virial=True)
+
+
+@pytest.mark.parametrize("make", [
+    pytest.param(lambda: W.random_box(1_024_000, seed=3010), id="periodic_1M"),
+    pytest.param(lambda: W.water_box(), id="water_4096"),
+    pytest.param(lambda: W.rocksalt(ncell=32), id="rocksalt_32"),
+])
+def test_full_size_parity(make):
+    w = make()
+    r = fwd_bwd(w)
+    check(r, oracle_msm(w), w.q)
+
+
+def test_batch_512_full_size():
+    systems = W.batch_systems()
+    batch = Batch(systems, device=DEV)
+    pos = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(DEV)
+    q = torch.from_numpy(np.concatenate([s.q for s in systems])).to(DEV)
+    E, phi, F = batch.forward(pos, q, forces=True, virial=True)
+    gp, gq, Wb = batch.backward(torch.ones(len(systems), dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    E, phi, F, Wb = E.cpu().numpy(), phi.cpu().numpy(), F.cpu().numpy(), Wb.cpu().numpy()
+    gp, gq = gp.cpu().numpy(), gq.cpu().numpy()
+    off = 0
+    for s, sysw in enumerate(systems):
+        n = sysw.n
+        ref = oracle_msm(sysw)
+        r = dict(E=float(E[s]), phi=phi[off:off + n], F=F[off:off + n], W=Wb[s], dpos=gp[off:off + n],
+                 dq=gq[off:off + n])
+        check(r, ref, sysw.q)
+        off += n
