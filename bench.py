@@ -415,6 +415,9 @@ def run_gpu(args):
                         else read_traffic("short_1M", "k_short.cu")),
             "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (no FP32 peak in MEASURED_PEAKS.json)",
             "phase_ms": {k: round(v, 4) for k, v in ph_ms.items()},
+            "phase_note": "the short-range kernel runs on a second stream, concurrently with anterp .. interp; "
+                          "each phase is timed by events on its own stream, so overlapping phases include "
+                          "the contention (the ncu launch list in profiles/ has isolated durations)",
             "algorithmic_flops": {"stencil": st_flops, "short": sr_flops}}
 
     batch_res = None

@@ -78,10 +78,14 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
     launch_prologue(w, E.total_cells, E.d_sys, E.single ? n_single : -1, s);
     launch_bin(w, t, E.d_atom_items, nai, E.total_cells, n_total, pos, q, s);
   }
+  // fork: the short-range pairs (side stream) overlap the grid chain (caller's stream)
+  cudaEventRecord(E.ev_fork, s);
+  cudaStreamWaitEvent(E.side, E.ev_fork, 0);
   {
-    Phase ph(E, MSM_PH_SHORT, s);
-    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, s, E.p);
+    Phase ph(E, MSM_PH_SHORT, E.side);
+    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, E.side, E.p);
   }
+  cudaEventRecord(E.ev_join, E.side);
   {
     Phase ph(E, MSM_PH_ANTERP, s);
     launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p);
@@ -110,6 +114,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
     Phase ph(E, MSM_PH_INTERP, s);
     launch_interp(w, t, E.d_atom_items, nai, want_f, s, E.p);
   }
+  cudaStreamWaitEvent(s, E.ev_join, 0);  // join
   {
     Phase ph(E, MSM_PH_FINAL, s);
     launch_finalize(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, s);

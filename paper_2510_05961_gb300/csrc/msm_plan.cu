@@ -757,12 +757,22 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   }
   prolong_off[prolong_steps.size()] = (int)all.size();
   if ((rc = up(all, &d_range_items, err))) return rc;
+  // second stream for the short-range kernel, which overlaps the grid chain
+  if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (err) *err = "stream or event creation failed";
+    return MSM_ERR_CUDA;
+  }
   return MSM_OK;
 }
 
 Engine::~Engine() {
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (side) cudaStreamDestroy(side);
   cudaFree(d_sys);
   cudaFree(d_lev);
   cudaFree(d_kpool);

@@ -91,6 +91,10 @@ struct Engine {
   cudaEvent_t ev[2 * 10] = {};
   bool ev_used[10] = {};
   int launches_fwd = 0, launches_bwd = 0;
+  // the short-range kernel runs on `side`, forked from and joined to the
+  // caller's stream, so it overlaps the grid chain
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   Engine() = default;
   Engine(const Engine&) = delete;
