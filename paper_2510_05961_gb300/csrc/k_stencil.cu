@@ -384,12 +384,13 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ s
     for (int o = 0; o < BZ; o++) qown[o] = (y < L.n[1] && z0 + o < L.n[2]) ? row[z0 + o] : 0.f;
   }
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // the half-space weights vanish for dx < 0: walk the planes dx = 0 .. Rx only
   const int nsteps = 2 * Rx + 1;
-  stage_ball(L, it, 0, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes, kslabs, wsl, stride);
-  for (int step = 0; step < nsteps; step++) {
+  stage_ball(L, it, Rx, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes, kslabs, wsl, stride);
+  for (int step = Rx; step < nsteps; step++) {
     cp_async_wait_all();
     __syncthreads();
-    const int b = step & 1;
+    const int b = (step - Rx) & 1;
     if (step + 1 < nsteps)
       stage_ball(L, it, step + 1, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes + (b ^ 1) * plane_sz,
                  kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax, stride);
