@@ -107,7 +107,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
     Phase ph(E, MSM_PH_PROLONG, s);
     for (int l = E.maxcomp - 1; l >= 1; l--) {
       int a = E.prolong_off[l - 1], b = E.prolong_off[l];
-      launch_prolong(w, t, E.d_range_items + a, b - a, s, E.p);
+      launch_prolong(w, t, E.d_pro_items + a, b - a, s, E.p);
     }
   }
   {

@@ -22,7 +22,8 @@ constexpr int kBallTZ = 32;        // stencil tile depth (z)
 constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
 constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
-constexpr int kGridChunk = 256;    // points per restriction/prolongation item
+constexpr int kGridChunk = 256;    // coarse points per restriction item
+constexpr int kProTX = 4, kProTY = 4, kProTZ = 32;  // prolongation tiles (fine points)
 constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)
 
 // device status bits (mirrors MSM_DEV_* of the public header)
@@ -130,7 +131,7 @@ void launch_interp(const Work& w, const Tables& t, const AtomItem* items, int ni
                    cudaStream_t s, int p);
 // restriction / prolongation (k_grid.cu)
 void launch_restrict(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
-void launch_prolong(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
+void launch_prolong(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p);
 // stencils and grid virial (k_stencil.cu)
 void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitems, int pre_r, cudaStream_t s);
 void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,

@@ -664,7 +664,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   vb_off[nsys] = (int)ball_items.size();
   vx_off[nsys] = (int)box_items.size();
   restrict_steps.assign(std::max(0, maxcomp - 1), std::vector<RangeItem>());
-  prolong_steps.assign(std::max(0, maxcomp - 1), std::vector<RangeItem>());
+  prolong_steps.assign(std::max(0, maxcomp - 1), std::vector<TileItem>());
   for (int l = 1; l < maxcomp; l++) {
     for (int s = 0; s < nsys; s++) {
       if (sys[s].ncomp <= l) continue;
@@ -674,9 +674,9 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       long long nc = (long long)Cc.n[0] * Cc.n[1] * Cc.n[2];
       for (long long st = 0; st < nc; st += kGridChunk)
         restrict_steps[l - 1].push_back({ci, (int)st, (int)std::min<long long>(kGridChunk, nc - st)});
-      long long nf = (long long)F.n[0] * F.n[1] * F.n[2];
-      for (long long st = 0; st < nf; st += kGridChunk)
-        prolong_steps[l - 1].push_back({fi, (int)st, (int)std::min<long long>(kGridChunk, nf - st)});
+      for (int x = 0; x < F.n[0]; x += kProTX)
+        for (int y = 0; y < F.n[1]; y += kProTY)
+          for (int z = 0; z < F.n[2]; z += kProTZ) prolong_steps[l - 1].push_back({fi, x, y, z});
     }
   }
   // device tables
@@ -750,13 +750,15 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
     all.insert(all.end(), restrict_steps[i].begin(), restrict_steps[i].end());
   }
   restrict_off[restrict_steps.size()] = (int)all.size();
+  if ((rc = up(all, &d_range_items, err))) return rc;
+  std::vector<TileItem> pro;
   prolong_off.assign(prolong_steps.size() + 1, 0);
   for (size_t i = 0; i < prolong_steps.size(); i++) {
-    prolong_off[i] = (int)all.size();
-    all.insert(all.end(), prolong_steps[i].begin(), prolong_steps[i].end());
+    prolong_off[i] = (int)pro.size();
+    pro.insert(pro.end(), prolong_steps[i].begin(), prolong_steps[i].end());
   }
-  prolong_off[prolong_steps.size()] = (int)all.size();
-  if ((rc = up(all, &d_range_items, err))) return rc;
+  prolong_off[prolong_steps.size()] = (int)pro.size();
+  if ((rc = up(pro, &d_pro_items, err))) return rc;
   // second stream for the short-range kernel, which overlaps the grid chain
   if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -784,6 +786,7 @@ Engine::~Engine() {
   cudaFree(d_pad_items);
   cudaFree(d_voff);
   cudaFree(d_range_items);
+  cudaFree(d_pro_items);
 }
 
 Work Engine::resolve(void* ws) const {

@@ -62,7 +62,8 @@ struct Engine {
   std::vector<TileItem> anterp_items, ball_items;
   std::vector<RangeItem> box_items;
   std::vector<TileItem> pad_items;
-  std::vector<std::vector<RangeItem>> restrict_steps, prolong_steps;
+  std::vector<std::vector<RangeItem>> restrict_steps;
+  std::vector<std::vector<TileItem>> prolong_steps;
   std::vector<int> restrict_off, prolong_off;
   std::vector<int> vb_off, vx_off;
   // device tables (owned)
@@ -75,7 +76,8 @@ struct Engine {
   TileItem* d_ball_items = nullptr;
   RangeItem* d_box_items = nullptr;
   TileItem* d_pad_items = nullptr;
-  RangeItem* d_range_items = nullptr;
+  RangeItem* d_range_items = nullptr;  // restriction items of all level steps
+  TileItem* d_pro_items = nullptr;     // prolongation tiles of all level steps
   int* d_voff = nullptr;
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
