@@ -34,11 +34,11 @@ def build(force: bool = False) -> str:
 class Plan(C.Structure):
     _fields_ = [
         ("L", C.c_double * 3), ("pbc", C.c_int * 3), ("h", C.c_double), ("grid_override", C.c_int * 3),
-        ("a", C.c_double), ("p", C.c_int), ("levels", C.c_int),
+        ("a", C.c_double), ("p", C.c_int), ("levels", C.c_int), ("qi_mode", C.c_int),
         ("nlev", C.c_int), ("ncomp", C.c_int), ("top_kept", C.c_int),
         ("M", C.c_int * 3), ("h1", C.c_double * 3),
         ("lo", (C.c_int * 3) * MAXLEV), ("n", (C.c_int * 3) * MAXLEV),
-        ("S", C.c_int * 3), ("R", C.c_int * 3),
+        ("S", C.c_int * 3), ("R", C.c_int * 3), ("hw", C.c_int),
         ("C", C.c_int * 3), ("edge", C.c_double * 3), ("nnbr", C.c_int * 3),
         ("invLf", C.c_float * 3),
     ]
@@ -76,6 +76,8 @@ def lib():
         L.or_J.argtypes = [C.c_int, _dp]
         L.or_omega.restype = C.c_int
         L.or_omega.argtypes = [C.c_int, _dp]
+        L.or_omega_exact.restype = C.c_int
+        L.or_omega_exact.argtypes = [C.c_int, _dp, C.c_int]
         L.or_plan_init.restype = C.c_int
         L.or_plan_init.argtypes = [C.POINTER(Plan)]
         L.or_bin.restype = C.c_int
@@ -148,8 +150,16 @@ def omega(p):
     return out
 
 
+def omega_exact(p, maxhw=96):
+    """omega' of exact interpolation (qi_mode 1), indices -hw .. hw."""
+    buf = np.zeros(2 * maxhw + 1)
+    hw = lib().or_omega_exact(p, _ptr(buf), maxhw)
+    assert hw >= 0
+    return buf[:2 * hw + 1].copy()
+
+
 # --------------------------------------------------------------------------- plan
-def make_plan(cell, pbc, h, a, p, levels=0, grid_override=(0, 0, 0)):
+def make_plan(cell, pbc, h, a, p, levels=0, grid_override=(0, 0, 0), qi_mode=0):
     P = Plan()
     for d in range(3):
         P.L[d] = float(cell[d])
@@ -159,6 +169,7 @@ def make_plan(cell, pbc, h, a, p, levels=0, grid_override=(0, 0, 0)):
     P.a = float(a)
     P.p = int(p)
     P.levels = int(levels)
+    P.qi_mode = int(qi_mode)
     rc = lib().or_plan_init(C.byref(P))
     if rc != 0:
         raise ValueError("oracle plan rejected the parameters (code %d)" % rc)
@@ -166,7 +177,7 @@ def make_plan(cell, pbc, h, a, p, levels=0, grid_override=(0, 0, 0)):
 
 
 def plan_for(w):
-    return make_plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override)
+    return make_plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, getattr(w, "qi_mode", 0))
 
 
 def plan_summary(P):
@@ -176,7 +187,7 @@ def plan_summary(P):
         "M": [P.M[d] for d in range(3)], "h1": [P.h1[d] for d in range(3)],
         "lo": [[P.lo[l][d] for d in range(3)] for l in range(P.ncomp)],
         "n": [[P.n[l][d] for d in range(3)] for l in range(P.ncomp)],
-        "S": [P.S[d] for d in range(3)], "R": [P.R[d] for d in range(3)],
+        "S": [P.S[d] for d in range(3)], "R": [P.R[d] for d in range(3)], "hw": P.hw,
         "C": [P.C[d] for d in range(3)], "edge": [P.edge[d] for d in range(3)],
         "nnbr": [P.nnbr[d] for d in range(3)],
     }

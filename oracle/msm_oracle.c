@@ -27,6 +27,8 @@
 /* status bits of or_bin */
 #define OR_ST_OUTSIDE 1
 #define OR_ST_NONFINITE 2
+#define OR_MAXHW 96  /* largest omega' half-width a plan may use */
+#define OR_PI 3.14159265358979323846
 
 typedef struct {
   /* inputs */
@@ -37,6 +39,7 @@ typedef struct {
   double a;             /* level-zero cutoff r_cut^(0) */
   int p;                /* B-spline order (even) */
   int levels;           /* L, 0 = rule below */
+  int qi_mode;          /* 0 minimal quasi-interpolation, 1 exact interpolation (or_omega_exact) */
   /* derived by or_plan_init */
   int nlev;             /* number of grid levels L (top level included) */
   int ncomp;            /* levels whose grids are evaluated (nlev, or nlev-1 when the top is dropped) */
@@ -46,7 +49,8 @@ typedef struct {
   int lo[OR_MAXLEV][3]; /* first grid index per level (index 0 = level 1) */
   int n[OR_MAXLEV][3];  /* grid points per level */
   int S[3];             /* kernel-sample radius of the level stencils */
-  int R[3];             /* stencil radius S + p/2 - 1 */
+  int R[3];             /* stencil radius S + hw */
+  int hw;               /* half-width of omega': p/2 - 1 (qi_mode 0) or the truncation of or_omega_exact */
   int C[3];             /* binning cells per axis (periodic: M / 2^k, edge <= a/2; open: floor(2L/a)) */
   double edge[3];       /* binning cell edges */
   int nnbr[3];          /* neighbour-cell reach ceil(a/edge) */
@@ -224,6 +228,48 @@ int or_omega(int p, double* w) {
   return 0;
 }
 
+/* Exact-interpolation coefficients (qi_mode 1): omega' = omega * omega with
+ * omega the inverse of the sampled B-spline b_n = Phi_p(n), i.e. the Fourier
+ * coefficients of 1 / b(theta)^2, b(theta) = sum_n Phi_p(n) cos(n theta) > 0:
+ *   omega'_n = (1/2 pi) int_(-pi)^(pi) cos(n theta) / b(theta)^2 d theta,
+ * evaluated by the trapezoidal rule on 4096 points (exponentially accurate for
+ * this analytic periodic integrand). Reading of the truncation: keep |n| <= hw,
+ * hw the largest n with |omega'_n| >= 1e-12 |omega'_0| (FP64 resolves the
+ * coefficients to about 1e-16 |omega'_0|, so a 1e-17 cut cannot be decided;
+ * FP32 stencils resolve neither). w receives omega'_(-hw) .. omega'_(hw), at
+ * most 2 maxhw + 1 values; returns hw, or -1 if maxhw is too small. */
+int or_omega_exact(int p, double* w, int maxhw) {
+  const int N = 4096, H = p / 2;
+  double bn[8];
+  for (int m = 0; m < H; m++) bn[m] = or_bspline(p, (double)m);
+  double* f = (double*)malloc(sizeof(double) * N);
+  for (int j = 0; j < N; j++) {
+    double th = 2.0 * OR_PI * j / N, b = bn[0];
+    for (int m = 1; m < H; m++) b += 2.0 * bn[m] * cos(m * th);
+    f[j] = 1.0 / (b * b);
+  }
+  double c[256];
+  int lim = maxhw + 1 < 255 ? maxhw + 1 : 255;
+  for (int n = 0; n <= lim; n++) {
+    double s = 0.0;
+    for (int j = 0; j < N; j++) s += f[j] * cos(2.0 * OR_PI * (double)((long)n * j % N) / N);
+    c[n] = s / N;
+  }
+  free(f);
+  int hw = -1;
+  for (int n = 0; n <= lim; n++)
+    if (fabs(c[n]) >= 1e-12 * fabs(c[0])) hw = n;
+  if (hw >= lim) return -1;
+  for (int n = -hw; n <= hw; n++) w[n + hw] = c[n < 0 ? -n : n];
+  return hw;
+}
+
+/* omega' of the plan's interpolation mode, indices -hw .. hw (w needs 2 hw + 1) */
+static void plan_omega(const or_plan* P, double* w) {
+  if (P->qi_mode == 1) or_omega_exact(P->p, w, P->hw);
+  else or_omega(P->p, w);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Grid set-up (Sec. 4.1 for periodic axes; readings for open axes).         */
 /* ------------------------------------------------------------------------ */
@@ -241,6 +287,14 @@ static int ceildiv(int a, int b) { return -floordiv(-a, b); }
 int or_plan_init(or_plan* P) {
   int p = P->p;
   if (p != 4 && p != 6 && p != 8) return 1;
+  if (P->qi_mode != 0 && P->qi_mode != 1) return 1;
+  if (P->qi_mode == 1) {
+    double tmp[2 * OR_MAXHW + 1];
+    P->hw = or_omega_exact(p, tmp, OR_MAXHW);
+    if (P->hw < 0) return 1;
+  } else {
+    P->hw = p / 2 - 1;
+  }
   if (!(P->a > 0.0)) return 1;
   int anyper = 0, Mper = 0;
   for (int d = 0; d < 3; d++) {
@@ -319,7 +373,7 @@ int or_plan_init(or_plan* P) {
   for (int d = 0; d < 3; d++) {
     P->S[d] = (int)ceil(2.0 * P->a / P->h1[d]) - 1;
     if (P->S[d] < 0) P->S[d] = 0;
-    P->R[d] = P->S[d] + hp - 1;
+    P->R[d] = P->S[d] + P->hw;
     int C;
     if (P->pbc[d]) {
       /* periodic axis: cells of k level-1 intervals, k the largest power of
@@ -584,9 +638,9 @@ void or_stencil_box(const or_plan* P, int l, int* lo, int* sz) {
  * K_m = sum_n omega'_(mx-nx) omega'_(my-ny) omega'_(mz-nz) sample(n), applied
  * one axis at a time; periodic axes then folded onto [0, n_l). */
 void or_stencil_build(const or_plan* P, int l, int which, const double* G, double* out) {
-  int p = P->p, r = p / 2 - 1;
-  double om[8];
-  or_omega(p, om);
+  int p = P->p, r = P->hw;
+  double om[2 * OR_MAXHW + 1];
+  plan_omega(P, om);
   /* unfolded output box */
   int olo[3], osz[3], slo[3], ssz[3];
   for (int d = 0; d < 3; d++) {

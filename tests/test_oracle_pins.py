@@ -307,6 +307,64 @@ def test_binning_contract(oracle):
 
 
 # ----------------------------------------------------------------- whole method
+def test_omega_exact_closed_form_p4(oracle):
+    """Exact interpolation, p = 4: the sampled cubic B-spline is (1/6, 2/3, 1/6),
+    whose inverse is omega_n = sqrt(3) z^|n| with z = sqrt(3) - 2 (the root of
+    z^2 + 4 z + 1 inside the unit circle); omega' = omega * omega is then
+    3 z^|n| (|n| + (1 + z^2) / (1 - z^2))."""
+    w = oracle.omega_exact(4)
+    hw = (len(w) - 1) // 2
+    z = math.sqrt(3.0) - 2.0
+    for n in range(-hw, hw + 1):
+        ref = 3.0 * z ** abs(n) * (abs(n) + (1 + z * z) / (1 - z * z))
+        assert w[n + hw] == pytest.approx(ref, rel=1e-12, abs=1e-15)
+    # truncation: the first dropped coefficient is below 1e-12 of omega'_0
+    ref_next = 3.0 * abs(z) ** (hw + 1) * (hw + 1 + (1 + z * z) / (1 - z * z))
+    assert ref_next < 1e-12 * w[hw] <= 3.0 * abs(z) ** hw * (hw + (1 + z * z) / (1 - z * z))
+
+
+@pytest.mark.parametrize("p", [6, 8])
+def test_omega_exact_inverts_the_sampled_bspline(oracle, p):
+    """omega' convolved with the sampled B-spline b twice is the unit impulse
+    (b * b * omega' = delta), checked against the direct inverse of the banded
+    Toeplitz matrix of b (numpy linear algebra, an independent method)."""
+    w = oracle.omega_exact(p)
+    hw = (len(w) - 1) // 2
+    b = np.array([oracle.bspline(p, m) for m in range(-p // 2 + 1, p // 2)])
+    bb = np.convolve(b, b)
+    d = np.convolve(bb, w)
+    c = len(d) // 2
+    impulse = np.zeros_like(d)
+    impulse[c] = 1.0
+    assert np.abs(d[c - hw + 2 * p:c + hw - 2 * p + 1] - impulse[c - hw + 2 * p:c + hw - 2 * p + 1]).max() < 1e-11
+    n = 4 * hw + 1
+    T = np.zeros((n, n))
+    for i in range(n):
+        for k, bk in enumerate(b):
+            j = i + k - (len(b) - 1) // 2
+            if 0 <= j < n:
+                T[i, j] = bk
+    om = np.linalg.solve(T, np.eye(n)[:, n // 2])  # omega, the inverse of b
+    om2 = np.convolve(om, om)[n - 1 - hw:n + hw]   # omega * omega around the centre
+    assert np.abs(om2 - w).max() < 1e-10 * w[hw]
+
+
+def test_exact_interpolation_msm_against_direct(oracle):
+    """The open cluster (config 1 settings): exact interpolation of the grid kernels
+    is closer to the direct Coulomb sum than minimal quasi-interpolation."""
+    w = W.open_cluster()
+    pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+    E0, phi0, F0 = oracle.direct_open(pos, q)
+    errs = {}
+    for qi in (0, 1):
+        P = oracle.make_plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, qi_mode=qi)
+        assert P.hw == (1 if qi == 0 else 23) and P.R[0] == P.S[0] + P.hw
+        r = oracle.msm(P, pos, q, virial=False)
+        ferr = np.sqrt(((r["F"] - F0) ** 2).sum(1).mean() / (F0 ** 2).sum(1).mean())
+        errs[qi] = (abs(r["E"] - E0) / abs(E0), ferr)
+    assert errs[1][1] < errs[0][1] / 2 and errs[1][0] < errs[0][0] / 2
+
+
 def test_open_cluster_against_direct_coulomb(oracle):
     w = W.open_cluster()
     pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
