@@ -73,6 +73,15 @@ typedef struct msm_batch_s* msm_batch;
  *  levels         number of grid levels L; 0 = automatic. With any periodic
  *                 axis L = log2(M) + 1 is fixed (spacing doubles until one
  *                 point remains, Sec. 4.1) and any other value is rejected.
+ *  qi_mode        interpolation of the grid kernels (Sec. 3.4, the omega'
+ *                 coefficients of Eq. kernel_stencil_by_conv_with_universal_coeff):
+ *                 0 = minimal quasi-interpolation (half-width p/2 - 1, the
+ *                 default); 1 = exact interpolation, omega' = omega * omega with
+ *                 omega the inverse of the sampled B-spline (Phi_p(n))_n,
+ *                 truncated where |omega'_n| < 1e-12 |omega'_0| (half-width 23,
+ *                 36, 49 for p = 4, 6, 8): an accuracy reference whose stencils
+ *                 are wider than the ball kernels take, so every level runs the
+ *                 dense folded-box kernel (practical for grids up to ~32^3).
  *  max_atoms      largest n a forward call may pass (sizes the workspace). */
 typedef struct {
   double cell[9];
@@ -82,6 +91,7 @@ typedef struct {
   double cutoff;
   int order;
   int levels;
+  int qi_mode;
   int max_atoms;
 } msm_params;
 

@@ -43,7 +43,8 @@ class MsmError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("cell", C.c_double * 9), ("pbc", C.c_int * 3), ("h", C.c_double), ("grid_override", C.c_int * 3),
-                ("cutoff", C.c_double), ("order", C.c_int), ("levels", C.c_int), ("max_atoms", C.c_int)]
+                ("cutoff", C.c_double), ("order", C.c_int), ("levels", C.c_int), ("qi_mode", C.c_int),
+                ("max_atoms", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -99,7 +100,7 @@ def check(rc):
         raise MsmError(rc, msg.decode() if msg else "")
 
 
-def make_params(cell, pbc, h, cutoff, order, levels=0, grid_override=(0, 0, 0), max_atoms=0):
+def make_params(cell, pbc, h, cutoff, order, levels=0, grid_override=(0, 0, 0), max_atoms=0, qi_mode=0):
     P = Params()
     cell = list(cell)
     if len(cell) == 3:
@@ -113,5 +114,6 @@ def make_params(cell, pbc, h, cutoff, order, levels=0, grid_override=(0, 0, 0), 
     P.cutoff = float(cutoff)
     P.order = int(order)
     P.levels = int(levels)
+    P.qi_mode = int(qi_mode)
     P.max_atoms = int(max_atoms)
     return P

@@ -81,6 +81,54 @@ static void bspline_pieces(int p, double out[4][8]) {
     for (int k = 0; k < 8; k++) out[i][k] = (i < p / 2 && k < p) ? cur[p / 2 + i][k] : 0.0;
 }
 
+// qi_mode 1: omega' = omega * omega, omega the inverse of the sampled
+// B-spline b_n = Phi_p(n). omega solves the banded symmetric Toeplitz system
+// T omega = e_0 on a window of 2W + 1 points by Gaussian elimination without
+// pivoting (T is positive definite: its symbol is the B-spline sampling
+// symbol, > 0); omega decays like |z_1|^|n| with |z_1| <= 0.54 (the root of
+// the sampling polynomial nearest the unit circle, p <= 8), so the window
+// edges do not reach the centre. Kept: |n| <= hw, hw the largest n with
+// |omega'_n| >= 1e-12 |omega'_0|.
+static int exact_omega(int p, std::vector<double>& omh) {
+  double pc[4][8];
+  bspline_pieces(p, pc);
+  const int H = p / 2, bw = H - 1, nb = 2 * bw + 1;
+  double b[4];
+  for (int m = 0; m < H; m++) b[m] = pc[m][0];  // Phi_p(m): piece m at its left end
+  const int W = 240, N = 2 * W + 1;
+  std::vector<double> A((size_t)N * nb, 0.0), x(N, 0.0);
+  auto at = [&](int i, int j) -> double& { return A[(size_t)i * nb + (j - i + bw)]; };
+  for (int i = 0; i < N; i++)
+    for (int j = std::max(0, i - bw); j <= std::min(N - 1, i + bw); j++) at(i, j) = b[std::abs(i - j)];
+  x[W] = 1.0;
+  for (int k = 0; k < N; k++)
+    for (int i = k + 1; i <= std::min(N - 1, k + bw); i++) {
+      const double f = at(i, k) / at(k, k);
+      for (int j = k; j <= std::min(N - 1, k + bw); j++) at(i, j) -= f * at(k, j);
+      x[i] -= f * x[k];
+    }
+  for (int k = N - 1; k >= 0; k--) {
+    double s = x[k];
+    for (int j = k + 1; j <= std::min(N - 1, k + bw); j++) s -= at(k, j) * x[j];
+    x[k] = s / at(k, k);
+  }
+  const int nmax = 120;
+  std::vector<double> wp(nmax + 1, 0.0);
+  for (int n = 0; n <= nmax; n++) {
+    double s = 0.0;
+    for (int k = -W; k <= W; k++) {
+      const int j = n - k;
+      if (j >= -W && j <= W) s += x[k + W] * x[j + W];
+    }
+    wp[n] = s;
+  }
+  int hw = 0;
+  for (int n = 0; n <= nmax; n++)
+    if (std::abs(wp[n]) >= 1e-12 * std::abs(wp[0])) hw = n;
+  omh.assign(wp.begin(), wp.begin() + hw + 1);
+  return hw;
+}
+
 // omega'_0 .. omega'_(p/2-1) (symmetric), exact rationals: the shortest
 // symmetric sequence whose symbol times the squared B-spline sampling symbol
 // is 1 + O(theta^p) (equivalently, 1-D kernel interpolation reproduces
@@ -111,9 +159,8 @@ struct Box3 {
 // [-E, E] (per axis), sample(n) = f(h o n) for the level spacing hl. comp = 0:
 // k_l(|v|); comp 1..6: k_l'(|v|) v_a v_b / |v| with ab = xx,yy,zz,xy,xz,yz.
 static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box3& out) {
-  const int r = S.p / 2 - 1;
-  double wh[4];
-  omega_half(S.p, wh);
+  const int r = S.hw;
+  const std::vector<double>& wh = S.omh;
   double hl[3];
   for (int d = 0; d < 3; d++) hl[d] = S.h1[d] * std::ldexp(1.0, l - 1);
   static const int AB[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
@@ -238,8 +285,18 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
   }
   if (P.order != 4 && P.order != 6 && P.order != 8) return fail(err, MSM_ERR_INVALID_ARG, "order must be 4, 6 or 8");
   if (!(P.cutoff > 0.0) || !std::isfinite(P.cutoff)) return fail(err, MSM_ERR_INVALID_ARG, "cutoff must be > 0");
+  if (P.qi_mode != 0 && P.qi_mode != 1) return fail(err, MSM_ERR_INVALID_ARG, "qi_mode must be 0 or 1");
   S.p = P.order;
   S.a = P.cutoff;
+  S.qi_mode = P.qi_mode;
+  if (S.qi_mode == 1) {
+    S.hw = exact_omega(S.p, S.omh);
+  } else {
+    double wh[4];
+    omega_half(S.p, wh);
+    S.hw = S.p / 2 - 1;
+    S.omh.assign(wh, wh + S.hw + 1);
+  }
   int Mper = 0;
   for (int d = 0; d < 3; d++) {
     S.L[d] = P.cell[4 * d];
@@ -320,8 +377,8 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
   // stencil radius, binning cells
   for (int d = 0; d < 3; d++) {
     S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a / S.h1[d]) - 1);
-    S.R[d] = S.S[d] + H - 1;
-    S.prefilter = (S.p == 4);
+    S.R[d] = S.S[d] + S.hw;
+    S.prefilter = (S.p == 4 && S.qi_mode == 0);
     S.B[d] = S.prefilter ? S.S[d] : S.R[d];
     if (S.pbc[d]) {
       // periodic axis: cells aligned with the grid, k = 2^j level-1 intervals
@@ -356,7 +413,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     // still applied as a ball: its halo holds the periodic images (wrapped
     // more than once where the grid is shorter than the halo), which sums
     // every image of each offset exactly as the folded stencil does.
-    bool ball = !top;
+    bool ball = !top && S.qi_mode == 0;  // exact interpolation: dense boxes (wide stencils, accuracy reference)
     for (int d = 0; d < 3; d++)
       if (S.B[d] > kBallRmax) ball = false;
     for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];

@@ -27,6 +27,9 @@ struct SysHost {
   double h1[3];
   int nlev = 0, ncomp = 0;
   int S[3], R[3];
+  int qi_mode = 0;                   // 0 minimal quasi-interpolation, 1 exact interpolation
+  int hw = 1;                        // half-width of omega' (p/2 - 1, or the exact-interpolation truncation)
+  std::vector<double> omh;           // omega'_0 .. omega'_hw (symmetric)
   int B[3];                          // radius of the ball-kernel stencil: S (raw samples, p = 4) or R (K)
   bool prefilter = false;            // ball kernels apply raw samples to the omega'-prefiltered grid
   int C[3];

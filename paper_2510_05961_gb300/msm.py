@@ -32,11 +32,11 @@ class Plan:
     """
 
     def __init__(self, cell, pbc, h, cutoff, order=4, levels=0, grid_override=(0, 0, 0), max_atoms=1,
-                 device=None):
+                 device=None, qi_mode=0):
         self.lib = L.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
-            self.params = L.make_params(cell, pbc, h, cutoff, order, levels, grid_override, max_atoms)
+            self.params = L.make_params(cell, pbc, h, cutoff, order, levels, grid_override, max_atoms, qi_mode)
             h_ = C.c_void_p()
             L.check(self.lib.msm_plan_create(C.byref(self.params), C.byref(h_)))
             self.handle = h_
@@ -191,7 +191,7 @@ class Batch:
         self.counts = []
         for i, s in enumerate(systems):
             arr[i] = L.make_params(s.cell, s.pbc, s.h, s.a, s.p, getattr(s, "levels", 0),
-                                   getattr(s, "grid_override", (0, 0, 0)), 0)
+                                   getattr(s, "grid_override", (0, 0, 0)), 0, getattr(s, "qi_mode", 0))
             counts[i] = int(s.n)
             self.counts.append(int(s.n))
         with torch.cuda.device(self.device):

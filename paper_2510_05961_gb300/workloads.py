@@ -34,6 +34,7 @@ class Workload:
     p: int                       # B-spline order
     levels: int = 0              # 0 = planner's rule
     grid_override: tuple = (0, 0, 0)
+    qi_mode: int = 0             # 0 = minimal quasi-interpolation, 1 = exact interpolation
     meta: dict = field(default_factory=dict)
 
     @property

@@ -42,7 +42,7 @@ def _describe(lib, w=None, **kw):
         kw = dict(cell=w.cell, pbc=w.pbc, h=w.h, cutoff=w.a, order=w.p, levels=w.levels,
                   grid_override=w.grid_override)
     P = _lib.make_params(kw["cell"], kw["pbc"], kw["h"], kw["cutoff"], kw["order"], kw.get("levels", 0),
-                         kw.get("grid_override", (0, 0, 0)), 1)
+                         kw.get("grid_override", (0, 0, 0)), 1, kw.get("qi_mode", 0))
     I = _lib.PlanInfo()
     rc = lib.msm_plan_describe(C.byref(P), C.byref(I))
     return rc, I, P
@@ -61,15 +61,19 @@ CASES = [
     dict(cell=(17.0, 23.0, 29.0), pbc=(0, 0, 0), h=1.3, cutoff=4.5, order=8),
     dict(cell=(1.0, 1.0, 1.0), pbc=(1, 1, 1), h=0.0, cutoff=2.0, order=6, grid_override=(16, 16, 16)),
     dict(cell=(12.0, 12.0, 12.0), pbc=(0, 0, 0), h=1.0, cutoff=3.0, order=4, levels=1),
+    # exact interpolation (qi_mode 1): wide omega', dense boxes on every level
+    dict(cell=(30, 30, 30), pbc=(0, 0, 0), h=2.5, cutoff=10.0, order=4, levels=3, qi_mode=1),
+    dict(cell=(8.0, 8.0, 8.0), pbc=(1, 1, 1), h=2.0, cutoff=2.0, order=6, qi_mode=1),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s_%s_p%d" % (c["pbc"], c["cell"][0], c["order"]))
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s_%s_p%d_qi%d" % (c["pbc"], c["cell"][0], c["order"],
+                                                                          c.get("qi_mode", 0)))
 def test_planner_matches_oracle(lib, oracle, case):
     rc, I, _ = _describe(lib, **case)
     assert rc == 0, lib.msm_last_error()
     P = oracle.make_plan(case["cell"], case["pbc"], case["h"], case["cutoff"], case["order"], case.get("levels", 0),
-                         case.get("grid_override", (0, 0, 0)))
+                         case.get("grid_override", (0, 0, 0)), case.get("qi_mode", 0))
     s = oracle.plan_summary(P)
     assert I.nlev == s["nlev"] and I.ncomp == s["ncomp"]
     assert list(I.M) == s["M"]
@@ -99,18 +103,22 @@ def _fold(K, lo, n, pbc):
     return out
 
 
-@pytest.mark.parametrize("case", CASES[:2] + CASES[4:9] + CASES[10:], ids=lambda c: "%s_%s" % (c["pbc"], c["cell"][0]))
+@pytest.mark.parametrize("case", CASES[:2] + CASES[4:9] + CASES[10:],
+                         ids=lambda c: "%s_%s_qi%d" % (c["pbc"], c["cell"][0], c.get("qi_mode", 0)))
 def test_stencils_match_oracle(lib, oracle, case):
     rc, I, Pl = _describe(lib, **case)
     P = oracle.make_plan(case["cell"], case["pbc"], case["h"], case["cutoff"], case["order"], case.get("levels", 0),
-                         case.get("grid_override", (0, 0, 0)))
+                         case.get("grid_override", (0, 0, 0)), case.get("qi_mode", 0))
+    # every library query rebuilds the plan; the wide exact-interpolation stencils
+    # are checked on K and two derivative components to keep the CPU suite short
+    whiches = range(7) if case.get("qi_mode", 0) == 0 else (0, 1, 4)
     for l in range(1, I.ncomp + 1):
-        ref = [oracle.stencil(P, l, which)[0] for which in range(7)]
+        ref = {which: oracle.stencil(P, l, which)[0] for which in range(7)}
         # tolerance: float32 rounding of the stored values, relative to the
         # largest entry of the stencil (which 0) or of the six derivatives
         scale_k = np.abs(ref[0]).max()
-        scale_d = max(np.abs(r).max() for r in ref[1:])
-        for which in range(7):
+        scale_d = max(np.abs(ref[w]).max() for w in range(1, 7))
+        for which in whiches:
             K, lo = _lib_stencil(lib, Pl, l, which)
             Kf = _fold(K, lo, P.level_shape(l), case["pbc"])
             assert Kf.shape == ref[which].shape, (l, which)

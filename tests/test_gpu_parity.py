@@ -7,6 +7,7 @@ Intermediate grids are compared to the oracle's to 1e-4 of the largest
 entry of the level-1 grid (each level's potential is prolonged onto level 1
 with weights <= 1, so that is the scale its FP32 rounding matters on).
 """
+import dataclasses
 import functools
 
 import numpy as np
@@ -38,7 +39,8 @@ def rel_rms(a, b):
 
 
 def make_plan(w, n=None):
-    return Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=n or w.n, device=DEV)
+    return Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=n or w.n, device=DEV,
+                qi_mode=w.qi_mode)
 
 
 def gpu_run(w, plan=None, forces=True, virial=True):
@@ -73,6 +75,9 @@ WORKLOADS = {
     "tiny_open_25": lambda: W.random_box(25, density=0.08, seed=35, pbc=(0, 0, 0)),
     "rocksalt_6": lambda: W.rocksalt(ncell=6, seed=36),
     "open_p8": lambda: W.open_cluster(n=700, side=24.0, seed=37, h=1.6, a=6.0, p=8, levels=0),
+    # exact interpolation of the grid kernels (qi_mode 1): dense boxes on every level
+    "open_qi1": lambda: dataclasses.replace(W.open_cluster(n=400, seed=38), qi_mode=1),
+    "periodic_qi1": lambda: dataclasses.replace(W.random_box(300, seed=39, h=2.0, a=4.0), qi_mode=1),
 }
 
 
