@@ -150,28 +150,39 @@ class Plan:
 
 
 class MSMFunction(torch.autograd.Function):
-    """E = MSM energy of (pos, q); backward gives dE/dpos, dE/dq; plan.last_virial holds W * dL/dE."""
+    """(E, phi, F) of (pos, q) through the library; backward gives dE/dpos and
+    dE/dq scaled by the upstream gradient of E, and plan.last_virial holds
+    W * dL/dE. Upstream gradients on phi or F (second-order terms) are not
+    implemented: a nonzero one raises NotImplementedError."""
 
     @staticmethod
     def forward(ctx, pos, q, plan):
-        need_f = pos.requires_grad
-        E, _, _ = plan.forward(pos.detach().contiguous(), q.detach().contiguous(), forces=need_f, virial=True,
-                               phi=False)
+        ctx.set_materialize_grads(False)
+        E, phi, F = plan.forward(pos.detach().contiguous(), q.detach().contiguous(), forces=True, virial=True,
+                                 phi=True)
         ctx.plan = plan
         ctx.need = (pos.requires_grad, q.requires_grad)
-        return E.reshape(())
+        return E.reshape(()), phi, F
 
     @staticmethod
-    def backward(ctx, gE):
+    def backward(ctx, gE, gphi, gF):
+        for name, g in (("phi", gphi), ("forces", gF)):
+            if g is not None and bool((g != 0).any()):
+                raise NotImplementedError("gradients through the MSM %s output are not implemented "
+                                          "(second-order terms); differentiate E only" % name)
         if gE is None:
             return None, None, None
-        plan = ctx.plan
-        gp, gq, _ = plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
+        gp, gq, _ = ctx.plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
         return gp, gq, None
 
 
 def msm_energy(pos, q, plan):
     """Differentiable MSM energy (autograd through the library's adjoint kernels)."""
+    return MSMFunction.apply(pos, q, plan)[0]
+
+
+def msm_outputs(pos, q, plan):
+    """(E, phi, F); E is differentiable, phi and F are not (their upstream must be zero)."""
     return MSMFunction.apply(pos, q, plan)
 
 

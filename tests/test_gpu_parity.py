@@ -166,6 +166,26 @@ def test_autograd_function():
     assert np.abs(Wv - 3.0 * ref["W"]).max() <= F_TOL * 3.0 * np.abs(ref["W"]).max()
 
 
+def test_autograd_outputs_phi_and_forces():
+    # (E, phi, F) from the autograd function: phi and F match the plain forward; a
+    # loss on E alone differentiates, an upstream gradient on phi or F is refused
+    from paper_2510_05961_gb300 import msm_outputs
+    key = "rocksalt_6"
+    w = WORKLOADS[key]()
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV).requires_grad_(True)
+    q = torch.from_numpy(w.q).to(DEV).requires_grad_(True)
+    E, phi, F = msm_outputs(pos, q, plan)
+    P, ref = _oracle(key)
+    assert rel_rms(phi.detach().cpu().numpy(), ref["phi"]) <= F_TOL
+    assert rel_rms(F.detach().cpu().numpy(), ref["F"]) <= F_TOL
+    E.backward()
+    assert rel_rms(q.grad.cpu().numpy(), ref["phi"]) <= F_TOL
+    E2, phi2, F2 = msm_outputs(pos, q, plan)
+    with pytest.raises(NotImplementedError):
+        (E2 + phi2.sum()).backward()
+
+
 def test_finite_differences_on_gpu():
     # central differences of the GPU energy (FP32 inputs, FP64 energy) for a few atoms
     w = W.rocksalt(ncell=4, seed=40)
