@@ -225,16 +225,21 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- batched systems
-def batch_bench(dev, nsys, steps, warmup):
+def batch_bench(dev, nsys, steps, warmup, rank=0, world=1):
     """512 independent systems (log-uniform 20-4000 atoms, open / slab / periodic):
     forward + backward of the whole batch as one captured CUDA graph, against a
-    loop of single-system forward + backward calls on the same systems."""
+    loop of single-system forward + backward calls on the same systems. With
+    several ranks each evaluates its shard of the systems (no collective)."""
     import torch
 
-    from paper_2510_05961_gb300 import Batch, Plan
+    from paper_2510_05961_gb300 import Batch, Plan, shard
     from paper_2510_05961_gb300 import workloads as W
 
     systems = W.batch_systems(nsys=nsys)
+    if world > 1:
+        parts, _ = shard.shard(systems, world)
+        systems = [systems[i] for i in parts[rank]]
+        nsys = len(systems)
     ntot = sum(s.n for s in systems)
     batch = Batch(systems, device=dev)
     pos = torch.from_numpy(__import__("numpy").concatenate([s.pos for s in systems])).to(dev)
@@ -425,8 +430,18 @@ def run_gpu(args):
             "algorithmic_flops": {"stencil": st_flops, "short": sr_flops}}
 
     batch_res = None
-    if rank == 0 and not args.no_batch:
-        batch_res = batch_bench(dev, args.batch_systems, max(args.steps, 5), args.warmup)
+    if not args.no_batch:
+        batch_res = batch_bench(dev, args.batch_systems, max(args.steps, 5), args.warmup, rank, world)
+        if world > 1:
+            # shards run independently; the batch's time is the slowest rank's
+            t = torch.tensor([batch_res["ms_batched_graph"], float(batch_res["atoms"])], device=dev)
+            tmax = t.clone()
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            batch_res = {"sharded": True, "ranks": world, "systems": args.batch_systems, "atoms": int(t[1].item()),
+                         "ms_batched_graph_max_over_ranks": float(tmax[0].item()),
+                         "atoms_per_s_batched": float(t[1].item()) / (float(tmax[0].item()) / 1e3),
+                         "rank0_speedup_vs_single_calls": batch_res["speedup"], "workload": batch_res["workload"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
