@@ -108,6 +108,8 @@ typedef struct {
   int C[3];          /* binning cells per axis */
   int nnbr[3];       /* neighbour-cell reach per axis */
   int stencil_kind[20]; /* 0 = ball stencil with wrap/zero, 1 = dense folded box */
+  int anterp_tz;     /* anterpolation tile z-extent in use (16, 32, 64; msm_autotune) */
+  int short_block;   /* short-range threads per block in use (128, 256; msm_autotune) */
 } msm_plan_info;
 
 /* Create a plan: validates the settings synchronously, builds the level
@@ -162,6 +164,22 @@ int msm_forward(msm_plan plan, void* workspace, size_t workspace_bytes, int n, c
  * computed here. Returns MSM_ERR_NO_FORWARD without a prior forward. */
 int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,
                  double* virial, void* stream);
+
+/* Autotuner (no counterpart in the paper, whose JAX code leaves launch shapes
+ * to XLA): runs one forward on (n, pos, q) to fill workspace, then times each
+ * tunable launch shape on those inputs and keeps the fastest for every later
+ * call on this plan: the z-extent of the anterpolation tiles (16, 32, 64
+ * level-1 points) and the short-range threads per block (256, or 128 = two
+ * blocks per 256-atom item). Arguments as msm_forward. Synchronises stream
+ * (not capturable into a graph); afterwards msm_backward needs a new
+ * msm_forward. The choices are reported by msm_plan_get_info. */
+int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos, const float* q,
+                 void* stream);
+
+/* Sets the tuned launch shapes directly (for callers that keep earlier
+ * msm_autotune results): anterp_tz in {16, 32, 64}, short_block in {128, 256};
+ * MSM_ERR_INVALID_ARG otherwise. Host-side; affects the next calls. */
+int msm_set_tuning(msm_plan plan, int anterp_tz, int short_block);
 
 /* Synchronises stream and returns the device status word (MSM_DEV_* bits)
  * of the last call on workspace in *device_status (host). */
@@ -233,6 +251,11 @@ int msm_batch_forward(msm_batch batch, void* workspace, size_t workspace_bytes, 
 int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_energy, float* dE_dpos,
                        float* dE_dq, double* virial, void* stream);
 int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status);
+/* msm_autotune for a batch (all systems share the tuned shapes), and the shapes in use. */
+int msm_batch_autotune(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,
+                       void* stream);
+int msm_batch_set_tuning(msm_batch batch, int anterp_tz, int short_block);
+int msm_batch_get_tuning(msm_batch batch, int* anterp_tz, int* short_block);
 
 #ifdef __cplusplus
 }

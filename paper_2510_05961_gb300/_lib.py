@@ -29,7 +29,8 @@ EXPORTS = [
     "msm_workspace_bytes", "msm_forward",
     "msm_backward", "msm_status", "msm_debug_offset", "msm_last_error", "msm_batch_create", "msm_batch_destroy",
     "msm_batch_workspace_bytes", "msm_batch_forward", "msm_batch_backward", "msm_batch_status", "msm_profile",
-    "msm_profile_read", "msm_forward_noalloc",
+    "msm_profile_read", "msm_forward_noalloc", "msm_autotune", "msm_batch_autotune", "msm_batch_get_tuning",
+    "msm_set_tuning", "msm_batch_set_tuning",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 PHASES = ["bin", "short", "anterp", "restrict", "stencil", "prolong", "interp", "final", "virial", "bscale"]
@@ -50,7 +51,8 @@ class Params(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("nlev", C.c_int), ("ncomp", C.c_int), ("M", C.c_int * 3), ("h1", C.c_double * 3),
                 ("lo", (C.c_int * 3) * 20), ("n", (C.c_int * 3) * 20), ("R", C.c_int * 3), ("C", C.c_int * 3),
-                ("nnbr", C.c_int * 3), ("stencil_kind", C.c_int * 20)]
+                ("nnbr", C.c_int * 3), ("stencil_kind", C.c_int * 20), ("anterp_tz", C.c_int),
+                ("short_block", C.c_int)]
 
 
 _lib = None

@@ -77,7 +77,7 @@ __device__ __forceinline__ float bspline_value(float t, const float (&cf)[P / 2]
 }
 
 // Anterpolation by grid columns. A block owns a tile of 16 x 8 grid columns
-// (x, y) and kAnterpTZ points along z; each thread owns one column and sums,
+// (x, y) and TZ points along z (16, 32 or 64, chosen by the autotuner); each thread owns one column and sums,
 // over the atoms of the cells whose B-spline support reaches that column,
 // q_i Phi(m_x - u_x) Phi(m_y - u_y) times the p weights of the atom's z-base
 // into a private z-array in shared memory (u: atom position in level-1 grid
@@ -89,14 +89,14 @@ __device__ __forceinline__ float bspline_value(float t, const float (&cf)[P / 2]
 constexpr int kAntNT = kAnterpTX * kAnterpTY;
 static_assert(kAnterpTX == 16 && kAnterpTY == 8, "one parity class of 8 x 4 columns per warp");
 
-template <int P>
+template <int P, int TZ>
 __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                   const TileItem* __restrict__ items,
                                                   const int* __restrict__ cell_start,
                                                   const float4* __restrict__ uq, float* __restrict__ grid) {
   constexpr int H = P / 2;
   constexpr int PAD = P - 1;
-  constexpr int NZ = kAnterpTZ + 2 * PAD;
+  constexpr int NZ = TZ + 2 * PAD;
   __shared__ float col[NZ][kAntNT];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__
   for (int i = 0; i < H; i++)
 #pragma unroll
     for (int k = 0; k < P; k++) cf[i][k] = S.bsp[i][k];
-  const int zlen = min(kAnterpTZ, L.n[2] - it.z0);
+  const int zlen = min(TZ, L.n[2] - it.z0);
   // grid indices of this column and of the tile's z-range; atom cell ranges
   const int m[3] = {gx + L.lo[0], gy + L.lo[1], it.z0 + L.lo[2]};
   const int mhi[3] = {m[0], m[1], m[2] + zlen - 1};
@@ -235,12 +235,20 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
   }
 }
 
-void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p) {
+template <int P>
+static void run_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int tz) {
+  if (tz == 16) k_anterp<P, 16><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
+  else if (tz == 64) k_anterp<P, 64><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
+  else k_anterp<P, 32><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
+}
+
+// tz: the z-extent of the tiles the items were built for (16, 32 or 64)
+void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p, int tz) {
   if (nitems <= 0) return;
   switch (p) {
-    case 4: k_anterp<4><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
-    case 6: k_anterp<6><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
-    default: k_anterp<8><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid); break;
+    case 4: run_anterp<4>(w, t, items, nitems, s, tz); break;
+    case 6: run_anterp<6>(w, t, items, nitems, s, tz); break;
+    default: run_anterp<8>(w, t, items, nitems, s, tz); break;
   }
 }
 

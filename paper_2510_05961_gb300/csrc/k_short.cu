@@ -37,15 +37,20 @@ __device__ __forceinline__ float image_shift(int k, double L, float z) {
   return (float)(k * L - (double)z);
 }
 
-template <int P, bool WF, bool WW>
-__global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
-                                                  const int* __restrict__ cell_start, const int* __restrict__ scell,
-                                                  const float4* __restrict__ xq, float* __restrict__ phi_sr,
-                                                  float4* __restrict__ f_sr, double* __restrict__ part_w0) {
-  AtomItem it = items[blockIdx.x];
+// NB threads per block: NB = kChunk (one block per atom item) or kChunk / 2
+// (two blocks per item), chosen by the autotuner
+template <int P, bool WF, bool WW, int NB>
+__global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                                              const int* __restrict__ cell_start, const int* __restrict__ scell,
+                                              const float4* __restrict__ xq, float* __restrict__ phi_sr,
+                                              float4* __restrict__ f_sr, double* __restrict__ part_w0) {
+  constexpr int NSPLIT = kChunk / NB;
+  const int item = blockIdx.x / NSPLIT, part = blockIdx.x % NSPLIT;
+  AtomItem it = items[item];
   const SysDev& S = sys[it.sys];
-  int local = it.start + threadIdx.x;
-  bool active = (int)threadIdx.x < it.count && local < S.n;
+  const int slot = part * NB + (int)threadIdx.x;  // atom of the item
+  int local = it.start + slot;
+  bool active = slot < it.count && local < S.n;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (active) {
     const int k = S.atom_off + local;
@@ -135,29 +140,38 @@ __global__ void __launch_bounds__(kChunk) k_short(const SysDev* __restrict__ sys
   }
   if (!WW) return;
   // per-warp FP64 partials of the six virial components (fixed order, no block barrier)
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = slot >> 5;
 #pragma unroll
   for (int c = 0; c < 6; c++) {
     double v = (double)w6[c];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) part_w0[6 * ((long long)blockIdx.x * kChunkWarps + wid) + c] = v;
+    if (lane == 0) part_w0[6 * ((long long)item * kChunkWarps + wid) + c] = v;
   }
+}
+
+template <int P, int NB>
+static void run_short_nb(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
+                         cudaStream_t s) {
+  auto kern = virial ? (forces ? k_short<P, true, true, NB> : k_short<P, false, true, NB>)
+                     : (forces ? k_short<P, true, false, NB> : k_short<P, false, false, NB>);
+  kern<<<nitems * (kChunk / NB), NB, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr,
+                                             w.part_w0);
 }
 
 template <int P>
 static void run_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
-                      cudaStream_t s) {
-  auto kern = virial ? (forces ? k_short<P, true, true> : k_short<P, false, true>)
-                     : (forces ? k_short<P, true, false> : k_short<P, false, false>);
-  kern<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.phi_sr, w.f_sr, w.part_w0);
+                      cudaStream_t s, int block) {
+  if (block == kChunk / 2) run_short_nb<P, kChunk / 2>(w, t, items, nitems, forces, virial, s);
+  else run_short_nb<P, kChunk>(w, t, items, nitems, forces, virial, s);
 }
 
+// block: threads per block, kChunk or kChunk / 2
 void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
-                  cudaStream_t s, int p) {
+                  cudaStream_t s, int p, int block) {
   switch (p) {
-    case 4: run_short<4>(w, t, items, nitems, forces, virial, s); break;
-    case 6: run_short<6>(w, t, items, nitems, forces, virial, s); break;
-    default: run_short<8>(w, t, items, nitems, forces, virial, s); break;
+    case 4: run_short<4>(w, t, items, nitems, forces, virial, s, block); break;
+    case 6: run_short<6>(w, t, items, nitems, forces, virial, s, block); break;
+    default: run_short<8>(w, t, items, nitems, forces, virial, s, block); break;
   }
 }
 

@@ -83,12 +83,12 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   cudaStreamWaitEvent(E.side, E.ev_fork, 0);
   {
     Phase ph(E, MSM_PH_SHORT, E.side);
-    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, E.side, E.p);
+    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, E.side, E.p, E.short_block);
   }
   cudaEventRecord(E.ev_join, E.side);
   {
     Phase ph(E, MSM_PH_ANTERP, s);
-    launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p);
+    launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz);
   }
   {
     Phase ph(E, MSM_PH_RESTRICT, s);
@@ -147,7 +147,7 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
     // the forward skipped these parts; the short-range kernel rewrites its
     // potential with identical values, so running it again is safe
     Phase ph(E, MSM_PH_SHORT, s);
-    launch_short(w, t, E.d_atom_items, nai, need_f || had_f, need_w || had_w, s, E.p);
+    launch_short(w, t, E.d_atom_items, nai, need_f || had_f, need_w || had_w, s, E.p, E.short_block);
     nl++;
     if (need_f && !had_f) {
       launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
@@ -170,6 +170,62 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   }
   E.launches_bwd = nl;
   return check_launch("msm_backward");
+}
+
+// Autotuner: one forward fills the workspace (bins, sorted atoms, level-1
+// grid), then each tunable launch shape is timed on those inputs (CUDA events,
+// one warm-up and three timed launches per candidate) and the fastest is kept.
+// Each shape belongs to one kernel, so the shapes are tuned independently.
+static int run_autotune(Engine& E, void* ws, size_t ws_bytes, int n_single, const float* pos, const float* q,
+                        cudaStream_t s) {
+  if (!E.d_energy_scratch && cudaMalloc((void**)&E.d_energy_scratch, sizeof(double) * std::max(E.nsys, 1)) != cudaSuccess)
+    return set_err(MSM_ERR_CUDA, "autotune: cudaMalloc failed");
+  int rc = run_forward(E, ws, ws_bytes, n_single, pos, q, E.d_energy_scratch, nullptr, nullptr, 0, s);
+  if (rc) return rc;
+  Work w = E.resolve(ws);
+  Tables t = E.tables();
+  const int nai = (int)E.atom_items.size();
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    return set_err(MSM_ERR_CUDA, "autotune: cudaEventCreate failed");
+  auto timed = [&](auto&& launch) {
+    launch();
+    cudaEventRecord(a, s);
+    for (int r = 0; r < 3; r++) launch();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  };
+  std::string err;
+  int best_tz = E.anterp_tz;
+  float best = 1e30f;
+  for (int tz : {16, 32, 64}) {
+    if ((rc = E.set_anterp_tz(tz, &err))) break;
+    const float ms = timed([&] { launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, tz); });
+    if (ms < best) {
+      best = ms;
+      best_tz = tz;
+    }
+  }
+  if (!rc) rc = E.set_anterp_tz(best_tz, &err);
+  int best_nb = E.short_block;
+  best = 1e30f;
+  if (!rc)
+    for (int nb : {kChunk, kChunk / 2}) {
+      const float ms = timed([&] { launch_short(w, t, E.d_atom_items, nai, true, true, s, E.p, nb); });
+      if (ms < best) {
+        best = ms;
+        best_nb = nb;
+      }
+    }
+  E.short_block = best_nb;
+  E.have_fwd = false;  // the timed launches reused the workspace: a new forward is needed
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return set_err(rc, "autotune: " + err);
+  return check_launch("msm_autotune");
 }
 
 static int read_status(Engine& E, void* ws, cudaStream_t s, int* out) {
@@ -257,6 +313,8 @@ int msm_plan_destroy(msm_plan plan) {
 int msm_plan_get_info(msm_plan plan, msm_plan_info* info) {
   if (!plan || !info) return set_err(MSM_ERR_INVALID_ARG, "plan and info must not be NULL");
   fill_info(plan->eng.sys[0], info);
+  info->anterp_tz = plan->eng.anterp_tz;
+  info->short_block = plan->eng.short_block;
   return MSM_OK;
 }
 
@@ -326,6 +384,28 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
   return run_backward(plan->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
 }
 
+int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos, const float* q,
+                 void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  if (n < 0 || n > plan->eng.total_atoms) return set_err(MSM_ERR_CAPACITY, "n outside [0, max_atoms]");
+  return run_autotune(plan->eng, workspace, workspace_bytes, n, pos, q, (cudaStream_t)stream);
+}
+
+static int set_tuning(Engine& E, int anterp_tz, int short_block) {
+  if (short_block != kChunk && short_block != kChunk / 2)
+    return set_err(MSM_ERR_INVALID_ARG, "short_block must be 128 or 256");
+  std::string err;
+  int rc = E.set_anterp_tz(anterp_tz, &err);
+  if (rc) return set_err(rc, err);
+  E.short_block = short_block;
+  return MSM_OK;
+}
+
+int msm_set_tuning(msm_plan plan, int anterp_tz, int short_block) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  return set_tuning(plan->eng, anterp_tz, short_block);
+}
+
 int msm_status(msm_plan plan, void* workspace, void* stream, int* device_status) {
   if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
   return read_status(plan->eng, workspace, (cudaStream_t)stream, device_status);
@@ -388,6 +468,24 @@ int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_ener
                        double* virial, void* stream) {
   if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
   return run_backward(batch->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
+}
+
+int msm_batch_autotune(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,
+                       void* stream) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return run_autotune(batch->eng, workspace, workspace_bytes, -1, pos, q, (cudaStream_t)stream);
+}
+
+int msm_batch_set_tuning(msm_batch batch, int anterp_tz, int short_block) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return set_tuning(batch->eng, anterp_tz, short_block);
+}
+
+int msm_batch_get_tuning(msm_batch batch, int* anterp_tz, int* short_block) {
+  if (!batch || !anterp_tz || !short_block) return set_err(MSM_ERR_INVALID_ARG, "NULL argument");
+  *anterp_tz = batch->eng.anterp_tz;
+  *short_block = batch->eng.short_block;
+  return MSM_OK;
 }
 
 int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status) {

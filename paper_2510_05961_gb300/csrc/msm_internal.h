@@ -15,7 +15,7 @@ namespace msm {
 constexpr int kMaxLev = 20;
 constexpr int kChunk = 256;        // atoms per per-atom work item
 constexpr int kChunkWarps = kChunk / 32;
-constexpr int kAnterpTX = 16, kAnterpTY = 8, kAnterpTZ = 32;  // anterpolation tile (grid points)
+constexpr int kAnterpTX = 16, kAnterpTY = 8;  // anterpolation tile columns (x, y); its z-extent is tuned
 constexpr int kBallTY = 32;        // stencil tile rows (y)
 constexpr int kBallBZ = 16;        // outputs per thread along z
 constexpr int kBallTZ = 32;        // stencil tile depth (z)
@@ -124,9 +124,9 @@ void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitem
                 int total_atoms, const float* pos, const float* q, cudaStream_t s);
 // short range (k_short.cu)
 void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
-                  cudaStream_t s, int p);
+                  cudaStream_t s, int p, int block);
 // anterpolation / interpolation (k_interp.cu)
-void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p);
+void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p, int tz);
 void launch_interp(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces,
                    cudaStream_t s, int p);
 // restriction / prolongation (k_grid.cu)

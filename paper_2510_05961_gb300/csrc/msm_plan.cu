@@ -697,10 +697,6 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     for (int l = 1; l <= S.ncomp; l++) {
       int li = hs[s].lev0 + l - 1;
       const LevDev& L = hlev[li];
-      if (l == 1)
-        for (int x = 0; x < L.n[0]; x += kAnterpTX)
-          for (int y = 0; y < L.n[1]; y += kAnterpTY)
-            for (int z = 0; z < L.n[2]; z += kAnterpTZ) anterp_items.push_back({li, x, y, z});
       if (L.kind == 0) {
         for (int x = 0; x < L.n[0]; x++)
           for (int y = 0; y < L.n[1]; y += kBallTY)
@@ -743,6 +739,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     voff[nsys + 1 + s] = (int)ball_items.size() + vx_off[s];
   }
   hsys = hs;
+  build_anterp_items(anterp_tz);
   int rc = upload(kp, wp, voff, err);
   if (rc) return rc;
   // workspace layout
@@ -780,11 +777,34 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
 
 template <class T>
 static int up(const std::vector<T>& h, T** d, std::string* err) {
+  cudaFree(*d);
+  *d = nullptr;
   size_t b = sizeof(T) * std::max<size_t>(h.size(), 1);
   if (cudaMalloc((void**)d, b) != cudaSuccess) return fail(err, MSM_ERR_CUDA, "cudaMalloc of plan tables failed");
   if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(err, MSM_ERR_CUDA, "cudaMemcpy of plan tables failed");
   return MSM_OK;
+}
+
+// anterpolation tiles of kAnterpTX x kAnterpTY x tz level-1 points (tz = 16, 32, 64)
+void Engine::build_anterp_items(int tz) {
+  anterp_items.clear();
+  for (int s = 0; s < nsys; s++) {
+    if (sys[s].ncomp < 1) continue;
+    const int li = hsys[s].lev0;
+    const LevDev& L = hlev[li];
+    for (int x = 0; x < L.n[0]; x += kAnterpTX)
+      for (int y = 0; y < L.n[1]; y += kAnterpTY)
+        for (int z = 0; z < L.n[2]; z += tz) anterp_items.push_back({li, x, y, z});
+  }
+  anterp_tz = tz;
+}
+
+int Engine::set_anterp_tz(int tz, std::string* err) {
+  if (tz != 16 && tz != 32 && tz != 64) return fail(err, MSM_ERR_INVALID_ARG, "anterpolation tile must be 16, 32 or 64");
+  if (tz == anterp_tz) return MSM_OK;
+  build_anterp_items(tz);
+  return up(anterp_items, &d_anterp_items, err);
 }
 
 int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, const std::vector<int>& voff,
@@ -844,6 +864,7 @@ Engine::~Engine() {
   cudaFree(d_voff);
   cudaFree(d_range_items);
   cudaFree(d_pro_items);
+  cudaFree(d_energy_scratch);
 }
 
 Work Engine::resolve(void* ws) const {

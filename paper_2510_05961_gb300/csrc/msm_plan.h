@@ -108,6 +108,13 @@ struct Engine {
   int build(const msm_params* prm, const int* counts, int nsys, bool single, std::string* err);
   int upload(const std::vector<float>& kp, const std::vector<int>& wp, const std::vector<int>& voff,
              std::string* err);
+  // tuned launch shapes (msm_autotune): anterpolation tile z-extent and
+  // short-range threads per block
+  int anterp_tz = 32;
+  int short_block = kChunk;
+  double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
+  void build_anterp_items(int tz);
+  int set_anterp_tz(int tz, std::string* err);
   Work resolve(void* ws) const;
   Tables tables() const;
 };

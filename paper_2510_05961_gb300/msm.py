@@ -64,6 +64,7 @@ class Plan:
             "lo": [list(I.lo[l]) for l in range(I.ncomp)], "n": [list(I.n[l]) for l in range(I.ncomp)],
             "R": list(I.R), "C": list(I.C), "nnbr": list(I.nnbr),
             "stencil_kind": [I.stencil_kind[l] for l in range(I.ncomp)],
+            "anterp_tz": I.anterp_tz, "short_block": I.short_block,
         }
 
     def debug_array(self, which, level=1):
@@ -103,6 +104,19 @@ class Plan:
             W = W.view(3, 3)
             self.last_virial = W
         return gp, gq, W
+
+    def autotune(self, pos, q):
+        """Time the tunable launch shapes on these inputs and keep the fastest; returns them.
+        A new forward is needed before the next backward."""
+        n = int(pos.shape[0])
+        assert pos.dtype == torch.float32 and q.dtype == torch.float32 and pos.is_contiguous() and q.is_contiguous()
+        L.check(self.lib.msm_autotune(self.handle, _ptr(self.workspace), self.workspace.numel(), n, _ptr(pos), _ptr(q),
+                                      _stream(self.device)))
+        info = self.info()
+        return {"anterp_tz": info["anterp_tz"], "short_block": info["short_block"]}
+
+    def set_tuning(self, anterp_tz=32, short_block=256):
+        L.check(self.lib.msm_set_tuning(self.handle, int(anterp_tz), int(short_block)))
 
     def status(self):
         st = C.c_int()
@@ -248,6 +262,18 @@ class Batch:
         L.check(self.lib.msm_batch_backward(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gp), _ptr(gq), _ptr(W),
                                             _stream(self.device)))
         return gp, gq, (None if W is None else W.view(self.nsys, 3, 3))
+
+    def set_tuning(self, anterp_tz=32, short_block=256):
+        L.check(self.lib.msm_batch_set_tuning(self.handle, int(anterp_tz), int(short_block)))
+
+    def autotune(self, pos, q):
+        """Time the tunable launch shapes on this batch's inputs and keep the fastest; returns them.
+        A new forward is needed before the next backward; call it before capturing a graph."""
+        L.check(self.lib.msm_batch_autotune(self.handle, _ptr(self.workspace), self.workspace.numel(), _ptr(pos), _ptr(q),
+                                            _stream(self.device)))
+        tz, nb = C.c_int(), C.c_int()
+        L.check(self.lib.msm_batch_get_tuning(self.handle, C.byref(tz), C.byref(nb)))
+        return {"anterp_tz": tz.value, "short_block": nb.value}
 
     def status(self):
         st = C.c_int()
