@@ -60,11 +60,10 @@ __global__ void k_energy(const SysDev* __restrict__ sys, const double* __restric
   }
 }
 
-// Virial reduction, stage 1: block (s, b) of a (nsys x kVirialSlices) grid sums
+// Virial reduction, stage 1: block (s, b) of a (nsys x nslice) grid sums
 // slice b of system s's partials (short-range per warp, then grid per tile)
 // in a fixed order; stage 2: one block per system sums its slices and scales
 // by g. Deterministic; the FP64 additions are spread over the whole GPU.
-constexpr int kVirialSlices = 64;
 
 __device__ __forceinline__ void block_sum6(double (&acc)[6], double (*red)[6], double* out) {
   for (int c = 0; c < 6; c++) {
@@ -85,13 +84,13 @@ __global__ void __launch_bounds__(256) k_virial_slices(const SysDev* __restrict_
                                                        const double* __restrict__ part_wg,
                                                        const int* __restrict__ vitem_off, double* __restrict__ slices) {
   __shared__ double red[8][6];
-  const int s = blockIdx.x, b = blockIdx.y, ns = gridDim.x;
+  const int s = blockIdx.x, b = blockIdx.y, ns = gridDim.x, nslice = gridDim.y;
   const SysDev& S = sys[s];
   const int n0 = S.nitem * kChunkWarps;
   const int nb = vitem_off[s + 1] - vitem_off[s];
   const int nx = vitem_off[ns + 1 + s + 1] - vitem_off[ns + 1 + s];
   const int total = n0 + nb + nx;
-  const int per = (total + kVirialSlices - 1) / kVirialSlices;
+  const int per = (total + nslice - 1) / nslice;
   const int lo = b * per, hi = min(total, lo + per);
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -101,15 +100,15 @@ __global__ void __launch_bounds__(256) k_virial_slices(const SysDev* __restrict_
     else src = part_wg + 6 * (long long)(vitem_off[ns + 1 + s] + (i - n0 - nb));
     for (int c = 0; c < 6; c++) acc[c] += src[c];
   }
-  block_sum6(acc, red, slices + 6 * ((long long)s * kVirialSlices + b));
+  block_sum6(acc, red, slices + 6 * ((long long)s * nslice + b));
 }
 
-__global__ void __launch_bounds__(64) k_virial_out(const double* __restrict__ slices,
+__global__ void __launch_bounds__(64) k_virial_out(const double* __restrict__ slices, int nslice,
                                                    const double* __restrict__ grad, double* __restrict__ virial) {
   __shared__ double red[2][6];
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const double* src = slices + 6 * (long long)blockIdx.x * kVirialSlices;
-  for (int i = threadIdx.x; i < kVirialSlices; i += blockDim.x)
+  const double* src = slices + 6 * (long long)blockIdx.x * nslice;
+  for (int i = threadIdx.x; i < nslice; i += blockDim.x)
     for (int c = 0; c < 6; c++) acc[c] += src[6 * i + c];
   __shared__ double w[6];
   block_sum6(acc, red, w);
@@ -158,10 +157,12 @@ void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cud
   k_energy<<<nsys, 256, 0, s>>>(t.sys, w.part_e, energy);
 }
 
-void launch_virial_out(const Work& w, const Tables& t, int nsys, const int* vitem_off, const double* grad,
-                       double* virial, cudaStream_t s) {
-  k_virial_slices<<<dim3(nsys, kVirialSlices), 256, 0, s>>>(t.sys, w.part_w0, w.part_wg, vitem_off, w.part_vs);
-  k_virial_out<<<nsys, 64, 0, s>>>(w.part_vs, grad, virial);
+// nslice (1 .. kVirialSlices) slices per system: about 1024 partials each for
+// the largest system, so small batches do not launch idle blocks
+void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, const int* vitem_off,
+                       const double* grad, double* virial, cudaStream_t s) {
+  k_virial_slices<<<dim3(nsys, nslice), 256, 0, s>>>(t.sys, w.part_w0, w.part_wg, vitem_off, w.part_vs);
+  k_virial_out<<<nsys, 64, 0, s>>>(w.part_vs, nslice, grad, virial);
 }
 
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,

@@ -160,7 +160,7 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
     const int nb = (int)E.ball_items.size();
     launch_virial_ball(w, t, E.d_ball_items, nb, E.rmax, E.ryz, 0, E.p == 4, s);
     launch_virial_box(w, t, E.d_box_items, (int)E.box_items.size(), nb, s);
-    launch_virial_out(w, t, E.nsys, E.d_voff, grad, virial, s);
+    launch_virial_out(w, t, E.nsys, E.vslices, E.d_voff, grad, virial, s);
     nl += (nb ? 1 : 0) + (E.box_items.empty() ? 0 : 1) + 2;
   }
   if (dE_dpos || dE_dq) {

@@ -23,6 +23,7 @@ constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
 constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
 constexpr int kGridChunk = 256;    // coarse points per restriction item
+constexpr int kVirialSlices = 64;  // most virial reduction slices per system
 constexpr int kProTX = 4, kProTY = 4, kProTZ = 32;  // prolongation tiles (fine points)
 constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)
 
@@ -145,8 +146,8 @@ void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, i
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
                      float* forces, cudaStream_t s);
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);
-void launch_virial_out(const Work& w, const Tables& t, int nsys, const int* vitem_off, const double* grad,
-                       double* virial, cudaStream_t s);
+void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, const int* vitem_off,
+                       const double* grad, double* virial, cudaStream_t s);
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
 

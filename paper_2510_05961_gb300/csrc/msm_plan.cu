@@ -740,6 +740,15 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   }
   hsys = hs;
   build_anterp_items(anterp_tz);
+  {
+    // virial partials of the largest system: per-warp short-range items plus ball and box items
+    long long most = 0;
+    for (int s = 0; s < nsys; s++) {
+      long long tot = (long long)hs[s].nitem * kChunkWarps + (vb_off[s + 1] - vb_off[s]) + (vx_off[s + 1] - vx_off[s]);
+      most = std::max(most, tot);
+    }
+    vslices = (int)std::min<long long>(kVirialSlices, std::max<long long>(1, (most + 1023) / 1024));
+  }
   int rc = upload(kp, wp, voff, err);
   if (rc) return rc;
   // workspace layout

@@ -110,6 +110,7 @@ struct Engine {
              std::string* err);
   // tuned launch shapes (msm_autotune): anterpolation tile z-extent and
   // short-range threads per block
+  int vslices = 1;                  // virial reduction slices per system (k_virial_slices)
   int anterp_tz = 32;
   int short_block = kChunk;
   double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
