@@ -117,9 +117,12 @@ def stencil_flops(plan_params, info, cell, a, p):
     """Algorithmic FLOPs of one stencil phase.
 
     Ball levels apply the raw kernel samples s (nonzero for |h_1 o n| < 2a) to
-    the omega'-prefiltered grid: 2 x points x nnz(s), plus the prefilter,
-    2 x (p-1)^3 per padded point. Box levels apply the folded stencil:
-    2 x points x its nonzeros."""
+    the omega'-prefiltered grid. s is even in x and in y, so per output the
+    input rows (x0 -+ dx, y -+ dy) are first summed, (multiplicity - 1) adds
+    per nonempty column of the quarter dx, dy >= 0, and each quarter sample
+    then takes one FMA: points x (2 nnz_quarter + sum (mult - 1)), plus the
+    prefilter, 2 x (p-1)^3 per padded point. Box levels apply the folded
+    stencil: 2 x points x its nonzeros."""
     import ctypes as C
 
     import numpy as np
@@ -131,14 +134,20 @@ def stencil_flops(plan_params, info, cell, a, p):
     assert p == 4, "ball levels apply raw samples (and prefilter) for p = 4 only"
     g = [np.arange(-S[d], S[d] + 1) * h1[d] for d in range(3)]
     r2 = g[0][:, None, None] ** 2 + g[1][None, :, None] ** 2 + g[2][None, None, :] ** 2
-    nnz_s = int(np.count_nonzero(r2 < (2 * a) ** 2))
+    inside = r2 < (2 * a) ** 2
+    quarter = inside[S[0]:, S[1]:, :]                      # dx >= 0, dy >= 0
+    cols = quarter.any(axis=2)
+    mult = np.ones(cols.shape)
+    mult[1:, :] *= 2
+    mult[:, 1:] *= 2
+    per_point = 2.0 * int(np.count_nonzero(quarter)) + float(((mult - 1) * cols).sum())
     total = 0.0
     for l in range(1, info["ncomp"] + 1):
         n = info["n"][l - 1]
         pts = n[0] * n[1] * n[2]
         if info["stencil_kind"][l - 1] == 0:
             padded = (n[0] + 2 * S[0]) * (n[1] + 2 * S[1]) * (n[2] + 2 * S[2])
-            total += 2.0 * pts * nnz_s + 2.0 * padded * (p - 1) ** 3
+            total += pts * per_point + 2.0 * padded * (p - 1) ** 3
         else:
             lo = (C.c_int * 3)()
             sz = (C.c_int * 3)()

@@ -10,13 +10,15 @@
 // ball (|h o n| < 2a, about two thirds of K's nonzeros) and the 3-tap-per-axis
 // prefilter is fused into a pad kernel that writes a halo-padded copy of the
 // prefiltered grid (periodic images or zeros in the halo), so every tile's
-// input box is a plain rectangle. One block per output tile of 1 x 32 x 32 points
-// streams the 2R+1 input x-planes of the tile's halo through shared memory
-// (16-byte cp.async rows, double buffered) together with the matching x-slab
-// of the stencil, stored column by column with dz aligned to 16 bytes. Each
-// thread owns 16 consecutive z outputs in registers; per (dx, dy) stencil
-// column of half-width w it loads its 16 + 2w window and the 2w + 1 stencil
-// values with 128-bit shared loads and issues 16 (2w + 1) FFMA from registers.
+// input box is a plain rectangle. The samples are even in x and in y, so one
+// block per output tile of 1 x 32 x 32 points streams the input x-planes in
+// mirrored pairs x0 - dx, x0 + dx (dx = 0 .. R; 16-byte cp.async rows, double
+// buffered) together with the stencil x-slab of +dx, stored column by column
+// with dz aligned to 16 bytes. Each thread owns 16 consecutive z outputs in
+// registers; per column (dx, dy >= 0) of half-width w it sums the 16 + 2w
+// windows of the 1, 2 or 4 rows (x0 -+ dx, y -+ dy) that share the column,
+// loads the 2w + 1 stencil values with 128-bit shared loads and issues
+// 16 (2w + 1) FFMA from registers: a quarter of the FMAs of the plain sum.
 // w (rounded up to an even value by the planner) selects an unrolled variant,
 // so the ball shape costs little for short columns and nothing for empty ones. The arithmetic is FP32 on the CUDA cores: the sum has no dense
 // reduction axis, and a Toeplitz recast for the tensor cores would multiply
@@ -172,6 +174,45 @@ __device__ __forceinline__ void ball_column(float (&acc)[BZ], const float* __res
   }
 }
 
+// The stencil is even in x and in y (its samples depend on |dx|, |dy|, |dz|),
+// so the 2 or 4 input rows that share a column (x0 -+ dx, y -+ dy) are summed
+// before the FMAs: nr = 1, 2 or 4 rows r[0..nr).
+template <int W>
+__device__ __forceinline__ void ball_column_sym(float (&acc)[BZ], const float* r0, const float* r1, const float* r2,
+                                                const float* r3, int nr, const float* __restrict__ kc) {
+  const float* r[4] = {r0, r1, r2, r3};
+  constexpr int A = (W + 3) & ~3;
+  constexpr int NQ = BZ + 2 * A;
+  constexpr int NK = 2 * A + 4;
+  float qv[NQ], kv[NK];
+#pragma unroll
+  for (int t = 0; t < NQ; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(r[0] - A + t);
+    qv[t] = v.x; qv[t + 1] = v.y; qv[t + 2] = v.z; qv[t + 3] = v.w;
+  }
+#pragma unroll
+  for (int k = 1; k < 4; k++) {
+    if (k < nr) {
+#pragma unroll
+      for (int t = 0; t < NQ; t += 4) {
+        float4 v = *reinterpret_cast<const float4*>(r[k] - A + t);
+        qv[t] += v.x; qv[t + 1] += v.y; qv[t + 2] += v.z; qv[t + 3] += v.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 2 * A + 1; t += 4) {
+    float4 v = *reinterpret_cast<const float4*>(kc - A + t);
+    kv[t] = v.x; kv[t + 1] = v.y; kv[t + 2] = v.z; kv[t + 3] = v.w;
+  }
+#pragma unroll
+  for (int dz = -W; dz <= W; dz++) {
+    const float k = kv[dz + A];
+#pragma unroll
+    for (int o = 0; o < BZ; o++) acc[o] = fmaf(k, qv[o - dz + A], acc[o]);
+  }
+}
+
 template <int W>
 __device__ __forceinline__ void virial_column(float (&w6)[6], const float (&qown)[BZ],
                                               const float* __restrict__ qrow, const float* __restrict__ kd,
@@ -254,6 +295,13 @@ struct Col {
     else
       Col<W + 2, WMAX>::stencil(w, acc, q, k);
   }
+  static __device__ __forceinline__ void stencil_sym(int w, float (&acc)[BZ], const float* r0, const float* r1,
+                                                     const float* r2, const float* r3, int nr, const float* k) {
+    if (w == W)
+      ball_column_sym<W>(acc, r0, r1, r2, r3, nr, k);
+    else
+      Col<W + 2, WMAX>::stencil_sym(w, acc, r0, r1, r2, r3, nr, k);
+  }
   static __device__ __forceinline__ void virial(int w, float (&w6)[6], const float (&qown)[BZ], const float* q,
                                                 const float* k, int ks) {
     if (w == W)
@@ -273,6 +321,10 @@ template <int WMAX>
 struct Col<WMAX, WMAX> {
   static __device__ __forceinline__ void stencil(int, float (&acc)[BZ], const float* q, const float* k) {
     ball_column<WMAX>(acc, q, k);
+  }
+  static __device__ __forceinline__ void stencil_sym(int, float (&acc)[BZ], const float* r0, const float* r1,
+                                                     const float* r2, const float* r3, int nr, const float* k) {
+    ball_column_sym<WMAX>(acc, r0, r1, r2, r3, nr, k);
   }
   static __device__ __forceinline__ void virial(int, float (&w6)[6], const float (&qown)[BZ], const float* q,
                                                 const float* k, int ks) {
@@ -306,14 +358,39 @@ __device__ __forceinline__ void stage_ball(const LevDev& L, const TileItem& it, 
   cp_async_commit();
 }
 
+// Copies of input planes x0 - dx and x0 + dx (one plane for dx = 0) of the
+// padded grid, of the stencil slab of +dx and of its column table, into one
+// stage buffer.
+__device__ __forceinline__ void stage_pair(const LevDev& L, const TileItem& it, int dx,
+                                           const float* __restrict__ grid, const float* __restrict__ kpool,
+                                           const int* __restrict__ wpool, float* planeA, float* planeB,
+                                           float* kslab, int* wsl, int stride) {
+  const int Rx = L.R[0], Ry = L.R[1], hz = L.hz;
+  const int rows = TY + 2 * Ry, cpr = (TZ + 2 * hz) / 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pl = 0; pl < (dx > 0 ? 2 : 1); pl++) {
+    const int px = it.x0 + Rx + (pl == 0 ? -dx : dx);  // padded index of x0 -+ dx
+    float* dst = pl == 0 ? planeA : planeB;
+    const float* src = grid + L.p_off + ((long long)px * L.pn[1] + it.y0) * L.pn[2] + it.z0;
+    for (int r = warp; r < rows; r += NT / 32)
+      if (lane < cpr) cp_async16(dst + r * stride + 4 * lane, src + (long long)r * L.pn[2] + 4 * lane);
+  }
+  const int step = Rx + dx;
+  const int kchunks = (2 * Ry + 1) * kSK(hz) / 4;
+  const float* ks = kpool + L.k_off + (long long)step * (2 * Ry + 1) * kSK(hz);
+  for (int e = threadIdx.x; e < kchunks; e += NT) cp_async16(kslab + 4 * e, ks + 4 * e);
+  for (int e = threadIdx.x; e < 2 * Ry + 1; e += NT) wsl[e] = wpool[L.w_off + (long long)step * (2 * Ry + 1) + e];
+  cp_async_commit();
+}
+
 template <int WMAX>
 __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ levs,
                                                      const TileItem* __restrict__ items,
                                                      const float* __restrict__ kpool, const int* __restrict__ wpool,
                                                      float* __restrict__ grid, int stride, int plane_sz, int kslab_sz) {
   extern __shared__ __align__(16) float smem[];
-  float* planes = smem;
-  float* kslabs = smem + 2 * plane_sz;
+  float* planes = smem;                    // 2 stage buffers x 2 planes
+  float* kslabs = smem + 4 * plane_sz;
   int* wsl = reinterpret_cast<int*>(kslabs + 2 * kslab_sz);
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
@@ -322,24 +399,27 @@ __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ 
   float acc[BZ];
 #pragma unroll
   for (int o = 0; o < BZ; o++) acc[o] = 0.f;
-  const int nsteps = 2 * Rx + 1;
-  stage_ball(L, it, 0, grid, kpool, L.k_off, 1, wpool, L.w_off, planes, kslabs, wsl, stride);
-  for (int step = 0; step < nsteps; step++) {
+  stage_pair(L, it, 0, grid, kpool, wpool, planes, planes + plane_sz, kslabs, wsl, stride);
+  for (int dx = 0; dx <= Rx; dx++) {
     cp_async_wait_all();
     __syncthreads();
-    const int b = step & 1;
-    if (step + 1 < nsteps)
-      stage_ball(L, it, step + 1, grid, kpool, L.k_off, 1, wpool, L.w_off, planes + (b ^ 1) * plane_sz,
-                 kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax, stride);
-    const float* plane = planes + b * plane_sz;
+    const int b = dx & 1;
+    if (dx < Rx)
+      stage_pair(L, it, dx + 1, grid, kpool, wpool, planes + (b ^ 1) * 2 * plane_sz,
+                 planes + (b ^ 1) * 2 * plane_sz + plane_sz, kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax,
+                 stride);
+    const float* pa = planes + b * 2 * plane_sz;
+    const float* pb = pa + plane_sz;
     const float* kslab = kslabs + b * kslab_sz;
     const int* wc = wsl + b * kWslMax;
-    for (int dy = -Ry; dy <= Ry; dy++) {
+    for (int dy = 0; dy <= Ry; dy++) {
       const int w = wc[dy + Ry];
       if (w < 0) continue;
-      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz;
-      const float* kc = kslab + (dy + Ry) * SK + hz;
-      Col<0, WMAX>::stencil(w, acc, qrow, kc);
+      const int o1 = (ty - dy + Ry) * stride + zb * BZ + hz, o2 = (ty + dy + Ry) * stride + zb * BZ + hz;
+      // rows sharing the column: (x0-dx, y-dy), (x0-dx, y+dy), (x0+dx, y-dy), (x0+dx, y+dy)
+      const int nr = (dx > 0 ? 2 : 1) * (dy > 0 ? 2 : 1);
+      const float* r1 = dy > 0 ? pa + o2 : pb + o1;
+      Col<0, WMAX>::stencil_sym(w, acc, pa + o1, r1, pb + o1, pb + o2, nr, kslab + (dy + Ry) * SK + hz);
     }
   }
   const int y = it.y0 + ty;
@@ -549,6 +629,7 @@ static void run_ball(const Work& w, const Tables& t, const TileItem* items, int 
   int stride, plane_sz, kslab_sz;
   size_t bytes;
   ball_smem(ryz_max, 1, stride, plane_sz, kslab_sz, bytes);
+  bytes += sizeof(float) * 2 * (size_t)plane_sz;  // the mirrored planes x0 + dx
   static size_t attr = 0;  // raise the dynamic shared-memory limit once per size
   if (bytes > attr && cudaFuncSetAttribute(k_stencil_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)bytes) == cudaSuccess)
