@@ -43,6 +43,7 @@ class Plan:
             nb = C.c_size_t()
             L.check(self.lib.msm_workspace_bytes(self.handle, C.byref(nb)))
             self.workspace = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        self._copy_stream = None
         self.max_atoms = int(max_atoms)
         self.last_virial = None
         self._n = None
@@ -128,6 +129,8 @@ class Plan:
 
         pos (n, 3) and q (n,) are float32 CPU tensors (pinned for asynchronous
         copies). Returns host (E, dE/dpos, dE/dq, virial) after synchronising.
+        The backward runs in two calls: the per-atom gradients first, whose
+        copy to the host then overlaps the grid virial on a second stream.
         """
         n = int(pos.shape[0])
         dpos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
@@ -136,19 +139,28 @@ class Plan:
         dq.copy_(q, non_blocking=True)
         E, _, _ = self.forward(dpos, dq, forces=True, virial=virial, phi=False)
         g = torch.ones(1, dtype=torch.float64, device=self.device)
-        gp, gq, W = self.backward(g, dpos=True, dq=True, virial=virial)
+        gp, gq, _ = self.backward(g, dpos=True, dq=True, virial=False)
         if pinned_out is None:
             pinned_out = (torch.empty(1, dtype=torch.float64, pin_memory=True),
                           torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
                           torch.empty(n, dtype=torch.float32, pin_memory=True),
                           torch.empty((3, 3), dtype=torch.float64, pin_memory=True))
         oE, op, oq, oW = pinned_out
-        oE.copy_(E, non_blocking=True)
-        op.copy_(gp, non_blocking=True)
-        oq.copy_(gq, non_blocking=True)
-        if W is not None:
+        cur = torch.cuda.current_stream(self.device)
+        if self._copy_stream is None:
+            self._copy_stream = torch.cuda.Stream(self.device)
+        ready = torch.cuda.Event()
+        ready.record(cur)
+        with torch.cuda.stream(self._copy_stream):
+            self._copy_stream.wait_event(ready)
+            oE.copy_(E, non_blocking=True)
+            op.copy_(gp, non_blocking=True)
+            oq.copy_(gq, non_blocking=True)
+        if virial:
+            _, _, W = self.backward(g, dpos=False, dq=False, virial=True)
             oW.copy_(W, non_blocking=True)
-        torch.cuda.current_stream(self.device).synchronize()
+        cur.synchronize()
+        self._copy_stream.synchronize()
         return oE, op, oq, oW
 
     def profile(self, enable=True):

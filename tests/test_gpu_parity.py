@@ -186,6 +186,19 @@ def test_autograd_outputs_phi_and_forces():
         (E2 + phi2.sum()).backward()
 
 
+def test_evaluate_host_end_to_end():
+    # host buffers in and out (the benchmark's end-to-end call) against the oracle
+    key = "periodic_20001"
+    w = WORKLOADS[key]()
+    plan = make_plan(w)
+    E, gp, gq, Wv = plan.evaluate_host(torch.from_numpy(w.pos).pin_memory(), torch.from_numpy(w.q).pin_memory())
+    P, ref = _oracle(key)
+    assert abs(float(E[0]) - ref["E"]) <= E_TOL * abs(ref["E"])
+    assert rel_rms(gp.numpy(), -ref["F"]) <= F_TOL
+    assert rel_rms(gq.numpy(), ref["phi"]) <= F_TOL
+    assert np.abs(Wv.numpy() - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max()
+
+
 def test_finite_differences_on_gpu():
     # central differences of the GPU energy (FP32 inputs, FP64 energy) for a few atoms
     w = W.rocksalt(ncell=4, seed=40)
