@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-atoms", type=int, default=N_HEADLINE)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--tuning", type=int, nargs=2, metavar=("ANTERP_TZ", "SHORT_BLOCK"), default=None,
+                    help="fixed launch shapes for the 1M-atom plan instead of msm_autotune")
     ap.add_argument("--batch-systems", type=int, default=512)
     ap.add_argument("--sweep", action="store_true",
                     help="linear-scaling sweep instead of the headline step: forward only (E, phi, F) on periodic "
@@ -335,9 +337,13 @@ def run_gpu(args):
     n = args.atoms
     w = W.random_box(n, seed=3010 + rank)
     plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, 0, max_atoms=n, device=dev)
-    info = plan.info()
     pos = torch.from_numpy(w.pos).to(dev)
     q = torch.from_numpy(w.q).to(dev)
+    if args.tuning:
+        plan.set_tuning(*args.tuning)
+    else:
+        plan.autotune(pos, q)  # launch shapes for this workload, before the timed steps
+    info = plan.info()
     g = torch.ones(1, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     E = torch.empty(1, dtype=torch.float64, device=dev)
@@ -467,7 +473,9 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(n), "atoms_per_gpu": n, "parallelism": "replicas",
                        "l2": "flushed (256 MB write) before every step", "levels": info["nlev"],
-                       "M": info["M"][0]},
+                       "M": info["M"][0],
+                       "tuning": {"anterp_tz": info["anterp_tz"], "short_block": info["short_block"],
+                                  "how": "fixed" if args.tuning else "msm_autotune"}},
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_val, "unit": "atoms/s", "h2d_bytes_per_step": n * 16,
                     "d2h_bytes_per_step": n * 16 + 8 + 72, "ms_per_step": ms_e2e},

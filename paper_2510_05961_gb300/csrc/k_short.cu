@@ -6,6 +6,15 @@
 //   W0     += -1/2 q_i q_j k_0'(r) d d^T / r,
 // and phi0_i -= q_i gamma(0)/a (the self term, sum_(l>=1) k_l(0)).
 //
+// The virial is not summed pair by pair. With g_ij = q_i q_j k_0'(r)/r and
+// F_i = sum_(j,n) g_ij d_ij, d_ij = r_j + A n - r_i, pairing every ordered
+// pair (i, j, n) with (j, i, -n) gives the exact identity
+//   -1/2 sum g d d^T = sum_i r_i F_i^T - 1/2 sum_(i,j,n) (A n) (g d)^T,
+// where the last sum only has terms for periodic images n != 0. Each thread
+// sums its pairs per candidate run (one column, one image), so the image
+// term takes one outer product per run with n != 0 and the pair loop carries
+// no virial arithmetic (6 FMAs per pair less); the symmetric part is kept.
+//
 // Candidates: for each (dx, dy) column of cells around i's cell whose xy
 // distance to i is below a, the cells of that column along z within
 // sqrt(a^2 - dxy^2) of i. Cells of one column are consecutive in the sorted
@@ -40,7 +49,7 @@ __device__ __forceinline__ float image_shift(int k, double L, float z) {
 // NB threads per block: NB = kChunk (one block per atom item) or kChunk / 2
 // (two blocks per item), chosen by the autotuner
 template <int P, bool WF, bool WW, int NB>
-__global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+__global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                                               const int* __restrict__ cell_start, const int* __restrict__ scell,
                                               const float4* __restrict__ xq, float* __restrict__ phi_sr,
                                               float4* __restrict__ f_sr, double* __restrict__ part_w0) {
@@ -52,6 +61,13 @@ __global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, co
   int local = it.start + slot;
   bool active = slot < it.count && local < S.n;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // image term sum_runs (A n)(sum q_j k_0'(r)/r d)^T of this thread, symmetric
+  // part; in shared memory (rarely touched) to keep registers for the pair loop
+  __shared__ float wimg[6][NB];
+  if (WW) {
+#pragma unroll
+    for (int c = 0; c < 6; c++) wimg[c][threadIdx.x] = 0.f;
+  }
   if (active) {
     const int k = S.atom_off + local;
     const float4 xi = xq[k];
@@ -72,7 +88,8 @@ __global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, co
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
       const int ux = ci[0] + ox;
       if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
-      const int wx = ux - floordiv_s(ux, Cx) * Cx;
+      const int nxc = floordiv_s(ux, Cx) * Cx;  // image shift along x, in cells
+      const int wx = ux - nxc;
       const float bx = (float)ox * ex - xi.x;  // d_x = bx + x_j
       const float mx = fmaxf((ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f)) - mg * ex, 0.f);
       for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
@@ -82,7 +99,8 @@ __global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, co
         const float my = fmaxf((oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f)) - mg * ey, 0.f);
         const float rxy2 = mx * mx + my * my;
         if (rxy2 >= a2) continue;
-        const int wy = uy - floordiv_s(uy, Cy) * Cy;
+        const int nyc = floordiv_s(uy, Cy) * Cy;
+        const int wy = uy - nyc;
         const float zr = sqrtf(a2 - rxy2) + mg * S.edge[2];
         int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
         if (!S.pbc[2]) {
@@ -97,6 +115,7 @@ __global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, co
           const int wend = min(Cz - 1, wz + (zhi - uz));
           const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
           const float bz = image_shift(kz, S.Ld[2], xi.z);
+          float sx = 0.f, sy = 0.f, sz = 0.f;  // sum of q_j k_0'(r)/r d over this run
           for (int j = jb; j < je; j++) {
             const float4 xj = xq[j];
             const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
@@ -114,29 +133,44 @@ __global__ void __launch_bounds__(NB) k_short(const SysDev* __restrict__ sys, co
               for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, s, gdc[t]);
               // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
               const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
-              const float frx = fr * dx, fry = fr * dy, frz = fr * dz;
-              fx += frx;
-              fy += fry;
-              fz += frz;
-              if (WW) {
-                w6[0] = fmaf(frx, dx, w6[0]);
-                w6[1] = fmaf(fry, dy, w6[1]);
-                w6[2] = fmaf(frz, dz, w6[2]);
-                w6[3] = fmaf(frx, dy, w6[3]);
-                w6[4] = fmaf(frx, dz, w6[4]);
-                w6[5] = fmaf(fry, dz, w6[5]);
-              }
+              sx = fmaf(fr, dx, sx);
+              sy = fmaf(fr, dy, sy);
+              sz = fmaf(fr, dz, sz);
             }
           }
         }
+          fx += sx;
+          fy += sy;
+          fz += sz;
+          if (WW && (nxc | nyc | kz) != 0) {
+            // image term of the run: (A n) s^T, symmetric part
+            const float tx = (float)nxc * ex, ty = (float)nyc * ey, tz = (float)kz * S.Lf[2];
+            float* wi = &wimg[0][threadIdx.x];
+            wi[0] = fmaf(tx, sx, wi[0]);
+            wi[NB] = fmaf(ty, sy, wi[NB]);
+            wi[2 * NB] = fmaf(tz, sz, wi[2 * NB]);
+            wi[3 * NB] = fmaf(0.5f * tx, sy, fmaf(0.5f * ty, sx, wi[3 * NB]));
+            wi[4 * NB] = fmaf(0.5f * tx, sz, fmaf(0.5f * tz, sx, wi[4 * NB]));
+            wi[5 * NB] = fmaf(0.5f * ty, sz, fmaf(0.5f * tz, sy, wi[5 * NB]));
+          }
           uz += wend - wz + 1;
         }
       }
     }
     phi_sr[k] = ph - xi.w * S.self_coef;
     if (WF) f_sr[k] = make_float4(xi.w * fx, xi.w * fy, xi.w * fz, 0.f);
-#pragma unroll
-    for (int c = 0; c < 6; c++) w6[c] *= -0.5f * xi.w;
+    if (WW) {
+      // q_i [sym(r_i f^T) - 1/2 image term], r_i relative to the cell's lower
+      // corner for x, y and the sorted z (the frame the displacements use)
+      const float rx = (float)ci[0] * ex + xi.x, ry = (float)ci[1] * ey + xi.y, rz = xi.z;
+      const float hq = -0.5f * xi.w;
+      w6[0] = xi.w * (rx * fx) + hq * wimg[0][threadIdx.x];
+      w6[1] = xi.w * (ry * fy) + hq * wimg[1][threadIdx.x];
+      w6[2] = xi.w * (rz * fz) + hq * wimg[2][threadIdx.x];
+      w6[3] = xi.w * (0.5f * (rx * fy + ry * fx)) + hq * wimg[3][threadIdx.x];
+      w6[4] = xi.w * (0.5f * (rx * fz + rz * fx)) + hq * wimg[4][threadIdx.x];
+      w6[5] = xi.w * (0.5f * (ry * fz + rz * fy)) + hq * wimg[5][threadIdx.x];
+    }
   }
   if (!WW) return;
   // per-warp FP64 partials of the six virial components (fixed order, no block barrier)
