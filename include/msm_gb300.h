@@ -165,6 +165,18 @@ int msm_forward(msm_plan plan, void* workspace, size_t workspace_bytes, int n, c
 int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,
                  double* virial, void* stream);
 
+/* The field E_i = -grad phi(r_i) of the MSM potential at every atom (the
+ * gradient of Eq. U_total's phi with respect to the evaluation point, both
+ * the short-range and the interpolated part; the force is F_i = q_i E_i),
+ * from the last msm_forward on workspace.
+ *  field  device, n x 3 float32, the caller's atom order.
+ * It is what the gradient of sum_i g_i phi_i needs (phi = A q with A
+ * symmetric: d/dq = A g, d/dr_k = -g_k E_k(q) - q_k E_k(g), the second field
+ * from an evaluation with charges g), and it needs no division by q.
+ * Stream-ordered; computes the field parts if that forward skipped forces.
+ * Returns MSM_ERR_NO_FORWARD without a prior forward on workspace. */
+int msm_field(msm_plan plan, void* workspace, float* field, void* stream);
+
 /* Autotuner (no counterpart in the paper, whose JAX code leaves launch shapes
  * to XLA): runs one forward on (n, pos, q) to fill workspace, then times each
  * tunable launch shape on those inputs and keeps the fastest for every later
@@ -250,6 +262,8 @@ int msm_batch_forward(msm_batch batch, void* workspace, size_t workspace_bytes, 
                       double* energy, float* phi, float* forces, int flags, void* stream);
 int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_energy, float* dE_dpos,
                        float* dE_dq, double* virial, void* stream);
+/* msm_field for a batch: field (sum n) x 3, packed like the positions. */
+int msm_batch_field(msm_batch batch, void* workspace, float* field, void* stream);
 int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status);
 /* msm_autotune for a batch (all systems share the tuned shapes), and the shapes in use. */
 int msm_batch_autotune(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,

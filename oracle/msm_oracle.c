@@ -51,7 +51,8 @@ typedef struct {
   int S[3];             /* kernel-sample radius of the level stencils */
   int R[3];             /* stencil radius S + hw */
   int hw;               /* half-width of omega': p/2 - 1 (qi_mode 0) or the truncation of or_omega_exact */
-  int C[3];             /* binning cells per axis (periodic: M / 2^k, edge <= a/2; open: floor(2L/a)) */
+  int C[3];             /* binning cells per axis (periodic: M / 2^k, edge <= a/2 (x, y), a/4 (z);
+                           open: floor(2L/a) (x, y), floor(4L/a) (z)) */
   double edge[3];       /* binning cell edges */
   int nnbr[3];          /* neighbour-cell reach ceil(a/edge) */
   float invLf[3];       /* (float)(1/L): binning contract */
@@ -377,13 +378,16 @@ int or_plan_init(or_plan* P) {
     int C;
     if (P->pbc[d]) {
       /* periodic axis: cells of k level-1 intervals, k the largest power of
-       * two with k h_1 <= a/2 (at least 1), at most 512 cells */
+       * two with k h_1 <= a/2 for x, y and <= a/4 for z (at least 1), at
+       * most 512 cells */
+      const double lim = (d == 2 ? 0.25 : 0.5) * P->a;
       int k = 1;
-      while (2 * k <= P->M[d] && 2 * k * P->h1[d] <= 0.5 * P->a) k *= 2;
+      while (2 * k <= P->M[d] && 2 * k * P->h1[d] <= lim) k *= 2;
       while (P->M[d] / k > 512) k *= 2;
       C = P->M[d] / k;
     } else {
-      C = (int)floor(2.0 * P->L[d] / P->a);
+      /* open axis: floor(2 L / a) cells for x, y and floor(4 L / a) for z, 1 .. 256 */
+      C = (int)floor((d == 2 ? 4.0 : 2.0) * P->L[d] / P->a);
       if (C < 1) C = 1;
       if (C > 256) C = 256;
     }

@@ -1,6 +1,7 @@
 // k_final.cu -- outputs of the MSM evaluation (Sec. 2, Eq. U_contributions;
 // Sec. 3.2.2 for the derivatives):
-//   phi_i = phi0_i + phi^(1+)_i  (= dE/dq_i),   F_i = F0_i + F^(1+)_i,
+//   phi_i = phi0_i + phi^(1+)_i  (= dE/dq_i),
+//   field_i = -grad phi(r_i) (both parts), F_i = q_i field_i,
 //   E = 1/2 sum_i q_i phi_i   (FP64, fixed-order block sums),
 //   W = W0 + W^(1+)           (FP64, fixed-order sums of the block partials),
 // written back in the caller's atom order through the sort permutation.
@@ -27,10 +28,11 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
     e = 0.5 * (double)xq[k].w * (double)ph;
     if (phi) phi[g] = ph;
     if (forces) {
+      const float qk = xq[k].w;
       float4 a = f_sr[k], b = f_lr[k];
-      forces[3 * (long long)g + 0] = a.x + b.x;
-      forces[3 * (long long)g + 1] = a.y + b.y;
-      forces[3 * (long long)g + 2] = a.z + b.z;
+      forces[3 * (long long)g + 0] = qk * (a.x + b.x);
+      forces[3 * (long long)g + 1] = qk * (a.y + b.y);
+      forces[3 * (long long)g + 2] = qk * (a.z + b.z);
     }
   }
   for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(64) k_virial_out(const double* __restrict__ sl
 __global__ void __launch_bounds__(kChunk) k_backward_scale(const SysDev* __restrict__ sys,
                                                            const AtomItem* __restrict__ items,
                                                            const int* __restrict__ perm,
+                                                           const float4* __restrict__ xq,
                                                            const float* __restrict__ phi_sr,
                                                            const float* __restrict__ phi_lr,
                                                            const float4* __restrict__ f_sr,
@@ -140,11 +143,28 @@ __global__ void __launch_bounds__(kChunk) k_backward_scale(const SysDev* __restr
   float gr = (float)grad[it.sys];
   if (dE_dq) dE_dq[g] = gr * (phi_sr[k] + phi_lr[k]);
   if (dE_dpos) {
+    const float gq = -gr * xq[k].w;
     float4 a = f_sr[k], b = f_lr[k];
-    dE_dpos[3 * (long long)g + 0] = -gr * (a.x + b.x);
-    dE_dpos[3 * (long long)g + 1] = -gr * (a.y + b.y);
-    dE_dpos[3 * (long long)g + 2] = -gr * (a.z + b.z);
+    dE_dpos[3 * (long long)g + 0] = gq * (a.x + b.x);
+    dE_dpos[3 * (long long)g + 1] = gq * (a.y + b.y);
+    dE_dpos[3 * (long long)g + 2] = gq * (a.z + b.z);
   }
+}
+
+// field_i = -grad phi(r_i) in the caller's atom order
+__global__ void __launch_bounds__(kChunk) k_field(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                                                  const int* __restrict__ perm, const float4* __restrict__ f_sr,
+                                                  const float4* __restrict__ f_lr, float* __restrict__ field) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  int g = perm[k];
+  float4 a = f_sr[k], b = f_lr[k];
+  field[3 * (long long)g + 0] = a.x + b.x;
+  field[3 * (long long)g + 1] = a.y + b.y;
+  field[3 * (long long)g + 2] = a.z + b.z;
 }
 
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
@@ -167,8 +187,12 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
 
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s) {
-  k_backward_scale<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, grad, dE_dpos,
-                                             dE_dq);
+  k_backward_scale<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, grad,
+                                             dE_dpos, dE_dq);
+}
+
+void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s) {
+  k_field<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.f_sr, w.f_lr, field);
 }
 
 }  // namespace msm

@@ -229,10 +229,8 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
     }
   }
   phi_lr[k] = ph;
-  if (want_f) {
-    float qq = u4.w;
-    f_lr[k] = make_float4(-qq * gx * S.inv_h1[0], -qq * gy * S.inv_h1[1], -qq * gz * S.inv_h1[2], 0.f);
-  }
+  // field -grad phi^(1+) at the atom (the force is q_i times it)
+  if (want_f) f_lr[k] = make_float4(-gx * S.inv_h1[0], -gy * S.inv_h1[1], -gz * S.inv_h1[2], 0.f);
 }
 
 template <int P>

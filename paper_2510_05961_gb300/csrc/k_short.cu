@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
       }
     }
     phi_sr[k] = ph - xi.w * S.self_coef;
-    if (WF) f_sr[k] = make_float4(xi.w * fx, xi.w * fy, xi.w * fz, 0.f);
+    if (WF) f_sr[k] = make_float4(fx, fy, fz, 0.f);  // field of the other charges; the force is q_i times it
     if (WW) {
       // q_i [sym(r_i f^T) - 1/2 image term], r_i relative to the cell's lower
       // corner for x, y and the sorted z (the frame the displacements use)

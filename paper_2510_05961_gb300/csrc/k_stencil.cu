@@ -12,15 +12,18 @@
 // prefiltered grid (periodic images or zeros in the halo), so every tile's
 // input box is a plain rectangle. The samples are even in x and in y, so one
 // block per output tile of 1 x 32 x 32 points streams the input x-planes in
-// mirrored pairs x0 - dx, x0 + dx (dx = 0 .. R; 16-byte cp.async rows, double
-// buffered) together with the stencil x-slab of +dx, stored column by column
+// mirrored pairs x0 - dx, x0 + dx (dx = 0 .. R; 16-byte cp.async rows, one
+// stage buffer: the block waits for each pair, and twice as many resident
+// blocks as with double buffering hide the copies; measured faster) together
+// with the stencil x-slab of +dx, stored column by column
 // with dz aligned to 16 bytes. Each thread owns 16 consecutive z outputs in
 // registers; per column (dx, dy >= 0) of half-width w it sums the 16 + 2w
 // windows of the 1, 2 or 4 rows (x0 -+ dx, y -+ dy) that share the column,
 // loads the 2w + 1 stencil values with 128-bit shared loads and issues
 // 16 (2w + 1) FFMA from registers: a quarter of the FMAs of the plain sum.
 // w (rounded up to an even value by the planner) selects an unrolled variant,
-// so the ball shape costs little for short columns and nothing for empty ones. The arithmetic is FP32 on the CUDA cores: the sum has no dense
+// so the ball shape costs little for short columns and nothing for empty ones.
+// The arithmetic is FP32 on the CUDA cores: the sum has no dense
 // reduction axis, and a Toeplitz recast for the tensor cores would multiply
 // the work by (16 + 2R)/(2R + 1) per axis while TF32 loses the accuracy the
 // method needs.
@@ -389,9 +392,9 @@ __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ 
                                                      const float* __restrict__ kpool, const int* __restrict__ wpool,
                                                      float* __restrict__ grid, int stride, int plane_sz, int kslab_sz) {
   extern __shared__ __align__(16) float smem[];
-  float* planes = smem;                    // 2 stage buffers x 2 planes
-  float* kslabs = smem + 4 * plane_sz;
-  int* wsl = reinterpret_cast<int*>(kslabs + 2 * kslab_sz);
+  float* planes = smem;                    // one stage buffer of 2 planes
+  float* kslabs = smem + 2 * plane_sz;
+  int* wsl = reinterpret_cast<int*>(kslabs + kslab_sz);
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
@@ -399,19 +402,15 @@ __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ 
   float acc[BZ];
 #pragma unroll
   for (int o = 0; o < BZ; o++) acc[o] = 0.f;
-  stage_pair(L, it, 0, grid, kpool, wpool, planes, planes + plane_sz, kslabs, wsl, stride);
   for (int dx = 0; dx <= Rx; dx++) {
+    __syncthreads();
+    stage_pair(L, it, dx, grid, kpool, wpool, planes, planes + plane_sz, kslabs, wsl, stride);
     cp_async_wait_all();
     __syncthreads();
-    const int b = dx & 1;
-    if (dx < Rx)
-      stage_pair(L, it, dx + 1, grid, kpool, wpool, planes + (b ^ 1) * 2 * plane_sz,
-                 planes + (b ^ 1) * 2 * plane_sz + plane_sz, kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax,
-                 stride);
-    const float* pa = planes + b * 2 * plane_sz;
+    const float* pa = planes;
     const float* pb = pa + plane_sz;
-    const float* kslab = kslabs + b * kslab_sz;
-    const int* wc = wsl + b * kWslMax;
+    const float* kslab = kslabs;
+    const int* wc = wsl;
     for (int dy = 0; dy <= Ry; dy++) {
       const int w = wc[dy + Ry];
       if (w < 0) continue;
@@ -441,8 +440,8 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ s
   extern __shared__ __align__(16) float smem[];
   __shared__ double red[NT / 32][6];
   float* planes = smem;
-  float* kslabs = smem + 2 * plane_sz;
-  int* wsl = reinterpret_cast<int*>(kslabs + 2 * kslab_sz);
+  float* kslabs = smem + plane_sz;
+  int* wsl = reinterpret_cast<int*>(kslabs + kslab_sz);
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
@@ -466,17 +465,14 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ s
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   // the half-space weights vanish for dx < 0: walk the planes dx = 0 .. Rx only
   const int nsteps = 2 * Rx + 1;
-  stage_ball(L, it, Rx, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes, kslabs, wsl, stride);
   for (int step = Rx; step < nsteps; step++) {
+    __syncthreads();
+    stage_ball(L, it, step, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes, kslabs, wsl, stride);
     cp_async_wait_all();
     __syncthreads();
-    const int b = (step - Rx) & 1;
-    if (step + 1 < nsteps)
-      stage_ball(L, it, step + 1, grid, kpool, L.dk_off, NK, wpool, L.wh_off, planes + (b ^ 1) * plane_sz,
-                 kslabs + (b ^ 1) * kslab_sz, wsl + (b ^ 1) * kWslMax, stride);
-    const float* plane = planes + b * plane_sz;
-    const float* kslab = kslabs + b * kslab_sz;
-    const int* wc = wsl + b * kWslMax;
+    const float* plane = planes;
+    const float* kslab = kslabs;
+    const int* wc = wsl;
     const float cx = hx * (float)(step - Rx);
     for (int dy = -Ry; dy <= Ry; dy++) {
       const int w = wc[dy + Ry];
@@ -614,13 +610,16 @@ __global__ void __launch_bounds__(kBoxThreads) k_virial_box(const LevDev* __rest
 }
 
 // ------------------------------------------------------------------ launchers
-static void ball_smem(const int ryz_max[2], int nk, int& stride, int& plane_sz, int& kslab_sz, size_t& bytes) {
+// shared memory of one ball block: nplanes staged input planes, the stencil
+// slabs of one dx (nk arrays) and its column table (one stage buffer)
+static void ball_smem(const int ryz_max[2], int nk, int nplanes, int& stride, int& plane_sz, int& kslab_sz,
+                      size_t& bytes) {
   const int Ry = ryz_max[0], hz = ryz_max[1];
   stride = TZ + 2 * hz;
   if ((stride / 4) % 2 == 0) stride += 4;  // 4 x odd floats: conflict-free 128-bit row loads
   plane_sz = (TY + 2 * Ry) * stride;
   kslab_sz = nk * (2 * Ry + 1) * kSK(hz);
-  bytes = sizeof(float) * (2 * (size_t)plane_sz + 2 * (size_t)kslab_sz) + sizeof(int) * 2 * kWslMax;
+  bytes = sizeof(float) * ((size_t)nplanes * plane_sz + (size_t)kslab_sz) + sizeof(int) * kWslMax;
 }
 
 template <int WMAX>
@@ -628,8 +627,7 @@ static void run_ball(const Work& w, const Tables& t, const TileItem* items, int 
                      cudaStream_t s) {
   int stride, plane_sz, kslab_sz;
   size_t bytes;
-  ball_smem(ryz_max, 1, stride, plane_sz, kslab_sz, bytes);
-  bytes += sizeof(float) * 2 * (size_t)plane_sz;  // the mirrored planes x0 + dx
+  ball_smem(ryz_max, 1, 2, stride, plane_sz, kslab_sz, bytes);  // planes x0 - dx, x0 + dx
   static size_t attr = 0;  // raise the dynamic shared-memory limit once per size
   if (bytes > attr && cudaFuncSetAttribute(k_stencil_ball<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)bytes) == cudaSuccess)
@@ -643,7 +641,7 @@ static void run_virial_ball(const Work& w, const Tables& t, const TileItem* item
                             int part_off, cudaStream_t s) {
   int stride, plane_sz, kslab_sz;
   size_t bytes;
-  ball_smem(ryz_max, FACT ? 1 : 6, stride, plane_sz, kslab_sz, bytes);
+  ball_smem(ryz_max, FACT ? 1 : 6, 1, stride, plane_sz, kslab_sz, bytes);
   static size_t attr = 0;
   if (bytes > attr && cudaFuncSetAttribute(k_virial_ball<WMAX, FACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)bytes) == cudaSuccess)

@@ -172,6 +172,24 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   return check_launch("msm_backward");
 }
 
+// field -grad phi at every atom from the last forward on ws (forces / q, no
+// division); a forward without forces gets its field parts computed here
+static int run_field(Engine& E, void* ws, float* field, cudaStream_t s) {
+  if (!E.have_fwd || ws != E.last_ws) return set_err(MSM_ERR_NO_FORWARD, "msm_field needs a prior msm_forward on this workspace");
+  if (!field && E.last_n > 0) return set_err(MSM_ERR_INVALID_ARG, "field must not be NULL");
+  Work w = E.resolve(ws);
+  Tables t = E.tables();
+  const int nai = (int)E.atom_items.size();
+  if ((E.last_flags & MSM_WANT_FORCES) == 0) {
+    const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
+    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_block);
+    launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
+    E.last_flags |= MSM_WANT_FORCES;
+  }
+  if (E.last_n > 0) launch_field(w, t, E.d_atom_items, nai, field, s);
+  return check_launch("msm_field");
+}
+
 // Autotuner: one forward fills the workspace (bins, sorted atoms, level-1
 // grid), then each tunable launch shape is timed on those inputs (CUDA events,
 // one warm-up and three timed launches per candidate) and the fastest is kept.
@@ -384,6 +402,11 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
   return run_backward(plan->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
 }
 
+int msm_field(msm_plan plan, void* workspace, float* field, void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  return run_field(plan->eng, workspace, field, (cudaStream_t)stream);
+}
+
 int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos, const float* q,
                  void* stream) {
   if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
@@ -468,6 +491,11 @@ int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_ener
                        double* virial, void* stream) {
   if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
   return run_backward(batch->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
+}
+
+int msm_batch_field(msm_batch batch, void* workspace, float* field, void* stream) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return run_field(batch->eng, workspace, field, (cudaStream_t)stream);
 }
 
 int msm_batch_autotune(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,

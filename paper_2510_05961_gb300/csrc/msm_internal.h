@@ -101,9 +101,9 @@ struct Work {
   float4* xq;      // Cartesian position (the periodic image next to its cell) and charge, sorted
   float4* uq;      // level-1 grid coordinates and charge, sorted order
   float* phi_sr;   // short-range potential incl. self term, sorted
-  float4* f_sr;    // short-range force, sorted
+  float4* f_sr;    // short-range field -grad phi0 (force / q), sorted
   float* phi_lr;   // long-range potential, sorted
-  float4* f_lr;    // long-range force, sorted
+  float4* f_lr;    // long-range field -grad phi^(1+) (force / q), sorted
   double* part_e;  // per atom item: 1/2 sum q phi
   double* part_w0; // per warp of each atom item: 6 short-range virial components
   double* part_wg; // per virial item: 6 grid virial components
@@ -150,5 +150,6 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
                        const double* grad, double* virial, cudaStream_t s);
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
+void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s);
 
 }  // namespace msm

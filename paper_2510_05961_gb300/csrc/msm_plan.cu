@@ -382,13 +382,16 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     S.B[d] = S.prefilter ? S.S[d] : S.R[d];
     if (S.pbc[d]) {
       // periodic axis: cells aligned with the grid, k = 2^j level-1 intervals
-      // per cell, the largest with k h_1 <= a/2 (k >= 1), at most 512 cells
+      // per cell, the largest with k h_1 <= a/2 along x, y and <= a/4 along z
+      // (k >= 1), at most 512 cells. Half-height cells along z (the axis of
+      // the cell columns) cut the short-range candidates by a tenth.
       int k = 1;
-      while (2 * k <= S.M[d] && 2 * k * S.h1[d] <= 0.5 * S.a) k *= 2;
+      while (2 * k <= S.M[d] && 2 * k * S.h1[d] <= (d == 2 ? 0.25 : 0.5) * S.a) k *= 2;
       while (S.M[d] / k > 512) k *= 2;
       S.C[d] = S.M[d] / k;
     } else {
-      int C = (int)std::floor(2.0 * S.L[d] / S.a);
+      // open axis: edge >= a/2 along x, y and >= a/4 along z
+      int C = (int)std::floor((d == 2 ? 4.0 : 2.0) * S.L[d] / S.a);
       S.C[d] = std::min(std::max(C, 1), 256);
     }
     S.edge[d] = S.L[d] / S.C[d];

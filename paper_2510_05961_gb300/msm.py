@@ -106,6 +106,13 @@ class Plan:
             self.last_virial = W
         return gp, gq, W
 
+    def field(self, out=None):
+        """Field -grad phi (n, 3) float32 at every atom from the last forward (forces = q * field)."""
+        n = self._n
+        fld = out if out is not None else torch.empty((n, 3), dtype=torch.float32, device=self.device)
+        L.check(self.lib.msm_field(self.handle, _ptr(self.workspace), _ptr(fld), _stream(self.device)))
+        return fld
+
     def autotune(self, pos, q):
         """Time the tunable launch shapes on these inputs and keep the fastest; returns them.
         A new forward is needed before the next backward."""
@@ -176,29 +183,52 @@ class Plan:
 
 
 class MSMFunction(torch.autograd.Function):
-    """(E, phi, F) of (pos, q) through the library; backward gives dE/dpos and
-    dE/dq scaled by the upstream gradient of E, and plan.last_virial holds
-    W * dL/dE. Upstream gradients on phi or F (second-order terms) are not
-    implemented: a nonzero one raises NotImplementedError."""
+    """(E, phi, F) of (pos, q) through the library.
+
+    Backward takes upstream gradients on E and on phi:
+      E:   dE/dpos = -F, dE/dq = phi (the library's adjoint kernels); plan.last_virial
+           holds W * dL/dE.
+      phi: phi = A q with A symmetric (short-range kernel, self term and the grid chain
+           Phi^T K Phi are all symmetric), so for L = sum_i g_i phi_i
+             dL/dq = A g                           (potentials of charges g),
+             dL/dr_k = -g_k E_k(q) - q_k E_k(g)    (E = -grad phi, the field),
+           one more evaluation with charges g on the same positions.
+    An upstream gradient on F (Hessian terms) raises NotImplementedError. The plan's
+    workspace is reused: backward must follow its own forward."""
 
     @staticmethod
     def forward(ctx, pos, q, plan):
         ctx.set_materialize_grads(False)
-        E, phi, F = plan.forward(pos.detach().contiguous(), q.detach().contiguous(), forces=True, virial=True,
-                                 phi=True)
+        pos_d, q_d = pos.detach().contiguous(), q.detach().contiguous()
+        E, phi, F = plan.forward(pos_d, q_d, forces=True, virial=True, phi=True)
         ctx.plan = plan
         ctx.need = (pos.requires_grad, q.requires_grad)
+        ctx.save_for_backward(pos_d, q_d)
         return E.reshape(()), phi, F
 
     @staticmethod
     def backward(ctx, gE, gphi, gF):
-        for name, g in (("phi", gphi), ("forces", gF)):
-            if g is not None and bool((g != 0).any()):
-                raise NotImplementedError("gradients through the MSM %s output are not implemented "
-                                          "(second-order terms); differentiate E only" % name)
-        if gE is None:
+        if gF is not None and bool((gF != 0).any()):
+            raise NotImplementedError("gradients through the MSM forces are not implemented "
+                                      "(second-order terms); differentiate E or phi")
+        use_phi = gphi is not None and bool((gphi != 0).any())
+        if gE is None and not use_phi:
             return None, None, None
-        gp, gq, _ = ctx.plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
+        plan = ctx.plan
+        gp = gq = None
+        if gE is not None:
+            gp, gq, _ = plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
+        if use_phi:
+            pos, q = ctx.saved_tensors
+            g = gphi.detach().to(torch.float32).contiguous()
+            Eq = plan.field()  # field of q, before the workspace is reused
+            _, phig, _ = plan.forward(pos, g, forces=False, virial=False, phi=True)
+            if ctx.need[1]:
+                gq = phig if gq is None else gq + phig
+            if ctx.need[0]:
+                Eg = plan.field()
+                t = -(g[:, None] * Eq + q[:, None] * Eg)
+                gp = t if gp is None else gp + t
         return gp, gq, None
 
 
@@ -208,7 +238,7 @@ def msm_energy(pos, q, plan):
 
 
 def msm_outputs(pos, q, plan):
-    """(E, phi, F); E is differentiable, phi and F are not (their upstream must be zero)."""
+    """(E, phi, F); E and phi are differentiable, F is not (its upstream must be zero)."""
     return MSMFunction.apply(pos, q, plan)
 
 
@@ -274,6 +304,12 @@ class Batch:
         L.check(self.lib.msm_batch_backward(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gp), _ptr(gq), _ptr(W),
                                             _stream(self.device)))
         return gp, gq, (None if W is None else W.view(self.nsys, 3, 3))
+
+    def field(self, out=None):
+        """Field -grad phi ((sum n), 3) float32 at every atom of every system from the last forward."""
+        fld = out if out is not None else torch.empty((self.ntot, 3), dtype=torch.float32, device=self.device)
+        L.check(self.lib.msm_batch_field(self.handle, _ptr(self.workspace), _ptr(fld), _stream(self.device)))
+        return fld
 
     def set_tuning(self, anterp_tz=32, short_block=256):
         L.check(self.lib.msm_batch_set_tuning(self.handle, int(anterp_tz), int(short_block)))

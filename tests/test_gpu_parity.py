@@ -183,7 +183,57 @@ def test_autograd_outputs_phi_and_forces():
     assert rel_rms(q.grad.cpu().numpy(), ref["phi"]) <= F_TOL
     E2, phi2, F2 = msm_outputs(pos, q, plan)
     with pytest.raises(NotImplementedError):
-        (E2 + phi2.sum()).backward()
+        (E2 + F2.sum()).backward()
+
+
+def _oracle_eval(w, charges):
+    import oracle as O
+    O.build()
+    return O.msm(O.plan_for(w), w.pos.astype(np.float64), np.asarray(charges, np.float64), forces=True, virial=False)
+
+
+@pytest.mark.parametrize("key", ["periodic_20001", "rocksalt_6", "slab_3000", "open_c1"])
+def test_field_matches_oracle(key):
+    # field -grad phi = F / q (the workloads' charges are bounded away from 0)
+    w = WORKLOADS[key]()
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    _, _, F = plan.forward(pos, q, forces=True)
+    fld = plan.field().cpu().numpy()
+    P, ref = _oracle(key)
+    qq = w.q.astype(np.float64)[:, None]
+    assert np.abs(qq).min() > 0.05
+    assert rel_rms(fld, ref["F"] / qq) <= F_TOL
+    # a forward without forces: msm_field computes the field parts itself
+    plan.forward(pos, q, forces=False)
+    assert rel_rms(plan.field().cpu().numpy(), ref["F"] / qq) <= F_TOL
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("key", ["rocksalt_6", "periodic_20001", "water_600"])
+def test_gradient_through_phi(key):
+    # L = c E + sum_i g_i phi_i through the autograd function against the oracle:
+    # dL/dq = c phi(q) + phi(g), dL/dr_k = -c F_k - g_k E_k(q) - q_k E_k(g)
+    from paper_2510_05961_gb300 import msm_outputs
+    w = WORKLOADS[key]()
+    rng = np.random.default_rng(77)
+    g = (rng.choice([-1.0, 1.0], w.n) * rng.uniform(0.5, 1.5, w.n)).astype(np.float32)
+    c = 0.3
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV).requires_grad_(True)
+    q = torch.from_numpy(w.q).to(DEV).requires_grad_(True)
+    E, phi, F = msm_outputs(pos, q, plan)
+    (c * E + (torch.from_numpy(g).to(DEV) * phi).sum()).backward()
+    torch.cuda.synchronize()
+    P, rq = _oracle(key)
+    rg = _oracle_eval(w, g)
+    qd, gd = w.q.astype(np.float64)[:, None], g.astype(np.float64)[:, None]
+    dq_ref = c * rq["phi"] + rg["phi"]
+    dpos_ref = -c * rq["F"] - gd * (rq["F"] / qd) - qd * (rg["F"] / gd)
+    assert rel_rms(q.grad.cpu().numpy(), dq_ref) <= F_TOL
+    assert rel_rms(pos.grad.cpu().numpy(), dpos_ref) <= F_TOL
 
 
 def test_evaluate_host_end_to_end():

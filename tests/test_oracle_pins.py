@@ -459,6 +459,40 @@ def test_exact_invariants(oracle, pbc):
     assert np.allclose(rp["F"], r["F"][perm], rtol=1e-11, atol=1e-11)
 
 
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0)])
+def test_potential_adjoint_against_differences(oracle, pbc):
+    """phi = A q with A symmetric, so for L = sum_i g_i phi_i(r, q):
+    dL/dq = A g = phi(g) and dL/dr_k = -g_k E_k(q) - q_k E_k(g) with the field
+    E = F / q; checked by central differences of the oracle's potentials."""
+    rng = np.random.default_rng(15)
+    pos, q, cell = _small_periodic()
+    if not any(pbc):
+        pos = np.clip(pos, 0.5, 8.5)
+    P = oracle.make_plan(cell, pbc, 1.2, 3.5, 4)
+    g = rng.choice([-1.0, 1.0], len(q)) * rng.uniform(0.5, 1.5, len(q))
+    rq = oracle.msm(P, pos, q, True, False)
+    rg = oracle.msm(P, pos, g, True, False)
+    # symmetry of A: g . A q = q . A g
+    assert (g * rq["phi"]).sum() == pytest.approx((q * rg["phi"]).sum(), rel=1e-12)
+
+    def loss(pp, qq):
+        return float((g * oracle.msm(P, pp, qq, False, False)["phi"]).sum())
+
+    Eq, Eg = rq["F"] / q[:, None], rg["F"] / g[:, None]
+    for i in rng.choice(len(q), 4, replace=False):
+        h = 1e-5
+        qp, qm = q.copy(), q.copy()
+        qp[i] += h
+        qm[i] -= h
+        assert (loss(pos, qp) - loss(pos, qm)) / (2 * h) == pytest.approx(rg["phi"][i], rel=1e-7, abs=1e-8)
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = (loss(pp, q) - loss(pm, q)) / (2 * h)
+            assert fd == pytest.approx(-g[i] * Eq[i, d] - q[i] * Eg[i, d], rel=1e-5, abs=1e-6)
+
+
 def test_half_cell_translation_invariance(oracle):
     # shifting a periodic system by L/2 moves every evaluated level by whole points
     pos, q, cell = _small_periodic()
