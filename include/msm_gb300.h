@@ -120,6 +120,24 @@ int msm_plan_create(const msm_params* params, msm_plan* out);
 int msm_plan_destroy(msm_plan plan);
 int msm_plan_get_info(msm_plan plan, msm_plan_info* info);
 
+/* Dynamic cell (Sec. 3.2.2: with a changing cell the stencils K^l must be
+ * recomputed, as they sample the level kernels on grids that scale with the
+ * cell; Sec. 4.1 lists the limits of fixed-size stencil arrays). Gives the
+ * plan a new orthorhombic cell while keeping its grid counts M, level ranges,
+ * binning cells and stencil array sizes: the level-1 spacings become
+ * h_1 = L / M and the stencil samples, the virial weights, the column tables
+ * and the system descriptor are recomputed on the device, stream-ordered
+ * (no host synchronisation; NPT loops call it between steps).
+ *  cell    host, 9 doubles, row-major, diagonal (as msm_params.cell).
+ * Supported for periodic systems (pbc 1, 1, 1) with order 4 and qi_mode 0
+ * (MSM_ERR_UNSUPPORTED otherwise). The new cell may expand freely (coarser
+ * spacings lower the accuracy, as the paper notes); it may be compressed
+ * only while ceil(2 a / h_1) - 1 stays within the stencil radius the plan was
+ * built with (MSM_ERR_CAPACITY otherwise: create the plan for the most
+ * compressed cell it must serve). A later msm_backward needs a new
+ * msm_forward. Positions passed afterwards are in the new cell. */
+int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream);
+
 /* Host-only (no device needed): the plan msm_plan_create would build from
  * params, described in *info. Same validation and return codes. */
 int msm_plan_describe(const msm_params* params, msm_plan_info* info);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(HERE, "lib", "libmsm_gb300.so")
 SOURCES = ["msm_api.cu", "msm_plan.cu", "k_bin.cu", "k_short.cu", "k_interp.cu", "k_grid.cu", "k_stencil.cu",
-           "k_final.cu", "msm_static.cu"]
+           "k_final.cu", "k_cell.cu", "msm_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

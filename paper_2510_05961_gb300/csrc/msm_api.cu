@@ -6,6 +6,7 @@
 #include <string>
 
 #include "msm_plan.h"
+#include <cmath>
 
 using namespace msm;
 
@@ -400,6 +401,54 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
                  double* virial, void* stream) {
   if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
   return run_backward(plan->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
+}
+
+int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
+  if (!plan || !cell) return set_err(MSM_ERR_INVALID_ARG, "plan and cell must not be NULL");
+  Engine& E = plan->eng;
+  SysHost& S = E.sys[0];
+  for (int i = 0; i < 9; i++) {
+    if (!std::isfinite(cell[i])) return set_err(MSM_ERR_INVALID_ARG, "cell has a non-finite entry");
+    if (i % 4 != 0 && cell[i] != 0.0) return set_err(MSM_ERR_UNSUPPORTED, "only orthorhombic (diagonal) cells are supported");
+  }
+  for (int d = 0; d < 3; d++)
+    if (!(cell[4 * d] > 0.0)) return set_err(MSM_ERR_INVALID_ARG, "cell lengths must be > 0");
+  if (!(S.pbc[0] && S.pbc[1] && S.pbc[2]))
+    return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell needs a periodic system (pbc 1, 1, 1)");
+  if (!S.prefilter) return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell needs order 4 and qi_mode 0");
+  for (const LevelHost& Lv : S.lev)
+    if (Lv.kind != 0) return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell needs ball kernels on every level");
+  double h1[3];
+  int Snew[3];
+  for (int d = 0; d < 3; d++) {
+    h1[d] = cell[4 * d] / S.M[d];
+    Snew[d] = std::max(0, (int)std::ceil(2.0 * S.a / h1[d]) - 1);
+    if (Snew[d] > S.B[d])
+      return set_err(MSM_ERR_CAPACITY, "cell compressed beyond the plan's stencil radius: create the plan for the "
+                                       "most compressed cell it must serve");
+  }
+  SysDev D = E.hsys[0];
+  for (int d = 0; d < 3; d++) {
+    S.L[d] = cell[4 * d];
+    S.h1[d] = h1[d];
+    S.S[d] = Snew[d];
+    S.edge[d] = S.L[d] / S.C[d];
+    S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
+    D.Ld[d] = S.L[d];
+    D.edged[d] = S.edge[d];
+    D.edge[d] = (float)S.edge[d];
+    D.invL[d] = (float)(1.0 / S.L[d]);
+    D.inv_h1[d] = (float)(1.0 / S.h1[d]);
+    D.Lf[d] = (float)S.L[d];
+    D.h1f[d] = (float)S.h1[d];
+    D.nnbr[d] = S.nnbr[d];
+  }
+  E.hsys[0] = D;
+  const int hz = (S.B[2] + 3) & ~3;
+  launch_cell_update(E.d_sys, D, S.h1, S.a, S.p, S.B, hz, S.kball_off, S.dkh_off, S.wb_off, S.wh_off, E.d_kpool,
+                     E.d_wpool, (cudaStream_t)stream);
+  E.have_fwd = false;  // the workspace holds results for the old cell
+  return check_launch("msm_plan_set_cell");
 }
 
 int msm_field(msm_plan plan, void* workspace, float* field, void* stream) {

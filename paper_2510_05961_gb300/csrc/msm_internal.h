@@ -151,5 +151,9 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s);
+// dynamic cell (k_cell.cu): new system descriptor and ball stencils of a periodic p = 4 plan
+void launch_cell_update(SysDev* d_sys, const SysDev& val, const double h1[3], double a, int p, const int B[3], int hz,
+                        long long kball_off, long long dkh_off, long long wb_off, long long wh_off, float* kpool,
+                        int* wpool, cudaStream_t s);
 
 }  // namespace msm

@@ -664,6 +664,10 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       wh_off = (long long)wp.size();
       wp.insert(wp.end(), S.whalf.begin(), S.whalf.end());
     }
+    S.kball_off = kball_off;
+    S.dkh_off = dkh_off;
+    S.wb_off = wb_off;
+    S.wh_off = wh_off;
     for (int l = 1; l <= S.ncomp; l++) {
       LevDev& L = hlev[hs[s].lev0 + l - 1];
       const LevelHost& Lv = S.lev[l - 1];

@@ -43,6 +43,8 @@ struct SysHost {
   std::vector<float> sball, dsh;     // ball-kernel stencil on [-B, B]^3 and half-space virial weights (6x)
   std::vector<float> fsh;            // p = 4: factorized half-space virial weights g = k_1'(|v|)/|v|
   std::vector<int> wball, whalf;     // column half-widths of sball / dsh, -1 = empty column
+  // offsets of this system's ball stencil, virial weights and column tables in the device pools
+  long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1;
 };
 
 int plan_system(const msm_params& P, SysHost& S, std::string* err);

@@ -11,6 +11,8 @@ from __future__ import annotations
 
 import ctypes as C
 
+import numpy as np
+
 import torch
 
 from . import _lib as L
@@ -105,6 +107,14 @@ class Plan:
             W = W.view(3, 3)
             self.last_virial = W
         return gp, gq, W
+
+    def set_cell(self, cell):
+        """New orthorhombic cell (3 lengths or a 3x3 / 9-entry matrix) for this periodic p = 4 plan: the
+        stencils are recomputed on the device; grid counts and stencil sizes stay (see msm_plan_set_cell)."""
+        c = np.asarray(cell, dtype=np.float64)
+        c = np.diag(c) if c.shape == (3,) else c.reshape(3, 3)
+        arr = (C.c_double * 9)(*[float(v) for v in c.reshape(9)])
+        L.check(self.lib.msm_plan_set_cell(self.handle, arr, _stream(self.device)))
 
     def field(self, out=None):
         """Field -grad phi (n, 3) float32 at every atom from the last forward (forces = q * field)."""

@@ -1,0 +1,105 @@
+"""Dynamic cells (msm_plan_set_cell): one plan, its cell changed between calls.
+
+The plan keeps its grid counts M and stencil sizes; the device recomputes the
+stencils for the new spacings h_1 = L / M. Each cell is checked against the
+FP64 oracle planned for that cell with the same M (grid_override), with the
+parity tolerances; a compression beyond the plan's stencil radius is refused;
+returning to the creation cell reproduces a fresh plan.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2510_05961_gb300 import Plan, build  # noqa: E402
+from paper_2510_05961_gb300 import _lib as L  # noqa: E402
+from paper_2510_05961_gb300 import workloads as W  # noqa: E402
+
+E_TOL = 1e-5
+F_TOL = 1e-4
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    import oracle as O
+    O.build()
+
+
+def rel_rms(a, b):
+    a = np.asarray(a, np.float64).reshape(len(a), -1)
+    b = np.asarray(b, np.float64).reshape(len(b), -1)
+    return float(np.sqrt(((a - b) ** 2).sum(1).mean() / max((b ** 2).sum(1).mean(), 1e-300)))
+
+
+def run(plan, pos, q):
+    E, phi, F = plan.forward(torch.from_numpy(pos).to(DEV), torch.from_numpy(q).to(DEV), forces=True, virial=True)
+    gp, gq, Wv = plan.backward(torch.ones(1, dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return dict(E=float(E.cpu()[0]), phi=phi.cpu().numpy(), F=F.cpu().numpy(), W=Wv.cpu().numpy())
+
+
+def oracle_for(cell, w, M, pos):
+    import oracle as O
+    P = O.make_plan(cell, w.pbc, w.h, w.a, w.p, w.levels, tuple(M))
+    return O.msm(P, pos.astype(np.float64), w.q.astype(np.float64), forces=True, virial=True)
+
+
+@pytest.mark.parametrize("n,seed", [(20001, 91), (3000, 92)])
+def test_cell_changes_match_oracle(n, seed):
+    import oracle as O
+    w = W.random_box(n, seed=seed)
+    M = [O.plan_for(w).M[d] for d in range(3)]
+    base = np.array(w.cell, np.float64)
+    # built for the most compressed cell it will serve
+    plan = Plan(tuple(base * 0.97), w.pbc, w.h, w.a, w.p, w.levels, tuple(M), max_atoms=w.n, device=DEV)
+    for s in [(1.0, 1.0, 1.0), (1.04, 0.99, 1.02), (0.97, 0.97, 0.97), (1.1, 1.1, 1.1)]:
+        cell = base * np.array(s)
+        pos = (w.pos.astype(np.float64) * np.array(s)).astype(np.float32)
+        plan.set_cell(cell)
+        info = plan.info()
+        assert np.allclose(info["h1"], cell / np.array(M))
+        r = run(plan, pos, w.q)
+        ref = oracle_for(cell, w, M, pos)
+        assert abs(r["E"] - ref["E"]) <= E_TOL * abs(ref["E"]), (s, r["E"], ref["E"])
+        assert rel_rms(r["F"], ref["F"]) <= F_TOL, s
+        assert rel_rms(r["phi"], ref["phi"]) <= F_TOL, s
+        assert np.abs(r["W"] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), s
+
+
+def test_compression_beyond_capacity_is_refused_and_creation_cell_is_reproduced():
+    import oracle as O
+    w = W.random_box(8000, seed=93)
+    M = [O.plan_for(w).M[d] for d in range(3)]
+    base = np.array(w.cell, np.float64)
+    plan = Plan(tuple(base), w.pbc, w.h, w.a, w.p, w.levels, tuple(M), max_atoms=w.n, device=DEV)
+    r0 = run(plan, w.pos, w.q)
+    with pytest.raises(L.MsmError) as e:
+        plan.set_cell(base * 0.8)
+    assert e.value.code == L.MSM_ERR_CAPACITY
+    plan.set_cell(base * 1.05)
+    run(plan, (w.pos.astype(np.float64) * 1.05).astype(np.float32), w.q)
+    plan.set_cell(base)
+    r1 = run(plan, w.pos, w.q)
+    assert r1["E"] == pytest.approx(r0["E"], rel=1e-6)
+    assert np.allclose(r1["F"], r0["F"], rtol=1e-4, atol=1e-5 * np.abs(r0["F"]).max())
+    assert np.allclose(r1["W"], r0["W"], rtol=1e-5, atol=1e-6 * np.abs(r0["W"]).max())
+
+
+def test_unsupported_plans_are_refused():
+    w = W.random_box(500, seed=94, pbc=(1, 1, 0))
+    plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, max_atoms=w.n, device=DEV)
+    with pytest.raises(L.MsmError) as e:
+        plan.set_cell(np.array(w.cell) * 1.01)
+    assert e.value.code == L.MSM_ERR_UNSUPPORTED
+    w6 = W.random_box(500, seed=95, p=6)
+    plan6 = Plan(w6.cell, w6.pbc, w6.h, w6.a, w6.p, w6.levels, max_atoms=w6.n, device=DEV)
+    with pytest.raises(L.MsmError) as e:
+        plan6.set_cell(np.array(w6.cell) * 1.01)
+    assert e.value.code == L.MSM_ERR_UNSUPPORTED
