@@ -195,6 +195,24 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
  * Returns MSM_ERR_NO_FORWARD without a prior forward on workspace. */
 int msm_field(msm_plan plan, void* workspace, float* field, void* stream);
 
+/* Vector-Jacobian product of the forces of the last msm_forward on workspace
+ * (the derivatives of Sec. 3.2.2 taken once more, for training through the
+ * forces): for an upstream u, L = sum_k u_k . F_k,
+ *   dL/dq_i = u_i . E_i - psi(r_i),
+ *   dL/dr_i = -q_i ((grad grad G)(r_i) u_i + grad psi(r_i)),
+ * with E the field (msm_field), G(r) = sum_b q_b A(r, r_b) the potential of
+ * the charges as a function of the evaluation point and psi the potential of
+ * the dipoles p_b = q_b u_b (phi = A q with A symmetric). The grid part of psi
+ * sends the dipole grid charge sum_b p_b . grad Phi_m(r_b) through the same
+ * restriction, stencils and prolongation as the charges; the short-range part
+ * and the pair Hessians use k_0, k_0', k_0''.
+ *  u        device, n x 3 float32, caller's order.
+ *  dL_dq    device, n float32, or NULL.
+ *  dL_dpos  device, n x 3 float32, or NULL.
+ * Stream-ordered. Consumes the workspace: a later msm_backward needs a new
+ * msm_forward. Returns MSM_ERR_NO_FORWARD without a prior forward. */
+int msm_force_vjp(msm_plan plan, void* workspace, const float* u, float* dL_dq, float* dL_dpos, void* stream);
+
 /* Autotuner (no counterpart in the paper, whose JAX code leaves launch shapes
  * to XLA): runs one forward on (n, pos, q) to fill workspace, then times each
  * tunable launch shape on those inputs and keeps the fastest for every later
@@ -282,6 +300,9 @@ int msm_batch_backward(msm_batch batch, void* workspace, const double* grad_ener
                        float* dE_dq, double* virial, void* stream);
 /* msm_field for a batch: field (sum n) x 3, packed like the positions. */
 int msm_batch_field(msm_batch batch, void* workspace, float* field, void* stream);
+/* msm_force_vjp for a batch: u, dL_dpos (sum n) x 3 and dL_dq (sum n), packed like the positions. */
+int msm_batch_force_vjp(msm_batch batch, void* workspace, const float* u, float* dL_dq, float* dL_dpos,
+                        void* stream);
 int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status);
 /* msm_autotune for a batch (all systems share the tuned shapes), and the shapes in use. */
 int msm_batch_autotune(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,

@@ -30,7 +30,8 @@ EXPORTS = [
     "msm_backward", "msm_status", "msm_debug_offset", "msm_last_error", "msm_batch_create", "msm_batch_destroy",
     "msm_batch_workspace_bytes", "msm_batch_forward", "msm_batch_backward", "msm_batch_status", "msm_profile",
     "msm_profile_read", "msm_forward_noalloc", "msm_autotune", "msm_batch_autotune", "msm_batch_get_tuning",
-    "msm_set_tuning", "msm_batch_set_tuning", "msm_field", "msm_batch_field", "msm_plan_set_cell",
+    "msm_set_tuning", "msm_batch_set_tuning", "msm_field", "msm_batch_field", "msm_plan_set_cell", "msm_force_vjp",
+    "msm_batch_force_vjp",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 PHASES = ["bin", "short", "anterp", "restrict", "stencil", "prolong", "interp", "final", "virial", "bscale"]
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
     L.msm_batch_status.argtypes = [_vp, _vp, _vp, C.POINTER(C.c_int)]
     L.msm_field.argtypes = [_vp, _vp, _vp, _vp]
     L.msm_plan_set_cell.argtypes = [_vp, C.POINTER(C.c_double), _vp]
+    L.msm_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.msm_batch_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_batch_field.argtypes = [_vp, _vp, _vp, _vp]
     L.msm_forward_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]
     L.msm_profile.argtypes = [_vp, C.c_int]

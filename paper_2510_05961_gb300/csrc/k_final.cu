@@ -191,6 +191,56 @@ void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items
                                              dE_dpos, dE_dq);
 }
 
+// upstream vectors of the forces into the sorted order, with the charge: us[k] = (u_perm[k], q_k)
+__global__ void __launch_bounds__(kChunk) k_sort_u(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                                                   const int* __restrict__ perm, const float4* __restrict__ xq,
+                                                   const float* __restrict__ u, float4* __restrict__ us) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  long long g = perm[k];
+  us[k] = make_float4(u[3 * g], u[3 * g + 1], u[3 * g + 2], xq[k].w);
+}
+
+// L = sum_k u_k . F_k:  dL/dq_i = u_i . E_i - psi_i,
+//                        dL/dr_i = -q_i ((grad grad G) u_i + grad psi)_i,
+// hg = ((H u)_grid, u . E), hs = ((H u)_short incl. grad psi_short, psi_short),
+// phi_lr = psi_grid and f_lr = -grad psi_grid from the dipole grid chain.
+__global__ void __launch_bounds__(kChunk) k_fvjp_final(const SysDev* __restrict__ sys,
+                                                       const AtomItem* __restrict__ items,
+                                                       const int* __restrict__ perm, const float4* __restrict__ xq,
+                                                       const float4* __restrict__ hg, const float4* __restrict__ hs,
+                                                       const float* __restrict__ psi_lr,
+                                                       const float4* __restrict__ f_lr, float* __restrict__ dq,
+                                                       float* __restrict__ dpos) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  long long g = perm[k];
+  const float4 a = hg[k], b = hs[k], c = f_lr[k];
+  if (dq) dq[g] = a.w - b.w - psi_lr[k];
+  if (dpos) {
+    const float q = xq[k].w;
+    dpos[3 * g + 0] = -q * (a.x + b.x - c.x);
+    dpos[3 * g + 1] = -q * (a.y + b.y - c.y);
+    dpos[3 * g + 2] = -q * (a.z + b.z - c.z);
+  }
+}
+
+void launch_sort_u(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float* u, float4* us,
+                   cudaStream_t s) {
+  k_sort_u<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, u, us);
+}
+
+void launch_fvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* hs, float* dq,
+                       float* dpos, cudaStream_t s) {
+  k_fvjp_final<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.f_sr, hs, w.phi_lr, w.f_lr, dq, dpos);
+}
+
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s) {
   k_field<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.f_sr, w.f_lr, field);
 }

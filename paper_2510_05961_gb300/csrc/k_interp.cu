@@ -58,6 +58,41 @@ __device__ __forceinline__ void bspline_weights(float f, float (&w)[P], float (&
   }
 }
 
+// Weights, u-derivatives and second u-derivatives of the P grid points of
+// one axis: N_P'' (x) = N_(P-2)(x) - 2 N_(P-2)(x-1) + N_(P-2)(x-2).
+template <int P>
+__device__ __forceinline__ void bspline_weights2(float f, float (&w)[P], float (&dw)[P], float (&d2w)[P]) {
+  float c[P], cp[P], cpp[P];
+#pragma unroll
+  for (int k = 0; k < P; k++) c[k] = (k == 0) ? 1.0f : 0.0f;
+#pragma unroll
+  for (int m = 2; m <= P; m++) {
+    if (m == P - 1) {
+#pragma unroll
+      for (int k = 0; k < P; k++) cpp[k] = c[k];  // N_(P-2)(f + k)
+    }
+    if (m == P) {
+#pragma unroll
+      for (int k = 0; k < P; k++) cp[k] = c[k];   // N_(P-1)(f + k)
+    }
+    const float inv = 1.0f / (float)(m - 1);
+#pragma unroll
+    for (int k = m - 1; k >= 0; k--) {
+      float lower = (k > 0) ? c[k - 1] : 0.0f;
+      c[k] = ((f + (float)k) * c[k] + ((float)(m - k) - f) * lower) * inv;
+    }
+  }
+  auto at2 = [&](int k) { return (k >= 0 && k <= P - 3) ? cpp[k] : 0.0f; };
+#pragma unroll
+  for (int j = 0; j < P; j++) {
+    w[j] = c[P - 1 - j];
+    float hi = (P - 1 - j <= P - 2) ? cp[P - 1 - j] : 0.0f;
+    float lo = (P - 2 - j >= 0) ? cp[P - 2 - j] : 0.0f;
+    dw[j] = hi - lo;
+    d2w[j] = at2(P - 1 - j) - 2.0f * at2(P - 2 - j) + at2(P - 3 - j);
+  }
+}
+
 // Centred B-spline Phi_P(t): zero for |t| >= P/2; on |t| in [i, i+1) the
 // polynomial S.bsp[i][.] (ascending powers) of the local variable |t| - i.
 template <int P>
@@ -76,6 +111,28 @@ __device__ __forceinline__ float bspline_value(float t, const float (&cf)[P / 2]
   return w;
 }
 
+// Phi_P(t) and its derivative Phi_P'(t) (odd) from the same pieces.
+template <int P>
+__device__ __forceinline__ void bspline_value_d(float t, const float (&cf)[P / 2][P], float& v, float& dv) {
+  const float a = fabsf(t);
+  const int i = (int)a;
+  v = 0.f;
+  dv = 0.f;
+#pragma unroll
+  for (int piece = 0; piece < P / 2; piece++) {
+    const float s = a - (float)piece;
+    float pv = cf[piece][P - 1], pd = (float)(P - 1) * cf[piece][P - 1];
+#pragma unroll
+    for (int k = P - 2; k >= 0; k--) {
+      pv = fmaf(pv, s, cf[piece][k]);
+      if (k >= 1) pd = fmaf(pd, s, (float)k * cf[piece][k]);
+    }
+    v = (i == piece) ? pv : v;
+    dv = (i == piece) ? pd : dv;
+  }
+  dv = t < 0.f ? -dv : dv;
+}
+
 // Anterpolation by grid columns. A block owns a tile of 16 x 8 grid columns
 // (x, y) and TZ points along z (16, 32 or 64, chosen by the autotuner); each thread owns one column and sums,
 // over the atoms of the cells whose B-spline support reaches that column,
@@ -89,11 +146,17 @@ __device__ __forceinline__ float bspline_value(float t, const float (&cf)[P / 2]
 constexpr int kAntNT = kAnterpTX * kAnterpTY;
 static_assert(kAnterpTX == 16 && kAnterpTY == 8, "one parity class of 8 x 4 columns per warp");
 
-template <int P, int TZ>
+//
+// DIP: the same gather for point dipoles p_i = q_i u_i (us holds (u_i, q_i)
+// sorted): the grid charge of a dipole is p_i . grad Phi_m(r_i), i.e. per
+// column A w_z + B dw_z with A = p_x Phi_x' Phi_y / h_x + p_y Phi_x Phi_y' / h_y
+// and B = p_z Phi_x Phi_y / h_z (the force vector-Jacobian product).
+template <int P, int TZ, bool DIP = false>
 __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                   const TileItem* __restrict__ items,
                                                   const int* __restrict__ cell_start,
-                                                  const float4* __restrict__ uq, float* __restrict__ grid) {
+                                                  const float4* __restrict__ uq, float* __restrict__ grid,
+                                                  const float4* __restrict__ us = nullptr) {
   constexpr int H = P / 2;
   constexpr int PAD = P - 1;
   constexpr int NZ = TZ + 2 * PAD;
@@ -146,27 +209,52 @@ __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__
         const int kz = floordiv_i(uz, Cz), wz = uz - kz * Cz;
         const int wend = min(Cz - 1, wz + (ch[2] - uz));
         const int zsh = kz * S.M[2] - m[2];  // z-base relative to the tile's first point
-        auto add = [&](const float4 u) {
-          const float wxy = u.w * bspline_value<P>(mx - u.x, cf) * bspline_value<P>(my - u.y, cf);
+        auto add = [&](const float4 u, const float4 pu) {
           const float fl = floorf(u.z);
           const int r = (int)fl + zsh - H + 1;  // first of the p z-points, tile-relative
-          if (wxy != 0.f && r >= -PAD && r < zlen) {
-            float wz[P], dummy[P];
-            bspline_weights<P, false>(u.z - fl, wz, dummy);
+          if constexpr (!DIP) {
+            const float wxy = u.w * bspline_value<P>(mx - u.x, cf) * bspline_value<P>(my - u.y, cf);
+            if (wxy != 0.f && r >= -PAD && r < zlen) {
+              float wz[P], dummy[P];
+              bspline_weights<P, false>(u.z - fl, wz, dummy);
 #pragma unroll
-            for (int jz = 0; jz < P; jz++) col[r + PAD + jz][t] = fmaf(wxy, wz[jz], col[r + PAD + jz][t]);
+              for (int jz = 0; jz < P; jz++) col[r + PAD + jz][t] = fmaf(wxy, wz[jz], col[r + PAD + jz][t]);
+            }
+          } else {
+            float vx, dvx, vy, dvy;
+            bspline_value_d<P>(mx - u.x, cf, vx, dvx);  // d/du Phi(u - m) = -Phi'(m - u)
+            bspline_value_d<P>(my - u.y, cf, vy, dvy);
+            const float px = pu.w * pu.x, py = pu.w * pu.y, pz = pu.w * pu.z;
+            const float A = -(px * dvx * vy * S.inv_h1[0] + py * vx * dvy * S.inv_h1[1]);
+            const float B = pz * vx * vy * S.inv_h1[2];
+            if ((A != 0.f || B != 0.f) && r >= -PAD && r < zlen) {
+              float wz[P], dwz[P];
+              bspline_weights<P, true>(u.z - fl, wz, dwz);
+#pragma unroll
+              for (int jz = 0; jz < P; jz++)
+                col[r + PAD + jz][t] = fmaf(A, wz[jz], fmaf(B, dwz[jz], col[r + PAD + jz][t]));
+            }
           }
         };
         const int je = cs[wend + 1];
         int j = cs[wz];
+        const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
         for (; j + 3 < je; j += 4) {  // four loads in flight
           const float4 u0 = uq[j], u1 = uq[j + 1], u2 = uq[j + 2], u3 = uq[j + 3];
-          add(u0);
-          add(u1);
-          add(u2);
-          add(u3);
+          if constexpr (DIP) {
+            const float4 p0 = us[j], p1 = us[j + 1], p2 = us[j + 2], p3 = us[j + 3];
+            add(u0, p0);
+            add(u1, p1);
+            add(u2, p2);
+            add(u3, p3);
+          } else {
+            add(u0, none);
+            add(u1, none);
+            add(u2, none);
+            add(u3, none);
+          }
         }
-        for (; j < je; j++) add(uq[j]);
+        for (; j < je; j++) add(uq[j], DIP ? us[j] : none);
         uz += wend - wz + 1;
       }
     }
@@ -238,6 +326,107 @@ static void run_anterp(const Work& w, const Tables& t, const TileItem* items, in
   if (tz == 16) k_anterp<P, 16><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
   else if (tz == 64) k_anterp<P, 64><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
   else k_anterp<P, 32><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
+}
+
+template <int P>
+static void run_anterp_dipole(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s,
+                              int tz, const float4* us) {
+  if (tz == 16) k_anterp<P, 16, true><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid, us);
+  else if (tz == 64) k_anterp<P, 64, true><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid, us);
+  else k_anterp<P, 32, true><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid, us);
+}
+
+void launch_anterp_dipole(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p,
+                          int tz, const float4* us) {
+  if (nitems <= 0) return;
+  switch (p) {
+    case 4: run_anterp_dipole<4>(w, t, items, nitems, s, tz, us); break;
+    case 6: run_anterp_dipole<6>(w, t, items, nitems, s, tz, us); break;
+    default: run_anterp_dipole<8>(w, t, items, nitems, s, tz, us); break;
+  }
+}
+
+// Hessian of the interpolated potential at every atom times its upstream
+// vector, (grad grad phi^(1+)(r_i)) u_i (second derivatives of the tensor
+// B-spline basis), and u_i . E_i from the stored field parts; in place over
+// the short-range field array: fout[k] = ((H u)_grid, u . E).
+template <int P>
+__global__ void __launch_bounds__(kChunk) k_interp_hess(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
+                                                        const AtomItem* __restrict__ items,
+                                                        const float4* __restrict__ uq, const float* __restrict__ grid,
+                                                        const float4* __restrict__ us, const float4* f_lr,
+                                                        float4* fsr_inout) {
+  constexpr int H = P / 2;
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  const float4 u = us[k];
+  const float4 ea = fsr_inout[k], eb = f_lr[k];
+  const float uE = u.x * (ea.x + eb.x) + u.y * (ea.y + eb.y) + u.z * (ea.z + eb.z);
+  float hx = 0.f, hy = 0.f, hz = 0.f;
+  if (S.ncomp >= 1) {
+    const LevDev& L = levs[S.lev0];
+    float4 u4 = uq[k];
+    float uu[3] = {u4.x, u4.y, u4.z};
+    float w[3][P], dw[3][P], d2w[3][P];
+    int ix[3][P];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      float fl = floorf(uu[d]);
+      int base = (int)fl - H + 1;
+      bspline_weights2<P>(uu[d] - fl, w[d], dw[d], d2w[d]);
+#pragma unroll
+      for (int j = 0; j < P; j++) {
+        int m = base + j;
+        ix[d][j] = L.per[d] ? wrap_i(m, L.n[d]) : m - L.lo[d];
+      }
+    }
+    const float* e = grid + L.e_off;
+    float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+#pragma unroll
+    for (int jx = 0; jx < P; jx++) {
+#pragma unroll
+      for (int jy = 0; jy < P; jy++) {
+        const float* row = e + ((long long)ix[0][jx] * L.n[1] + ix[1][jy]) * L.n[2];
+        float sz = 0.f, dsz = 0.f, d2sz = 0.f;
+#pragma unroll
+        for (int jz = 0; jz < P; jz++) {
+          float ev = __ldg(row + ix[2][jz]);
+          sz = fmaf(w[2][jz], ev, sz);
+          dsz = fmaf(dw[2][jz], ev, dsz);
+          d2sz = fmaf(d2w[2][jz], ev, d2sz);
+        }
+        gxx = fmaf(d2w[0][jx] * w[1][jy], sz, gxx);
+        gyy = fmaf(w[0][jx] * d2w[1][jy], sz, gyy);
+        gzz = fmaf(w[0][jx] * w[1][jy], d2sz, gzz);
+        gxy = fmaf(dw[0][jx] * dw[1][jy], sz, gxy);
+        gxz = fmaf(dw[0][jx] * w[1][jy], dsz, gxz);
+        gyz = fmaf(w[0][jx] * dw[1][jy], dsz, gyz);
+      }
+    }
+    const float ax = S.inv_h1[0], ay = S.inv_h1[1], az = S.inv_h1[2];
+    gxx *= ax * ax;
+    gyy *= ay * ay;
+    gzz *= az * az;
+    gxy *= ax * ay;
+    gxz *= ax * az;
+    gyz *= ay * az;
+    hx = gxx * u.x + gxy * u.y + gxz * u.z;
+    hy = gxy * u.x + gyy * u.y + gyz * u.z;
+    hz = gxz * u.x + gyz * u.y + gzz * u.z;
+  }
+  fsr_inout[k] = make_float4(hx, hy, hz, uE);
+}
+
+void launch_interp_hess(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
+                        cudaStream_t s, int p) {
+  switch (p) {
+    case 4: k_interp_hess<4><<<nitems, kChunk, 0, s>>>(t.sys, t.lev, items, w.uq, w.grid, us, w.f_lr, w.f_sr); break;
+    case 6: k_interp_hess<6><<<nitems, kChunk, 0, s>>>(t.sys, t.lev, items, w.uq, w.grid, us, w.f_lr, w.f_sr); break;
+    default: k_interp_hess<8><<<nitems, kChunk, 0, s>>>(t.sys, t.lev, items, w.uq, w.grid, us, w.f_lr, w.f_sr); break;
+  }
 }
 
 // tz: the z-extent of the tiles the items were built for (16, 32 or 64)

@@ -183,6 +183,110 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
   }
 }
 
+// Short-range part of the vector-Jacobian product of the forces (L =
+// sum_k u_k . F_k for an upstream u, Sec. 3.2.2's derivatives taken once
+// more): with p_b = q_b u_b, f1 = k_0'(r)/r and the pair Hessian
+// H0(d) = f2 d d^T + f1 I, f2 = (k_0'' - k_0'/r)/r^2,
+//   psi0_i = sum_(b,n) f1 p_b . d           (potential at r_i of the dipoles p_b),
+//   h0_i   = sum_(b,n) q_b H0(d) (u_i - u_b) (the short-range rows of H u, / q_i),
+// d = r_b + A n - r_i, over the same candidates as k_short. In s = 1 - r^2/a^2,
+// f1 = -1/r^3 + sum_k gdca[k] s^k and f2 = 3/r^5 - (2/a^2) sum_k k gdca[k] s^(k-1).
+// us holds (u, q) in the sorted order; out gets (h0, psi0).
+template <int P>
+__global__ void __launch_bounds__(kChunk) k_short_fvjp(const SysDev* __restrict__ sys,
+                                                       const AtomItem* __restrict__ items,
+                                                       const int* __restrict__ cell_start,
+                                                       const int* __restrict__ scell, const float4* __restrict__ xq,
+                                                       const float4* __restrict__ us, float4* __restrict__ out) {
+  const AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int local = it.start + (int)threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  const int k = S.atom_off + local;
+  const float4 xi = xq[k];
+  const float4 ui = us[k];
+  const int cell = scell[k];
+  const int Cx = S.C[0], Cy = S.C[1], Cz = S.C[2];
+  const int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
+  float gdc[P - 1];
+#pragma unroll
+  for (int t = 0; t < P - 1; t++) gdc[t] = S.gdca[t];
+  const float a2 = S.a2, inv_a2 = S.inv_a2;
+  const float ex = S.edge[0], ey = S.edge[1], inv_ez = 1.0f / S.edge[2];
+  constexpr float mg = 2e-4f;
+  float psi = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+  for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
+    const int ux = ci[0] + ox;
+    if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
+    const int wx = ux - floordiv_s(ux, Cx) * Cx;
+    const float bx = (float)ox * ex - xi.x;
+    const float mx = fmaxf((ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f)) - mg * ex, 0.f);
+    for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
+      const int uy = ci[1] + oy;
+      if (!S.pbc[1] && (uy < 0 || uy >= Cy)) continue;
+      const float by = (float)oy * ey - xi.y;
+      const float my = fmaxf((oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f)) - mg * ey, 0.f);
+      const float rxy2 = mx * mx + my * my;
+      if (rxy2 >= a2) continue;
+      const int wy = uy - floordiv_s(uy, Cy) * Cy;
+      const float zr = sqrtf(a2 - rxy2) + mg * S.edge[2];
+      int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
+      if (!S.pbc[2]) {
+        zlo = max(zlo, 0);
+        zhi = min(zhi, Cz - 1);
+      }
+      const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
+      int uz = zlo;
+      while (uz <= zhi) {
+        const int kz = floordiv_s(uz, Cz);
+        const int wz = uz - kz * Cz;
+        const int wend = min(Cz - 1, wz + (zhi - uz));
+        const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+        const float bz = image_shift(kz, S.Ld[2], xi.z);
+        for (int j = jb; j < je; j++) {
+          const float4 xj = xq[j];
+          const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < a2 && r2 > 0.f) {
+            const float4 uj = us[j];
+            const float rinv = rsqrtf(r2);
+            const float rinv2 = rinv * rinv;
+            const float s = 1.0f - r2 * inv_a2;
+            float p1 = gdc[P - 2], dp1 = (float)(P - 2) * gdc[P - 2];
+#pragma unroll
+            for (int c = P - 3; c >= 0; c--) {
+              p1 = fmaf(p1, s, gdc[c]);
+              if (c >= 1) dp1 = fmaf(dp1, s, (float)c * gdc[c]);
+            }
+            if (P - 2 < 1) dp1 = 0.f;
+            const float f1 = fmaf(-rinv2, rinv, p1);
+            const float f2 = fmaf(3.0f * rinv2 * rinv2, rinv, -2.0f * inv_a2 * dp1);
+            // dipole potential p_b . d f1
+            psi = fmaf(f1 * uj.w, uj.x * dx + uj.y * dy + uj.z * dz, psi);
+            // q_b H0(d) (u_i - u_b)
+            const float wxv = ui.x - uj.x, wyv = ui.y - uj.y, wzv = ui.z - uj.z;
+            const float dw = f2 * (dx * wxv + dy * wyv + dz * wzv);
+            hx = fmaf(uj.w, fmaf(dw, dx, f1 * wxv), hx);
+            hy = fmaf(uj.w, fmaf(dw, dy, f1 * wyv), hy);
+            hz = fmaf(uj.w, fmaf(dw, dz, f1 * wzv), hz);
+          }
+        }
+        uz += wend - wz + 1;
+      }
+    }
+  }
+  out[k] = make_float4(hx, hy, hz, psi);
+}
+
+void launch_short_fvjp(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
+                       float4* out, cudaStream_t s, int p) {
+  switch (p) {
+    case 4: k_short_fvjp<4><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, us, out); break;
+    case 6: k_short_fvjp<6><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, us, out); break;
+    default: k_short_fvjp<8><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, us, out); break;
+  }
+}
+
 template <int P, int NB>
 static void run_short_nb(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                          cudaStream_t s) {

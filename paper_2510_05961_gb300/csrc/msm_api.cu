@@ -403,6 +403,59 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
   return run_backward(plan->eng, workspace, grad_energy, dE_dpos, dE_dq, virial, (cudaStream_t)stream);
 }
 
+// Vector-Jacobian product of the forces of the last forward on ws for an
+// upstream u (n x 3, caller's order): L = sum_k u_k . F_k. With phi = A q (A
+// symmetric), G(r) = sum_b q_b A(r, r_b) and psi(r) = sum_b p_b . d_2 A(r, r_b)
+// the potential of the dipoles p_b = q_b u_b:
+//   dL/dq_i = u_i . E_i - psi(r_i),   dL/dr_i = -q_i ((grad grad G)(r_i) u_i + grad psi(r_i)).
+// The grid part of psi runs the dipole grid charge sum_b p_b . grad Phi_m(r_b)
+// through the same restriction, stencils and prolongation as the charges.
+// Consumes the workspace: a later msm_backward needs a new msm_forward.
+static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* dpos, cudaStream_t s) {
+  if (!E.have_fwd || ws != E.last_ws) return set_err(MSM_ERR_NO_FORWARD, "msm_force_vjp needs a prior msm_forward on this workspace");
+  if (E.last_n > 0 && !u) return set_err(MSM_ERR_INVALID_ARG, "u must not be NULL");
+  Work w = E.resolve(ws);
+  Tables t = E.tables();
+  const int nai = (int)E.atom_items.size();
+  if ((E.last_flags & MSM_WANT_FORCES) == 0) {
+    const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
+    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_block);
+    launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
+  }
+  if (E.last_n > 0) {
+    launch_sort_u(w, t, E.d_atom_items, nai, u, w.vjp_u, s);
+    launch_interp_hess(w, t, E.d_atom_items, nai, w.vjp_u, s, E.p);  // f_sr <- ((H u)_grid, u . E)
+    launch_short_fvjp(w, t, E.d_atom_items, nai, w.vjp_u, w.vjp_h, s, E.p);
+    launch_anterp_dipole(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz, w.vjp_u);
+    for (int l = 1; l < E.maxcomp; l++) {
+      int a = E.restrict_off[l - 1], b = E.restrict_off[l];
+      launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
+    }
+    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
+    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, s);
+    launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
+    for (int l = E.maxcomp - 1; l >= 1; l--) {
+      int a = E.prolong_off[l - 1], b = E.prolong_off[l];
+      launch_prolong(w, t, E.d_pro_items + a, b - a, s, E.p);
+    }
+    launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);  // phi_lr <- psi_grid, f_lr <- -grad psi_grid
+    launch_fvjp_final(w, t, E.d_atom_items, nai, w.vjp_h, dq, dpos, s);
+  }
+  E.have_fwd = false;
+  return check_launch("msm_force_vjp");
+}
+
+int msm_force_vjp(msm_plan plan, void* workspace, const float* u, float* dL_dq, float* dL_dpos, void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  return run_force_vjp(plan->eng, workspace, u, dL_dq, dL_dpos, (cudaStream_t)stream);
+}
+
+int msm_batch_force_vjp(msm_batch batch, void* workspace, const float* u, float* dL_dq, float* dL_dpos,
+                        void* stream) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return run_force_vjp(batch->eng, workspace, u, dL_dq, dL_dpos, (cudaStream_t)stream);
+}
+
 int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
   if (!plan || !cell) return set_err(MSM_ERR_INVALID_ARG, "plan and cell must not be NULL");
   Engine& E = plan->eng;

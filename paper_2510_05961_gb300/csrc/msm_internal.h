@@ -109,6 +109,8 @@ struct Work {
   double* part_wg; // per virial item: 6 grid virial components
   double* part_vs; // per system and reduction slice: 6 virial components
   float* grid;     // grid pool
+  float4* vjp_u;   // force vector-Jacobian product: upstream (u, q), sorted
+  float4* vjp_h;   // force vector-Jacobian product: short-range rows of H u and psi, sorted
 };
 
 struct Tables {
@@ -151,6 +153,17 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s);
+// vector-Jacobian product of the forces (k_final.cu, k_short.cu, k_interp.cu)
+void launch_sort_u(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float* u, float4* us,
+                   cudaStream_t s);
+void launch_short_fvjp(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
+                       float4* out, cudaStream_t s, int p);
+void launch_interp_hess(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
+                        cudaStream_t s, int p);
+void launch_anterp_dipole(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p,
+                          int tz, const float4* us);
+void launch_fvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* hs, float* dq,
+                       float* dpos, cudaStream_t s);
 // dynamic cell (k_cell.cu): new system descriptor and ball stencils of a periodic p = 4 plan
 void launch_cell_update(SysDev* d_sys, const SysDev& val, const double h1[3], double a, int p, const int B[3], int hz,
                         long long kball_off, long long dkh_off, long long wb_off, long long wh_off, float* kpool,

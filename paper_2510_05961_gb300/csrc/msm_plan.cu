@@ -787,6 +787,8 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(ball_items.size() + box_items.size(), 1));
   L_part_vs = take(sizeof(double) * 6 * 64 * (size_t)nsys);
   L_grid = take(sizeof(float) * std::max<long long>(grid_floats, 1));
+  L_vjp_u = take(sizeof(float4) * N);
+  L_vjp_h = take(sizeof(float4) * N);
   ws_bytes = off;
   return MSM_OK;
 }
@@ -906,6 +908,8 @@ Work Engine::resolve(void* ws) const {
   w.part_wg = (double*)(b + L_part_wg);
   w.part_vs = (double*)(b + L_part_vs);
   w.grid = (float*)(b + L_grid);
+  w.vjp_u = (float4*)(b + L_vjp_u);
+  w.vjp_h = (float4*)(b + L_vjp_h);
   return w;
 }
 

@@ -86,7 +86,8 @@ struct Engine {
   int* d_voff = nullptr;
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
-      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_w0, L_part_wg, L_part_vs, L_grid;
+      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_w0, L_part_wg, L_part_vs, L_grid, L_vjp_u,
+      L_vjp_h;
   size_t ws_bytes = 0;
   // state of the last forward pass
   bool have_fwd = false;

@@ -123,6 +123,17 @@ class Plan:
         L.check(self.lib.msm_field(self.handle, _ptr(self.workspace), _ptr(fld), _stream(self.device)))
         return fld
 
+    def force_vjp(self, u, dq=True, dpos=True):
+        """(dL/dq, dL/dpos) for L = sum_k u_k . F_k of the last forward (u: (n, 3) float32 device).
+        Consumes the workspace: a later backward needs a new forward."""
+        n = self._n
+        u = u.detach().to(device=self.device, dtype=torch.float32).contiguous()
+        gq = torch.empty(n, dtype=torch.float32, device=self.device) if dq else None
+        gp = torch.empty((n, 3), dtype=torch.float32, device=self.device) if dpos else None
+        L.check(self.lib.msm_force_vjp(self.handle, _ptr(self.workspace), _ptr(u), _ptr(gq), _ptr(gp),
+                                       _stream(self.device)))
+        return gq, gp
+
     def autotune(self, pos, q):
         """Time the tunable launch shapes on these inputs and keep the fastest; returns them.
         A new forward is needed before the next backward."""
@@ -195,7 +206,7 @@ class Plan:
 class MSMFunction(torch.autograd.Function):
     """(E, phi, F) of (pos, q) through the library.
 
-    Backward takes upstream gradients on E and on phi:
+    Backward takes upstream gradients on E, phi and F:
       E:   dE/dpos = -F, dE/dq = phi (the library's adjoint kernels); plan.last_virial
            holds W * dL/dE.
       phi: phi = A q with A symmetric (short-range kernel, self term and the grid chain
@@ -203,8 +214,8 @@ class MSMFunction(torch.autograd.Function):
              dL/dq = A g                           (potentials of charges g),
              dL/dr_k = -g_k E_k(q) - q_k E_k(g)    (E = -grad phi, the field),
            one more evaluation with charges g on the same positions.
-    An upstream gradient on F (Hessian terms) raises NotImplementedError. The plan's
-    workspace is reused: backward must follow its own forward."""
+      F:   msm_force_vjp (dipole potential and Hessian-vector products).
+    The plan's workspace is reused: backward must follow its own forward."""
 
     @staticmethod
     def forward(ctx, pos, q, plan):
@@ -218,20 +229,25 @@ class MSMFunction(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gE, gphi, gF):
-        if gF is not None and bool((gF != 0).any()):
-            raise NotImplementedError("gradients through the MSM forces are not implemented "
-                                      "(second-order terms); differentiate E or phi")
         use_phi = gphi is not None and bool((gphi != 0).any())
-        if gE is None and not use_phi:
+        use_F = gF is not None and bool((gF != 0).any())
+        if gE is None and not use_phi and not use_F:
             return None, None, None
         plan = ctx.plan
         gp = gq = None
+
+        def acc(a, b):
+            return b if a is None else (a if b is None else a + b)
+
         if gE is not None:
             gp, gq, _ = plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
+        Eq = plan.field() if use_phi else None  # field of q, before the workspace is reused
+        if use_F:
+            fq, fp = plan.force_vjp(gF, dq=ctx.need[1], dpos=ctx.need[0])
+            gq, gp = acc(gq, fq), acc(gp, fp)
         if use_phi:
             pos, q = ctx.saved_tensors
             g = gphi.detach().to(torch.float32).contiguous()
-            Eq = plan.field()  # field of q, before the workspace is reused
             _, phig, _ = plan.forward(pos, g, forces=False, virial=False, phi=True)
             if ctx.need[1]:
                 gq = phig if gq is None else gq + phig
@@ -314,6 +330,15 @@ class Batch:
         L.check(self.lib.msm_batch_backward(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gp), _ptr(gq), _ptr(W),
                                             _stream(self.device)))
         return gp, gq, (None if W is None else W.view(self.nsys, 3, 3))
+
+    def force_vjp(self, u, dq=True, dpos=True):
+        """Plan.force_vjp for the packed atoms of all systems."""
+        u = u.detach().to(device=self.device, dtype=torch.float32).contiguous()
+        gq = torch.empty(self.ntot, dtype=torch.float32, device=self.device) if dq else None
+        gp = torch.empty((self.ntot, 3), dtype=torch.float32, device=self.device) if dpos else None
+        L.check(self.lib.msm_batch_force_vjp(self.handle, _ptr(self.workspace), _ptr(u), _ptr(gq), _ptr(gp),
+                                             _stream(self.device)))
+        return gq, gp
 
     def field(self, out=None):
         """Field -grad phi ((sum n), 3) float32 at every atom of every system from the last forward."""

@@ -168,7 +168,7 @@ def test_autograd_function():
 
 def test_autograd_outputs_phi_and_forces():
     # (E, phi, F) from the autograd function: phi and F match the plain forward; a
-    # loss on E alone differentiates, an upstream gradient on phi or F is refused
+    # loss on E alone differentiates (phi and F upstreams: the tests below)
     from paper_2510_05961_gb300 import msm_outputs
     key = "rocksalt_6"
     w = WORKLOADS[key]()
@@ -181,9 +181,6 @@ def test_autograd_outputs_phi_and_forces():
     assert rel_rms(F.detach().cpu().numpy(), ref["F"]) <= F_TOL
     E.backward()
     assert rel_rms(q.grad.cpu().numpy(), ref["phi"]) <= F_TOL
-    E2, phi2, F2 = msm_outputs(pos, q, plan)
-    with pytest.raises(NotImplementedError):
-        (E2 + F2.sum()).backward()
 
 
 def _oracle_eval(w, charges):
@@ -210,6 +207,62 @@ def test_field_matches_oracle(key):
     assert rel_rms(plan.field().cpu().numpy(), ref["F"] / qq) <= F_TOL
     torch.cuda.synchronize()
     assert plan.status() == 0
+
+
+def _oracle_directional(w, u, eps=1e-4):
+    # references for L = sum_k u_k . F_k: dL/dq = -D_u phi and dL/dr = D_u F
+    # (central differences of the FP64 oracle when every atom moves along u)
+    import oracle as O
+    O.build()
+    P = O.plan_for(w)
+    pos = w.pos.astype(np.float64)
+    rp = O.msm(P, pos + eps * u, w.q.astype(np.float64), forces=True, virial=False)
+    rm = O.msm(P, pos - eps * u, w.q.astype(np.float64), forces=True, virial=False)
+    return -(rp["phi"] - rm["phi"]) / (2 * eps), (rp["F"] - rm["F"]) / (2 * eps)
+
+
+@pytest.mark.parametrize("key", ["rocksalt_6", "periodic_20001", "water_600", "slab_3000", "open_c1"])
+def test_gradient_through_forces(key):
+    # L = sum_k u_k . F_k through the autograd function (msm_force_vjp) against the oracle
+    from paper_2510_05961_gb300 import msm_outputs
+    w = WORKLOADS[key]()
+    rng = np.random.default_rng(78)
+    u = rng.normal(size=(w.n, 3)).astype(np.float32)
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV).requires_grad_(True)
+    q = torch.from_numpy(w.q).to(DEV).requires_grad_(True)
+    E, phi, F = msm_outputs(pos, q, plan)
+    (torch.from_numpy(u).to(DEV) * F).sum().backward()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    dq_ref, dr_ref = _oracle_directional(w, u.astype(np.float64))
+    assert rel_rms(q.grad.cpu().numpy(), dq_ref) <= F_TOL
+    assert rel_rms(pos.grad.cpu().numpy(), dr_ref) <= F_TOL
+
+
+def test_gradient_through_all_outputs():
+    # one loss on E, phi and F at once: the three backward parts add up
+    from paper_2510_05961_gb300 import msm_outputs
+    key = "rocksalt_6"
+    w = WORKLOADS[key]()
+    rng = np.random.default_rng(79)
+    u = rng.normal(size=(w.n, 3)).astype(np.float32)
+    g = (rng.choice([-1.0, 1.0], w.n) * rng.uniform(0.5, 1.5, w.n)).astype(np.float32)
+    c = 0.7
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV).requires_grad_(True)
+    q = torch.from_numpy(w.q).to(DEV).requires_grad_(True)
+    E, phi, F = msm_outputs(pos, q, plan)
+    (c * E + (torch.from_numpy(g).to(DEV) * phi).sum() + (torch.from_numpy(u).to(DEV) * F).sum()).backward()
+    torch.cuda.synchronize()
+    P, rq = _oracle(key)
+    rg = _oracle_eval(w, g)
+    qd, gd = w.q.astype(np.float64)[:, None], g.astype(np.float64)[:, None]
+    dq_F, dr_F = _oracle_directional(w, u.astype(np.float64))
+    dq_ref = c * rq["phi"] + rg["phi"] + dq_F
+    dpos_ref = -c * rq["F"] - gd * (rq["F"] / qd) - qd * (rg["F"] / gd) + dr_F
+    assert rel_rms(q.grad.cpu().numpy(), dq_ref) <= F_TOL
+    assert rel_rms(pos.grad.cpu().numpy(), dpos_ref) <= F_TOL
 
 
 @pytest.mark.parametrize("key", ["rocksalt_6", "periodic_20001", "water_600"])

@@ -493,6 +493,41 @@ def test_potential_adjoint_against_differences(oracle, pbc):
             assert fd == pytest.approx(-g[i] * Eq[i, d] - q[i] * Eg[i, d], rel=1e-5, abs=1e-6)
 
 
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0)])
+def test_force_vjp_identities_against_differences(oracle, pbc):
+    """For L = sum_k u_k . F_k: dL/dq = -D_u phi (the derivative of the potentials
+    when every atom moves along u, by the symmetry of A) and dL/dr = -H u =
+    D_u F (the symmetry of the Hessian); both sides by central differences
+    of the oracle."""
+    rng = np.random.default_rng(16)
+    pos, q, cell = _small_periodic()
+    if not any(pbc):
+        pos = np.clip(pos, 0.5, 8.5)
+    P = oracle.make_plan(cell, pbc, 1.2, 3.5, 4)
+    u = rng.normal(size=pos.shape)
+
+    def loss(pp, qq):
+        return float((u * oracle.msm(P, pp, qq, True, False)["F"]).sum())
+
+    eps = 1e-5
+    rp = oracle.msm(P, pos + eps * u, q, True, False)
+    rm = oracle.msm(P, pos - eps * u, q, True, False)
+    dq_ref = -(rp["phi"] - rm["phi"]) / (2 * eps)
+    dr_ref = (rp["F"] - rm["F"]) / (2 * eps)
+    for i in rng.choice(len(q), 4, replace=False):
+        h = 1e-5
+        qp, qm = q.copy(), q.copy()
+        qp[i] += h
+        qm[i] -= h
+        assert (loss(pos, qp) - loss(pos, qm)) / (2 * h) == pytest.approx(dq_ref[i], rel=1e-5, abs=1e-6)
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = (loss(pp, q) - loss(pm, q)) / (2 * h)
+            assert fd == pytest.approx(dr_ref[i, d], rel=1e-4, abs=1e-5)
+
+
 def test_half_cell_translation_invariance(oracle):
     # shifting a periodic system by L/2 moves every evaluated level by whole points
     pos, q, cell = _small_periodic()
