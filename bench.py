@@ -418,6 +418,32 @@ def run_gpu(args):
         dyn = {"set_cell_us": e0.elapsed_time(e1) / 20 * 1e3, "what": "msm_plan_set_cell: new cell lengths, "
                "stencil samples, virial weights and column tables recomputed on the device"}
 
+    # second-order backward paths (gradients through the outputs), CUDA events, 3 repetitions each:
+    # force VJP (L = sum u . F: dipole grid chain, B-spline and pair Hessians) and the potential
+    # gradient (one more evaluation with the upstream as charges), each after a fresh forward
+    import numpy as np
+    rng = np.random.default_rng(5)
+    u_dev = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).to(dev)
+    g_dev = torch.from_numpy(rng.normal(size=n).astype(np.float32)).to(dev)
+    tv, tp = 0.0, 0.0
+    for _ in range(3):
+        plan.forward(pos, q, forces=True, virial=False, phi=False)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        plan.force_vjp(u_dev)
+        a1.record(stream)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        plan.forward(pos, g_dev, forces=True, virial=False, phi=True)
+        plan.field()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        tv += a0.elapsed_time(a1) / 3
+        tp += b0.elapsed_time(b1) / 3
+    second = {"force_vjp_ms": tv, "phi_grad_ms": tp,
+              "what": "after a forward with forces: msm_force_vjp for a random upstream on F; the extra "
+                      "evaluation with charges g plus msm_field that the upstream on phi needs"}
+
     # end-to-end through the public API with host buffers (copies in the timed region)
     pos_h = torch.from_numpy(w.pos).pin_memory()
     q_h = torch.from_numpy(w.q).pin_memory()
@@ -497,6 +523,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_val, "unit": "atoms/s", "h2d_bytes_per_step": n * 16,
                     "d2h_bytes_per_step": n * 16 + 8 + 72, "ms_per_step": ms_e2e},
             "roofline": roof, "cpu_baseline": cpu, "batch": batch_res, "dynamic_cell": dyn,
+            "second_order": second,
         }
         print(json.dumps(line))
     if world > 1:

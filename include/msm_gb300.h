@@ -125,17 +125,20 @@ int msm_plan_get_info(msm_plan plan, msm_plan_info* info);
  * cell; Sec. 4.1 lists the limits of fixed-size stencil arrays). Gives the
  * plan a new orthorhombic cell while keeping its grid counts M, level ranges,
  * binning cells and stencil array sizes: the level-1 spacings become
- * h_1 = L / M and the stencil samples, the virial weights, the column tables
- * and the system descriptor are recomputed on the device, stream-ordered
- * (no host synchronisation; NPT loops call it between steps).
- *  cell    host, 9 doubles, row-major, diagonal (as msm_params.cell).
- * Supported for periodic systems (pbc 1, 1, 1) with order 4 and qi_mode 0
- * (MSM_ERR_UNSUPPORTED otherwise). The new cell may expand freely (coarser
- * spacings lower the accuracy, as the paper notes); it may be compressed
- * only while ceil(2 a / h_1) - 1 stays within the stencil radius the plan was
- * built with (MSM_ERR_CAPACITY otherwise: create the plan for the most
- * compressed cell it must serve). A later msm_backward needs a new
- * msm_forward. Positions passed afterwards are in the new cell. */
+ * h_1 = L / M and the stencils, the virial weights, the column tables and
+ * the system descriptor are recomputed, stream-ordered: on the device for a
+ * periodic system of order 4 with qi_mode 0 (every level a ball of raw
+ * samples, no host synchronisation), otherwise on the host with the plan's
+ * array sizes and copied from pinned staging buffers (the call then waits
+ * for the previous call's copy only).
+ *  cell    host, 9 doubles, row-major, diagonal (as msm_params.cell;
+ *          MSM_ERR_UNSUPPORTED for other cells).
+ * The new cell may expand freely (coarser spacings lower the accuracy, as
+ * the paper notes); it may be compressed only while ceil(2 a / h_1) - 1 stays
+ * within the sample radius the plan was built with (MSM_ERR_CAPACITY
+ * otherwise: create the plan for the most compressed cell it must serve).
+ * Open axes need the positions inside the new cell. A later msm_backward
+ * needs a new msm_forward. */
 int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream);
 
 /* Host-only (no device needed): the plan msm_plan_create would build from

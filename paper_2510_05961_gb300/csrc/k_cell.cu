@@ -115,6 +115,8 @@ __global__ void k_set_sys(SysDev* __restrict__ dst, SysDev val) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = val;
 }
 
+void launch_set_sys(SysDev* d_sys, const SysDev& val, cudaStream_t s) { k_set_sys<<<1, 32, 0, s>>>(d_sys, val); }
+
 void launch_cell_update(SysDev* d_sys, const SysDev& val, const double h1[3], double a, int p, const int B[3], int hz,
                         long long kball_off, long long dkh_off, long long wb_off, long long wh_off, float* kpool,
                         int* wpool, cudaStream_t s) {

@@ -466,17 +466,13 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
   }
   for (int d = 0; d < 3; d++)
     if (!(cell[4 * d] > 0.0)) return set_err(MSM_ERR_INVALID_ARG, "cell lengths must be > 0");
-  if (!(S.pbc[0] && S.pbc[1] && S.pbc[2]))
-    return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell needs a periodic system (pbc 1, 1, 1)");
-  if (!S.prefilter) return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell needs order 4 and qi_mode 0");
-  for (const LevelHost& Lv : S.lev)
-    if (Lv.kind != 0) return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell needs ball kernels on every level");
   double h1[3];
   int Snew[3];
   for (int d = 0; d < 3; d++) {
     h1[d] = cell[4 * d] / S.M[d];
     Snew[d] = std::max(0, (int)std::ceil(2.0 * S.a / h1[d]) - 1);
-    if (Snew[d] > S.B[d])
+    // the plan's arrays hold samples out to R - hw (its sample radius at creation)
+    if (Snew[d] > S.R[d] - S.hw)
       return set_err(MSM_ERR_CAPACITY, "cell compressed beyond the plan's stencil radius: create the plan for the "
                                        "most compressed cell it must serve");
   }
@@ -497,10 +493,23 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
     D.nnbr[d] = S.nnbr[d];
   }
   E.hsys[0] = D;
-  const int hz = (S.B[2] + 3) & ~3;
-  launch_cell_update(E.d_sys, D, S.h1, S.a, S.p, S.B, hz, S.kball_off, S.dkh_off, S.wb_off, S.wh_off, E.d_kpool,
-                     E.d_wpool, (cudaStream_t)stream);
   E.have_fwd = false;  // the workspace holds results for the old cell
+  bool device_path = S.pbc[0] && S.pbc[1] && S.pbc[2] && S.prefilter;
+  for (const LevelHost& Lv : S.lev) device_path = device_path && Lv.kind == 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (device_path) {
+    // every level a ball of raw samples: pointwise in h_1, computed on the device
+    const int hz = (S.B[2] + 3) & ~3;
+    launch_cell_update(E.d_sys, D, S.h1, S.a, S.p, S.B, hz, S.kball_off, S.dkh_off, S.wb_off, S.wh_off, E.d_kpool,
+                       E.d_wpool, st);
+  } else {
+    // omega'-convolved stencils and folded boxes: rebuilt on the host with the
+    // plan's sizes, copied through pinned staging buffers (stream-ordered)
+    std::string err;
+    int rc = E.set_cell_host(S.L, st, &err);
+    if (rc) return set_err(rc, "msm_plan_set_cell: " + err);
+    launch_set_sys(E.d_sys, D, st);
+  }
   return check_launch("msm_plan_set_cell");
 }
 

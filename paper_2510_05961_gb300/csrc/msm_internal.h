@@ -164,7 +164,8 @@ void launch_anterp_dipole(const Work& w, const Tables& t, const TileItem* items,
                           int tz, const float4* us);
 void launch_fvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* hs, float* dq,
                        float* dpos, cudaStream_t s);
-// dynamic cell (k_cell.cu): new system descriptor and ball stencils of a periodic p = 4 plan
+// dynamic cell (k_cell.cu): new system descriptor (alone, or with the ball stencils of a periodic p = 4 plan)
+void launch_set_sys(SysDev* d_sys, const SysDev& val, cudaStream_t s);
 void launch_cell_update(SysDev* d_sys, const SysDev& val, const double h1[3], double a, int p, const int B[3], int hz,
                         long long kball_off, long long dkh_off, long long wb_off, long long wh_off, float* kpool,
                         int* wpool, cudaStream_t s);

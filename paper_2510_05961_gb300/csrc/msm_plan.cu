@@ -271,6 +271,120 @@ static void fold(const Box3& in, const int n[3], const int per[3], double scale,
       }
 }
 
+// Stencil values of a planned system for its current spacings h_1: K^1 and
+// its strain derivatives, the folded boxes of the box levels, the ball
+// samples, virial weights and column half-widths. With decide set it also
+// chooses each level's kernel (ball or box) and radius; without, the kinds,
+// radii and array sizes of the plan are kept (a new cell for an existing plan).
+static void fill_stencils(SysHost& S, bool decide) {
+  // level-1 shape stencil K^1 (intermediate levels are K^1 / 2^(l-1)) and its
+  // strain derivatives; the ball kernels apply the raw samples s^1 instead,
+  // to the omega'-prefiltered grid: K * q = (omega'^3 * s) * q = s * (omega'^3 * q)
+  const bool any_mid = S.ncomp >= 1 && S.nlev > 1;
+  if (decide) S.has_ball = false;
+  Box3 K1, dK1[6];
+  if (any_mid) {
+    build_stencil(S, 1, S.R, 0, K1);
+    for (int c = 0; c < 6; c++) build_stencil(S, 1, S.R, c + 1, dK1[c]);
+  }
+  for (int l = 1; l <= S.ncomp; l++) {
+    LevelHost& Lv = S.lev[l - 1];
+    Lv.scale = (float)std::ldexp(1.0, -(l - 1));
+    bool top = (l == S.nlev);
+    // ball kernels are compiled for radii up to kBallRmax; larger stencils use
+    // the box kernel. A ball that overlaps itself on a small periodic grid is
+    // still applied as a ball: its halo holds the periodic images (wrapped
+    // more than once where the grid is shorter than the halo), which sums
+    // every image of each offset exactly as the folded stencil does.
+    if (decide) {
+      bool ball = !top && S.qi_mode == 0;  // exact interpolation: dense boxes (wide stencils, accuracy reference)
+      for (int d = 0; d < 3; d++)
+        if (S.B[d] > kBallRmax) ball = false;
+      for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
+      if (ball) {
+        Lv.kind = 0;
+        S.has_ball = true;
+        continue;
+      }
+      Lv.kind = 1;
+      for (int d = 0; d < 3; d++) Lv.R[d] = S.R[d];
+    } else if (Lv.kind == 0) {
+      continue;
+    }
+    Box3 Kf, dKf[6];
+    if (top) {
+      int E[3];
+      for (int d = 0; d < 3; d++) E[d] = Lv.n[d] - 1;
+      Box3 Kt, dKt[6];
+      build_stencil(S, l, E, 0, Kt);
+      for (int c = 0; c < 6; c++) build_stencil(S, l, E, c + 1, dKt[c]);
+      fold(Kt, Lv.n, Lv.per, 1.0, Kf);
+      for (int c = 0; c < 6; c++) fold(dKt[c], Lv.n, Lv.per, 1.0, dKf[c]);
+    } else {
+      double sc = std::ldexp(1.0, -(l - 1));
+      fold(K1, Lv.n, Lv.per, sc, Kf);
+      for (int c = 0; c < 6; c++) fold(dK1[c], Lv.n, Lv.per, sc, dKf[c]);
+    }
+    Lv.scale = 1.0f;
+    for (int d = 0; d < 3; d++) {
+      Lv.blo[d] = Kf.o[d];
+      Lv.bsz[d] = Kf.s[d];
+    }
+    Lv.kbox.assign(Kf.v.begin(), Kf.v.end());
+    Lv.dkbox.clear();
+    for (int c = 0; c < 6; c++) Lv.dkbox.insert(Lv.dkbox.end(), dKf[c].v.begin(), dKf[c].v.end());
+  }
+  if (any_mid) {
+    S.kball.assign(K1.v.begin(), K1.v.end());
+    S.dk1.clear();
+    for (int c = 0; c < 6; c++) S.dk1.insert(S.dk1.end(), dK1[c].v.begin(), dK1[c].v.end());
+  }
+  if (S.has_ball) {
+    Box3 s1, ds1[6];
+    if (S.prefilter) {
+      build_samples(S, 1, S.B, 0, s1);
+      for (int c = 0; c < 6; c++) build_samples(S, 1, S.B, c + 1, ds1[c]);
+    } else {
+      s1 = K1;
+      for (int c = 0; c < 6; c++) ds1[c] = dK1[c];
+    }
+    const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
+    S.sball.assign(s1.v.begin(), s1.v.end());
+    S.dsh.assign((size_t)6 * nx * ny * nz, 0.0f);
+    S.fsh.assign(S.prefilter ? (size_t)nx * ny * nz : 0, 0.0f);
+    // column half-widths, rounded up to even values (the stored rows are zero
+    // beyond the support): half as many unrolled column variants
+    S.wball.assign((size_t)nx * ny, -1);
+    S.whalf.assign((size_t)nx * ny, -1);
+    for (int x = -S.B[0]; x <= S.B[0]; x++)
+      for (int y = -S.B[1]; y <= S.B[1]; y++)
+        for (int z = -S.B[2]; z <= S.B[2]; z++) {
+          size_t at = ((size_t)(x + S.B[0]) * ny + (y + S.B[1])) * nz + (z + S.B[2]);
+          size_t col = (size_t)(x + S.B[0]) * ny + (y + S.B[1]);
+          if ((float)s1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z) + (std::abs(z) & 1));
+          // half-space weights: C'_d = C'_-d, so sum_d ds_d C'_d = ds_0 C'_0 + 2 sum_(d in half) ds_d C'_d
+          bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
+          bool zero = x == 0 && y == 0 && z == 0;
+          double f = half ? 2.0 : (zero ? 1.0 : 0.0);
+          bool any = false;
+          for (int c = 0; c < 6; c++) {
+            float v = (float)(f * ds1[c].v[at]);
+            S.dsh[(size_t)c * nx * ny * nz + at] = v;
+            if (v != 0.0f) any = true;
+          }
+          if (S.prefilter) {
+            // raw samples factor: ds_ab(n) = g(n) v_a v_b with g = k_1'(|v|)/|v|, v = h_1 o n
+            const double vx = S.h1[0] * x, vy = S.h1[1] * y, vz = S.h1[2] * z;
+            const double rr = std::sqrt(vx * vx + vy * vy + vz * vz);
+            const float g = rr > 0.0 ? (float)(f * klev(S, 1, rr, true) / rr) : 0.0f;
+            S.fsh[at] = g;
+            any = g != 0.0f;
+          }
+          if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z) + (std::abs(z) & 1));
+        }
+  }
+}
+
 // ------------------------------------------------------------------ planning
 static int fail(std::string* err, int code, const char* msg) {
   if (err) *err = msg;
@@ -397,108 +511,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     S.edge[d] = S.L[d] / S.C[d];
     S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
   }
-  // level-1 shape stencil K^1 (intermediate levels are K^1 / 2^(l-1)) and its
-  // strain derivatives; the ball kernels apply the raw samples s^1 instead,
-  // to the omega'-prefiltered grid: K * q = (omega'^3 * s) * q = s * (omega'^3 * q)
-  const bool any_mid = S.ncomp >= 1 && S.nlev > 1;
-  S.has_ball = false;
-  Box3 K1, dK1[6];
-  if (any_mid) {
-    build_stencil(S, 1, S.R, 0, K1);
-    for (int c = 0; c < 6; c++) build_stencil(S, 1, S.R, c + 1, dK1[c]);
-  }
-  for (int l = 1; l <= S.ncomp; l++) {
-    LevelHost& Lv = S.lev[l - 1];
-    Lv.scale = (float)std::ldexp(1.0, -(l - 1));
-    bool top = (l == S.nlev);
-    // ball kernels are compiled for radii up to kBallRmax; larger stencils use
-    // the box kernel. A ball that overlaps itself on a small periodic grid is
-    // still applied as a ball: its halo holds the periodic images (wrapped
-    // more than once where the grid is shorter than the halo), which sums
-    // every image of each offset exactly as the folded stencil does.
-    bool ball = !top && S.qi_mode == 0;  // exact interpolation: dense boxes (wide stencils, accuracy reference)
-    for (int d = 0; d < 3; d++)
-      if (S.B[d] > kBallRmax) ball = false;
-    for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
-    if (ball) {
-      Lv.kind = 0;
-      S.has_ball = true;
-      continue;
-    }
-    Lv.kind = 1;
-    for (int d = 0; d < 3; d++) Lv.R[d] = S.R[d];
-    Box3 Kf, dKf[6];
-    if (top) {
-      int E[3];
-      for (int d = 0; d < 3; d++) E[d] = Lv.n[d] - 1;
-      Box3 Kt, dKt[6];
-      build_stencil(S, l, E, 0, Kt);
-      for (int c = 0; c < 6; c++) build_stencil(S, l, E, c + 1, dKt[c]);
-      fold(Kt, Lv.n, Lv.per, 1.0, Kf);
-      for (int c = 0; c < 6; c++) fold(dKt[c], Lv.n, Lv.per, 1.0, dKf[c]);
-    } else {
-      double sc = std::ldexp(1.0, -(l - 1));
-      fold(K1, Lv.n, Lv.per, sc, Kf);
-      for (int c = 0; c < 6; c++) fold(dK1[c], Lv.n, Lv.per, sc, dKf[c]);
-    }
-    Lv.scale = 1.0f;
-    for (int d = 0; d < 3; d++) {
-      Lv.blo[d] = Kf.o[d];
-      Lv.bsz[d] = Kf.s[d];
-    }
-    Lv.kbox.assign(Kf.v.begin(), Kf.v.end());
-    Lv.dkbox.clear();
-    for (int c = 0; c < 6; c++) Lv.dkbox.insert(Lv.dkbox.end(), dKf[c].v.begin(), dKf[c].v.end());
-  }
-  if (any_mid) {
-    S.kball.assign(K1.v.begin(), K1.v.end());
-    S.dk1.clear();
-    for (int c = 0; c < 6; c++) S.dk1.insert(S.dk1.end(), dK1[c].v.begin(), dK1[c].v.end());
-  }
-  if (S.has_ball) {
-    Box3 s1, ds1[6];
-    if (S.prefilter) {
-      build_samples(S, 1, S.B, 0, s1);
-      for (int c = 0; c < 6; c++) build_samples(S, 1, S.B, c + 1, ds1[c]);
-    } else {
-      s1 = K1;
-      for (int c = 0; c < 6; c++) ds1[c] = dK1[c];
-    }
-    const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
-    S.sball.assign(s1.v.begin(), s1.v.end());
-    S.dsh.assign((size_t)6 * nx * ny * nz, 0.0f);
-    S.fsh.assign(S.prefilter ? (size_t)nx * ny * nz : 0, 0.0f);
-    // column half-widths, rounded up to even values (the stored rows are zero
-    // beyond the support): half as many unrolled column variants
-    S.wball.assign((size_t)nx * ny, -1);
-    S.whalf.assign((size_t)nx * ny, -1);
-    for (int x = -S.B[0]; x <= S.B[0]; x++)
-      for (int y = -S.B[1]; y <= S.B[1]; y++)
-        for (int z = -S.B[2]; z <= S.B[2]; z++) {
-          size_t at = ((size_t)(x + S.B[0]) * ny + (y + S.B[1])) * nz + (z + S.B[2]);
-          size_t col = (size_t)(x + S.B[0]) * ny + (y + S.B[1]);
-          if ((float)s1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z) + (std::abs(z) & 1));
-          // half-space weights: C'_d = C'_-d, so sum_d ds_d C'_d = ds_0 C'_0 + 2 sum_(d in half) ds_d C'_d
-          bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
-          bool zero = x == 0 && y == 0 && z == 0;
-          double f = half ? 2.0 : (zero ? 1.0 : 0.0);
-          bool any = false;
-          for (int c = 0; c < 6; c++) {
-            float v = (float)(f * ds1[c].v[at]);
-            S.dsh[(size_t)c * nx * ny * nz + at] = v;
-            if (v != 0.0f) any = true;
-          }
-          if (S.prefilter) {
-            // raw samples factor: ds_ab(n) = g(n) v_a v_b with g = k_1'(|v|)/|v|, v = h_1 o n
-            const double vx = S.h1[0] * x, vy = S.h1[1] * y, vz = S.h1[2] * z;
-            const double rr = std::sqrt(vx * vx + vy * vy + vz * vz);
-            const float g = rr > 0.0 ? (float)(f * klev(S, 1, rr, true) / rr) : 0.0f;
-            S.fsh[at] = g;
-            any = g != 0.0f;
-          }
-          if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z) + (std::abs(z) & 1));
-        }
-  }
+  fill_stencils(S, true);
   // scalar coefficients
   softening_coeffs(S.p, S.gc);
   {
@@ -513,6 +526,76 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
 
 // ------------------------------------------------------------------ engine
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Device pools of the stencil values: per system the ball stencil (a row of
+// kSK(hz) floats per (dx, dy) column), its virial weights and column tables,
+// then each box level's folded K and dK; records the offsets in the level
+// descriptors and the systems. The layout depends only on the plan's sizes.
+void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>& kp, std::vector<int>& wp) {
+  kp.clear();
+  wp.clear();
+  for (int s = 0; s < nsys; s++) {
+    SysHost& S = sys[s];
+    long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1;
+    if (S.has_ball) {
+      // column layout read by the ball kernels: for each (dx, dy) a row of
+      // kSK(hz) floats with dz = -hz .. hz at [0, 2hz]; virial weights [dx][6][dy][row]
+      const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
+      const int hz = (S.B[2] + 3) & ~3, SK = kSK(hz);
+      while (kp.size() % 4) kp.push_back(0.f);
+      kball_off = (long long)kp.size();
+      kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
+      for (int x = 0; x < nx; x++)
+        for (int y = 0; y < ny; y++)
+          for (int z = 0; z < nz; z++)
+            kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.sball[((size_t)x * ny + y) * nz + z];
+      dkh_off = (long long)kp.size();
+      if (S.prefilter) {
+        // factorized virial weights g(n), one array [dx][dy][row]
+        kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
+        for (int x = 0; x < nx; x++)
+          for (int y = 0; y < ny; y++)
+            for (int z = 0; z < nz; z++)
+              kp[dkh_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.fsh[((size_t)x * ny + y) * nz + z];
+      } else {
+        kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
+        for (int x = 0; x < nx; x++)
+          for (int c = 0; c < 6; c++)
+            for (int y = 0; y < ny; y++)
+              for (int z = 0; z < nz; z++)
+                kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.B[2] + hz)] =
+                    S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
+      }
+      wb_off = (long long)wp.size();
+      wp.insert(wp.end(), S.wball.begin(), S.wball.end());
+      wh_off = (long long)wp.size();
+      wp.insert(wp.end(), S.whalf.begin(), S.whalf.end());
+    }
+    S.kball_off = kball_off;
+    S.dkh_off = dkh_off;
+    S.wb_off = wb_off;
+    S.wh_off = wh_off;
+    for (int l = 1; l <= S.ncomp; l++) {
+      LevDev& L = hlev[lev0_of[s] + l - 1];
+      const LevelHost& Lv = S.lev[l - 1];
+      if (L.kind == 0) {
+        L.k_off = kball_off;
+        L.dk_off = dkh_off;
+        L.w_off = wb_off;
+        L.wh_off = wh_off;
+      } else {
+        while (kp.size() % 4) kp.push_back(0.f);
+        L.k_off = (long long)kp.size();
+        kp.insert(kp.end(), Lv.kbox.begin(), Lv.kbox.end());
+        L.dk_off = (long long)kp.size();
+        kp.insert(kp.end(), Lv.dkbox.begin(), Lv.dkbox.end());
+      }
+    }
+    while (kp.size() % 4) kp.push_back(0.f);
+  }
+  if (kp.empty()) kp.push_back(0.f);
+  if (wp.empty()) wp.push_back(0);
+}
 
 int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool single_, std::string* err) {
   nsys = nsys_;
@@ -627,67 +710,11 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   // stencil pools
   std::vector<float> kp;
   std::vector<int> wp;
-  for (int s = 0; s < nsys; s++) {
-    SysHost& S = sys[s];
-    long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1;
-    if (S.has_ball) {
-      // column layout read by the ball kernels: for each (dx, dy) a row of
-      // kSK(hz) floats with dz = -hz .. hz at [0, 2hz]; virial weights [dx][6][dy][row]
-      const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
-      const int hz = (S.B[2] + 3) & ~3, SK = kSK(hz);
-      while (kp.size() % 4) kp.push_back(0.f);
-      kball_off = (long long)kp.size();
-      kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
-      for (int x = 0; x < nx; x++)
-        for (int y = 0; y < ny; y++)
-          for (int z = 0; z < nz; z++)
-            kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.sball[((size_t)x * ny + y) * nz + z];
-      dkh_off = (long long)kp.size();
-      if (S.prefilter) {
-        // factorized virial weights g(n), one array [dx][dy][row]
-        kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
-        for (int x = 0; x < nx; x++)
-          for (int y = 0; y < ny; y++)
-            for (int z = 0; z < nz; z++)
-              kp[dkh_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.fsh[((size_t)x * ny + y) * nz + z];
-      } else {
-        kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
-        for (int x = 0; x < nx; x++)
-          for (int c = 0; c < 6; c++)
-            for (int y = 0; y < ny; y++)
-              for (int z = 0; z < nz; z++)
-                kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.B[2] + hz)] =
-                    S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
-      }
-      wb_off = (long long)wp.size();
-      wp.insert(wp.end(), S.wball.begin(), S.wball.end());
-      wh_off = (long long)wp.size();
-      wp.insert(wp.end(), S.whalf.begin(), S.whalf.end());
-    }
-    S.kball_off = kball_off;
-    S.dkh_off = dkh_off;
-    S.wb_off = wb_off;
-    S.wh_off = wh_off;
-    for (int l = 1; l <= S.ncomp; l++) {
-      LevDev& L = hlev[hs[s].lev0 + l - 1];
-      const LevelHost& Lv = S.lev[l - 1];
-      if (L.kind == 0) {
-        L.k_off = kball_off;
-        L.dk_off = dkh_off;
-        L.w_off = wb_off;
-        L.wh_off = wh_off;
-      } else {
-        while (kp.size() % 4) kp.push_back(0.f);
-        L.k_off = (long long)kp.size();
-        kp.insert(kp.end(), Lv.kbox.begin(), Lv.kbox.end());
-        L.dk_off = (long long)kp.size();
-        kp.insert(kp.end(), Lv.dkbox.begin(), Lv.dkbox.end());
-      }
-    }
-    while (kp.size() % 4) kp.push_back(0.f);
+  {
+    std::vector<int> lev0_of(nsys);
+    for (int s = 0; s < nsys; s++) lev0_of[s] = hs[s].lev0;
+    assemble_pools(lev0_of, kp, wp);
   }
-  if (kp.empty()) kp.push_back(0.f);
-  if (wp.empty()) wp.push_back(0);
   // work lists
   anterp_items.clear();
   ball_items.clear();
@@ -832,6 +859,8 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   if ((rc = up(hlev, &d_lev, err))) return rc;
   if ((rc = up(kp, &d_kpool, err))) return rc;
   if ((rc = up(wp, &d_wpool, err))) return rc;
+  kpool_n = kp.size();
+  wpool_n = wp.size();
   if ((rc = up(atom_items, &d_atom_items, err))) return rc;
   if ((rc = up(anterp_items, &d_anterp_items, err))) return rc;
   if ((rc = up(ball_items, &d_ball_items, err))) return rc;
@@ -864,7 +893,37 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   return MSM_OK;
 }
 
+int Engine::set_cell_host(const double Lnew[3], cudaStream_t s, std::string* err) {
+  SysHost& S = sys[0];
+  (void)Lnew;  // the caller has set S.L and S.h1
+  fill_stencils(S, false);
+  std::vector<int> lev0_of(1, hsys[0].lev0);
+  std::vector<float> kp;
+  std::vector<int> wp;
+  assemble_pools(lev0_of, kp, wp);
+  if (kp.size() != kpool_n || wp.size() != wpool_n) return fail(err, MSM_ERR_CAPACITY, "stencil pools changed size");
+  if (!h_kstage) {
+    if (cudaMallocHost((void**)&h_kstage, sizeof(float) * kpool_n) != cudaSuccess ||
+        cudaMallocHost((void**)&h_wstage, sizeof(int) * wpool_n) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_stage, cudaEventDisableTiming) != cudaSuccess)
+      return fail(err, MSM_ERR_CUDA, "pinned staging buffers for the stencils could not be allocated");
+  } else if (cudaEventSynchronize(ev_stage) != cudaSuccess) {  // the previous copy has left the buffers
+    return fail(err, MSM_ERR_CUDA, "cudaEventSynchronize failed");
+  }
+  std::memcpy(h_kstage, kp.data(), sizeof(float) * kpool_n);
+  std::memcpy(h_wstage, wp.data(), sizeof(int) * wpool_n);
+  if (cudaMemcpyAsync(d_kpool, h_kstage, sizeof(float) * kpool_n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_wpool, h_wstage, sizeof(int) * wpool_n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaEventRecord(ev_stage, s) != cudaSuccess)
+    return fail(err, MSM_ERR_CUDA, "stencil upload failed");
+  return MSM_OK;
+}
+
 Engine::~Engine() {
+  if (ev_stage) cudaEventSynchronize(ev_stage);
+  if (h_kstage) cudaFreeHost(h_kstage);
+  if (h_wstage) cudaFreeHost(h_wstage);
+  if (ev_stage) cudaEventDestroy(ev_stage);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   if (ev_fork) cudaEventDestroy(ev_fork);

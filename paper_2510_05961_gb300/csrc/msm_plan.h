@@ -119,6 +119,14 @@ struct Engine {
   double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
   void build_anterp_items(int tz);
   int set_anterp_tz(int tz, std::string* err);
+  void assemble_pools(const std::vector<int>& lev0_of, std::vector<float>& kp, std::vector<int>& wp);
+  // new cell for a single-system plan (msm_plan_set_cell), host path: stencils
+  // rebuilt on the host and copied through pinned staging buffers
+  int set_cell_host(const double L[3], cudaStream_t s, std::string* err);
+  float* h_kstage = nullptr;
+  int* h_wstage = nullptr;
+  size_t kpool_n = 0, wpool_n = 0;
+  cudaEvent_t ev_stage = nullptr;
   Work resolve(void* ws) const;
   Tables tables() const;
 };

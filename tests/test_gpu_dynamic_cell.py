@@ -1,11 +1,14 @@
 """Dynamic cells (msm_plan_set_cell): one plan, its cell changed between calls.
 
-The plan keeps its grid counts M and stencil sizes; the device recomputes the
-stencils for the new spacings h_1 = L / M. Each cell is checked against the
+The plan keeps its grid counts M and stencil sizes; the stencils for the new
+spacings h_1 = L / M are recomputed on the device (periodic, p = 4) or on the
+host (every other setting). Each cell is checked against the
 FP64 oracle planned for that cell with the same M (grid_override), with the
 parity tolerances; a compression beyond the plan's stencil radius is refused;
 returning to the creation cell reproduces a fresh plan.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -47,18 +50,31 @@ def run(plan, pos, q):
 
 def oracle_for(cell, w, M, pos):
     import oracle as O
-    P = O.make_plan(cell, w.pbc, w.h, w.a, w.p, w.levels, tuple(M))
+    P = O.make_plan(cell, w.pbc, w.h, w.a, w.p, w.levels, tuple(M), w.qi_mode)
     return O.msm(P, pos.astype(np.float64), w.q.astype(np.float64), forces=True, virial=True)
 
 
-@pytest.mark.parametrize("n,seed", [(20001, 91), (3000, 92)])
-def test_cell_changes_match_oracle(n, seed):
+CASES = {
+    # device path: periodic, p = 4, raw-sample balls on every level
+    "periodic_p4_20001": lambda: W.random_box(20001, seed=91),
+    "periodic_p4_3000": lambda: W.random_box(3000, seed=92),
+    # host path: omega'-convolved stencils (p = 6), folded or dense boxes (open, slab, exact interpolation)
+    "periodic_p6_3000": lambda: W.random_box(3000, seed=96, p=6, h=1.5, a=6.0),
+    "slab_3000": lambda: W.random_box(3000, seed=97, pbc=(1, 1, 0)),
+    "open_1500": lambda: W.random_box(1500, seed=98, pbc=(0, 0, 0)),
+    "periodic_qi1_400": lambda: dataclasses.replace(W.random_box(400, seed=99, h=2.0, a=4.0), qi_mode=1),
+}
+
+
+@pytest.mark.parametrize("key", list(CASES))
+def test_cell_changes_match_oracle(key):
     import oracle as O
-    w = W.random_box(n, seed=seed)
+    w = CASES[key]()
     M = [O.plan_for(w).M[d] for d in range(3)]
     base = np.array(w.cell, np.float64)
     # built for the most compressed cell it will serve
-    plan = Plan(tuple(base * 0.97), w.pbc, w.h, w.a, w.p, w.levels, tuple(M), max_atoms=w.n, device=DEV)
+    plan = Plan(tuple(base * 0.97), w.pbc, w.h, w.a, w.p, w.levels, tuple(M), max_atoms=w.n, device=DEV,
+                qi_mode=w.qi_mode)
     for s in [(1.0, 1.0, 1.0), (1.04, 0.99, 1.02), (0.97, 0.97, 0.97), (1.1, 1.1, 1.1)]:
         cell = base * np.array(s)
         pos = (w.pos.astype(np.float64) * np.array(s)).astype(np.float32)
@@ -92,14 +108,11 @@ def test_compression_beyond_capacity_is_refused_and_creation_cell_is_reproduced(
     assert np.allclose(r1["W"], r0["W"], rtol=1e-5, atol=1e-6 * np.abs(r0["W"]).max())
 
 
-def test_unsupported_plans_are_refused():
-    w = W.random_box(500, seed=94, pbc=(1, 1, 0))
+def test_non_orthorhombic_cell_is_refused():
+    w = W.random_box(500, seed=94)
     plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, max_atoms=w.n, device=DEV)
+    c = np.diag(np.array(w.cell, np.float64))
+    c[0, 1] = 0.5
     with pytest.raises(L.MsmError) as e:
-        plan.set_cell(np.array(w.cell) * 1.01)
-    assert e.value.code == L.MSM_ERR_UNSUPPORTED
-    w6 = W.random_box(500, seed=95, p=6)
-    plan6 = Plan(w6.cell, w6.pbc, w6.h, w6.a, w6.p, w6.levels, max_atoms=w6.n, device=DEV)
-    with pytest.raises(L.MsmError) as e:
-        plan6.set_cell(np.array(w6.cell) * 1.01)
+        plan.set_cell(c)
     assert e.value.code == L.MSM_ERR_UNSUPPORTED
