@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-atoms", type=int, default=N_HEADLINE)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the dynamic-cell and second-order timings (e.g. for a launch list of the step alone)")
     ap.add_argument("--tuning", type=int, nargs=2, metavar=("ANTERP_TZ", "SHORT_BLOCK"), default=None,
                     help="fixed launch shapes for the 1M-atom plan instead of msm_autotune")
     ap.add_argument("--batch-systems", type=int, default=512)
@@ -404,7 +406,7 @@ def run_gpu(args):
     # dynamic cell: msm_plan_set_cell recomputes the stencils on the device (stream-ordered);
     # alternate a 1% larger cell and the benchmark cell, CUDA events around 20 calls
     dyn = None
-    if tuple(w.pbc) == (1, 1, 1) and w.p == 4:
+    if tuple(w.pbc) == (1, 1, 1) and w.p == 4 and not args.no_extras:
         import numpy as np
         base = np.array(w.cell, np.float64)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -426,7 +428,7 @@ def run_gpu(args):
     u_dev = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).to(dev)
     g_dev = torch.from_numpy(rng.normal(size=n).astype(np.float32)).to(dev)
     tv, tp = 0.0, 0.0
-    for _ in range(3):
+    for _ in range(0 if args.no_extras else 3):
         plan.forward(pos, q, forces=True, virial=False, phi=False)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
@@ -440,7 +442,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         tv += a0.elapsed_time(a1) / 3
         tp += b0.elapsed_time(b1) / 3
-    second = {"force_vjp_ms": tv, "phi_grad_ms": tp,
+    second = None if args.no_extras else {"force_vjp_ms": tv, "phi_grad_ms": tp,
               "what": "after a forward with forces: msm_force_vjp for a random upstream on F; the extra "
                       "evaluation with charges g plus msm_field that the upstream on phi needs"}
 
@@ -550,9 +552,10 @@ def run_sweep(args):
     for n in W.scaling_sizes(args.sweep_kmax):
         w = W.random_box(n, seed=3000 + n % 997)
         plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, 0, max_atoms=n, device=dev)
-        info = plan.info()
         pos = torch.from_numpy(w.pos).to(dev)
         q = torch.from_numpy(w.q).to(dev)
+        plan.autotune(pos, q)  # launch shapes per size, as the main benchmark
+        info = plan.info()
         E = torch.empty(1, dtype=torch.float64, device=dev)
         phi = torch.empty(n, dtype=torch.float32, device=dev)
         F = torch.empty((n, 3), dtype=torch.float32, device=dev)
@@ -587,6 +590,7 @@ def run_sweep(args):
               "stencil": stencil_flops(plan.params, info, w.cell, w.a, w.p)}
         roof = {k: (fl[k] / (phase[k] / 1e3) / 1e12 / peak if phase.get(k, 0) > 0 else None) for k in fl}
         rows.append({"atoms": n, "M": info["M"][0], "h1": round(info["h1"][0], 4), "levels": info["nlev"],
+                     "tuning": [info["anterp_tz"], info["short_block"]],
                      "ms_per_forward": ms, "atoms_per_s": n / (ms / 1e3),
                      "fp32_frac": roof, "phase_ms": {k: round(v, 4) for k, v in phase.items() if v > 0}})
         del plan, pos, q, E, phi, F
