@@ -342,6 +342,23 @@ def ewald(cell, pos, q, alpha, rcut, kmax, forces=True):
     return float(E[0]), phi, F
 
 
+def ewald2d(Lx, Ly, pos, q, alpha=0.0):
+    """2-D Ewald sum of a neutral slab (x, y periodic, z open): (E, phi)."""
+    pos, q = _d(pos), _d(q)
+    n = pos.shape[0]
+    E = np.zeros(1)
+    phi = np.zeros(n)
+    lib().or_ewald2d(C.c_double(Lx), C.c_double(Ly), n, _ptr(pos), _ptr(q), C.c_double(alpha), _ptr(E), _ptr(phi))
+    return float(E[0]), phi
+
+
+def slab_top(p, a, nlev, Lx, Ly, z):
+    """Top-level kernel of a slab at the z offset z (k_L summed over the 2-D lattice)."""
+    f = lib().or_slab_top
+    f.restype = C.c_double
+    return float(f(int(p), C.c_double(a), int(nlev), C.c_double(Lx), C.c_double(Ly), C.c_double(z)))
+
+
 def ewald_auto(cell, pos, q, tol=1e-13, rcut=None, forces=True):
     """Ewald sum with alpha / kmax chosen so both truncation errors are below tol."""
     import math

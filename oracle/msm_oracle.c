@@ -43,7 +43,7 @@ typedef struct {
   /* derived by or_plan_init */
   int nlev;             /* number of grid levels L (top level included) */
   int ncomp;            /* levels whose grids are evaluated (nlev, or nlev-1 when the top is dropped) */
-  int top_kept;         /* 1 when the top level's stencil is applied (all axes open) */
+  int top_kept;         /* 1 when the top level's stencil is applied (all axes open, or a slab) */
   int M[3];             /* level-1 interval counts */
   double h1[3];         /* level-1 spacings L/M */
   int lo[OR_MAXLEV][3]; /* first grid index per level (index 0 = level 1) */
@@ -122,6 +122,128 @@ double or_dkl(int p, double a, int nlev, int l, double r) {
   double s2 = ldexp(a, l);
   if (r >= s2) return 0.0;
   return or_dgamma(p, r / s1) / (s1 * s1) - or_dgamma(p, r / s2) / (s2 * s2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Slab geometry (x, y periodic with edges Lx, Ly; z open): the 2-D lattice  */
+/* sums the exact slab top level and the 2-D Ewald pin need.                 */
+/* ------------------------------------------------------------------------ */
+
+/* 2-D Ewald split of sum_R 1/|r + R| over R = (i Lx, j Ly, 0) at r = (x, y, z)
+ * (the textbook slab Ewald sum):
+ *   real space  sum_R erfc(alpha s)/s,  s = |r + R| (R = 0 left out if skip0),
+ *   reciprocal  (pi/A) sum_(G != 0) cos(G.rho)/|G| [e^(|G| z) erfc(|G|/(2 alpha) + alpha z)
+ *                                                  + e^(-|G| z) erfc(|G|/(2 alpha) - alpha z)],
+ *   G = 0       -(2 pi/A) [z erf(alpha z) + exp(-alpha^2 z^2)/(alpha sqrt(pi))],
+ * A = Lx Ly, G = 2 pi (i/Lx, j/Ly). The lattice sum itself diverges; this is
+ * it without the infinite constant of the G = 0 term, which multiplies the
+ * squared total charge and so vanishes for neutral systems. Truncation: real
+ * space to |r + R| < 7/alpha, reciprocal space to |G| < 14 alpha (terms below
+ * 1e-21 relative). */
+/* e^(g z) erfc(g/(2 alpha) + alpha z) without overflow: for a positive erfc
+ * argument x it is exp(-g^2/(4 alpha^2) - alpha^2 z^2) erfcx(x), erfcx(x) =
+ * e^(x^2) erfc(x) taken directly below x = 10 and from its asymptotic series
+ * 1/(x sqrt(pi)) sum_n (-1)^n (2n-1)!!/(2 x^2)^n above (12 terms). */
+static double ewald2d_term(double g, double z, double alpha) {
+  double x = g / (2.0 * alpha) + alpha * z;
+  if (x <= 0.0) return exp(g * z) * erfc(x);
+  double ex;
+  if (x < 10.0) {
+    ex = exp(x * x) * erfc(x);
+  } else {
+    double t = 1.0, sum = 1.0, inv = 1.0 / (2.0 * x * x);
+    for (int k = 1; k <= 12; k++) {
+      t *= -(2.0 * k - 1.0) * inv;
+      sum += t;
+    }
+    ex = sum / (x * sqrt(OR_PI));
+  }
+  return exp(-g * g / (4.0 * alpha * alpha) - alpha * alpha * z * z) * ex;
+}
+
+double or_ewald2d_pair(double Lx, double Ly, double x, double y, double z, double alpha, int skip0) {
+  const double A = Lx * Ly, rc = 7.0 / alpha, gc = 14.0 * alpha;
+  double acc = 0.0;
+  int ni = (int)ceil((rc + fabs(x)) / Lx) + 1, nj = (int)ceil((rc + fabs(y)) / Ly) + 1;
+  for (int i = -ni; i <= ni; i++)
+    for (int j = -nj; j <= nj; j++) {
+      if (skip0 && i == 0 && j == 0) continue;
+      double dx = x + i * Lx, dy = y + j * Ly;
+      double s = sqrt(dx * dx + dy * dy + z * z);
+      if (s < rc) acc += erfc(alpha * s) / s;
+    }
+  int mi = (int)ceil(gc * Lx / (2.0 * OR_PI)) + 1, mj = (int)ceil(gc * Ly / (2.0 * OR_PI)) + 1;
+  double rec = 0.0;
+  for (int i = -mi; i <= mi; i++)
+    for (int j = -mj; j <= mj; j++) {
+      if (i == 0 && j == 0) continue;
+      double gx = 2.0 * OR_PI * i / Lx, gy = 2.0 * OR_PI * j / Ly;
+      double g = sqrt(gx * gx + gy * gy);
+      if (g >= gc) continue;
+      double t = ewald2d_term(g, z, alpha) + ewald2d_term(g, -z, alpha);
+      rec += cos(gx * x + gy * y) / g * t;
+    }
+  acc += OR_PI / A * rec;
+  acc -= 2.0 * OR_PI / A * (z * erf(alpha * z) + exp(-alpha * alpha * z * z) / (alpha * sqrt(OR_PI)));
+  return acc;
+}
+
+/* 2-D Ewald sum of a neutral slab: phi_i = sum_j q_j psi(r_j - r_i) with psi
+ * the pair sum above (R = 0 left out for j = i) minus 2 alpha/sqrt(pi) q_i;
+ * E = 1/2 sum q phi. alpha <= 0 picks 6 / min(Lx, Ly). */
+void or_ewald2d(double Lx, double Ly, int n, const double* pos, const double* q, double alpha, double* E,
+                double* phi) {
+  if (alpha <= 0.0) alpha = 6.0 / (Lx < Ly ? Lx : Ly);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0;
+    for (int j = 0; j < n; j++) {
+      double dx = pos[3 * j] - pos[3 * i], dy = pos[3 * j + 1] - pos[3 * i + 1], dz = pos[3 * j + 2] - pos[3 * i + 2];
+      dx -= Lx * floor(dx / Lx + 0.5);
+      dy -= Ly * floor(dy / Ly + 0.5);
+      ph += q[j] * or_ewald2d_pair(Lx, Ly, dx, dy, dz, alpha, j == i);
+    }
+    phi[i] = ph - 2.0 * alpha / sqrt(OR_PI) * q[i];
+  }
+  double e = 0.0;
+  for (int i = 0; i < n; i++) e += 0.5 * q[i] * phi[i];
+  *E = e;
+}
+
+/* Top-level kernel of a slab (reading of the top level for x, y periodic and
+ * z open): the level-L kernel k_L summed over the 2-D lattice, at the pure z
+ * offset z. With k_L = 1/r - h_L, h_L(r) = 1/r - gamma(r/a_L)/a_L (zero for
+ * r >= a_L, a_L = 2^(L-1) a), the 1/r part is the 2-D Ewald sum above and
+ * the h_L part a finite direct sum; at z = 0 the R = 0 term is the limit
+ * (erfc(alpha r) - 1)/r + gamma(r/a_L)/a_L -> -2 alpha/sqrt(pi) + gamma(0)/a_L. */
+double or_slab_top(int p, double a, int nlev, double Lx, double Ly, double z) {
+  const double aL = ldexp(a, nlev - 1), alpha = 6.0 / (Lx < Ly ? Lx : Ly);
+  const int zero = fabs(z) < 1e-300;
+  double v = or_ewald2d_pair(Lx, Ly, 0.0, 0.0, z, alpha, zero);
+  if (zero) v += -2.0 * alpha / sqrt(OR_PI) + or_gamma(p, 0.0) / aL;
+  int ni = (int)ceil(aL / Lx) + 1, nj = (int)ceil(aL / Ly) + 1;
+  for (int i = -ni; i <= ni; i++)
+    for (int j = -nj; j <= nj; j++) {
+      if (zero && i == 0 && j == 0) continue;
+      double r = sqrt((i * Lx) * (i * Lx) + (j * Ly) * (j * Ly) + z * z);
+      if (r < aL) v -= 1.0 / r - or_gamma(p, r / aL) / aL;
+    }
+  return v;
+}
+
+/* Strain derivatives of the slab top-level kernel at the z offset z, which =
+ * 1..6 for eps_xx, yy, zz, xy, xz, yz: d/d eps of or_slab_top with the lattice
+ * and the offset strained, by central differences (step 1e-5; the kernel is
+ * smooth in the cell). xy, xz and yz vanish: the lattice is symmetric under
+ * x -> -x and y -> -y. */
+double or_slab_top_deps(int p, double a, int nlev, double Lx, double Ly, double z, int which) {
+  const double e = 1e-5;
+  switch (which) {
+    case 1: return (or_slab_top(p, a, nlev, Lx * (1 + e), Ly, z) - or_slab_top(p, a, nlev, Lx * (1 - e), Ly, z)) / (2 * e);
+    case 2: return (or_slab_top(p, a, nlev, Lx, Ly * (1 + e), z) - or_slab_top(p, a, nlev, Lx, Ly * (1 - e), z)) / (2 * e);
+    case 3: return (or_slab_top(p, a, nlev, Lx, Ly, z * (1 + e)) - or_slab_top(p, a, nlev, Lx, Ly, z * (1 - e))) / (2 * e);
+    default: return 0.0;
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -330,8 +452,15 @@ int or_plan_init(or_plan* P) {
     while ((1 << (nl - 1)) < Mper) nl++;
     if (P->levels > 0 && P->levels != nl) return 2;
     P->nlev = nl;
-    P->top_kept = 0;
-    P->ncomp = nl - 1;
+    if (P->pbc[0] && P->pbc[1] && !P->pbc[2]) {
+      /* slab: the top level (one point along x, y; open along z) is kept,
+       * with k_L summed over the 2-D lattice (or_slab_top) */
+      P->top_kept = 1;
+      P->ncomp = nl;
+    } else {
+      P->top_kept = 0;
+      P->ncomp = nl - 1;
+    }
   } else {
     P->top_kept = 1;
     P->nlev = P->levels;
@@ -616,7 +745,7 @@ void or_prolong_add(const or_plan* P, int l, const double* coarse, double* fine)
 /* ------------------------------------------------------------------------ */
 
 /* Offset box of the stencil applied on level l (1-based): d in [lo, lo+sz).
- * Levels below the top: [-R, R] per axis. Top level kept (all axes open): the
+ * Levels below the top: [-R, R] per axis. Top level kept (all axes open, or a slab): the
  * full range of grid displacements. Periodic axes are folded onto [0, n_l):
  * on a periodic grid the operator sums every image of an offset. */
 void or_stencil_box(const or_plan* P, int l, int* lo, int* sz) {
@@ -661,6 +790,7 @@ void or_stencil_build(const or_plan* P, int l, int which, const double* G, doubl
   double hl[3];
   for (int d = 0; d < 3; d++) hl[d] = ldexp(P->h1[d], l - 1);
   int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  const int slab_top = l == P->nlev && P->pbc[0] && P->pbc[1] && !P->pbc[2];
   size_t ns = (size_t)ssz[0] * ssz[1] * ssz[2];
   double* smp = (double*)malloc(sizeof(double) * ns);
 #pragma omp parallel for schedule(static)
@@ -673,7 +803,14 @@ void or_stencil_build(const or_plan* P, int l, int which, const double* G, doubl
           v[a] = G ? G[3 * a + 0] * g[0] + G[3 * a + 1] * g[1] + G[3 * a + 2] * g[2] : g[a];
         double rr = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         double val;
-        if (which == 0) {
+        if (slab_top) {
+          /* x, y offsets are lattice vectors here: the lattice sum depends on z only
+           * (a strain G, if given, is taken diagonal) */
+          double gx = G ? G[0] : 1.0, gy = G ? G[4] : 1.0;
+          double lx = P->L[0] * gx, ly = P->L[1] * gy;
+          val = which == 0 ? or_slab_top(p, P->a, P->nlev, lx, ly, v[2])
+                           : or_slab_top_deps(p, P->a, P->nlev, lx, ly, v[2], which);
+        } else if (which == 0) {
           val = or_kl(p, P->a, P->nlev, l, rr);
         } else {
           int a = ab[which - 1][0], b = ab[which - 1][1];

@@ -55,6 +55,81 @@ static double klev(const SysHost& S, int l, double r, bool deriv) {
   return soft(S.p, r / s1) / s1 - soft(S.p, r / s2) / s2;
 }
 
+// ------------------------------------------------------------------ slab top level
+// A slab (x, y periodic, z open) keeps its top level, whose grid has one point
+// per period along x and y: the level-L kernel k_L summed over the 2-D lattice
+// R = (i Lx, j Ly, 0) at the pure z offset. The sum of the 1/r tail diverges
+// by a constant that multiplies the squared total charge (zero for neutral
+// systems) and is left out; what remains is split the Ewald way:
+//   sum_R k_L = sum_R [erfc(al s)/s - h_L(s)] + (pi/A) sum_(G != 0) (1/|G|) [u(G, z) + u(G, -z)]
+//               - (2 pi/A) [z erf(al z) + exp(-al^2 z^2)/(al sqrt(pi))],
+// s = |R + z e_z|, h_L(s) = 1/s - gamma(s/a_L)/a_L (zero beyond a_L),
+// u(G, z) = e^(|G| z) erfc(|G|/(2 al) + al z), G = 2 pi (i/Lx, j/Ly), A = Lx Ly.
+// At z = 0 the R = 0 term is its limit -2 al/sqrt(pi) + gamma(0)/a_L.
+
+// e^(g z) erfc(g/(2 al) + al z) without overflow (scaled erfc for large arguments)
+static double slab_u(double g, double z, double al) {
+  const double x = g / (2.0 * al) + al * z;
+  if (x <= 0.0) return std::exp(g * z) * std::erfc(x);
+  double sc;  // e^(x^2) erfc(x)
+  if (x < 10.0) {
+    sc = std::exp(x * x) * std::erfc(x);
+  } else {
+    double term = 1.0, sum = 1.0;
+    const double inv = 0.5 / (x * x);
+    for (int k = 1; k <= 12; k++) {
+      term *= -(2.0 * k - 1.0) * inv;
+      sum += term;
+    }
+    sc = sum / (x * std::sqrt(M_PI));
+  }
+  return std::exp(-g * g / (4.0 * al * al) - al * al * z * z) * sc;
+}
+
+static double slab_top_kernel(const SysHost& S, double Lx, double Ly, double z) {
+  const double aL = S.a * std::ldexp(1.0, S.nlev - 1);
+  const double al = 6.0 / std::min(Lx, Ly), A = Lx * Ly;
+  const double rc = 7.0 / al, gc = 14.0 * al;
+  const bool at0 = std::fabs(z) < 1e-300;
+  double v = 0.0;
+  const int ni = (int)std::ceil(std::max(rc, aL) / Lx) + 1, nj = (int)std::ceil(std::max(rc, aL) / Ly) + 1;
+  for (int i = -ni; i <= ni; i++)
+    for (int j = -nj; j <= nj; j++) {
+      if (at0 && i == 0 && j == 0) continue;
+      const double sx = i * Lx, sy = j * Ly;
+      const double sd = std::sqrt(sx * sx + sy * sy + z * z);
+      if (sd < rc) v += std::erfc(al * sd) / sd;
+      if (sd < aL) v -= 1.0 / sd - soft(S.p, sd / aL) / aL;
+    }
+  if (at0) v += -2.0 * al / std::sqrt(M_PI) + soft(S.p, 0.0) / aL;
+  const int mi = (int)std::ceil(gc * Lx / (2.0 * M_PI)) + 1, mj = (int)std::ceil(gc * Ly / (2.0 * M_PI)) + 1;
+  double rec = 0.0;
+  for (int i = -mi; i <= mi; i++)
+    for (int j = -mj; j <= mj; j++) {
+      if (i == 0 && j == 0) continue;
+      const double gx = 2.0 * M_PI * i / Lx, gy = 2.0 * M_PI * j / Ly;
+      const double g = std::sqrt(gx * gx + gy * gy);
+      if (g >= gc) continue;
+      rec += (slab_u(g, z, al) + slab_u(g, -z, al)) / g;
+    }
+  v += M_PI / A * rec;
+  v -= 2.0 * M_PI / A * (z * std::erf(al * z) + std::exp(-al * al * z * z) / (al * std::sqrt(M_PI)));
+  return v;
+}
+
+// strain derivatives (comp 1..6 = xx, yy, zz, xy, xz, yz) by central
+// differences of the lattice sum with the lattice or the offset strained;
+// the shear components vanish by the x -> -x, y -> -y symmetry of the lattice
+static double slab_top_deps(const SysHost& S, double z, int comp) {
+  const double e = 1e-5, Lx = S.L[0], Ly = S.L[1];
+  switch (comp) {
+    case 1: return (slab_top_kernel(S, Lx * (1 + e), Ly, z) - slab_top_kernel(S, Lx * (1 - e), Ly, z)) / (2 * e);
+    case 2: return (slab_top_kernel(S, Lx, Ly * (1 + e), z) - slab_top_kernel(S, Lx, Ly * (1 - e), z)) / (2 * e);
+    case 3: return (slab_top_kernel(S, Lx, Ly, z * (1 + e)) - slab_top_kernel(S, Lx, Ly, z * (1 - e))) / (2 * e);
+    default: return 0.0;
+  }
+}
+
 // Pieces of the centred B-spline Phi_p(t) = N_p(t + p/2), N_p the cardinal
 // B-spline on [0, p): out[i][k] is the coefficient of s^k of Phi_p(i + s),
 // s in [0, 1), i = 0 .. p/2 - 1. Built from N_1 = 1 on [0, 1) by the
@@ -159,6 +234,7 @@ struct Box3 {
 // [-E, E] (per axis), sample(n) = f(h o n) for the level spacing hl. comp = 0:
 // k_l(|v|); comp 1..6: k_l'(|v|) v_a v_b / |v| with ab = xx,yy,zz,xy,xz,yz.
 static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box3& out) {
+  const bool slab_top = l == S.nlev && S.pbc[0] && S.pbc[1] && !S.pbc[2];
   const int r = S.hw;
   const std::vector<double>& wh = S.omh;
   double hl[3];
@@ -179,6 +255,12 @@ static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box
         double v[3] = {hl[0] * x, hl[1] * y, hl[2] * z};
         double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         double val;
+        if (slab_top) {
+          // x, y offsets are lattice vectors: the lattice sum depends on z alone
+          val = comp == 0 ? slab_top_kernel(S, S.L[0], S.L[1], v[2]) : slab_top_deps(S, v[2], comp);
+          smp.at(x, y, z) = val;
+          continue;
+        }
         if (comp == 0) {
           val = klev(S, l, rr, false);
         } else {
@@ -462,7 +544,9 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     if (P.levels > 0 && P.levels != L)
       return fail(err, MSM_ERR_UNSUPPORTED, "levels is fixed by the periodic grid (log2(M) + 1)");
     S.nlev = L;
-    S.ncomp = L - 1;
+    // periodic cells drop the one-point top level (zero for neutral systems);
+    // a slab keeps it, with k_L summed over the 2-D lattice (slab_top_kernel)
+    S.ncomp = (S.pbc[0] && S.pbc[1] && !S.pbc[2]) ? L : L - 1;
   } else {
     if (P.levels > 0) {
       S.nlev = P.levels;

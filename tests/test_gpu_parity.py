@@ -289,6 +289,19 @@ def test_gradient_through_phi(key):
     assert rel_rms(pos.grad.cpu().numpy(), dpos_ref) <= F_TOL
 
 
+def test_slab_against_ewald2d():
+    # the slab's top level (k_L summed over the 2-D lattice) on the GPU against the 2-D Ewald sum,
+    # at the accuracy the method reaches with p = 8 (the periodic MSM reaches the same against 3-D Ewald)
+    import oracle as O
+    O.build()
+    w = W.random_box(800, seed=41, pbc=(1, 1, 0), p=8, h=1.2, a=10.0)
+    r = gpu_run(w)
+    E2, phi2 = O.ewald2d(w.cell[0], w.cell[1], w.pos.astype(np.float64), w.q.astype(np.float64))
+    assert rel_rms(r["phi"], phi2) <= 1e-3
+    assert abs(r["E"] - E2) <= 5e-3 * abs(E2)
+    assert r["plan"].info()["stencil_kind"][-1] == 1  # the top level is evaluated (a box)
+
+
 def test_evaluate_host_end_to_end():
     # host buffers in and out (the benchmark's end-to-end call) against the oracle
     key = "periodic_20001"

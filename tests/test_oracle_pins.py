@@ -528,6 +528,49 @@ def test_force_vjp_identities_against_differences(oracle, pbc):
             assert fd == pytest.approx(dr_ref[i, d], rel=1e-4, abs=1e-5)
 
 
+def test_ewald2d_alpha_independence_and_gap_limit(oracle):
+    """The 2-D Ewald sum of a neutral slab does not depend on the splitting
+    parameter, and the 3-D Ewald sum with a vacuum gap plus the slab dipole
+    correction 2 pi M_z^2 / V converges to it as the gap grows."""
+    rng = np.random.default_rng(17)
+    Lx, Ly, n = 10.0, 12.0, 40
+    pos = np.column_stack([rng.uniform(0, Lx, n), rng.uniform(0, Ly, n), rng.uniform(0, 6, n)])
+    q = np.concatenate([np.ones(n // 2), -np.ones(n // 2)])
+    rng.shuffle(q)
+    Es = [oracle.ewald2d(Lx, Ly, pos, q, al)[0] for al in (0.4, 0.6, 0.9)]
+    assert max(Es) - min(Es) <= 1e-12 * abs(Es[0])
+    Mz = (q * pos[:, 2]).sum()
+    errs = []
+    for gap in (20.0, 40.0, 80.0):
+        Lz = 6.0 + gap
+        E3 = oracle.ewald_auto((Lx, Ly, Lz), pos, q, forces=False)[0]
+        errs.append(abs(E3 + 2 * math.pi / (Lx * Ly * Lz) * Mz ** 2 - Es[0]))
+    assert errs[0] > errs[1] > errs[2] and errs[2] <= 1e-9 * abs(Es[0])
+
+
+def test_slab_top_level_against_ewald2d(oracle):
+    """A slab keeps its top level with k_L summed over the 2-D lattice: the MSM
+    potentials then match the 2-D Ewald sum to the method's accuracy (as the
+    periodic MSM matches the 3-D Ewald sum); dropping the top level, as for
+    periodic cells, would leave a 100x larger error."""
+    from paper_2510_05961_gb300 import workloads as W
+    w = W.random_box(800, seed=41, pbc=(1, 1, 0), p=8, h=1.2, a=10.0)
+    pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+    P = oracle.plan_for(w)
+    assert P.top_kept == 1 and P.ncomp == P.nlev
+    r = oracle.msm(P, pos, q, forces=False, virial=False)
+    E2, phi2 = oracle.ewald2d(w.cell[0], w.cell[1], pos, q)
+    rel = np.sqrt(((r["phi"] - phi2) ** 2).mean() / (phi2 ** 2).mean())
+    assert rel <= 1e-3 and abs(r["E"] - E2) <= 5e-3 * abs(E2)
+    P.ncomp = P.nlev - 1  # the top level left out
+    rd = oracle.msm(P, pos, q, forces=False, virial=False)
+    assert np.sqrt(((rd["phi"] - phi2) ** 2).mean() / (phi2 ** 2).mean()) >= 20 * rel
+    # the lattice-summed top kernel is even in z and smooth through z = 0
+    k = [oracle.slab_top(8, 10.0, P.nlev, w.cell[0], w.cell[1], z) for z in (-3.0, -1e-4, 0.0, 1e-4, 3.0)]
+    assert k[0] == pytest.approx(k[4], rel=1e-12) and k[1] == pytest.approx(k[3], rel=1e-12)
+    assert abs(k[2] - k[1]) <= 1e-6 * abs(k[2])
+
+
 def test_half_cell_translation_invariance(oracle):
     # shifting a periodic system by L/2 moves every evaluated level by whole points
     pos, q, cell = _small_periodic()
@@ -541,11 +584,12 @@ def test_half_cell_translation_invariance(oracle):
         assert np.allclose(rs["F"], r["F"], rtol=1e-10, atol=1e-10)
 
 
-@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0)])
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0), (1, 1, 0)])
 def test_virial_against_strain_differences(oracle, pbc):
-    """W = -dE/d eps under r -> (1+eps) r, A -> (1+eps) A (grid coordinates fixed)."""
+    """W = -dE/d eps under r -> (1+eps) r, A -> (1+eps) A (grid coordinates fixed);
+    for the slab this includes the strain derivative of the lattice-summed top level."""
     pos, q, cell = _small_periodic()
-    if not any(pbc):
+    if not all(pbc):
         pos = np.clip(pos, 0.5, 8.5)
     P = oracle.make_plan(cell, pbc, 0, 3.5, 4, grid_override=(8, 8, 8))
     r = oracle.msm(P, pos, q)
