@@ -41,6 +41,8 @@ class Plan(C.Structure):
         ("S", C.c_int * 3), ("R", C.c_int * 3), ("hw", C.c_int),
         ("C", C.c_int * 3), ("edge", C.c_double * 3), ("nnbr", C.c_int * 3),
         ("invLf", C.c_float * 3),
+        ("A", C.c_double * 9), ("tri", C.c_int), ("Ainv", C.c_double * 9), ("Tinv", C.c_double * 9),
+        ("Tf", C.c_float * 9), ("wplane", C.c_double * 3),
     ]
 
     def level_shape(self, l):
@@ -160,7 +162,13 @@ def omega_exact(p, maxhw=96):
 
 # --------------------------------------------------------------------------- plan
 def make_plan(cell, pbc, h, a, p, levels=0, grid_override=(0, 0, 0), qi_mode=0):
+    """cell: 3 edge lengths, or a 3x3 / 9-entry matrix whose rows are the cell vectors."""
     P = Plan()
+    cm = np.asarray(cell, np.float64)
+    if cm.size == 9:
+        for k in range(9):
+            P.A[k] = float(cm.reshape(9)[k])
+        cell = [float(np.linalg.norm(cm.reshape(3, 3)[d])) for d in range(3)]
     for d in range(3):
         P.L[d] = float(cell[d])
         P.pbc[d] = int(pbc[d])
@@ -340,6 +348,30 @@ def ewald(cell, pos, q, alpha, rcut, kmax, forces=True):
     lib().or_ewald(_ptr(L), n, _ptr(pos), _ptr(q), float(alpha), float(rcut), float(kmax), _ptr(E), _ptr(phi),
                    _ptr(F))
     return float(E[0]), phi, F
+
+
+def ewald_tri(A, pos, q, alpha, rcut, kmax):
+    """Ewald sum for a general periodic cell (rows of A are the cell vectors): (E, phi)."""
+    pos, q = _d(pos), _d(q)
+    A = _d(np.asarray(A, np.float64).reshape(9))
+    n = pos.shape[0]
+    E = np.zeros(1)
+    phi = np.zeros(n)
+    lib().or_ewald_tri(_ptr(A), n, _ptr(pos), _ptr(q), C.c_double(alpha), C.c_double(rcut), C.c_double(kmax),
+                       _ptr(E), _ptr(phi))
+    return float(E[0]), phi
+
+
+def ewald_tri_auto(A, pos, q, tol=1e-13):
+    """ewald_tri with alpha / kmax from the shortest face distance (truncation errors below tol)."""
+    import math
+    Am = np.asarray(A, np.float64).reshape(3, 3)
+    V = abs(np.linalg.det(Am))
+    w = [V / np.linalg.norm(np.cross(Am[(d + 1) % 3], Am[(d + 2) % 3])) for d in range(3)]
+    rcut = min(0.5 * min(w), 12.0)
+    x = math.sqrt(-math.log(tol))
+    alpha = x / rcut
+    return ewald_tri(Am, pos, q, alpha, rcut, 2 * alpha * x)
 
 
 def ewald2d(Lx, Ly, pos, q, alpha=0.0):

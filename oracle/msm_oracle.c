@@ -56,6 +56,13 @@ typedef struct {
   double edge[3];       /* binning cell edges */
   int nnbr[3];          /* neighbour-cell reach ceil(a/edge) */
   float invLf[3];       /* (float)(1/L): binning contract */
+  /* general (triclinic) cells, Sec. 3.2.2's transform to the unit cube */
+  double A[9];          /* input: cell rows a, b, c (row-major); all zero = diag(L) */
+  int tri;              /* derived: 1 when A has off-diagonal entries */
+  double Ainv[9];       /* A^-1 */
+  double Tinv[9];       /* A^-T: fractional coordinates s = A^-T r */
+  float Tf[9];          /* (float) A^-T: binning contract of general cells */
+  double wplane[3];     /* distances between opposite cell faces, V / |a_e x a_f| */
 } or_plan;
 
 /* ------------------------------------------------------------------------ */
@@ -407,9 +414,60 @@ static int ceildiv(int a, int b) { return -floordiv(-a, b); }
  * M = ceil(L/h), level-1 indices [-p/2, M+p/2], each coarser level keeping the
  * indices that restriction can reach; with every axis open the top level is
  * evaluated with its full-range stencil. */
+static void mat_inv3(const double* m, double* inv, double* det) {
+  double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  double d = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  *det = d;
+  inv[0] = c00 / d;
+  inv[1] = (m[2] * m[7] - m[1] * m[8]) / d;
+  inv[2] = (m[1] * m[5] - m[2] * m[4]) / d;
+  inv[3] = c01 / d;
+  inv[4] = (m[0] * m[8] - m[2] * m[6]) / d;
+  inv[5] = (m[2] * m[3] - m[0] * m[5]) / d;
+  inv[6] = c02 / d;
+  inv[7] = (m[1] * m[6] - m[0] * m[7]) / d;
+  inv[8] = (m[0] * m[4] - m[1] * m[3]) / d;
+}
+
+/* general cells: rows a, b, c of A; lengths, A^-1, A^-T, face distances.
+ * Returns 1 for a degenerate or left-handed cell, 2 for a tilted cell with
+ * an open axis (not supported). */
+static int plan_cell(or_plan* P) {
+  int any = 0;
+  for (int k = 0; k < 9; k++) if (P->A[k] != 0.0) any = 1;
+  if (!any) {
+    for (int d = 0; d < 3; d++) P->A[4 * d] = P->L[d];
+  } else {
+    for (int d = 0; d < 3; d++)
+      P->L[d] = sqrt(P->A[3 * d] * P->A[3 * d] + P->A[3 * d + 1] * P->A[3 * d + 1] + P->A[3 * d + 2] * P->A[3 * d + 2]);
+  }
+  P->tri = 0;
+  for (int k = 0; k < 9; k++) if (k % 4 != 0 && P->A[k] != 0.0) P->tri = 1;
+  if (P->tri && !(P->pbc[0] && P->pbc[1] && P->pbc[2])) return 2;
+  double det;
+  mat_inv3(P->A, P->Ainv, &det);
+  if (!(det > 0.0)) return 1;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      P->Tinv[3 * i + j] = P->Ainv[3 * j + i];
+      P->Tf[3 * i + j] = (float)P->Tinv[3 * i + j];
+    }
+  for (int d = 0; d < 3; d++) {
+    const double* u = P->A + 3 * ((d + 1) % 3);
+    const double* v = P->A + 3 * ((d + 2) % 3);
+    double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    P->wplane[d] = det / sqrt(cx * cx + cy * cy + cz * cz);
+  }
+  return 0;
+}
+
 int or_plan_init(or_plan* P) {
   int p = P->p;
   if (p != 4 && p != 6 && p != 8) return 1;
+  {
+    int rc = plan_cell(P);
+    if (rc) return rc;
+  }
   if (P->qi_mode != 0 && P->qi_mode != 1) return 1;
   if (P->qi_mode == 1) {
     double tmp[2 * OR_MAXHW + 1];
@@ -501,17 +559,28 @@ int or_plan_init(or_plan* P) {
         if (P->n[l][d] < 1) P->n[l][d] = 1;
       }
   for (int d = 0; d < 3; d++) {
-    P->S[d] = (int)ceil(2.0 * P->a / P->h1[d]) - 1;
+    if (!P->tri) {
+      P->S[d] = (int)ceil(2.0 * P->a / P->h1[d]) - 1;
+    } else {
+      /* tilted cell: the samples |A^T (n / M)| < 2a lie in an ellipsoid whose
+       * extent along index axis d is 2a M_d sqrt((G^-1)_dd), G = A A^T, and
+       * (G^-1)_dd is the squared length of the d-th column of A^-1 */
+      double c2 = 0.0;
+      for (int e = 0; e < 3; e++) c2 += P->Ainv[3 * e + d] * P->Ainv[3 * e + d];
+      P->S[d] = (int)ceil(2.0 * P->a * P->M[d] * sqrt(c2)) - 1;
+    }
     if (P->S[d] < 0) P->S[d] = 0;
     P->R[d] = P->S[d] + P->hw;
     int C;
+    /* spacing of the grid planes across axis d (h_1 for a rectangular cell) */
+    const double hp = P->tri ? P->wplane[d] / P->M[d] : P->h1[d];
     if (P->pbc[d]) {
       /* periodic axis: cells of k level-1 intervals, k the largest power of
        * two with k h_1 <= a/2 for x, y and <= a/4 for z (at least 1), at
-       * most 512 cells */
+       * most 512 cells; h_1 is the spacing of the grid planes */
       const double lim = (d == 2 ? 0.25 : 0.5) * P->a;
       int k = 1;
-      while (2 * k <= P->M[d] && 2 * k * P->h1[d] <= lim) k *= 2;
+      while (2 * k <= P->M[d] && 2 * k * hp <= lim) k *= 2;
       while (P->M[d] / k > 512) k *= 2;
       C = P->M[d] / k;
     } else {
@@ -521,7 +590,7 @@ int or_plan_init(or_plan* P) {
       if (C > 256) C = 256;
     }
     P->C[d] = C;
-    P->edge[d] = P->L[d] / C;
+    P->edge[d] = (P->tri ? P->wplane[d] : P->L[d]) / C;  /* distance between cell faces */
     P->nnbr[d] = (int)ceil(P->a / P->edge[d]);
     P->invLf[d] = (float)(1.0 / P->L[d]);
   }
@@ -551,6 +620,17 @@ int or_bin(const or_plan* P, int n, const float* pos, const float* q, int* cell_
       c[d] = 0;
       if (!isfinite(x)) { status |= OR_ST_NONFINITE; continue; }
       float s = x * P->invLf[d];
+      if (P->tri) {
+        /* general cell: s_d = ((T_d0 x + T_d1 y) + T_d2 z), FP32, each product and
+         * sum rounded once (T = (float) A^-T); a rectangular cell gives exactly
+         * the single product above */
+        const float* Tr = P->Tf + 3 * d;
+        s = ((Tr[0] * pos[3 * i]) + (Tr[1] * pos[3 * i + 1])) + (Tr[2] * pos[3 * i + 2]);
+        if (!isfinite(pos[3 * i]) || !isfinite(pos[3 * i + 1]) || !isfinite(pos[3 * i + 2])) {
+          status |= OR_ST_NONFINITE;
+          continue;
+        }
+      }
       if (P->pbc[d]) {
         s = s - floorf(s);
         if (s >= 1.0f) s = 0.0f;
@@ -602,6 +682,20 @@ static double to_u(const or_plan* P, int d, double x) {
   return x / P->h1[d];
 }
 
+/* level-1 grid coordinates of atom position r: u = M o s, s = A^-T r wrapped
+ * into [0, 1) (general cells; rectangular cells use to_u per axis) */
+static void atom_u(const or_plan* P, const double* r, double* u) {
+  for (int d = 0; d < 3; d++) {
+    if (!P->tri) {
+      u[d] = to_u(P, d, r[d]);
+      continue;
+    }
+    double sd = P->Tinv[3 * d] * r[0] + P->Tinv[3 * d + 1] * r[1] + P->Tinv[3 * d + 2] * r[2];
+    sd -= floor(sd);
+    u[d] = sd * P->M[d];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Anterpolation, interpolation (Sec. 3.2.2, Alg. anterpolation_double_loop,  */
 /* Eqs. grid_charge, uoneplus_interpolation_with_index_set,                  */
@@ -616,9 +710,10 @@ void or_anterp(const or_plan* P, int n, const double* pos, const double* q, doub
   for (int k = 0; k < nsz; k++) grid[k] = 0.0;
   for (int i = 0; i < n; i++) {
     int base[3], idx[3][8];
-    double w[3][8];
+    double w[3][8], uu[3];
+    atom_u(P, pos + 3 * i, uu);
     for (int d = 0; d < 3; d++) {
-      double u = to_u(P, d, pos[3 * i + d]);
+      double u = uu[d];
       base[d] = (int)floor(u) - p / 2 + 1;
       for (int j = 0; j < p; j++) {
         w[d][j] = or_bspline(p, u - (base[d] + j));
@@ -644,13 +739,15 @@ void or_interp(const or_plan* P, int n, const double* pos, const double* q, cons
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; i++) {
     int base[3], idx[3][8];
-    double w[3][8], dw[3][8];
+    double w[3][8], dw[3][8], uu[3];
+    atom_u(P, pos + 3 * i, uu);
     for (int d = 0; d < 3; d++) {
-      double u = to_u(P, d, pos[3 * i + d]);
+      double u = uu[d];
       base[d] = (int)floor(u) - p / 2 + 1;
       for (int j = 0; j < p; j++) {
         w[d][j] = or_bspline(p, u - (base[d] + j));
-        dw[d][j] = or_dbspline(p, u - (base[d] + j)) / P->h1[d];
+        /* d/dx_d for rectangular cells; d/du_d for general cells (mapped below) */
+        dw[d][j] = or_dbspline(p, u - (base[d] + j)) / (P->tri ? 1.0 : P->h1[d]);
         idx[d][j] = gidx(P, 1, d, base[d] + j);
       }
     }
@@ -666,6 +763,16 @@ void or_interp(const or_plan* P, int n, const double* pos, const double* q, cons
           gz += ev * w[0][jx] * w[1][jy] * dw[2][jz];
         }
     phi1[i] = ph;
+    if (P->tri) {
+      /* grad_r = A^-1 diag(M) grad_u (u = M o A^-T r) */
+      double gu[3] = {gx, gy, gz};
+      double gr[3];
+      for (int e = 0; e < 3; e++)
+        gr[e] = P->Ainv[3 * e] * P->M[0] * gu[0] + P->Ainv[3 * e + 1] * P->M[1] * gu[1] + P->Ainv[3 * e + 2] * P->M[2] * gu[2];
+      gx = gr[0];
+      gy = gr[1];
+      gz = gr[2];
+    }
     if (F1) {
       F1[3 * i + 0] = -q[i] * gx;
       F1[3 * i + 1] = -q[i] * gy;
@@ -798,6 +905,13 @@ void or_stencil_build(const or_plan* P, int l, int which, const double* G, doubl
     for (int iy = 0; iy < ssz[1]; iy++)
       for (int iz = 0; iz < ssz[2]; iz++) {
         double g[3] = {hl[0] * (ix + slo[0]), hl[1] * (iy + slo[1]), hl[2] * (iz + slo[2])};
+        if (P->tri) {
+          /* general cell: the grid displacement n (level-l index steps) is the
+           * Cartesian vector sum_d n_d 2^(l-1) / M_d a_d */
+          double f[3] = {ldexp((double)(ix + slo[0]), l - 1) / P->M[0], ldexp((double)(iy + slo[1]), l - 1) / P->M[1],
+                         ldexp((double)(iz + slo[2]), l - 1) / P->M[2]};
+          for (int c = 0; c < 3; c++) g[c] = f[0] * P->A[c] + f[1] * P->A[3 + c] + f[2] * P->A[6 + c];
+        }
         double v[3];
         for (int a = 0; a < 3; a++)
           v[a] = G ? G[3 * a + 0] * g[0] + G[3 * a + 1] * g[1] + G[3 * a + 2] * g[2] : g[a];
@@ -963,8 +1077,115 @@ void or_grid_virial_level(const or_plan* P, int l, const double* qg, double W6[6
  * W0 = -1/2 sum_i sum_(j,n) q_i q_j k_0'(|d|) d d^T / |d| (row-major 3x3).
  * E0 = 1/2 sum_i q_i phi0_i. Candidates come from a cell list with cells of
  * edge >= a. F0, W0 may be NULL. */
+/* or_short_range for a general (tilted, periodic) cell: the same sums over a
+ * cell list in fractional coordinates s = A^-T r; a point within a of r_i has
+ * |s_d - s_i,d| <= a / w_d (w_d the distance between the cell faces across d),
+ * which bounds the cells visited; displacements d = A^T (s_j + k - s_i). */
+static void short_range_tri(const or_plan* P, int n, const double* pos, const double* q, double* phi0, double* F0,
+                            double* W0) {
+  int p = P->p;
+  double a = P->a;
+  int C[3];
+  for (int d = 0; d < 3; d++) {
+    C[d] = (int)floor(P->wplane[d] / a);
+    if (C[d] < 1) C[d] = 1;
+    if (C[d] > 512) C[d] = 512;
+  }
+  double* sf = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+  for (int i = 0; i < n; i++)
+    for (int d = 0; d < 3; d++) {
+      const double* r = pos + 3 * i;
+      double sd = P->Tinv[3 * d] * r[0] + P->Tinv[3 * d + 1] * r[1] + P->Tinv[3 * d + 2] * r[2];
+      sd -= floor(sd);
+      if (sd >= 1.0) sd -= 1.0;
+      sf[3 * i + d] = sd;
+    }
+  int ncell = C[0] * C[1] * C[2];
+  int* head = (int*)calloc((size_t)ncell + 1, sizeof(int));
+  int* list = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  int* cid = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int i = 0; i < n; i++) {
+    int c[3];
+    for (int d = 0; d < 3; d++) {
+      int ci = (int)floor(sf[3 * i + d] * C[d]);
+      c[d] = ci < 0 ? 0 : (ci > C[d] - 1 ? C[d] - 1 : ci);
+    }
+    cid[i] = (c[0] * C[1] + c[1]) * C[2] + c[2];
+    head[cid[i] + 1]++;
+  }
+  for (int c = 0; c < ncell; c++) head[c + 1] += head[c];
+  {
+    int* cur = (int*)malloc(sizeof(int) * (ncell > 0 ? ncell : 1));
+    for (int c = 0; c < ncell; c++) cur[c] = head[c];
+    for (int i = 0; i < n; i++) list[cur[cid[i]]++] = i;
+    free(cur);
+  }
+  double self = or_gamma(p, 0.0) / a;
+  double* Wi = W0 ? (double*)malloc(sizeof(double) * 9 * (n > 0 ? n : 1)) : NULL;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int i = 0; i < n; i++) {
+    const double* si = sf + 3 * i;
+    int clo[3], chi[3];
+    for (int d = 0; d < 3; d++) {
+      double reach = a / P->wplane[d];
+      clo[d] = (int)floor((si[d] - reach) * C[d]);
+      chi[d] = (int)floor((si[d] + reach) * C[d]);
+    }
+    double ph = 0.0, f[3] = {0, 0, 0}, wv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int ux = clo[0]; ux <= chi[0]; ux++)
+      for (int uy = clo[1]; uy <= chi[1]; uy++)
+        for (int uz = clo[2]; uz <= chi[2]; uz++) {
+          int u[3] = {ux, uy, uz}, cw[3], k[3];
+          int zero_shift = 1;
+          for (int d = 0; d < 3; d++) {
+            k[d] = floordiv(u[d], C[d]);
+            cw[d] = u[d] - k[d] * C[d];
+            if (k[d] != 0) zero_shift = 0;
+          }
+          int c = (cw[0] * C[1] + cw[1]) * C[2] + cw[2];
+          for (int t = head[c]; t < head[c + 1]; t++) {
+            int j = list[t];
+            if (j == i && zero_shift) continue;
+            double ds[3], d[3];
+            for (int e = 0; e < 3; e++) ds[e] = sf[3 * j + e] + k[e] - si[e];
+            for (int c2 = 0; c2 < 3; c2++) d[c2] = ds[0] * P->A[c2] + ds[1] * P->A[3 + c2] + ds[2] * P->A[6 + c2];
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= a * a) continue;
+            double r = sqrt(r2);
+            ph += q[j] * or_kl(p, a, P->nlev, 0, r);
+            double dk = or_dkl(p, a, P->nlev, 0, r);
+            for (int dd = 0; dd < 3; dd++) f[dd] += q[i] * q[j] * dk * d[dd] / r;
+            if (Wi)
+              for (int aa = 0; aa < 3; aa++)
+                for (int bb = 0; bb < 3; bb++) wv[3 * aa + bb] += -0.5 * q[i] * q[j] * dk * d[aa] * d[bb] / r;
+          }
+        }
+    phi0[i] = ph - q[i] * self;
+    if (F0)
+      for (int dd = 0; dd < 3; dd++) F0[3 * i + dd] = f[dd];
+    if (Wi)
+      for (int k2 = 0; k2 < 9; k2++) Wi[9 * i + k2] = wv[k2];
+  }
+  if (W0) {
+    for (int k2 = 0; k2 < 9; k2++) {
+      double acc = 0.0;
+      for (int i = 0; i < n; i++) acc += Wi[9 * i + k2];
+      W0[k2] = acc;
+    }
+    free(Wi);
+  }
+  free(sf);
+  free(head);
+  free(list);
+  free(cid);
+}
+
 void or_short_range(const or_plan* P, int n, const double* pos, const double* q, double* phi0, double* F0,
                     double* W0) {
+  if (P->tri) {
+    short_range_tri(P, n, pos, q, phi0, F0, W0);
+    return;
+  }
   int p = P->p;
   double a = P->a;
   int C[3];
@@ -1299,4 +1520,96 @@ void or_ewald(const double* L, int n, const double* pos, const double* q, double
   free(Sre);
   free(Sim);
   free(Ak);
+}
+
+/* Ewald sum for a general periodic cell (rows a, b, c of A; tin-foil): real
+ * space over lattice vectors A^T n with |r_ij + A^T n| < rcut, reciprocal
+ * space over k = 2 pi sum_j m_j b_j (b_j the columns of A^-1, a_i . b_j =
+ * delta_ij) with |k| <= kmax, self term -2 alpha/sqrt(pi) q_i; E = 1/2 sum q phi. */
+void or_ewald_tri(const double* A, int n, const double* pos, const double* q, double alpha, double rcut, double kmax,
+                  double* E, double* phi) {
+  double Ai[9], det;
+  mat_inv3(A, Ai, &det);
+  double V = det, w[3];
+  for (int d = 0; d < 3; d++) {
+    const double* u = A + 3 * ((d + 1) % 3);
+    const double* v = A + 3 * ((d + 2) % 3);
+    double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    w[d] = det / sqrt(cx * cx + cy * cy + cz * cz);
+  }
+  int im[3];
+  for (int d = 0; d < 3; d++) im[d] = (int)ceil(rcut / w[d]) + 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0;
+    for (int j = 0; j < n; j++) {
+      double ds[3];
+      for (int d = 0; d < 3; d++) {
+        double rd[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
+        ds[d] = Ai[d] * rd[0] + Ai[3 + d] * rd[1] + Ai[6 + d] * rd[2];  /* (A^-T r)_d */
+        ds[d] -= floor(ds[d] + 0.5);
+      }
+      for (int nx = -im[0]; nx <= im[0]; nx++)
+        for (int ny = -im[1]; ny <= im[1]; ny++)
+          for (int nz = -im[2]; nz <= im[2]; nz++) {
+            if (j == i && nx == 0 && ny == 0 && nz == 0) continue;
+            double f[3] = {ds[0] + nx, ds[1] + ny, ds[2] + nz}, d[3];
+            for (int c = 0; c < 3; c++) d[c] = f[0] * A[c] + f[1] * A[3 + c] + f[2] * A[6 + c];
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rcut * rcut) continue;
+            double r = sqrt(r2);
+            ph += q[j] * erfc(alpha * r) / r;
+          }
+    }
+    phi[i] = ph - 2.0 * alpha / sqrt(OR_PI) * q[i];
+  }
+  int mm[3];
+  for (int d = 0; d < 3; d++) {
+    double la = sqrt(A[3 * d] * A[3 * d] + A[3 * d + 1] * A[3 * d + 1] + A[3 * d + 2] * A[3 * d + 2]);
+    mm[d] = (int)floor(kmax * la / (2.0 * OR_PI)) + 1;
+  }
+  long nkx = 2L * mm[0] + 1, nky = 2L * mm[1] + 1, nkz = 2L * mm[2] + 1, nk = nkx * nky * nkz;
+  double* Ak = (double*)malloc(sizeof(double) * nk);
+  double* Sre = (double*)malloc(sizeof(double) * nk);
+  double* Sim = (double*)malloc(sizeof(double) * nk);
+  double (*kv)[3] = (double (*)[3])malloc(sizeof(double) * 3 * nk);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (long t = 0; t < nk; t++) {
+    int m[3] = {(int)(t / (nky * nkz)) - mm[0], (int)((t / nkz) % nky) - mm[1], (int)(t % nkz) - mm[2]};
+    double k[3];
+    for (int c = 0; c < 3; c++) k[c] = 2.0 * OR_PI * (m[0] * Ai[3 * c] + m[1] * Ai[3 * c + 1] + m[2] * Ai[3 * c + 2]);
+    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    for (int c = 0; c < 3; c++) kv[t][c] = k[c];
+    if ((m[0] == 0 && m[1] == 0 && m[2] == 0) || k2 > kmax * kmax) {
+      Ak[t] = 0.0;
+      Sre[t] = Sim[t] = 0.0;
+      continue;
+    }
+    Ak[t] = 4.0 * OR_PI / V * exp(-k2 / (4.0 * alpha * alpha)) / k2;
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < n; j++) {
+      double kr = k[0] * pos[3 * j] + k[1] * pos[3 * j + 1] + k[2] * pos[3 * j + 2];
+      sr += q[j] * cos(kr);
+      si += q[j] * sin(kr);
+    }
+    Sre[t] = sr;
+    Sim[t] = si;
+  }
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0;
+    for (long t = 0; t < nk; t++) {
+      if (Ak[t] == 0.0) continue;
+      double kr = kv[t][0] * pos[3 * i] + kv[t][1] * pos[3 * i + 1] + kv[t][2] * pos[3 * i + 2];
+      ph += Ak[t] * (Sre[t] * cos(kr) + Sim[t] * sin(kr));
+    }
+    phi[i] += ph;
+  }
+  double e = 0.0;
+  for (int i = 0; i < n; i++) e += 0.5 * q[i] * phi[i];
+  *E = e;
+  free(Ak);
+  free(Sre);
+  free(Sim);
+  free(kv);
 }

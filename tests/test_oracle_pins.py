@@ -420,6 +420,102 @@ def test_msm_madelung(oracle):
     assert np.allclose(r["W"], np.eye(3) * r["E"] / 3, rtol=5e-5, atol=5e-5 * abs(r["E"]))
 
 
+def _sheared(L=12.0, n=60, seed=5):
+    # a cube of atoms and a tilted cell spanning the same lattice (b' = a + b)
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0, L, (n, 3))
+    q = np.concatenate([np.ones(n // 2), -np.ones(n // 2)])
+    rng.shuffle(q)
+    return pos, q, L, np.array([[L, 0, 0], [L, L, 0], [0, 0, L]])
+
+
+def test_triclinic_ewald_lattice_invariance(oracle):
+    """The general-cell Ewald sum depends on the lattice, not on the cell that
+    spans it, and reduces to the rectangular sum for a diagonal cell."""
+    pos, q, L, A = _sheared()
+    E0 = oracle.ewald_auto((L, L, L), pos, q, forces=False)[0]
+    Ed = oracle.ewald_tri_auto(np.diag([L, L, L]), pos, q)[0]
+    Es = oracle.ewald_tri_auto(A, pos, q)[0]
+    Es2 = oracle.ewald_tri_auto(np.array([[L, 0, 0], [2 * L, L, 0], [L, -L, L]]), pos, q)[0]
+    assert Ed == pytest.approx(E0, rel=1e-12)
+    assert Es == pytest.approx(E0, rel=1e-10) and Es2 == pytest.approx(E0, rel=1e-10)
+
+
+def test_triclinic_msm_against_ewald(oracle):
+    """MSM in a tilted cell (fractional grids, metric-aware stencils) converges to
+    the Ewald sum of the same lattice as the grid is refined."""
+    pos, q, L, A = _sheared()
+    E0, phi0 = oracle.ewald_auto((L, L, L), pos, q, forces=False)[:2]
+    errs = []
+    for M in (16, 32):
+        P = oracle.make_plan(A, (1, 1, 1), 0, 6.0, 6, grid_override=(M, M, M))
+        assert P.tri == 1
+        r = oracle.msm(P, pos, q, forces=False, virial=False)
+        errs.append(np.sqrt(((r["phi"] - phi0) ** 2).mean() / (phi0 ** 2).mean()))
+    assert errs[1] <= 1e-4 and errs[0] > 10 * errs[1]
+
+
+def test_triclinic_forces_and_virial_by_differences(oracle):
+    """F = -dE/dr and all six W = -dE/d eps (r -> (1+eps) r, cell rows -> (1+eps) rows)
+    by central differences in a tilted cell."""
+    pos, q, L, A = _sheared()
+    P = oracle.make_plan(A, (1, 1, 1), 0, 6.0, 4, grid_override=(16, 16, 16))
+    r = oracle.msm(P, pos, q)
+    for i in (3, 7):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += 1e-5
+            pm[i, d] -= 1e-5
+            fd = (oracle.msm(P, pp, q, False, False)["E"] - oracle.msm(P, pm, q, False, False)["E"]) / 2e-5
+            assert -fd == pytest.approx(r["F"][i, d], rel=1e-6, abs=1e-7)
+    for a, b in [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]:
+        es = []
+        for sg in (1, -1):
+            eps = np.zeros((3, 3))
+            eps[a, b] += 0.5e-6 * sg
+            eps[b, a] += 0.5e-6 * sg
+            Fm = np.eye(3) + eps
+            P2 = oracle.make_plan(A @ Fm.T, (1, 1, 1), 0, 6.0, 4, grid_override=(16, 16, 16))
+            es.append(oracle.msm(P2, pos @ Fm.T, q, False, False)["E"])
+        assert -(es[0] - es[1]) / 2e-6 == pytest.approx(r["W"][a, b], rel=1e-5, abs=1e-7)
+
+
+def test_primitive_nacl_madelung(oracle):
+    """Rock salt in its primitive (rhombohedral) cell, two ions: the general-cell
+    Ewald sum and the MSM (p = 6) reproduce the Madelung constant of the
+    conventional cell (Sec. 4.1's non-orthorhombic check)."""
+    ref = float(_golden_lines("madelung_nacl.txt")[0][0])
+    A = 0.5 * np.array([[0, 1, 1], [1, 0, 1], [1, 1, 0]])
+    pos = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    q = np.array([1.0, -1.0])
+    assert -oracle.ewald_tri_auto(A, pos, q)[0] * 0.5 == pytest.approx(ref, abs=1e-6)
+    P = oracle.make_plan(A, (1, 1, 1), 0, 4.0 * 0.5, 6, grid_override=(16, 16, 16))  # a = 4 d_min
+    r = oracle.msm(P, pos, q, virial=False)
+    assert -r["E"] * 0.5 == pytest.approx(ref, abs=1e-6)
+    assert np.abs(r["F"]).max() < 1e-10
+
+
+def test_triclinic_binning_contract(oracle):
+    """The FP32 cell contract of a general cell, written out in numpy float32:
+    s_d = ((T_d0 x + T_d1 y) + T_d2 z) with T = (float) A^-T, each step rounded."""
+    pos, q, L, A = _sheared(n=500, seed=9)
+    pos = (pos + np.array([0.3, -0.2, 0.1]) * L).astype(np.float32)  # some atoms outside the cell
+    P = oracle.make_plan(A, (1, 1, 1), 0, 6.0, 4, grid_override=(16, 16, 16))
+    cid, start, perm, st = oracle.bin_atoms(P, pos, q.astype(np.float32))
+    assert st == 0
+    T = np.linalg.inv(A).T.astype(np.float32)
+    C = np.array([P.C[d] for d in range(3)])
+    c = np.zeros((len(pos), 3), np.int64)
+    for d in range(3):
+        s = ((T[d, 0] * pos[:, 0]).astype(np.float32) + (T[d, 1] * pos[:, 1]).astype(np.float32)).astype(np.float32)
+        s = (s + (T[d, 2] * pos[:, 2]).astype(np.float32)).astype(np.float32)
+        s = (s - np.floor(s)).astype(np.float32)
+        s[s >= np.float32(1.0)] = np.float32(0.0)
+        t = (s * np.float32(C[d])).astype(np.float32)
+        c[:, d] = np.minimum(t.astype(np.int64), C[d] - 1)
+    assert np.array_equal(cid, (c[:, 0] * C[1] + c[:, 1]) * C[2] + c[:, 2])
+
+
 def _small_periodic():
     pos, q = _random_atoms(40, 9.0, 13)
     return pos, q, (9.0, 9.0, 9.0)
