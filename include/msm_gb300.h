@@ -60,8 +60,13 @@ typedef struct msm_batch_s* msm_batch;
 
 /* Settings of one system; the arguments of the paper's set_up_msm_params
  * (Sec. 3.5): cell, periodicity, level-one spacing, level-zero cutoff, order.
- *  cell[9]        row-major 3x3 cell matrix, rows = cell vectors a, b, c. This
- *                 build accepts diagonal matrices only (orthorhombic cells).
+ *  cell[9]        row-major 3x3 cell matrix, rows = cell vectors a, b, c, a
+ *                 right-handed basis. Off-diagonal entries (a tilted cell,
+ *                 Sec. 3.2.2's transform to the unit cube: grids in the
+ *                 fractional coordinates s = A^-T r) need pbc 1, 1, 1; L below
+ *                 is then the length of each cell vector, the stencils follow
+ *                 the cell's metric and every level uses dense boxes.
+ *                 msm_force_vjp and msm_plan_set_cell refuse tilted cells.
  *  pbc[3]         1 = periodic along that axis, 0 = open.
  *  h              target level-1 grid spacing h_1 (> 0 unless overridden).
  *                 Periodic axes use M = 2^round(log2(L/h)) intervals (all

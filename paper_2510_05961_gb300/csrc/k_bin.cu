@@ -2,7 +2,8 @@
 // batch in one set of launches).
 //
 // Cell-index contract (bit-exact, FP32, round-to-nearest, no contraction):
-//   s = x * (float)(1/L); periodic: s -= floorf(s), s >= 1 -> 0;
+//   s = x * (float)(1/L) (tilted cells: s_d = ((T_d0 x + T_d1 y) + T_d2 z),
+//   T = (float) A^-T); periodic: s -= floorf(s), s >= 1 -> 0;
 //   open: s outside [0,1] -> MSM_DEV_OUT_OF_CELL (axis cell 0);
 //   c = min((int)(s * (float)C), C-1); cell = (cx*Cy + cy)*Cz + cz.
 // Within a cell the sorted order is ascending atom index (stable), so the
@@ -41,6 +42,22 @@ __device__ __forceinline__ int reduced_coord(const SysDev& S, int d, float x, fl
   return 0;
 }
 
+// Tilted (periodic) cells: s_d = ((T_d0 x + T_d1 y) + T_d2 z) in FP32 with
+// every product and sum rounded once (T = (float) A^-T), then wrapped as a
+// periodic axis; for a rectangular cell this is the single product above.
+__device__ __forceinline__ int tilted_coords(const SysDev& S, const float* x, float (&s)[3]) {
+  s[0] = s[1] = s[2] = 0.0f;
+  if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) return kDevNonFinite;
+  for (int d = 0; d < 3; d++) {
+    const float* T = S.Tf + 3 * d;
+    float v = __fadd_rn(__fadd_rn(__fmul_rn(T[0], x[0]), __fmul_rn(T[1], x[1])), __fmul_rn(T[2], x[2]));
+    v = __fsub_rn(v, floorf(v));
+    if (v >= 1.0f) v = 0.0f;
+    s[d] = v;
+  }
+  return 0;
+}
+
 __device__ __forceinline__ int axis_cell(const SysDev& S, int d, float s, float& t) {
   t = __fmul_rn(s, (float)S.C[d]);
   int c = (int)t;
@@ -57,11 +74,20 @@ __global__ void k_bin_count(const SysDev* __restrict__ sys, const AtomItem* __re
   int g = S.atom_off + local;
   int bad = isfinite(q[g]) ? 0 : kDevNonFinite;
   int c[3];
-  for (int d = 0; d < 3; d++) {
-    float s, t;
-    int b = reduced_coord(S, d, pos[3 * g + d], s);
-    bad |= b;
-    c[d] = b ? 0 : axis_cell(S, d, s, t);
+  if (S.tri) {
+    float s[3];
+    bad |= tilted_coords(S, pos + 3 * (long long)g, s);
+    for (int d = 0; d < 3; d++) {
+      float t;
+      c[d] = bad ? 0 : axis_cell(S, d, s[d], t);
+    }
+  } else {
+    for (int d = 0; d < 3; d++) {
+      float s, t;
+      int b = reduced_coord(S, d, pos[3 * g + d], s);
+      bad |= b;
+      c[d] = b ? 0 : axis_cell(S, d, s, t);
+    }
   }
   int cell = (c[0] * S.C[1] + c[1]) * S.C[2] + c[2];
   cell_id[g] = cell;
@@ -173,6 +199,28 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   // FP32 input so that displacements between nearby atoms are exact to FP32
   float loc[3], u[3];
   int c[3] = {cell / (S.C[1] * S.C[2]), (cell / S.C[2]) % S.C[1], cell % S.C[2]};
+  if (S.tri) {
+    // Cartesian position relative to the base of the cell's column, c_x / C_x a +
+    // c_y / C_y b, formed in FP64 from the FP32 input and wrapped the way the
+    // FP32 contract placed the atom (a fractional coordinate that rounds across
+    // a face follows its cell)
+    float sf[3];
+    tilted_coords(S, pos + 3 * (long long)g, sf);
+    const double x[3] = {pos[3 * g], pos[3 * g + 1], pos[3 * g + 2]};
+    double sd[3];
+    for (int d = 0; d < 3; d++) {
+      double v = S.Td[3 * d] * x[0] + S.Td[3 * d + 1] * x[1] + S.Td[3 * d + 2] * x[2];
+      v -= floor(v);
+      if (c[d] == 0 && v > 0.5) v -= 1.0;
+      if (c[d] == S.C[d] - 1 && v < 0.5) v += 1.0;
+      sd[d] = v - (d < 2 ? (double)c[d] / S.C[d] : 0.0);
+      u[d] = sf[d] * S.Mf[d];
+    }
+    for (int e = 0; e < 3; e++) loc[e] = (float)(sd[0] * S.Ad[e] + sd[1] * S.Ad[3 + e] + sd[2] * S.Ad[6 + e]);
+    xq[dst] = make_float4(loc[0], loc[1], loc[2], qq);
+    uq[dst] = make_float4(u[0], u[1], u[2], qq);
+    return;
+  }
   for (int d = 0; d < 3; d++) {
     float s, t;
     const float x = pos[3 * g + d];

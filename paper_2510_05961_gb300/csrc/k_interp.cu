@@ -317,8 +317,17 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
     }
   }
   phi_lr[k] = ph;
-  // field -grad phi^(1+) at the atom (the force is q_i times it)
-  if (want_f) f_lr[k] = make_float4(-gx * S.inv_h1[0], -gy * S.inv_h1[1], -gz * S.inv_h1[2], 0.f);
+  // field -grad phi^(1+) at the atom (the force is q_i times it); a tilted cell
+  // maps the grid derivatives by A^-1 diag(M)
+  if (want_f) {
+    if (S.tri) {
+      const float* J = S.Jg;
+      f_lr[k] = make_float4(-(J[0] * gx + J[1] * gy + J[2] * gz), -(J[3] * gx + J[4] * gy + J[5] * gz),
+                            -(J[6] * gx + J[7] * gy + J[8] * gz), 0.f);
+    } else {
+      f_lr[k] = make_float4(-gx * S.inv_h1[0], -gy * S.inv_h1[1], -gz * S.inv_h1[2], 0.f);
+    }
+  }
 }
 
 template <int P>

@@ -287,6 +287,139 @@ void launch_short_fvjp(const Work& w, const Tables& t, const AtomItem* items, in
   }
 }
 
+// General-cell variant (tilted periodic cells; correct for rectangular cells
+// too): positions are Cartesian offsets from the base c_x/C_x a + c_y/C_y b of
+// the atom's cell column, so the displacement to a candidate of column
+// (c_x + ox, c_y + oy) at z image kz is ox a/C_x + oy b/C_y + kz c + x_j - x_i,
+// the shift formed in FP64 once per run. A point within a of atom i has
+// |s_d - s_i,d| <= a / w_d (w_d the distance between the cell faces across d),
+// so every column within nnbr cells and, in each, the z cells within that
+// reach are visited; the pair test selects. The virial uses the same identity
+// as k_short, the image term (A n) s^T with A n = n_x a + n_y b + kz c.
+template <int P, bool WF, bool WW>
+__global__ void __launch_bounds__(kChunk) k_short_tri(const SysDev* __restrict__ sys,
+                                                      const AtomItem* __restrict__ items,
+                                                      const int* __restrict__ cell_start,
+                                                      const int* __restrict__ scell, const float4* __restrict__ xq,
+                                                      const float4* __restrict__ uq, float* __restrict__ phi_sr,
+                                                      float4* __restrict__ f_sr, double* __restrict__ part_w0) {
+  const int item = blockIdx.x;
+  AtomItem it = items[item];
+  const SysDev& S = sys[it.sys];
+  const int slot = (int)threadIdx.x;
+  const int local = it.start + slot;
+  const bool active = slot < it.count && local < S.n;
+  float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (active) {
+    const int k = S.atom_off + local;
+    const float4 xi = xq[k];
+    const float siz = uq[k].z / S.Mf[2];
+    const int cell = scell[k];
+    const int Cx = S.C[0], Cy = S.C[1], Cz = S.C[2];
+    const int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
+    float gc[P], gdc[P - 1];
+#pragma unroll
+    for (int t = 0; t < P; t++) gc[t] = S.gca[t];
+#pragma unroll
+    for (int t = 0; t < P - 1; t++) gdc[t] = S.gdca[t];
+    const float a2 = S.a2, inv_a2 = S.inv_a2;
+    const double ta[3] = {S.Ad[0] / Cx, S.Ad[1] / Cx, S.Ad[2] / Cx}, tb[3] = {S.Ad[3] / Cy, S.Ad[4] / Cy, S.Ad[5] / Cy};
+    const float rz = S.reach[2] + 2e-4f / Cz;  // fractional reach along c, with a rounding margin
+    int zlo = (int)floorf((siz - rz) * Cz), zhi = (int)floorf((siz + rz) * Cz);
+    float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    float img[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
+      const int ux = ci[0] + ox;
+      const int nxw = floordiv_s(ux, Cx), wx = ux - nxw * Cx;
+      for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
+        const int uy = ci[1] + oy;
+        const int nyw = floordiv_s(uy, Cy), wy = uy - nyw * Cy;
+        const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
+        double bxy[3];
+        for (int e = 0; e < 3; e++) bxy[e] = ox * ta[e] + oy * tb[e];
+        int uz = zlo;
+        while (uz <= zhi) {
+          const int kz = floordiv_s(uz, Cz);
+          const int wz = uz - kz * Cz;
+          const int wend = min(Cz - 1, wz + (zhi - uz));
+          const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+          const float bx = (float)(bxy[0] + kz * S.Ad[6] - (double)xi.x);
+          const float by = (float)(bxy[1] + kz * S.Ad[7] - (double)xi.y);
+          const float bz = (float)(bxy[2] + kz * S.Ad[8] - (double)xi.z);
+          float sx = 0.f, sy = 0.f, sz = 0.f;
+          for (int j = jb; j < je; j++) {
+            const float4 xj = xq[j];
+            const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < a2 && r2 > 0.f) {
+              const float rinv = rsqrtf(r2);
+              const float sg = 1.0f - r2 * inv_a2;
+              float g = gc[P - 1];
+#pragma unroll
+              for (int t = P - 2; t >= 0; t--) g = fmaf(g, sg, gc[t]);
+              ph = fmaf(xj.w, rinv - g, ph);
+              if (WF || WW) {
+                float dg = gdc[P - 2];
+#pragma unroll
+                for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, sg, gdc[t]);
+                const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
+                sx = fmaf(fr, dx, sx);
+                sy = fmaf(fr, dy, sy);
+                sz = fmaf(fr, dz, sz);
+              }
+            }
+          }
+          fx += sx;
+          fy += sy;
+          fz += sz;
+          if (WW && (nxw | nyw | kz) != 0) {
+            float tv[3];
+            for (int e = 0; e < 3; e++) tv[e] = (float)(nxw * S.Ad[e] + nyw * S.Ad[3 + e] + kz * S.Ad[6 + e]);
+            img[0] = fmaf(tv[0], sx, img[0]);
+            img[1] = fmaf(tv[1], sy, img[1]);
+            img[2] = fmaf(tv[2], sz, img[2]);
+            img[3] = fmaf(0.5f * tv[0], sy, fmaf(0.5f * tv[1], sx, img[3]));
+            img[4] = fmaf(0.5f * tv[0], sz, fmaf(0.5f * tv[2], sx, img[4]));
+            img[5] = fmaf(0.5f * tv[1], sz, fmaf(0.5f * tv[2], sy, img[5]));
+          }
+          uz += wend - wz + 1;
+        }
+      }
+    }
+    phi_sr[k] = ph - xi.w * S.self_coef;
+    if (WF) f_sr[k] = make_float4(fx, fy, fz, 0.f);
+    if (WW) {
+      // r_i in the frame of the displacements: the column base plus the offset
+      float r[3];
+      for (int e = 0; e < 3; e++)
+        r[e] = (float)(ci[0] * ta[e] + ci[1] * tb[e] + (double)(e == 0 ? xi.x : (e == 1 ? xi.y : xi.z)));
+      const float hq = -0.5f * xi.w;
+      w6[0] = xi.w * (r[0] * fx) + hq * img[0];
+      w6[1] = xi.w * (r[1] * fy) + hq * img[1];
+      w6[2] = xi.w * (r[2] * fz) + hq * img[2];
+      w6[3] = xi.w * (0.5f * (r[0] * fy + r[1] * fx)) + hq * img[3];
+      w6[4] = xi.w * (0.5f * (r[0] * fz + r[2] * fx)) + hq * img[4];
+      w6[5] = xi.w * (0.5f * (r[1] * fz + r[2] * fy)) + hq * img[5];
+    }
+  }
+  if (!WW) return;
+  const int lane = threadIdx.x & 31, wid = slot >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    double v = (double)w6[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) part_w0[6 * ((long long)item * kChunkWarps + wid) + c] = v;
+  }
+}
+
+template <int P>
+static void run_short_tri(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
+                          cudaStream_t s) {
+  auto kern = virial ? (forces ? k_short_tri<P, true, true> : k_short_tri<P, false, true>)
+                     : (forces ? k_short_tri<P, true, false> : k_short_tri<P, false, false>);
+  kern<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.uq, w.phi_sr, w.f_sr, w.part_w0);
+}
+
 template <int P, int NB>
 static void run_short_nb(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                          cudaStream_t s) {
@@ -299,11 +432,12 @@ static void run_short_nb(const Work& w, const Tables& t, const AtomItem* items, 
 template <int P>
 static void run_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                       cudaStream_t s, int block) {
-  if (block == kChunk / 2) run_short_nb<P, kChunk / 2>(w, t, items, nitems, forces, virial, s);
+  if (block == kShortTilted) run_short_tri<P>(w, t, items, nitems, forces, virial, s);
+  else if (block == kChunk / 2) run_short_nb<P, kChunk / 2>(w, t, items, nitems, forces, virial, s);
   else run_short_nb<P, kChunk>(w, t, items, nitems, forces, virial, s);
 }
 
-// block: threads per block, kChunk or kChunk / 2
+// block: threads per block of the rectangular-cell kernel (kChunk or kChunk / 2), or kShortTilted
 void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                   cudaStream_t s, int p, int block) {
   switch (p) {

@@ -84,7 +84,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   cudaStreamWaitEvent(E.side, E.ev_fork, 0);
   {
     Phase ph(E, MSM_PH_SHORT, E.side);
-    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, E.side, E.p, E.short_block);
+    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, E.side, E.p, E.short_code());
   }
   cudaEventRecord(E.ev_join, E.side);
   {
@@ -148,7 +148,7 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
     // the forward skipped these parts; the short-range kernel rewrites its
     // potential with identical values, so running it again is safe
     Phase ph(E, MSM_PH_SHORT, s);
-    launch_short(w, t, E.d_atom_items, nai, need_f || had_f, need_w || had_w, s, E.p, E.short_block);
+    launch_short(w, t, E.d_atom_items, nai, need_f || had_f, need_w || had_w, s, E.p, E.short_code());
     nl++;
     if (need_f && !had_f) {
       launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
@@ -183,7 +183,7 @@ static int run_field(Engine& E, void* ws, float* field, cudaStream_t s) {
   const int nai = (int)E.atom_items.size();
   if ((E.last_flags & MSM_WANT_FORCES) == 0) {
     const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
-    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_block);
+    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_code());
     launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
     E.last_flags |= MSM_WANT_FORCES;
   }
@@ -231,7 +231,7 @@ static int run_autotune(Engine& E, void* ws, size_t ws_bytes, int n_single, cons
   if (!rc) rc = E.set_anterp_tz(best_tz, &err);
   int best_nb = E.short_block;
   best = 1e30f;
-  if (!rc)
+  if (!rc && !E.any_tri)
     for (int nb : {kChunk, kChunk / 2}) {
       const float ms = timed([&] { launch_short(w, t, E.d_atom_items, nai, true, true, s, E.p, nb); });
       if (ms < best) {
@@ -413,13 +413,14 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
 // Consumes the workspace: a later msm_backward needs a new msm_forward.
 static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* dpos, cudaStream_t s) {
   if (!E.have_fwd || ws != E.last_ws) return set_err(MSM_ERR_NO_FORWARD, "msm_force_vjp needs a prior msm_forward on this workspace");
+  if (E.any_tri) return set_err(MSM_ERR_UNSUPPORTED, "msm_force_vjp: tilted cells are not supported");
   if (E.last_n > 0 && !u) return set_err(MSM_ERR_INVALID_ARG, "u must not be NULL");
   Work w = E.resolve(ws);
   Tables t = E.tables();
   const int nai = (int)E.atom_items.size();
   if ((E.last_flags & MSM_WANT_FORCES) == 0) {
     const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
-    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_block);
+    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_code());
     launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
   }
   if (E.last_n > 0) {
@@ -460,6 +461,7 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
   if (!plan || !cell) return set_err(MSM_ERR_INVALID_ARG, "plan and cell must not be NULL");
   Engine& E = plan->eng;
   SysHost& S = E.sys[0];
+  if (S.tri) return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell: tilted cells are not supported");
   for (int i = 0; i < 9; i++) {
     if (!std::isfinite(cell[i])) return set_err(MSM_ERR_INVALID_ARG, "cell has a non-finite entry");
     if (i % 4 != 0 && cell[i] != 0.0) return set_err(MSM_ERR_UNSUPPORTED, "only orthorhombic (diagonal) cells are supported");

@@ -15,6 +15,7 @@ namespace msm {
 constexpr int kMaxLev = 20;
 constexpr int kChunk = 256;        // atoms per per-atom work item
 constexpr int kChunkWarps = kChunk / 32;
+constexpr int kShortTilted = -1;  // short-range launch code of plans with tilted cells (k_short_tri)
 constexpr int kAnterpTX = 16, kAnterpTY = 8;  // anterpolation tile columns (x, y); its z-extent is tuned
 constexpr int kBallTY = 32;        // stencil tile rows (y)
 constexpr int kBallBZ = 16;        // outputs per thread along z
@@ -59,6 +60,13 @@ struct SysDev {
   float bsp[4][8];  // centred B-spline Phi_p on |t| in [i, i+1): sum_k bsp[i][k] (|t| - i)^k
   float om[4];      // prefilter of the ball levels: omega'_0 .. omega'_(pre_r) (symmetric), or identity
   int pre_r;        // prefilter half-width (p/2 - 1 when the ball kernels apply raw samples, else 0)
+  // general (tilted, periodic) cells; tri = 0 for rectangular cells
+  int tri;
+  float Tf[9];      // (float) A^-T: binning contract s_d = ((T_d0 x + T_d1 y) + T_d2 z)
+  double Ad[9];     // cell rows a, b, c (FP64: positions and image shifts)
+  double Td[9];     // A^-T (FP64)
+  float Jg[9];      // A^-1 diag(M): Cartesian gradient from level-1 grid derivatives
+  float reach[3];   // a / (distance between cell faces): fractional reach of the cutoff per axis
 };
 
 struct LevDev {

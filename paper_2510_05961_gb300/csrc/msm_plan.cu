@@ -253,6 +253,12 @@ static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box
     for (int y = slo[1]; y < slo[1] + ssz[1]; y++)
       for (int z = slo[2]; z < slo[2] + ssz[2]; z++) {
         double v[3] = {hl[0] * x, hl[1] * y, hl[2] * z};
+        if (S.tri) {
+          // tilted cell: the index step n is the vector sum_d n_d 2^(l-1) / M_d a_d
+          const double f[3] = {std::ldexp((double)x, l - 1) / S.M[0], std::ldexp((double)y, l - 1) / S.M[1],
+                               std::ldexp((double)z, l - 1) / S.M[2]};
+          for (int c = 0; c < 3; c++) v[c] = f[0] * S.A[c] + f[1] * S.A[3 + c] + f[2] * S.A[6 + c];
+        }
         double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         double val;
         if (slab_top) {
@@ -379,7 +385,9 @@ static void fill_stencils(SysHost& S, bool decide) {
     // more than once where the grid is shorter than the halo), which sums
     // every image of each offset exactly as the folded stencil does.
     if (decide) {
-      bool ball = !top && S.qi_mode == 0;  // exact interpolation: dense boxes (wide stencils, accuracy reference)
+      // exact interpolation: dense boxes (wide stencils, accuracy reference); tilted
+      // cells too (their stencils lack the reflection symmetry of the ball kernels)
+      bool ball = !top && S.qi_mode == 0 && !S.tri;
       for (int d = 0; d < 3; d++)
         if (S.B[d] > kBallRmax) ball = false;
       for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
@@ -473,11 +481,53 @@ static int fail(std::string* err, int code, const char* msg) {
   return code;
 }
 
+// 3x3 inverse by cofactors; returns the determinant
+static double inv3(const double* m, double* inv) {
+  const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  inv[0] = c00 / det;
+  inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+  inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+  inv[3] = c01 / det;
+  inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+  inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+  inv[6] = c02 / det;
+  inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+  inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+  return det;
+}
+
 int plan_system(const msm_params& P, SysHost& S, std::string* err) {
+  S.tri = false;
   for (int i = 0; i < 9; i++) {
     if (!std::isfinite(P.cell[i])) return fail(err, MSM_ERR_INVALID_ARG, "cell has a non-finite entry");
-    if (i % 4 != 0 && P.cell[i] != 0.0)
-      return fail(err, MSM_ERR_UNSUPPORTED, "only orthorhombic (diagonal) cells are supported");
+    if (i % 4 != 0 && P.cell[i] != 0.0) S.tri = true;
+  }
+  for (int i = 0; i < 9; i++) S.A[i] = P.cell[i];
+  double det = 0.0;
+  if (S.tri) {
+    // a tilted cell (Sec. 3.2.2's transform to the unit cube): periodic only
+    if (!(P.pbc[0] == 1 && P.pbc[1] == 1 && P.pbc[2] == 1))
+      return fail(err, MSM_ERR_UNSUPPORTED, "a non-orthorhombic cell must be periodic along all three axes");
+    det = inv3(S.A, S.Ainv);
+    if (!(det > 0.0)) return fail(err, MSM_ERR_INVALID_ARG, "cell rows must form a right-handed basis");
+  } else {
+    for (int i = 0; i < 9; i++) S.Ainv[i] = 0.0;
+    for (int d = 0; d < 3; d++) S.Ainv[4 * d] = 1.0 / P.cell[4 * d];
+  }
+  {
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) S.Tinv[3 * i + j] = S.Ainv[3 * j + i];
+    for (int d = 0; d < 3; d++) {
+      if (!S.tri) {
+        S.wplane[d] = P.cell[4 * d];
+        continue;
+      }
+      const double* u = S.A + 3 * ((d + 1) % 3);
+      const double* v = S.A + 3 * ((d + 2) % 3);
+      const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+      S.wplane[d] = det / std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
   }
   if (P.order != 4 && P.order != 6 && P.order != 8) return fail(err, MSM_ERR_INVALID_ARG, "order must be 4, 6 or 8");
   if (!(P.cutoff > 0.0) || !std::isfinite(P.cutoff)) return fail(err, MSM_ERR_INVALID_ARG, "cutoff must be > 0");
@@ -495,7 +545,9 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
   }
   int Mper = 0;
   for (int d = 0; d < 3; d++) {
-    S.L[d] = P.cell[4 * d];
+    S.L[d] = S.tri ? std::sqrt(P.cell[3 * d] * P.cell[3 * d] + P.cell[3 * d + 1] * P.cell[3 * d + 1] +
+                               P.cell[3 * d + 2] * P.cell[3 * d + 2])
+                   : P.cell[4 * d];
     if (!(S.L[d] > 0.0)) return fail(err, MSM_ERR_INVALID_ARG, "cell lengths must be > 0");
     if (P.pbc[d] != 0 && P.pbc[d] != 1) return fail(err, MSM_ERR_INVALID_ARG, "pbc entries must be 0 or 1");
     S.pbc[d] = P.pbc[d];
@@ -574,17 +626,27 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
   }
   // stencil radius, binning cells
   for (int d = 0; d < 3; d++) {
-    S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a / S.h1[d]) - 1);
+    if (!S.tri) {
+      S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a / S.h1[d]) - 1);
+    } else {
+      // samples |A^T (n / M)| < 2a fill an ellipsoid whose extent along index
+      // axis d is 2a M_d |column d of A^-1|
+      double c2 = 0.0;
+      for (int e = 0; e < 3; e++) c2 += S.Ainv[3 * e + d] * S.Ainv[3 * e + d];
+      S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a * S.M[d] * std::sqrt(c2)) - 1);
+    }
     S.R[d] = S.S[d] + S.hw;
-    S.prefilter = (S.p == 4 && S.qi_mode == 0);
+    S.prefilter = (S.p == 4 && S.qi_mode == 0 && !S.tri);
     S.B[d] = S.prefilter ? S.S[d] : S.R[d];
     if (S.pbc[d]) {
       // periodic axis: cells aligned with the grid, k = 2^j level-1 intervals
       // per cell, the largest with k h_1 <= a/2 along x, y and <= a/4 along z
-      // (k >= 1), at most 512 cells. Half-height cells along z (the axis of
+      // (k >= 1), at most 512 cells; h_1 is the spacing of the grid planes
+      // (wplane / M for a tilted cell). Half-height cells along z (the axis of
       // the cell columns) cut the short-range candidates by a tenth.
+      const double hp = S.tri ? S.wplane[d] / S.M[d] : S.h1[d];
       int k = 1;
-      while (2 * k <= S.M[d] && 2 * k * S.h1[d] <= (d == 2 ? 0.25 : 0.5) * S.a) k *= 2;
+      while (2 * k <= S.M[d] && 2 * k * hp <= (d == 2 ? 0.25 : 0.5) * S.a) k *= 2;
       while (S.M[d] / k > 512) k *= 2;
       S.C[d] = S.M[d] / k;
     } else {
@@ -592,7 +654,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
       int C = (int)std::floor((d == 2 ? 4.0 : 2.0) * S.L[d] / S.a);
       S.C[d] = std::min(std::max(C, 1), 256);
     }
-    S.edge[d] = S.L[d] / S.C[d];
+    S.edge[d] = S.wplane[d] / S.C[d];  // distance between cell faces
     S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
   }
   fill_stencils(S, true);
@@ -692,6 +754,8 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     if (sys[s].p != sys[0].p) return fail(err, MSM_ERR_UNSUPPORTED, "all systems of a batch need the same order");
   }
   p = sys[0].p;
+  any_tri = false;
+  for (const SysHost& S : sys) any_tri = any_tri || S.tri;
   // systems, atoms, cells, levels, grid pool
   std::vector<SysDev> hs(nsys);
   hlev.clear();
@@ -724,6 +788,15 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       D.Lf[d] = (float)S.L[d];
       D.h1f[d] = (float)S.h1[d];
     }
+    D.tri = S.tri ? 1 : 0;
+    for (int k = 0; k < 9; k++) {
+      D.Tf[k] = (float)S.Tinv[k];
+      D.Ad[k] = S.A[k];
+      D.Td[k] = S.Tinv[k];
+    }
+    for (int e = 0; e < 3; e++)
+      for (int d = 0; d < 3; d++) D.Jg[3 * e + d] = (float)(S.Ainv[3 * e + d] * S.M[d]);
+    for (int d = 0; d < 3; d++) D.reach[d] = (float)(S.a / S.wplane[d]);
     D.a2 = (float)(S.a * S.a);
     D.inv_a = (float)(1.0 / S.a);
     D.inv_a2 = (float)(1.0 / (S.a * S.a));

@@ -19,7 +19,11 @@ struct LevelHost {
 };
 
 struct SysHost {
-  double L[3];
+  double L[3];                       // lengths of the cell vectors (edge lengths of a rectangular cell)
+  // general (tilted, periodic) cells: rows a, b, c of A; fractional s = A^-T r
+  bool tri = false;
+  double A[9], Ainv[9], Tinv[9];
+  double wplane[3];                  // distances between opposite cell faces
   int pbc[3];
   double a;
   int p;
@@ -116,6 +120,8 @@ struct Engine {
   int vslices = 1;                  // virial reduction slices per system (k_virial_slices)
   int anterp_tz = 32;
   int short_block = kChunk;
+  bool any_tri = false;             // some system has a tilted cell: k_short_tri for all
+  int short_code() const { return any_tri ? kShortTilted : short_block; }
   double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
   void build_anterp_items(int tz);
   int set_anterp_tz(int tz, std::string* err);

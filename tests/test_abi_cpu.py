@@ -64,11 +64,17 @@ CASES = [
     # exact interpolation (qi_mode 1): wide omega', dense boxes on every level
     dict(cell=(30, 30, 30), pbc=(0, 0, 0), h=2.5, cutoff=10.0, order=4, levels=3, qi_mode=1),
     dict(cell=(8.0, 8.0, 8.0), pbc=(1, 1, 1), h=2.0, cutoff=2.0, order=6, qi_mode=1),
+    # tilted periodic cells (rows a, b, c): a sheared cube, primitive fcc, monoclinic
+    dict(cell=(12.0, 0, 0, 12.0, 12.0, 0, 0, 0, 12.0), pbc=(1, 1, 1), h=0.0, cutoff=6.0, order=4,
+         grid_override=(16, 16, 16)),
+    dict(cell=(0, 2.82, 2.82, 2.82, 0, 2.82, 2.82, 2.82, 0), pbc=(1, 1, 1), h=0.5, cutoff=2.0, order=6),
+    dict(cell=(10.0, 0, 0, 0, 10.0, 0, 3.0, 0, 9.539392014169456), pbc=(1, 1, 1), h=1.2, cutoff=5.0, order=4),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s_%s_p%d_qi%d" % (c["pbc"], c["cell"][0], c["order"],
-                                                                          c.get("qi_mode", 0)))
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s_%s_p%d_qi%d%s" % (c["pbc"], c["cell"][0], c["order"],
+                                                                            c.get("qi_mode", 0),
+                                                                            "_tri" if len(c["cell"]) == 9 else ""))
 def test_planner_matches_oracle(lib, oracle, case):
     rc, I, _ = _describe(lib, **case)
     assert rc == 0, lib.msm_last_error()
@@ -104,7 +110,8 @@ def _fold(K, lo, n, pbc):
 
 
 @pytest.mark.parametrize("case", CASES[:2] + CASES[4:9] + CASES[10:],
-                         ids=lambda c: "%s_%s_qi%d" % (c["pbc"], c["cell"][0], c.get("qi_mode", 0)))
+                         ids=lambda c: "%s_%s_qi%d%s" % (c["pbc"], c["cell"][0], c.get("qi_mode", 0),
+                                                        "_tri" if len(c["cell"]) == 9 else ""))
 def test_stencils_match_oracle(lib, oracle, case):
     rc, I, Pl = _describe(lib, **case)
     P = oracle.make_plan(case["cell"], case["pbc"], case["h"], case["cutoff"], case["order"], case.get("levels", 0),
@@ -141,10 +148,12 @@ def test_planner_rejects_bad_settings(lib):
         rc, _, _ = _describe(lib, **kw)
         assert rc == code, (kw, rc)
         assert lib.msm_last_error()
-    # a sheared cell is outside this build
-    P = _lib.make_params([10, 1, 0, 0, 10, 0, 0, 0, 10], (1, 1, 1), 1.0, 3.0, 4)
+    # a tilted cell needs all three axes periodic, and a right-handed basis
+    P = _lib.make_params([10, 1, 0, 0, 10, 0, 0, 0, 10], (1, 1, 0), 1.0, 3.0, 4)
     I = _lib.PlanInfo()
     assert lib.msm_plan_describe(C.byref(P), C.byref(I)) == _lib.MSM_ERR_UNSUPPORTED
+    P = _lib.make_params([10, 1, 0, 0, 0, 10, 0, 10, 0], (1, 1, 1), 1.0, 3.0, 4)
+    assert lib.msm_plan_describe(C.byref(P), C.byref(I)) == _lib.MSM_ERR_INVALID_ARG
 
 
 def test_batch_systems_plan(lib, oracle):
