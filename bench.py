@@ -52,6 +52,10 @@ def parse():
                     help="linear-scaling sweep instead of the headline step: forward only (E, phi, F) on periodic "
                          "cubes of 1000 * 2^k atoms, k = 0 .. --sweep-kmax; prints one JSON object")
     ap.add_argument("--sweep-kmax", type=int, default=14)
+    ap.add_argument("--cells", action="store_true",
+                    help="cell-shape comparison instead of the headline step: forward + backward of the same number "
+                         "of atoms in a periodic cube, a slab and tilted cells; prints one JSON object")
+    ap.add_argument("--cells-atoms", type=int, default=128000)
     return ap.parse_args()
 
 
@@ -602,12 +606,71 @@ def run_sweep(args):
                                         "phase overlaps the grid chain, so both include the contention"}))
 
 
+def run_cells(args):
+    """Forward + backward (E, F, dE/dq, virial) of N atoms at 0.1 atoms/A^3 in cells of different shape:
+    periodic cube, slab (x, y periodic; the lattice-summed top level), and tilted periodic cells (dense-box
+    stencils, general short-range kernel). Same p = 4, a = 8 and grid counts; CUDA events, L2 flushed."""
+    import numpy as np
+    import torch
+
+    from paper_2510_05961_gb300 import Plan, build
+    dev = torch.device("cuda", 0)
+    build.build()
+    n = args.cells_atoms
+    L = (n / 0.1) ** (1.0 / 3.0)
+    M = 2 ** int(round(math.log2(L / 2.0)))
+    shapes = {
+        "cube": (np.diag([L, L, L]), (1, 1, 1)),
+        "slab": (np.diag([L, L, L]), (1, 1, 0)),
+        "sheared": (np.array([[L, 0, 0], [0.5 * L, L, 0], [0.2 * L, -0.3 * L, L]]), (1, 1, 1)),
+        "hexagonal": (np.array([[L, 0, 0], [-0.5 * L, math.sqrt(3) / 2 * L, 0], [0, 0, L / (math.sqrt(3) / 2)]]),
+                      (1, 1, 1)),
+    }
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(77)
+    frac = rng.uniform(0, 1, (n, 3))
+    q = np.concatenate([np.ones(n // 2), -np.ones(n - n // 2)]).astype(np.float32)
+    rng.shuffle(q)
+    rows = {}
+    for name, (A, pbc) in shapes.items():
+        pos = (frac @ A).astype(np.float32)
+        plan = Plan(A.reshape(9), pbc, 0.0, 8.0, 4, 0, (M, M, M), max_atoms=n, device=dev)
+        tp, tq = torch.from_numpy(pos).to(dev), torch.from_numpy(q).to(dev)
+        plan.autotune(tp, tq)
+        g = torch.ones(1, dtype=torch.float64, device=dev)
+        for _ in range(max(args.warmup, 3)):
+            plan.forward(tp, tq, forces=True, virial=True)
+            plan.backward(g)
+        torch.cuda.synchronize()
+        t = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.forward(tp, tq, forces=True, virial=True)
+            plan.backward(g)
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1)
+        ms = t / args.steps
+        info = plan.info()
+        rows[name] = {"ms_per_step": ms, "atoms_per_s": n / (ms / 1e3), "R": info["R"],
+                      "stencil_kind": info["stencil_kind"], "pbc": list(pbc)}
+        del plan
+        torch.cuda.empty_cache()
+    print(json.dumps({"cells": rows, "atoms": n, "M": M, "unit": "atoms/s",
+                      "workload": "uniform fractional positions at 0.1 atoms/A^3, +/-1 charges; p=4, a=8, "
+                                  "M=%d; fwd+bwd (E, F, dE/dq, virial)" % M}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.cells:
+        run_cells(args)
     else:
         run_gpu(args)
 

@@ -431,7 +431,53 @@ __global__ void __launch_bounds__(NT) k_stencil_ball(const LevDev* __restrict__ 
   }
 }
 
-template <int WMAX, bool FACT>
+// General ball (tilted cells, where the samples have only the point symmetry
+// s(n) = s(-n)): every x-plane x0 - dx, dx = -R .. R, is staged in turn with
+// the stencil x-slab of that dx, and every column (dx, dy) applies its
+// samples on dz in [c - w, c + w] about the column's centre c (a multiple of
+// 4, so the shifted 16-byte row loads stay aligned; the halo hz covers
+// |c| + w). Same per-thread register blocking as the symmetric kernel, with
+// no mirrored rows to fold: 16 (2w + 1) FMA per column and output tile row.
+template <int WMAX>
+__global__ void __launch_bounds__(NT) k_stencil_gen(const LevDev* __restrict__ levs, const TileItem* __restrict__ items,
+                                                    const float* __restrict__ kpool, const int* __restrict__ wpool,
+                                                    float* __restrict__ grid, int stride, int plane_sz, int kslab_sz) {
+  extern __shared__ __align__(16) float smem[];
+  float* plane = smem;
+  float* kslab = smem + plane_sz;
+  int* wsl = reinterpret_cast<int*>(kslab + kslab_sz);
+  const TileItem it = items[blockIdx.x];
+  const LevDev& L = levs[it.lev];
+  const int Rx = L.R[0], Ry = L.R[1], hz = L.hz, SK = kSK(hz);
+  const int ty = threadIdx.x % TY, zb = threadIdx.x / TY;
+  float acc[BZ];
+#pragma unroll
+  for (int o = 0; o < BZ; o++) acc[o] = 0.f;
+  for (int step = 0; step <= 2 * Rx; step++) {
+    __syncthreads();
+    stage_ball(L, it, step, grid, kpool, L.k_off, 1, wpool, L.w_off, plane, kslab, wsl, stride);
+    cp_async_wait_all();
+    __syncthreads();
+    const int* cen = wpool + L.c_off + (long long)step * (2 * Ry + 1);
+    for (int dy = -Ry; dy <= Ry; dy++) {
+      const int w = wsl[dy + Ry];
+      if (w < 0) continue;
+      const int c = __ldg(cen + dy + Ry);
+      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz - c;
+      Col<0, WMAX>::stencil(w, acc, qrow, kslab + (dy + Ry) * SK + hz);
+    }
+  }
+  const int y = it.y0 + ty;
+  if (y < L.n[1]) {
+    float* out = grid + L.e_off + ((long long)it.x0 * L.n[1] + y) * L.n[2];
+    const int z0 = it.z0 + zb * BZ;
+#pragma unroll
+    for (int o = 0; o < BZ; o++)
+      if (z0 + o < L.n[2]) out[z0 + o] = acc[o] * L.scale;
+  }
+}
+
+template <int WMAX, bool FACT, bool GEN = false>
 __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                     const TileItem* __restrict__ items,
                                                     const float* __restrict__ kpool, const int* __restrict__ wpool,
@@ -474,10 +520,12 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ s
     const float* kslab = kslabs;
     const int* wc = wsl;
     const float cx = hx * (float)(step - Rx);
+    const int* cen = GEN ? wpool + L.c_off + (long long)step * (2 * Ry + 1) : nullptr;
     for (int dy = -Ry; dy <= Ry; dy++) {
       const int w = wc[dy + Ry];
       if (w < 0) continue;
-      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz;
+      const int c = GEN ? __ldg(cen + dy + Ry) : 0;  // column centre (tilted cells)
+      const float* qrow = plane + (ty - dy + Ry) * stride + zb * BZ + hz - c;
       const float* kd = kslab + (dy + Ry) * SK + hz;
       if (FACT)
         Col<0, WMAX>::virial_fact(w, w6, qown, qrow, kd, cx, hy * (float)dy);
@@ -636,28 +684,41 @@ static void run_ball(const Work& w, const Tables& t, const TileItem* items, int 
                                                  kslab_sz);
 }
 
-template <int WMAX, bool FACT>
+template <int WMAX, bool FACT, bool GEN>
 static void run_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int ryz_max[2],
                             int part_off, cudaStream_t s) {
   int stride, plane_sz, kslab_sz;
   size_t bytes;
   ball_smem(ryz_max, FACT ? 1 : 6, 1, stride, plane_sz, kslab_sz, bytes);
   static size_t attr = 0;
-  if (bytes > attr && cudaFuncSetAttribute(k_virial_ball<WMAX, FACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)bytes) == cudaSuccess)
+  if (bytes > attr && cudaFuncSetAttribute(k_virial_ball<WMAX, FACT, GEN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
     attr = bytes;
-  k_virial_ball<WMAX, FACT><<<nitems, NT, bytes, s>>>(t.sys, t.lev, items, t.kpool, t.wpool, w.grid,
-                                                      w.part_wg + 6 * (long long)part_off, stride, plane_sz,
-                                                      kslab_sz);
+  k_virial_ball<WMAX, FACT, GEN><<<nitems, NT, bytes, s>>>(t.sys, t.lev, items, t.kpool, t.wpool, w.grid,
+                                                           w.part_wg + 6 * (long long)part_off, stride, plane_sz,
+                                                           kslab_sz);
 }
 
-template <bool FACT>
+template <bool FACT, bool GEN>
 static void dispatch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
                                  int ryz_max[2], int part_off, cudaStream_t s) {
-  if (rmax <= 8) run_virial_ball<8, FACT>(w, t, items, nitems, ryz_max, part_off, s);
-  else if (rmax <= 12) run_virial_ball<12, FACT>(w, t, items, nitems, ryz_max, part_off, s);
-  else if (rmax <= 16) run_virial_ball<16, FACT>(w, t, items, nitems, ryz_max, part_off, s);
-  else run_virial_ball<24, FACT>(w, t, items, nitems, ryz_max, part_off, s);
+  if (rmax <= 8) run_virial_ball<8, FACT, GEN>(w, t, items, nitems, ryz_max, part_off, s);
+  else if (rmax <= 12) run_virial_ball<12, FACT, GEN>(w, t, items, nitems, ryz_max, part_off, s);
+  else if (rmax <= 16) run_virial_ball<16, FACT, GEN>(w, t, items, nitems, ryz_max, part_off, s);
+  else run_virial_ball<24, FACT, GEN>(w, t, items, nitems, ryz_max, part_off, s);
+}
+
+template <int WMAX>
+static void run_gen(const Work& w, const Tables& t, const TileItem* items, int nitems, int ryz_max[2],
+                    cudaStream_t s) {
+  int stride, plane_sz, kslab_sz;
+  size_t bytes;
+  ball_smem(ryz_max, 1, 1, stride, plane_sz, kslab_sz, bytes);
+  static size_t attr = 0;
+  if (bytes > attr && cudaFuncSetAttribute(k_stencil_gen<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bytes) == cudaSuccess)
+    attr = bytes;
+  k_stencil_gen<WMAX><<<nitems, NT, bytes, s>>>(t.lev, items, t.kpool, t.wpool, w.grid, stride, plane_sz, kslab_sz);
 }
 
 void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitems, int pre_r, cudaStream_t s) {
@@ -668,8 +729,15 @@ void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitem
 
 // ryz_max = {largest R_y, largest halo hz} over the ball levels; rmax = largest R_z
 void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
-                         int ryz_max[2], cudaStream_t s) {
+                         int ryz_max[2], bool general, cudaStream_t s) {
   if (nitems <= 0) return;
+  if (general) {  // tilted cells: shifted, non-symmetric columns
+    if (rmax <= 8) run_gen<8>(w, t, items, nitems, ryz_max, s);
+    else if (rmax <= 12) run_gen<12>(w, t, items, nitems, ryz_max, s);
+    else if (rmax <= 16) run_gen<16>(w, t, items, nitems, ryz_max, s);
+    else run_gen<24>(w, t, items, nitems, ryz_max, s);
+    return;
+  }
   if (rmax <= 8) run_ball<8>(w, t, items, nitems, ryz_max, s);
   else if (rmax <= 12) run_ball<12>(w, t, items, nitems, ryz_max, s);
   else if (rmax <= 16) run_ball<16>(w, t, items, nitems, ryz_max, s);
@@ -679,10 +747,11 @@ void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, 
 // factorized: the ball tables hold raw samples (p = 4) with the one-column
 // virial weights g
 void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
-                        int ryz_max[2], int part_off, bool factorized, cudaStream_t s) {
+                        int ryz_max[2], int part_off, bool factorized, bool general, cudaStream_t s) {
   if (nitems <= 0) return;
-  if (factorized) dispatch_virial_ball<true>(w, t, items, nitems, rmax, ryz_max, part_off, s);
-  else dispatch_virial_ball<false>(w, t, items, nitems, rmax, ryz_max, part_off, s);
+  if (factorized) dispatch_virial_ball<true, false>(w, t, items, nitems, rmax, ryz_max, part_off, s);
+  else if (general) dispatch_virial_ball<false, true>(w, t, items, nitems, rmax, ryz_max, part_off, s);
+  else dispatch_virial_ball<false, false>(w, t, items, nitems, rmax, ryz_max, part_off, s);
 }
 
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s) {

@@ -101,7 +101,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   {
     Phase ph(E, MSM_PH_STENCIL, s);
     launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
-    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, s);
+    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
     launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
   }
   {
@@ -159,7 +159,7 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   if (need_w) {
     Phase ph(E, MSM_PH_VIRIAL, s);
     const int nb = (int)E.ball_items.size();
-    launch_virial_ball(w, t, E.d_ball_items, nb, E.rmax, E.ryz, 0, E.p == 4, s);
+    launch_virial_ball(w, t, E.d_ball_items, nb, E.rmax, E.ryz, 0, E.p == 4 && !E.any_tri, E.any_tri, s);
     launch_virial_box(w, t, E.d_box_items, (int)E.box_items.size(), nb, s);
     launch_virial_out(w, t, E.nsys, E.vslices, E.d_voff, grad, virial, s);
     nl += (nb ? 1 : 0) + (E.box_items.empty() ? 0 : 1) + 2;
@@ -433,7 +433,7 @@ static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* 
       launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
     }
     launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
-    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, s);
+    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
     launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
     for (int l = E.maxcomp - 1; l >= 1; l--) {
       int a = E.prolong_off[l - 1], b = E.prolong_off[l];

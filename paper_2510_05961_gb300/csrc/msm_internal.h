@@ -84,6 +84,7 @@ struct LevDev {
   long long wh_off;         // ball: column half-widths of the virial weights
   int hz;                   // ball: z halo of the padded grid (>= R[2], multiple of 4)
   int pn[3];                // ball: padded grid dims
+  long long c_off;          // ball: column centres (int pool; all zero for rectangular cells)
   long long p_off;          // ball: float offset of the halo-padded, omega'-prefiltered copy of q~^l
                             // (ball levels apply raw kernel samples; R is the sample radius)
 };
@@ -146,10 +147,10 @@ void launch_prolong(const Work& w, const Tables& t, const TileItem* items, int n
 // stencils and grid virial (k_stencil.cu)
 void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitems, int pre_r, cudaStream_t s);
 void launch_stencil_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
-                         int ryz_max[2], cudaStream_t s);
+                         int ryz_max[2], bool general, cudaStream_t s);
 void launch_stencil_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s);
 void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, int nitems, int rmax,
-                        int ryz_max[2], int part_off, bool factorized, cudaStream_t s);
+                        int ryz_max[2], int part_off, bool factorized, bool general, cudaStream_t s);
 void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, int part_off,
                        cudaStream_t s);
 // outputs (k_final.cu)

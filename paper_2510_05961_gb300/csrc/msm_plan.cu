@@ -323,6 +323,11 @@ static void build_samples(const SysHost& S, int l, const int E[3], int comp, Box
     for (int y = -E[1]; y <= E[1]; y++)
       for (int z = -E[2]; z <= E[2]; z++) {
         double v[3] = {hl[0] * x, hl[1] * y, hl[2] * z};
+        if (S.tri) {
+          const double f[3] = {std::ldexp((double)x, l - 1) / S.M[0], std::ldexp((double)y, l - 1) / S.M[1],
+                               std::ldexp((double)z, l - 1) / S.M[2]};
+          for (int c = 0; c < 3; c++) v[c] = f[0] * S.A[c] + f[1] * S.A[3 + c] + f[2] * S.A[6 + c];
+        }
         double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         double val;
         if (comp == 0) {
@@ -385,9 +390,8 @@ static void fill_stencils(SysHost& S, bool decide) {
     // more than once where the grid is shorter than the halo), which sums
     // every image of each offset exactly as the folded stencil does.
     if (decide) {
-      // exact interpolation: dense boxes (wide stencils, accuracy reference); tilted
-      // cells too (their stencils lack the reflection symmetry of the ball kernels)
-      bool ball = !top && S.qi_mode == 0 && !S.tri;
+      // exact interpolation: dense boxes (wide stencils, accuracy reference)
+      bool ball = !top && S.qi_mode == 0 && S.allow_ball;
       for (int d = 0; d < 3; d++)
         if (S.B[d] > kBallRmax) ball = false;
       for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
@@ -442,8 +446,31 @@ static void fill_stencils(SysHost& S, bool decide) {
     S.sball.assign(s1.v.begin(), s1.v.end());
     S.dsh.assign((size_t)6 * nx * ny * nz, 0.0f);
     S.fsh.assign(S.prefilter ? (size_t)nx * ny * nz : 0, 0.0f);
-    // column half-widths, rounded up to even values (the stored rows are zero
-    // beyond the support): half as many unrolled column variants
+    // Column centres: zero for rectangular cells (every column is even in dz);
+    // a tilted cell's column (dx, dy) holds its samples on an interval around
+    // a shifted centre, taken here as the midpoint of the nonzero samples
+    // (of K and of the virial weights) rounded down to a multiple of 4, so the
+    // kernels' 16-byte row loads stay aligned after the shift.
+    S.cball.assign((size_t)nx * ny, 0);
+    if (S.tri)
+      for (int x = -S.B[0]; x <= S.B[0]; x++)
+        for (int y = -S.B[1]; y <= S.B[1]; y++) {
+          int lo = 1 << 30, hi = -(1 << 30);
+          for (int z = -S.B[2]; z <= S.B[2]; z++) {
+            size_t at = ((size_t)(x + S.B[0]) * ny + (y + S.B[1])) * nz + (z + S.B[2]);
+            bool nz0 = (float)s1.v[at] != 0.0f;
+            for (int c = 0; c < 6 && !nz0; c++) nz0 = (float)ds1[c].v[at] != 0.0f;
+            if (nz0) {
+              lo = std::min(lo, z);
+              hi = std::max(hi, z);
+            }
+          }
+          int cen = lo <= hi ? (lo + hi) / 2 : 0;
+          cen = (cen >= 0 ? cen : cen - 3) / 4 * 4;  // round down to a multiple of 4
+          S.cball[(size_t)(x + S.B[0]) * ny + (y + S.B[1])] = cen;
+        }
+    // column half-widths about the centre, rounded up to even values (the
+    // stored rows are zero beyond the support): half as many unrolled variants
     S.wball.assign((size_t)nx * ny, -1);
     S.whalf.assign((size_t)nx * ny, -1);
     for (int x = -S.B[0]; x <= S.B[0]; x++)
@@ -451,7 +478,8 @@ static void fill_stencils(SysHost& S, bool decide) {
         for (int z = -S.B[2]; z <= S.B[2]; z++) {
           size_t at = ((size_t)(x + S.B[0]) * ny + (y + S.B[1])) * nz + (z + S.B[2]);
           size_t col = (size_t)(x + S.B[0]) * ny + (y + S.B[1]);
-          if ((float)s1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], std::abs(z) + (std::abs(z) & 1));
+          const int zc = std::abs(z - S.cball[col]);
+          if ((float)s1.v[at] != 0.0f) S.wball[col] = std::max(S.wball[col], zc + (zc & 1));
           // half-space weights: C'_d = C'_-d, so sum_d ds_d C'_d = ds_0 C'_0 + 2 sum_(d in half) ds_d C'_d
           bool half = x > 0 || (x == 0 && y > 0) || (x == 0 && y == 0 && z > 0);
           bool zero = x == 0 && y == 0 && z == 0;
@@ -462,7 +490,7 @@ static void fill_stencils(SysHost& S, bool decide) {
             S.dsh[(size_t)c * nx * ny * nz + at] = v;
             if (v != 0.0f) any = true;
           }
-          if (S.prefilter) {
+          if (S.prefilter && !S.tri) {
             // raw samples factor: ds_ab(n) = g(n) v_a v_b with g = k_1'(|v|)/|v|, v = h_1 o n
             const double vx = S.h1[0] * x, vy = S.h1[1] * y, vz = S.h1[2] * z;
             const double rr = std::sqrt(vx * vx + vy * vy + vz * vz);
@@ -470,8 +498,18 @@ static void fill_stencils(SysHost& S, bool decide) {
             S.fsh[at] = g;
             any = g != 0.0f;
           }
-          if (any) S.whalf[col] = std::max(S.whalf[col], std::abs(z) + (std::abs(z) & 1));
+          if (any) S.whalf[col] = std::max(S.whalf[col], zc + (zc & 1));
         }
+    // z halo of the padded grid and of the stored rows: every shifted window
+    // (centre +- the 4-rounded half-width) must stay inside it
+    S.hzb = (S.B[2] + 3) & ~3;
+    S.wmax = 0;
+    for (size_t col = 0; col < S.cball.size(); col++) {
+      const int w = std::max(S.wball[col], S.whalf[col]);
+      if (w < 0) continue;
+      S.wmax = std::max(S.wmax, w);
+      if (S.tri) S.hzb = std::max(S.hzb, (std::abs(S.cball[col]) + ((w + 3) & ~3) + 3) & ~3);
+    }
   }
 }
 
@@ -636,7 +674,7 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
       S.S[d] = std::max(0, (int)std::ceil(2.0 * S.a * S.M[d] * std::sqrt(c2)) - 1);
     }
     S.R[d] = S.S[d] + S.hw;
-    S.prefilter = (S.p == 4 && S.qi_mode == 0 && !S.tri);
+    S.prefilter = (S.p == 4 && S.qi_mode == 0);
     S.B[d] = S.prefilter ? S.S[d] : S.R[d];
     if (S.pbc[d]) {
       // periodic axis: cells aligned with the grid, k = 2^j level-1 intervals
@@ -658,6 +696,11 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
     S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
   }
   fill_stencils(S, true);
+  if (S.has_ball && S.wmax > kBallRmax) {
+    // a tilted cell whose shifted columns are wider than the compiled ball kernels
+    S.allow_ball = false;
+    fill_stencils(S, true);
+  }
   // scalar coefficients
   softening_coeffs(S.p, S.gc);
   {
@@ -687,35 +730,47 @@ void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>&
       // column layout read by the ball kernels: for each (dx, dy) a row of
       // kSK(hz) floats with dz = -hz .. hz at [0, 2hz]; virial weights [dx][6][dy][row]
       const int nx = 2 * S.B[0] + 1, ny = 2 * S.B[1] + 1, nz = 2 * S.B[2] + 1;
-      const int hz = (S.B[2] + 3) & ~3, SK = kSK(hz);
+      const int hz = S.hzb, SK = kSK(hz);
+      // row index of sample z of column (x, y): z about the column's centre (entries
+      // outside the row are zero by construction of hzb)
+      auto rowpos = [&](int x, int y, int z) { return z - S.B[2] - S.cball[(size_t)x * ny + y] + hz; };
+      auto inrow = [&](int r) { return r >= 0 && r <= 2 * hz; };
+      const bool fact = S.prefilter && !any_tri;
       while (kp.size() % 4) kp.push_back(0.f);
       kball_off = (long long)kp.size();
       kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
       for (int x = 0; x < nx; x++)
         for (int y = 0; y < ny; y++)
-          for (int z = 0; z < nz; z++)
-            kp[kball_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.sball[((size_t)x * ny + y) * nz + z];
+          for (int z = 0; z < nz; z++) {
+            const int r = rowpos(x, y, z);
+            if (inrow(r)) kp[kball_off + ((size_t)x * ny + y) * SK + r] = S.sball[((size_t)x * ny + y) * nz + z];
+          }
       dkh_off = (long long)kp.size();
-      if (S.prefilter) {
+      if (fact) {
         // factorized virial weights g(n), one array [dx][dy][row]
         kp.resize(kp.size() + (size_t)nx * ny * SK, 0.f);
         for (int x = 0; x < nx; x++)
           for (int y = 0; y < ny; y++)
             for (int z = 0; z < nz; z++)
-              kp[dkh_off + ((size_t)x * ny + y) * SK + (z - S.B[2] + hz)] = S.fsh[((size_t)x * ny + y) * nz + z];
+              kp[dkh_off + ((size_t)x * ny + y) * SK + rowpos(x, y, z)] = S.fsh[((size_t)x * ny + y) * nz + z];
       } else {
         kp.resize(kp.size() + (size_t)nx * 6 * ny * SK, 0.f);
         for (int x = 0; x < nx; x++)
           for (int c = 0; c < 6; c++)
             for (int y = 0; y < ny; y++)
-              for (int z = 0; z < nz; z++)
-                kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + (z - S.B[2] + hz)] =
-                    S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
+              for (int z = 0; z < nz; z++) {
+                const int r = rowpos(x, y, z);
+                if (inrow(r))
+                  kp[dkh_off + (((size_t)x * 6 + c) * ny + y) * SK + r] =
+                      S.dsh[(size_t)c * nx * ny * nz + ((size_t)x * ny + y) * nz + z];
+              }
       }
       wb_off = (long long)wp.size();
       wp.insert(wp.end(), S.wball.begin(), S.wball.end());
       wh_off = (long long)wp.size();
       wp.insert(wp.end(), S.whalf.begin(), S.whalf.end());
+      S.cb_off = (long long)wp.size();
+      wp.insert(wp.end(), S.cball.begin(), S.cball.end());
     }
     S.kball_off = kball_off;
     S.dkh_off = dkh_off;
@@ -729,6 +784,7 @@ void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>&
         L.dk_off = dkh_off;
         L.w_off = wb_off;
         L.wh_off = wh_off;
+        L.c_off = S.cb_off;
       } else {
         while (kp.size() % 4) kp.push_back(0.f);
         L.k_off = (long long)kp.size();
@@ -851,7 +907,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       if (L.kind == 0) {
         // halo-padded copy of q~^l read by the ball kernels: halos R_x, R_y and
         // hz = R_z rounded up to 4 floats; y and z extents rounded up to whole tiles
-        L.hz = (L.R[2] + 3) & ~3;
+        L.hz = S.hzb;
         L.pn[0] = L.n[0] + 2 * L.R[0];
         L.pn[1] = (int)align_up(L.n[1], kBallTY) + 2 * L.R[1];
         L.pn[2] = (int)align_up(L.n[2], kBallTZ) + 2 * L.hz;
@@ -892,7 +948,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
         for (int x = 0; x < L.n[0]; x++)
           for (int y = 0; y < L.n[1]; y += kBallTY)
             for (int z = 0; z < L.n[2]; z += kBallTZ) ball_items.push_back({li, x, y, z});
-        rmax = std::max(rmax, L.R[2] + (L.R[2] & 1));  // column half-widths are even
+        rmax = std::max(rmax, std::max(L.R[2] + (L.R[2] & 1), S.wmax));  // column half-widths are even
         ryz[0] = std::max(ryz[0], L.R[1]);
         ryz[1] = std::max(ryz[1], L.hz);
         for (int x = 0; x < L.pn[0]; x += kPadTX)

@@ -46,9 +46,13 @@ struct SysHost {
   std::vector<double> kball, dk1;    // K^1 and its 6 strain derivatives, dense on [-R, R]^3 (host queries)
   std::vector<float> sball, dsh;     // ball-kernel stencil on [-B, B]^3 and half-space virial weights (6x)
   std::vector<float> fsh;            // p = 4: factorized half-space virial weights g = k_1'(|v|)/|v|
-  std::vector<int> wball, whalf;     // column half-widths of sball / dsh, -1 = empty column
+  std::vector<int> wball, whalf;     // column half-widths of sball / dsh about cball, -1 = empty column
+  std::vector<int> cball;            // column centres (multiples of 4; zero for rectangular cells)
+  int hzb = 0;                       // z halo of the ball levels' padded grids and stored rows
+  int wmax = 0;                      // widest ball column (half-width about its centre)
+  bool allow_ball = true;            // false: every level a dense box
   // offsets of this system's ball stencil, virial weights and column tables in the device pools
-  long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1;
+  long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1, cb_off = -1;
 };
 
 int plan_system(const msm_params& P, SysHost& S, std::string* err);

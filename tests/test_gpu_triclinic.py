@@ -98,3 +98,41 @@ def test_tilted_cell_field_and_refusals():
         plan.force_vjp(torch.zeros((len(q), 3), device=DEV))
     with pytest.raises(L.MsmError):
         plan.set_cell(A)
+
+
+def test_batch_mixing_tilted_and_rectangular_cells():
+    # one batch with tilted and rectangular cells: every system against the oracle
+    import dataclasses
+
+    import oracle as O
+    from paper_2510_05961_gb300 import Batch
+    from paper_2510_05961_gb300 import workloads as W
+    systems, refs = [], []
+    for k, (kind, n, seed) in enumerate([("sheared", 1500, 61), ("hexagonal", 900, 62), (None, 1200, 63),
+                                         ("monoclinic", 700, 64)]):
+        if kind is None:
+            w = W.random_box(n, seed=seed, h=2.0, a=6.0)
+            w = dataclasses.replace(w, grid_override=(16, 16, 16), h=0.0)
+            A = np.diag(w.cell)
+            pos, q = w.pos, w.q
+        else:
+            A, pos, q = tilted(kind, n, seed)
+            w = W.Workload(name=kind, pos=pos, q=q, cell=tuple(A.reshape(9)), pbc=(1, 1, 1), h=0.0, a=6.0, p=4,
+                           grid_override=(16, 16, 16))
+        systems.append(w)
+        P = O.make_plan(A, (1, 1, 1), 0, 6.0, 4, grid_override=(16, 16, 16))
+        refs.append(O.msm(P, pos.astype(np.float64), q.astype(np.float64), forces=True, virial=True))
+    batch = Batch(systems, device=DEV)
+    tp = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(DEV)
+    tq = torch.from_numpy(np.concatenate([s.q for s in systems])).to(DEV)
+    E, phi, F = batch.forward(tp, tq, forces=True, virial=True)
+    _, _, Wb = batch.backward(torch.ones(len(systems), dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    E, F, Wb = E.cpu().numpy(), F.cpu().numpy(), Wb.cpu().numpy()
+    off = 0
+    for s, (w, r) in enumerate(zip(systems, refs)):
+        assert abs(E[s] - r["E"]) <= E_TOL * abs(r["E"]) + 1e-7 * 0.5 * float(np.abs(w.q * r["phi"]).sum())
+        assert rel_rms(F[off:off + w.n], r["F"]) <= F_TOL
+        assert np.abs(Wb[s] - r["W"]).max() <= F_TOL * np.abs(r["W"]).max()
+        off += w.n
