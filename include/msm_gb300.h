@@ -65,8 +65,10 @@ typedef struct msm_batch_s* msm_batch;
  *                 Sec. 3.2.2's transform to the unit cube: grids in the
  *                 fractional coordinates s = A^-T r) need pbc 1, 1, 1; L below
  *                 is then the length of each cell vector, the stencils follow
- *                 the cell's metric and every level uses dense boxes.
- *                 msm_force_vjp and msm_plan_set_cell refuse tilted cells.
+ *                 the cell's metric (ball kernels with shifted column
+ *                 centres). A plan built for a tilted cell takes any later
+ *                 right-handed cell in msm_plan_set_cell; a rectangular plan
+ *                 only rectangular ones.
  *  pbc[3]         1 = periodic along that axis, 0 = open.
  *  h              target level-1 grid spacing h_1 (> 0 unless overridden).
  *                 Periodic axes use M = 2^round(log2(L/h)) intervals (all

@@ -224,9 +224,23 @@ __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__
             float vx, dvx, vy, dvy;
             bspline_value_d<P>(mx - u.x, cf, vx, dvx);  // d/du Phi(u - m) = -Phi'(m - u)
             bspline_value_d<P>(my - u.y, cf, vy, dvy);
-            const float px = pu.w * pu.x, py = pu.w * pu.y, pz = pu.w * pu.z;
-            const float A = -(px * dvx * vy * S.inv_h1[0] + py * vx * dvy * S.inv_h1[1]);
-            const float B = pz * vx * vy * S.inv_h1[2];
+            // the dipole in grid units, p_u = J^T p (J = A^-1 diag(M); diag(1/h_1) for a
+            // rectangular cell): p . grad_r Phi = p_u . grad_u Phi
+            float px = pu.w * pu.x, py = pu.w * pu.y, pz = pu.w * pu.z;
+            if (S.tri) {
+              const float* J = S.Jg;
+              const float ux = J[0] * px + J[3] * py + J[6] * pz, uy = J[1] * px + J[4] * py + J[7] * pz,
+                          uz = J[2] * px + J[5] * py + J[8] * pz;
+              px = ux;
+              py = uy;
+              pz = uz;
+            } else {
+              px *= S.inv_h1[0];
+              py *= S.inv_h1[1];
+              pz *= S.inv_h1[2];
+            }
+            const float A = -(px * dvx * vy + py * vx * dvy);
+            const float B = pz * vx * vy;
             if ((A != 0.f || B != 0.f) && r >= -PAD && r < zlen) {
               float wz[P], dwz[P];
               bspline_weights<P, true>(u.z - fl, wz, dwz);
@@ -415,16 +429,28 @@ __global__ void __launch_bounds__(kChunk) k_interp_hess(const SysDev* __restrict
         gyz = fmaf(w[0][jx] * dw[1][jy], dsz, gyz);
       }
     }
-    const float ax = S.inv_h1[0], ay = S.inv_h1[1], az = S.inv_h1[2];
-    gxx *= ax * ax;
-    gyy *= ay * ay;
-    gzz *= az * az;
-    gxy *= ax * ay;
-    gxz *= ax * az;
-    gyz *= ay * az;
-    hx = gxx * u.x + gxy * u.y + gxz * u.z;
-    hy = gxy * u.x + gyy * u.y + gyz * u.z;
-    hz = gxz * u.x + gyz * u.y + gzz * u.z;
+    if (S.tri) {
+      // grad_r grad_r G = J H_u J^T (J = A^-1 diag(M)): (H u) = J (H_u (J^T u))
+      const float* J = S.Jg;
+      const float vx = J[0] * u.x + J[3] * u.y + J[6] * u.z, vy = J[1] * u.x + J[4] * u.y + J[7] * u.z,
+                  vz = J[2] * u.x + J[5] * u.y + J[8] * u.z;
+      const float wx = gxx * vx + gxy * vy + gxz * vz, wy = gxy * vx + gyy * vy + gyz * vz,
+                  wz = gxz * vx + gyz * vy + gzz * vz;
+      hx = J[0] * wx + J[1] * wy + J[2] * wz;
+      hy = J[3] * wx + J[4] * wy + J[5] * wz;
+      hz = J[6] * wx + J[7] * wy + J[8] * wz;
+    } else {
+      const float ax = S.inv_h1[0], ay = S.inv_h1[1], az = S.inv_h1[2];
+      gxx *= ax * ax;
+      gyy *= ay * ay;
+      gzz *= az * az;
+      gxy *= ax * ay;
+      gxz *= ax * az;
+      gyz *= ay * az;
+      hx = gxx * u.x + gxy * u.y + gxz * u.z;
+      hy = gxy * u.x + gyy * u.y + gyz * u.z;
+      hz = gxz * u.x + gyz * u.y + gzz * u.z;
+    }
   }
   fsr_inout[k] = make_float4(hx, hy, hz, uE);
 }

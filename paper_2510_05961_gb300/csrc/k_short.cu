@@ -278,8 +278,93 @@ __global__ void __launch_bounds__(kChunk) k_short_fvjp(const SysDev* __restrict_
   out[k] = make_float4(hx, hy, hz, psi);
 }
 
+// k_short_fvjp over the candidates of k_short_tri (tilted cells)
+template <int P>
+__global__ void __launch_bounds__(kChunk) k_short_fvjp_tri(const SysDev* __restrict__ sys,
+                                                           const AtomItem* __restrict__ items,
+                                                           const int* __restrict__ cell_start,
+                                                           const int* __restrict__ scell,
+                                                           const float4* __restrict__ xq, const float4* __restrict__ uq,
+                                                           const float4* __restrict__ us, float4* __restrict__ out) {
+  const AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int local = it.start + (int)threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  const int k = S.atom_off + local;
+  const float4 xi = xq[k];
+  const float4 ui = us[k];
+  const float siz = uq[k].z / S.Mf[2];
+  const int cell = scell[k];
+  const int Cx = S.C[0], Cy = S.C[1], Cz = S.C[2];
+  const int ci[3] = {cell / (Cy * Cz), (cell / Cz) % Cy, cell % Cz};
+  float gdc[P - 1];
+#pragma unroll
+  for (int t = 0; t < P - 1; t++) gdc[t] = S.gdca[t];
+  const float a2 = S.a2, inv_a2 = S.inv_a2;
+  const double ta[3] = {S.Ad[0] / Cx, S.Ad[1] / Cx, S.Ad[2] / Cx}, tb[3] = {S.Ad[3] / Cy, S.Ad[4] / Cy, S.Ad[5] / Cy};
+  const float rz = S.reach[2] + 2e-4f / Cz;
+  const int zlo = (int)floorf((siz - rz) * Cz), zhi = (int)floorf((siz + rz) * Cz);
+  float psi = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+  for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
+    const int ux = ci[0] + ox;
+    const int wx = ux - floordiv_s(ux, Cx) * Cx;
+    for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
+      const int uy = ci[1] + oy;
+      const int wy = uy - floordiv_s(uy, Cy) * Cy;
+      const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
+      double bxy[3];
+      for (int e = 0; e < 3; e++) bxy[e] = ox * ta[e] + oy * tb[e];
+      int uz = zlo;
+      while (uz <= zhi) {
+        const int kz = floordiv_s(uz, Cz);
+        const int wz = uz - kz * Cz;
+        const int wend = min(Cz - 1, wz + (zhi - uz));
+        const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+        const float bx = (float)(bxy[0] + kz * S.Ad[6] - (double)xi.x);
+        const float by = (float)(bxy[1] + kz * S.Ad[7] - (double)xi.y);
+        const float bz = (float)(bxy[2] + kz * S.Ad[8] - (double)xi.z);
+        for (int j = jb; j < je; j++) {
+          const float4 xj = xq[j];
+          const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < a2 && r2 > 0.f) {
+            const float4 uj = us[j];
+            const float rinv = rsqrtf(r2);
+            const float rinv2 = rinv * rinv;
+            const float sg = 1.0f - r2 * inv_a2;
+            float p1 = gdc[P - 2], dp1 = (float)(P - 2) * gdc[P - 2];
+#pragma unroll
+            for (int c = P - 3; c >= 0; c--) {
+              p1 = fmaf(p1, sg, gdc[c]);
+              if (c >= 1) dp1 = fmaf(dp1, sg, (float)c * gdc[c]);
+            }
+            const float f1 = fmaf(-rinv2, rinv, p1);
+            const float f2 = fmaf(3.0f * rinv2 * rinv2, rinv, -2.0f * inv_a2 * dp1);
+            psi = fmaf(f1 * uj.w, uj.x * dx + uj.y * dy + uj.z * dz, psi);
+            const float wxv = ui.x - uj.x, wyv = ui.y - uj.y, wzv = ui.z - uj.z;
+            const float dw = f2 * (dx * wxv + dy * wyv + dz * wzv);
+            hx = fmaf(uj.w, fmaf(dw, dx, f1 * wxv), hx);
+            hy = fmaf(uj.w, fmaf(dw, dy, f1 * wyv), hy);
+            hz = fmaf(uj.w, fmaf(dw, dz, f1 * wzv), hz);
+          }
+        }
+        uz += wend - wz + 1;
+      }
+    }
+  }
+  out[k] = make_float4(hx, hy, hz, psi);
+}
+
 void launch_short_fvjp(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
-                       float4* out, cudaStream_t s, int p) {
+                       float4* out, cudaStream_t s, int p, bool tilted) {
+  if (tilted) {
+    switch (p) {
+      case 4: k_short_fvjp_tri<4><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.uq, us, out); break;
+      case 6: k_short_fvjp_tri<6><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.uq, us, out); break;
+      default: k_short_fvjp_tri<8><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, w.uq, us, out); break;
+    }
+    return;
+  }
   switch (p) {
     case 4: k_short_fvjp<4><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, us, out); break;
     case 6: k_short_fvjp<6><<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_start, w.scell, w.xq, us, out); break;

@@ -413,7 +413,6 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
 // Consumes the workspace: a later msm_backward needs a new msm_forward.
 static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* dpos, cudaStream_t s) {
   if (!E.have_fwd || ws != E.last_ws) return set_err(MSM_ERR_NO_FORWARD, "msm_force_vjp needs a prior msm_forward on this workspace");
-  if (E.any_tri) return set_err(MSM_ERR_UNSUPPORTED, "msm_force_vjp: tilted cells are not supported");
   if (E.last_n > 0 && !u) return set_err(MSM_ERR_INVALID_ARG, "u must not be NULL");
   Work w = E.resolve(ws);
   Tables t = E.tables();
@@ -426,7 +425,7 @@ static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* 
   if (E.last_n > 0) {
     launch_sort_u(w, t, E.d_atom_items, nai, u, w.vjp_u, s);
     launch_interp_hess(w, t, E.d_atom_items, nai, w.vjp_u, s, E.p);  // f_sr <- ((H u)_grid, u . E)
-    launch_short_fvjp(w, t, E.d_atom_items, nai, w.vjp_u, w.vjp_h, s, E.p);
+    launch_short_fvjp(w, t, E.d_atom_items, nai, w.vjp_u, w.vjp_h, s, E.p, E.any_tri);
     launch_anterp_dipole(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz, w.vjp_u);
     for (int l = 1; l < E.maxcomp; l++) {
       int a = E.restrict_off[l - 1], b = E.restrict_off[l];
@@ -461,11 +460,19 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
   if (!plan || !cell) return set_err(MSM_ERR_INVALID_ARG, "plan and cell must not be NULL");
   Engine& E = plan->eng;
   SysHost& S = E.sys[0];
-  if (S.tri) return set_err(MSM_ERR_UNSUPPORTED, "msm_plan_set_cell: tilted cells are not supported");
-  for (int i = 0; i < 9; i++) {
+  for (int i = 0; i < 9; i++)
     if (!std::isfinite(cell[i])) return set_err(MSM_ERR_INVALID_ARG, "cell has a non-finite entry");
-    if (i % 4 != 0 && cell[i] != 0.0) return set_err(MSM_ERR_UNSUPPORTED, "only orthorhombic (diagonal) cells are supported");
+  if (S.tri) {
+    // a plan built for a tilted cell takes any right-handed cell within its capacity
+    std::string err;
+    int rc = E.set_cell_tilted(cell, (cudaStream_t)stream, &err);
+    if (rc) return set_err(rc, "msm_plan_set_cell: " + err);
+    E.have_fwd = false;
+    return check_launch("msm_plan_set_cell");
   }
+  for (int i = 0; i < 9; i++)
+    if (i % 4 != 0 && cell[i] != 0.0)
+      return set_err(MSM_ERR_UNSUPPORTED, "a plan built for a rectangular cell takes rectangular cells only");
   for (int d = 0; d < 3; d++)
     if (!(cell[4 * d] > 0.0)) return set_err(MSM_ERR_INVALID_ARG, "cell lengths must be > 0");
   double h1[3];

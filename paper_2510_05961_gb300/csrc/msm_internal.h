@@ -166,7 +166,7 @@ void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nit
 void launch_sort_u(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float* u, float4* us,
                    cudaStream_t s);
 void launch_short_fvjp(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
-                       float4* out, cudaStream_t s, int p);
+                       float4* out, cudaStream_t s, int p, bool tilted);
 void launch_interp_hess(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* us,
                         cudaStream_t s, int p);
 void launch_anterp_dipole(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p,

@@ -1106,10 +1106,79 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   return MSM_OK;
 }
 
-int Engine::set_cell_host(const double Lnew[3], cudaStream_t s, std::string* err) {
+// A new cell for a single-system plan with a tilted cell (msm_plan_set_cell):
+// the cell geometry, the SysDev fields that follow from it and the stencils
+// (host rebuild with the plan's sizes). The ball columns' centres may move;
+// the new halo and widths must fit the plan's (MSM_ERR_CAPACITY otherwise).
+int Engine::set_cell_tilted(const double* cell, cudaStream_t s, std::string* err) {
+  SysHost& S = sys[0];
+  double A[9], Ai[9];
+  for (int i = 0; i < 9; i++) A[i] = cell[i];
+  const double det = inv3(A, Ai);
+  if (!(det > 0.0)) return fail(err, MSM_ERR_INVALID_ARG, "cell rows must form a right-handed basis");
+  int Snew[3];
+  for (int d = 0; d < 3; d++) {
+    double c2 = 0.0;
+    for (int e = 0; e < 3; e++) c2 += Ai[3 * e + d] * Ai[3 * e + d];
+    Snew[d] = std::max(0, (int)std::ceil(2.0 * S.a * S.M[d] * std::sqrt(c2)) - 1);
+    if (Snew[d] > S.R[d] - S.hw)
+      return fail(err, MSM_ERR_CAPACITY, "cell compressed or tilted beyond the plan's stencil radius");
+  }
+  const SysHost keep = S;
+  for (int i = 0; i < 9; i++) {
+    S.A[i] = A[i];
+    S.Ainv[i] = Ai[i];
+  }
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) S.Tinv[3 * i + j] = S.Ainv[3 * j + i];
+  for (int d = 0; d < 3; d++) {
+    const double* u = S.A + 3 * ((d + 1) % 3);
+    const double* v = S.A + 3 * ((d + 2) % 3);
+    const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    S.wplane[d] = det / std::sqrt(cx * cx + cy * cy + cz * cz);
+    S.L[d] = std::sqrt(A[3 * d] * A[3 * d] + A[3 * d + 1] * A[3 * d + 1] + A[3 * d + 2] * A[3 * d + 2]);
+    S.h1[d] = S.L[d] / S.M[d];
+    S.S[d] = Snew[d];
+    S.edge[d] = S.wplane[d] / S.C[d];
+    S.nnbr[d] = (int)std::ceil(S.a / S.edge[d]);
+  }
+  const int hz_old = keep.hzb, rmax_old = rmax;
+  fill_stencils(S, false);
+  if (S.has_ball && (S.hzb > hz_old || S.wmax > rmax_old)) {
+    S = keep;
+    fill_stencils(S, false);
+    return fail(err, MSM_ERR_CAPACITY, "the new cell's stencil columns do not fit the plan's halo");
+  }
+  S.hzb = hz_old;  // the stored rows keep the plan's halo
+  SysDev& D = hsys[0];
+  for (int d = 0; d < 3; d++) {
+    D.Ld[d] = S.L[d];
+    D.edged[d] = S.edge[d];
+    D.edge[d] = (float)S.edge[d];
+    D.invL[d] = (float)(1.0 / S.L[d]);
+    D.inv_h1[d] = (float)(1.0 / S.h1[d]);
+    D.Lf[d] = (float)S.L[d];
+    D.h1f[d] = (float)S.h1[d];
+    D.nnbr[d] = S.nnbr[d];
+    D.reach[d] = (float)(S.a / S.wplane[d]);
+  }
+  for (int k = 0; k < 9; k++) {
+    D.Tf[k] = (float)S.Tinv[k];
+    D.Ad[k] = S.A[k];
+    D.Td[k] = S.Tinv[k];
+  }
+  for (int e = 0; e < 3; e++)
+    for (int d = 0; d < 3; d++) D.Jg[3 * e + d] = (float)(S.Ainv[3 * e + d] * S.M[d]);
+  int rc = set_cell_host(S.L, s, err, false);
+  if (rc) return rc;
+  launch_set_sys(d_sys, D, s);
+  return MSM_OK;
+}
+
+int Engine::set_cell_host(const double Lnew[3], cudaStream_t s, std::string* err, bool refill) {
   SysHost& S = sys[0];
   (void)Lnew;  // the caller has set S.L and S.h1
-  fill_stencils(S, false);
+  if (refill) fill_stencils(S, false);
   std::vector<int> lev0_of(1, hsys[0].lev0);
   std::vector<float> kp;
   std::vector<int> wp;

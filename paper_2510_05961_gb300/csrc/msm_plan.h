@@ -132,7 +132,8 @@ struct Engine {
   void assemble_pools(const std::vector<int>& lev0_of, std::vector<float>& kp, std::vector<int>& wp);
   // new cell for a single-system plan (msm_plan_set_cell), host path: stencils
   // rebuilt on the host and copied through pinned staging buffers
-  int set_cell_host(const double L[3], cudaStream_t s, std::string* err);
+  int set_cell_host(const double L[3], cudaStream_t s, std::string* err, bool refill = true);
+  int set_cell_tilted(const double* cell, cudaStream_t s, std::string* err);
   float* h_kstage = nullptr;
   int* h_wstage = nullptr;
   size_t kpool_n = 0, wpool_n = 0;

@@ -84,20 +84,57 @@ def test_tilted_cell_matches_oracle(kind, n, seed, p, a, M):
     assert np.abs(Wv.cpu().numpy() - Wr).max() <= F_TOL * np.abs(Wr).max()
 
 
-def test_tilted_cell_field_and_refusals():
+def test_tilted_cell_field_and_force_gradients():
+    # msm_field and the force vector-Jacobian product (L = sum u . F) in a tilted cell:
+    # dL/dq = -D_u phi and dL/dr = D_u F, central differences of the FP64 oracle along u
     import oracle as O
-    from paper_2510_05961_gb300 import _lib as L
+    from paper_2510_05961_gb300 import msm_outputs
     A, pos, q = tilted("sheared", 3000, 55)
     plan = Plan(A.reshape(9), (1, 1, 1), 0.0, 6.0, 4, 0, (16, 16, 16), max_atoms=len(q), device=DEV)
     tp, tq = torch.from_numpy(pos).to(DEV), torch.from_numpy(q).to(DEV)
     plan.forward(tp, tq, forces=True)
     P = O.make_plan(A, (1, 1, 1), 0, 6.0, 4, grid_override=(16, 16, 16))
-    ref = O.msm(P, pos.astype(np.float64), q.astype(np.float64), forces=True, virial=False)
-    assert rel_rms(plan.field().cpu().numpy(), ref["F"] / q.astype(np.float64)[:, None]) <= F_TOL
-    with pytest.raises(L.MsmError):
-        plan.force_vjp(torch.zeros((len(q), 3), device=DEV))
-    with pytest.raises(L.MsmError):
-        plan.set_cell(A)
+    pd, qd = pos.astype(np.float64), q.astype(np.float64)
+    ref = O.msm(P, pd, qd, forces=True, virial=False)
+    assert rel_rms(plan.field().cpu().numpy(), ref["F"] / qd[:, None]) <= F_TOL
+    u = np.random.default_rng(56).normal(size=pos.shape)
+    x = tp.clone().requires_grad_(True)
+    y = tq.clone().requires_grad_(True)
+    E, phi, F = msm_outputs(x, y, plan)
+    (torch.from_numpy(u.astype(np.float32)).to(DEV) * F).sum().backward()
+    torch.cuda.synchronize()
+    eps = 1e-4
+    rp = O.msm(P, pd + eps * u, qd, forces=True, virial=False)
+    rm = O.msm(P, pd - eps * u, qd, forces=True, virial=False)
+    assert rel_rms(y.grad.cpu().numpy(), -(rp["phi"] - rm["phi"]) / (2 * eps)) <= F_TOL
+    assert rel_rms(x.grad.cpu().numpy(), (rp["F"] - rm["F"]) / (2 * eps)) <= F_TOL
+
+
+def test_tilted_cell_dynamic_cell():
+    # a plan built for a tilted cell takes later cells (strained, re-tilted, rectangular) within its
+    # capacity; each against the oracle planned for that cell with the same grid counts
+    import oracle as O
+    from paper_2510_05961_gb300 import _lib as L
+    A, pos, q = tilted("sheared", 3000, 57)
+    plan = Plan((A * 0.96).reshape(9), (1, 1, 1), 0.0, 6.0, 4, 0, (16, 16, 16), max_atoms=len(q), device=DEV)
+    frac = pos.astype(np.float64) @ np.linalg.inv(A)
+    for B in (A, A @ (np.eye(3) + np.array([[0.02, 0.01, 0], [0, -0.01, 0.02], [0, 0, 0.03]])).T,
+              np.diag(np.diag(A)) * 1.0):
+        plan.set_cell(B)
+        pb = (frac @ B).astype(np.float32)
+        tp, tq = torch.from_numpy(pb).to(DEV), torch.from_numpy(q).to(DEV)
+        E, phi, F = plan.forward(tp, tq, forces=True, virial=True)
+        gp, gq, Wv = plan.backward(torch.ones(1, dtype=torch.float64, device=DEV))
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        P = O.make_plan(B, (1, 1, 1), 0, 6.0, 4, grid_override=(16, 16, 16))
+        ref = O.msm(P, pb.astype(np.float64), q.astype(np.float64), forces=True, virial=True)
+        assert abs(float(E.cpu()[0]) - ref["E"]) <= E_TOL * abs(ref["E"])
+        assert rel_rms(F.cpu().numpy(), ref["F"]) <= F_TOL
+        assert np.abs(Wv.cpu().numpy() - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max()
+    with pytest.raises(L.MsmError) as e:
+        plan.set_cell(A * 0.8)
+    assert e.value.code == L.MSM_ERR_CAPACITY
 
 
 def test_batch_mixing_tilted_and_rectangular_cells():
