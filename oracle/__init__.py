@@ -384,6 +384,27 @@ def ewald2d(Lx, Ly, pos, q, alpha=0.0):
     return float(E[0]), phi
 
 
+def ewald1d(L, pos, q, alpha=0.0, axis=2):
+    """1-D Ewald sum of a neutral wire periodic along `axis` with period L (the
+    other two axes open): (E, phi)."""
+    pos, q = _d(pos), _d(q)
+    if axis != 2:
+        order = [d for d in range(3) if d != axis] + [axis]
+        pos = np.ascontiguousarray(pos[:, order])
+    n = pos.shape[0]
+    E = np.zeros(1)
+    phi = np.zeros(n)
+    lib().or_ewald1d(C.c_double(L), n, _ptr(pos), _ptr(q), C.c_double(alpha), _ptr(E), _ptr(phi))
+    return float(E[0]), phi
+
+
+def wire_top(p, a, nlev, L, rho):
+    """Top-level kernel of a wire at the transverse distance rho (k_L summed over the 1-D lattice)."""
+    f = lib().or_wire_top
+    f.restype = C.c_double
+    return float(f(int(p), C.c_double(a), int(nlev), C.c_double(L), C.c_double(rho)))
+
+
 def slab_top(p, a, nlev, Lx, Ly, z):
     """Top-level kernel of a slab at the z offset z (k_L summed over the 2-D lattice)."""
     f = lib().or_slab_top

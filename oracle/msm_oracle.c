@@ -43,7 +43,7 @@ typedef struct {
   /* derived by or_plan_init */
   int nlev;             /* number of grid levels L (top level included) */
   int ncomp;            /* levels whose grids are evaluated (nlev, or nlev-1 when the top is dropped) */
-  int top_kept;         /* 1 when the top level's stencil is applied (all axes open, or a slab) */
+  int top_kept;         /* 1 when the top level's stencil is applied (all axes open, a slab or a wire) */
   int M[3];             /* level-1 interval counts */
   double h1[3];         /* level-1 spacings L/M */
   int lo[OR_MAXLEV][3]; /* first grid index per level (index 0 = level 1) */
@@ -238,19 +238,211 @@ double or_slab_top(int p, double a, int nlev, double Lx, double Ly, double z) {
   return v;
 }
 
-/* Strain derivatives of the slab top-level kernel at the z offset z, which =
- * 1..6 for eps_xx, yy, zz, xy, xz, yz: d/d eps of or_slab_top with the lattice
- * and the offset strained, by central differences (step 1e-5; the kernel is
- * smooth in the cell). xy, xz and yz vanish: the lattice is symmetric under
- * x -> -x and y -> -y. */
-double or_slab_top_deps(int p, double a, int nlev, double Lx, double Ly, double z, int which) {
-  const double e = 1e-5;
-  switch (which) {
-    case 1: return (or_slab_top(p, a, nlev, Lx * (1 + e), Ly, z) - or_slab_top(p, a, nlev, Lx * (1 - e), Ly, z)) / (2 * e);
-    case 2: return (or_slab_top(p, a, nlev, Lx, Ly * (1 + e), z) - or_slab_top(p, a, nlev, Lx, Ly * (1 - e), z)) / (2 * e);
-    case 3: return (or_slab_top(p, a, nlev, Lx, Ly, z * (1 + e)) - or_slab_top(p, a, nlev, Lx, Ly, z * (1 - e))) / (2 * e);
-    default: return 0.0;
+/* ------------------------------------------------------------------------ */
+/* Wires (one periodic axis): 1-D Ewald sum and the wire top-level kernel.   */
+/* ------------------------------------------------------------------------ */
+
+#define OR_EULER_GAMMA 0.57721566490153286061
+
+/* n-point Gauss-Legendre rule on [-1, 1]: nodes are the roots of P_n, found by
+ * Newton's method from cos(pi (i - 1/4) / (n + 1/2)); P_n and P_(n-1) from the
+ * three-term recurrence, P_n' = n (x P_n - P_(n-1)) / (x^2 - 1), weights
+ * 2 / ((1 - x^2) P_n'^2). */
+#define OR_GLN 12
+static void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; i++) {
+    double t = cos(OR_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; it++) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; k++) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      double dt = p1 / dp;
+      t -= dt;
+      if (fabs(dt) < 1e-16) break;
+    }
+    x[i] = t;
+    w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
   }
+}
+
+/* Ein(x) = int_0^x (1 - e^-t)/t dt = sum_(k>=1) (-1)^(k+1) x^k / (k k!)
+ * (an entire function; E1(x) = -gamma - ln x + Ein(x)), for 0 <= x < 4. */
+static double ein_series(double x) {
+  double term = x, sum = x;
+  for (int k = 2; k < 200; k++) {
+    term *= -x / k;
+    double add = term / k;
+    sum += add;
+    if (fabs(add) < 1e-18 * fabs(sum)) break;
+  }
+  return sum;
+}
+
+/* E1(x) for x >= 1 by the continued fraction
+ * E1(x) = e^-x / (x + 1 - 1^2/(x + 3 - 2^2/(x + 5 - ...))), modified Lentz. */
+static double e1_cfrac(double x) {
+  const double tiny = 1e-300;
+  double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int k = 1; k < 1000; k++) {
+    double an = -(double)k * k;
+    b += 2.0;
+    d = an * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = 1.0 / d;
+    double del = d * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+/* I(G, rho) = int_0^(alpha^2) u^-1 exp(-u rho^2 - G^2/(4u)) du (G != 0): the
+ * Fourier transform along the wire of erf(alpha r)/r at transverse distance
+ * rho. With u = alpha^2 e^-s it is int_0^inf exp(-alpha^2 rho^2 e^-s - b e^s) ds,
+ * b = G^2/(4 alpha^2), an integrand that dies double-exponentially; the
+ * range is cut where b e^s = 46 and split into panels of width 1/2, each
+ * summed by a 12-point Gauss-Legendre rule. */
+static double wire_fourier(double b, double c2) {
+  if (b >= 46.0) return 0.0;
+  double x[OR_GLN], w[OR_GLN];
+  gauss_legendre(OR_GLN, x, w);
+  const double smax = log(46.0 / b);
+  const int np = (int)ceil(smax / 0.5);
+  const double hw = 0.5 * smax / np;
+  double acc = 0.0;
+  for (int k = 0; k < np; k++) {
+    const double mid = (2 * k + 1) * hw;
+    for (int i = 0; i < OR_GLN; i++) {
+      const double s = mid + hw * x[i];
+      acc += w[i] * exp(-c2 * exp(-s) - b * exp(s));
+    }
+  }
+  return acc * hw;
+}
+
+/* 1-D Ewald sum of 1/r over the lattice n L e_z at the offset (rho, z)
+ * (rho = transverse distance): with the Poisson sum of the erf part along z,
+ *   real space  sum_n erfc(alpha s_n)/s_n,  s_n = |(rho, z + n L)| (n = 0 left
+ *               out if skip0),
+ *   reciprocal  (2/L) sum_(k >= 1) cos(G_k z) I(G_k, rho), G_k = 2 pi k / L,
+ *   G = 0       (1/L) [ln(alpha^2) - Ein(alpha^2 rho^2)]
+ *               (= (1/L) [-gamma - ln(rho^2) - E1(alpha^2 rho^2)] for rho > 0).
+ * The lattice sum diverges logarithmically; the G = 0 integral is cut at
+ * small u and the cut's constant -ln(eps)/L, which depends on neither the
+ * offset nor alpha, is left out (it multiplies the squared total charge and
+ * vanishes for neutral systems). Truncation: real space to s < 7/alpha,
+ * reciprocal space to G^2/(4 alpha^2) < 46. */
+double or_ewald1d_pair(double L, double rho, double z, double alpha, int skip0) {
+  const double rc = 7.0 / alpha;
+  double acc = 0.0;
+  const int nr = (int)ceil((rc + fabs(z)) / L) + 1;
+  for (int n = -nr; n <= nr; n++) {
+    if (skip0 && n == 0) continue;
+    double dz = z + n * L;
+    double s = sqrt(rho * rho + dz * dz);
+    if (s < rc) acc += erfc(alpha * s) / s;
+  }
+  const double c2 = alpha * alpha * rho * rho;
+  double rec = 0.0;
+  for (int k = 1;; k++) {
+    double g = 2.0 * OR_PI * k / L, b = g * g / (4.0 * alpha * alpha);
+    if (b >= 46.0) break;
+    rec += cos(g * z) * wire_fourier(b, c2);
+  }
+  acc += 2.0 / L * rec;
+  double g0;
+  if (c2 < 4.0)
+    g0 = log(alpha * alpha) - ein_series(c2);
+  else
+    g0 = -OR_EULER_GAMMA - log(rho * rho) - e1_cfrac(c2);
+  return acc + g0 / L;
+}
+
+/* 1-D Ewald sum of a neutral wire periodic along z with period L (x, y
+ * open): phi_i = sum_j q_j psi(r_j - r_i) with psi the pair sum above (n = 0
+ * left out for j = i) minus 2 alpha/sqrt(pi) q_i; E = 1/2 sum q phi.
+ * alpha <= 0 picks 6 / L. */
+void or_ewald1d(double L, int n, const double* pos, const double* q, double alpha, double* E, double* phi) {
+  if (alpha <= 0.0) alpha = 6.0 / L;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int i = 0; i < n; i++) {
+    double ph = 0.0;
+    for (int j = 0; j < n; j++) {
+      double dx = pos[3 * j] - pos[3 * i], dy = pos[3 * j + 1] - pos[3 * i + 1], dz = pos[3 * j + 2] - pos[3 * i + 2];
+      dz -= L * floor(dz / L + 0.5);
+      ph += q[j] * or_ewald1d_pair(L, sqrt(dx * dx + dy * dy), dz, alpha, j == i);
+    }
+    phi[i] = ph - 2.0 * alpha / sqrt(OR_PI) * q[i];
+  }
+  double e = 0.0;
+  for (int i = 0; i < n; i++) e += 0.5 * q[i] * phi[i];
+  *E = e;
+}
+
+/* Top-level kernel of a wire (reading of the top level for one periodic axis,
+ * the grid there has one point per period): k_L summed over the 1-D lattice
+ * n L e at the transverse distance rho, without the divergent constant; as
+ * for the slab, the 1/r part is the 1-D Ewald sum and the h_L part a finite
+ * direct sum, with the R = 0 limit -2 alpha/sqrt(pi) + gamma(0)/a_L at rho = 0. */
+double or_wire_top(int p, double a, int nlev, double L, double rho) {
+  const double aL = ldexp(a, nlev - 1), alpha = 6.0 / L;
+  const int zero = rho < 1e-300;
+  double v = or_ewald1d_pair(L, rho, 0.0, alpha, zero);
+  if (zero) v += -2.0 * alpha / sqrt(OR_PI) + or_gamma(p, 0.0) / aL;
+  const int nn = (int)ceil(aL / L) + 1;
+  for (int n = -nn; n <= nn; n++) {
+    if (zero && n == 0) continue;
+    double r = sqrt(rho * rho + (n * L) * (n * L));
+    if (r < aL) v -= 1.0 / r - or_gamma(p, r / aL) / aL;
+  }
+  return v;
+}
+
+/* Top-level kernel of a partially periodic system (one or two periodic
+ * axes) at the sample vector v, the periodic axes' periods Lp[d] (entries of
+ * open axes unused): two periodic axes give the slab kernel at the offset
+ * along the open axis, one the wire kernel at the distance across it. */
+static double lattice_top(const or_plan* P, const double* Lp, const double* v) {
+  int per[3], opn[3], np = 0, no = 0;
+  for (int d = 0; d < 3; d++) {
+    if (P->pbc[d])
+      per[np++] = d;
+    else
+      opn[no++] = d;
+  }
+  if (np == 2) return or_slab_top(P->p, P->a, P->nlev, Lp[per[0]], Lp[per[1]], v[opn[0]]);
+  return or_wire_top(P->p, P->a, P->nlev, Lp[per[0]], sqrt(v[opn[0]] * v[opn[0]] + v[opn[1]] * v[opn[1]]));
+}
+
+/* Strain derivatives (which = 1..6 for eps_xx, yy, zz, xy, xz, yz) of the
+ * lattice-summed top level: d/d eps of lattice_top with the lattice and the
+ * offset strained by (1 + eps E_ab), by central differences (step 1e-5; the
+ * kernel is smooth in the cell). A diagonal strain of a periodic axis scales
+ * its period, of an open axis the offset; a shear that involves a periodic
+ * axis has zero derivative (the lattice sum is even under the mirror of that
+ * axis); a shear of two open axes (wires) moves the offset. */
+static double lattice_top_deps(const or_plan* P, const double* Lp, const double* v, int which) {
+  static const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  const int a = ab[which - 1][0], b = ab[which - 1][1];
+  if (a != b && (P->pbc[a] || P->pbc[b])) return 0.0;
+  const double e = 1e-5;
+  double f[2];
+  for (int k = 0; k < 2; k++) {
+    const double s = k == 0 ? e : -e;
+    double L2[3] = {Lp[0], Lp[1], Lp[2]}, v2[3] = {v[0], v[1], v[2]};
+    if (a == b && P->pbc[a])
+      L2[a] *= 1.0 + s;
+    else
+      v2[a] += s * v[b];
+    f[k] = lattice_top(P, L2, v2);
+  }
+  return (f[0] - f[1]) / (2.0 * e);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -510,9 +702,10 @@ int or_plan_init(or_plan* P) {
     while ((1 << (nl - 1)) < Mper) nl++;
     if (P->levels > 0 && P->levels != nl) return 2;
     P->nlev = nl;
-    if (P->pbc[0] && P->pbc[1] && !P->pbc[2]) {
-      /* slab: the top level (one point along x, y; open along z) is kept,
-       * with k_L summed over the 2-D lattice (or_slab_top) */
+    if (!(P->pbc[0] && P->pbc[1] && P->pbc[2])) {
+      /* slab (two periodic axes) or wire (one): the top level, one point per
+       * period along the periodic axes, is kept, with k_L summed over the
+       * 2-D (or_slab_top) or 1-D (or_wire_top) lattice */
       P->top_kept = 1;
       P->ncomp = nl;
     } else {
@@ -852,7 +1045,7 @@ void or_prolong_add(const or_plan* P, int l, const double* coarse, double* fine)
 /* ------------------------------------------------------------------------ */
 
 /* Offset box of the stencil applied on level l (1-based): d in [lo, lo+sz).
- * Levels below the top: [-R, R] per axis. Top level kept (all axes open, or a slab): the
+ * Levels below the top: [-R, R] per axis. Top level kept (all axes open, a slab or a wire): the
  * full range of grid displacements. Periodic axes are folded onto [0, n_l):
  * on a periodic grid the operator sums every image of an offset. */
 void or_stencil_box(const or_plan* P, int l, int* lo, int* sz) {
@@ -897,7 +1090,8 @@ void or_stencil_build(const or_plan* P, int l, int which, const double* G, doubl
   double hl[3];
   for (int d = 0; d < 3; d++) hl[d] = ldexp(P->h1[d], l - 1);
   int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-  const int slab_top = l == P->nlev && P->pbc[0] && P->pbc[1] && !P->pbc[2];
+  const int npbc = P->pbc[0] + P->pbc[1] + P->pbc[2];
+  const int lat_top = l == P->nlev && npbc >= 1 && npbc <= 2;
   size_t ns = (size_t)ssz[0] * ssz[1] * ssz[2];
   double* smp = (double*)malloc(sizeof(double) * ns);
 #pragma omp parallel for schedule(static)
@@ -917,13 +1111,13 @@ void or_stencil_build(const or_plan* P, int l, int which, const double* G, doubl
           v[a] = G ? G[3 * a + 0] * g[0] + G[3 * a + 1] * g[1] + G[3 * a + 2] * g[2] : g[a];
         double rr = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         double val;
-        if (slab_top) {
-          /* x, y offsets are lattice vectors here: the lattice sum depends on z only
-           * (a strain G, if given, is taken diagonal) */
-          double gx = G ? G[0] : 1.0, gy = G ? G[4] : 1.0;
-          double lx = P->L[0] * gx, ly = P->L[1] * gy;
-          val = which == 0 ? or_slab_top(p, P->a, P->nlev, lx, ly, v[2])
-                           : or_slab_top_deps(p, P->a, P->nlev, lx, ly, v[2], which);
+        if (lat_top) {
+          /* offsets along the periodic axes are lattice vectors here: the
+           * lattice sum depends on the open components only (a strain G, if
+           * given, scales the periods by its diagonal) */
+          double Lp[3];
+          for (int d = 0; d < 3; d++) Lp[d] = P->L[d] * (G ? G[4 * d] : 1.0);
+          val = which == 0 ? lattice_top(P, Lp, v) : lattice_top_deps(P, Lp, v, which);
         } else if (which == 0) {
           val = or_kl(p, P->a, P->nlev, l, rr);
         } else {

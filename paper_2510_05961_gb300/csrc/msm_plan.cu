@@ -12,7 +12,9 @@
 #include "msm_plan.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <cstring>
 
 namespace msm {
@@ -117,17 +119,130 @@ static double slab_top_kernel(const SysHost& S, double Lx, double Ly, double z) 
   return v;
 }
 
-// strain derivatives (comp 1..6 = xx, yy, zz, xy, xz, yz) by central
-// differences of the lattice sum with the lattice or the offset strained;
-// the shear components vanish by the x -> -x, y -> -y symmetry of the lattice
-static double slab_top_deps(const SysHost& S, double z, int comp) {
-  const double e = 1e-5, Lx = S.L[0], Ly = S.L[1];
-  switch (comp) {
-    case 1: return (slab_top_kernel(S, Lx * (1 + e), Ly, z) - slab_top_kernel(S, Lx * (1 - e), Ly, z)) / (2 * e);
-    case 2: return (slab_top_kernel(S, Lx, Ly * (1 + e), z) - slab_top_kernel(S, Lx, Ly * (1 - e), z)) / (2 * e);
-    case 3: return (slab_top_kernel(S, Lx, Ly, z * (1 + e)) - slab_top_kernel(S, Lx, Ly, z * (1 - e))) / (2 * e);
-    default: return 0.0;
+// ------------------------------------------------------------------ wire top level
+// A wire (one periodic axis, period Lw; the other two open) keeps its top
+// level as well, one point per period along the wire: k_L summed over the
+// 1-D lattice n Lw e at the transverse distance rho. The 1/r tail diverges
+// logarithmically, by a constant that multiplies the squared total charge
+// and is left out. Split:
+//   sum_n k_L = sum_n [erfc(al s_n)/s_n - h_L(s_n)] + (2/Lw) sum_(k >= 1) F(G_k, rho)
+//               + (1/Lw) [-gamma_E - ln rho^2 - E1(al^2 rho^2)],
+// s_n = |(rho, n Lw)|, G_k = 2 pi k / Lw, F(G, rho) = int_0^(al^2) exp(-u rho^2
+// - G^2/(4u)) du/u (the transform along the wire of erf(al r)/r). At rho = 0
+// the bracket is ln al^2, F(G, 0) = E1(G^2/(4 al^2)) and the n = 0 term is the
+// limit -2 al/sqrt(pi) + gamma(0)/a_L.
+namespace {
+constexpr double kEulerGamma = 0.5772156649015328606;
+
+// 16-point Gauss-Legendre nodes and weights on [-1, 1] (Newton on the
+// Legendre recurrence)
+struct GaussLegendre16 {
+  double x[16], w[16];
+  GaussLegendre16() {
+    const int n = 16;
+    for (int i = 0; i < n; i++) {
+      double t = std::cos(M_PI * (i + 0.75) / (n + 0.5)), d = 1.0;
+      for (int it = 0; it < 60; it++) {
+        double pm = 1.0, pc = t;
+        for (int k = 2; k <= n; k++) {
+          const double pn = ((2 * k - 1) * t * pc - (k - 1) * pm) / k;
+          pm = pc;
+          pc = pn;
+        }
+        d = n * (t * pc - pm) / (t * t - 1.0);
+        const double step = pc / d;
+        t -= step;
+        if (std::fabs(step) < 1e-16) break;
+      }
+      x[i] = t;
+      w[i] = 2.0 / ((1.0 - t * t) * d * d);
+    }
   }
+};
+}  // namespace
+
+static double wire_F(double G, double rho, double al) {
+  const double b = G * G / (4.0 * al * al);
+  if (b > 50.0) return 0.0;
+  if (rho == 0.0) return -std::expint(-b);  // E1(b)
+  // u = al^2 e^-t: int_0^inf exp(-al^2 rho^2 e^-t - b e^t) dt, cut at b e^t = 50,
+  // panels of width <= 0.4
+  static const GaussLegendre16 gl;
+  const double c = al * al * rho * rho, tmax = std::log(50.0 / b);
+  const int np = std::max(1, (int)std::ceil(tmax / 0.4));
+  const double half = 0.5 * tmax / np;
+  double acc = 0.0;
+  for (int k = 0; k < np; k++)
+    for (int i = 0; i < 16; i++) {
+      const double t = (2 * k + 1) * half + half * gl.x[i];
+      acc += gl.w[i] * std::exp(-c * std::exp(-t) - b * std::exp(t));
+    }
+  return acc * half;
+}
+
+static double wire_top_kernel(const SysHost& S, double Lw, double rho) {
+  const double aL = S.a * std::ldexp(1.0, S.nlev - 1);
+  const double al = 5.0 / Lw, rc = 7.0 / al;
+  const bool at0 = rho < 1e-300;
+  double v = 0.0;
+  const int nn = (int)std::ceil(std::max(rc, aL) / Lw) + 1;
+  for (int n = -nn; n <= nn; n++) {
+    if (at0 && n == 0) continue;
+    const double z = n * Lw, sd = std::sqrt(rho * rho + z * z);
+    if (sd < rc) v += std::erfc(al * sd) / sd;
+    if (sd < aL) v -= 1.0 / sd - soft(S.p, sd / aL) / aL;
+  }
+  if (at0) v += -2.0 * al / std::sqrt(M_PI) + soft(S.p, 0.0) / aL;
+  double rec = 0.0;
+  for (int k = 1;; k++) {
+    const double G = 2.0 * M_PI * k / Lw;
+    if (G * G / (4.0 * al * al) > 50.0) break;
+    rec += wire_F(G, rho, al);
+  }
+  v += 2.0 / Lw * rec;
+  const double x = al * al * rho * rho;
+  v += (at0 ? std::log(al * al) : -kEulerGamma - std::log(rho * rho) + std::expint(-x)) / Lw;  // Ei(-x) = -E1(x)
+  return v;
+}
+
+// Top level of a partially periodic system (one or two periodic axes): k_L
+// summed over the lattice of the periodic axes, Lp the periods (entries of
+// open axes unused), v the sample vector; offsets along periodic axes are
+// lattice vectors there, so only the open components enter.
+static double lattice_top_kernel(const SysHost& S, const double Lp[3], const double v[3]) {
+  int per[3], opn[3], np = 0, no = 0;
+  for (int d = 0; d < 3; d++) {
+    if (S.pbc[d])
+      per[np++] = d;
+    else
+      opn[no++] = d;
+  }
+  if (np == 2) return slab_top_kernel(S, Lp[per[0]], Lp[per[1]], v[opn[0]]);
+  return wire_top_kernel(S, Lp[per[0]], std::hypot(v[opn[0]], v[opn[1]]));
+}
+
+// strain derivatives (comp 1..6 = xx, yy, zz, xy, xz, yz): lattice and offset
+// strained by (1 + eps E_ab), central differences. A diagonal strain of a
+// periodic axis scales its period, of an open axis the offset; a shear that
+// involves a periodic axis leaves the sum unchanged to first order (it is
+// even under the mirror of that axis); a shear of the two open axes of a
+// wire moves the offset.
+static double lattice_top_deps(const SysHost& S, const double v[3], int comp) {
+  static const int AB[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  const int a = AB[comp - 1][0], b = AB[comp - 1][1];
+  if (a != b && (S.pbc[a] || S.pbc[b])) return 0.0;
+  const double e = 1e-5;
+  double f[2];
+  for (int k = 0; k < 2; k++) {
+    const double sg = k == 0 ? e : -e;
+    double Lp[3] = {S.L[0], S.L[1], S.L[2]}, w[3] = {v[0], v[1], v[2]};
+    if (a == b && S.pbc[a])
+      Lp[a] *= 1.0 + sg;
+    else
+      w[a] += sg * v[b];
+    f[k] = lattice_top_kernel(S, Lp, w);
+  }
+  return (f[0] - f[1]) / (2.0 * e);
 }
 
 // Pieces of the centred B-spline Phi_p(t) = N_p(t + p/2), N_p the cardinal
@@ -234,7 +349,8 @@ struct Box3 {
 // [-E, E] (per axis), sample(n) = f(h o n) for the level spacing hl. comp = 0:
 // k_l(|v|); comp 1..6: k_l'(|v|) v_a v_b / |v| with ab = xx,yy,zz,xy,xz,yz.
 static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box3& out) {
-  const bool slab_top = l == S.nlev && S.pbc[0] && S.pbc[1] && !S.pbc[2];
+  const int npbc = S.pbc[0] + S.pbc[1] + S.pbc[2];
+  const bool lat_top = l == S.nlev && npbc >= 1 && npbc <= 2;  // slab or wire top level
   const int r = S.hw;
   const std::vector<double>& wh = S.omh;
   double hl[3];
@@ -249,6 +365,9 @@ static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box
   }
   Box3 smp;
   smp.init(slo, ssz);
+  // the lattice-summed top level depends on the open components alone:
+  // samples that differ only along periodic axes share one evaluation
+  std::map<std::array<double, 3>, double> lat_memo;
   for (int x = slo[0]; x < slo[0] + ssz[0]; x++)
     for (int y = slo[1]; y < slo[1] + ssz[1]; y++)
       for (int z = slo[2]; z < slo[2] + ssz[2]; z++) {
@@ -261,9 +380,15 @@ static void build_stencil(const SysHost& S, int l, const int E[3], int comp, Box
         }
         double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         double val;
-        if (slab_top) {
-          // x, y offsets are lattice vectors: the lattice sum depends on z alone
-          val = comp == 0 ? slab_top_kernel(S, S.L[0], S.L[1], v[2]) : slab_top_deps(S, v[2], comp);
+        if (lat_top) {
+          const std::array<double, 3> key = {S.pbc[0] ? 0.0 : v[0], S.pbc[1] ? 0.0 : v[1], S.pbc[2] ? 0.0 : v[2]};
+          auto hit = lat_memo.find(key);
+          if (hit != lat_memo.end()) {
+            val = hit->second;
+          } else {
+            val = comp == 0 ? lattice_top_kernel(S, S.L, key.data()) : lattice_top_deps(S, key.data(), comp);
+            lat_memo.emplace(key, val);
+          }
           smp.at(x, y, z) = val;
           continue;
         }
@@ -635,8 +760,9 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
       return fail(err, MSM_ERR_UNSUPPORTED, "levels is fixed by the periodic grid (log2(M) + 1)");
     S.nlev = L;
     // periodic cells drop the one-point top level (zero for neutral systems);
-    // a slab keeps it, with k_L summed over the 2-D lattice (slab_top_kernel)
-    S.ncomp = (S.pbc[0] && S.pbc[1] && !S.pbc[2]) ? L : L - 1;
+    // slabs and wires keep it, with k_L summed over the 2-D or 1-D lattice
+    // of their periodic axes (slab_top_kernel, wire_top_kernel)
+    S.ncomp = (S.pbc[0] && S.pbc[1] && S.pbc[2]) ? L - 1 : L;
   } else {
     if (P.levels > 0) {
       S.nlev = P.levels;

@@ -69,6 +69,11 @@ CASES = [
          grid_override=(16, 16, 16)),
     dict(cell=(0, 2.82, 2.82, 2.82, 0, 2.82, 2.82, 2.82, 0), pbc=(1, 1, 1), h=0.5, cutoff=2.0, order=6),
     dict(cell=(10.0, 0, 0, 0, 10.0, 0, 3.0, 0, 9.539392014169456), pbc=(1, 1, 1), h=1.2, cutoff=5.0, order=4),
+    # slabs open along x or y and wires (one periodic axis): lattice-summed top levels
+    dict(cell=(24.0, 20.0, 20.0), pbc=(0, 1, 1), h=2.0, cutoff=8.0, order=4),
+    dict(cell=(20.0, 18.0, 20.0), pbc=(1, 0, 1), h=1.5, cutoff=6.0, order=6),
+    dict(cell=(20.0, 20.0, 16.0), pbc=(0, 0, 1), h=2.0, cutoff=6.0, order=4),
+    dict(cell=(32.0, 22.0, 26.0), pbc=(1, 0, 0), h=2.0, cutoff=8.0, order=8),
 ]
 
 

@@ -58,9 +58,10 @@ CASES = {
     # device path: periodic, p = 4, raw-sample balls on every level
     "periodic_p4_20001": lambda: W.random_box(20001, seed=91),
     "periodic_p4_3000": lambda: W.random_box(3000, seed=92),
-    # host path: omega'-convolved stencils (p = 6), folded or dense boxes (open, slab, exact interpolation)
+    # host path: omega'-convolved stencils (p = 6), folded or dense boxes (open, slab, wire, exact interpolation)
     "periodic_p6_3000": lambda: W.random_box(3000, seed=96, p=6, h=1.5, a=6.0),
     "slab_3000": lambda: W.random_box(3000, seed=97, pbc=(1, 1, 0)),
+    "wire_1500": lambda: W.random_box(1500, seed=95, pbc=(0, 0, 1)),
     "open_1500": lambda: W.random_box(1500, seed=98, pbc=(0, 0, 0)),
     "periodic_qi1_400": lambda: dataclasses.replace(W.random_box(400, seed=99, h=2.0, a=4.0), qi_mode=1),
 }

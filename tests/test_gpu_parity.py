@@ -71,6 +71,10 @@ WORKLOADS = {
     "periodic_20001": lambda: W.random_box(20001, seed=31),
     "water_600": lambda: W.water_box(nmol=600, L=26.2, seed=32),
     "slab_3000": lambda: W.random_box(3000, seed=33, pbc=(1, 1, 0)),
+    # slabs open along x or y and wires: the top level summed over the lattice of the periodic axes
+    "slab_open_x_2000": lambda: W.random_box(2000, seed=45, pbc=(0, 1, 1)),
+    "wire_z_2000": lambda: W.random_box(2000, seed=46, pbc=(0, 0, 1)),
+    "wire_y_1200_p6": lambda: W.random_box(1200, seed=47, pbc=(0, 1, 0), p=6, h=1.5, a=6.0),
     "tiny_periodic_40": lambda: W.random_box(40, density=0.08, seed=34),
     "tiny_open_25": lambda: W.random_box(25, density=0.08, seed=35, pbc=(0, 0, 0)),
     "rocksalt_6": lambda: W.rocksalt(ncell=6, seed=36),
@@ -300,6 +304,45 @@ def test_slab_against_ewald2d():
     assert rel_rms(r["phi"], phi2) <= 1e-3
     assert abs(r["E"] - E2) <= 5e-3 * abs(E2)
     assert r["plan"].info()["stencil_kind"][-1] == 1  # the top level is evaluated (a box)
+
+
+@pytest.mark.parametrize("axis", [2, 0])
+def test_wire_against_ewald1d(axis):
+    # a wire's top level (k_L summed over the 1-D lattice) on the GPU against the 1-D Ewald sum
+    import oracle as O
+    O.build()
+    pbc = tuple(1 if d == axis else 0 for d in range(3))
+    w = W.random_box(500, seed=43, pbc=pbc, p=8, h=1.2, a=10.0)
+    r = gpu_run(w)
+    E1, phi1 = O.ewald1d(w.cell[axis], w.pos.astype(np.float64), w.q.astype(np.float64), axis=axis)
+    assert rel_rms(r["phi"], phi1) <= 1e-3
+    assert abs(r["E"] - E1) <= 5e-3 * abs(E1)
+    assert r["plan"].info()["stencil_kind"][-1] == 1  # the top level is evaluated (a box)
+
+
+def test_batch_of_mixed_boundaries():
+    # one batch holding every boundary kind: open, wires along each axis, slabs open along each axis, periodic
+    import oracle as O
+    O.build()
+    kinds = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (0, 1, 1), (1, 0, 1), (1, 1, 0), (1, 1, 1)]
+    systems = [W.random_box(150 + 37 * i, density=0.08, seed=60 + i, pbc=k) for i, k in enumerate(kinds)]
+    batch = Batch(systems, device=DEV)
+    pos = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(DEV)
+    q = torch.from_numpy(np.concatenate([s.q for s in systems])).to(DEV)
+    E, phi, F = batch.forward(pos, q, forces=True, virial=True)
+    gp, gq, Wb = batch.backward(torch.ones(len(systems), dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    E, phi, F, Wb = E.cpu().numpy(), phi.cpu().numpy(), F.cpu().numpy(), Wb.cpu().numpy()
+    off = 0
+    for s, sysw in enumerate(systems):
+        n = sysw.n
+        ref = O.msm(O.plan_for(sysw), sysw.pos.astype(np.float64), sysw.q.astype(np.float64))
+        assert abs(E[s] - ref["E"]) <= E_TOL * abs(ref["E"]) + 1e-9, (kinds[s], E[s], ref["E"])
+        assert rel_rms(F[off:off + n], ref["F"]) <= F_TOL, kinds[s]
+        assert rel_rms(phi[off:off + n], ref["phi"]) <= F_TOL, kinds[s]
+        assert np.abs(Wb[s] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), kinds[s]
+        off += n
 
 
 def test_evaluate_host_end_to_end():

@@ -667,6 +667,121 @@ def test_slab_top_level_against_ewald2d(oracle):
     assert abs(k[2] - k[1]) <= 1e-6 * abs(k[2])
 
 
+def test_wire_top_level_strain_derivatives(oracle):
+    """dK/d eps of a wire's top level (z periodic) against stencils of a
+    strained cell: the diagonal components (the period, the open offsets) and
+    the shear of the two open axes; shears with the periodic axis vanish."""
+    P = oracle.make_plan((14.0, 15.0, 12.0), (0, 0, 1), 1.5, 4.0, 4)
+    l = P.nlev
+    for which, (a, b) in zip(range(1, 5), [(0, 0), (1, 1), (2, 2), (0, 1)]):
+        dK, _ = oracle.stencil(P, l, which)
+        eps = 1e-5
+        Ks = []
+        for sg in (1, -1):
+            G = np.eye(3)
+            G[a, b] += sg * eps / (2 if a != b else 1)
+            G[b, a] += sg * eps / 2 if a != b else 0
+            Ks.append(oracle.stencil(P, l, 0, G)[0])
+        fd = (Ks[0] - Ks[1]) / (2 * eps)
+        assert np.abs(dK).max() > 0
+        assert np.abs(fd - dK).max() <= 1e-5 * np.abs(dK).max(), which
+    for which in (5, 6):
+        assert np.abs(oracle.stencil(P, l, which)[0]).max() == 0.0
+
+
+def test_ewald1d_alpha_independence_and_direct_sum(oracle):
+    """The 1-D Ewald sum of a neutral wire does not depend on the splitting
+    parameter and equals the direct sum over replicas of the cell, whose
+    truncation error falls as 1/K^2 (cell-cell terms decay as 1/n^3)."""
+    rng = np.random.default_rng(19)
+    L, n = 10.0, 12
+    pos = np.column_stack([rng.uniform(0, 6, n), rng.uniform(0, 6, n), rng.uniform(0, L, n)])
+    q = np.array([1.0, -1.0] * (n // 2))
+    rng.shuffle(q)
+    Es = [oracle.ewald1d(L, pos, q, al)[0] for al in (0.4, 0.6, 0.9)]
+    assert max(Es) - min(Es) <= 1e-12 * abs(Es[0])
+    d = pos[None, :, :] - pos[:, None, :]
+
+    def direct(K):
+        ns = np.arange(-K, K + 1)
+        E = 0.0
+        for i in range(n):
+            for j in range(n):
+                r = np.sqrt(d[i, j, 0] ** 2 + d[i, j, 1] ** 2 + (d[i, j, 2] + ns * L) ** 2)
+                if i == j:
+                    r = r[ns != 0]
+                E += 0.5 * q[i] * q[j] * (1.0 / r).sum()
+        return E
+    errs = [abs(direct(K) - Es[0]) for K in (250, 1000, 4000)]
+    assert errs[0] / errs[1] > 10 and errs[1] / errs[2] > 10 and errs[2] <= 1e-7 * abs(Es[0])
+    # potentials: the same sum with the charge of atom 0 as probe
+    E0, phi = oracle.ewald1d(L, pos, q)
+    assert 0.5 * (q * phi).sum() == pytest.approx(E0, rel=1e-14)
+
+
+@pytest.mark.parametrize("axis", [2, 0])
+def test_wire_top_level_against_ewald1d(oracle, axis):
+    """A wire (one periodic axis) keeps its top level with k_L summed over the
+    1-D lattice: the MSM potentials then match the 1-D Ewald sum to the
+    method's accuracy; dropping the top level leaves a 20x larger error."""
+    from paper_2510_05961_gb300 import workloads as W
+    pbc = tuple(1 if d == axis else 0 for d in range(3))
+    w = W.random_box(500, seed=43, pbc=pbc, p=8, h=1.2, a=10.0)
+    pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+    P = oracle.plan_for(w)
+    assert P.top_kept == 1 and P.ncomp == P.nlev
+    r = oracle.msm(P, pos, q, forces=False, virial=False)
+    E1, phi1 = oracle.ewald1d(w.cell[axis], pos, q, axis=axis)
+    rel = np.sqrt(((r["phi"] - phi1) ** 2).mean() / (phi1 ** 2).mean())
+    assert rel <= 1e-3 and abs(r["E"] - E1) <= 5e-3 * abs(E1)
+    P.ncomp = P.nlev - 1  # the top level left out
+    rd = oracle.msm(P, pos, q, forces=False, virial=False)
+    assert np.sqrt(((rd["phi"] - phi1) ** 2).mean() / (phi1 ** 2).mean()) >= 20 * rel
+    # the lattice-summed top kernel is smooth through rho = 0 and decays like
+    # -(2/L) ln rho far from the wire (the 2-D Coulomb law of a line charge)
+    k = [oracle.wire_top(8, 10.0, P.nlev, 16.0, x) for x in (0.0, 1e-4, 400.0, 800.0)]
+    assert abs(k[1] - k[0]) <= 1e-7 * abs(k[0])
+    assert (k[3] - k[2]) == pytest.approx(-2.0 / 16.0 * math.log(2.0), rel=1e-9)
+
+
+@pytest.mark.parametrize("pbc,perm", [((0, 1, 1), (2, 0, 1)), ((1, 0, 1), (1, 2, 0)), ((1, 0, 0), (2, 0, 1)),
+                                      ((0, 1, 0), (1, 2, 0))])
+def test_axis_relabelling_invariance(oracle, pbc, perm):
+    """Relabelling the axes maps a slab open along x or y onto the slab open
+    along z, and a wire along x or y onto the wire along z: the MSM's grids,
+    stencils and level sums are per axis, so E, phi, F and W agree to rounding.
+    perm[d] is the axis that takes axis d's coordinates."""
+    rng = np.random.default_rng(23)
+    cell = np.array([14.0, 16.0, 18.0])
+    n = 60
+    pos = rng.uniform(0.5, 1.0, (n, 3)) * cell * 0.9
+    q = rng.normal(size=n)
+    q -= q.mean()
+    c2 = np.zeros(3)
+    p2 = np.zeros_like(pos)
+    pbc2 = [0, 0, 0]
+    for d in range(3):
+        c2[perm[d]] = cell[d]
+        p2[:, perm[d]] = pos[:, d]
+        pbc2[perm[d]] = pbc[d]
+    assert tuple(pbc2) in ((1, 1, 0), (0, 0, 1))
+    P1 = oracle.make_plan(tuple(cell), pbc, 1.6, 5.0, 4)
+    P2 = oracle.make_plan(tuple(c2), tuple(pbc2), 1.6, 5.0, 4)
+    assert P1.top_kept == 1 and P2.top_kept == 1
+    r1 = oracle.msm(P1, pos, q)
+    r2 = oracle.msm(P2, p2, q)
+    assert r2["E"] == pytest.approx(r1["E"], rel=1e-12)
+    assert np.allclose(r2["phi"], r1["phi"], rtol=1e-11, atol=1e-12)
+    F1 = np.zeros_like(r1["F"])
+    W1 = np.zeros((3, 3))
+    for d in range(3):
+        F1[:, perm[d]] = r1["F"][:, d]
+        for e in range(3):
+            W1[perm[d], perm[e]] = r1["W"][d, e]
+    assert np.allclose(r2["F"], F1, rtol=1e-10, atol=1e-12 * np.abs(F1).max())
+    assert np.allclose(r2["W"], W1, rtol=1e-10, atol=1e-12 * np.abs(W1).max())
+
+
 def test_half_cell_translation_invariance(oracle):
     # shifting a periodic system by L/2 moves every evaluated level by whole points
     pos, q, cell = _small_periodic()
@@ -680,10 +795,11 @@ def test_half_cell_translation_invariance(oracle):
         assert np.allclose(rs["F"], r["F"], rtol=1e-10, atol=1e-10)
 
 
-@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0), (1, 1, 0)])
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 0, 1)])
 def test_virial_against_strain_differences(oracle, pbc):
     """W = -dE/d eps under r -> (1+eps) r, A -> (1+eps) A (grid coordinates fixed);
-    for the slab this includes the strain derivative of the lattice-summed top level."""
+    for slabs and wires this includes the strain derivatives of the lattice-summed
+    top level (the period of each periodic axis, the offsets along open ones)."""
     pos, q, cell = _small_periodic()
     if not all(pbc):
         pos = np.clip(pos, 0.5, 8.5)
