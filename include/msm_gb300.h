@@ -69,7 +69,12 @@ typedef struct msm_batch_s* msm_batch;
  *                 centres). A plan built for a tilted cell takes any later
  *                 right-handed cell in msm_plan_set_cell; a rectangular plan
  *                 only rectangular ones.
- *  pbc[3]         1 = periodic along that axis, 0 = open.
+ *  pbc[3]         1 = periodic along that axis, 0 = open. Any combination:
+ *                 three periodic axes drop the one-point top level (zero for
+ *                 a neutral cell, Sec. 4.1); two (a slab) or one (a wire)
+ *                 keep it, with the level-L kernel summed over the 2-D or
+ *                 1-D lattice of the periodic axes (the divergent constant,
+ *                 which multiplies the squared total charge, left out).
  *  h              target level-1 grid spacing h_1 (> 0 unless overridden).
  *                 Periodic axes use M = 2^round(log2(L/h)) intervals (all
  *                 periodic axes must give the same M); open axes M = ceil(L/h).
