@@ -608,8 +608,8 @@ def run_sweep(args):
 
 def run_cells(args):
     """Forward + backward (E, F, dE/dq, virial) of N atoms at 0.1 atoms/A^3 in cells of different shape:
-    periodic cube, slab (x, y periodic; the lattice-summed top level), and tilted periodic cells (dense-box
-    stencils, general short-range kernel). Same p = 4, a = 8 and grid counts; CUDA events, L2 flushed."""
+    periodic cube, slabs (open along z or x) and a wire (periodic along z) with lattice-summed top levels,
+    and tilted periodic cells (general ball stencils, general short-range kernel). Same p = 4, a = 8 and grid counts; CUDA events, L2 flushed."""
     import numpy as np
     import torch
 
@@ -622,13 +622,15 @@ def run_cells(args):
     shapes = {
         "cube": (np.diag([L, L, L]), (1, 1, 1)),
         "slab": (np.diag([L, L, L]), (1, 1, 0)),
+        "slab_open_x": (np.diag([L, L, L]), (0, 1, 1)),
+        "wire": (np.diag([L, L, L]), (0, 0, 1)),
         "sheared": (np.array([[L, 0, 0], [0.5 * L, L, 0], [0.2 * L, -0.3 * L, L]]), (1, 1, 1)),
         "hexagonal": (np.array([[L, 0, 0], [-0.5 * L, math.sqrt(3) / 2 * L, 0], [0, 0, L / (math.sqrt(3) / 2)]]),
                       (1, 1, 1)),
     }
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     rng = np.random.default_rng(77)
-    frac = rng.uniform(0, 1, (n, 3))
+    frac = rng.uniform(0, 1 - 1e-6, (n, 3))  # strictly inside the cell along open axes after FP32 rounding
     q = np.concatenate([np.ones(n // 2), -np.ones(n - n // 2)]).astype(np.float32)
     rng.shuffle(q)
     rows = {}
@@ -653,9 +655,18 @@ def run_cells(args):
             torch.cuda.synchronize()
             t += e0.elapsed_time(e1)
         ms = t / args.steps
+        # per-phase CUDA-event times of one more step (outside the timed steps)
+        plan.profile(True)
+        flush.zero_()
+        plan.forward(tp, tq, forces=True, virial=True)
+        plan.backward(g)
+        torch.cuda.synchronize()
+        phase, _ = plan.profile_read()
+        plan.profile(False)
         info = plan.info()
         rows[name] = {"ms_per_step": ms, "atoms_per_s": n / (ms / 1e3), "R": info["R"],
-                      "stencil_kind": info["stencil_kind"], "pbc": list(pbc)}
+                      "stencil_kind": info["stencil_kind"], "pbc": list(pbc),
+                      "phase_ms": {k: round(v, 4) for k, v in phase.items() if v > 0}}
         del plan
         torch.cuda.empty_cache()
     print(json.dumps({"cells": rows, "atoms": n, "M": M, "unit": "atoms/s",

@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
       const int ux = ci[0] + ox;
       if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
-      const int nxc = floordiv_s(ux, Cx) * Cx;  // image shift along x, in cells
+      // image shift along x, in cells: C is a power of two on a periodic axis,
+      // and an open axis only visits u in [0, C)
+      const int nxc = (ux >> S.cshift[0]) << S.cshift[0];
       const int wx = ux - nxc;
       const float bx = (float)ox * ex - xi.x;  // d_x = bx + x_j
       const float mx = fmaxf((ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f)) - mg * ex, 0.f);
@@ -99,9 +101,10 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
         const float my = fmaxf((oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f)) - mg * ey, 0.f);
         const float rxy2 = mx * mx + my * my;
         if (rxy2 >= a2) continue;
-        const int nyc = floordiv_s(uy, Cy) * Cy;
+        const int nyc = (uy >> S.cshift[1]) << S.cshift[1];
         const int wy = uy - nyc;
-        const float zr = sqrtf(a2 - rxy2) + mg * S.edge[2];
+        const float zr2 = a2 - rxy2;  // > 0
+        const float zr = zr2 * rsqrtf(zr2) + mg * S.edge[2];
         int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
         if (!S.pbc[2]) {
           zlo = max(zlo, 0);
@@ -110,8 +113,8 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
         const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
         int uz = zlo;
         while (uz <= zhi) {
-          const int kz = floordiv_s(uz, Cz);
-          const int wz = uz - kz * Cz;
+          const int kz = uz >> S.cshift[2];
+          const int wz = uz - (kz << S.cshift[2]);
           const int wend = min(Cz - 1, wz + (zhi - uz));
           const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
           const float bz = image_shift(kz, S.Ld[2], xi.z);

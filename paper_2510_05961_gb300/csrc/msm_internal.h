@@ -40,6 +40,7 @@ struct SysDev {
   int C[3];         // binning cells per axis
   int cell_off;     // first packed cell index
   int nnbr[3];      // neighbour-cell reach ceil(a / edge)
+  int cshift[3];    // log2 of C rounded up (C is a power of two on periodic axes)
   int pbc[3];
   int M[3];         // level-1 interval counts (u = s * M)
   int p;            // B-spline order

@@ -959,6 +959,8 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     for (int d = 0; d < 3; d++) {
       D.C[d] = S.C[d];
       D.nnbr[d] = S.nnbr[d];
+      D.cshift[d] = 0;
+      while ((1 << D.cshift[d]) < S.C[d]) D.cshift[d]++;
       D.pbc[d] = S.pbc[d];
       D.M[d] = S.M[d];
       D.edge[d] = (float)S.edge[d];
