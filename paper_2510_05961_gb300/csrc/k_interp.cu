@@ -188,8 +188,14 @@ __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__
       cl[d] = floordiv_i(m[d] - H, k);
       ch[d] = floordiv_i(mhi[d] + H - 1, k);
     } else {
-      cl[d] = floordiv_i((m[d] - H) * S.C[d], S.M[d]) - 1;
-      ch[d] = floordiv_i((mhi[d] + H) * S.C[d], S.M[d]) + 1;
+      // cells not aligned with the grid (open axes): the atoms reaching the
+      // points [m, mhi] have u in [m - H, mhi + H), and an atom binned in cell
+      // c has u C / M within 1e-4 of [c, c + 1] (s C and s M are FP32 products
+      // of one s, and C <= 256 on an open axis); with the rounding of the
+      // bounds below, a margin of 2e-4 cells keeps every such atom
+      const float rc = (float)S.C[d] / (float)S.M[d];
+      cl[d] = (int)floorf((float)(m[d] - H) * rc - 2e-4f);
+      ch[d] = (int)floorf((float)(mhi[d] + H) * rc + 2e-4f);
     }
     if (!S.pbc[d]) {
       cl[d] = max(cl[d], 0);

@@ -40,6 +40,14 @@ __device__ __forceinline__ int floordiv_s(int a, int b) {
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
+// 1/sqrt(x) for a normal x > 0: the hardware approximation (relative error
+// below 2^-22), flush-to-zero form, so no rescaling of subnormal inputs
+__device__ __forceinline__ float rsqrt_nrm(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // k L - z, rounded once (FP64 only for the z-runs across a periodic face)
 __device__ __forceinline__ float image_shift(int k, double L, float z) {
   if (k == 0) return -z;
@@ -104,7 +112,7 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
         const int nyc = (uy >> S.cshift[1]) << S.cshift[1];
         const int wy = uy - nyc;
         const float zr2 = a2 - rxy2;  // > 0
-        const float zr = zr2 * rsqrtf(zr2) + mg * S.edge[2];
+        const float zr = zr2 * rsqrt_nrm(zr2) + mg * S.edge[2];
         int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
         if (!S.pbc[2]) {
           zlo = max(zlo, 0);
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
             const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < a2 && r2 > 0.f) {
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_nrm(r2);
             const float s = 1.0f - r2 * inv_a2;
             float g = gc[P - 1];
 #pragma unroll
@@ -232,7 +240,8 @@ __global__ void __launch_bounds__(kChunk) k_short_fvjp(const SysDev* __restrict_
       const float rxy2 = mx * mx + my * my;
       if (rxy2 >= a2) continue;
       const int wy = uy - floordiv_s(uy, Cy) * Cy;
-      const float zr = sqrtf(a2 - rxy2) + mg * S.edge[2];
+      const float zr2 = a2 - rxy2;  // > 0
+      const float zr = zr2 * rsqrt_nrm(zr2) + mg * S.edge[2];
       int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
       if (!S.pbc[2]) {
         zlo = max(zlo, 0);
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(kChunk) k_short_fvjp(const SysDev* __restrict_
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < a2 && r2 > 0.f) {
             const float4 uj = us[j];
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_nrm(r2);
             const float rinv2 = rinv * rinv;
             const float s = 1.0f - r2 * inv_a2;
             float p1 = gdc[P - 2], dp1 = (float)(P - 2) * gdc[P - 2];
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(kChunk) k_short_fvjp_tri(const SysDev* __restr
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < a2 && r2 > 0.f) {
             const float4 uj = us[j];
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_nrm(r2);
             const float rinv2 = rinv * rinv;
             const float sg = 1.0f - r2 * inv_a2;
             float p1 = gdc[P - 2], dp1 = (float)(P - 2) * gdc[P - 2];
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(kChunk) k_short_tri(const SysDev* __restrict__
             const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < a2 && r2 > 0.f) {
-              const float rinv = rsqrtf(r2);
+              const float rinv = rsqrt_nrm(r2);
               const float sg = 1.0f - r2 * inv_a2;
               float g = gc[P - 1];
 #pragma unroll
