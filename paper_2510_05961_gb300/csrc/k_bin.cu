@@ -183,6 +183,11 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
                            float4* __restrict__ xq, float4* __restrict__ uq) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
+  // low part of the binning cell edges, edged - (float)edged (once per block:
+  // the per-atom corner below then needs no FP64 arithmetic)
+  __shared__ float s_elo[2];
+  if (threadIdx.x < 2) s_elo[threadIdx.x] = (float)(S.edged[threadIdx.x] - (double)S.edge[threadIdx.x]);
+  __syncthreads();
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
@@ -198,8 +203,8 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   // (the Cartesian z of the image next to the cell), formed in FP64 from the
   // FP32 input so that displacements between nearby atoms are exact to FP32
   float loc[3], u[3];
-  int c[3] = {cell / (S.C[1] * S.C[2]), (cell / S.C[2]) % S.C[1], cell % S.C[2]};
   if (S.tri) {
+    const int c[3] = {cell / (S.C[1] * S.C[2]), (cell / S.C[2]) % S.C[1], cell % S.C[2]};
     // Cartesian position relative to the base of the cell's column, c_x / C_x a +
     // c_y / C_y b, formed in FP64 from the FP32 input and wrapped the way the
     // FP32 contract placed the atom (a fractional coordinate that rounds across
@@ -229,14 +234,30 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
       u[d] = 0.0f;
       continue;
     }
-    axis_cell(S, d, s, t);
-    double xd = x;
-    if (S.pbc[d]) {
-      if (!(xd >= 0.0 && xd < S.Ld[d])) xd -= S.Ld[d] * floor(xd / S.Ld[d]);
-      if (c[d] == 0 && xd > 0.5 * S.Ld[d]) xd -= S.Ld[d];  // s rounded up to 1 wraps to cell 0
-    }
-    loc[d] = d < 2 ? (float)(xd - c[d] * S.edged[d]) : (float)xd;
+    const int cd = axis_cell(S, d, s, t);  // the cell coordinate k_bin_count packed into cell_id
     u[d] = s * S.Mf[d];
+    // A periodic coordinate outside [0, L), or one in cell 0 near the far face
+    // (s rounded up to 1 wraps to cell 0), is wrapped in FP64. x < (float)L
+    // implies x < L whichever way L rounded; for C <= 2 the cell-0 test also
+    // sends some inner atoms here, which only costs time.
+    if (S.pbc[d] && !(x >= 0.0f && x < S.Lf[d] && !(cd == 0 && x >= 0.25f * S.Lf[d]))) {
+      double xd = x;
+      if (!(xd >= 0.0 && xd < S.Ld[d])) xd -= S.Ld[d] * floor(xd / S.Ld[d]);
+      if (cd == 0 && xd > 0.5 * S.Ld[d]) xd -= S.Ld[d];
+      loc[d] = d < 2 ? (float)(xd - cd * S.edged[d]) : (float)xd;
+      continue;
+    }
+    if (d == 2) {
+      loc[d] = x;
+      continue;
+    }
+    // x - c e rounded once, with c e = ph + pe + c elo exactly up to the last
+    // term's rounding: ph = fl(c eh), pe = c eh - ph (exact by FMA), and
+    // x - ph is exact (x lies in cell c, so ph / 2 <= x <= 2 ph, Sterbenz)
+    const float cf = (float)cd, eh = S.edge[d];
+    const float ph = cf * eh;
+    const float pe = fmaf(cf, eh, -ph);
+    loc[d] = (x - ph) - fmaf(cf, s_elo[d], pe);
   }
   xq[dst] = make_float4(loc[0], loc[1], loc[2], qq);
   uq[dst] = make_float4(u[0], u[1], u[2], qq);

@@ -22,7 +22,7 @@
 
 namespace {
 
-__device__ __align__(256) unsigned char g_noalloc_scratch[MSM_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MSM_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
