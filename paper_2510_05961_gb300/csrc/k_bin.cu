@@ -191,10 +191,6 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
-  // the atom's own inputs first: their loads overlap the dependent chain
-  // cell_id -> cell_start -> bucket below
-  const float xin[3] = {pos[3 * (long long)g], pos[3 * (long long)g + 1], pos[3 * (long long)g + 2]};
-  const float qq = q[g];
   int cell = cell_id[g];
   int b = cell_start[S.cell_off + cell], e = cell_start[S.cell_off + cell + 1];
   int rank = 0;
@@ -202,6 +198,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   int dst = b + rank;
   perm[dst] = g;
   scell[dst] = cell;
+  float qq = q[g];
   // x, y relative to the cell's lower faces, z relative to the column base
   // (the Cartesian z of the image next to the cell), formed in FP64 from the
   // FP32 input so that displacements between nearby atoms are exact to FP32
@@ -213,8 +210,8 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
     // FP32 contract placed the atom (a fractional coordinate that rounds across
     // a face follows its cell)
     float sf[3];
-    tilted_coords(S, xin, sf);
-    const double x[3] = {xin[0], xin[1], xin[2]};
+    tilted_coords(S, pos + 3 * (long long)g, sf);
+    const double x[3] = {pos[3 * g], pos[3 * g + 1], pos[3 * g + 2]};
     double sd[3];
     for (int d = 0; d < 3; d++) {
       double v = S.Td[3 * d] * x[0] + S.Td[3 * d + 1] * x[1] + S.Td[3 * d + 2] * x[2];
@@ -231,7 +228,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   }
   for (int d = 0; d < 3; d++) {
     float s, t;
-    const float x = xin[d];
+    const float x = pos[3 * g + d];
     if (reduced_coord(S, d, x, s)) {
       loc[d] = 0.0f;
       u[d] = 0.0f;
