@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kGridChunk) k_restrict(const SysDev* __restric
     for (int k = 0; k <= P; k++) {
       int f = 2 * m + (k - H);
       if (Fl.per[d]) {
-        fi[d][k] = wrap_g(f, Fl.n[d]);
+        fi[d][k] = f & (Fl.n[d] - 1);  // periodic level sizes are powers of two
       } else {
         int s = f - Fl.lo[d];
         fi[d][k] = (s >= 0 && s < Fl.n[d]) ? s : -1;

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
 #pragma unroll
     for (int j = 0; j < P; j++) {
       int m = base + j;
-      ix[d][j] = L.per[d] ? wrap_i(m, L.n[d]) : m - L.lo[d];
+      ix[d][j] = L.per[d] ? (m & (L.n[d] - 1)) : m - L.lo[d];  // periodic grid counts are powers of two
     }
   }
   const float* e = grid + L.e_off;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kChunk) k_interp_hess(const SysDev* __restrict
 #pragma unroll
       for (int j = 0; j < P; j++) {
         int m = base + j;
-        ix[d][j] = L.per[d] ? wrap_i(m, L.n[d]) : m - L.lo[d];
+        ix[d][j] = L.per[d] ? (m & (L.n[d] - 1)) : m - L.lo[d];  // periodic grid counts are powers of two
       }
     }
     const float* e = grid + L.e_off;
