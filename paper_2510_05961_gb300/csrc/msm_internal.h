@@ -26,6 +26,7 @@ constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one blo
 constexpr int kGridChunk = 256;    // coarse points per restriction item
 constexpr int kVirialSlices = 64;  // most virial reduction slices per system
 constexpr int kProTX = 4, kProTY = 4, kProTZ = 32;  // prolongation tiles (fine points)
+constexpr int kFoldPts = 512;      // batch plans fold levels this small into dense boxes
 constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)
 
 // device status bits (mirrors MSM_DEV_* of the public header)

@@ -519,6 +519,12 @@ static void fill_stencils(SysHost& S, bool decide) {
       bool ball = !top && S.qi_mode == 0 && S.allow_ball;
       for (int d = 0; d < 3; d++)
         if (S.B[d] > kBallRmax) ball = false;
+      // batch plans: a level of a few hundred points costs a ball kernel a whole
+      // 32 x 32 tile per x-plane and a halo-padded copy much larger than itself;
+      // folded onto the grid, its dense box has at most n^3 entries per point.
+      // (Single-system plans keep every level a ball, which msm_plan_set_cell
+      // can recompute on the device.)
+      if (S.fold_small && (long long)Lv.n[0] * Lv.n[1] * Lv.n[2] <= kFoldPts) ball = false;
       for (int d = 0; d < 3; d++) Lv.R[d] = S.B[d];
       if (ball) {
         Lv.kind = 0;
@@ -930,6 +936,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   single = single_;
   sys.assign(nsys, SysHost());
   for (int s = 0; s < nsys; s++) {
+    sys[s].fold_small = !single_;
     int rc = plan_system(prm[s], sys[s], err);
     if (rc) return rc;
     if (counts[s] < 0) return fail(err, MSM_ERR_INVALID_ARG, "atom counts must be >= 0");

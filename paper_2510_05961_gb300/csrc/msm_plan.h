@@ -51,6 +51,7 @@ struct SysHost {
   int hzb = 0;                       // z halo of the ball levels' padded grids and stored rows
   int wmax = 0;                      // widest ball column (half-width about its centre)
   bool allow_ball = true;            // false: every level a dense box
+  bool fold_small = false;           // batch plans: levels of <= kFoldPts points as folded dense boxes
   // offsets of this system's ball stencil, virial weights and column tables in the device pools
   long long kball_off = -1, dkh_off = -1, wb_off = -1, wh_off = -1, cb_off = -1;
 };

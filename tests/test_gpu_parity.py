@@ -460,6 +460,9 @@ def test_batch_matches_single_and_oracle():
         assert rel_rms(F[off:off + n], ref["F"]) <= F_TOL, s
         assert rel_rms(phi[off:off + n], ref["phi"]) <= F_TOL, s
         assert np.abs(Wb[s] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), s
+        # a batch plan applies its small levels (<= 512 points) as folded dense boxes of
+        # K = omega'^3 * s, a single plan applies s to the omega'-prefiltered grid: equal in
+        # exact arithmetic, so the two agree to the FP32 energy tolerance, not bitwise
         single = gpu_run(sysw)
-        assert abs(single["E"] - E[s]) <= 1e-6 * abs(E[s]) + 1e-12
+        assert abs(single["E"] - E[s]) <= E_TOL * abs(E[s]) + 1e-9
         off += n
