@@ -305,6 +305,10 @@ const char* msm_last_error(void);
  *  n_per_sys  host, nsys atom counts (fixed for the batch).
  * Atoms of all systems are packed back to back in system order: positions
  * (sum n) x 3, charges sum n; energy has nsys entries, virial 9 * nsys.
+ * A batch applies each system's grid levels of at most 512 points as folded
+ * dense stencils (a single-system plan applies them as ball stencils on the
+ * prefiltered grid); the two are equal in exact arithmetic, so a system's
+ * results in a batch and in its own plan agree to FP32 rounding, not bitwise.
  * ------------------------------------------------------------------------- */
 int msm_batch_create(const msm_params* per_sys, const int* n_per_sys, int nsys, msm_batch* out);
 int msm_batch_destroy(msm_batch batch);
