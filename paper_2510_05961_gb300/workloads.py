@@ -209,6 +209,46 @@ def batch_systems(nsys=512, seed=5000, nmin=20, nmax=4000, density=0.08, h=2.0, 
     return out
 
 
+def redraw(w, seed, qsigma=0.5):
+    """Same system shape (cell, periodicity, settings, atom count), new inputs:
+    positions uniform in the cell, charges N(0, qsigma) shifted to zero sum.
+    A plan made for w serves the redrawn system too."""
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0.0, 1.0, size=(w.n, 3)) * np.asarray(w.cell, np.float64)
+    q = rng.normal(0.0, qsigma, size=w.n)
+    q -= q.mean()
+    return Workload(w.name + "_redrawn", pos.astype(np.float32), q.astype(np.float32), w.cell, w.pbc, w.h, w.a,
+                    w.p, w.levels, w.grid_override, w.qi_mode)
+
+
+def lattice_on_grid(ncell=4, a0=4.0, pbc=(1, 1, 1), seed=6000, qsigma=0.1, h=2.0, a=8.0, p=4):
+    """Undisplaced rock-salt lattice whose sites fall exactly on level-1 grid
+    points and binning-cell faces (with h = a0 / 2 and a power-of-two grid),
+    charges +/-(1 + qsigma N(0,1)) shifted to zero sum. Along an open axis the
+    crystal gets one more layer of sites, so that its sites lie exactly on both
+    faces of the cell (s = 0 and s = 1, i.e. x = 0 and x = L)."""
+    rng = np.random.default_rng(seed)
+    m = 2 * ncell
+    g = np.arange(m)
+    idx = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    cell = [ncell * a0] * 3
+    extra = []
+    # open axes: add the layer at the far face (index m) along each open axis
+    for d in range(3):
+        if not pbc[d]:
+            layer = idx[idx[:, d] == 0].copy()
+            layer[:, d] = m
+            extra.append(layer)
+    if extra:
+        idx = np.unique(np.concatenate([idx] + extra), axis=0)
+    pos = idx * (0.5 * a0)
+    sign = np.where(idx.sum(1) % 2 == 0, 1.0, -1.0)
+    q = sign * (1.0 + qsigma * rng.normal(size=len(sign)))
+    q -= q.mean()
+    return Workload("lattice_on_grid_%d" % ncell, pos.astype(np.float32), q.astype(np.float32), tuple(cell),
+                    tuple(pbc), h, a, p)
+
+
 def scaling_sizes(kmax=14):
     """The sweep sizes n = 1000 * 2**k, k = 0 .. kmax."""
     return [1000 * 2 ** k for k in range(kmax + 1)]

@@ -24,6 +24,7 @@ from paper_2510_05961_gb300 import workloads as W  # noqa: E402
 
 E_TOL = 1e-5
 F_TOL = 1e-4
+BATCH_SINGLE_TOL = 2e-6
 DEV = torch.device("cuda", 0)
 
 
@@ -451,6 +452,7 @@ def test_batch_matches_single_and_oracle():
     phi = phi.cpu().numpy()
     F = F.cpu().numpy()
     Wb = Wb.cpu().numpy()
+    gaps = []
     off = 0
     for s, sysw in enumerate(systems):
         n = sysw.n
@@ -462,7 +464,10 @@ def test_batch_matches_single_and_oracle():
         assert np.abs(Wb[s] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), s
         # a batch plan applies its small levels (<= 512 points) as folded dense boxes of
         # K = omega'^3 * s, a single plan applies s to the omega'-prefiltered grid: equal in
-        # exact arithmetic, so the two agree to the FP32 energy tolerance, not bitwise
+        # exact arithmetic, so the two differ by FP32 rounding only; the measured gaps
+        # are printed, and the bound is set a few times above them
         single = gpu_run(sysw)
-        assert abs(single["E"] - E[s]) <= E_TOL * abs(E[s]) + 1e-9
+        gaps.append(abs(single["E"] - E[s]) / abs(E[s]))
+        assert abs(single["E"] - E[s]) <= BATCH_SINGLE_TOL * abs(E[s]) + 1e-9, (s, gaps[-1])
         off += n
+    print("batch vs single relative energy gaps: max %.3g, median %.3g" % (max(gaps), float(np.median(gaps))))

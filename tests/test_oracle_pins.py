@@ -211,20 +211,50 @@ def test_plan_rules(oracle):
         oracle.make_plan((10, 10, 10), (0, 0, 0), 1.0, 3.0, 5)  # odd order
 
 
-@pytest.mark.parametrize("pbc", [(0, 0, 0), (1, 1, 1)])
-def test_stencil_symmetry_and_level_scaling(oracle, pbc):
+def test_stencil_symmetry_and_level_scaling_open(oracle):
+    # K_m = K_-m, the cube's axis symmetry, and K^l = K^1 / 2^(l-1) below the top level (Sec. 3.4)
     side = 19.0
-    P = oracle.make_plan((side,) * 3, pbc, 1.2, 3.0, 4)
+    P = oracle.make_plan((side,) * 3, (0, 0, 0), 1.2, 3.0, 4)
     K1, lo1 = oracle.stencil(P, 1)
-    if not any(pbc):
-        assert np.allclose(K1, K1[::-1, ::-1, ::-1], rtol=1e-14, atol=0)
-        assert np.allclose(K1, np.transpose(K1, (1, 0, 2)), rtol=1e-14, atol=0)
-    for l in range(2, P.ncomp if not any(pbc) else P.ncomp + 1):
-        if l == P.nlev:
-            continue
+    assert np.allclose(K1, K1[::-1, ::-1, ::-1], rtol=1e-14, atol=0)
+    assert np.allclose(K1, np.transpose(K1, (1, 0, 2)), rtol=1e-14, atol=0)
+    assert P.ncomp >= 3
+    for l in range(2, P.ncomp):
         Kl, _ = oracle.stencil(P, l)
-        if not any(pbc):
-            assert np.abs(Kl - K1 / 2 ** (l - 1)).max() <= 1e-14 * np.abs(K1).max()
+        assert np.abs(Kl - K1 / 2 ** (l - 1)).max() <= 1e-14 * np.abs(K1).max()
+
+
+def _fold(K, n):
+    """Sum of a periodic stencil over its images on a grid of n points per axis (n divides K's size)."""
+    m = K.shape[0] // n
+    return K.reshape(m, n, m, n, m, n).sum(axis=(0, 2, 4))
+
+
+def test_stencil_symmetry_and_level_scaling_periodic(oracle):
+    """Periodic levels store the folded stencil on the level's own grid (index m mod n_l).
+    It is even (K_m = K_(-m mod n)) and symmetric under exchanging the axes of the
+    cube; and since k_l(|h_l n|) = k_1(|h_1 n|) / 2^(l-1), each coarser level is the
+    level-1 stencil folded onto its grid and scaled: K^l = fold_(n_l)(K^1) / 2^(l-1).
+    Level 1 here has 2R + 1 = 13 < 16 points per axis (no self-overlap), level 2
+    folds onto 8 points, so images that overlap must be summed."""
+    side = 19.0
+    P = oracle.make_plan((side,) * 3, (1, 1, 1), 1.2, 3.0, 4)
+    assert P.M[0] == 16 and 2 * P.R[0] + 1 < 16 and P.ncomp == 4
+    K1, lo1 = oracle.stencil(P, 1)
+    assert K1.shape == (16, 16, 16) and tuple(lo1) == (0, 0, 0)
+    # the unfolded support [-R, R] maps one to one onto the 16-point grid
+    R = P.R[0]
+    idx = np.r_[np.arange(0, R + 1), np.arange(16 - R, 16)]
+    assert np.abs(np.delete(K1, idx, axis=0)).max() == 0.0
+    scale = np.abs(K1).max()
+    for l in range(1, P.ncomp + 1):
+        Kl, lo = oracle.stencil(P, l)
+        n = Kl.shape[0]
+        neg = np.roll(Kl[::-1, ::-1, ::-1], 1, axis=(0, 1, 2))  # K[(-m) mod n]
+        assert np.abs(Kl - neg).max() <= 1e-14 * scale
+        for perm in [(1, 0, 2), (0, 2, 1), (2, 1, 0)]:
+            assert np.abs(Kl - np.transpose(Kl, perm)).max() <= 1e-14 * scale
+        assert np.abs(Kl - _fold(K1, n) / 2 ** (l - 1)).max() <= 1e-13 * scale, l
 
 
 @pytest.mark.parametrize("p", [4, 6])
@@ -835,3 +865,34 @@ def test_strain_derivative_stencils(oracle):
         Km, _ = oracle.stencil(P, 1, 0, G)
         fd = (Kp - Km) / (2 * eps)
         assert np.abs(fd - dK).max() <= 1e-6 * np.abs(dK).max()
+
+
+def _read_fd_golden():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fd_rocksalt32.txt")
+    rows, vir = [], None
+    for ln in open(path):
+        if ln.startswith("virial"):
+            vir = np.array([float(v) for v in ln.split()[1:]])
+        elif ln[:1].isdigit():
+            rows.append([float(v) for v in ln.split()])
+    rows = np.array(rows)
+    return rows[:, 0].astype(int), rows[:, 1:4], rows[:, 4], vir
+
+
+def test_rocksalt32_gradients_against_stored_differences(oracle):
+    """The oracle's analytic gradients on the full 32^3 rock-salt supercell (262,144
+    atoms) against central differences of its own energy (tests/golden/fd_rocksalt32.txt,
+    written by make_fd_rocksalt32.py beside it): dE/dr = -F and dE/dq = phi at 64
+    seeded atoms (Sec. 3.2.2 derivatives) and the six virial components W = -dE/d eps
+    from strained cells (sheared ones through the general-cell path)."""
+    from paper_2510_05961_gb300 import workloads as W
+    idx, dEdr, dEdq, vir = _read_fd_golden()
+    w = W.rocksalt(ncell=32)
+    P = oracle.make_plan(w.cell, w.pbc, w.h, w.a, w.p, grid_override=(64, 64, 64))
+    r = oracle.msm(P, w.pos.astype(np.float64), w.q.astype(np.float64))
+    assert np.abs(dEdr + r["F"][idx]).max() <= 5e-6 * np.abs(r["F"][idx]).max()
+    assert np.abs(dEdq - r["phi"][idx]).max() <= 1e-6 * np.abs(r["phi"][idx]).max()
+    Wr = r["W"]
+    ref = np.array([Wr[0, 0], Wr[1, 1], Wr[2, 2], Wr[0, 1], Wr[0, 2], Wr[1, 2]])
+    assert np.abs(vir - ref).max() <= 1e-8 * np.abs(ref).max()
