@@ -28,9 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MSM fwd+bwd atoms/s at 1M atoms (FP32 vs FP64 oracle), % roofline, batch speedup"
 N_HEADLINE = 1_024_000
-SM_COUNT = 152
-FP32_LANES = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES = 128          # FP32 lanes per SM (Blackwell)
+FALLBACK_HBM_GBS = 6800.0  # used only when MEASURED_PEAKS.json is absent
 
 
 def parse():
@@ -167,11 +166,115 @@ def stencil_flops(plan_params, info, cell, a, p):
     return total
 
 
-def short_flops(n, density, a):
-    """Algorithmic FLOPs of the short-range kernel with forces and virial: in-cutoff
-    ordered pairs of uniform random positions (n * density * 4/3 pi a^3) times
-    54 FLOPs per pair (FMA = 2)."""
-    return n * density * 4.0 / 3.0 * math.pi * a ** 3 * 54.0
+SHORT_FLOP_PER_PAIR = 40.0  # about 20 FMA per in-cutoff ordered pair (Horner gamma, gamma', E, phi, F, W)
+
+
+def short_pairs(n, density, a):
+    """In-cutoff ordered pairs of uniform random positions: n * density * 4/3 pi a^3."""
+    return n * density * 4.0 / 3.0 * math.pi * a ** 3
+
+
+def peaks(dev, clk):
+    """FP32 FMA peak from the device's SM count and the maximum SM clock seen by
+    nvidia-smi (else MEASURED_PEAKS.json's), HBM from MEASURED_PEAKS.json."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mp = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mp = json.load(open(path))
+    mhz = (clk or {}).get("sm_max_mhz") or mp.get("sm_max_mhz") or 2070.0
+    fp32 = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    hbm = mp.get("hbm_gbs")
+    return {"fp32_tflops": fp32, "sms": sms, "sm_max_mhz": mhz,
+            "hbm_gbs": hbm if hbm else FALLBACK_HBM_GBS, "hbm_of": "measured" if hbm else "fallback",
+            "fp32_of": "derived: %d SMs x %d lanes x 2 x %.0f MHz" % (sms, FP32_LANES, mhz)}
+
+
+def level_points(info):
+    return [n[0] * n[1] * n[2] for n in info["n"][:info["ncomp"]]]
+
+
+def ball_sample_flops(info, a, p):
+    """Algorithmic FLOPs of the level stencils in the factored form K = omega'^3 * s
+    (Eq. kernel_stencil_by_conv_with_universal_coeff): per point of a ball level one
+    FMA per nonzero kernel sample s (|h_1 o n| < 2a), plus the separable omega'
+    prefilter, 2 (p-1) FLOP per axis per padded point. The kernel also sums the
+    rows that share a column (the samples are even in x and y) before its FMAs;
+    that saving is not counted as work here. Returns (flops, sample count)."""
+    import numpy as np
+    h1 = np.array(info["h1"])
+    S = [int(math.ceil(2 * a / h1[d])) - 1 for d in range(3)]
+    g = [np.arange(-S[d], S[d] + 1) * h1[d] for d in range(3)]
+    nnz = int(np.count_nonzero((g[0][:, None, None] ** 2 + g[1][None, :, None] ** 2 +
+                                g[2][None, None, :] ** 2) < (2 * a) ** 2))
+    total = 0.0
+    for n, kind in zip(info["n"][:info["ncomp"]], info["stencil_kind"]):
+        if kind == 0:
+            pts = n[0] * n[1] * n[2]
+            padded = (n[0] + 2 * S[0]) * (n[1] + 2 * S[1]) * (n[2] + 2 * S[2])
+            total += 2.0 * pts * nnz + 3 * 2.0 * (p - 1) * padded
+    return total, nnz
+
+
+def virial_sample_flops(info, a, p):
+    """Algorithmic FLOPs of the grid virial: the autocorrelation C_d = sum_m q_m q_(m+d)
+    over the unique lags of the sample ball (C_d = C_-d: half of them, the zero lag
+    once), one FMA per lag per point of a ball level."""
+    f, nnz = ball_sample_flops(info, a, p)
+    pts = sum(n[0] * n[1] * n[2] for n, kind in zip(info["n"][:info["ncomp"]], info["stencil_kind"]) if kind == 0)
+    return 2.0 * pts * (nnz + 1) / 2
+
+
+def kernel_table(info, n, a, p, ph, pk, st_flops_exec, serial_note):
+    """Per-phase roofline rows from serialised phase times ph (ms): algorithmic work per
+    launch / time, against the binding peak (FP32 FMA or HBM)."""
+    pts = level_points(info)
+    f_ball, nnz = ball_sample_flops(info, a, p)
+    f_vir = virial_sample_flops(info, a, p)
+    rows = {}
+
+    def add(name, kernel, bound, work, unit_work, extra=None):
+        t = ph.get(name, 0.0)
+        if t <= 0:
+            return
+        if bound == "alu":
+            ach = work / (t / 1e3) / 1e12
+            row = {"kernel": kernel, "bound": "alu", "ms": round(t, 4), "achieved": ach, "unit": "TFLOP/s",
+                   "peak": pk["fp32_tflops"], "frac": ach / pk["fp32_tflops"], "work": work, "work_unit": unit_work}
+        else:
+            ach = work / (t / 1e3) / 1e9
+            row = {"kernel": kernel, "bound": "hbm", "ms": round(t, 4), "achieved": ach, "unit": "GB/s",
+                   "peak": pk["hbm_gbs"], "frac": ach / pk["hbm_gbs"], "work": work, "work_unit": unit_work}
+        if extra:
+            row.update(extra)
+        rows[name] = row
+
+    add("bin", "k_prologue, k_bin_count, k_scan_tiles, k_scan_fix, k_bin_scatter, k_bin_rank", "hbm", 36.0 * n,
+        "bytes: 36 per atom (read 16, write 16 sorted + 4 permutation)")
+    pairs = short_pairs(n, 0.1, a)
+    add("short", "k_short", "alu", SHORT_FLOP_PER_PAIR * pairs,
+        "FLOP: %.0f per in-cutoff ordered pair (about 20 FMA), %.3g pairs" % (SHORT_FLOP_PER_PAIR, pairs))
+    add("anterp", "k_anterp", "alu", 2.0 * (p ** 3 + 3 * p) * n,
+        "FLOP: p^3 FMA + 3p weight FMA per atom")
+    add("restrict", "k_restrict (all level steps)", "hbm", 4.0 * sum(pts[l] + pts[l + 1] for l in range(len(pts) - 1)),
+        "bytes: read level l, write level l+1 (4 B per point)")
+    add("stencil", "k_pad, k_stencil_ball, k_stencil_box", "alu", f_ball,
+        "FLOP: 2 per kernel sample of the ball (%d) per point of the ball levels, plus the omega' prefilter" % nnz,
+        {"executed_flops": st_flops_exec, "executed_frac": st_flops_exec / (ph["stencil"] / 1e3) / 1e12 /
+         pk["fp32_tflops"] if ph.get("stencil") else None,
+         "executed_note": "the kernel sums mirrored rows first (the samples are even in x and y), so it executes "
+                          "fewer FLOPs than the ball count"})
+    add("prolong", "k_prolong (all level steps)", "hbm", 4.0 * sum(pts[l + 1] + 2 * pts[l] for l in range(len(pts) - 1)),
+        "bytes: read level l+1, read and write level l (4 B per point)")
+    add("interp", "k_interp", "alu", 2.0 * 4 * p ** 3 * n, "FLOP: 4 p^3 FMA per atom (potential and gradient)")
+    add("final", "k_finalize, k_energy", "hbm", 76.0 * n,
+        "bytes: read phi (2 x 4), fields (2 x 16), q (16), perm (4); write phi (4) and F (12) per atom")
+    add("virial", "k_virial_ball, k_virial_box, k_virial_slices, k_virial_out", "alu", f_vir,
+        "FLOP: 2 per unique lag (half of the %d samples) per point of the ball levels (autocorrelation)" % nnz)
+    add("bscale", "k_backward_scale", "hbm", 72.0 * n,
+        "bytes: read phi (2 x 4), fields (2 x 16), q (16), perm (4); write dE/dr (12) and dE/dq (4) per atom")
+    return {"rows": rows, "note": serial_note}
 
 
 def source_sha(src):
@@ -474,26 +577,44 @@ def run_gpu(args):
         ms_e2e = float(t.item())
     e2e_val = world * n / (ms_e2e / 1e3)
 
-    # roofline of the dominant kernel (by measured phase time)
+    # per-kernel rooflines: a serialised pass (every phase on the caller's stream, so each
+    # phase's CUDA-event time is its own), 5 steps after the timed region
+    pk = peaks(dev, clk)
+    plan.profile(True, serial=True)
+    ser = {}
+    for i in range(7):
+        flush.zero_()
+        step()
+        ph, _ = plan.profile_read()
+        if i >= 2:
+            for k, v in ph.items():
+                ser[k] = ser.get(k, 0.0) + v / 5
+    plan.profile(False)
+    st_exec = stencil_flops(plan.params, info, w.cell, w.a, w.p)
+    table = kernel_table(info, n, w.a, w.p, ser, pk, st_exec,
+                         "phases timed one after the other on one stream (msm_profile mode 2), CUDA events, "
+                         "mean of 5 steps after the timed region, L2 flushed before each step")
+    # headline roofline: the dominant kernel (longest serialised phase), its algorithmic work
+    # over its live phase time in the timed region (events on its own stream)
     ph_ms = {k: v / args.steps for k, v in phase_tot.items()}
-    peak_fp32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    st_flops = stencil_flops(plan.params, info, w.cell, w.a, w.p)
-    sr_flops = short_flops(n, 0.1, w.a)
-    cand = {"stencil": (st_flops, ph_ms.get("stencil", 0.0)), "short": (sr_flops, ph_ms.get("short", 0.0))}
-    dom = max(cand, key=lambda k: cand[k][1])
-    fl, tms = cand[dom]
-    achieved = fl / (tms / 1e3) / 1e12 if tms > 0 else 0.0
-    roof = {"bound": "alu", "kernel": {"stencil": "k_stencil_ball (level stencils)",
-                                        "short": "k_short (short-range pairs)"}[dom],
-            "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
-            "traffic": (read_traffic("stencil_ball_1M", "k_stencil.cu") if dom == "stencil"
-                        else read_traffic("short_1M", "k_short.cu")),
-            "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2070 MHz (no FP32 peak in MEASURED_PEAKS.json)",
-            "phase_ms": {k: round(v, 4) for k, v in ph_ms.items()},
-            "phase_note": "the short-range kernel runs on a second stream, concurrently with anterp .. interp; "
-                          "each phase is timed by events on its own stream, so overlapping phases include "
-                          "the contention (the ncu launch list in profiles/ has isolated durations)",
-            "algorithmic_flops": {"stencil": st_flops, "short": sr_flops}}
+    dom = max(table["rows"], key=lambda k: table["rows"][k]["ms"])
+    row = table["rows"][dom]
+    tms = ph_ms.get(dom, 0.0)
+    if row["bound"] == "alu":
+        achieved = row["work"] / (tms / 1e3) / 1e12 if tms > 0 else 0.0
+        peak, unit = pk["fp32_tflops"], "TFLOP/s"
+    else:
+        achieved = row["work"] / (tms / 1e3) / 1e9 if tms > 0 else 0.0
+        peak, unit = pk["hbm_gbs"], "GB/s"
+    traffic_key = {"short": ("short_1M", "k_short.cu"), "stencil": ("stencil_ball_1M", "k_stencil.cu")}.get(dom)
+    roof = {"bound": row["bound"], "kernel": row["kernel"], "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": read_traffic(*traffic_key) if traffic_key else None,
+            "work": row["work"], "work_unit": row["work_unit"], "peak_note": pk["fp32_of"] if row["bound"] == "alu"
+            else "HBM copy bandwidth, %s" % pk["hbm_of"],
+            "live_phase_ms": {k: round(v, 4) for k, v in ph_ms.items()},
+            "phase_note": "live: the short-range kernel runs on a second stream, concurrently with anterp .. "
+                          "interp, so live phase times include the contention; kernels below are serialised",
+            "kernels": table}
 
     batch_res = None
     if not args.no_batch:
@@ -589,9 +710,9 @@ def run_sweep(args):
         torch.cuda.synchronize()
         plan.profile(False)
         ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        fl = {"short": short_flops(n, 0.1, w.a) * 42.0 / 54.0,  # no virial terms in a forward
-              "stencil": stencil_flops(plan.params, info, w.cell, w.a, w.p)}
+        peak = peaks(dev, None)["fp32_tflops"]
+        fl = {"short": SHORT_FLOP_PER_PAIR * short_pairs(n, 0.1, w.a),
+              "stencil": ball_sample_flops(info, w.a, w.p)[0]}
         roof = {k: (fl[k] / (phase[k] / 1e3) / 1e12 / peak if phase.get(k, 0) > 0 else None) for k in fl}
         rows.append({"atoms": n, "M": info["M"][0], "h1": round(info["h1"][0], 4), "levels": info["nlev"],
                      "tuning": [info["anterp_tz"], info["short_block"]],
@@ -602,8 +723,10 @@ def run_sweep(args):
     print(json.dumps({"sweep": rows, "unit": "atoms/s", "workload": "periodic cubes at 0.1 atoms/A^3, uniform "
                       "positions, +/-1 charges; p=4, h=2, a=8; forward only (E, phi, F)",
                       "l2": "flushed (256 MB write) before every step", "data": "synthetic",
-                      "fp32_frac_note": "algorithmic FLOP of the phase / its event time / 80.5 TFLOP/s; the short-range "
-                                        "phase overlaps the grid chain, so both include the contention"}))
+                      "fp32_frac_note": "algorithmic FLOP of the phase (40 per in-cutoff pair; 2 per kernel sample of "
+                                        "the ball per point, plus the prefilter) / its event time / the FP32 FMA peak from the SM count and "
+                                        "maximum clock; the short-range phase overlaps the grid chain, so both "
+                                        "include the contention"}))
 
 
 def run_cells(args):

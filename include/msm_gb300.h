@@ -50,6 +50,15 @@ extern "C" {
 /* bits of the device status word (msm_status) */
 #define MSM_DEV_OUT_OF_CELL 1  /* an atom outside [0, L] along an open axis */
 #define MSM_DEV_NONFINITE 2    /* a NaN or infinite position or charge */
+/* A warning, not an error: a system with a periodic axis whose total charge
+ * is not zero, |sum q| > 1e-5 sum |q| (set by msm_forward). The paper's
+ * method assumes neutral periodic systems (Sec. 4.1: the dropped one-point
+ * top level holds sum q); it prescribes no background correction, so none is
+ * applied and the outputs are those of the method as defined (the dropped
+ * top level, and the left-out lattice-sum constant of slabs and wires, then
+ * omit a term proportional to (sum q)^2). */
+#define MSM_DEV_NON_NEUTRAL 4
+#define MSM_DEV_ERRORS (MSM_DEV_OUT_OF_CELL | MSM_DEV_NONFINITE)  /* bits after which outputs are unspecified */
 
 /* msm_forward flags */
 #define MSM_WANT_FORCES 1      /* compute forces in the forward pass */
@@ -228,6 +237,25 @@ int msm_field(msm_plan plan, void* workspace, float* field, void* stream);
  * msm_forward. Returns MSM_ERR_NO_FORWARD without a prior forward. */
 int msm_force_vjp(msm_plan plan, void* workspace, const float* u, float* dL_dq, float* dL_dpos, void* stream);
 
+/* Vector-Jacobian product of the potentials of the last msm_forward on
+ * workspace (Sec. 3.2.2's derivatives of phi, for training through the
+ * potentials, e.g. an MLIP with predicted charges): for an upstream g,
+ * L = sum_k g_k phi_k. phi = A q with A symmetric (the short-range kernel,
+ * the self term and the grid chain Phi^T K Phi are symmetric), so
+ *   dL/dq_i = (A g)_i                          (the potentials of charges g),
+ *   dL/dr_i = -g_i E_i(q) - q_i E_i(g)          (E = -grad phi, the field).
+ * The library keeps the field of q from the forward, evaluates the method
+ * once more with charges g on the same sorted positions and bins (short
+ * range, anterpolation, restrictions, stencils, prolongations,
+ * interpolation, all in its kernels) and combines the two in a final kernel.
+ *  g        device, n float32, caller's order.
+ *  dL_dq    device, n float32, or NULL.
+ *  dL_dpos  device, n x 3 float32, or NULL.
+ * Stream-ordered. Consumes the workspace: a later msm_backward, msm_field or
+ * msm_force_vjp needs a new msm_forward. Returns MSM_ERR_NO_FORWARD without
+ * a prior forward, MSM_ERR_INVALID_ARG if g is NULL for n > 0. */
+int msm_potential_vjp(msm_plan plan, void* workspace, const float* g, float* dL_dq, float* dL_dpos, void* stream);
+
 /* Autotuner (no counterpart in the paper, whose JAX code leaves launch shapes
  * to XLA): runs one forward on (n, pos, q) to fill workspace, then times each
  * tunable launch shape on those inputs and keeps the fastest for every later
@@ -259,7 +287,12 @@ int msm_debug_offset(msm_plan plan, int which, int level, size_t* offset_bytes, 
  * CUDA event pair on the call's stream around each phase; msm_profile_read
  * synchronises those events and returns, per phase, the milliseconds of the
  * most recent forward and backward (host, ms[MSM_NPHASE]) and the number of
- * kernels those two calls launched (host, *launches). Phases: */
+ * kernels those two calls launched (host, *launches). enable = 1 keeps the
+ * normal schedule (the short-range phase on the library's second stream,
+ * overlapping the grid chain, so phase times include the contention);
+ * enable = 2 runs every phase on the call's stream, one after the other, so
+ * each phase's time is its own (same results); 0 turns profiling off.
+ * Phases: */
 #define MSM_PH_BIN 0        /* binning (counting sort) */
 #define MSM_PH_SHORT 1      /* short-range pair sum */
 #define MSM_PH_ANTERP 2     /* anterpolation */
@@ -322,6 +355,9 @@ int msm_batch_field(msm_batch batch, void* workspace, float* field, void* stream
 /* msm_force_vjp for a batch: u, dL_dpos (sum n) x 3 and dL_dq (sum n), packed like the positions. */
 int msm_batch_force_vjp(msm_batch batch, void* workspace, const float* u, float* dL_dq, float* dL_dpos,
                         void* stream);
+/* msm_potential_vjp for a batch: g, dL_dq (sum n) and dL_dpos (sum n) x 3, packed like the positions. */
+int msm_batch_potential_vjp(msm_batch batch, void* workspace, const float* g, float* dL_dq, float* dL_dpos,
+                            void* stream);
 int msm_batch_status(msm_batch batch, void* workspace, void* stream, int* device_status);
 /* msm_autotune for a batch (all systems share the tuned shapes), and the shapes in use. */
 int msm_batch_autotune(msm_batch batch, void* workspace, size_t workspace_bytes, const float* pos, const float* q,

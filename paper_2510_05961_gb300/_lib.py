@@ -20,6 +20,8 @@ MSM_ERR_NO_FORWARD = 4
 MSM_ERR_CAPACITY = 5
 MSM_DEV_OUT_OF_CELL = 1
 MSM_DEV_NONFINITE = 2
+MSM_DEV_NON_NEUTRAL = 4  # warning: a periodic system with a net charge (computed as defined)
+MSM_DEV_ERRORS = MSM_DEV_OUT_OF_CELL | MSM_DEV_NONFINITE
 MSM_WANT_FORCES = 1
 MSM_WANT_VIRIAL = 2
 
@@ -31,7 +33,7 @@ EXPORTS = [
     "msm_batch_workspace_bytes", "msm_batch_forward", "msm_batch_backward", "msm_batch_status", "msm_profile",
     "msm_profile_read", "msm_forward_noalloc", "msm_autotune", "msm_batch_autotune", "msm_batch_get_tuning",
     "msm_set_tuning", "msm_batch_set_tuning", "msm_field", "msm_batch_field", "msm_plan_set_cell", "msm_force_vjp",
-    "msm_batch_force_vjp",
+    "msm_batch_force_vjp", "msm_potential_vjp", "msm_batch_potential_vjp",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 PHASES = ["bin", "short", "anterp", "restrict", "stencil", "prolong", "interp", "final", "virial", "bscale"]
@@ -92,6 +94,8 @@ def load(path: str = LIB_PATH):
     L.msm_plan_set_cell.argtypes = [_vp, C.POINTER(C.c_double), _vp]
     L.msm_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_batch_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.msm_potential_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.msm_batch_potential_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_batch_field.argtypes = [_vp, _vp, _vp, _vp]
     L.msm_forward_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]
     L.msm_profile.argtypes = [_vp, C.c_int]

@@ -15,17 +15,20 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
                                                      const float* __restrict__ phi_sr, const float* __restrict__ phi_lr,
                                                      const float4* __restrict__ f_sr, const float4* __restrict__ f_lr,
                                                      float* __restrict__ phi, float* __restrict__ forces,
-                                                     double* __restrict__ part_e) {
-  __shared__ double red[kChunk / 32];
+                                                     double* __restrict__ part_e, double* __restrict__ part_q) {
+  __shared__ double red[kChunk / 32][3];
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   int local = it.start + threadIdx.x;
   double e = 0.0;
+  float qs = 0.f, qa = 0.f;  // sum q and sum |q| (FP32 within a warp: only compared with a 1e-5 threshold)
   if ((int)threadIdx.x < it.count && local < S.n) {
     int k = S.atom_off + local;
     int g = perm[k];
     float ph = phi_sr[k] + phi_lr[k];
     e = 0.5 * (double)xq[k].w * (double)ph;
+    qs = xq[k].w;
+    qa = fabsf(qs);
     if (phi) phi[g] = ph;
     if (forces) {
       const float qk = xq[k].w;
@@ -35,30 +38,57 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
       forces[3 * (long long)g + 2] = qk * (a.z + b.z);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, o);
+    qs += __shfl_down_sync(0xffffffffu, qs, o);
+    qa += __shfl_down_sync(0xffffffffu, qa, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = e;
+    red[threadIdx.x >> 5][1] = (double)qs;
+    red[threadIdx.x >> 5][2] = (double)qa;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 3) {
     double s = 0.0;
-    for (int w = 0; w < kChunk / 32; w++) s += red[w];
-    part_e[blockIdx.x] = s;
+    for (int w = 0; w < kChunk / 32; w++) s += red[w][threadIdx.x];
+    if (threadIdx.x == 0) part_e[blockIdx.x] = s;
+    else part_q[2 * blockIdx.x + threadIdx.x - 1] = s;
   }
 }
 
-// one block per system: energy = sum of the system's item partials in order
+// one block per system: energy = sum of the system's item partials in order;
+// a system with a periodic axis and a net charge raises the non-neutral warning
 __global__ void k_energy(const SysDev* __restrict__ sys, const double* __restrict__ part_e,
-                         double* __restrict__ energy) {
-  __shared__ double red[32];
+                         const double* __restrict__ part_q, double* __restrict__ energy, int* __restrict__ status) {
+  __shared__ double red[32][3];
   const SysDev& S = sys[blockIdx.x];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < S.nitem; i += blockDim.x) acc += part_e[S.item0 + i];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  double acc = 0.0, qs = 0.0, qa = 0.0;
+  for (int i = threadIdx.x; i < S.nitem; i += blockDim.x) {
+    acc += part_e[S.item0 + i];
+    qs += part_q[2 * (S.item0 + i)];
+    qa += part_q[2 * (S.item0 + i) + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_down_sync(0xffffffffu, acc, o);
+    qs += __shfl_down_sync(0xffffffffu, qs, o);
+    qa += __shfl_down_sync(0xffffffffu, qa, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = acc;
+    red[threadIdx.x >> 5][1] = qs;
+    red[threadIdx.x >> 5][2] = qa;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    double s = 0.0, sq = 0.0, sa = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      s += red[w][0];
+      sq += red[w][1];
+      sa += red[w][2];
+    }
     energy[blockIdx.x] = s;
+    if ((S.pbc[0] | S.pbc[1] | S.pbc[2]) && fabs(sq) > (double)kNeutralTol * sa) atomicOr(status, kDevNonNeutral);
   }
 }
 
@@ -170,11 +200,11 @@ __global__ void __launch_bounds__(kChunk) k_field(const SysDev* __restrict__ sys
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
                      float* forces, cudaStream_t s) {
   k_finalize<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, phi, forces,
-                                       w.part_e);
+                                       w.part_e, w.part_q);
 }
 
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s) {
-  k_energy<<<nsys, 256, 0, s>>>(t.sys, w.part_e, energy);
+  k_energy<<<nsys, 256, 0, s>>>(t.sys, w.part_e, w.part_q, energy, w.status);
 }
 
 // nslice (1 .. kVirialSlices) slices per system: about 1024 partials each for
@@ -239,6 +269,67 @@ void launch_sort_u(const Work& w, const Tables& t, const AtomItem* items, int ni
 void launch_fvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* hs, float* dq,
                        float* dpos, cudaStream_t s) {
   k_fvjp_final<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.f_sr, hs, w.phi_lr, w.f_lr, dq, dpos);
+}
+
+// potential VJP, before the evaluation with charges g: keep (E(q), q) per
+// sorted atom in keep[k] and put g (caller's order -> sorted) in place of the
+// charges in xq and uq
+__global__ void __launch_bounds__(kChunk) k_pvjp_prep(const SysDev* __restrict__ sys,
+                                                      const AtomItem* __restrict__ items, const int* __restrict__ perm,
+                                                      const float* __restrict__ g, const float4* __restrict__ f_sr,
+                                                      const float4* __restrict__ f_lr, float4* __restrict__ xq,
+                                                      float4* __restrict__ uq, float4* __restrict__ keep) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  const float4 a = f_sr[k], b = f_lr[k];
+  const float gk = g[perm[k]];
+  keep[k] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, xq[k].w);
+  xq[k].w = gk;
+  uq[k].w = gk;
+}
+
+// potential VJP, after the evaluation with charges g: dL/dq = phi(g),
+// dL/dr = -(g E(q) + q E(g)); the charges q go back into xq and uq
+__global__ void __launch_bounds__(kChunk) k_pvjp_final(const SysDev* __restrict__ sys,
+                                                       const AtomItem* __restrict__ items,
+                                                       const int* __restrict__ perm, float4* __restrict__ xq,
+                                                       float4* __restrict__ uq, const float4* __restrict__ keep,
+                                                       const float* __restrict__ phi_sr,
+                                                       const float* __restrict__ phi_lr,
+                                                       const float4* __restrict__ f_sr,
+                                                       const float4* __restrict__ f_lr, float* __restrict__ dq,
+                                                       float* __restrict__ dpos) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  int k = S.atom_off + local;
+  long long gi = perm[k];
+  const float4 eq = keep[k];
+  const float gk = xq[k].w, qk = eq.w;
+  if (dq) dq[gi] = phi_sr[k] + phi_lr[k];
+  if (dpos) {
+    const float4 a = f_sr[k], b = f_lr[k];
+    dpos[3 * gi + 0] = -(gk * eq.x + qk * (a.x + b.x));
+    dpos[3 * gi + 1] = -(gk * eq.y + qk * (a.y + b.y));
+    dpos[3 * gi + 2] = -(gk * eq.z + qk * (a.z + b.z));
+  }
+  xq[k].w = qk;
+  uq[k].w = qk;
+}
+
+void launch_pvjp_prep(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float* g,
+                      cudaStream_t s) {
+  k_pvjp_prep<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, g, w.f_sr, w.f_lr, w.xq, w.uq, w.vjp_u);
+}
+
+void launch_pvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* dq, float* dpos,
+                       cudaStream_t s) {
+  k_pvjp_final<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.uq, w.vjp_u, w.phi_sr, w.phi_lr, w.f_sr,
+                                         w.f_lr, dq, dpos);
 }
 
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s) {

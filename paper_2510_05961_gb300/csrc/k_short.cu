@@ -6,30 +6,30 @@
 //   W0     += -1/2 q_i q_j k_0'(r) d d^T / r,
 // and phi0_i -= q_i gamma(0)/a (the self term, sum_(l>=1) k_l(0)).
 //
-// The virial is not summed pair by pair. With g_ij = q_i q_j k_0'(r)/r and
-// F_i = sum_(j,n) g_ij d_ij, d_ij = r_j + A n - r_i, pairing every ordered
-// pair (i, j, n) with (j, i, -n) gives the exact identity
+// Rectangular cells sum the virial pair by pair (k_short): each term
+// g d d^T is bounded by the cutoff, so its FP32 rounding does not grow with
+// the atoms' distance from the origin. The tilted-cell kernel uses the
+// identity (g_ij = q_i q_j k_0'(r)/r, F_i = sum_(j,n) g_ij d_ij, pairing
+// (i, j, n) with (j, i, -n))
 //   -1/2 sum g d d^T = sum_i r_i F_i^T - 1/2 sum_(i,j,n) (A n) (g d)^T,
-// where the last sum only has terms for periodic images n != 0. Each thread
-// sums its pairs per candidate run (one column, one image), so the image
-// term takes one outer product per run with n != 0 and the pair loop carries
-// no virial arithmetic (6 FMAs per pair less); the symmetric part is kept.
+// whose last sum only has terms for periodic images n != 0; it costs no
+// per-pair virial arithmetic but its rounding grows with |r_i| |F_i|.
 //
-// Candidates: for each (dx, dy) column of cells around i's cell whose xy
-// distance to i is below a, the cells of that column along z within
-// sqrt(a^2 - dxy^2) of i. Cells of one column are consecutive in the sorted
-// order, so each column contributes one contiguous range of atoms per
-// periodic image along z. Sorted positions keep x, y relative to the cell
-// corner and z relative to the column base, so the displacement to a
-// candidate is (ox * edge_x + x_j - x_i, oy * edge_y + y_j - y_i,
-// z_j + kz * L_z - z_i) with no wrap arithmetic per pair. The self pair
-// gives exactly d = 0 and every other image of i lies a period away, so the
-// pair test 0 < r^2 < a^2 excludes exactly (j, image) = (i, 0) (distinct
-// atoms at one point have infinite Coulomb energy and are outside the
-// method's domain). Small periodic cells visit the same cells at several
-// offsets: every image within the cutoff counts. One thread per sorted atom;
-// each thread sums its own pairs, so the result does not depend on
-// scheduling. Whether forces and the virial are wanted are template
+// Rectangular cells (k_short): one thread per sorted atom i. Candidates: for
+// each (dx, dy) column of cells around i's cell whose xy distance to i is
+// below a, the cells of that column along z within sqrt(a^2 - dxy^2) of i.
+// Cells of one column are consecutive in the sorted order, so each column
+// contributes one contiguous range of atoms per periodic image along z.
+// Sorted positions keep x, y relative to the cell corner and z relative to
+// the column base, so the displacement to a candidate is (ox * edge_x + x_j -
+// x_i, oy * edge_y + y_j - y_i, z_j + kz * L_z - z_i) with no wrap arithmetic
+// per pair. The self pair gives exactly d = 0 and every other image of i lies
+// a period away, so the pair test 0 < r^2 < a^2 excludes exactly (j, image) =
+// (i, 0) (distinct atoms at one point have infinite Coulomb energy and are
+// outside the method's domain). Small periodic cells visit the same cells at
+// several offsets: every image within the cutoff counts. One thread per
+// sorted atom; each thread sums its own pairs, so the result does not depend
+// on scheduling. Whether forces and the virial are wanted are template
 // parameters, so the pair loop carries no runtime flags.
 #include "msm_internal.h"
 
@@ -69,13 +69,6 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
   int local = it.start + slot;
   bool active = slot < it.count && local < S.n;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  // image term sum_runs (A n)(sum q_j k_0'(r)/r d)^T of this thread, symmetric
-  // part; in shared memory (rarely touched) to keep registers for the pair loop
-  __shared__ float wimg[6][NB];
-  if (WW) {
-#pragma unroll
-    for (int c = 0; c < 6; c++) wimg[c][threadIdx.x] = 0.f;
-  }
   if (active) {
     const int k = S.atom_off + local;
     const float4 xi = xq[k];
@@ -93,13 +86,15 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
     // faces; culling keeps a margin of 2e-4 cell edges (enough for C <= 512)
     constexpr float mg = 2e-4f;
     float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    // sum of q_j k_0'(r)/r d d^T over the pairs (xx yy zz xy xz yz): each term is
+    // bounded by the cutoff, so its rounding does not grow with |r_i|
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
       const int ux = ci[0] + ox;
       if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
       // image shift along x, in cells: C is a power of two on a periodic axis,
       // and an open axis only visits u in [0, C)
-      const int nxc = (ux >> S.cshift[0]) << S.cshift[0];
-      const int wx = ux - nxc;
+      const int wx = ux - ((ux >> S.cshift[0]) << S.cshift[0]);
       const float bx = (float)ox * ex - xi.x;  // d_x = bx + x_j
       const float mx = fmaxf((ox > 0 ? bx : (ox < 0 ? -(bx + ex) : 0.f)) - mg * ex, 0.f);
       for (int oy = -S.nnbr[1]; oy <= S.nnbr[1]; oy++) {
@@ -109,8 +104,7 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
         const float my = fmaxf((oy > 0 ? by : (oy < 0 ? -(by + ey) : 0.f)) - mg * ey, 0.f);
         const float rxy2 = mx * mx + my * my;
         if (rxy2 >= a2) continue;
-        const int nyc = (uy >> S.cshift[1]) << S.cshift[1];
-        const int wy = uy - nyc;
+        const int wy = uy - ((uy >> S.cshift[1]) << S.cshift[1]);
         const float zr2 = a2 - rxy2;  // > 0
         const float zr = zr2 * rsqrt_nrm(zr2) + mg * S.edge[2];
         int zlo = (int)floorf((xi.z - zr) * inv_ez), zhi = (int)floorf((xi.z + zr) * inv_ez);
@@ -125,44 +119,42 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
           const int wz = uz - (kz << S.cshift[2]);
           const int wend = min(Cz - 1, wz + (zhi - uz));
           const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
-          const float bz = image_shift(kz, S.Ld[2], xi.z);
-          float sx = 0.f, sy = 0.f, sz = 0.f;  // sum of q_j k_0'(r)/r d over this run
+          const float bz = image_shift(kz, S.Ld[2], xi.z);  // d_z = bz + z_j
           for (int j = jb; j < je; j++) {
             const float4 xj = xq[j];
             const float dx = bx + xj.x, dy = by + xj.y, dz = bz + xj.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 < a2 && r2 > 0.f) {
-            const float rinv = rsqrt_nrm(r2);
-            const float s = 1.0f - r2 * inv_a2;
-            float g = gc[P - 1];
+            if (r2 < a2 && r2 > 0.f) {
+              const float rinv = rsqrt_nrm(r2);
+              const float s = 1.0f - r2 * inv_a2;
+              float g = gc[P - 1];
 #pragma unroll
-            for (int t = P - 2; t >= 0; t--) g = fmaf(g, s, gc[t]);
-            ph = fmaf(xj.w, rinv - g, ph);  // k_0 = 1/r - gamma(r/a)/a
-            if (WF || WW) {
-              float dg = gdc[P - 2];
+              for (int t = P - 2; t >= 0; t--) g = fmaf(g, s, gc[t]);
+              ph = fmaf(xj.w, rinv - g, ph);  // k_0 = 1/r - gamma(r/a)/a
+              if (WF || WW) {
+                float dg = gdc[P - 2];
 #pragma unroll
-              for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, s, gdc[t]);
-              // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
-              const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
-              sx = fmaf(fr, dx, sx);
-              sy = fmaf(fr, dy, sy);
-              sz = fmaf(fr, dz, sz);
+                for (int t = P - 3; t >= 0; t--) dg = fmaf(dg, s, gdc[t]);
+                // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
+                const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
+                if (WW) {
+                  const float gx = fr * dx, gy = fr * dy, gz = fr * dz;
+                  fx += gx;
+                  fy += gy;
+                  fz += gz;
+                  v[0] = fmaf(gx, dx, v[0]);
+                  v[1] = fmaf(gy, dy, v[1]);
+                  v[2] = fmaf(gz, dz, v[2]);
+                  v[3] = fmaf(gx, dy, v[3]);
+                  v[4] = fmaf(gx, dz, v[4]);
+                  v[5] = fmaf(gy, dz, v[5]);
+                } else {
+                  fx = fmaf(fr, dx, fx);
+                  fy = fmaf(fr, dy, fy);
+                  fz = fmaf(fr, dz, fz);
+                }
+              }
             }
-          }
-        }
-          fx += sx;
-          fy += sy;
-          fz += sz;
-          if (WW && (nxc | nyc | kz) != 0) {
-            // image term of the run: (A n) s^T, symmetric part
-            const float tx = (float)nxc * ex, ty = (float)nyc * ey, tz = (float)kz * S.Lf[2];
-            float* wi = &wimg[0][threadIdx.x];
-            wi[0] = fmaf(tx, sx, wi[0]);
-            wi[NB] = fmaf(ty, sy, wi[NB]);
-            wi[2 * NB] = fmaf(tz, sz, wi[2 * NB]);
-            wi[3 * NB] = fmaf(0.5f * tx, sy, fmaf(0.5f * ty, sx, wi[3 * NB]));
-            wi[4 * NB] = fmaf(0.5f * tx, sz, fmaf(0.5f * tz, sx, wi[4 * NB]));
-            wi[5 * NB] = fmaf(0.5f * ty, sz, fmaf(0.5f * tz, sy, wi[5 * NB]));
           }
           uz += wend - wz + 1;
         }
@@ -171,26 +163,20 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
     phi_sr[k] = ph - xi.w * S.self_coef;
     if (WF) f_sr[k] = make_float4(fx, fy, fz, 0.f);  // field of the other charges; the force is q_i times it
     if (WW) {
-      // q_i [sym(r_i f^T) - 1/2 image term], r_i relative to the cell's lower
-      // corner for x, y and the sorted z (the frame the displacements use)
-      const float rx = (float)ci[0] * ex + xi.x, ry = (float)ci[1] * ey + xi.y, rz = xi.z;
-      const float hq = -0.5f * xi.w;
-      w6[0] = xi.w * (rx * fx) + hq * wimg[0][threadIdx.x];
-      w6[1] = xi.w * (ry * fy) + hq * wimg[1][threadIdx.x];
-      w6[2] = xi.w * (rz * fz) + hq * wimg[2][threadIdx.x];
-      w6[3] = xi.w * (0.5f * (rx * fy + ry * fx)) + hq * wimg[3][threadIdx.x];
-      w6[4] = xi.w * (0.5f * (rx * fz + rz * fx)) + hq * wimg[4][threadIdx.x];
-      w6[5] = xi.w * (0.5f * (ry * fz + rz * fy)) + hq * wimg[5][threadIdx.x];
+      const float hq = -0.5f * xi.w;  // W0 += -1/2 q_i sum q_j k_0'(r)/r d d^T
+#pragma unroll
+      for (int c = 0; c < 6; c++) w6[c] = hq * v[c];
     }
   }
   if (!WW) return;
-  // per-warp FP64 partials of the six virial components (fixed order, no block barrier)
+  // per-warp partials of the six virial components: FP32 across the warp's 32
+  // atoms, FP64 from there on (fixed order, no block barrier)
   const int lane = threadIdx.x & 31, wid = slot >> 5;
 #pragma unroll
   for (int c = 0; c < 6; c++) {
-    double v = (double)w6[c];
+    float v = w6[c];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) part_w0[6 * ((long long)item * kChunkWarps + wid) + c] = v;
+    if (lane == 0) part_w0[6 * ((long long)item * kChunkWarps + wid) + c] = (double)v;
   }
 }
 

@@ -79,14 +79,19 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
     launch_prologue(w, E.total_cells, E.d_sys, E.single ? n_single : -1, s);
     launch_bin(w, t, E.d_atom_items, nai, E.total_cells, n_total, pos, q, s);
   }
-  // fork: the short-range pairs (side stream) overlap the grid chain (caller's stream)
-  cudaEventRecord(E.ev_fork, s);
-  cudaStreamWaitEvent(E.side, E.ev_fork, 0);
-  {
-    Phase ph(E, MSM_PH_SHORT, E.side);
-    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, E.side, E.p, E.short_code());
+  // fork: the short-range pairs (side stream) overlap the grid chain (caller's
+  // stream); serial profiling keeps them on the caller's stream
+  cudaStream_t ss = E.serial ? s : E.side;
+  if (!E.serial) {
+    cudaEventRecord(E.ev_fork, s);
+    cudaStreamWaitEvent(E.side, E.ev_fork, 0);
   }
-  cudaEventRecord(E.ev_join, E.side);
+  {
+    Phase ph(E, MSM_PH_SHORT, ss);
+    launch_short(w, t, E.d_atom_items, nai, want_f, want_w, ss, E.p,
+                 E.short_code());
+  }
+  if (!E.serial) cudaEventRecord(E.ev_join, E.side);
   {
     Phase ph(E, MSM_PH_ANTERP, s);
     launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz);
@@ -115,7 +120,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
     Phase ph(E, MSM_PH_INTERP, s);
     launch_interp(w, t, E.d_atom_items, nai, want_f, s, E.p);
   }
-  cudaStreamWaitEvent(s, E.ev_join, 0);  // join
+  if (!E.serial) cudaStreamWaitEvent(s, E.ev_join, 0);  // join
   {
     Phase ph(E, MSM_PH_FINAL, s);
     launch_finalize(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, s);
@@ -288,7 +293,9 @@ int msm_profile(msm_plan plan, int enable) {
   if (enable && !E.ev[0])
     for (auto& e : E.ev)
       if (cudaEventCreate(&e) != cudaSuccess) return set_err(MSM_ERR_CUDA, "cudaEventCreate failed");
+  if (enable < 0 || enable > 2) return set_err(MSM_ERR_INVALID_ARG, "enable must be 0, 1 or 2");
   E.profiling = enable != 0;
+  E.serial = enable == 2;
   return MSM_OK;
 }
 
@@ -443,6 +450,62 @@ static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* 
   }
   E.have_fwd = false;
   return check_launch("msm_force_vjp");
+}
+
+// Vector-Jacobian product of the potentials of the last forward on ws for an
+// upstream g (n, caller's order): L = sum_k g_k phi_k, phi = A q with A
+// symmetric, so dL/dq = A g and dL/dr_k = -g_k E_k(q) - q_k E_k(g). The field
+// of q is kept, the method runs once more with charges g on the forward's
+// sorted positions and bins (short range on the second stream, overlapping
+// the grid chain, as in the forward), and a last kernel combines the two.
+// Consumes the workspace.
+static int run_potential_vjp(Engine& E, void* ws, const float* g, float* dq, float* dpos, cudaStream_t s) {
+  if (!E.have_fwd || ws != E.last_ws)
+    return set_err(MSM_ERR_NO_FORWARD, "msm_potential_vjp needs a prior msm_forward on this workspace");
+  if (E.last_n > 0 && !g) return set_err(MSM_ERR_INVALID_ARG, "g must not be NULL");
+  Work w = E.resolve(ws);
+  Tables t = E.tables();
+  const int nai = (int)E.atom_items.size();
+  if ((E.last_flags & MSM_WANT_FORCES) == 0) {
+    const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
+    launch_short(w, t, E.d_atom_items, nai, true, had_w, s, E.p, E.short_code());
+    launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
+  }
+  if (E.last_n > 0) {
+    launch_pvjp_prep(w, t, E.d_atom_items, nai, g, s);
+    cudaEventRecord(E.ev_fork, s);
+    cudaStreamWaitEvent(E.side, E.ev_fork, 0);
+    launch_short(w, t, E.d_atom_items, nai, true, false, E.side, E.p, E.short_code());
+    cudaEventRecord(E.ev_join, E.side);
+    launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz);
+    for (int l = 1; l < E.maxcomp; l++) {
+      int a = E.restrict_off[l - 1], b = E.restrict_off[l];
+      launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
+    }
+    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
+    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
+    launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
+    for (int l = E.maxcomp - 1; l >= 1; l--) {
+      int a = E.prolong_off[l - 1], b = E.prolong_off[l];
+      launch_prolong(w, t, E.d_pro_items + a, b - a, s, E.p);
+    }
+    launch_interp(w, t, E.d_atom_items, nai, true, s, E.p);
+    cudaStreamWaitEvent(s, E.ev_join, 0);
+    launch_pvjp_final(w, t, E.d_atom_items, nai, dq, dpos, s);
+  }
+  E.have_fwd = false;
+  return check_launch("msm_potential_vjp");
+}
+
+int msm_potential_vjp(msm_plan plan, void* workspace, const float* g, float* dL_dq, float* dL_dpos, void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  return run_potential_vjp(plan->eng, workspace, g, dL_dq, dL_dpos, (cudaStream_t)stream);
+}
+
+int msm_batch_potential_vjp(msm_batch batch, void* workspace, const float* g, float* dL_dq, float* dL_dpos,
+                            void* stream) {
+  if (!batch) return set_err(MSM_ERR_INVALID_ARG, "batch must not be NULL");
+  return run_potential_vjp(batch->eng, workspace, g, dL_dq, dL_dpos, (cudaStream_t)stream);
 }
 
 int msm_force_vjp(msm_plan plan, void* workspace, const float* u, float* dL_dq, float* dL_dpos, void* stream) {

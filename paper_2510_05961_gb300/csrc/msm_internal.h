@@ -32,6 +32,8 @@ constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x pl
 // device status bits (mirrors MSM_DEV_* of the public header)
 constexpr int kDevOutOfCell = 1;
 constexpr int kDevNonFinite = 2;
+constexpr int kDevNonNeutral = 4;
+constexpr float kNeutralTol = 1e-5f;  // |sum q| > kNeutralTol * sum |q| counts as non-neutral
 
 struct SysDev {
   double Ld[3];     // cell lengths (FP64: periodic image shifts of the pair displacements)
@@ -116,6 +118,7 @@ struct Work {
   float* phi_lr;   // long-range potential, sorted
   float4* f_lr;    // long-range field -grad phi^(1+) (force / q), sorted
   double* part_e;  // per atom item: 1/2 sum q phi
+  double* part_q;  // per atom item: sum q and sum |q|
   double* part_w0; // per warp of each atom item: 6 short-range virial components
   double* part_wg; // per virial item: 6 grid virial components
   double* part_vs; // per system and reduction slice: 6 virial components
@@ -158,7 +161,7 @@ void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, i
 // outputs (k_final.cu)
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
                      float* forces, cudaStream_t s);
-void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);
+void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);  // also flags non-neutral periodic systems
 void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, const int* vitem_off,
                        const double* grad, double* virial, cudaStream_t s);
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
@@ -173,6 +176,11 @@ void launch_interp_hess(const Work& w, const Tables& t, const AtomItem* items, i
                         cudaStream_t s, int p);
 void launch_anterp_dipole(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p,
                           int tz, const float4* us);
+// vector-Jacobian product of the potentials (k_final.cu)
+void launch_pvjp_prep(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float* g,
+                      cudaStream_t s);
+void launch_pvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* dq, float* dpos,
+                       cudaStream_t s);
 void launch_fvjp_final(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float4* hs, float* dq,
                        float* dpos, cudaStream_t s);
 // dynamic cell (k_cell.cu): new system descriptor (alone, or with the ball stencils of a periodic p = 4 plan)

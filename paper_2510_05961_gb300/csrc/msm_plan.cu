@@ -1158,6 +1158,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_f_sr = take(sizeof(float4) * N);
   L_f_lr = take(sizeof(float4) * N);
   L_part_e = take(sizeof(double) * atom_items.size());
+  L_part_q = take(sizeof(double) * 2 * atom_items.size());
   L_part_w0 = take(sizeof(double) * 6 * kChunkWarps * atom_items.size());
   L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(ball_items.size() + box_items.size(), 1));
   L_part_vs = take(sizeof(double) * 6 * 64 * (size_t)nsys);
@@ -1380,6 +1381,7 @@ Work Engine::resolve(void* ws) const {
   w.f_sr = (float4*)(b + L_f_sr);
   w.f_lr = (float4*)(b + L_f_lr);
   w.part_e = (double*)(b + L_part_e);
+  w.part_q = (double*)(b + L_part_q);
   w.part_w0 = (double*)(b + L_part_w0);
   w.part_wg = (double*)(b + L_part_wg);
   w.part_vs = (double*)(b + L_part_vs);

@@ -95,7 +95,7 @@ struct Engine {
   int* d_voff = nullptr;
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
-      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_w0, L_part_wg, L_part_vs, L_grid, L_vjp_u,
+      L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_q, L_part_w0, L_part_wg, L_part_vs, L_grid, L_vjp_u,
       L_vjp_h;
   size_t ws_bytes = 0;
   // state of the last forward pass
@@ -105,6 +105,7 @@ struct Engine {
   int last_n = 0;
   // phase timing (msm_profile) and launch counts
   bool profiling = false;
+  bool serial = false;              // profiling mode 2: every phase on the caller's stream
   cudaEvent_t ev[2 * 10] = {};
   bool ev_used[10] = {};
   int launches_fwd = 0, launches_bwd = 0;

@@ -134,6 +134,18 @@ class Plan:
                                        _stream(self.device)))
         return gq, gp
 
+    def potential_vjp(self, g, dq=True, dpos=True):
+        """(dL/dq, dL/dpos) for L = sum_k g_k phi_k of the last forward (g: (n,) float32 device):
+        dL/dq = A g, dL/dr = -g E(q) - q E(g), computed by the library (msm_potential_vjp).
+        Consumes the workspace: a later backward needs a new forward."""
+        n = self._n
+        g = g.detach().to(device=self.device, dtype=torch.float32).contiguous()
+        gq = torch.empty(n, dtype=torch.float32, device=self.device) if dq else None
+        gp = torch.empty((n, 3), dtype=torch.float32, device=self.device) if dpos else None
+        L.check(self.lib.msm_potential_vjp(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gq), _ptr(gp),
+                                           _stream(self.device)))
+        return gq, gp
+
     def autotune(self, pos, q):
         """Time the tunable launch shapes on these inputs and keep the fastest; returns them.
         A new forward is needed before the next backward."""
@@ -191,9 +203,10 @@ class Plan:
         self._copy_stream.synchronize()
         return oE, op, oq, oW
 
-    def profile(self, enable=True):
-        """Record CUDA-event times per phase of every forward/backward."""
-        L.check(self.lib.msm_profile(self.handle, 1 if enable else 0))
+    def profile(self, enable=True, serial=False):
+        """Record CUDA-event times per phase of every forward/backward; serial=True runs
+        every phase on the caller's stream (no overlap), so each phase time is its own."""
+        L.check(self.lib.msm_profile(self.handle, (2 if serial else 1) if enable else 0))
 
     def profile_read(self):
         """(dict phase -> ms of the last forward + backward, kernels launched by them)."""
@@ -206,16 +219,16 @@ class Plan:
 class MSMFunction(torch.autograd.Function):
     """(E, phi, F) of (pos, q) through the library.
 
-    Backward takes upstream gradients on E, phi and F:
-      E:   dE/dpos = -F, dE/dq = phi (the library's adjoint kernels); plan.last_virial
+    Backward takes upstream gradients on E, phi and F, each through a library call:
+      E:   msm_backward (the adjoint kernels): dE/dpos = -F, dE/dq = phi; plan.last_virial
            holds W * dL/dE.
-      phi: phi = A q with A symmetric (short-range kernel, self term and the grid chain
-           Phi^T K Phi are all symmetric), so for L = sum_i g_i phi_i
-             dL/dq = A g                           (potentials of charges g),
-             dL/dr_k = -g_k E_k(q) - q_k E_k(g)    (E = -grad phi, the field),
-           one more evaluation with charges g on the same positions.
+      phi: msm_potential_vjp: phi = A q with A symmetric, so for L = sum_i g_i phi_i
+           dL/dq = A g and dL/dr_k = -g_k E_k(q) - q_k E_k(g), one more evaluation with
+           charges g on the same sorted positions.
       F:   msm_force_vjp (dipole potential and Hessian-vector products).
-    The plan's workspace is reused: backward must follow its own forward."""
+    The plan's workspace is reused: backward must follow its own forward. The two VJPs
+    consume the workspace, so when both upstreams are given the forward is run again
+    between them."""
 
     @staticmethod
     def forward(ctx, pos, q, plan):
@@ -241,20 +254,15 @@ class MSMFunction(torch.autograd.Function):
 
         if gE is not None:
             gp, gq, _ = plan.backward(gE, dpos=ctx.need[0], dq=ctx.need[1], virial=True)
-        Eq = plan.field() if use_phi else None  # field of q, before the workspace is reused
+        if use_phi:
+            pq, pp = plan.potential_vjp(gphi, dq=ctx.need[1], dpos=ctx.need[0])
+            gq, gp = acc(gq, pq), acc(gp, pp)
         if use_F:
+            if use_phi:  # the potential VJP consumed the workspace
+                pos, q = ctx.saved_tensors
+                plan.forward(pos, q, forces=True, virial=False, phi=False)
             fq, fp = plan.force_vjp(gF, dq=ctx.need[1], dpos=ctx.need[0])
             gq, gp = acc(gq, fq), acc(gp, fp)
-        if use_phi:
-            pos, q = ctx.saved_tensors
-            g = gphi.detach().to(torch.float32).contiguous()
-            _, phig, _ = plan.forward(pos, g, forces=False, virial=False, phi=True)
-            if ctx.need[1]:
-                gq = phig if gq is None else gq + phig
-            if ctx.need[0]:
-                Eg = plan.field()
-                t = -(g[:, None] * Eq + q[:, None] * Eg)
-                gp = t if gp is None else gp + t
         return gp, gq, None
 
 
@@ -330,6 +338,15 @@ class Batch:
         L.check(self.lib.msm_batch_backward(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gp), _ptr(gq), _ptr(W),
                                             _stream(self.device)))
         return gp, gq, (None if W is None else W.view(self.nsys, 3, 3))
+
+    def potential_vjp(self, g, dq=True, dpos=True):
+        """Plan.potential_vjp for the packed atoms of all systems."""
+        g = g.detach().to(device=self.device, dtype=torch.float32).contiguous()
+        gq = torch.empty(self.ntot, dtype=torch.float32, device=self.device) if dq else None
+        gp = torch.empty((self.ntot, 3), dtype=torch.float32, device=self.device) if dpos else None
+        L.check(self.lib.msm_batch_potential_vjp(self.handle, _ptr(self.workspace), _ptr(g), _ptr(gq), _ptr(gp),
+                                                 _stream(self.device)))
+        return gq, gp
 
     def force_vjp(self, u, dq=True, dpos=True):
         """Plan.force_vjp for the packed atoms of all systems."""

@@ -21,6 +21,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2510_05961_gb300 import Batch, Plan, build, msm_energy  # noqa: E402
 from paper_2510_05961_gb300 import workloads as W  # noqa: E402
+from msm_testutil import expected_status  # noqa: E402
 
 E_TOL = 1e-5
 F_TOL = 1e-4
@@ -55,7 +56,7 @@ def gpu_run(w, plan=None, forces=True, virial=True):
         gp, gq, Wv = plan.backward(g)
         out.update(W=Wv.cpu().numpy(), dpos=gp.cpu().numpy(), dq=gq.cpu().numpy())
     torch.cuda.synchronize()
-    assert plan.status() == 0
+    assert plan.status() == expected_status(w)
     return out
 
 
@@ -211,7 +212,7 @@ def test_field_matches_oracle(key):
     plan.forward(pos, q, forces=False)
     assert rel_rms(plan.field().cpu().numpy(), ref["F"] / qq) <= F_TOL
     torch.cuda.synchronize()
-    assert plan.status() == 0
+    assert plan.status() == expected_status(w)
 
 
 def _oracle_directional(w, u, eps=1e-4):
@@ -239,7 +240,7 @@ def test_gradient_through_forces(key):
     E, phi, F = msm_outputs(pos, q, plan)
     (torch.from_numpy(u).to(DEV) * F).sum().backward()
     torch.cuda.synchronize()
-    assert plan.status() == 0
+    assert plan.status() == expected_status(w)
     dq_ref, dr_ref = _oracle_directional(w, u.astype(np.float64))
     assert rel_rms(q.grad.cpu().numpy(), dq_ref) <= F_TOL
     assert rel_rms(pos.grad.cpu().numpy(), dr_ref) <= F_TOL
@@ -294,6 +295,55 @@ def test_gradient_through_phi(key):
     assert rel_rms(pos.grad.cpu().numpy(), dpos_ref) <= F_TOL
 
 
+@pytest.mark.parametrize("key", ["periodic_20001", "slab_3000", "open_c1"])
+def test_potential_vjp_call(key):
+    # msm_potential_vjp through the C ABI (no autograd): L = sum g phi gives
+    # dL/dq = phi(g) and dL/dr = -g E(q) - q E(g), against the oracle evaluated at charges q and g
+    w = WORKLOADS[key]()
+    rng = np.random.default_rng(81)
+    g = (rng.choice([-1.0, 1.0], w.n) * rng.uniform(0.5, 1.5, w.n)).astype(np.float32)
+    plan = make_plan(w)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    plan.forward(pos, q, forces=False, virial=False)  # the call computes the fields it needs
+    dq, dpos = plan.potential_vjp(torch.from_numpy(g).to(DEV))
+    torch.cuda.synchronize()
+    P, rq = _oracle(key)
+    rg = _oracle_eval(w, g)
+    qd, gd = w.q.astype(np.float64)[:, None], g.astype(np.float64)[:, None]
+    assert rel_rms(dq.cpu().numpy(), rg["phi"]) <= F_TOL
+    assert rel_rms(dpos.cpu().numpy(), -gd * (rq["F"] / qd) - qd * (rg["F"] / gd)) <= F_TOL
+    # the call consumed the workspace
+    with pytest.raises(RuntimeError):
+        plan.backward(torch.ones(1, dtype=torch.float64, device=DEV))
+
+
+def test_batch_potential_vjp_call():
+    import oracle as O
+    O.build()
+    systems = W.batch_systems(nsys=12, seed=82, nmax=500)
+    batch = Batch(systems, device=DEV)
+    pos = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(DEV)
+    q = torch.from_numpy(np.concatenate([s.q for s in systems])).to(DEV)
+    rng = np.random.default_rng(83)
+    g = rng.normal(0.0, 1.0, size=batch.ntot).astype(np.float32)
+    batch.forward(pos, q, forces=True, virial=False)
+    dq, dpos = batch.potential_vjp(torch.from_numpy(g).to(DEV))
+    dq, dpos = dq.cpu().numpy(), dpos.cpu().numpy()
+    off = 0
+    for s in systems:
+        n = s.n
+        P = O.plan_for(s)
+        rq = O.msm(P, s.pos.astype(np.float64), s.q.astype(np.float64), forces=True, virial=False)
+        gs = g[off:off + n].astype(np.float64)
+        rg = O.msm(P, s.pos.astype(np.float64), gs, forces=True, virial=False)
+        qd = s.q.astype(np.float64)[:, None]
+        assert rel_rms(dq[off:off + n], rg["phi"]) <= F_TOL
+        ref = -gs[:, None] * (rq["F"] / qd) - qd * (rg["F"] / gs[:, None])
+        assert rel_rms(dpos[off:off + n], ref) <= F_TOL
+        off += n
+
+
 def test_slab_against_ewald2d():
     # the slab's top level (k_L summed over the 2-D lattice) on the GPU against the 2-D Ewald sum,
     # at the accuracy the method reaches with p = 8 (the periodic MSM reaches the same against 3-D Ewald)
@@ -333,7 +383,7 @@ def test_batch_of_mixed_boundaries():
     E, phi, F = batch.forward(pos, q, forces=True, virial=True)
     gp, gq, Wb = batch.backward(torch.ones(len(systems), dtype=torch.float64, device=DEV))
     torch.cuda.synchronize()
-    assert batch.status() == 0
+    assert batch.status() == expected_status(systems)
     E, phi, F, Wb = E.cpu().numpy(), phi.cpu().numpy(), F.cpu().numpy(), Wb.cpu().numpy()
     off = 0
     for s, sysw in enumerate(systems):
@@ -447,7 +497,7 @@ def test_batch_matches_single_and_oracle():
     g = torch.ones(len(systems), dtype=torch.float64, device=DEV)
     gp, gq, Wb = batch.backward(g)
     torch.cuda.synchronize()
-    assert batch.status() == 0
+    assert batch.status() == expected_status(systems)
     E = E.cpu().numpy()
     phi = phi.cpu().numpy()
     F = F.cpu().numpy()
@@ -464,10 +514,12 @@ def test_batch_matches_single_and_oracle():
         assert np.abs(Wb[s] - ref["W"]).max() <= F_TOL * np.abs(ref["W"]).max(), s
         # a batch plan applies its small levels (<= 512 points) as folded dense boxes of
         # K = omega'^3 * s, a single plan applies s to the omega'-prefiltered grid: equal in
-        # exact arithmetic, so the two differ by FP32 rounding only; the measured gaps
-        # are printed, and the bound is set a few times above them
+        # exact arithmetic, so the two differ by FP32 rounding only: relative to the energy
+        # plus, for energies that cancel, the FP32 rounding floor 1e-7 sum |q phi| / 2; the
+        # measured gaps (in units of that bound) are printed
         single = gpu_run(sysw)
-        gaps.append(abs(single["E"] - E[s]) / abs(E[s]))
-        assert abs(single["E"] - E[s]) <= BATCH_SINGLE_TOL * abs(E[s]) + 1e-9, (s, gaps[-1])
+        bound = BATCH_SINGLE_TOL * abs(E[s]) + 1e-7 * 0.5 * float(np.abs(sysw.q * ref["phi"]).sum())
+        gaps.append(abs(single["E"] - E[s]) / bound)
+        assert abs(single["E"] - E[s]) <= bound, (s, gaps[-1])
         off += n
-    print("batch vs single relative energy gaps: max %.3g, median %.3g" % (max(gaps), float(np.median(gaps))))
+    print("batch vs single energy gaps / bound: max %.3g, median %.3g" % (max(gaps), float(np.median(gaps))))
