@@ -58,7 +58,11 @@ extern "C" {
  * top level, and the left-out lattice-sum constant of slabs and wires, then
  * omit a term proportional to (sum q)^2). */
 #define MSM_DEV_NON_NEUTRAL 4
-#define MSM_DEV_ERRORS (MSM_DEV_OUT_OF_CELL | MSM_DEV_NONFINITE)  /* bits after which outputs are unspecified */
+/* Debug builds only (compiled with -DMSM_CHECKS=1): a kernel found a
+ * data-dependent index outside its array and skipped the access. A stand-in
+ * for a device memory checker; normal builds never set it. */
+#define MSM_DEV_CHECK 8
+#define MSM_DEV_ERRORS (MSM_DEV_OUT_OF_CELL | MSM_DEV_NONFINITE | MSM_DEV_CHECK)  /* outputs unspecified */
 
 /* msm_forward flags */
 #define MSM_WANT_FORCES 1      /* compute forces in the forward pass */

@@ -21,7 +21,8 @@ MSM_ERR_CAPACITY = 5
 MSM_DEV_OUT_OF_CELL = 1
 MSM_DEV_NONFINITE = 2
 MSM_DEV_NON_NEUTRAL = 4  # warning: a periodic system with a net charge (computed as defined)
-MSM_DEV_ERRORS = MSM_DEV_OUT_OF_CELL | MSM_DEV_NONFINITE
+MSM_DEV_CHECK = 8  # debug builds: an out-of-range index was caught (the access skipped)
+MSM_DEV_ERRORS = MSM_DEV_OUT_OF_CELL | MSM_DEV_NONFINITE | MSM_DEV_CHECK
 MSM_WANT_FORCES = 1
 MSM_WANT_VIRIAL = 2
 
@@ -62,11 +63,14 @@ _lib = None
 _vp = C.c_void_p
 
 
-def load(path: str = LIB_PATH):
-    """Load the shared library (built by build.py / __graft_entry__.build())."""
+def load(path: str = None):
+    """Load the shared library (built by build.py / __graft_entry__.build()). The
+    environment variable MSM_GB300_LIB selects another build of it (the debug
+    build with device-side index checks, libmsm_gb300_checks.so)."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("MSM_GB300_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError("libmsm_gb300.so not found at %s: build it first (python -m paper_2510_05961_gb300.build)"
                           % path)

@@ -17,9 +17,10 @@
 namespace msm {
 
 __global__ void k_prologue(int* __restrict__ cell_count, int total_cells, int* __restrict__ status,
-                           SysDev* __restrict__ sys, int n_single) {
+                           SysDev* __restrict__ sys, int nsys, int n_single) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   for (int c = t; c < total_cells; c += gridDim.x * blockDim.x) cell_count[c] = 0;
+  for (int s = t; s < nsys; s += gridDim.x * blockDim.x) sys[s].status = status;
   if (t == 0) {
     *status = 0;
     if (n_single >= 0) sys[0].n = n_single;
@@ -173,7 +174,8 @@ __global__ void k_bin_scatter(const SysDev* __restrict__ sys, const AtomItem* __
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
-  bucket[cell_start[S.cell_off + cell_id[g]] + slot[g]] = g;
+  const int b = cell_start[S.cell_off + cell_id[g]] + slot[g];
+  if (MSM_CHECK(S, b >= S.atom_off && b < S.atom_off + S.n)) bucket[b] = g;
 }
 
 __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
@@ -193,6 +195,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   int g = S.atom_off + local;
   int cell = cell_id[g];
   int b = cell_start[S.cell_off + cell], e = cell_start[S.cell_off + cell + 1];
+  if (!MSM_CHECK(S, b >= S.atom_off && e <= S.atom_off + S.n && b <= e)) return;
   int rank = 0;
   for (int t = b; t < e; t++) rank += (bucket[t] < g);
   int dst = b + rank;
@@ -263,11 +266,11 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   uq[dst] = make_float4(u[0], u[1], u[2], qq);
 }
 
-void launch_prologue(const Work& w, int total_cells, SysDev* sys, int n_single, cudaStream_t s) {
+void launch_prologue(const Work& w, int total_cells, SysDev* sys, int nsys, int n_single, cudaStream_t s) {
   int blocks = (total_cells + 255) / 256;
   if (blocks < 1) blocks = 1;
   if (blocks > 1024) blocks = 1024;
-  k_prologue<<<blocks, 256, 0, s>>>(w.cell_count, total_cells, w.status, sys, n_single);
+  k_prologue<<<blocks, 256, 0, s>>>(w.cell_count, total_cells, w.status, sys, nsys, n_single);
 }
 
 void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitems, int total_cells,

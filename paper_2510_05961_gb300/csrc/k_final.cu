@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
   if ((int)threadIdx.x < it.count && local < S.n) {
     int k = S.atom_off + local;
     int g = perm[k];
+    if (!MSM_CHECK(S, g >= S.atom_off && g < S.atom_off + S.n)) g = S.atom_off;
     float ph = phi_sr[k] + phi_lr[k];
     e = 0.5 * (double)xq[k].w * (double)ph;
     qs = xq[k].w;
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kChunk) k_backward_scale(const SysDev* __restr
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int k = S.atom_off + local;
   int g = perm[k];
+  if (!MSM_CHECK(S, g >= S.atom_off && g < S.atom_off + S.n)) return;
   float gr = (float)grad[it.sys];
   if (dE_dq) dE_dq[g] = gr * (phi_sr[k] + phi_lr[k]);
   if (dE_dpos) {

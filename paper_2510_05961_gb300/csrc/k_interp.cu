@@ -256,8 +256,9 @@ __global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__
             }
           }
         };
-        const int je = cs[wend + 1];
+        int je = cs[wend + 1];
         int j = cs[wz];
+        if (!MSM_CHECK(S, j >= S.atom_off && je <= S.atom_off + S.n)) je = j;
         const float4 none = make_float4(0.f, 0.f, 0.f, 0.f);
         for (; j + 3 < je; j += 4) {  // four loads in flight
           const float4 u0 = uq[j], u1 = uq[j + 1], u2 = uq[j + 2], u3 = uq[j + 3];
@@ -316,6 +317,11 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
     }
   }
   const float* e = grid + L.e_off;
+#if MSM_CHECKS
+  for (int d = 0; d < 3; d++)
+    for (int j = 0; j < P; j++)
+      if (!MSM_CHECK(S, ix[d][j] >= 0 && ix[d][j] < L.n[d])) ix[d][j] = 0;
+#endif
   float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int jx = 0; jx < P; jx++) {

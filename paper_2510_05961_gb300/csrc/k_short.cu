@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
           const int kz = uz >> S.cshift[2];
           const int wz = uz - (kz << S.cshift[2]);
           const int wend = min(Cz - 1, wz + (zhi - uz));
-          const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+          int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+          if (!MSM_CHECK(S, jb >= S.atom_off && je <= S.atom_off + S.n)) je = jb;
           const float bz = image_shift(kz, S.Ld[2], xi.z);  // d_z = bz + z_j
           for (int j = jb; j < je; j++) {
             const float4 xj = xq[j];
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(kChunk) k_short_fvjp(const SysDev* __restrict_
         const int kz = floordiv_s(uz, Cz);
         const int wz = uz - kz * Cz;
         const int wend = min(Cz - 1, wz + (zhi - uz));
-        const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+        int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+        if (!MSM_CHECK(S, jb >= S.atom_off && je <= S.atom_off + S.n)) je = jb;
         const float bz = image_shift(kz, S.Ld[2], xi.z);
         for (int j = jb; j < je; j++) {
           const float4 xj = xq[j];
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kChunk) k_short_fvjp_tri(const SysDev* __restr
         const int kz = floordiv_s(uz, Cz);
         const int wz = uz - kz * Cz;
         const int wend = min(Cz - 1, wz + (zhi - uz));
-        const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+        int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+        if (!MSM_CHECK(S, jb >= S.atom_off && je <= S.atom_off + S.n)) je = jb;
         const float bx = (float)(bxy[0] + kz * S.Ad[6] - (double)xi.x);
         const float by = (float)(bxy[1] + kz * S.Ad[7] - (double)xi.y);
         const float bz = (float)(bxy[2] + kz * S.Ad[8] - (double)xi.z);
@@ -425,7 +428,8 @@ __global__ void __launch_bounds__(kChunk) k_short_tri(const SysDev* __restrict__
           const int kz = floordiv_s(uz, Cz);
           const int wz = uz - kz * Cz;
           const int wend = min(Cz - 1, wz + (zhi - uz));
-          const int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+          int jb = cell_start[colbase + wz], je = cell_start[colbase + wend + 1];
+          if (!MSM_CHECK(S, jb >= S.atom_off && je <= S.atom_off + S.n)) je = jb;
           const float bx = (float)(bxy[0] + kz * S.Ad[6] - (double)xi.x);
           const float by = (float)(bxy[1] + kz * S.Ad[7] - (double)xi.y);
           const float bz = (float)(bxy[2] + kz * S.Ad[8] - (double)xi.z);

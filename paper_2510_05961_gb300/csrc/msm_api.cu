@@ -5,6 +5,8 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "msm_plan.h"
 #include <cmath>
 
@@ -32,12 +34,18 @@ static int check_launch(const char* where) {
   return MSM_OK;
 }
 
-// phase timing: an event pair around each phase when profiling is on
+// phase timing: an event pair around each phase when profiling is on, and an
+// NVTX range named after the phase (host side: it brackets the launches, so
+// a profiler's timeline groups each phase's kernels)
+static const char* const kPhaseName[MSM_NPHASE] = {"msm:bin",    "msm:short",  "msm:anterp", "msm:restrict",
+                                                   "msm:stencil", "msm:prolong", "msm:interp", "msm:final",
+                                                   "msm:virial", "msm:bscale"};
 struct Phase {
   Engine& E;
   int ph;
   cudaStream_t s;
   Phase(Engine& e, int p, cudaStream_t st) : E(e), ph(p), s(st) {
+    nvtxRangePushA(kPhaseName[ph]);
     if (E.profiling) {
       cudaEventRecord(E.ev[2 * ph], s);
       E.ev_used[ph] = true;
@@ -45,6 +53,7 @@ struct Phase {
   }
   ~Phase() {
     if (E.profiling) cudaEventRecord(E.ev[2 * ph + 1], s);
+    nvtxRangePop();
   }
 };
 
@@ -76,7 +85,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   const int nai = (int)E.atom_items.size();
   {
     Phase ph(E, MSM_PH_BIN, s);
-    launch_prologue(w, E.total_cells, E.d_sys, E.single ? n_single : -1, s);
+    launch_prologue(w, E.total_cells, E.d_sys, E.nsys, E.single ? n_single : -1, s);
     launch_bin(w, t, E.d_atom_items, nai, E.total_cells, n_total, pos, q, s);
   }
   // fork: the short-range pairs (side stream) overlap the grid chain (caller's

@@ -33,9 +33,11 @@ constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x pl
 constexpr int kDevOutOfCell = 1;
 constexpr int kDevNonFinite = 2;
 constexpr int kDevNonNeutral = 4;
+constexpr int kDevCheck = 8;  // MSM_CHECKS builds: an index outside its array was caught and the access skipped
 constexpr float kNeutralTol = 1e-5f;  // |sum q| > kNeutralTol * sum |q| counts as non-neutral
 
 struct SysDev {
+  int* status;      // the call's device status word (written by the prologue; used by MSM_CHECKS builds)
   double Ld[3];     // cell lengths (FP64: periodic image shifts of the pair displacements)
   double edged[3];  // binning cell edges (FP64)
   int n;            // atoms of this system
@@ -72,6 +74,20 @@ struct SysDev {
   float Jg[9];      // A^-1 diag(M): Cartesian gradient from level-1 grid derivatives
   float reach[3];   // a / (distance between cell faces): fractional reach of the cutoff per axis
 };
+
+// Debug builds (-DMSM_CHECKS=1, build.build(checks=True)): kernels test their
+// data-dependent indices before the access; a failed test sets kDevCheck in
+// the status word (through S.status) and skips the access, so the call ends
+// with the bit set instead of touching memory outside an array. Normal builds
+// compile the tests away.
+#ifndef MSM_CHECKS
+#define MSM_CHECKS 0
+#endif
+#if MSM_CHECKS
+#define MSM_CHECK(S, cond) ((cond) ? true : (atomicOr((S).status, kDevCheck), false))
+#else
+#define MSM_CHECK(S, cond) true
+#endif
 
 struct LevDev {
   int sys, level;           // owning system, level number (1-based)
@@ -136,7 +152,7 @@ struct Tables {
 
 // ---------------------------------------------------------------- launchers
 // binning (k_bin.cu)
-void launch_prologue(const Work& w, int total_cells, SysDev* sys, int n_single, cudaStream_t s);
+void launch_prologue(const Work& w, int total_cells, SysDev* sys, int nsys, int n_single, cudaStream_t s);
 void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitems, int total_cells,
                 int total_atoms, const float* pos, const float* q, cudaStream_t s);
 // short range (k_short.cu)

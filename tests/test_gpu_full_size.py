@@ -55,11 +55,21 @@ def fwd_bwd(w):
                 dpos=gp.cpu().numpy(), dq=gq.cpu().numpy())
 
 
-def check(r, ref, q):
-    # 1e-5 relative, with an FP32 rounding floor for energies that cancel:
-    # 1e-7 of the sum of the magnitudes of the terms 1/2 q_i phi_i
-    floor = 1e-7 * 0.5 * float(np.abs(np.asarray(q, np.float64) * ref["phi"]).sum())
-    assert abs(r["E"] - ref["E"]) <= E_TOL * abs(ref["E"]) + floor, (r["E"], ref["E"], floor)
+COND_FLOOR = 100.0  # condition number of the energy sum above which the FP32 rounding floor applies
+
+
+def check(r, ref, q, name=""):
+    # 1e-5 relative; for energies whose terms cancel (condition number
+    # kappa = sum |q_i phi_i| / |2E| above 100, where 1e-7 of the terms exceeds
+    # 1e-5 of E) an FP32 rounding floor of 1e-7 of the sum of the magnitudes of
+    # the terms 1/2 q_i phi_i is added; the systems that need it are printed
+    terms = 0.5 * float(np.abs(np.asarray(q, np.float64) * ref["phi"]).sum())
+    kappa = terms / max(abs(ref["E"]), 1e-300)
+    floor = 1e-7 * terms if kappa > COND_FLOOR else 0.0
+    if floor:
+        print("energy floor applied: %s kappa %.0f, |dE| %.3g, bound %.3g" %
+              (name, kappa, abs(r["E"] - ref["E"]), E_TOL * abs(ref["E"]) + floor))
+    assert abs(r["E"] - ref["E"]) <= E_TOL * abs(ref["E"]) + floor, (name, r["E"], ref["E"], kappa)
     assert rel_rms(r["F"], ref["F"]) <= F_TOL
     assert rel_rms(r["phi"], ref["phi"]) <= F_TOL
     assert rel_rms(r["dq"], ref["phi"]) <= F_TOL
@@ -101,7 +111,7 @@ def test_batch_512_full_size():
         ref = oracle_msm(sysw)
         r = dict(E=float(E[s]), phi=phi[off:off + n], F=F[off:off + n], W=Wb[s], dpos=gp[off:off + n],
                  dq=gq[off:off + n])
-        check(r, ref, sysw.q)
+        check(r, ref, sysw.q, "batch system %d" % s)
         off += n
 
 
