@@ -211,6 +211,24 @@ int msm_forward(msm_plan plan, void* workspace, size_t workspace_bytes, int n, c
 int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,
                  double* virial, void* stream);
 
+/* End-to-end evaluation on host buffers: copies the inputs to the device (into
+ * the workspace), runs msm_forward (forces, virial) and msm_backward with
+ * dL/dE = 1, copies E, dE/dpos (= -F), dE/dq (= phi) and, if virial_host is
+ * not NULL, W back, and waits for the copies. The per-atom gradients are
+ * copied while the grid virial runs (a second stream). Unlike the other
+ * calls this one returns only after the results are on the host.
+ *  pos_host      host, n x 3 float32 (page-locked memory makes the copies asynchronous).
+ *  q_host        host, n float32.
+ *  energy_host   host, 1 double.
+ *  dE_dpos_host  host, n x 3 float32; dE_dq_host host, n float32.
+ *  virial_host   host, 9 doubles (row-major 3x3), or NULL to skip the virial.
+ * The workspace must have msm_workspace_bytes (it includes the staging arrays);
+ * afterwards it holds the forward's state like msm_forward (a later msm_field,
+ * msm_force_vjp or msm_potential_vjp may follow). */
+int msm_evaluate_host(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos_host,
+                      const float* q_host, double* energy_host, float* dE_dpos_host, float* dE_dq_host,
+                      double* virial_host, void* stream);
+
 /* The field E_i = -grad phi(r_i) of the MSM potential at every atom (the
  * gradient of Eq. U_total's phi with respect to the evaluation point, both
  * the short-range and the interpolated part; the force is F_i = q_i E_i),

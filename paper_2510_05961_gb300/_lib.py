@@ -34,7 +34,7 @@ EXPORTS = [
     "msm_batch_workspace_bytes", "msm_batch_forward", "msm_batch_backward", "msm_batch_status", "msm_profile",
     "msm_profile_read", "msm_forward_noalloc", "msm_autotune", "msm_batch_autotune", "msm_batch_get_tuning",
     "msm_set_tuning", "msm_batch_set_tuning", "msm_field", "msm_batch_field", "msm_plan_set_cell", "msm_force_vjp",
-    "msm_batch_force_vjp", "msm_potential_vjp", "msm_batch_potential_vjp",
+    "msm_batch_force_vjp", "msm_potential_vjp", "msm_batch_potential_vjp", "msm_evaluate_host",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 PHASES = ["bin", "short", "anterp", "restrict", "stencil", "prolong", "interp", "final", "virial", "bscale"]
@@ -99,6 +99,7 @@ def load(path: str = None):
     L.msm_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_batch_force_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_potential_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.msm_evaluate_host.argtypes = [_vp, _vp, C.c_size_t, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_batch_potential_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.msm_batch_field.argtypes = [_vp, _vp, _vp, _vp]
     L.msm_forward_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]

@@ -334,6 +334,14 @@ void launch_pvjp_final(const Work& w, const Tables& t, const AtomItem* items, in
                                          w.f_lr, dq, dpos);
 }
 
+__global__ void k_fill_d(double* __restrict__ p, int n, double v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+void launch_fill(double* p, int n, double v, cudaStream_t s) {
+  if (n > 0) k_fill_d<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
+}
+
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s) {
   k_field<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.f_sr, w.f_lr, field);
 }

@@ -187,6 +187,47 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   return check_launch("msm_backward");
 }
 
+// End-to-end evaluation on host buffers (msm_evaluate_host): inputs copied into
+// the workspace's staging arrays, forward (forces, virial) and backward with
+// dL/dE = 1 on the caller's stream; E and the per-atom gradients are copied back
+// on a second stream while the grid virial runs, then the virial; waits for both.
+static int run_evaluate_host(Engine& E, void* ws, size_t ws_bytes, int n, const float* pos_h, const float* q_h,
+                             double* e_h, float* dpos_h, float* dq_h, double* w_h, cudaStream_t s) {
+  if (!ws || !e_h) return set_err(MSM_ERR_INVALID_ARG, "workspace and energy_host must not be NULL");
+  if (n > 0 && (!pos_h || !q_h || !dpos_h || !dq_h))
+    return set_err(MSM_ERR_INVALID_ARG, "host positions, charges and gradient buffers must not be NULL");
+  if (ws_bytes < E.ws_bytes) return set_err(MSM_ERR_CAPACITY, "workspace smaller than msm_workspace_bytes");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return set_err(MSM_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if (!E.copy && (cudaStreamCreateWithFlags(&E.copy, cudaStreamNonBlocking) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&E.ev_grad, cudaEventDisableTiming) != cudaSuccess))
+    return set_err(MSM_ERR_CUDA, "msm_evaluate_host: stream or event creation failed");
+  Work w = E.resolve(ws);
+  const int nsys = E.nsys;
+  if (n > 0 && (cudaMemcpyAsync(w.io_pos, pos_h, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(w.io_q, q_h, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess))
+    return set_err(MSM_ERR_CUDA, "msm_evaluate_host: input copy failed");
+  launch_fill(w.io_e + nsys, nsys, 1.0, s);  // dL/dE = 1
+  int rc = run_forward(E, ws, ws_bytes, n, w.io_pos, w.io_q, w.io_e, nullptr, nullptr,
+                       MSM_WANT_FORCES | (w_h ? MSM_WANT_VIRIAL : 0), s);
+  if (rc) return rc;
+  if ((rc = run_backward(E, ws, w.io_e + nsys, w.io_dpos, w.io_dq, nullptr, s))) return rc;
+  cudaEventRecord(E.ev_grad, s);
+  cudaStreamWaitEvent(E.copy, E.ev_grad, 0);
+  bool ok = cudaMemcpyAsync(e_h, w.io_e, sizeof(double), cudaMemcpyDeviceToHost, E.copy) == cudaSuccess;
+  if (n > 0)
+    ok = ok && cudaMemcpyAsync(dpos_h, w.io_dpos, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToHost, E.copy) ==
+                   cudaSuccess &&
+         cudaMemcpyAsync(dq_h, w.io_dq, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, E.copy) == cudaSuccess;
+  if (ok && w_h) {
+    if ((rc = run_backward(E, ws, w.io_e + nsys, nullptr, nullptr, w.io_e + 2 * nsys, s))) return rc;
+    ok = cudaMemcpyAsync(w_h, w.io_e + 2 * nsys, sizeof(double) * 9, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  }
+  if (!ok) return set_err(MSM_ERR_CUDA, "msm_evaluate_host: output copy failed");
+  if (cudaStreamSynchronize(E.copy) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return set_err(MSM_ERR_CUDA, std::string("msm_evaluate_host: ") + cudaGetErrorString(cudaGetLastError()));
+  return check_launch("msm_evaluate_host");
+}
+
 // field -grad phi at every atom from the last forward on ws (forces / q, no
 // division); a forward without forces gets its field parts computed here
 static int run_field(Engine& E, void* ws, float* field, cudaStream_t s) {
@@ -411,6 +452,15 @@ int msm_forward(msm_plan plan, void* workspace, size_t workspace_bytes, int n, c
   if (n < 0 || n > plan->eng.total_atoms) return set_err(MSM_ERR_CAPACITY, "n outside [0, max_atoms]");
   return run_forward(plan->eng, workspace, workspace_bytes, n, pos, q, energy, phi, forces, flags,
                      (cudaStream_t)stream);
+}
+
+int msm_evaluate_host(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos_host,
+                      const float* q_host, double* energy_host, float* dE_dpos_host, float* dE_dq_host,
+                      double* virial_host, void* stream) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  if (n < 0 || n > plan->eng.total_atoms) return set_err(MSM_ERR_CAPACITY, "n outside [0, max_atoms]");
+  return run_evaluate_host(plan->eng, workspace, workspace_bytes, n, pos_host, q_host, energy_host, dE_dpos_host,
+                           dE_dq_host, virial_host, (cudaStream_t)stream);
 }
 
 int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, float* dE_dpos, float* dE_dq,

@@ -141,6 +141,12 @@ struct Work {
   float* grid;     // grid pool
   float4* vjp_u;   // force vector-Jacobian product: upstream (u, q), sorted
   float4* vjp_h;   // force vector-Jacobian product: short-range rows of H u and psi, sorted
+  // staging of msm_evaluate_host (caller's atom order)
+  float* io_pos;   // n x 3 positions
+  float* io_q;     // n charges
+  float* io_dpos;  // n x 3 dE/dpos
+  float* io_dq;    // n dE/dq
+  double* io_e;    // energy per system, then dL/dE = 1 per system, then 9 virial components per system
 };
 
 struct Tables {
@@ -183,6 +189,7 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s);
+void launch_fill(double* p, int n, double v, cudaStream_t s);
 // vector-Jacobian product of the forces (k_final.cu, k_short.cu, k_interp.cu)
 void launch_sort_u(const Work& w, const Tables& t, const AtomItem* items, int nitems, const float* u, float4* us,
                    cudaStream_t s);

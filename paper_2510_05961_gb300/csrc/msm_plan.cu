@@ -1165,6 +1165,11 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_grid = take(sizeof(float) * std::max<long long>(grid_floats, 1));
   L_vjp_u = take(sizeof(float4) * N);
   L_vjp_h = take(sizeof(float4) * N);
+  L_io_pos = take(sizeof(float) * 3 * N);
+  L_io_q = take(sizeof(float) * N);
+  L_io_dpos = take(sizeof(float) * 3 * N);
+  L_io_dq = take(sizeof(float) * N);
+  L_io_e = take(sizeof(double) * 11 * (size_t)std::max(nsys, 1));
   ws_bytes = off;
   return MSM_OK;
 }
@@ -1346,6 +1351,8 @@ Engine::~Engine() {
     if (e) cudaEventDestroy(e);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
+  if (ev_grad) cudaEventDestroy(ev_grad);
+  if (copy) cudaStreamDestroy(copy);
   if (side) cudaStreamDestroy(side);
   cudaFree(d_sys);
   cudaFree(d_lev);
@@ -1381,6 +1388,11 @@ Work Engine::resolve(void* ws) const {
   w.f_sr = (float4*)(b + L_f_sr);
   w.f_lr = (float4*)(b + L_f_lr);
   w.part_e = (double*)(b + L_part_e);
+  w.io_pos = (float*)(b + L_io_pos);
+  w.io_q = (float*)(b + L_io_q);
+  w.io_dpos = (float*)(b + L_io_dpos);
+  w.io_dq = (float*)(b + L_io_dq);
+  w.io_e = (double*)(b + L_io_e);
   w.part_q = (double*)(b + L_part_q);
   w.part_w0 = (double*)(b + L_part_w0);
   w.part_wg = (double*)(b + L_part_wg);

@@ -45,7 +45,6 @@ class Plan:
             nb = C.c_size_t()
             L.check(self.lib.msm_workspace_bytes(self.handle, C.byref(nb)))
             self.workspace = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
-        self._copy_stream = None
         self.max_atoms = int(max_atoms)
         self.last_virial = None
         self._n = None
@@ -165,42 +164,22 @@ class Plan:
         return st.value
 
     def evaluate_host(self, pos, q, virial=True, pinned_out=None):
-        """End-to-end call on host tensors: copy in, forward + backward, copy out.
-
-        pos (n, 3) and q (n,) are float32 CPU tensors (pinned for asynchronous
-        copies). Returns host (E, dE/dpos, dE/dq, virial) after synchronising.
-        The backward runs in two calls: the per-atom gradients first, whose
-        copy to the host then overlaps the grid virial on a second stream.
-        """
+        """End-to-end call on host tensors (msm_evaluate_host): the library copies the
+        inputs in, runs forward + backward and copies E, dE/dpos, dE/dq and the virial
+        out, then returns. pos (n, 3) and q (n,) are float32 CPU tensors (pinned for
+        asynchronous copies); pinned_out optionally gives the four host outputs."""
         n = int(pos.shape[0])
-        dpos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
-        dq = torch.empty(n, dtype=torch.float32, device=self.device)
-        dpos.copy_(pos, non_blocking=True)
-        dq.copy_(q, non_blocking=True)
-        E, _, _ = self.forward(dpos, dq, forces=True, virial=virial, phi=False)
-        g = torch.ones(1, dtype=torch.float64, device=self.device)
-        gp, gq, _ = self.backward(g, dpos=True, dq=True, virial=False)
+        assert pos.dtype == torch.float32 and q.dtype == torch.float32 and pos.is_contiguous() and q.is_contiguous()
         if pinned_out is None:
             pinned_out = (torch.empty(1, dtype=torch.float64, pin_memory=True),
                           torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
                           torch.empty(n, dtype=torch.float32, pin_memory=True),
                           torch.empty((3, 3), dtype=torch.float64, pin_memory=True))
         oE, op, oq, oW = pinned_out
-        cur = torch.cuda.current_stream(self.device)
-        if self._copy_stream is None:
-            self._copy_stream = torch.cuda.Stream(self.device)
-        ready = torch.cuda.Event()
-        ready.record(cur)
-        with torch.cuda.stream(self._copy_stream):
-            self._copy_stream.wait_event(ready)
-            oE.copy_(E, non_blocking=True)
-            op.copy_(gp, non_blocking=True)
-            oq.copy_(gq, non_blocking=True)
-        if virial:
-            _, _, W = self.backward(g, dpos=False, dq=False, virial=True)
-            oW.copy_(W, non_blocking=True)
-        cur.synchronize()
-        self._copy_stream.synchronize()
+        L.check(self.lib.msm_evaluate_host(self.handle, _ptr(self.workspace), self.workspace.numel(), n, _ptr(pos),
+                                           _ptr(q), _ptr(oE), _ptr(op), _ptr(oq), _ptr(oW) if virial else None,
+                                           _stream(self.device)))
+        self._n = n
         return oE, op, oq, oW
 
     def profile(self, enable=True, serial=False):

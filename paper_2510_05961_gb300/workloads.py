@@ -249,6 +249,39 @@ def lattice_on_grid(ncell=4, a0=4.0, pbc=(1, 1, 1), seed=6000, qsigma=0.1, h=2.0
                     tuple(pbc), h, a, p)
 
 
+def sheet(n=400, side=24.0, thickness=2.0, periodic=True, seed=7000, h=0.8, a=8.0, p=8):
+    """A two-dimensional arrangement: n charges in the plane z = 0 of a cell
+    side x side x thickness (periodic in x, y and open along z, a slab of zero
+    thickness; or open along all axes), jittered square lattice (no two charges
+    closer than 0.4 of the spacing), charges +/-1 alternating on the lattice,
+    neutral for even n."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(math.sqrt(n)))
+    sp = side / m
+    idx = np.stack(np.meshgrid(np.arange(m), np.arange(m), indexing="ij"), axis=-1).reshape(-1, 2)[:n]
+    pos = np.zeros((n, 3))
+    pos[:, :2] = (idx + 0.5 + rng.uniform(-0.3, 0.3, size=(n, 2))) * sp
+    q = np.where(idx.sum(1) % 2 == 0, 1.0, -1.0)
+    q -= q.mean()
+    return Workload("sheet_%d" % n, pos.astype(np.float32), q.astype(np.float32), (side, side, thickness),
+                    (1, 1, 0) if periodic else (0, 0, 0), h, a, p)
+
+
+def chain(n=200, length=80.0, width=2.0, periodic=True, seed=7100, h=0.8, a=8.0, p=8):
+    """A one-dimensional arrangement: n charges on the line x = y = 0 of a cell
+    width x width x length (periodic along z and open across, a wire of zero
+    width; or open along all axes), jittered lattice along z, charges +/-1
+    alternating, neutral for even n."""
+    rng = np.random.default_rng(seed)
+    sp = length / n
+    pos = np.zeros((n, 3))
+    pos[:, 2] = (np.arange(n) + 0.5 + rng.uniform(-0.3, 0.3, size=n)) * sp
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    q -= q.mean()
+    return Workload("chain_%d" % n, pos.astype(np.float32), q.astype(np.float32), (width, width, length),
+                    (0, 0, 1) if periodic else (0, 0, 0), h, a, p)
+
+
 def scaling_sizes(kmax=14):
     """The sweep sizes n = 1000 * 2**k, k = 0 .. kmax."""
     return [1000 * 2 ** k for k in range(kmax + 1)]

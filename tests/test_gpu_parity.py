@@ -84,6 +84,11 @@ WORKLOADS = {
     # exact interpolation of the grid kernels (qi_mode 1): dense boxes on every level
     "open_qi1": lambda: dataclasses.replace(W.open_cluster(n=400, seed=38), qi_mode=1),
     "periodic_qi1": lambda: dataclasses.replace(W.random_box(300, seed=39, h=2.0, a=4.0), qi_mode=1),
+    # one- and two-dimensional arrangements: charges on a plane or a line of a thin cell
+    "sheet_slab": lambda: W.sheet(periodic=True, p=4, h=1.0),
+    "sheet_open": lambda: W.sheet(periodic=False, p=6, h=0.8),
+    "chain_wire": lambda: W.chain(periodic=True, p=4, h=1.0),
+    "chain_open": lambda: W.chain(periodic=False, p=4, h=1.0),
 }
 
 
@@ -94,7 +99,8 @@ def _oracle(key):
 
 
 # ---------------------------------------------------------------- binning
-@pytest.mark.parametrize("key", ["open_c1", "periodic_20001", "slab_3000", "tiny_periodic_40", "water_600"])
+@pytest.mark.parametrize("key", ["open_c1", "periodic_20001", "slab_3000", "tiny_periodic_40", "water_600",
+                                 "sheet_slab", "chain_open"])
 def test_binning_bit_exact(key):
     import oracle as O
     O.build()
@@ -342,6 +348,22 @@ def test_batch_potential_vjp_call():
         ref = -gs[:, None] * (rq["F"] / qd) - qd * (rg["F"] / gs[:, None])
         assert rel_rms(dpos[off:off + n], ref) <= F_TOL
         off += n
+
+
+@pytest.mark.parametrize("kind", ["sheet", "chain"])
+def test_lower_dimensional_against_exact_sums(kind):
+    # a sheet (charges on the plane z = 0, periodic in x, y) against the 2-D Ewald sum and a chain
+    # (charges on the z axis, periodic along z) against the 1-D Ewald sum, on the GPU with p = 8
+    import oracle as O
+    O.build()
+    w = W.sheet(periodic=True, p=8, h=0.8) if kind == "sheet" else W.chain(periodic=True, p=8, h=0.8)
+    r = gpu_run(w)
+    pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+    if kind == "sheet":
+        _, phi_ref = O.ewald2d(w.cell[0], w.cell[1], pos, q)
+    else:
+        _, phi_ref = O.ewald1d(w.cell[2], pos, q, axis=2)
+    assert rel_rms(r["phi"], phi_ref) <= 5e-5
 
 
 def test_slab_against_ewald2d():

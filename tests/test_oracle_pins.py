@@ -896,3 +896,42 @@ def test_rocksalt32_gradients_against_stored_differences(oracle):
     Wr = r["W"]
     ref = np.array([Wr[0, 0], Wr[1, 1], Wr[2, 2], Wr[0, 1], Wr[0, 2], Wr[1, 2]])
     assert np.abs(vir - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("periodic", [True, False], ids=["slab", "open"])
+def test_sheet_against_exact_sums(oracle, periodic):
+    """A two-dimensional arrangement (charges in the plane z = 0 of a cell 2 A
+    thick): the MSM against the 2-D Ewald sum (periodic in x, y) or the direct
+    Coulomb sum (open), potentials to the method's accuracy and improving from
+    p = 4 to p = 8."""
+    from paper_2510_05961_gb300 import workloads as W
+    errs = []
+    for p, h in [(4, 1.0), (8, 0.8)]:
+        w = W.sheet(periodic=periodic, p=p, h=h)
+        pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+        r = oracle.msm(oracle.plan_for(w), pos, q, forces=False, virial=False)
+        if periodic:
+            _, phi_ref = oracle.ewald2d(w.cell[0], w.cell[1], pos, q)
+        else:
+            _, phi_ref, _ = oracle.direct_open(pos, q)
+        errs.append(np.sqrt(((r["phi"] - phi_ref) ** 2).mean() / (phi_ref ** 2).mean()))
+    assert errs[1] < errs[0] and errs[1] < 3e-5 and errs[0] < 2e-4, errs
+
+
+@pytest.mark.parametrize("periodic", [True, False], ids=["wire", "open"])
+def test_chain_against_exact_sums(oracle, periodic):
+    """A one-dimensional arrangement (charges on the line x = y = 0): the MSM
+    against the 1-D Ewald sum (periodic along z) or the direct Coulomb sum
+    (open), improving from p = 4 to p = 8."""
+    from paper_2510_05961_gb300 import workloads as W
+    errs = []
+    for p, h in [(4, 1.0), (8, 0.8)]:
+        w = W.chain(periodic=periodic, p=p, h=h)
+        pos, q = w.pos.astype(np.float64), w.q.astype(np.float64)
+        r = oracle.msm(oracle.plan_for(w), pos, q, forces=False, virial=False)
+        if periodic:
+            _, phi_ref = oracle.ewald1d(w.cell[2], pos, q, axis=2)
+        else:
+            _, phi_ref, _ = oracle.direct_open(pos, q)
+        errs.append(np.sqrt(((r["phi"] - phi_ref) ** 2).mean() / (phi_ref ** 2).mean()))
+    assert errs[1] < errs[0] and errs[1] < 5e-6 and errs[0] < 5e-5, errs
