@@ -6,14 +6,23 @@
 //   W0     += -1/2 q_i q_j k_0'(r) d d^T / r,
 // and phi0_i -= q_i gamma(0)/a (the self term, sum_(l>=1) k_l(0)).
 //
-// Rectangular cells sum the virial pair by pair (k_short): each term
-// g d d^T is bounded by the cutoff, so its FP32 rounding does not grow with
-// the atoms' distance from the origin. The tilted-cell kernel uses the
-// identity (g_ij = q_i q_j k_0'(r)/r, F_i = sum_(j,n) g_ij d_ij, pairing
-// (i, j, n) with (j, i, -n))
+// Virial. With g_ij = q_i q_j k_0'(r)/r and F_i = sum_(j,n) g_ij d_ij, write
+// d = xi_j + t - xi_i with xi the atom's offset from a reference point of its
+// own and t the offset between the two reference points (periodic image
+// included). Pairing every ordered pair (i, j, n) with (j, i, -n) turns the
+// sum over xi_j into one over xi_i, which gives the exact identity
+//   -1/2 sum g d d^T = sum_i xi_i F_i^T - 1/2 sum_i sum_runs t (sum_run g d)^T.
+// Rectangular cells (k_short) use it for the x and y components with xi the
+// offset from the cell corner (at most one cell edge) and t the column offset
+// (ox e_x, oy e_y), constant over a neighbour column, so the x, y parts cost
+// one outer product per column; the z components (where the sorted z is
+// measured from the column base, up to L_z) are summed pair by pair. Every term
+// is then bounded by a few cell edges times |g d|, so the rounding does not
+// grow with the atoms' distance from the origin. The tilted-cell kernel uses
+// the identity with xi = r_i (the whole position) and t = A n, i.e.
 //   -1/2 sum g d d^T = sum_i r_i F_i^T - 1/2 sum_(i,j,n) (A n) (g d)^T,
-// whose last sum only has terms for periodic images n != 0; it costs no
-// per-pair virial arithmetic but its rounding grows with |r_i| |F_i|.
+// whose last sum only has terms for periodic images n != 0; its rounding
+// grows with |r_i| |F_i|.
 //
 // Rectangular cells (k_short): one thread per sorted atom i. Candidates: for
 // each (dx, dy) column of cells around i's cell whose xy distance to i is
@@ -86,10 +95,11 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
     // faces; culling keeps a margin of 2e-4 cell edges (enough for C <= 512)
     constexpr float mg = 2e-4f;
     float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    // sum of q_j k_0'(r)/r d d^T over the pairs (xx yy zz xy xz yz): each term is
-    // bounded by the cutoff, so its rounding does not grow with |r_i|
+    // virial sums (xx yy zz xy xz yz): xx, yy, xy the column terms t (sum g d)^T of
+    // the identity above, zz, xz, yz sum q_j k_0'(r)/r d_z d pair by pair
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int ox = -S.nnbr[0]; ox <= S.nnbr[0]; ox++) {
+      const float tx = (float)ox * ex;  // offset between the cell corners of i and of this column
       const int ux = ci[0] + ox;
       if (!S.pbc[0] && (ux < 0 || ux >= Cx)) continue;
       // image shift along x, in cells: C is a power of two on a periodic axis,
@@ -113,6 +123,7 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
           zhi = min(zhi, Cz - 1);
         }
         const int colbase = S.cell_off + (wx * Cy + wy) * Cz;
+        float sx = 0.f, sy = 0.f;  // sum of q_j k_0'(r)/r d_x, d_y over the column
         int uz = zlo;
         while (uz <= zhi) {
           const int kz = uz >> S.cshift[2];
@@ -139,16 +150,13 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
                 // k_0'(r)/r = -1/r^3 + (2/a^3) d gamma/d s
                 const float fr = xj.w * fmaf(-rinv * rinv, rinv, dg);
                 if (WW) {
-                  const float gx = fr * dx, gy = fr * dy, gz = fr * dz;
-                  fx += gx;
-                  fy += gy;
+                  sx = fmaf(fr, dx, sx);
+                  sy = fmaf(fr, dy, sy);
+                  const float gz = fr * dz;
                   fz += gz;
-                  v[0] = fmaf(gx, dx, v[0]);
-                  v[1] = fmaf(gy, dy, v[1]);
                   v[2] = fmaf(gz, dz, v[2]);
-                  v[3] = fmaf(gx, dy, v[3]);
-                  v[4] = fmaf(gx, dz, v[4]);
-                  v[5] = fmaf(gy, dz, v[5]);
+                  v[4] = fmaf(gz, dx, v[4]);
+                  v[5] = fmaf(gz, dy, v[5]);
                 } else {
                   fx = fmaf(fr, dx, fx);
                   fy = fmaf(fr, dy, fy);
@@ -159,14 +167,29 @@ __global__ void __launch_bounds__(NB, 1024 / NB) k_short(const SysDev* __restric
           }
           uz += wend - wz + 1;
         }
+        if (WW) {
+          fx += sx;
+          fy += sy;
+          const float ty = (float)oy * ey;
+          v[0] = fmaf(tx, sx, v[0]);
+          v[1] = fmaf(ty, sy, v[1]);
+          v[3] = fmaf(tx, sy, fmaf(ty, sx, v[3]));
+        }
       }
     }
     phi_sr[k] = ph - xi.w * S.self_coef;
     if (WF) f_sr[k] = make_float4(fx, fy, fz, 0.f);  // field of the other charges; the force is q_i times it
     if (WW) {
-      const float hq = -0.5f * xi.w;  // W0 += -1/2 q_i sum q_j k_0'(r)/r d d^T
-#pragma unroll
-      for (int c = 0; c < 6; c++) w6[c] = hq * v[c];
+      // xx, yy, xy: q_i (xi_i f_i^T) - 1/2 q_i sum_columns t (s_col)^T with xi_i the atom's
+      // offset from its cell corner and t the offset between the cell corners; zz, xz, yz:
+      // -1/2 q_i sum q_j k_0'(r)/r d d^T pair by pair
+      const float hq = -0.5f * xi.w;
+      w6[0] = xi.w * (xi.x * fx) + hq * v[0];
+      w6[1] = xi.w * (xi.y * fy) + hq * v[1];
+      w6[2] = hq * v[2];
+      w6[3] = xi.w * (0.5f * (xi.x * fy + xi.y * fx)) + 0.5f * hq * v[3];
+      w6[4] = hq * v[4];
+      w6[5] = hq * v[5];
     }
   }
   if (!WW) return;
