@@ -4,8 +4,8 @@
 //   prolongation  e^l_m     += sum_n J_(m-2n) e^(l+1)_n   (the transpose),
 // with the separable J_n = J_nx J_ny J_nz (B-spline two-scale coefficients,
 // J_k = 2^(1-p) C(p, k+p/2)). Periodic axes wrap; open axes drop points
-// outside the level's index range. Restriction: one thread per coarse point;
-// prolongation: one block per fine tile, separable passes in shared memory.
+// outside the level's index range. Both run as one block per tile with three
+// separable 1-D passes in shared memory.
 // All systems of a batch in one launch per level step.
 #include "msm_internal.h"
 
@@ -28,65 +28,99 @@ __device__ __forceinline__ int grid_index(const LevDev& L, int d, int m) {
   return (s >= 0 && s < L.n[d]) ? s : -1;
 }
 
-// Restriction, one thread per coarse point: (p+1)^3 taps read from L1.
+// Copies the box of points (ix[x], iy[y], iz[z]) of a level grid into shared
+// memory (z fastest), zero where an index is -1. Every load of a thread is
+// issued before its first store, so each thread waits for one memory round
+// trip instead of one per point.
+template <int NX, int NY, int NZ, int NT>
+__device__ __forceinline__ void stage_box(float* __restrict__ dst, const float* __restrict__ src, const int* ix,
+                                          const int* iy, const int* iz, int n1, int n2) {
+  constexpr int N = NX * NY * NZ, R = (N + NT - 1) / NT;
+  float v[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int e = (int)threadIdx.x + r * NT;
+    v[r] = 0.f;
+    if (e < N) {
+      const int z = e % NZ, y = (e / NZ) % NY, x = e / (NZ * NY);
+      const int a = ix[x], b = iy[y], c = iz[z];
+      if (a >= 0 && b >= 0 && c >= 0) v[r] = __ldg(src + ((long long)a * n1 + b) * n2 + c);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int e = (int)threadIdx.x + r * NT;
+    if (e < N) dst[e] = v[r];
+  }
+}
+
+// Restriction, one block per coarse tile of kResTX x kResTY x kResTZ points,
+// as three 1-D passes: the block stages the fine points its tile reads
+// (2 T + p - 1 per axis, wrapped or zero), then applies J along x, y and z in
+// turn in shared memory. Coarse offset i along an axis reads the staged fine
+// offsets 2 i + k, k = 0 .. p, with weight J_(k - p/2).
 template <int P>
-__global__ void __launch_bounds__(kGridChunk) k_restrict(const SysDev* __restrict__ sys,
-                                                         const LevDev* __restrict__ levs,
-                                                         const RangeItem* __restrict__ items,
-                                                         float* __restrict__ grid) {
-  constexpr int H = P / 2;
-  RangeItem it = items[blockIdx.x];
-  if ((int)threadIdx.x >= it.count) return;
+__global__ void __launch_bounds__(kResNT) k_restrict(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
+                                                     const TileItem* __restrict__ items, float* __restrict__ grid) {
+  constexpr int H = P / 2, NT = kResNT;
+  constexpr int FX = 2 * kResTX + P - 1, FY = 2 * kResTY + P - 1, FZ = 2 * kResTZ + P - 1;
+  __shared__ float fine[FX * FY * FZ];      // staged fine points; later the output of the y pass
+  __shared__ float ax[kResTX * FY * FZ];    // output of the x pass
+  __shared__ int ix[FX], iy[FY], iz[FZ];
+  const TileItem it = items[blockIdx.x];
   const LevDev& Cl = levs[it.lev];
   const LevDev& Fl = levs[it.lev - 1];
   const SysDev& S = sys[Cl.sys];
-  int idx = it.start + threadIdx.x;
-  int cz = idx % Cl.n[2], cy = (idx / Cl.n[2]) % Cl.n[1], cx = idx / (Cl.n[2] * Cl.n[1]);
-  int c[3] = {cx, cy, cz};
-  int fi[3][P + 1];
+  const int t = threadIdx.x;
+  // first staged fine coordinate per axis: 2 m0 - p/2, m0 the tile's first coarse coordinate
+  const int f0[3] = {2 * (it.x0 + Cl.lo[0]) - H, 2 * (it.y0 + Cl.lo[1]) - H, 2 * (it.z0 + Cl.lo[2]) - H};
+  for (int e = t; e < FX; e += NT) ix[e] = grid_index(Fl, 0, f0[0] + e);
+  for (int e = t; e < FY; e += NT) iy[e] = grid_index(Fl, 1, f0[1] + e);
+  for (int e = t; e < FZ; e += NT) iz[e] = grid_index(Fl, 2, f0[2] + e);
   float jw[P + 1];
 #pragma unroll
   for (int k = 0; k <= P; k++) jw[k] = S.jc[k];
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    int m = c[d] + Cl.lo[d];
-#pragma unroll
-    for (int k = 0; k <= P; k++) {
-      int f = 2 * m + (k - H);
-      if (Fl.per[d]) {
-        fi[d][k] = f & (Fl.n[d] - 1);  // periodic level sizes are powers of two
-      } else {
-        int s = f - Fl.lo[d];
-        fi[d][k] = (s >= 0 && s < Fl.n[d]) ? s : -1;
-      }
-    }
-  }
+  __syncthreads();
   const float* src = grid + Fl.q_off;
-  float acc = 0.f;
+  stage_box<FX, FY, FZ, NT>(fine, src, ix, iy, iz, Fl.n[1], Fl.n[2]);
+  __syncthreads();
+  for (int e = t; e < kResTX * FY * FZ; e += NT) {
+    const int yz = e % (FY * FZ), i = e / (FY * FZ);
+    const float* f = fine + 2 * i * (FY * FZ) + yz;
+    float v = 0.f;
 #pragma unroll
-  for (int kx = 0; kx <= P; kx++) {
-    if (fi[0][kx] < 0) continue;
-    float ay = 0.f;
-#pragma unroll
-    for (int ky = 0; ky <= P; ky++) {
-      if (fi[1][ky] < 0) continue;
-      const float* row = src + ((long long)fi[0][kx] * Fl.n[1] + fi[1][ky]) * Fl.n[2];
-      float az = 0.f;
-#pragma unroll
-      for (int kz = 0; kz <= P; kz++)
-        if (fi[2][kz] >= 0) az = fmaf(jw[kz], __ldg(row + fi[2][kz]), az);
-      ay = fmaf(jw[ky], az, ay);
-    }
-    acc = fmaf(jw[kx], ay, acc);
+    for (int k = 0; k <= P; k++) v = fmaf(jw[k], f[k * (FY * FZ)], v);
+    ax[e] = v;
   }
-  grid[Cl.q_off + idx] = acc;
+  __syncthreads();
+  float* ay = fine;  // kResTX x kResTY x FZ
+  for (int e = t; e < kResTX * kResTY * FZ; e += NT) {
+    const int z = e % FZ, ij = e / FZ, j = ij % kResTY, i = ij / kResTY;
+    const float* f = ax + (i * FY + 2 * j) * FZ + z;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k <= P; k++) v = fmaf(jw[k], f[k * FZ], v);
+    ay[e] = v;
+  }
+  __syncthreads();
+  for (int e = t; e < kResTX * kResTY * kResTZ; e += NT) {
+    const int kz = e % kResTZ, ij = e / kResTZ, j = ij % kResTY, i = ij / kResTY;
+    const int cx = it.x0 + i, cy = it.y0 + j, cz = it.z0 + kz;
+    if (cx >= Cl.n[0] || cy >= Cl.n[1] || cz >= Cl.n[2]) continue;
+    const float* f = ay + ij * FZ + 2 * kz;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k <= P; k++) v = fmaf(jw[k], f[k], v);
+    grid[Cl.q_off + ((long long)cx * Cl.n[1] + cy) * Cl.n[2] + cz] = v;
+  }
 }
 
 // Prolongation, one block per fine tile of kProTX x kProTY x kProTZ points:
 // e^l_m += sum_n J_(m - 2n) e^(l+1)_n. The block stages the coarse points the
 // tile reads (wrapped or zero) and applies the transposed filter along z, y
-// and x in turn; each fine point takes the at most H + 1 coarse points with
-// |m - 2n| <= H per axis.
+// and x in turn. A fine point m takes the coarse points n = n_1(m) + u,
+// n_1(m) = ceil((m - p/2) / 2), u = 0 .. p/2: J_(p/2 - 2u) when m - p/2 is
+// even, J_(p/2 - 1 - 2u) (u < p/2) when it is odd.
 template <int P>
 __global__ void __launch_bounds__(256) k_prolong(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                  const TileItem* __restrict__ items, float* __restrict__ grid) {
@@ -101,69 +135,92 @@ __global__ void __launch_bounds__(256) k_prolong(const SysDev* __restrict__ sys,
   const LevDev& Cl = levs[it.lev + 1];
   const SysDev& S = sys[Fl.sys];
   const int t = threadIdx.x;
-  // first coarse coordinate per axis: ceil((m0 - H) / 2), m0 the tile's first fine coordinate
+  // first coarse coordinate per axis: n_1(m0), m0 the tile's first fine coordinate
   const int m0[3] = {it.x0 + Fl.lo[0], it.y0 + Fl.lo[1], it.z0 + Fl.lo[2]};
   int n0[3];
 #pragma unroll
-  for (int d = 0; d < 3; d++) n0[d] = -floordiv_g(-(m0[d] - H), 2);
+  for (int d = 0; d < 3; d++) n0[d] = (m0[d] - H + 1) >> 1;
   for (int e = t; e < CX; e += NT) ix[e] = grid_index(Cl, 0, n0[0] + e);
   for (int e = t; e < CY; e += NT) iy[e] = grid_index(Cl, 1, n0[1] + e);
   for (int e = t; e < CZ; e += NT) iz[e] = grid_index(Cl, 2, n0[2] + e);
-  float jw[P + 1];
+  // weights by tap u and the parity of m - p/2 (the odd case has p/2 taps)
+  float we[H + 1], wo[H + 1];
 #pragma unroll
-  for (int k = 0; k <= P; k++) jw[k] = S.jc[k];
-  __syncthreads();
-  const float* src = grid + Cl.e_off;
-  for (int e = t; e < CX * CY * CZ; e += NT) {
-    const int z = e % CZ, y = (e / CZ) % CY, x = e / (CZ * CY);
-    const int a = ix[x], b = iy[y], c = iz[z];
-    crs[e] = (a >= 0 && b >= 0 && c >= 0) ? src[((long long)a * Cl.n[1] + b) * Cl.n[2] + c] : 0.f;
+  for (int u = 0; u <= H; u++) {
+    we[u] = S.jc[2 * H - 2 * u];
+    wo[u] = u < H ? S.jc[2 * H - 1 - 2 * u] : 0.f;
   }
   __syncthreads();
-  // weight of staged coarse index u for fine offset i along an axis: J_(m0 + i - 2 (n0 + u))
-  auto w = [&](int d, int i, int u) {
-    const int k = m0[d] + i - 2 * (n0[d] + u);
-    return (k >= -H && k <= H) ? jw[k + H] : 0.f;
+  // the fine values this thread adds to, loaded before the staging so that both round trips overlap
+  constexpr int RO = kProTX * kProTY * kProTZ / NT;
+  static_assert(RO * NT == kProTX * kProTY * kProTZ, "whole outputs per thread");
+  float old[RO];
+  long long dst[RO];
+#pragma unroll
+  for (int r = 0; r < RO; r++) {
+    const int e = t + r * NT;
+    const int z = e % kProTZ, y = (e / kProTZ) % kProTY, x = e / (kProTZ * kProTY);
+    const int fx = it.x0 + x, fy = it.y0 + y, fz = it.z0 + z;
+    dst[r] = -1;
+    old[r] = 0.f;
+    if (fx < Fl.n[0] && fy < Fl.n[1] && fz < Fl.n[2]) {
+      dst[r] = Fl.e_off + ((long long)fx * Fl.n[1] + fy) * Fl.n[2] + fz;
+      old[r] = grid[dst[r]];
+    }
+  }
+  const float* src = grid + Cl.e_off;
+  stage_box<CX, CY, CZ, NT>(crs, src, ix, iy, iz, Cl.n[1], Cl.n[2]);
+  __syncthreads();
+  // fine offset i along axis d: first staged coarse index u0 = n_1(m0 + i) - n0 and the parity
+  // of m0 + i - p/2; u0 + p/2 < T/2 + p/2 + 1 stays inside the staged range
+  auto taps = [&](int d, int i, int& u0) {
+    const int m = m0[d] + i - H;
+    u0 = ((m + 1) >> 1) - n0[d];
+    return (m & 1) != 0;
   };
   for (int e = t; e < CX * CY * kProTZ; e += NT) {
     const int z = e % kProTZ, xy = e / kProTZ;
-    const int u0 = (m0[2] + z - H - 2 * n0[2] + 1) >> 1;  // ceil((m - H) / 2) - n0: first u with k <= H
+    int u0;
+    const bool odd = taps(2, z, u0);
+    const float* c = crs + xy * CZ + u0;
     float v = 0.f;
 #pragma unroll
-    for (int u = 0; u <= H; u++)
-      if (u0 + u < CZ) v = fmaf(w(2, z, u0 + u), crs[xy * CZ + u0 + u], v);
+    for (int u = 0; u <= H; u++) v = fmaf(odd ? wo[u] : we[u], c[u], v);
     pz[e] = v;
   }
   __syncthreads();
   for (int e = t; e < CX * kProTY * kProTZ; e += NT) {
     const int z = e % kProTZ, y = (e / kProTZ) % kProTY, x = e / (kProTZ * kProTY);
-    const int u0 = (m0[1] + y - H - 2 * n0[1] + 1) >> 1;
+    int u0;
+    const bool odd = taps(1, y, u0);
+    const float* c = pz + (x * CY + u0) * kProTZ + z;
     float v = 0.f;
 #pragma unroll
-    for (int u = 0; u <= H; u++)
-      if (u0 + u < CY) v = fmaf(w(1, y, u0 + u), pz[(x * CY + u0 + u) * kProTZ + z], v);
+    for (int u = 0; u <= H; u++) v = fmaf(odd ? wo[u] : we[u], c[u * kProTZ], v);
     py[e] = v;
   }
   __syncthreads();
-  for (int e = t; e < kProTX * kProTY * kProTZ; e += NT) {
+#pragma unroll
+  for (int r = 0; r < RO; r++) {
+    if (dst[r] < 0) continue;
+    const int e = t + r * NT;
     const int z = e % kProTZ, y = (e / kProTZ) % kProTY, x = e / (kProTZ * kProTY);
-    const int fx = it.x0 + x, fy = it.y0 + y, fz = it.z0 + z;
-    if (fx >= Fl.n[0] || fy >= Fl.n[1] || fz >= Fl.n[2]) continue;
-    const int u0 = (m0[0] + x - H - 2 * n0[0] + 1) >> 1;
+    int u0;
+    const bool odd = taps(0, x, u0);
+    const float* c = py + (u0 * kProTY + y) * kProTZ + z;
     float v = 0.f;
 #pragma unroll
-    for (int u = 0; u <= H; u++)
-      if (u0 + u < CX) v = fmaf(w(0, x, u0 + u), py[((u0 + u) * kProTY + y) * kProTZ + z], v);
-    grid[Fl.e_off + ((long long)fx * Fl.n[1] + fy) * Fl.n[2] + fz] += v;
+    for (int u = 0; u <= H; u++) v = fmaf(odd ? wo[u] : we[u], c[u * (kProTY * kProTZ)], v);
+    grid[dst[r]] = old[r] + v;
   }
 }
 
-void launch_restrict(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p) {
+void launch_restrict(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p) {
   if (nitems <= 0) return;
   switch (p) {
-    case 4: k_restrict<4><<<nitems, kGridChunk, 0, s>>>(t.sys, t.lev, items, w.grid); break;
-    case 6: k_restrict<6><<<nitems, kGridChunk, 0, s>>>(t.sys, t.lev, items, w.grid); break;
-    default: k_restrict<8><<<nitems, kGridChunk, 0, s>>>(t.sys, t.lev, items, w.grid); break;
+    case 4: k_restrict<4><<<nitems, kResNT, 0, s>>>(t.sys, t.lev, items, w.grid); break;
+    case 6: k_restrict<6><<<nitems, kResNT, 0, s>>>(t.sys, t.lev, items, w.grid); break;
+    default: k_restrict<8><<<nitems, kResNT, 0, s>>>(t.sys, t.lev, items, w.grid); break;
   }
 }
 

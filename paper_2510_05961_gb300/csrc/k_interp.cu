@@ -152,7 +152,7 @@ static_assert(kAnterpTX == 16 && kAnterpTY == 8, "one parity class of 8 x 4 colu
 // column A w_z + B dw_z with A = p_x Phi_x' Phi_y / h_x + p_y Phi_x Phi_y' / h_y
 // and B = p_z Phi_x Phi_y / h_z (the force vector-Jacobian product).
 template <int P, int TZ, bool DIP = false>
-__global__ void __launch_bounds__(kAntNT, 6) k_anterp(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
+__global__ void __launch_bounds__(kAntNT, 8) k_anterp(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
                                                   const TileItem* __restrict__ items,
                                                   const int* __restrict__ cell_start,
                                                   const float4* __restrict__ uq, float* __restrict__ grid,
@@ -356,6 +356,219 @@ __global__ void __launch_bounds__(kChunk) k_interp(const SysDev* __restrict__ sy
   }
 }
 
+// ------------------------------------------- anterpolation by binning columns
+// Anterpolation runs from the cell-sorted atoms in two launches, with no
+// atomics and a fixed summation order:
+//  (1) k_anterp_cols: one warp per (binning column, z-segment of tz level-1
+//      points). The warp owns the grid columns its atoms can reach (the
+//      column's footprint, afoot[0] x afoot[1]) over the segment, in shared
+//      memory, and walks the column's atoms in sorted order: the lanes first
+//      evaluate the B-spline weights of 32 atoms at once (q w_x w_y for the
+//      p^2 (x, y) pairs, w_z), then the warp adds the p^3 products of one atom
+//      at a time, each lane a fixed set of (i, j, k) offsets, so the lanes of
+//      one atom write distinct points. The footprint is then written out as
+//      the column's partial sums.
+//  (2) k_anterp_sum: every level-1 point adds the partial sums of the binning
+//      columns whose footprint holds it, in order of the column index.
+// Along an axis, the footprint of binning cell c starts at cell_lo(c):
+// c k - p/2 + 1 when the cells are aligned with the grid (k = M / C = 2^ashift
+// level-1 intervals per cell; an atom of cell c has floor(u) in [ck, ck + k)),
+// else floor((c - 2e-4) M / C) - p/2 + 1 (an atom binned in cell c has u C / M
+// within 1e-4 of [c, c + 1]); its width afoot is k + p - 1, or
+// floor((1 + 4e-4) M / C) + p + 1, set by the planner.
+template <int P>
+__device__ __forceinline__ int cell_lo(const SysDev& S, int d, int c) {
+  constexpr int H = P / 2;
+  if (S.ashift[d] >= 0) return (c << S.ashift[d]) - H + 1;
+  return (int)floorf(((float)c - 2e-4f) * S.aratio[d]) - H + 1;
+}
+
+// shared-memory layout of one warp's footprint: point (fx, fy, z) of the
+// segment at fx * xs + fy * zp + z + p - 1, with p - 1 rows of padding on both
+// sides of the segment (the parts of an atom's support outside it land there);
+// zp >= tz + 2p - 2 with zp = 4 mod 16 and xs = fy_n zp rounded up to 16 mod 32,
+// so that for p = 4 the 32 lanes' offsets 16 i + zp j + k fall in 32 distinct banks
+__host__ __device__ inline int ant_zp(int tz, int p) {
+  int zp = tz + 2 * p - 2;
+  return zp + ((4 - zp % 16) + 16) % 16;
+}
+__host__ __device__ inline int ant_xs(int fy_n, int tz, int p) {
+  const int xs = fy_n * ant_zp(tz, p);
+  return xs + ((16 - xs % 32) + 32) % 32;
+}
+// staging of 32 atoms: q w_x w_y (p^2 + 1 per atom), w_z (p + 1 per atom), base offsets
+__host__ __device__ inline int ant_stage_floats(int p) { return 32 * (p * p + 1) + 32 * (p + 1) + 32; }
+
+template <int P>
+__global__ void __launch_bounds__(kAntWarps * 32, 4) k_anterp_cols(const SysDev* __restrict__ sys,
+                                                                const LevDev* __restrict__ levs,
+                                                                const TileItem* __restrict__ items, int nitems,
+                                                                int tz, int wstride,
+                                                                const int* __restrict__ cell_start,
+                                                                const float4* __restrict__ uq,
+                                                                float* __restrict__ apart) {
+  constexpr int H = P / 2, P3 = P * P * P, R = (P3 + 31) / 32, SQ = P * P + 1, SZ = P + 1;
+  extern __shared__ __align__(16) float smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int iw = blockIdx.x * kAntWarps + wib;
+  if (iw >= nitems) return;  // whole warps only; no block barriers below
+  const TileItem it = items[iw];
+  const LevDev& L = levs[it.lev];
+  const SysDev& S = sys[L.sys];
+  const int Fx = S.afoot[0], Fy = S.afoot[1];
+  const int ZP = ant_zp(tz, P), XS = ant_xs(Fy, tz, P);
+  float* acc = smem + (size_t)wib * wstride;
+  float* sq = acc + ((Fx * XS + 3) & ~3);  // q w_x w_y of 32 atoms
+  float* sz = sq + 32 * SQ;                // w_z of 32 atoms
+  int* sb = reinterpret_cast<int*>(sz + 32 * SZ);  // base offset of each atom in acc
+  for (int e = 4 * lane; e < Fx * XS; e += 128) *reinterpret_cast<float4*>(acc + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int cx = it.x0, cy = it.y0, z0 = it.z0;
+  const int lox = cell_lo<P>(S, 0, cx), loy = cell_lo<P>(S, 1, cy);
+  const int zlen = min(tz, L.n[2] - z0);
+  const int mz0 = z0 + L.lo[2];
+  // z-cells of the column whose atoms reach the points [mz0, mz0 + zlen)
+  int cl, ch;
+  if (S.ashift[2] >= 0) {
+    cl = (mz0 - H) >> S.ashift[2];
+    ch = (mz0 + zlen - 1 + H - 1) >> S.ashift[2];
+  } else {
+    const float rc = S.ainv[2];
+    cl = (int)floorf((float)(mz0 - H) * rc - 2e-4f);
+    ch = (int)floorf((float)(mz0 + zlen - 1 + H) * rc + 2e-4f);
+  }
+  if (!S.pbc[2]) {
+    cl = max(cl, 0);
+    ch = min(ch, S.C[2] - 1);
+  }
+  const int Cy = S.C[1], Cz = S.C[2];
+  const int* cs = cell_start + S.cell_off + (cx * Cy + cy) * Cz;
+  int uz = cl;
+  while (uz <= ch) {
+    const int kz = floordiv_i(uz, Cz), wz = uz - kz * Cz;
+    const int wend = min(Cz - 1, wz + (ch - uz));
+    const int zsh = kz * S.M[2] - mz0 - H + 1;  // z base relative to the segment: floor(u_z) + zsh
+    int j = cs[wz], je = cs[wend + 1];
+    if (!MSM_CHECK(S, j >= S.atom_off && je <= S.atom_off + S.n)) je = j;
+    for (; j < je; j += 32) {
+      const int na = min(32, je - j);
+      __syncwarp();  // the previous chunk's staging has been read
+      if (lane < na) {
+        const float4 u = uq[j + lane];
+        const float flx = floorf(u.x), fly = floorf(u.y), flz = floorf(u.z);
+        const int bx = (int)flx - H + 1 - lox, by = (int)fly - H + 1 - loy, bz = (int)flz + zsh;
+        float qq = u.w;
+        int base = bx * XS + by * ZP + bz + P - 1;
+        // every atom of the column lies inside its footprint; one outside is
+        // skipped (and reported by the checked build) instead of written; an
+        // atom whose support misses the segment adds nothing to it
+        if (!(bx >= 0 && bx <= Fx - P && by >= 0 && by <= Fy - P)) {
+          (void)MSM_CHECK(S, false);
+          qq = 0.f;
+          base = 0;
+        } else if (bz < 1 - P || bz >= zlen) {
+          qq = 0.f;
+          base = 0;
+        }
+        float wx[P], wy[P], w3[P], dummy[P];
+        bspline_weights<P, false>(u.x - flx, wx, dummy);
+        bspline_weights<P, false>(u.y - fly, wy, dummy);
+        bspline_weights<P, false>(u.z - flz, w3, dummy);
+#pragma unroll
+        for (int i = 0; i < P; i++) {
+          const float qx = qq * wx[i];
+#pragma unroll
+          for (int jj = 0; jj < P; jj++) sq[lane * SQ + i * P + jj] = qx * wy[jj];
+        }
+#pragma unroll
+        for (int k = 0; k < P; k++) sz[lane * SZ + k] = w3[k];
+        sb[lane] = base;
+      }
+      __syncwarp();
+      for (int a = 0; a < na; a++) {
+        const int base = sb[a];
+        const float* qa = sq + a * SQ;
+        const float* za = sz + a * SZ;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const int c = lane + 32 * r;
+          if (P3 % 32 != 0 && c >= P3) continue;
+          const int ij = c / P, k = c % P;
+          float* dst = acc + base + (ij / P) * XS + (ij % P) * ZP + k;
+          *dst = fmaf(qa[ij], za[k], *dst);
+        }
+        __syncwarp();  // lanes of the next atom may write the points this one wrote
+      }
+    }
+    uz += wend - wz + 1;
+  }
+  __syncwarp();
+  float* out = apart + S.apart + (long long)(cx * Cy + cy) * (Fx * Fy) * L.n[2] + z0;
+  for (int fx = 0; fx < Fx; fx++)
+    for (int fy = 0; fy < Fy; fy++) {
+      const float* src = acc + fx * XS + fy * ZP + P - 1;
+      float* dst = out + (long long)(fx * Fy + fy) * L.n[2];
+      for (int z = lane; z < zlen; z += 32) dst[z] = src[z];
+    }
+}
+
+// binning cells of one axis whose footprint may hold level-1 coordinate m:
+// candidates [c_a, c_b] (a cell c of a periodic axis may lie outside [0, C):
+// it stands for c mod C shifted by whole periods)
+template <int P>
+__device__ __forceinline__ void foot_cells(const SysDev& S, int d, int m, int F, int& ca, int& cb) {
+  constexpr int H = P / 2;
+  if (S.ashift[d] >= 0) {
+    ca = (m + H - F) >> S.ashift[d];
+    cb = (m + H - 1) >> S.ashift[d];
+  } else {
+    ca = max((int)floorf((float)(m + H - F) * S.ainv[d]) - 1, 0);
+    cb = min((int)floorf((float)(m + H) * S.ainv[d]) + 1, S.C[d] - 1);
+  }
+}
+
+// One block per level-1 grid column (gx, gy) and chunk of kAntSumZ points along
+// z: the block lists the (binning column, footprint offset) pairs that hold
+// the column once, then every thread sums them for its z.
+template <int P>
+__global__ void __launch_bounds__(kAntSumZ, 8) k_anterp_sum(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
+                                                         const TileItem* __restrict__ items,
+                                                         const float* __restrict__ apart, float* __restrict__ grid) {
+  __shared__ long long off[kAntFootMax * kAntFootMax];
+  __shared__ int noff;
+  const TileItem it = items[blockIdx.x];
+  const LevDev& L = levs[it.lev];
+  const SysDev& S = sys[L.sys];
+  const int gx = it.x0, gy = it.y0;
+  const long long nz = L.n[2];
+  if (threadIdx.x == 0) {
+    const int Fx = S.afoot[0], Fy = S.afoot[1], Cx = S.C[0], Cy = S.C[1];
+    const int mx = gx + L.lo[0], my = gy + L.lo[1];
+    int xa, xb, ya, yb;
+    foot_cells<P>(S, 0, mx, Fx, xa, xb);
+    foot_cells<P>(S, 1, my, Fy, ya, yb);
+    int n = 0;
+    for (int c = xa; c <= xb; c++) {
+      const int fx = mx - cell_lo<P>(S, 0, c);
+      if (fx < 0 || fx >= Fx) continue;
+      const int wx = S.pbc[0] ? (c & (Cx - 1)) : c;  // C is a power of two on a periodic axis
+      for (int e = ya; e <= yb; e++) {
+        const int fy = my - cell_lo<P>(S, 1, e);
+        if (fy < 0 || fy >= Fy) continue;
+        const int wy = S.pbc[1] ? (e & (Cy - 1)) : e;
+        if (n < kAntFootMax * kAntFootMax) off[n++] = S.apart + ((long long)(wx * Cy + wy) * (Fx * Fy) + fx * Fy + fy) * nz;
+      }
+    }
+    noff = n;
+  }
+  __syncthreads();
+  const int z = it.z0 + (int)threadIdx.x;
+  if (z >= L.n[2]) return;
+  const int n = noff;
+  float v = 0.f;
+  for (int t = 0; t < n; t++) v += __ldg(apart + off[t] + z);
+  grid[L.q_off + ((long long)gx * L.n[1] + gy) * nz + z] = v;
+}
+
 template <int P>
 static void run_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int tz) {
   if (tz == 16) k_anterp<P, 16><<<nitems, kAntNT, 0, s>>>(t.sys, t.lev, items, w.cell_start, w.uq, w.grid);
@@ -483,6 +696,34 @@ void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int ni
     case 4: run_anterp<4>(w, t, items, nitems, s, tz); break;
     case 6: run_anterp<6>(w, t, items, nitems, s, tz); break;
     default: run_anterp<8>(w, t, items, nitems, s, tz); break;
+  }
+}
+
+template <int P>
+static void run_anterp_cols(const Work& w, const Tables& t, const TileItem* cols, int ncol, const TileItem* sums,
+                            int nsum, int tz, int wstride, cudaStream_t s) {
+  const size_t bytes = sizeof(float) * kAntWarps * (size_t)wstride;
+  static size_t attr = 0;
+  if (bytes > 48 * 1024 && bytes > attr &&
+      cudaFuncSetAttribute(k_anterp_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    attr = bytes;
+  if (ncol > 0)
+    k_anterp_cols<P><<<(ncol + kAntWarps - 1) / kAntWarps, kAntWarps * 32, bytes, s>>>(
+        t.sys, t.lev, cols, ncol, tz, wstride, w.cell_start, w.uq, w.apart);
+  if (nsum > 0) k_anterp_sum<P><<<nsum, kAntSumZ, 0, s>>>(t.sys, t.lev, sums, w.apart, w.grid);
+}
+
+// floats of shared memory per warp of k_anterp_cols for footprints up to fx_max x fy_max
+int anterp_cols_wstride(int fx_max, int fy_max, int tz, int p) {
+  return ((fx_max * ant_xs(fy_max, tz, p) + 3) & ~3) + ant_stage_floats(p);
+}
+
+void launch_anterp_cols(const Work& w, const Tables& t, const TileItem* cols, int ncol, const TileItem* sums,
+                        int nsum, int tz, int wstride, cudaStream_t s, int p) {
+  switch (p) {
+    case 4: run_anterp_cols<4>(w, t, cols, ncol, sums, nsum, tz, wstride, s); break;
+    case 6: run_anterp_cols<6>(w, t, cols, ncol, sums, nsum, tz, wstride, s); break;
+    default: run_anterp_cols<8>(w, t, cols, ncol, sums, nsum, tz, wstride, s); break;
   }
 }
 

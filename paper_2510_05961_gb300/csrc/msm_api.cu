@@ -60,7 +60,7 @@ struct Phase {
 // kernels each phase launches (for the launch count)
 static int count_forward(const Engine& E, bool) {
   int n = 1 + 5 + 1;                                   // prologue, binning, short range
-  n += E.anterp_items.empty() ? 0 : 1;
+  n += E.anterp_items.empty() ? 0 : (E.ant_wstride > 0 ? 2 : 1);  // anterpolation (columns: partials + sums)
   for (int l = 1; l < E.maxcomp; l++) n += 2;          // restriction + prolongation per level step
   n += E.ball_items.empty() ? 0 : 2;                   // halo padding + ball stencil
   n += E.box_items.empty() ? 0 : 1;
@@ -88,8 +88,14 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
     launch_prologue(w, E.total_cells, E.d_sys, E.nsys, E.single ? n_single : -1, s);
     launch_bin(w, t, E.d_atom_items, nai, E.total_cells, n_total, pos, q, s);
   }
-  // fork: the short-range pairs (side stream) overlap the grid chain (caller's
-  // stream); serial profiling keeps them on the caller's stream
+  // anterpolation before the fork: its blocks then have the GPU to themselves
+  // (measured faster than running it beside the short-range kernel)
+  {
+    Phase ph(E, MSM_PH_ANTERP, s);
+    E.anterp(w, t, s);
+  }
+  // fork: the short-range pairs (side stream) overlap the rest of the grid
+  // chain (caller's stream); serial profiling keeps them on the caller's stream
   cudaStream_t ss = E.serial ? s : E.side;
   if (!E.serial) {
     cudaEventRecord(E.ev_fork, s);
@@ -102,14 +108,10 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   }
   if (!E.serial) cudaEventRecord(E.ev_join, E.side);
   {
-    Phase ph(E, MSM_PH_ANTERP, s);
-    launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz);
-  }
-  {
     Phase ph(E, MSM_PH_RESTRICT, s);
     for (int l = 1; l < E.maxcomp; l++) {
       int a = E.restrict_off[l - 1], b = E.restrict_off[l];
-      launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
+      launch_restrict(w, t, E.d_res_items + a, b - a, s, E.p);
     }
   }
   {
@@ -277,7 +279,7 @@ static int run_autotune(Engine& E, void* ws, size_t ws_bytes, int n_single, cons
   float best = 1e30f;
   for (int tz : {16, 32, 64}) {
     if ((rc = E.set_anterp_tz(tz, &err))) break;
-    const float ms = timed([&] { launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, tz); });
+    const float ms = timed([&] { E.anterp(w, t, s); });
     if (ms < best) {
       best = ms;
       best_tz = tz;
@@ -495,7 +497,7 @@ static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* 
     launch_anterp_dipole(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz, w.vjp_u);
     for (int l = 1; l < E.maxcomp; l++) {
       int a = E.restrict_off[l - 1], b = E.restrict_off[l];
-      launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
+      launch_restrict(w, t, E.d_res_items + a, b - a, s, E.p);
     }
     launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
     launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
@@ -532,14 +534,14 @@ static int run_potential_vjp(Engine& E, void* ws, const float* g, float* dq, flo
   }
   if (E.last_n > 0) {
     launch_pvjp_prep(w, t, E.d_atom_items, nai, g, s);
+    E.anterp(w, t, s);
     cudaEventRecord(E.ev_fork, s);
     cudaStreamWaitEvent(E.side, E.ev_fork, 0);
     launch_short(w, t, E.d_atom_items, nai, true, false, E.side, E.p, E.short_code());
     cudaEventRecord(E.ev_join, E.side);
-    launch_anterp(w, t, E.d_anterp_items, (int)E.anterp_items.size(), s, E.p, E.anterp_tz);
     for (int l = 1; l < E.maxcomp; l++) {
       int a = E.restrict_off[l - 1], b = E.restrict_off[l];
-      launch_restrict(w, t, E.d_range_items + a, b - a, s, E.p);
+      launch_restrict(w, t, E.d_res_items + a, b - a, s, E.p);
     }
     launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
     launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);

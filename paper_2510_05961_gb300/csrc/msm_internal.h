@@ -16,14 +16,18 @@ constexpr int kMaxLev = 20;
 constexpr int kChunk = 256;        // atoms per per-atom work item
 constexpr int kChunkWarps = kChunk / 32;
 constexpr int kShortTilted = -1;  // short-range launch code of plans with tilted cells (k_short_tri)
-constexpr int kAnterpTX = 16, kAnterpTY = 8;  // anterpolation tile columns (x, y); its z-extent is tuned
+constexpr int kAnterpTX = 16, kAnterpTY = 8;  // dipole anterpolation tile columns (x, y); its z-extent is tuned
+constexpr int kAntWarps = 4;       // anterpolation: binning-column items (one per warp) per block
+constexpr int kAntFootMax = 16;    // largest footprint of a binning column per axis (grid columns)
+constexpr int kAntSumZ = 128;      // anterpolation sums: level-1 points along z per block
 constexpr int kBallTY = 32;        // stencil tile rows (y)
 constexpr int kBallBZ = 16;        // outputs per thread along z
 constexpr int kBallTZ = 32;        // stencil tile depth (z)
 constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
 constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
-constexpr int kGridChunk = 256;    // coarse points per restriction item
+constexpr int kResTX = 4, kResTY = 4, kResTZ = 16;  // restriction tiles (coarse points)
+constexpr int kResNT = kResTX * kResTY * kResTZ;    // threads per restriction block
 constexpr int kVirialSlices = 64;  // most virial reduction slices per system
 constexpr int kProTX = 4, kProTY = 4, kProTZ = 32;  // prolongation tiles (fine points)
 constexpr int kFoldPts = 512;      // batch plans fold levels this small into dense boxes
@@ -73,6 +77,13 @@ struct SysDev {
   double Td[9];     // A^-T (FP64)
   float Jg[9];      // A^-1 diag(M): Cartesian gradient from level-1 grid derivatives
   float reach[3];   // a / (distance between cell faces): fractional reach of the cutoff per axis
+  // anterpolation by binning columns: level-1 grid columns (x, y) that the atoms of one
+  // binning column reach, and the float offset of this system's column partials
+  int afoot[2];
+  long long apart;
+  int ashift[3];    // log2 of the level-1 intervals per binning cell where the cells are aligned with the grid, else -1
+  float aratio[3];  // M / C (axes whose cells are not aligned with the grid)
+  float ainv[3];    // C / M
 };
 
 // Debug builds (-DMSM_CHECKS=1, build.build(checks=True)): kernels test their
@@ -139,6 +150,7 @@ struct Work {
   double* part_wg; // per virial item: 6 grid virial components
   double* part_vs; // per system and reduction slice: 6 virial components
   float* grid;     // grid pool
+  float* apart;    // anterpolation: level-1 partial sums of each binning column (per system at SysDev::apart)
   float4* vjp_u;   // force vector-Jacobian product: upstream (u, q), sorted
   float4* vjp_h;   // force vector-Jacobian product: short-range rows of H u and psi, sorted
   // staging of msm_evaluate_host (caller's atom order)
@@ -166,10 +178,14 @@ void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nit
                   cudaStream_t s, int p, int block);
 // anterpolation / interpolation (k_interp.cu)
 void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p, int tz);
+// anterpolation by binning columns (k_interp.cu): per-column partial sums, then their sum per point
+int anterp_cols_wstride(int fx_max, int fy_max, int tz, int p);
+void launch_anterp_cols(const Work& w, const Tables& t, const TileItem* cols, int ncol, const TileItem* sums,
+                        int nsum, int tz, int wstride, cudaStream_t s, int p);
 void launch_interp(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces,
                    cudaStream_t s, int p);
 // restriction / prolongation (k_grid.cu)
-void launch_restrict(const Work& w, const Tables& t, const RangeItem* items, int nitems, cudaStream_t s, int p);
+void launch_restrict(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p);
 void launch_prolong(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p);
 // stencils and grid virial (k_stencil.cu)
 void launch_pad(const Work& w, const Tables& t, const TileItem* items, int nitems, int pre_r, cudaStream_t s);

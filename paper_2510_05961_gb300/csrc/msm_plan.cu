@@ -1011,6 +1011,19 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       D.pre_r = S.prefilter ? S.p / 2 - 1 : 0;
       for (int k = 0; k < 4; k++) D.om[k] = S.prefilter ? (k < S.p / 2 ? (float)om[k] : 0.f) : (k == 0 ? 1.f : 0.f);
     }
+    // footprints of the binning columns on the level-1 grid (anterpolation by columns)
+    for (int d = 0; d < 3; d++) {
+      const int k = S.M[d] / S.C[d];
+      const bool aligned = S.pbc[d] && S.M[d] % S.C[d] == 0 && (k & (k - 1)) == 0;
+      D.ashift[d] = -1;
+      if (aligned)
+        for (D.ashift[d] = 0; (1 << D.ashift[d]) < k; D.ashift[d]++) {
+        }
+      D.aratio[d] = (float)((double)S.M[d] / (double)S.C[d]);
+      D.ainv[d] = (float)((double)S.C[d] / (double)S.M[d]);
+      if (d < 2)
+        D.afoot[d] = aligned ? k + S.p - 1 : (int)std::floor((1.0 + 4e-4) * (double)S.M[d] / (double)S.C[d]) + S.p + 1;
+    }
     for (int st = 0; st < counts[s]; st += kChunk) atom_items.push_back({s, st, std::min(kChunk, counts[s] - st)});
     if (counts[s] == 0) atom_items.push_back({s, 0, 0});
     D.nitem = (int)atom_items.size() - D.item0;
@@ -1098,7 +1111,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   }
   vb_off[nsys] = (int)ball_items.size();
   vx_off[nsys] = (int)box_items.size();
-  restrict_steps.assign(std::max(0, maxcomp - 1), std::vector<RangeItem>());
+  restrict_steps.assign(std::max(0, maxcomp - 1), std::vector<TileItem>());
   prolong_steps.assign(std::max(0, maxcomp - 1), std::vector<TileItem>());
   for (int l = 1; l < maxcomp; l++) {
     for (int s = 0; s < nsys; s++) {
@@ -1106,9 +1119,9 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
       int fi = hs[s].lev0 + l - 1, ci = fi + 1;
       const LevDev& F = hlev[fi];
       const LevDev& Cc = hlev[ci];
-      long long nc = (long long)Cc.n[0] * Cc.n[1] * Cc.n[2];
-      for (long long st = 0; st < nc; st += kGridChunk)
-        restrict_steps[l - 1].push_back({ci, (int)st, (int)std::min<long long>(kGridChunk, nc - st)});
+      for (int x = 0; x < Cc.n[0]; x += kResTX)
+        for (int y = 0; y < Cc.n[1]; y += kResTY)
+          for (int z = 0; z < Cc.n[2]; z += kResTZ) restrict_steps[l - 1].push_back({ci, x, y, z});
       for (int x = 0; x < F.n[0]; x += kProTX)
         for (int y = 0; y < F.n[1]; y += kProTY)
           for (int z = 0; z < F.n[2]; z += kProTZ) prolong_steps[l - 1].push_back({fi, x, y, z});
@@ -1119,6 +1132,13 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   for (int s = 0; s <= nsys; s++) {
     voff[s] = vb_off[s];
     voff[nsys + 1 + s] = (int)ball_items.size() + vx_off[s];
+  }
+  // column partials of the anterpolation: C_x C_y afoot_x afoot_y n_z floats per system
+  apart_floats = 0;
+  for (int s = 0; s < nsys; s++) {
+    hs[s].apart = apart_floats;
+    if (sys[s].ncomp < 1) continue;
+    apart_floats += (long long)hs[s].C[0] * hs[s].C[1] * hs[s].afoot[0] * hs[s].afoot[1] * hlev[hs[s].lev0].n[2];
   }
   hsys = hs;
   build_anterp_items(anterp_tz);
@@ -1170,6 +1190,8 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_io_dpos = take(sizeof(float) * 3 * N);
   L_io_dq = take(sizeof(float) * N);
   L_io_e = take(sizeof(double) * 11 * (size_t)std::max(nsys, 1));
+  // sized whenever the footprints fit the column kernel, whatever z-extent the tuning picks later
+  L_apart = take(sizeof(float) * (size_t)(ant_fmax[0] <= kAntFootMax && ant_fmax[1] <= kAntFootMax ? apart_floats : 0));
   ws_bytes = off;
   return MSM_OK;
 }
@@ -1185,9 +1207,15 @@ static int up(const std::vector<T>& h, T** d, std::string* err) {
   return MSM_OK;
 }
 
-// anterpolation tiles of kAnterpTX x kAnterpTY x tz level-1 points (tz = 16, 32, 64)
+// anterpolation work lists for z-extent tz (16, 32, 64): tiles of kAnterpTX x
+// kAnterpTY x tz level-1 points (dipole anterpolation, and every anterpolation
+// when a footprint is too wide for the column kernel), and the column items
+// (binning column, z-segment of tz points) with the sum items of k_anterp_sum
 void Engine::build_anterp_items(int tz) {
   anterp_items.clear();
+  acol_items.clear();
+  asum_items.clear();
+  int fmax[2] = {0, 0};
   for (int s = 0; s < nsys; s++) {
     if (sys[s].ncomp < 1) continue;
     const int li = hsys[s].lev0;
@@ -1195,6 +1223,22 @@ void Engine::build_anterp_items(int tz) {
     for (int x = 0; x < L.n[0]; x += kAnterpTX)
       for (int y = 0; y < L.n[1]; y += kAnterpTY)
         for (int z = 0; z < L.n[2]; z += tz) anterp_items.push_back({li, x, y, z});
+    const SysDev& D = hsys[s];
+    for (int cx = 0; cx < D.C[0]; cx++)
+      for (int cy = 0; cy < D.C[1]; cy++)
+        for (int z = 0; z < L.n[2]; z += tz) acol_items.push_back({li, cx, cy, z});
+    for (int x = 0; x < L.n[0]; x++)
+      for (int y = 0; y < L.n[1]; y++)
+        for (int z = 0; z < L.n[2]; z += kAntSumZ) asum_items.push_back({li, x, y, z});
+    fmax[0] = std::max(fmax[0], D.afoot[0]);
+    fmax[1] = std::max(fmax[1], D.afoot[1]);
+  }
+  ant_fmax[0] = fmax[0];
+  ant_fmax[1] = fmax[1];
+  ant_wstride = 0;
+  if (!acol_items.empty() && fmax[0] <= kAntFootMax && fmax[1] <= kAntFootMax) {
+    const int ws = anterp_cols_wstride(fmax[0], fmax[1], tz, p);
+    if (sizeof(float) * kAntWarps * (size_t)ws <= 100 * 1024) ant_wstride = ws;
   }
   anterp_tz = tz;
 }
@@ -1203,7 +1247,18 @@ int Engine::set_anterp_tz(int tz, std::string* err) {
   if (tz != 16 && tz != 32 && tz != 64) return fail(err, MSM_ERR_INVALID_ARG, "anterpolation tile must be 16, 32 or 64");
   if (tz == anterp_tz) return MSM_OK;
   build_anterp_items(tz);
-  return up(anterp_items, &d_anterp_items, err);
+  int rc = up(anterp_items, &d_anterp_items, err);
+  if (!rc) rc = up(acol_items, &d_acol_items, err);
+  if (!rc) rc = up(asum_items, &d_asum_items, err);
+  return rc;
+}
+
+void Engine::anterp(const Work& w, const Tables& t, cudaStream_t s) const {
+  if (ant_wstride > 0)
+    launch_anterp_cols(w, t, d_acol_items, (int)acol_items.size(), d_asum_items, (int)asum_items.size(), anterp_tz,
+                       ant_wstride, s, p);
+  else
+    launch_anterp(w, t, d_anterp_items, (int)anterp_items.size(), s, p, anterp_tz);
 }
 
 int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, const std::vector<int>& voff,
@@ -1217,18 +1272,20 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   wpool_n = wp.size();
   if ((rc = up(atom_items, &d_atom_items, err))) return rc;
   if ((rc = up(anterp_items, &d_anterp_items, err))) return rc;
+  if ((rc = up(acol_items, &d_acol_items, err))) return rc;
+  if ((rc = up(asum_items, &d_asum_items, err))) return rc;
   if ((rc = up(ball_items, &d_ball_items, err))) return rc;
   if ((rc = up(box_items, &d_box_items, err))) return rc;
   if ((rc = up(pad_items, &d_pad_items, err))) return rc;
   if ((rc = up(voff, &d_voff, err))) return rc;
-  std::vector<RangeItem> all;
+  std::vector<TileItem> all;
   restrict_off.assign(restrict_steps.size() + 1, 0);
   for (size_t i = 0; i < restrict_steps.size(); i++) {
     restrict_off[i] = (int)all.size();
     all.insert(all.end(), restrict_steps[i].begin(), restrict_steps[i].end());
   }
   restrict_off[restrict_steps.size()] = (int)all.size();
-  if ((rc = up(all, &d_range_items, err))) return rc;
+  if ((rc = up(all, &d_res_items, err))) return rc;
   std::vector<TileItem> pro;
   prolong_off.assign(prolong_steps.size() + 1, 0);
   for (size_t i = 0; i < prolong_steps.size(); i++) {
@@ -1360,11 +1417,13 @@ Engine::~Engine() {
   cudaFree(d_wpool);
   cudaFree(d_atom_items);
   cudaFree(d_anterp_items);
+  cudaFree(d_acol_items);
+  cudaFree(d_asum_items);
   cudaFree(d_ball_items);
   cudaFree(d_box_items);
   cudaFree(d_pad_items);
   cudaFree(d_voff);
-  cudaFree(d_range_items);
+  cudaFree(d_res_items);
   cudaFree(d_pro_items);
   cudaFree(d_energy_scratch);
 }
@@ -1400,6 +1459,7 @@ Work Engine::resolve(void* ws) const {
   w.grid = (float*)(b + L_grid);
   w.vjp_u = (float4*)(b + L_vjp_u);
   w.vjp_h = (float4*)(b + L_vjp_h);
+  w.apart = (float*)(b + L_apart);
   return w;
 }
 

@@ -74,9 +74,17 @@ struct Engine {
   std::vector<LevDev> hlev;
   std::vector<AtomItem> atom_items;
   std::vector<TileItem> anterp_items, ball_items;
+  // anterpolation by binning columns: one item per (binning column, z-segment), one sum
+  // item per (level-1 grid column, kAntSumZ points); used when every footprint fits
+  // (ant_wstride > 0)
+  std::vector<TileItem> acol_items;
+  std::vector<TileItem> asum_items;
+  long long apart_floats = 0;
+  int ant_fmax[2] = {0, 0};
+  int ant_wstride = 0;
   std::vector<RangeItem> box_items;
   std::vector<TileItem> pad_items;
-  std::vector<std::vector<RangeItem>> restrict_steps;
+  std::vector<std::vector<TileItem>> restrict_steps;
   std::vector<std::vector<TileItem>> prolong_steps;
   std::vector<int> restrict_off, prolong_off;
   std::vector<int> vb_off, vx_off;
@@ -87,16 +95,18 @@ struct Engine {
   int* d_wpool = nullptr;
   AtomItem* d_atom_items = nullptr;
   TileItem* d_anterp_items = nullptr;
+  TileItem* d_acol_items = nullptr;
+  TileItem* d_asum_items = nullptr;
   TileItem* d_ball_items = nullptr;
   RangeItem* d_box_items = nullptr;
   TileItem* d_pad_items = nullptr;
-  RangeItem* d_range_items = nullptr;  // restriction items of all level steps
+  TileItem* d_res_items = nullptr;     // restriction tiles of all level steps
   TileItem* d_pro_items = nullptr;     // prolongation tiles of all level steps
   int* d_voff = nullptr;
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
       L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_q, L_part_w0, L_part_wg, L_part_vs, L_grid, L_vjp_u,
-      L_vjp_h, L_io_pos, L_io_q, L_io_dpos, L_io_dq, L_io_e;
+      L_vjp_h, L_io_pos, L_io_q, L_io_dpos, L_io_dq, L_io_e, L_apart;
   size_t ws_bytes = 0;
   // state of the last forward pass
   bool have_fwd = false;
@@ -132,6 +142,7 @@ struct Engine {
   int short_code() const { return any_tri ? kShortTilted : short_block; }
   double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
   void build_anterp_items(int tz);
+  void anterp(const Work& w, const Tables& t, cudaStream_t s) const;  // level-1 grid charges
   int set_anterp_tz(int tz, std::string* err);
   void assemble_pools(const std::vector<int>& lev0_of, std::vector<float>& kp, std::vector<int>& wp);
   // new cell for a single-system plan (msm_plan_set_cell), host path: stencils
