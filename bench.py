@@ -255,7 +255,7 @@ def kernel_table(info, n, a, p, ph, pk, st_flops_exec, serial_note):
     pairs = short_pairs(n, 0.1, a)
     add("short", "k_short", "alu", SHORT_FLOP_PER_PAIR * pairs,
         "FLOP: %.0f per in-cutoff ordered pair (about 20 FMA), %.3g pairs" % (SHORT_FLOP_PER_PAIR, pairs))
-    add("anterp", "k_anterp", "alu", 2.0 * (p ** 3 + 3 * p) * n,
+    add("anterp", "k_anterp_cols, k_anterp_sum", "alu", 2.0 * (p ** 3 + 3 * p) * n,
         "FLOP: p^3 FMA + 3p weight FMA per atom")
     add("restrict", "k_restrict (all level steps)", "hbm", 4.0 * sum(pts[l] + pts[l + 1] for l in range(len(pts) - 1)),
         "bytes: read level l, write level l+1 (4 B per point)")
