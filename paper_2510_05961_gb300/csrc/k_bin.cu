@@ -11,7 +11,11 @@
 //
 // Pipeline: count (atomic slot per atom) -> exclusive scan of the packed cell
 // counts of all systems -> scatter atom ids into buckets -> rank each atom in
-// its bucket by original index and write the sorted arrays.
+// its bucket by original index and write the sorted arrays. The rank scan
+// costs n_c^2 comparisons per cell of n_c atoms; the short-range kernel
+// already tests every ordered pair of a cell's atoms (a cell is in its own
+// neighbourhood), so binning never costs more than a fraction of it, whatever
+// the clustering.
 #include "msm_internal.h"
 
 namespace msm {
@@ -166,21 +170,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_fix(int* __restrict__ sta
   if (blockIdx.x == (unsigned)(ntiles - 1) && threadIdx.x == 0) start[total_cells] = off + tiles[ntiles - 1];
 }
 
+// also keeps each atom's cell range [b, e) in atom order, so that the rank
+// kernel reads it with one coalesced load instead of a dependent one
 __global__ void k_bin_scatter(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                               const int* __restrict__ cell_id, const int* __restrict__ slot,
-                              const int* __restrict__ cell_start, int* __restrict__ bucket) {
+                              const int* __restrict__ cell_start, int* __restrict__ bucket,
+                              int2* __restrict__ crange) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
-  const int b = cell_start[S.cell_off + cell_id[g]] + slot[g];
+  const int* cs = cell_start + S.cell_off + cell_id[g];
+  const int c0 = cs[0], c1 = cs[1];
+  crange[g] = make_int2(c0, c1);
+  const int b = c0 + slot[g];
   if (MSM_CHECK(S, b >= S.atom_off && b < S.atom_off + S.n)) bucket[b] = g;
 }
 
 __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                            const float* __restrict__ pos, const float* __restrict__ q,
-                           const int* __restrict__ cell_id, const int* __restrict__ cell_start,
+                           const int* __restrict__ cell_id, const int2* __restrict__ crange,
                            const int* __restrict__ bucket, int* __restrict__ perm, int* __restrict__ scell,
                            float4* __restrict__ xq, float4* __restrict__ uq) {
   AtomItem it = items[blockIdx.x];
@@ -194,7 +204,8 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
   int cell = cell_id[g];
-  int b = cell_start[S.cell_off + cell], e = cell_start[S.cell_off + cell + 1];
+  const int2 rg = crange[g];
+  const int b = rg.x, e = rg.y;
   if (!MSM_CHECK(S, b >= S.atom_off && e <= S.atom_off + S.n && b <= e)) return;
   int rank = 0;
   for (int t = b; t < e; t++) rank += (bucket[t] < g);
@@ -280,8 +291,8 @@ void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitem
   int ntiles = (total_cells + kScanTile - 1) / kScanTile;
   k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(w.cell_count, total_cells, w.cell_start, w.scan_tiles);
   k_scan_fix<<<ntiles, kScanThreads, 0, s>>>(w.cell_start, total_cells, w.scan_tiles, ntiles);
-  k_bin_scatter<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_id, w.slot, w.cell_start, w.bucket);
-  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.cell_start, w.bucket, w.perm, w.scell,
+  k_bin_scatter<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_id, w.slot, w.cell_start, w.bucket, w.crange);
+  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.crange, w.bucket, w.perm, w.scell,
                                        w.xq, w.uq);
 }
 

@@ -2,37 +2,66 @@
 // Sec. 3.2.2 for the derivatives):
 //   phi_i = phi0_i + phi^(1+)_i  (= dE/dq_i),
 //   field_i = -grad phi(r_i) (both parts), F_i = q_i field_i,
-//   E = 1/2 sum_i q_i phi_i   (FP64, fixed-order block sums),
+//   E = 1/2 sum_i q_i phi_i   (each product exact as hi + lo in FP32, summed as
+//                              hi + lo pairs by error-free transformations in
+//                              a fixed order, FP64 for the final value),
 //   W = W0 + W^(1+)           (FP64, fixed-order sums of the block partials),
 // written back in the caller's atom order through the sort permutation.
 #include "msm_internal.h"
 
 namespace msm {
 
+// Knuth's TwoSum: s + t = a + b exactly (round-to-nearest, no contraction)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a += b for sums kept as hi + lo: the hi parts by TwoSum, every rounding
+// error of theirs collected in lo
+__device__ __forceinline__ void add_hl(float2& a, float2 b) {
+  float s, t;
+  two_sum(a.x, b.x, s, t);
+  a.x = s;
+  a.y = __fadd_rn(a.y, __fadd_rn(b.y, t));
+}
+
+__device__ __forceinline__ float2 shfl_down_hl(float2 v, int o) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+
+// The energy sum sum_i q_i phi_i: each product is split exactly as hi + lo
+// (lo by FMA) and the terms are summed as hi + lo pairs in a fixed order (warp
+// shuffles, then the block, then k_energy over the blocks in order): the
+// result is the exact sum up to the FP32 rounding of the lo parts, about
+// 2^-47 of sum |q phi|, with no FP64 arithmetic (slow on this GPU) before the
+// final conversion; 1/2 is applied at the end (exact).
 __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ sys,
                                                      const AtomItem* __restrict__ items,
                                                      const int* __restrict__ perm, const float4* __restrict__ xq,
                                                      const float* __restrict__ phi_sr, const float* __restrict__ phi_lr,
                                                      const float4* __restrict__ f_sr, const float4* __restrict__ f_lr,
                                                      float* __restrict__ phi, float* __restrict__ forces,
-                                                     double* __restrict__ part_e, double* __restrict__ part_q) {
-  __shared__ double red[kChunk / 32][3];
+                                                     float2* __restrict__ part_e, float2* __restrict__ part_q) {
+  __shared__ float2 red[kChunk / 32][2];
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   int local = it.start + threadIdx.x;
-  double e = 0.0;
-  float qs = 0.f, qa = 0.f;  // sum q and sum |q| (FP32 within a warp: only compared with a 1e-5 threshold)
+  float2 e = make_float2(0.f, 0.f);
+  float qs = 0.f, qa = 0.f;  // sum q and sum |q| (FP32: only compared with a 1e-5 threshold)
   if ((int)threadIdx.x < it.count && local < S.n) {
     int k = S.atom_off + local;
     int g = perm[k];
     if (!MSM_CHECK(S, g >= S.atom_off && g < S.atom_off + S.n)) g = S.atom_off;
-    float ph = phi_sr[k] + phi_lr[k];
-    e = 0.5 * (double)xq[k].w * (double)ph;
-    qs = xq[k].w;
-    qa = fabsf(qs);
+    const float qk = xq[k].w;
+    const float ph = phi_sr[k] + phi_lr[k];
+    e.x = __fmul_rn(qk, ph);
+    e.y = fmaf(qk, ph, -e.x);
+    qs = qk;
+    qa = fabsf(qk);
     if (phi) phi[g] = ph;
     if (forces) {
-      const float qk = xq[k].w;
       float4 a = f_sr[k], b = f_lr[k];
       forces[3 * (long long)g + 0] = qk * (a.x + b.x);
       forces[3 * (long long)g + 1] = qk * (a.y + b.y);
@@ -40,56 +69,62 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_down_sync(0xffffffffu, e, o);
+    add_hl(e, shfl_down_hl(e, o));
     qs += __shfl_down_sync(0xffffffffu, qs, o);
     qa += __shfl_down_sync(0xffffffffu, qa, o);
   }
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5][0] = e;
-    red[threadIdx.x >> 5][1] = (double)qs;
-    red[threadIdx.x >> 5][2] = (double)qa;
+    red[threadIdx.x >> 5][1] = make_float2(qs, qa);
   }
   __syncthreads();
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < kChunk / 32; w++) s += red[w][threadIdx.x];
-    if (threadIdx.x == 0) part_e[blockIdx.x] = s;
-    else part_q[2 * blockIdx.x + threadIdx.x - 1] = s;
+  if (threadIdx.x == 0) {
+    float2 t = red[0][0], u = red[0][1];
+    for (int w = 1; w < kChunk / 32; w++) {
+      add_hl(t, red[w][0]);
+      u.x += red[w][1].x;
+      u.y += red[w][1].y;
+    }
+    part_e[blockIdx.x] = t;
+    part_q[blockIdx.x] = u;
   }
 }
 
-// one block per system: energy = sum of the system's item partials in order;
-// a system with a periodic axis and a net charge raises the non-neutral warning
-__global__ void k_energy(const SysDev* __restrict__ sys, const double* __restrict__ part_e,
-                         const double* __restrict__ part_q, double* __restrict__ energy, int* __restrict__ status) {
-  __shared__ double red[32][3];
+// one block per system: energy = 1/2 (sum of the system's item partials, in
+// order); a system with a periodic axis and a net charge raises the
+// non-neutral warning
+__global__ void __launch_bounds__(1024) k_energy(const SysDev* __restrict__ sys, const float2* __restrict__ part_e,
+                                                 const float2* __restrict__ part_q, double* __restrict__ energy,
+                                                 int* __restrict__ status) {
+  __shared__ float2 red[32][2];
   const SysDev& S = sys[blockIdx.x];
-  double acc = 0.0, qs = 0.0, qa = 0.0;
+  float2 acc = make_float2(0.f, 0.f);
+  float qs = 0.f, qa = 0.f;
   for (int i = threadIdx.x; i < S.nitem; i += blockDim.x) {
-    acc += part_e[S.item0 + i];
-    qs += part_q[2 * (S.item0 + i)];
-    qa += part_q[2 * (S.item0 + i) + 1];
+    add_hl(acc, part_e[S.item0 + i]);
+    const float2 u = part_q[S.item0 + i];
+    qs += u.x;
+    qa += u.y;
   }
   for (int o = 16; o > 0; o >>= 1) {
-    acc += __shfl_down_sync(0xffffffffu, acc, o);
+    add_hl(acc, shfl_down_hl(acc, o));
     qs += __shfl_down_sync(0xffffffffu, qs, o);
     qa += __shfl_down_sync(0xffffffffu, qa, o);
   }
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5][0] = acc;
-    red[threadIdx.x >> 5][1] = qs;
-    red[threadIdx.x >> 5][2] = qa;
+    red[threadIdx.x >> 5][1] = make_float2(qs, qa);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0, sq = 0.0, sa = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-      s += red[w][0];
-      sq += red[w][1];
-      sa += red[w][2];
+    float2 t = red[0][0], u = red[0][1];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      add_hl(t, red[w][0]);
+      u.x += red[w][1].x;
+      u.y += red[w][1].y;
     }
-    energy[blockIdx.x] = s;
-    if ((S.pbc[0] | S.pbc[1] | S.pbc[2]) && fabs(sq) > (double)kNeutralTol * sa) atomicOr(status, kDevNonNeutral);
+    energy[blockIdx.x] = 0.5 * ((double)t.x + (double)t.y);
+    if ((S.pbc[0] | S.pbc[1] | S.pbc[2]) && fabsf(u.x) > kNeutralTol * u.y) atomicOr(status, kDevNonNeutral);
   }
 }
 
@@ -206,7 +241,7 @@ void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int 
 }
 
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s) {
-  k_energy<<<nsys, 256, 0, s>>>(t.sys, w.part_e, w.part_q, energy, w.status);
+  k_energy<<<nsys, 1024, 0, s>>>(t.sys, w.part_e, w.part_q, energy, w.status);
 }
 
 // nslice (1 .. kVirialSlices) slices per system: about 1024 partials each for

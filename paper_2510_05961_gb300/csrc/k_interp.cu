@@ -7,10 +7,11 @@
 // centred cardinal B-splines of order p (Sec. 3.3), evaluated in FP32 by the
 // uniform Cox-de Boor recursion on the fractional grid coordinate.
 //
-// Anterpolation reads the cell-sorted atoms: each thread owns one level-1 grid
-// column of a tile and sums, in a fixed order, the atoms of the cells whose
-// B-spline support reaches it. No atomics; the result is the same on every
-// run.
+// Anterpolation reads the cell-sorted atoms, one warp per binning column: the
+// column's partial sums over the grid points its atoms reach, then one sum per
+// grid point (k_anterp_cols, k_anterp_sum); the gather by grid columns
+// (k_anterp) serves dipole charges and footprints too wide for those. No
+// atomics; the result is the same on every run.
 #include "msm_internal.h"
 
 namespace msm {

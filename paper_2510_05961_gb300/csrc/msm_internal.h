@@ -138,14 +138,15 @@ struct Work {
   int* bucket;
   int* perm;
   int* scell;
+  int2* crange;    // binning: each atom's cell range [b, e) in the sorted order, atom order
   float4* xq;      // Cartesian position (the periodic image next to its cell) and charge, sorted
   float4* uq;      // level-1 grid coordinates and charge, sorted order
   float* phi_sr;   // short-range potential incl. self term, sorted
   float4* f_sr;    // short-range field -grad phi0 (force / q), sorted
   float* phi_lr;   // long-range potential, sorted
   float4* f_lr;    // long-range field -grad phi^(1+) (force / q), sorted
-  double* part_e;  // per atom item: 1/2 sum q phi
-  double* part_q;  // per atom item: sum q and sum |q|
+  float2* part_e;  // per atom item: sum q phi as hi + lo
+  float2* part_q;  // per atom item: sum q and sum |q|
   double* part_w0; // per warp of each atom item: 6 short-range virial components
   double* part_wg; // per virial item: 6 grid virial components
   double* part_vs; // per system and reduction slice: 6 virial components

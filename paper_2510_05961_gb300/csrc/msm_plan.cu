@@ -1171,6 +1171,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_bucket = take(sizeof(int) * N);
   L_perm = take(sizeof(int) * N);
   L_scell = take(sizeof(int) * N);
+  L_crange = take(sizeof(int2) * N);
   L_xq = take(sizeof(float4) * N);
   L_uq = take(sizeof(float4) * N);
   L_phi_sr = take(sizeof(float) * N);
@@ -1440,19 +1441,20 @@ Work Engine::resolve(void* ws) const {
   w.bucket = (int*)(b + L_bucket);
   w.perm = (int*)(b + L_perm);
   w.scell = (int*)(b + L_scell);
+  w.crange = (int2*)(b + L_crange);
   w.xq = (float4*)(b + L_xq);
   w.uq = (float4*)(b + L_uq);
   w.phi_sr = (float*)(b + L_phi_sr);
   w.phi_lr = (float*)(b + L_phi_lr);
   w.f_sr = (float4*)(b + L_f_sr);
   w.f_lr = (float4*)(b + L_f_lr);
-  w.part_e = (double*)(b + L_part_e);
+  w.part_e = (float2*)(b + L_part_e);
   w.io_pos = (float*)(b + L_io_pos);
   w.io_q = (float*)(b + L_io_q);
   w.io_dpos = (float*)(b + L_io_dpos);
   w.io_dq = (float*)(b + L_io_dq);
   w.io_e = (double*)(b + L_io_e);
-  w.part_q = (double*)(b + L_part_q);
+  w.part_q = (float2*)(b + L_part_q);
   w.part_w0 = (double*)(b + L_part_w0);
   w.part_wg = (double*)(b + L_part_wg);
   w.part_vs = (double*)(b + L_part_vs);
