@@ -135,6 +135,9 @@ typedef struct {
   int stencil_kind[20]; /* 0 = ball stencil with wrap/zero, 1 = dense folded box */
   int anterp_tz;     /* anterpolation tile z-extent in use (16, 32, 64; msm_autotune) */
   int short_block;   /* short-range threads per block in use (128, 256; msm_autotune) */
+  int anterp_kind;   /* anterpolation in use: 1 = by binning columns (column partials, then their
+                        sum per grid point), 0 = gather by grid columns (footprints too wide for
+                        the column kernel at this tile z-extent); -1 from msm_plan_describe */
 } msm_plan_info;
 
 /* Create a plan: validates the settings synchronously, builds the level

@@ -56,7 +56,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("nlev", C.c_int), ("ncomp", C.c_int), ("M", C.c_int * 3), ("h1", C.c_double * 3),
                 ("lo", (C.c_int * 3) * 20), ("n", (C.c_int * 3) * 20), ("R", C.c_int * 3), ("C", C.c_int * 3),
                 ("nnbr", C.c_int * 3), ("stencil_kind", C.c_int * 20), ("anterp_tz", C.c_int),
-                ("short_block", C.c_int)]
+                ("short_block", C.c_int), ("anterp_kind", C.c_int)]
 
 
 _lib = None

@@ -393,6 +393,7 @@ int msm_plan_get_info(msm_plan plan, msm_plan_info* info) {
   fill_info(plan->eng.sys[0], info);
   info->anterp_tz = plan->eng.anterp_tz;
   info->short_block = plan->eng.short_block;
+  info->anterp_kind = plan->eng.ant_wstride > 0 ? 1 : 0;
   return MSM_OK;
 }
 
@@ -403,6 +404,7 @@ int msm_plan_describe(const msm_params* params, msm_plan_info* info) {
   int rc = plan_system(*params, S, &err);
   if (rc) return set_err(rc, err);
   fill_info(S, info);
+  info->anterp_kind = -1;
   return MSM_OK;
 }
 

@@ -66,7 +66,7 @@ class Plan:
             "lo": [list(I.lo[l]) for l in range(I.ncomp)], "n": [list(I.n[l]) for l in range(I.ncomp)],
             "R": list(I.R), "C": list(I.C), "nnbr": list(I.nnbr),
             "stencil_kind": [I.stencil_kind[l] for l in range(I.ncomp)],
-            "anterp_tz": I.anterp_tz, "short_block": I.short_block,
+            "anterp_tz": I.anterp_tz, "short_block": I.short_block, "anterp_kind": I.anterp_kind,
         }
 
     def debug_array(self, which, level=1):

@@ -130,6 +130,30 @@ def test_level_grids(key):
         assert np.abs(eg - eo).max() <= 1e-4 * escale, ("e", l)
 
 
+def test_anterpolation_paths_agree():
+    """Both anterpolation kernels on one open cluster whose binning columns reach 11 x 11 grid
+    columns: by binning columns (column partials, then their sum per grid point) at a 16-point
+    z-extent, and the gather by grid columns that a 64-point z-extent falls back to (the column
+    kernel's footprint would not fit in shared memory). Each against the oracle's level-1 grid
+    charge (1e-4 of its largest entry) and against each other (FP32 summation order only: 1e-6)."""
+    import oracle as O
+    O.build()
+    w = W.open_cluster(n=500, side=24.0, seed=5, h=1.0)
+    P = O.plan_for(w)
+    ref = O.anterp(P, w.pos.astype(np.float64), w.q.astype(np.float64))
+    scale = np.abs(ref).max()
+    grids = {}
+    for tz, kind in ((16, 1), (64, 0)):
+        plan = make_plan(w)
+        plan.set_tuning(tz, 256)
+        r = gpu_run(w, plan=plan, forces=False, virial=False)
+        assert plan.info()["anterp_kind"] == kind, (tz, plan.info())
+        g = r["plan"].debug_array(2, 1).cpu().numpy().reshape(P.level_shape(1))
+        assert np.abs(g - ref).max() <= 1e-4 * scale, tz
+        grids[tz] = g
+    assert np.abs(grids[16] - grids[64]).max() <= 1e-6 * scale
+
+
 # ---------------------------------------------------------------- end to end
 @pytest.mark.parametrize("key", list(WORKLOADS))
 def test_forward_backward_parity(key):
