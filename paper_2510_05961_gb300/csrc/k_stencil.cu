@@ -554,9 +554,11 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ s
 }
 
 // ------------------------------------------------------------------ boxes
-// One warp per output point; the lanes split the box entries t (coalesced
-// stencil loads), then a shuffle reduction.
-constexpr int kBoxThreads = 256;
+// Levels of at most kBoxStage points (all folded levels of batch plans and the
+// usual open top levels): one block stages the whole level in shared memory
+// and each thread sums the box for one output point. Larger levels: one warp
+// per output point; the lanes split the box entries t (coalesced stencil
+// loads), then a shuffle reduction.
 
 struct BoxIter {
   int a, b, c;
@@ -588,16 +590,57 @@ __device__ __forceinline__ int box_src(const LevDev& L, const int m[3], const Bo
   return (s[0] * L.n[1] + s[1]) * L.n[2] + s[2];
 }
 
+// storage index of q_(m - d) along one axis of a box level, d = e + blo, or -1
+// (open axis, outside); periodic level sizes are powers of two
+__device__ __forceinline__ int box_axis(const LevDev& L, int d, int m, int e) {
+  const int s = m - (e + L.blo[d]);
+  if (L.per[d]) return s & (L.n[d] - 1);
+  return (s >= 0 && s < L.n[d]) ? s : -1;
+}
+
 __global__ void __launch_bounds__(kBoxThreads) k_stencil_box(const LevDev* __restrict__ levs,
                                                              const RangeItem* __restrict__ items,
                                                              const float* __restrict__ kpool,
                                                              float* __restrict__ grid) {
+  __shared__ float qs[kBoxStage];
   const RangeItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nt = L.bsz[0] * L.bsz[1] * L.bsz[2];
+  const int npts = L.n[0] * L.n[1] * L.n[2];
   const float* q = grid + L.q_off;
   const float* K = kpool + L.k_off;
+  if (npts <= kBoxStage) {
+    // the whole level in shared memory, one output per thread; the lanes of a
+    // warp read the same stencil entry (one broadcast load)
+    for (int e = threadIdx.x; e < npts; e += kBoxThreads) qs[e] = q[e];
+    __syncthreads();
+    if ((int)threadIdx.x >= it.count) return;
+    const int idx = it.start + threadIdx.x;
+    const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
+    // nested sums (row, plane, box) keep the rounding of each at a few dozen terms
+    float acc = 0.f;
+    for (int a = 0; a < L.bsz[0]; a++) {
+      const int sx = box_axis(L, 0, m[0], a);
+      if (sx < 0) continue;
+      float pl = 0.f;
+      for (int b = 0; b < L.bsz[1]; b++) {
+        const int sy = box_axis(L, 1, m[1], b);
+        if (sy < 0) continue;
+        const float* qr = qs + (sx * L.n[1] + sy) * L.n[2];
+        const float* kr = K + (a * L.bsz[1] + b) * L.bsz[2];
+        float row = 0.f;
+        for (int c = 0; c < L.bsz[2]; c++) {
+          const int sz = box_axis(L, 2, m[2], c);
+          if (sz >= 0) row = fmaf(__ldg(kr + c), qr[sz], row);
+        }
+        pl += row;
+      }
+      acc += pl;
+    }
+    grid[L.e_off + idx] = acc * L.scale;
+    return;
+  }
   for (int o = warp; o < it.count; o += kBoxThreads / 32) {
     const int idx = it.start + o;
     const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
@@ -620,27 +663,71 @@ __global__ void __launch_bounds__(kBoxThreads) k_virial_box(const LevDev* __rest
                                                             const float* __restrict__ grid,
                                                             double* __restrict__ part) {
   __shared__ double red[kBoxThreads / 32][6];
+  __shared__ float qs[kBoxStage];
   const RangeItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nt = L.bsz[0] * L.bsz[1] * L.bsz[2];
+  const int npts = L.n[0] * L.n[1] * L.n[2];
   const float* q = grid + L.q_off;
   const float* K = kpool + L.dk_off;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int o = warp; o < it.count; o += kBoxThreads / 32) {
-    const int idx = it.start + o;
-    const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
-    const float qm = q[idx];
-    BoxIter ti;
-    ti.init(lane, L);
-    for (int t = lane; t < nt; t += 32) {
-      int s = box_src(L, m, ti);
-      if (s >= 0) {
-        const float cq = qm * q[s];
+  if (npts <= kBoxStage) {
+    // the whole level in shared memory, one point m per thread:
+    // w6 += q_m sum_d dK_d q_(m - d)
+    for (int e = threadIdx.x; e < npts; e += kBoxThreads) qs[e] = q[e];
+    __syncthreads();
+    if ((int)threadIdx.x < it.count) {
+      const int idx = it.start + threadIdx.x;
+      const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
+      const float qm = qs[idx];
+      // nested sums (row, plane, box) as in the stencil
+      for (int a = 0; a < L.bsz[0]; a++) {
+        const int sx = box_axis(L, 0, m[0], a);
+        if (sx < 0) continue;
+        float pl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int b = 0; b < L.bsz[1]; b++) {
+          const int sy = box_axis(L, 1, m[1], b);
+          if (sy < 0) continue;
+          const float* qr = qs + (sx * L.n[1] + sy) * L.n[2];
+          const int t0 = (a * L.bsz[1] + b) * L.bsz[2];
+          float row[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int c = 0; c < L.bsz[2]; c++) {
+            const int sz = box_axis(L, 2, m[2], c);
+            if (sz < 0) continue;
+            const float cq = qm * qr[sz];
+            const float4 k0 = __ldg(reinterpret_cast<const float4*>(K + 8 * (long long)(t0 + c)));
+            const float4 k1 = __ldg(reinterpret_cast<const float4*>(K + 8 * (long long)(t0 + c) + 4));
+            row[0] = fmaf(k0.x, cq, row[0]);
+            row[1] = fmaf(k0.y, cq, row[1]);
+            row[2] = fmaf(k0.z, cq, row[2]);
+            row[3] = fmaf(k0.w, cq, row[3]);
+            row[4] = fmaf(k1.x, cq, row[4]);
+            row[5] = fmaf(k1.y, cq, row[5]);
+          }
 #pragma unroll
-        for (int k = 0; k < 6; k++) w6[k] = fmaf(__ldg(K + (long long)k * nt + t), cq, w6[k]);
+          for (int k = 0; k < 6; k++) pl[k] += row[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) w6[k] += pl[k];
       }
-      ti.advance32(L);
+    }
+  } else {
+    for (int o = warp; o < it.count; o += kBoxThreads / 32) {
+      const int idx = it.start + o;
+      const int m[3] = {idx / (L.n[1] * L.n[2]), (idx / L.n[2]) % L.n[1], idx % L.n[2]};
+      const float qm = q[idx];
+      BoxIter ti;
+      ti.init(lane, L);
+      for (int t = lane; t < nt; t += 32) {
+        int s = box_src(L, m, ti);
+        if (s >= 0) {
+          const float cq = qm * q[s];
+#pragma unroll
+          for (int k = 0; k < 6; k++) w6[k] = fmaf(__ldg(K + 8 * (long long)t + k), cq, w6[k]);
+        }
+        ti.advance32(L);
+      }
     }
   }
 #pragma unroll

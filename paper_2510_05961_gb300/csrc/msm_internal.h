@@ -25,7 +25,9 @@ constexpr int kBallBZ = 16;        // outputs per thread along z
 constexpr int kBallTZ = 32;        // stencil tile depth (z)
 constexpr int kBallThreads = kBallTY * (kBallTZ / kBallBZ);
 constexpr int kBallRmax = 24;      // largest ball-stencil radius with a compiled kernel
-constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block)
+constexpr int kBoxChunk = 16;      // outputs per box-stencil work item (one block) of a level above kBoxStage points
+constexpr int kBoxStage = 8192;    // box levels of at most this many points: staged in shared memory, one output per thread
+constexpr int kBoxThreads = 256;   // threads per box-stencil block
 constexpr int kResTX = 4, kResTY = 4, kResTZ = 16;  // restriction tiles (coarse points)
 constexpr int kResNT = kResTX * kResTY * kResTZ;    // threads per restriction block
 constexpr int kVirialSlices = 64;  // most virial reduction slices per system
@@ -110,7 +112,7 @@ struct LevDev {
   float scale;              // stencil scale 2^-(l-1) relative to the stored values
   long long k_off;          // stencil values. box: dense bsz product; ball: per (dx, dy)
                             // column, dz = -hz .. hz at [0, 2hz] of a row of kSK(hz) floats
-  long long dk_off;         // virial weights. box: 6 arrays like k; ball: [dx][6][dy][row]
+  long long dk_off;         // virial weights. box: per entry the 6 values padded to 8 (16-byte aligned); ball: [dx][6][dy][row]
   long long w_off;          // ball: column half-widths of K (int pool, (2Rx+1)(2Ry+1), -1 = empty)
   long long wh_off;         // ball: column half-widths of the virial weights
   int hz;                   // ball: z halo of the padded grid (>= R[2], multiple of 4)

@@ -921,8 +921,14 @@ void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>&
         while (kp.size() % 4) kp.push_back(0.f);
         L.k_off = (long long)kp.size();
         kp.insert(kp.end(), Lv.kbox.begin(), Lv.kbox.end());
+        // virial weights interleaved per entry, 6 values padded to 8 (two 16-byte loads;
+        // the array starts on a 16-byte boundary)
+        while (kp.size() % 4) kp.push_back(0.f);
         L.dk_off = (long long)kp.size();
-        kp.insert(kp.end(), Lv.dkbox.begin(), Lv.dkbox.end());
+        const size_t nt = Lv.kbox.size();
+        kp.resize(kp.size() + 8 * nt, 0.f);
+        for (size_t t = 0; t < nt; t++)
+          for (int c = 0; c < 6; c++) kp[L.dk_off + 8 * t + c] = Lv.dkbox[c * nt + t];
       }
     }
     while (kp.size() % 4) kp.push_back(0.f);
@@ -1104,8 +1110,9 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
             for (int z = 0; z < L.pn[2]; z += kPadTZ) pad_items.push_back({li, x, y, z});
       } else {
         long long npts = (long long)L.n[0] * L.n[1] * L.n[2];
-        for (long long st = 0; st < npts; st += kBoxChunk)
-          box_items.push_back({li, (int)st, (int)std::min<long long>(kBoxChunk, npts - st)});
+        const int chunk = npts <= kBoxStage ? kBoxThreads : kBoxChunk;  // one output per thread when staged
+        for (long long st = 0; st < npts; st += chunk)
+          box_items.push_back({li, (int)st, (int)std::min<long long>(chunk, npts - st)});
       }
     }
   }
