@@ -554,11 +554,11 @@ __global__ void __launch_bounds__(NT) k_virial_ball(const SysDev* __restrict__ s
 }
 
 // ------------------------------------------------------------------ boxes
-// Levels of at most kBoxStage points (all folded levels of batch plans and the
-// usual open top levels): one block stages the whole level in shared memory
-// and each thread sums the box for one output point. Larger levels: one warp
-// per output point; the lanes split the box entries t (coalesced stencil
-// loads), then a shuffle reduction.
+// Batch plans, levels of at most kBoxStage points (the folded small levels and
+// the open top levels): one block stages the whole level in shared memory and
+// each thread sums the box for one output point. Single-system plans and larger
+// levels: one warp per output point; the lanes split the box entries t
+// (coalesced stencil loads), then a shuffle reduction.
 
 struct BoxIter {
   int a, b, c;
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_stencil_box(const LevDev* __res
   const int npts = L.n[0] * L.n[1] * L.n[2];
   const float* q = grid + L.q_off;
   const float* K = kpool + L.k_off;
-  if (npts <= kBoxStage) {
+  if (L.box_tile) {
     // the whole level in shared memory, one output per thread; the lanes of a
     // warp read the same stencil entry (one broadcast load)
     for (int e = threadIdx.x; e < npts; e += kBoxThreads) qs[e] = q[e];
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_virial_box(const LevDev* __rest
   const float* q = grid + L.q_off;
   const float* K = kpool + L.dk_off;
   float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (npts <= kBoxStage) {
+  if (L.box_tile) {
     // the whole level in shared memory, one point m per thread:
     // w6 += q_m sum_d dK_d q_(m - d)
     for (int e = threadIdx.x; e < npts; e += kBoxThreads) qs[e] = q[e];

@@ -107,6 +107,8 @@ struct LevDev {
   int n[3], lo[3], per[3];  // grid points, first grid index, periodic flags
   long long q_off, e_off;   // float offsets of q~^l and e^l in the grid pool
   int kind;                 // 0 = ball stencil (radius R, wrap/zero), 1 = dense box (folded)
+  int box_tile;             // box: 1 = staged in shared memory, one output per thread (batch plans,
+                            // levels of at most kBoxStage points); 0 = one warp per output
   int R[3];                 // ball radius per axis
   int blo[3], bsz[3];       // box: offsets d in [blo, blo + bsz)
   float scale;              // stencil scale 2^-(l-1) relative to the stored values

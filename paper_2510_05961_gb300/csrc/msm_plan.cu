@@ -1110,7 +1110,10 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
             for (int z = 0; z < L.pn[2]; z += kPadTZ) pad_items.push_back({li, x, y, z});
       } else {
         long long npts = (long long)L.n[0] * L.n[1] * L.n[2];
-        const int chunk = npts <= kBoxStage ? kBoxThreads : kBoxChunk;  // one output per thread when staged
+        // staged boxes in batch plans (many levels at once); a single system's few outputs per
+        // level finish sooner with a warp per output (the lanes split the box entries)
+        hlev[li].box_tile = (!single && npts <= kBoxStage) ? 1 : 0;
+        const int chunk = hlev[li].box_tile ? kBoxThreads : kBoxChunk;
         for (long long st = 0; st < npts; st += chunk)
           box_items.push_back({li, (int)st, (int)std::min<long long>(chunk, npts - st)});
       }
