@@ -386,16 +386,20 @@ __device__ __forceinline__ int cell_lo(const SysDev& S, int d, int c) {
 
 // shared-memory layout of one warp's footprint: point (fx, fy, z) of the
 // segment at fx * xs + fy * zp + z + p - 1, with p - 1 rows of padding on both
-// sides of the segment (the parts of an atom's support outside it land there);
-// zp >= tz + 2p - 2 with zp = 4 mod 16 and xs = fy_n zp rounded up to 16 mod 32,
-// so that for p = 4 the 32 lanes' offsets 16 i + zp j + k fall in 32 distinct banks
+// sides of the segment (the parts of an atom's support outside it land there),
+// zp >= tz + 2p - 2. For p = 4, lane l adds the products (i, j, k) with
+// 4 i + j = l / 2 and k = l % 2 + {0, 2}: zp = 2 mod 16 and xs = 8 mod 32 put
+// the 32 lanes' offsets 8 i + zp j + k in 32 distinct banks; other orders use
+// zp = 4 mod 16 and xs = 16 mod 32 (their lanes take (ij, k) = divmod(l + 32 r, p))
 __host__ __device__ inline int ant_zp(int tz, int p) {
   int zp = tz + 2 * p - 2;
-  return zp + ((4 - zp % 16) + 16) % 16;
+  const int want = p == 4 ? 2 : 4;
+  return zp + ((want - zp % 16) + 16) % 16;
 }
 __host__ __device__ inline int ant_xs(int fy_n, int tz, int p) {
   const int xs = fy_n * ant_zp(tz, p);
-  return xs + ((16 - xs % 32) + 32) % 32;
+  const int want = p == 4 ? 8 : 16;
+  return xs + ((want - xs % 32) + 32) % 32;
 }
 // staging of 32 atoms: q w_x w_y (p^2 + 1 per atom), w_z (p + 1 per atom), base offsets
 __host__ __device__ inline int ant_stage_floats(int p) { return 32 * (p * p + 1) + 32 * (p + 1) + 32; }
@@ -480,24 +484,45 @@ __global__ void __launch_bounds__(kAntWarps * 32, 4) k_anterp_cols(const SysDev*
 #pragma unroll
           for (int jj = 0; jj < P; jj++) sq[lane * SQ + i * P + jj] = qx * wy[jj];
         }
+        if constexpr (P == 4) {
+          // w_z as (w0, w2, w1, w3): a lane reads its two values k0, k0 + 2 with one 8-byte load
+          sz[lane * 4 + 0] = w3[0];
+          sz[lane * 4 + 1] = w3[2];
+          sz[lane * 4 + 2] = w3[1];
+          sz[lane * 4 + 3] = w3[3];
+        } else {
 #pragma unroll
-        for (int k = 0; k < P; k++) sz[lane * SZ + k] = w3[k];
+          for (int k = 0; k < P; k++) sz[lane * SZ + k] = w3[k];
+        }
         sb[lane] = base;
       }
       __syncwarp();
-      for (int a = 0; a < na; a++) {
-        const int base = sb[a];
-        const float* qa = sq + a * SQ;
-        const float* za = sz + a * SZ;
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-          const int c = lane + 32 * r;
-          if (P3 % 32 != 0 && c >= P3) continue;
-          const int ij = c / P, k = c % P;
-          float* dst = acc + base + (ij / P) * XS + (ij % P) * ZP + k;
-          *dst = fmaf(qa[ij], za[k], *dst);
+      if constexpr (P == 4) {
+        const int ij = lane >> 1, k0 = lane & 1;
+        const int off = (ij >> 2) * XS + (ij & 3) * ZP + k0;
+        for (int a = 0; a < na; a++) {
+          float* dst = acc + sb[a] + off;
+          const float w = sq[a * SQ + ij];
+          const float2 z2 = *reinterpret_cast<const float2*>(sz + a * 4 + 2 * k0);
+          dst[0] = fmaf(w, z2.x, dst[0]);
+          dst[2] = fmaf(w, z2.y, dst[2]);
+          __syncwarp();  // lanes of the next atom may write the points this one wrote
         }
-        __syncwarp();  // lanes of the next atom may write the points this one wrote
+      } else {
+        for (int a = 0; a < na; a++) {
+          const int base = sb[a];
+          const float* qa = sq + a * SQ;
+          const float* za = sz + a * SZ;
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            const int c = lane + 32 * r;
+            if (P3 % 32 != 0 && c >= P3) continue;
+            const int ij = c / P, k = c % P;
+            float* dst = acc + base + (ij / P) * XS + (ij % P) * ZP + k;
+            *dst = fmaf(qa[ij], za[k], *dst);
+          }
+          __syncwarp();  // lanes of the next atom may write the points this one wrote
+        }
       }
     }
     uz += wend - wz + 1;
