@@ -552,46 +552,57 @@ __device__ __forceinline__ void foot_cells(const SysDev& S, int d, int m, int F,
   }
 }
 
-// One block per level-1 grid column (gx, gy) and chunk of kAntSumZ points along
-// z: the block lists the (binning column, footprint offset) pairs that hold
-// the column once, then every thread sums them for its z.
+// One block per kAntSumY level-1 grid columns (gx, gy .. gy + kAntSumY - 1) and
+// chunk of kAntSumZ points along z, kAntSumZ threads per column: the threads of
+// a column test the candidate (binning column, footprint offset) pairs that may
+// hold it in parallel, then each sums the valid ones for its z in the
+// candidates' order.
 template <int P>
-__global__ void __launch_bounds__(kAntSumZ, 8) k_anterp_sum(const SysDev* __restrict__ sys, const LevDev* __restrict__ levs,
-                                                         const TileItem* __restrict__ items,
-                                                         const float* __restrict__ apart, float* __restrict__ grid) {
-  __shared__ long long off[kAntFootMax * kAntFootMax];
-  __shared__ int noff;
+__global__ void __launch_bounds__(kAntSumZ * kAntSumY, 8) k_anterp_sum(const SysDev* __restrict__ sys,
+                                                                    const LevDev* __restrict__ levs,
+                                                                    const TileItem* __restrict__ items,
+                                                                    const float* __restrict__ apart,
+                                                                    float* __restrict__ grid) {
+  constexpr int NC = kAntFootMax * kAntFootMax;
+  __shared__ long long off[kAntSumY][NC];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = levs[it.lev];
   const SysDev& S = sys[L.sys];
-  const int gx = it.x0, gy = it.y0;
+  const int col = threadIdx.x / kAntSumZ, tz = threadIdx.x % kAntSumZ;
+  const int gx = it.x0, gy = it.y0 + col;
   const long long nz = L.n[2];
-  if (threadIdx.x == 0) {
-    const int Fx = S.afoot[0], Fy = S.afoot[1], Cx = S.C[0], Cy = S.C[1];
-    const int mx = gx + L.lo[0], my = gy + L.lo[1];
-    int xa, xb, ya, yb;
-    foot_cells<P>(S, 0, mx, Fx, xa, xb);
-    foot_cells<P>(S, 1, my, Fy, ya, yb);
-    int n = 0;
-    for (int c = xa; c <= xb; c++) {
-      const int fx = mx - cell_lo<P>(S, 0, c);
-      if (fx < 0 || fx >= Fx) continue;
+  const int Fx = S.afoot[0], Fy = S.afoot[1], Cx = S.C[0], Cy = S.C[1];
+  const int mx = gx + L.lo[0], my = gy + L.lo[1];
+  int xa, xb, ya, yb;
+  foot_cells<P>(S, 0, mx, Fx, xa, xb);
+  foot_cells<P>(S, 1, my, Fy, ya, yb);
+  const int ny = yb - ya + 1, nc = min((xb - xa + 1) * ny, NC);
+  for (int t = tz; t < nc; t += kAntSumZ) {
+    const int c = xa + t / ny, e = ya + t % ny;
+    const int fx = mx - cell_lo<P>(S, 0, c), fy = my - cell_lo<P>(S, 1, e);
+    long long o = -1;
+    if (fx >= 0 && fx < Fx && fy >= 0 && fy < Fy) {
       const int wx = S.pbc[0] ? (c & (Cx - 1)) : c;  // C is a power of two on a periodic axis
-      for (int e = ya; e <= yb; e++) {
-        const int fy = my - cell_lo<P>(S, 1, e);
-        if (fy < 0 || fy >= Fy) continue;
-        const int wy = S.pbc[1] ? (e & (Cy - 1)) : e;
-        if (n < kAntFootMax * kAntFootMax) off[n++] = S.apart + ((long long)(wx * Cy + wy) * (Fx * Fy) + fx * Fy + fy) * nz;
-      }
+      const int wy = S.pbc[1] ? (e & (Cy - 1)) : e;
+      o = S.apart + ((long long)(wx * Cy + wy) * (Fx * Fy) + fx * Fy + fy) * nz;
     }
-    noff = n;
+    off[col][t] = o;
   }
   __syncthreads();
-  const int z = it.z0 + (int)threadIdx.x;
-  if (z >= L.n[2]) return;
-  const int n = noff;
+  const int z = it.z0 + tz;
+  if (gy >= L.n[1] || z >= L.n[2]) return;
+  // eight loads in flight before their sum (in the candidates' order)
   float v = 0.f;
-  for (int t = 0; t < n; t++) v += __ldg(apart + off[t] + z);
+  for (int t0 = 0; t0 < nc; t0 += 8) {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const long long o = t0 + k < nc ? off[col][t0 + k] : -1;
+      x[k] = o >= 0 ? __ldg(apart + o + z) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) v += x[k];
+  }
   grid[L.q_off + ((long long)gx * L.n[1] + gy) * nz + z] = v;
 }
 
@@ -736,7 +747,7 @@ static void run_anterp_cols(const Work& w, const Tables& t, const TileItem* cols
   if (ncol > 0)
     k_anterp_cols<P><<<(ncol + kAntWarps - 1) / kAntWarps, kAntWarps * 32, bytes, s>>>(
         t.sys, t.lev, cols, ncol, tz, wstride, w.cell_start, w.uq, w.apart);
-  if (nsum > 0) k_anterp_sum<P><<<nsum, kAntSumZ, 0, s>>>(t.sys, t.lev, sums, w.apart, w.grid);
+  if (nsum > 0) k_anterp_sum<P><<<nsum, kAntSumZ * kAntSumY, 0, s>>>(t.sys, t.lev, sums, w.apart, w.grid);
 }
 
 // floats of shared memory per warp of k_anterp_cols for footprints up to fx_max x fy_max

@@ -19,7 +19,8 @@ constexpr int kShortTilted = -1;  // short-range launch code of plans with tilte
 constexpr int kAnterpTX = 16, kAnterpTY = 8;  // dipole anterpolation tile columns (x, y); its z-extent is tuned
 constexpr int kAntWarps = 4;       // anterpolation: binning-column items (one per warp) per block
 constexpr int kAntFootMax = 16;    // largest footprint of a binning column per axis (grid columns)
-constexpr int kAntSumZ = 128;      // anterpolation sums: level-1 points along z per block
+constexpr int kAntSumZ = 128;      // anterpolation sums: level-1 points along z per grid column and block
+constexpr int kAntSumY = 1;        // anterpolation sums: grid columns (consecutive y) per block (4 measured slower)
 constexpr int kBallTY = 32;        // stencil tile rows (y)
 constexpr int kBallBZ = 16;        // outputs per thread along z
 constexpr int kBallTZ = 32;        // stencil tile depth (z)

@@ -1239,7 +1239,7 @@ void Engine::build_anterp_items(int tz) {
       for (int cy = 0; cy < D.C[1]; cy++)
         for (int z = 0; z < L.n[2]; z += tz) acol_items.push_back({li, cx, cy, z});
     for (int x = 0; x < L.n[0]; x++)
-      for (int y = 0; y < L.n[1]; y++)
+      for (int y = 0; y < L.n[1]; y += kAntSumY)
         for (int z = 0; z < L.n[2]; z += kAntSumZ) asum_items.push_back({li, x, y, z});
     fmax[0] = std::max(fmax[0], D.afoot[0]);
     fmax[1] = std::max(fmax[1], D.afoot[1]);

@@ -75,7 +75,7 @@ struct Engine {
   std::vector<AtomItem> atom_items;
   std::vector<TileItem> anterp_items, ball_items;
   // anterpolation by binning columns: one item per (binning column, z-segment), one sum
-  // item per (level-1 grid column, kAntSumZ points); used when every footprint fits
+  // item per (kAntSumY level-1 grid columns, kAntSumZ points); used when every footprint fits
   // (ant_wstride > 0)
   std::vector<TileItem> acol_items;
   std::vector<TileItem> asum_items;
