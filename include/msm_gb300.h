@@ -134,7 +134,8 @@ typedef struct {
   int nnbr[3];       /* neighbour-cell reach per axis */
   int stencil_kind[20]; /* 0 = ball stencil with wrap/zero, 1 = dense folded box */
   int anterp_tz;     /* anterpolation tile z-extent in use (16, 32, 64; msm_autotune) */
-  int short_block;   /* short-range threads per block in use (128, 256; msm_autotune) */
+  int short_block;   /* short-range kernel in use: 128 or 256 threads per block of the per-atom
+                        kernel, or MSM_SHORT_CLUSTER (cluster-pair tiles); msm_autotune */
   int anterp_kind;   /* anterpolation in use: 1 = by binning columns (column partials, then their
                         sum per grid point), 0 = gather by grid columns (footprints too wide for
                         the column kernel at this tile z-extent); -1 from msm_plan_describe */
@@ -285,16 +286,28 @@ int msm_potential_vjp(msm_plan plan, void* workspace, const float* g, float* dL_
  * to XLA): runs one forward on (n, pos, q) to fill workspace, then times each
  * tunable launch shape on those inputs and keeps the fastest for every later
  * call on this plan: the z-extent of the anterpolation tiles (16, 32, 64
- * level-1 points) and the short-range threads per block (256, or 128 = two
- * blocks per 256-atom item). Arguments as msm_forward. Synchronises stream
+ * level-1 points) and the short-range kernel (the per-atom kernel with 256
+ * threads per block, or 128 = two blocks per 256-atom item, or, where the plan
+ * allows it, MSM_SHORT_CLUSTER: cluster-pair tiles). Arguments as msm_forward. Synchronises stream
  * (not capturable into a graph); afterwards msm_backward needs a new
  * msm_forward. The choices are reported by msm_plan_get_info. */
 int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos, const float* q,
                  void* stream);
 
+/* Short-range kernel code for short_block: Eq. U_zero's pair sums as
+ * cluster-pair tiles (one warp per cluster of 4 sorted atoms: candidates culled
+ * against the cluster's bounding box into a shared-memory queue, then 4 x 8 pair
+ * tiles). Allowed when every system of the plan has a rectangular cell, a
+ * neighbour-cell reach nnbr of at most 4 along x and y and, when z is periodic,
+ * L_z >= a + 2 e_z (e_z the binning cell edge along z); where a later
+ * msm_plan_set_cell breaks this, the plan runs the per-atom kernel (256 threads)
+ * until the condition holds again. Same sums, reproducible bit for bit. */
+#define MSM_SHORT_CLUSTER 4
+
 /* Sets the tuned launch shapes directly (for callers that keep earlier
- * msm_autotune results): anterp_tz in {16, 32, 64}, short_block in {128, 256};
- * MSM_ERR_INVALID_ARG otherwise. Host-side; affects the next calls. */
+ * msm_autotune results): anterp_tz in {16, 32, 64}, short_block in {128, 256,
+ * MSM_SHORT_CLUSTER}; MSM_ERR_INVALID_ARG otherwise, or for MSM_SHORT_CLUSTER on
+ * a plan that does not allow it. Host-side; affects the next calls. */
 int msm_set_tuning(msm_plan plan, int anterp_tz, int short_block);
 
 /* Synchronises stream and returns the device status word (MSM_DEV_* bits)

@@ -49,14 +49,6 @@ __device__ __forceinline__ int floordiv_s(int a, int b) {
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
-// 1/sqrt(x) for a normal x > 0: the hardware approximation (relative error
-// below 2^-22), flush-to-zero form, so no rescaling of subnormal inputs
-__device__ __forceinline__ float rsqrt_nrm(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // k L - z, rounded once (FP64 only for the z-runs across a periodic face)
 __device__ __forceinline__ float image_shift(int k, double L, float z) {
   if (k == 0) return -z;
@@ -543,11 +535,13 @@ template <int P>
 static void run_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                       cudaStream_t s, int block) {
   if (block == kShortTilted) run_short_tri<P>(w, t, items, nitems, forces, virial, s);
+  else if (block == kShortCluster) launch_short_cluster(w, t, items, nitems, forces, virial, s, P);
   else if (block == kChunk / 2) run_short_nb<P, kChunk / 2>(w, t, items, nitems, forces, virial, s);
   else run_short_nb<P, kChunk>(w, t, items, nitems, forces, virial, s);
 }
 
-// block: threads per block of the rectangular-cell kernel (kChunk or kChunk / 2), or kShortTilted
+// block: threads per block of the rectangular-cell kernel (kChunk or kChunk / 2), kShortCluster
+// (cluster-pair tiles, k_short_cl.cu) or kShortTilted
 void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                   cudaStream_t s, int p, int block) {
   switch (p) {

@@ -289,7 +289,8 @@ static int run_autotune(Engine& E, void* ws, size_t ws_bytes, int n_single, cons
   int best_nb = E.short_block;
   best = 1e30f;
   if (!rc && !E.any_tri)
-    for (int nb : {kChunk, kChunk / 2}) {
+    for (int nb : {kChunk, kChunk / 2, kShortCluster}) {
+      if (nb == kShortCluster && !E.cluster_ok()) continue;
       const float ms = timed([&] { launch_short(w, t, E.d_atom_items, nai, true, true, s, E.p, nb); });
       if (ms < best) {
         best = ms;
@@ -660,9 +661,14 @@ int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, 
   return run_autotune(plan->eng, workspace, workspace_bytes, n, pos, q, (cudaStream_t)stream);
 }
 
+static_assert(MSM_SHORT_CLUSTER == kShortCluster, "public and internal cluster-kernel codes agree");
+
 static int set_tuning(Engine& E, int anterp_tz, int short_block) {
-  if (short_block != kChunk && short_block != kChunk / 2)
-    return set_err(MSM_ERR_INVALID_ARG, "short_block must be 128 or 256");
+  if (short_block != kChunk && short_block != kChunk / 2 && short_block != kShortCluster)
+    return set_err(MSM_ERR_INVALID_ARG, "short_block must be 128, 256 or MSM_SHORT_CLUSTER");
+  if (short_block == kShortCluster && !E.cluster_ok())
+    return set_err(MSM_ERR_INVALID_ARG,
+                   "MSM_SHORT_CLUSTER needs rectangular cells, nnbr <= 4 along x and y and L_z >= a + 2 e_z");
   std::string err;
   int rc = E.set_anterp_tz(anterp_tz, &err);
   if (rc) return set_err(rc, err);

@@ -16,6 +16,7 @@ constexpr int kMaxLev = 20;
 constexpr int kChunk = 256;        // atoms per per-atom work item
 constexpr int kChunkWarps = kChunk / 32;
 constexpr int kShortTilted = -1;  // short-range launch code of plans with tilted cells (k_short_tri)
+constexpr int kShortCluster = 4;  // short-range launch code of the cluster-pair kernel (k_short_cl: i-clusters of 4 atoms)
 constexpr int kAnterpTX = 16, kAnterpTY = 8;  // dipole anterpolation tile columns (x, y); its z-extent is tuned
 constexpr int kAntWarps = 4;       // anterpolation: binning-column items (one per warp) per block
 constexpr int kAntFootMax = 16;    // largest footprint of a binning column per axis (grid columns)
@@ -128,6 +129,16 @@ struct LevDev {
 // row length (floats) of one stored ball-stencil column with halo hz
 __host__ __device__ constexpr int kSK(int hz) { return 2 * hz + 4; }
 
+#ifdef __CUDACC__
+// 1/sqrt(x) for a normal x > 0: the hardware approximation (relative error
+// below 2^-22), flush-to-zero form, so no rescaling of subnormal inputs
+__device__ __forceinline__ float rsqrt_nrm(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+#endif
+
 struct AtomItem { int sys, start, count; };
 struct TileItem { int lev, x0, y0, z0; };
 struct RangeItem { int lev, start, count; };
@@ -182,6 +193,9 @@ void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitem
 // short range (k_short.cu)
 void launch_short(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, bool virial,
                   cudaStream_t s, int p, int block);
+// short range as cluster-pair tiles (k_short_cl.cu), rectangular cells
+void launch_short_cluster(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces,
+                          bool virial, cudaStream_t s, int p);
 // anterpolation / interpolation (k_interp.cu)
 void launch_anterp(const Work& w, const Tables& t, const TileItem* items, int nitems, cudaStream_t s, int p, int tz);
 // anterpolation by binning columns (k_interp.cu): per-column partial sums, then their sum per point

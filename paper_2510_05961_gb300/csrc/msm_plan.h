@@ -139,7 +139,18 @@ struct Engine {
   int anterp_tz = 32;
   int short_block = kChunk;
   bool any_tri = false;             // some system has a tilted cell: k_short_tri for all
-  int short_code() const { return any_tri ? kShortTilted : short_block; }
+  // the cluster-pair kernel's preconditions (k_short_cl.cu): rectangular cells,
+  // nnbr <= 4 along x and y, at most three z images per column
+  bool cluster_ok() const {
+    for (const SysHost& S : sys)
+      if (S.tri || S.nnbr[0] > 4 || S.nnbr[1] > 4 || (S.pbc[2] && S.L[2] < S.a + 2.0 * S.edge[2])) return false;
+    return true;
+  }
+  int short_code() const {
+    if (any_tri) return kShortTilted;
+    if (short_block == kShortCluster && !cluster_ok()) return kChunk;
+    return short_block;
+  }
   double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
   void build_anterp_items(int tz);
   void anterp(const Work& w, const Tables& t, cudaStream_t s) const;  // level-1 grid charges

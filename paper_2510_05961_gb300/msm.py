@@ -26,6 +26,9 @@ def _stream(device):
     return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
+# short_block code of the cluster-pair short-range kernel (MSM_SHORT_CLUSTER in msm_gb300.h)
+SHORT_CLUSTER = 4
+
 class Plan:
     """One system: cell, periodicity, level-one spacing h, cutoff a, order p, levels.
 
@@ -156,6 +159,7 @@ class Plan:
         return {"anterp_tz": info["anterp_tz"], "short_block": info["short_block"]}
 
     def set_tuning(self, anterp_tz=32, short_block=256):
+        """anterp_tz in (16, 32, 64); short_block 128 or 256 (per-atom kernel) or SHORT_CLUSTER."""
         L.check(self.lib.msm_set_tuning(self.handle, int(anterp_tz), int(short_block)))
 
     def status(self):
@@ -343,6 +347,7 @@ class Batch:
         return fld
 
     def set_tuning(self, anterp_tz=32, short_block=256):
+        """anterp_tz in (16, 32, 64); short_block 128 or 256 (per-atom kernel) or SHORT_CLUSTER."""
         L.check(self.lib.msm_batch_set_tuning(self.handle, int(anterp_tz), int(short_block)))
 
     def autotune(self, pos, q):

@@ -1,6 +1,7 @@
 """The autotuner and every launch shape it chooses among.
 
-Each (anterpolation tile z-extent, short-range block size) pair is forced on a
+Each (anterpolation tile z-extent, short-range kernel: 128 or 256 threads per
+block of the per-atom kernel, or the cluster-pair kernel) pair is forced on a
 single system and on a batch and checked against the oracle with the parity
 tolerances; msm_autotune must pick valid shapes and leave results unchanged.
 """
@@ -13,7 +14,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2510_05961_gb300 import Batch, Plan, build  # noqa: E402
+from paper_2510_05961_gb300 import SHORT_CLUSTER, Batch, Plan, build  # noqa: E402
 from paper_2510_05961_gb300 import workloads as W  # noqa: E402
 
 DEV = torch.device("cuda", 0)
@@ -39,7 +40,7 @@ def _ref(w):
 
 
 @pytest.mark.parametrize("tz", [16, 32, 64])
-@pytest.mark.parametrize("nb", [128, 256])
+@pytest.mark.parametrize("nb", [128, 256, SHORT_CLUSTER])
 def test_every_shape_matches_oracle(tz, nb):
     w = W.random_box(9000, seed=61)
     ref = _ref(w)
@@ -63,7 +64,7 @@ def test_autotune_single_and_batch():
     plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, max_atoms=w.n, device=DEV)
     pos, q = torch.from_numpy(w.pos).to(DEV), torch.from_numpy(w.q).to(DEV)
     choice = plan.autotune(pos, q)
-    assert choice["anterp_tz"] in (16, 32, 64) and choice["short_block"] in (128, 256)
+    assert choice["anterp_tz"] in (16, 32, 64) and choice["short_block"] in (128, 256, SHORT_CLUSTER)
     E, phi, F = plan.forward(pos, q, forces=True)
     torch.cuda.synchronize()
     assert abs(float(E.cpu()[0]) - ref["E"]) <= 1e-5 * abs(ref["E"])
@@ -74,6 +75,7 @@ def test_autotune_single_and_batch():
     bpos = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(DEV)
     bq = torch.from_numpy(np.concatenate([s.q for s in systems])).to(DEV)
     bchoice = batch.autotune(bpos, bq)
+    # small periodic cubes of the batch are outside the cluster kernel's preconditions
     assert bchoice["anterp_tz"] in (16, 32, 64) and bchoice["short_block"] in (128, 256)
     for tz, nb in ((bchoice["anterp_tz"], bchoice["short_block"]), (16, 128), (64, 256)):
         batch.set_tuning(tz, nb)

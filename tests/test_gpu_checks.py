@@ -6,7 +6,9 @@ from cell_start, bucket slots, the sort permutation, grid indices of the
 interpolation) before each access; a failed test sets MSM_DEV_CHECK in the
 status word and skips the access. This test builds that library and runs it,
 in a fresh process (the binding loads one library per process), on small
-cases of every boundary kind, a tilted cell, a dense cluster and a batch:
+cases of every boundary kind (with the per-atom and, where the plan allows
+it, the cluster-pair short-range kernel), a tilted cell, a dense cluster and
+a batch:
 no check may fire, and the outputs must match the FP64 oracle as in the
 other parity tests.
 """
@@ -30,7 +32,7 @@ import json, sys
 import numpy as np, torch
 sys.path.insert(0, ROOT)
 import oracle as O
-from paper_2510_05961_gb300 import Batch, Plan, _lib
+from paper_2510_05961_gb300 import SHORT_CLUSTER, Batch, Plan, _lib
 from paper_2510_05961_gb300 import workloads as W
 O.build()
 dev = torch.device("cuda", 0)
@@ -59,16 +61,22 @@ cases = [W.random_box(3000, seed=6301), W.random_box(1200, seed=6302, pbc=(1, 1,
          W.random_box(900, seed=6303, pbc=(0, 0, 1)), W.open_cluster(n=500, side=24.0, seed=6304), cluster(),
          W.random_box(40, density=0.08, seed=6305)]
 for w in cases:
-    plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, max_atoms=w.n, device=dev)
-    pos = torch.from_numpy(w.pos).to(dev); q = torch.from_numpy(w.q).to(dev)
-    E, phi, F = plan.forward(pos, q, forces=True, virial=True)
-    gp, gq, Wv = plan.backward(torch.ones(1, dtype=torch.float64, device=dev))
-    torch.cuda.synchronize()
-    st = plan.status()
     ref = O.msm(O.plan_for(w), w.pos.astype(np.float64), w.q.astype(np.float64))
-    out["cases"].append({"name": w.name, "status": st, "eE": abs(E.item() - ref["E"]) / abs(ref["E"]),
-                         "eF": rel_rms(F.cpu().numpy(), ref["F"]), "ephi": rel_rms(phi.cpu().numpy(), ref["phi"]),
-                         "eW": float(np.abs(Wv.cpu().numpy() - ref["W"]).max() / np.abs(ref["W"]).max())})
+    for sb in (256, SHORT_CLUSTER):
+        plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, max_atoms=w.n, device=dev)
+        try:
+            plan.set_tuning(32, sb)
+        except Exception:
+            continue  # outside the cluster kernel's preconditions
+        pos = torch.from_numpy(w.pos).to(dev); q = torch.from_numpy(w.q).to(dev)
+        E, phi, F = plan.forward(pos, q, forces=True, virial=True)
+        gp, gq, Wv = plan.backward(torch.ones(1, dtype=torch.float64, device=dev))
+        torch.cuda.synchronize()
+        st = plan.status()
+        out["cases"].append({"name": "%s/%d" % (w.name, sb), "status": st,
+                             "eE": abs(E.item() - ref["E"]) / abs(ref["E"]),
+                             "eF": rel_rms(F.cpu().numpy(), ref["F"]), "ephi": rel_rms(phi.cpu().numpy(), ref["phi"]),
+                             "eW": float(np.abs(Wv.cpu().numpy() - ref["W"]).max() / np.abs(ref["W"]).max())})
 A, pos_t, q_t = tilted()
 plan = Plan(A.reshape(9), (1, 1, 1), 0.0, 6.0, 4, 0, (16, 16, 16), max_atoms=len(q_t), device=dev)
 E, phi, F = plan.forward(torch.from_numpy(pos_t).to(dev), torch.from_numpy(q_t).to(dev), forces=True, virial=True)

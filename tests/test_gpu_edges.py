@@ -12,6 +12,7 @@
   box (about 44 atoms / A^3; up to 1383 atoms in one binning cell, against
   about 2 at the benchmark density), so the stable rank within a cell is long;
   binning bit-exact and full parity.
+Both cases run with the per-atom and the cluster-pair short-range kernels.
 """
 import numpy as np
 import pytest
@@ -22,7 +23,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2510_05961_gb300 import Plan, build  # noqa: E402
+from paper_2510_05961_gb300 import SHORT_CLUSTER, Plan, build  # noqa: E402
 from paper_2510_05961_gb300 import workloads as W  # noqa: E402
 from msm_testutil import expected_status  # noqa: E402
 
@@ -44,9 +45,10 @@ def rel_rms(a, b):
     return float(np.sqrt(((a - b) ** 2).sum(1).mean() / max((b ** 2).sum(1).mean(), 1e-300)))
 
 
-def run_and_compare(w):
+def run_and_compare(w, short_block=256):
     import oracle as O
     plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=w.n, device=DEV)
+    plan.set_tuning(32, short_block)
     pos = torch.from_numpy(w.pos).to(DEV)
     q = torch.from_numpy(w.q).to(DEV)
     E, phi, F = plan.forward(pos, q, forces=True, virial=True)
@@ -69,10 +71,11 @@ def run_and_compare(w):
     return P
 
 
+@pytest.mark.parametrize("short_block", [256, SHORT_CLUSTER], ids=["per_atom", "cluster"])
 @pytest.mark.parametrize("pbc", [(1, 1, 1), (1, 1, 0), (0, 0, 0)], ids=["periodic", "slab", "open"])
-def test_lattice_on_grid_points_and_cell_faces(pbc):
+def test_lattice_on_grid_points_and_cell_faces(pbc, short_block):
     w = W.lattice_on_grid(pbc=pbc)
-    P = run_and_compare(w)
+    P = run_and_compare(w, short_block)
     # the sites really are on grid points and cell faces
     u = w.pos.astype(np.float64) / np.array([P.h1[d] for d in range(3)])
     assert np.array_equal(u, np.round(u))
@@ -83,7 +86,8 @@ def test_lattice_on_grid_points_and_cell_faces(pbc):
             assert (w.pos[:, d] == np.float32(w.cell[d])).any() and (w.pos[:, d] == 0).any()
 
 
-def test_clustered_input():
+@pytest.mark.parametrize("short_block", [256, SHORT_CLUSTER], ids=["per_atom", "cluster"])
+def test_clustered_input(short_block):
     rng = np.random.default_rng(6100)
     n, R, side = 5000, 3.0, 60.0
     v = rng.normal(size=(n, 3))
@@ -92,4 +96,4 @@ def test_clustered_input():
     q = rng.normal(0.0, 0.5, size=n)
     q -= q.mean()
     w = W.Workload("cluster_ball", pos, q.astype(np.float32), (side,) * 3, (0, 0, 0), 2.0, 8.0, 4)
-    run_and_compare(w)
+    run_and_compare(w, short_block)

@@ -10,6 +10,7 @@ input: the 1,024,000-atom periodic box (p = 4, h = 2, a = 8), the
 few small systems whose energy nearly cancels); relative RMS error of
 forces, potentials, dE/dq and dE/dr <= 1e-4; virial to 1e-4 of its largest
 entry.
+The single systems run with every short-range kernel the autotuner can pick.
 The oracle takes about a minute for the 1M-atom box.
 """
 import numpy as np
@@ -21,7 +22,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2510_05961_gb300 import Batch, Plan, build  # noqa: E402
+from paper_2510_05961_gb300 import SHORT_CLUSTER, Batch, Plan, build  # noqa: E402
 from paper_2510_05961_gb300 import workloads as W  # noqa: E402
 from msm_testutil import expected_status  # noqa: E402
 
@@ -43,8 +44,9 @@ def rel_rms(a, b):
     return float(np.sqrt(((a - b) ** 2).sum(1).mean() / max((b ** 2).sum(1).mean(), 1e-300)))
 
 
-def fwd_bwd(w):
+def fwd_bwd(w, short_block=256):
     plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=w.n, device=DEV)
+    plan.set_tuning(32, short_block)
     pos = torch.from_numpy(w.pos).to(DEV)
     q = torch.from_numpy(w.q).to(DEV)
     E, phi, F = plan.forward(pos, q, forces=True, virial=True)
@@ -89,9 +91,12 @@ def oracle_msm(w):
     pytest.param(lambda: W.rocksalt(ncell=32), id="rocksalt_32"),
 ])
 def test_full_size_parity(make):
+    # every short-range kernel the benchmark's autotuner can pick: the per-atom
+    # kernel with 256 and 128 threads per block and the cluster-pair kernel
     w = make()
-    r = fwd_bwd(w)
-    check(r, oracle_msm(w), w.q)
+    ref = oracle_msm(w)
+    for nb in (256, 128, SHORT_CLUSTER):
+        check(fwd_bwd(w, nb), ref, w.q, "short_block %d" % nb)
 
 
 def test_batch_512_full_size():
