@@ -46,6 +46,9 @@ def parse():
                     help="skip the dynamic-cell and second-order timings (e.g. for a launch list of the step alone)")
     ap.add_argument("--tuning", type=int, nargs=2, metavar=("ANTERP_TZ", "SHORT_BLOCK"), default=None,
                     help="fixed launch shapes for the 1M-atom plan instead of msm_autotune")
+    ap.add_argument("--level-method", choices=["auto", "ball", "spectral"], default="auto",
+                    help="level stencils of the 1M-atom plan: ball kernels, the spectral method (FFTs), or "
+                         "auto (msm_autotune's choice; ball with --tuning)")
     ap.add_argument("--batch-systems", type=int, default=512)
     ap.add_argument("--sweep", action="store_true",
                     help="linear-scaling sweep instead of the headline step: forward only (E, phi, F) on periodic "
@@ -259,19 +262,36 @@ def kernel_table(info, n, a, p, ph, pk, st_flops_exec, serial_note):
         "FLOP: p^3 FMA + 3p weight FMA per atom")
     add("restrict", "k_restrict (all level steps)", "hbm", 4.0 * sum(pts[l] + pts[l + 1] for l in range(len(pts) - 1)),
         "bytes: read level l, write level l+1 (4 B per point)")
-    add("stencil", "k_pad, k_stencil_ball, k_stencil_box", "alu", f_ball,
-        "FLOP: 2 per kernel sample of the ball (%d) per point of the ball levels, plus the omega' prefilter" % nnz,
-        {"executed_flops": st_flops_exec, "executed_frac": st_flops_exec / (ph["stencil"] / 1e3) / 1e12 /
-         pk["fp32_tflops"] if ph.get("stencil") else None,
-         "executed_note": "the kernel sums mirrored rows first (the samples are even in x and y), so it executes "
-                          "fewer FLOPs than the ball count"})
+    spectral = info.get("level_method", 0) == 1
+    if spectral:
+        fft = sum(2 * 5.0 * m * math.log2(m) + 2.0 * m + 14.0 * m for m in pts)
+        add("stencil", "k_spec_z_fwd, k_spec_y (x2), k_spec_x, k_spec_z_inv", "alu", fft,
+            "FLOP: forward and inverse 3-D complex FFT of every level grid at 5 N log2 N each, the product with "
+            "the real spectrum (2 N) and the virial sums over |Q|^2 (14 N)",
+            {"l2_bytes": 16.0 * 5 * sum(pts) - 8.0 * sum(pts), "l2_note": "five passes over the complex work "
+             "buffers (read and write 8 B per point each; the first reads and the last writes 4 B real values), "
+             "L2-resident at this size; the passes are bound by L2 traffic and the barriers between FFT stages, "
+             "not by FP32 arithmetic"})
+    else:
+        add("stencil", "k_pad, k_stencil_ball, k_stencil_box", "alu", f_ball,
+            "FLOP: 2 per kernel sample of the ball (%d) per point of the ball levels, plus the omega' prefilter" % nnz,
+            {"executed_flops": st_flops_exec, "executed_frac": st_flops_exec / (ph["stencil"] / 1e3) / 1e12 /
+             pk["fp32_tflops"] if ph.get("stencil") else None,
+             "executed_note": "the kernel sums mirrored rows first (the samples are even in x and y), so it executes "
+                              "fewer FLOPs than the ball count"})
     add("prolong", "k_prolong (all level steps)", "hbm", 4.0 * sum(pts[l + 1] + 2 * pts[l] for l in range(len(pts) - 1)),
         "bytes: read level l+1, read and write level l (4 B per point)")
     add("interp", "k_interp", "alu", 2.0 * 4 * p ** 3 * n, "FLOP: 4 p^3 FMA per atom (potential and gradient)")
     add("final", "k_finalize, k_energy", "hbm", 76.0 * n,
         "bytes: read phi (2 x 4), fields (2 x 16), q (16), perm (4); write phi (4) and F (12) per atom")
-    add("virial", "k_virial_ball, k_virial_box, k_virial_slices, k_virial_out", "alu", f_vir,
-        "FLOP: 2 per unique lag (half of the %d samples) per point of the ball levels (autocorrelation)" % nnz)
+    if spectral:
+        nparts = 8 * ((n + 255) // 256) + sum(
+            m[1] * -(-m[2] // min(m[2], 2048 // m[0])) for m in info["n"][:info["ncomp"]])
+        add("virial", "k_virial_slices, k_virial_out (the grid sums ran in the forward's k_spec_x)", "hbm",
+            48.0 * nparts, "bytes: 6 FP64 partial sums per short-range warp and per spectral x item (%d)" % nparts)
+    else:
+        add("virial", "k_virial_ball, k_virial_box, k_virial_slices, k_virial_out", "alu", f_vir,
+            "FLOP: 2 per unique lag (half of the %d samples) per point of the ball levels (autocorrelation)" % nnz)
     add("bscale", "k_backward_scale", "hbm", 72.0 * n,
         "bytes: read phi (2 x 4), fields (2 x 16), q (16), perm (4); write dE/dr (12) and dE/dq (4) per atom")
     return {"rows": rows, "note": serial_note}
@@ -450,6 +470,8 @@ def run_gpu(args):
     q = torch.from_numpy(w.q).to(dev)
     if args.tuning:
         plan.set_tuning(*args.tuning)
+    if args.level_method != "auto":
+        plan.set_level_method(1 if args.level_method == "spectral" else 0)
     else:
         plan.autotune(pos, q)  # launch shapes for this workload, before the timed steps
     info = plan.info()
@@ -645,6 +667,7 @@ def run_gpu(args):
                        "l2": "flushed (256 MB write) before every step", "levels": info["nlev"],
                        "M": info["M"][0],
                        "tuning": {"anterp_tz": info["anterp_tz"], "short_block": info["short_block"],
+                                  "level_method": ["ball", "spectral"][info["level_method"]],
                                   "how": "fixed" if args.tuning else "msm_autotune"}},
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_val, "unit": "atoms/s", "h2d_bytes_per_step": n * 16,

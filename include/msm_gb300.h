@@ -139,6 +139,9 @@ typedef struct {
   int anterp_kind;   /* anterpolation in use: 1 = by binning columns (column partials, then their
                         sum per grid point), 0 = gather by grid columns (footprints too wide for
                         the column kernel at this tile z-extent); -1 from msm_plan_describe */
+  int level_method;  /* level stencils in use: MSM_LEVELS_BALL or MSM_LEVELS_SPECTRAL (0 from
+                        msm_plan_describe) */
+  int spectral_ok;   /* 1 if the plan allows MSM_LEVELS_SPECTRAL (0 from msm_plan_describe) */
 } msm_plan_info;
 
 /* Create a plan: validates the settings synchronously, builds the level
@@ -179,8 +182,13 @@ int msm_plan_describe(const msm_params* params, msm_plan_info* info);
  * (Eq. kernel_stencil_by_conv_with_universal_coeff), 1..6 for the strain
  * derivatives dK^l/d eps_ab, ab = xx, yy, zz, xy, xz, yz. Ball levels are
  * returned unfolded on [-R, R] (the kernel wraps indices), box levels folded
- * along periodic axes onto [0, n). out (host, capacity `cap` floats) may be
- * NULL to query lo and sz only. MSM_ERR_CAPACITY if cap is too small. */
+ * along periodic axes onto [0, n). which = 7 .. 13: the spectra the spectral
+ * level method (MSM_LEVELS_SPECTRAL) stores for the level, on the octant
+ * k_d = 0 .. n_d / 2 (lo = 0, sz = n_d / 2 + 1): 7 the discrete Fourier
+ * transform of the folded K^l times 1/N, 8 .. 13 those of dK^l/d eps_ab times
+ * -1/2 (1/N), N the level's point count (MSM_ERR_UNSUPPORTED for levels
+ * without it). out (host, capacity `cap` floats) may be NULL to query lo and
+ * sz only. MSM_ERR_CAPACITY if cap is too small. */
 int msm_plan_stencil(const msm_params* params, int level, int which, float* out, size_t cap, int lo[3], int sz[3]);
 
 /* Bytes of device workspace a plan needs (for max_atoms atoms). The caller
@@ -288,7 +296,9 @@ int msm_potential_vjp(msm_plan plan, void* workspace, const float* g, float* dL_
  * call on this plan: the z-extent of the anterpolation tiles (16, 32, 64
  * level-1 points) and the short-range kernel (the per-atom kernel with 256
  * threads per block, or 128 = two blocks per 256-atom item, or, where the plan
- * allows it, MSM_SHORT_CLUSTER: cluster-pair tiles). Arguments as msm_forward. Synchronises stream
+ * allows it, MSM_SHORT_CLUSTER: cluster-pair tiles) and, where the plan allows
+ * the spectral method, the level method (the forward's stencils with the
+ * backward's grid virial). Arguments as msm_forward. Synchronises stream
  * (not capturable into a graph); afterwards msm_backward needs a new
  * msm_forward. The choices are reported by msm_plan_get_info. */
 int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, const float* pos, const float* q,
@@ -309,6 +319,35 @@ int msm_autotune(msm_plan plan, void* workspace, size_t workspace_bytes, int n, 
  * MSM_SHORT_CLUSTER}; MSM_ERR_INVALID_ARG otherwise, or for MSM_SHORT_CLUSTER on
  * a plan that does not allow it. Host-side; affects the next calls. */
 int msm_set_tuning(msm_plan plan, int anterp_tz, int short_block);
+
+/* Level methods: how the level stencils K^l of Eq. action_of_K_as_convolution
+ * (and, in the backward, the grid virial -1/2 q~^T dK^l q~ of every level) are
+ * applied.
+ *  MSM_LEVELS_BALL: stencil sums over a halo-padded copy of each level grid
+ *    (ball kernels; every plan).
+ *  MSM_LEVELS_SPECTRAL: on a periodic grid the stencil sum is a circular
+ *    convolution with the stencil folded onto the grid, so it is applied as a
+ *    product with the stencil's discrete Fourier transform (the unfolded
+ *    stencil's transform sampled at k / n: the same operator, up to FP32
+ *    rounding), between forward and inverse three-dimensional FFTs of the level
+ *    grid; the virial is the sum over k of dK^(k) |Q(k)|^2 / N (Parseval),
+ *    formed during the forward. Plans that allow it: a single system with a
+ *    fully periodic rectangular cell whose evaluated levels have 2 .. 256 points
+ *    per axis (the planner's periodic grids are powers of two), as reported by
+ *    msm_plan_info.spectral_ok. The spectra are computed on the host (FP64) at
+ *    plan creation and by msm_plan_set_cell, which therefore takes its host path
+ *    on a plan running this method.
+ * New plans run MSM_LEVELS_BALL; msm_autotune picks the faster method. */
+#define MSM_LEVELS_BALL 0
+#define MSM_LEVELS_SPECTRAL 1
+
+/* Selects the level method of a single-system plan (host-side; affects the next
+ * calls; a following msm_backward needs a new msm_forward). MSM_ERR_INVALID_ARG
+ * for an unknown method, MSM_ERR_UNSUPPORTED for MSM_LEVELS_SPECTRAL on a plan
+ * that does not allow it. Switching to the spectral method after a device-path
+ * msm_plan_set_cell recomputes the spectra on the host and waits for their
+ * upload. */
+int msm_set_level_method(msm_plan plan, int method);
 
 /* Synchronises stream and returns the device status word (MSM_DEV_* bits)
  * of the last call on workspace in *device_status (host). */

@@ -35,6 +35,7 @@ EXPORTS = [
     "msm_profile_read", "msm_forward_noalloc", "msm_autotune", "msm_batch_autotune", "msm_batch_get_tuning",
     "msm_set_tuning", "msm_batch_set_tuning", "msm_field", "msm_batch_field", "msm_plan_set_cell", "msm_force_vjp",
     "msm_batch_force_vjp", "msm_potential_vjp", "msm_batch_potential_vjp", "msm_evaluate_host",
+    "msm_set_level_method",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 PHASES = ["bin", "short", "anterp", "restrict", "stencil", "prolong", "interp", "final", "virial", "bscale"]
@@ -56,7 +57,8 @@ class PlanInfo(C.Structure):
     _fields_ = [("nlev", C.c_int), ("ncomp", C.c_int), ("M", C.c_int * 3), ("h1", C.c_double * 3),
                 ("lo", (C.c_int * 3) * 20), ("n", (C.c_int * 3) * 20), ("R", C.c_int * 3), ("C", C.c_int * 3),
                 ("nnbr", C.c_int * 3), ("stencil_kind", C.c_int * 20), ("anterp_tz", C.c_int),
-                ("short_block", C.c_int), ("anterp_kind", C.c_int)]
+                ("short_block", C.c_int), ("anterp_kind", C.c_int), ("level_method", C.c_int),
+                ("spectral_ok", C.c_int)]
 
 
 _lib = None
@@ -104,6 +106,7 @@ def load(path: str = None):
     L.msm_batch_field.argtypes = [_vp, _vp, _vp, _vp]
     L.msm_forward_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]
     L.msm_profile.argtypes = [_vp, C.c_int]
+    L.msm_set_level_method.argtypes = [_vp, C.c_int]
     L.msm_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int if name != "msm_last_error" else C.c_char_p

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "lib", "libmsm_gb300.so")
 # sets MSM_DEV_CHECK in the status word and skips the access
 OBJ_CHECKS = os.path.join(HERE, "lib", "obj_checks")
 LIB_CHECKS = os.path.join(HERE, "lib", "libmsm_gb300_checks.so")
-SOURCES = ["msm_api.cu", "msm_plan.cu", "k_bin.cu", "k_short.cu", "k_short_cl.cu", "k_interp.cu", "k_grid.cu", "k_stencil.cu",
+SOURCES = ["msm_api.cu", "msm_plan.cu", "k_bin.cu", "k_short.cu", "k_short_cl.cu", "k_fft.cu", "k_interp.cu", "k_grid.cu", "k_stencil.cu",
            "k_final.cu", "k_cell.cu", "msm_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -62,7 +62,8 @@ static int count_forward(const Engine& E, bool) {
   int n = 1 + 5 + 1;                                   // prologue, binning, short range
   n += E.anterp_items.empty() ? 0 : (E.ant_wstride > 0 ? 2 : 1);  // anterpolation (columns: partials + sums)
   for (int l = 1; l < E.maxcomp; l++) n += 2;          // restriction + prolongation per level step
-  n += E.ball_items.empty() ? 0 : 2;                   // halo padding + ball stencil
+  if (E.level_method == 1) n += 5;                     // spectral: z, y, x (with the product), y, z passes
+  else n += E.ball_items.empty() ? 0 : 2;              // halo padding + ball stencil
   n += E.box_items.empty() ? 0 : 1;
   n += 1 + 1 + 1;                                      // interp, finalize, energy
   return n;
@@ -82,6 +83,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   Work w = E.resolve(ws);
   Tables t = E.tables();
   for (bool& u : E.ev_used) u = false;
+  E.spec_virial_ready = false;
   const int nai = (int)E.atom_items.size();
   {
     Phase ph(E, MSM_PH_BIN, s);
@@ -116,9 +118,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   }
   {
     Phase ph(E, MSM_PH_STENCIL, s);
-    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
-    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
-    launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
+    E.stencils(w, t, s, want_w);
   }
   {
     Phase ph(E, MSM_PH_PROLONG, s);
@@ -174,11 +174,10 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   }
   if (need_w) {
     Phase ph(E, MSM_PH_VIRIAL, s);
-    const int nb = (int)E.ball_items.size();
-    launch_virial_ball(w, t, E.d_ball_items, nb, E.rmax, E.ryz, 0, E.p == 4 && !E.any_tri, E.any_tri, s);
-    launch_virial_box(w, t, E.d_box_items, (int)E.box_items.size(), nb, s);
-    launch_virial_out(w, t, E.nsys, E.vslices, E.d_voff, grad, virial, s);
-    nl += (nb ? 1 : 0) + (E.box_items.empty() ? 0 : 1) + 2;
+    if (E.level_method == 1) nl += E.spec_virial_ready ? 0 : 3;
+    else nl += E.ball_items.empty() ? 0 : 1;
+    E.grid_virial(w, t, grad, virial, s);
+    nl += (E.box_items.empty() ? 0 : 1) + 2;
   }
   if (dE_dpos || dE_dq) {
     Phase ph(E, MSM_PH_BSCALE, s);
@@ -298,6 +297,26 @@ static int run_autotune(Engine& E, void* ws, size_t ws_bytes, int n_single, cons
       }
     }
   E.short_block = best_nb;
+  // level method (plans that allow the spectral one): the forward's stencils with the
+  // backward's grid virial, per method
+  if (!rc && E.spec_ok) {
+    if (!E.d_virial_scratch && cudaMalloc((void**)&E.d_virial_scratch, sizeof(double) * 9) != cudaSuccess)
+      rc = MSM_ERR_CUDA, err = "cudaMalloc failed";
+    int best_m = E.level_method;
+    best = 1e30f;
+    for (int m : {0, 1}) {
+      if (rc || (rc = E.set_level_method(m, &err))) break;
+      const float ms = timed([&] {
+        E.stencils(w, t, s, true);
+        E.grid_virial(w, t, nullptr, E.d_virial_scratch, s);
+      });
+      if (ms < best) {
+        best = ms;
+        best_m = m;
+      }
+    }
+    if (!rc) rc = E.set_level_method(best_m, &err);
+  }
   E.have_fwd = false;  // the timed launches reused the workspace: a new forward is needed
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -395,6 +414,16 @@ int msm_plan_get_info(msm_plan plan, msm_plan_info* info) {
   info->anterp_tz = plan->eng.anterp_tz;
   info->short_block = plan->eng.short_block;
   info->anterp_kind = plan->eng.ant_wstride > 0 ? 1 : 0;
+  info->level_method = plan->eng.level_method;
+  info->spectral_ok = plan->eng.spec_ok ? 1 : 0;
+  return MSM_OK;
+}
+
+int msm_set_level_method(msm_plan plan, int method) {
+  if (!plan) return set_err(MSM_ERR_INVALID_ARG, "plan must not be NULL");
+  std::string err;
+  int rc = plan->eng.set_level_method(method, &err);
+  if (rc) return set_err(rc, "msm_set_level_method: " + err);
   return MSM_OK;
 }
 
@@ -411,7 +440,7 @@ int msm_plan_describe(const msm_params* params, msm_plan_info* info) {
 
 int msm_plan_stencil(const msm_params* params, int level, int which, float* out, size_t cap, int lo[3], int sz[3]) {
   if (!params || !lo || !sz) return set_err(MSM_ERR_INVALID_ARG, "NULL argument");
-  if (which < 0 || which > 6) return set_err(MSM_ERR_INVALID_ARG, "which must be 0..6");
+  if (which < 0 || which > 13) return set_err(MSM_ERR_INVALID_ARG, "which must be 0..13");
   SysHost S;
   std::string err;
   int rc = plan_system(*params, S, &err);
@@ -421,7 +450,20 @@ int msm_plan_stencil(const msm_params* params, int level, int which, float* out,
   size_t count;
   const float* src;
   std::vector<float> tmp;
-  if (Lv.kind == 0) {
+  if (which >= 7) {
+    // the spectral level method's octant of this level's spectrum, as stored on the device
+    bool ok = S.pbc[0] && S.pbc[1] && S.pbc[2] && !S.tri && Lv.kind == 0 && !S.kball.empty();
+    for (int d = 0; d < 3 && ok; d++) ok = Lv.n[d] >= 2 && Lv.n[d] <= kSpecNmax && (Lv.n[d] & (Lv.n[d] - 1)) == 0;
+    if (!ok) return set_err(MSM_ERR_UNSUPPORTED, "no spectral level method for this level");
+    for (int d = 0; d < 3; d++) {
+      lo[d] = 0;
+      sz[d] = Lv.n[d] / 2 + 1;
+    }
+    count = (size_t)sz[0] * sz[1] * sz[2];
+    tmp.resize(7 * count);
+    level_spectra(S, level, Lv.n, tmp.data());
+    src = tmp.data() + (size_t)(which - 7) * count;
+  } else if (Lv.kind == 0) {
     for (int d = 0; d < 3; d++) {
       lo[d] = -S.R[d];
       sz[d] = 2 * S.R[d] + 1;
@@ -502,9 +544,7 @@ static int run_force_vjp(Engine& E, void* ws, const float* u, float* dq, float* 
       int a = E.restrict_off[l - 1], b = E.restrict_off[l];
       launch_restrict(w, t, E.d_res_items + a, b - a, s, E.p);
     }
-    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
-    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
-    launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
+    E.stencils(w, t, s, false);
     for (int l = E.maxcomp - 1; l >= 1; l--) {
       int a = E.prolong_off[l - 1], b = E.prolong_off[l];
       launch_prolong(w, t, E.d_pro_items + a, b - a, s, E.p);
@@ -546,9 +586,7 @@ static int run_potential_vjp(Engine& E, void* ws, const float* g, float* dq, flo
       int a = E.restrict_off[l - 1], b = E.restrict_off[l];
       launch_restrict(w, t, E.d_res_items + a, b - a, s, E.p);
     }
-    launch_pad(w, t, E.d_pad_items, (int)E.pad_items.size(), E.p == 4 ? 1 : 0, s);
-    launch_stencil_ball(w, t, E.d_ball_items, (int)E.ball_items.size(), E.rmax, E.ryz, E.any_tri, s);
-    launch_stencil_box(w, t, E.d_box_items, (int)E.box_items.size(), s);
+    E.stencils(w, t, s, false);
     for (int l = E.maxcomp - 1; l >= 1; l--) {
       int a = E.prolong_off[l - 1], b = E.prolong_off[l];
       launch_prolong(w, t, E.d_pro_items + a, b - a, s, E.p);
@@ -630,7 +668,8 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
   }
   E.hsys[0] = D;
   E.have_fwd = false;  // the workspace holds results for the old cell
-  bool device_path = S.pbc[0] && S.pbc[1] && S.pbc[2] && S.prefilter;
+  // the spectral level method's spectra are computed on the host: a plan running it takes the host path
+  bool device_path = S.pbc[0] && S.pbc[1] && S.pbc[2] && S.prefilter && E.level_method == 0;
   for (const LevelHost& Lv : S.lev) device_path = device_path && Lv.kind == 0;
   cudaStream_t st = (cudaStream_t)stream;
   if (device_path) {
@@ -638,12 +677,14 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
     const int hz = (S.B[2] + 3) & ~3;
     launch_cell_update(E.d_sys, D, S.h1, S.a, S.p, S.B, hz, S.kball_off, S.dkh_off, S.wb_off, S.wh_off, E.d_kpool,
                        E.d_wpool, st);
+    E.spec_stale = E.spec_ok;  // the spectra follow when the plan switches to the spectral method
   } else {
     // omega'-convolved stencils and folded boxes: rebuilt on the host with the
     // plan's sizes, copied through pinned staging buffers (stream-ordered)
     std::string err;
     int rc = E.set_cell_host(S.L, st, &err);
     if (rc) return set_err(rc, "msm_plan_set_cell: " + err);
+    E.spec_stale = false;
     launch_set_sys(E.d_sys, D, st);
   }
   return check_launch("msm_plan_set_cell");

@@ -36,6 +36,8 @@ constexpr int kVirialSlices = 64;  // most virial reduction slices per system
 constexpr int kProTX = 4, kProTY = 4, kProTZ = 32;  // prolongation tiles (fine points)
 constexpr int kFoldPts = 512;      // batch plans fold levels this small into dense boxes
 constexpr int kPadTX = 16, kPadTY = 8, kPadTZ = 32;  // halo-padding tiles (x planes, y rows, z columns)
+constexpr int kSpecTile = 2048;    // spectral level method: complex values per FFT tile (lines x points)
+constexpr int kSpecNmax = 256;     // spectral level method: most points per axis (twiddle table of 256)
 
 // device status bits (mirrors MSM_DEV_* of the public header)
 constexpr int kDevOutOfCell = 1;
@@ -124,6 +126,11 @@ struct LevDev {
   long long c_off;          // ball: column centres (int pool; all zero for rectangular cells)
   long long p_off;          // ball: float offset of the halo-padded, omega'-prefiltered copy of q~^l
                             // (ball levels apply raw kernel samples; R is the sample radius)
+  // spectral level method (fully periodic single-system plans, k_fft.cu): float2 offset of the
+  // level's complex work buffer, float offsets of its seven spectrum octants and of the twiddle
+  // table in the stencil pool (-1 where the level has none), log2 of n per axis
+  long long f_off, sp_off, tw_off;
+  int lg[3];
 };
 
 // row length (floats) of one stored ball-stencil column with halo hz
@@ -168,6 +175,7 @@ struct Work {
   double* part_vs; // per system and reduction slice: 6 virial components
   float* grid;     // grid pool
   float* apart;    // anterpolation: level-1 partial sums of each binning column (per system at SysDev::apart)
+  float2* spec;    // spectral level method: complex work buffers of the levels (LevDev::f_off)
   float4* vjp_u;   // force vector-Jacobian product: upstream (u, q), sorted
   float4* vjp_h;   // force vector-Jacobian product: short-range rows of H u and psi, sorted
   // staging of msm_evaluate_host (caller's atom order)
@@ -220,6 +228,12 @@ void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, i
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
                      float* forces, cudaStream_t s);
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);  // also flags non-neutral periodic systems
+// spectral level method (k_fft.cu): e^l of every spectral level (part: grid virial partials, one
+// per x item, or null), or the virial partials alone
+void launch_spectral(const Work& w, const Tables& t, const TileItem* zi, int nz, const TileItem* yi, int ny,
+                     const TileItem* xi, int nx, double* part, cudaStream_t s);
+void launch_spectral_virial(const Work& w, const Tables& t, const TileItem* zi, int nz, const TileItem* yi, int ny,
+                            const TileItem* xi, int nx, double* part, cudaStream_t s);
 void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, const int* vitem_off,
                        const double* grad, double* virial, cudaStream_t s);
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,

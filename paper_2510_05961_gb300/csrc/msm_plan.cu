@@ -848,6 +848,84 @@ int plan_system(const msm_params& P, SysHost& S, std::string* err) {
 // ------------------------------------------------------------------ engine
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Spectra of the level-l stencil for the spectral level method (k_fft.cu) on a
+// periodic grid of n points per axis: the octant k_d in [0, n_d / 2] of the
+// discrete Fourier transform of K^l = K^1 / 2^(l-1) (the unfolded stencil's
+// transform sampled at k / n equals the transform of the stencil folded onto
+// the grid) and of the six strain-derivative stencils dK^1 / 2^(l-1) (xx yy zz
+// xy xz yz). K and dK_aa are even in every axis (cosine sums); dK_ab is odd in
+// a and b and even in the third axis, so its transform is minus the sum with
+// sines along a and b. Separable sums in FP64 (z, then y, then x), stored as
+// float times 1/N (K^) and -1/2 (1/N) (dK^), N = n_x n_y n_z, in seven
+// consecutive octant arrays [k_x][k_y][k_z].
+void level_spectra(const SysHost& S, int l, const int n[3], float* out) {
+  const int R[3] = {S.R[0], S.R[1], S.R[2]};
+  const int sz[3] = {2 * R[0] + 1, 2 * R[1] + 1, 2 * R[2] + 1};
+  const int h[3] = {n[0] / 2 + 1, n[1] / 2 + 1, n[2] / 2 + 1};
+  const size_t box = (size_t)sz[0] * sz[1] * sz[2];
+  const size_t oct = (size_t)h[0] * h[1] * h[2];
+  // trig[d][par][k * sz + (m + R)]: cos (par 0) or sin (par 1) of 2 pi k m / n_d, the
+  // angle reduced exactly (k m mod n_d) before the FP64 evaluation
+  std::vector<double> trig[3][2];
+  for (int d = 0; d < 3; d++) {
+    trig[d][0].assign((size_t)h[d] * sz[d], 0.0);
+    trig[d][1].assign((size_t)h[d] * sz[d], 0.0);
+    for (int k = 0; k < h[d]; k++)
+      for (int m = -R[d]; m <= R[d]; m++) {
+        long long km = ((long long)k * m) % n[d];
+        if (km < 0) km += n[d];
+        const double ang = 2.0 * M_PI * (double)km / (double)n[d];
+        trig[d][0][(size_t)k * sz[d] + m + R[d]] = std::cos(ang);
+        trig[d][1][(size_t)k * sz[d] + m + R[d]] = std::sin(ang);
+      }
+  }
+  const double N = (double)n[0] * n[1] * n[2];
+  const double scale = std::ldexp(1.0, -(l - 1)) / N;
+  static const int par[7][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+  std::vector<double> Az((size_t)sz[0] * sz[1] * h[2]), Ay((size_t)sz[0] * h[1] * h[2]), Ax(oct);
+  for (int arr = 0; arr < 7; arr++) {
+    const double* A = arr == 0 ? S.kball.data() : S.dk1.data() + (size_t)(arr - 1) * box;
+    const std::vector<double>& tx = trig[0][par[arr][0]];
+    const std::vector<double>& ty = trig[1][par[arr][1]];
+    const std::vector<double>& tz = trig[2][par[arr][2]];
+    for (int x = 0; x < sz[0]; x++)
+      for (int y = 0; y < sz[1]; y++) {
+        const double* row = A + ((size_t)x * sz[1] + y) * sz[2];
+        double* o = Az.data() + ((size_t)x * sz[1] + y) * h[2];
+        for (int kz = 0; kz < h[2]; kz++) {
+          const double* t = tz.data() + (size_t)kz * sz[2];
+          double acc = 0.0;
+          for (int z = 0; z < sz[2]; z++) acc += row[z] * t[z];
+          o[kz] = acc;
+        }
+      }
+    std::fill(Ay.begin(), Ay.end(), 0.0);
+    for (int x = 0; x < sz[0]; x++)
+      for (int ky = 0; ky < h[1]; ky++) {
+        double* o = Ay.data() + ((size_t)x * h[1] + ky) * h[2];
+        for (int y = 0; y < sz[1]; y++) {
+          const double c = ty[(size_t)ky * sz[1] + y];
+          const double* src = Az.data() + ((size_t)x * sz[1] + y) * h[2];
+          for (int kz = 0; kz < h[2]; kz++) o[kz] += c * src[kz];
+        }
+      }
+    std::fill(Ax.begin(), Ax.end(), 0.0);
+    const size_t plane = (size_t)h[1] * h[2];
+    for (int kx = 0; kx < h[0]; kx++) {
+      double* o = Ax.data() + (size_t)kx * plane;
+      for (int x = 0; x < sz[0]; x++) {
+        const double c = tx[(size_t)kx * sz[0] + x];
+        const double* src = Ay.data() + (size_t)x * plane;
+        for (size_t e = 0; e < plane; e++) o[e] += c * src[e];
+      }
+    }
+    const double f = (arr == 0 ? 1.0 : -0.5) * (arr >= 4 ? -1.0 : 1.0) * scale;
+    for (size_t e = 0; e < oct; e++) out[(size_t)arr * oct + e] = (float)(f * Ax[e]);
+  }
+}
+
+
+
 // Device pools of the stencil values: per system the ball stencil (a row of
 // kSK(hz) floats per (dx, dy) column), its virial weights and column tables,
 // then each box level's folded K and dK; records the offsets in the level
@@ -932,6 +1010,25 @@ void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>&
       }
     }
     while (kp.size() % 4) kp.push_back(0.f);
+  }
+  if (spec_ok) {
+    // spectral level method: twiddles exp(-2 pi i j / 256), then each level's spectrum octants
+    const SysHost& S = sys[0];
+    const long long tw = (long long)kp.size();
+    for (int j = 0; j < kSpecNmax; j++) {
+      const double a = -2.0 * M_PI * j / kSpecNmax;
+      kp.push_back((float)std::cos(a));
+      kp.push_back((float)std::sin(a));
+    }
+    for (int l = 1; l <= S.ncomp; l++) {
+      LevDev& L = hlev[lev0_of[0] + l - 1];
+      while (kp.size() % 4) kp.push_back(0.f);
+      L.tw_off = tw;
+      L.sp_off = (long long)kp.size();
+      const size_t oct = (size_t)(L.n[0] / 2 + 1) * (L.n[1] / 2 + 1) * (L.n[2] / 2 + 1);
+      kp.resize(kp.size() + 7 * oct, 0.f);
+      level_spectra(S, l, L.n, kp.data() + L.sp_off);
+    }
   }
   if (kp.empty()) kp.push_back(0.f);
   if (wp.empty()) wp.push_back(0);
@@ -1074,6 +1171,32 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   total_atoms = atom_off;
   total_cells = cell_off;
   grid_floats = grid_off;
+  // spectral level method: eligibility, log2 sizes and complex work buffers of the levels
+  spec_ok = false;
+  spec_complex = 0;
+  for (LevDev& L : hlev) {
+    L.f_off = L.sp_off = L.tw_off = -1;
+    for (int d = 0; d < 3; d++) L.lg[d] = 0;
+  }
+  if (single && nsys == 1) {
+    const SysHost& S = sys[0];
+    bool ok = S.pbc[0] && S.pbc[1] && S.pbc[2] && !S.tri && S.ncomp >= 1 && !S.kball.empty();
+    for (int l = 1; ok && l <= S.ncomp; l++) {
+      const LevDev& L = hlev[hs[0].lev0 + l - 1];
+      ok = L.kind == 0;
+      for (int d = 0; d < 3 && ok; d++) ok = L.n[d] >= 2 && L.n[d] <= kSpecNmax && (L.n[d] & (L.n[d] - 1)) == 0;
+    }
+    spec_ok = ok;
+    if (ok)
+      for (int l = 1; l <= S.ncomp; l++) {
+        LevDev& L = hlev[hs[0].lev0 + l - 1];
+        L.f_off = spec_complex;
+        spec_complex += (long long)L.n[0] * L.n[1] * L.n[2];
+        for (int d = 0; d < 3; d++)
+          while ((1 << L.lg[d]) < L.n[d]) L.lg[d]++;
+      }
+  }
+  if (!spec_ok) level_method = 0;
   // stencil pools
   std::vector<float> kp;
   std::vector<int> wp;
@@ -1121,6 +1244,22 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   }
   vb_off[nsys] = (int)ball_items.size();
   vx_off[nsys] = (int)box_items.size();
+  spec_z_items.clear();
+  spec_y_items.clear();
+  spec_x_items.clear();
+  if (spec_ok)
+    for (int l = 1; l <= sys[0].ncomp; l++) {
+      const int li = hs[0].lev0 + l - 1;
+      const LevDev& L = hlev[li];
+      const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+      const int tz = std::min(n1, kSpecTile / n2), ty = std::min(n2, kSpecTile / n1), tx = std::min(n2, kSpecTile / n0);
+      for (int x = 0; x < n0; x++)
+        for (int y = 0; y < n1; y += tz) spec_z_items.push_back({li, x, y, std::min(tz, n1 - y)});
+      for (int x = 0; x < n0; x++)
+        for (int z = 0; z < n2; z += ty) spec_y_items.push_back({li, x, z, std::min(ty, n2 - z)});
+      for (int y = 0; y < n1; y++)
+        for (int z = 0; z < n2; z += tx) spec_x_items.push_back({li, y, z, std::min(tx, n2 - z)});
+    }
   restrict_steps.assign(std::max(0, maxcomp - 1), std::vector<TileItem>());
   prolong_steps.assign(std::max(0, maxcomp - 1), std::vector<TileItem>());
   for (int l = 1; l < maxcomp; l++) {
@@ -1143,6 +1282,12 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     voff[s] = vb_off[s];
     voff[nsys + 1 + s] = (int)ball_items.size() + vx_off[s];
   }
+  // the spectral method's virial partials: one per x item of system 0, then the box items
+  voff_spec.assign(2 * (nsys + 1), 0);
+  for (int s = 0; s <= nsys; s++) {
+    voff_spec[s] = s == 0 ? 0 : (int)spec_x_items.size();
+    voff_spec[nsys + 1 + s] = (int)spec_x_items.size() + vx_off[s];
+  }
   // column partials of the anterpolation: C_x C_y afoot_x afoot_y n_z floats per system
   apart_floats = 0;
   for (int s = 0; s < nsys; s++) {
@@ -1156,7 +1301,9 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
     // virial partials of the largest system: per-warp short-range items plus ball and box items
     long long most = 0;
     for (int s = 0; s < nsys; s++) {
-      long long tot = (long long)hs[s].nitem * kChunkWarps + (vb_off[s + 1] - vb_off[s]) + (vx_off[s + 1] - vx_off[s]);
+      long long tot = (long long)hs[s].nitem * kChunkWarps +
+                      std::max<long long>(vb_off[s + 1] - vb_off[s], s == 0 ? (long long)spec_x_items.size() : 0) +
+                      (vx_off[s + 1] - vx_off[s]);
       most = std::max(most, tot);
     }
     vslices = (int)std::min<long long>(kVirialSlices, std::max<long long>(1, (most + 1023) / 1024));
@@ -1191,7 +1338,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_part_e = take(sizeof(double) * atom_items.size());
   L_part_q = take(sizeof(double) * 2 * atom_items.size());
   L_part_w0 = take(sizeof(double) * 6 * kChunkWarps * atom_items.size());
-  L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(ball_items.size() + box_items.size(), 1));
+  L_part_wg = take(sizeof(double) * 6 * std::max<size_t>(std::max(ball_items.size(), spec_x_items.size()) + box_items.size(), 1));
   L_part_vs = take(sizeof(double) * 6 * 64 * (size_t)nsys);
   L_grid = take(sizeof(float) * std::max<long long>(grid_floats, 1));
   L_vjp_u = take(sizeof(float4) * N);
@@ -1203,6 +1350,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_io_e = take(sizeof(double) * 11 * (size_t)std::max(nsys, 1));
   // sized whenever the footprints fit the column kernel, whatever z-extent the tuning picks later
   L_apart = take(sizeof(float) * (size_t)(ant_fmax[0] <= kAntFootMax && ant_fmax[1] <= kAntFootMax ? apart_floats : 0));
+  L_spec = take(sizeof(float2) * (size_t)spec_complex);
   ws_bytes = off;
   return MSM_OK;
 }
@@ -1272,6 +1420,53 @@ void Engine::anterp(const Work& w, const Tables& t, cudaStream_t s) const {
     launch_anterp(w, t, d_anterp_items, (int)anterp_items.size(), s, p, anterp_tz);
 }
 
+void Engine::stencils(const Work& w, const Tables& t, cudaStream_t s, bool virial) {
+  if (level_method == 1) {
+    launch_spectral(w, t, d_spec_z, (int)spec_z_items.size(), d_spec_y, (int)spec_y_items.size(), d_spec_x,
+                    (int)spec_x_items.size(), virial ? w.part_wg : nullptr, s);
+    if (virial) spec_virial_ready = true;
+  } else {
+    launch_pad(w, t, d_pad_items, (int)pad_items.size(), p == 4 ? 1 : 0, s);
+    launch_stencil_ball(w, t, d_ball_items, (int)ball_items.size(), rmax, ryz, any_tri, s);
+  }
+  launch_stencil_box(w, t, d_box_items, (int)box_items.size(), s);
+}
+
+void Engine::grid_virial(const Work& w, const Tables& t, const double* grad, double* virial, cudaStream_t s) {
+  if (level_method == 1) {
+    if (!spec_virial_ready)
+      launch_spectral_virial(w, t, d_spec_z, (int)spec_z_items.size(), d_spec_y, (int)spec_y_items.size(), d_spec_x,
+                             (int)spec_x_items.size(), w.part_wg, s);
+    spec_virial_ready = true;
+    launch_virial_box(w, t, d_box_items, (int)box_items.size(), (int)spec_x_items.size(), s);
+    launch_virial_out(w, t, nsys, vslices, d_voff_spec, grad, virial, s);
+    return;
+  }
+  const int nb = (int)ball_items.size();
+  launch_virial_ball(w, t, d_ball_items, nb, rmax, ryz, 0, p == 4 && !any_tri, any_tri, s);
+  launch_virial_box(w, t, d_box_items, (int)box_items.size(), nb, s);
+  launch_virial_out(w, t, nsys, vslices, d_voff, grad, virial, s);
+}
+
+int Engine::set_level_method(int method, std::string* err) {
+  if (method != 0 && method != 1) return fail(err, MSM_ERR_INVALID_ARG, "level method must be 0 (ball) or 1 (spectral)");
+  if (method == 1 && !spec_ok)
+    return fail(err, MSM_ERR_UNSUPPORTED,
+                "the spectral level method needs a single-system plan with a fully periodic rectangular cell and ball "
+                "levels of 2 .. 256 points per axis");
+  if (method == 1 && spec_stale) {
+    // a device-path msm_plan_set_cell updated the ball samples only: the spectra follow on the host
+    int rc = set_cell_host(sys[0].L, 0, err, true);
+    if (rc) return rc;
+    if (cudaEventSynchronize(ev_stage) != cudaSuccess) return fail(err, MSM_ERR_CUDA, "cudaEventSynchronize failed");
+    spec_stale = false;
+  }
+  level_method = method;
+  spec_virial_ready = false;
+  have_fwd = false;
+  return MSM_OK;
+}
+
 int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, const std::vector<int>& voff,
                    std::string* err) {
   int rc;
@@ -1289,6 +1484,10 @@ int Engine::upload(const std::vector<float>& kp, const std::vector<int>& wp, con
   if ((rc = up(box_items, &d_box_items, err))) return rc;
   if ((rc = up(pad_items, &d_pad_items, err))) return rc;
   if ((rc = up(voff, &d_voff, err))) return rc;
+  if ((rc = up(voff_spec, &d_voff_spec, err))) return rc;
+  if ((rc = up(spec_z_items, &d_spec_z, err))) return rc;
+  if ((rc = up(spec_y_items, &d_spec_y, err))) return rc;
+  if ((rc = up(spec_x_items, &d_spec_x, err))) return rc;
   std::vector<TileItem> all;
   restrict_off.assign(restrict_steps.size() + 1, 0);
   for (size_t i = 0; i < restrict_steps.size(); i++) {
@@ -1434,9 +1633,14 @@ Engine::~Engine() {
   cudaFree(d_box_items);
   cudaFree(d_pad_items);
   cudaFree(d_voff);
+  cudaFree(d_voff_spec);
+  cudaFree(d_spec_z);
+  cudaFree(d_spec_y);
+  cudaFree(d_spec_x);
   cudaFree(d_res_items);
   cudaFree(d_pro_items);
   cudaFree(d_energy_scratch);
+  cudaFree(d_virial_scratch);
 }
 
 Work Engine::resolve(void* ws) const {
@@ -1472,6 +1676,7 @@ Work Engine::resolve(void* ws) const {
   w.vjp_u = (float4*)(b + L_vjp_u);
   w.vjp_h = (float4*)(b + L_vjp_h);
   w.apart = (float*)(b + L_apart);
+  w.spec = (float2*)(b + L_spec);
   return w;
 }
 

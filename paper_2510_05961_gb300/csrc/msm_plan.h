@@ -58,6 +58,10 @@ struct SysHost {
 
 int plan_system(const msm_params& P, SysHost& S, std::string* err);
 
+// spectral level method: the seven spectrum octants of level l on a periodic grid of n points
+// per axis (K^ times 1/N, then dK^ xx yy zz xy xz yz times -1/2 (1/N)), each (n_d/2+1) per axis
+void level_spectra(const SysHost& S, int l, const int n[3], float* out);
+
 // records the thread's last-error message of the C ABI and returns code
 int api_error(int code, const std::string& msg);
 
@@ -88,6 +92,20 @@ struct Engine {
   std::vector<std::vector<TileItem>> prolong_steps;
   std::vector<int> restrict_off, prolong_off;
   std::vector<int> vb_off, vx_off;
+  // spectral level method (k_fft.cu): single-system plans with a fully periodic rectangular cell
+  // whose evaluated levels are ball levels of 2 .. kSpecNmax points per axis (powers of two).
+  // The FFT items: z lines (lev, x, y0, rows), y lines (lev, x, z0, cols), x lines (lev, y, z0, cols).
+  bool spec_ok = false;
+  int level_method = 0;             // 0 = ball stencils, 1 = spectral (MSM_LEVELS_*)
+  bool spec_stale = false;          // a device-path msm_plan_set_cell left the spectra of the old cell
+  bool spec_virial_ready = false;   // the last forward left the spectral grid-virial partials in part_wg
+  long long spec_complex = 0;       // float2 entries of the levels' complex work buffers
+  std::vector<TileItem> spec_z_items, spec_y_items, spec_x_items;
+  TileItem* d_spec_z = nullptr;
+  TileItem* d_spec_y = nullptr;
+  TileItem* d_spec_x = nullptr;
+  std::vector<int> voff_spec;
+  int* d_voff_spec = nullptr;       // virial partial ranges of the spectral method (x items, then boxes)
   // device tables (owned)
   SysDev* d_sys = nullptr;
   LevDev* d_lev = nullptr;
@@ -106,7 +124,7 @@ struct Engine {
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_scell, L_xq,
       L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_q, L_part_w0, L_part_wg, L_part_vs, L_grid, L_vjp_u,
-      L_vjp_h, L_io_pos, L_io_q, L_io_dpos, L_io_dq, L_io_e, L_apart, L_crange;
+      L_vjp_h, L_io_pos, L_io_q, L_io_dpos, L_io_dq, L_io_e, L_apart, L_crange, L_spec;
   size_t ws_bytes = 0;
   // state of the last forward pass
   bool have_fwd = false;
@@ -152,8 +170,15 @@ struct Engine {
     return short_block;
   }
   double* d_energy_scratch = nullptr;  // the autotuner's forward writes its energies here
+  double* d_virial_scratch = nullptr;  // the autotuner's grid-virial timing writes its virial here
   void build_anterp_items(int tz);
   void anterp(const Work& w, const Tables& t, cudaStream_t s) const;  // level-1 grid charges
+  // e^l of every level by the plan's level method; virial: also the grid-virial partials
+  // (spectral method; the ball method computes them in the backward)
+  void stencils(const Work& w, const Tables& t, cudaStream_t s, bool virial);
+  // grid-virial partials and their reduction to W^(1+) + W^0 times grad (backward)
+  void grid_virial(const Work& w, const Tables& t, const double* grad, double* virial, cudaStream_t s);
+  int set_level_method(int method, std::string* err);
   int set_anterp_tz(int tz, std::string* err);
   void assemble_pools(const std::vector<int>& lev0_of, std::vector<float>& kp, std::vector<int>& wp);
   // new cell for a single-system plan (msm_plan_set_cell), host path: stencils

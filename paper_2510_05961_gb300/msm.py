@@ -28,6 +28,10 @@ def _stream(device):
 
 # short_block code of the cluster-pair short-range kernel (MSM_SHORT_CLUSTER in msm_gb300.h)
 SHORT_CLUSTER = 4
+# level methods (MSM_LEVELS_* in msm_gb300.h): ball stencils, or products with the stencil
+# spectra between FFTs of the level grids (fully periodic single-system plans)
+LEVELS_BALL = 0
+LEVELS_SPECTRAL = 1
 
 class Plan:
     """One system: cell, periodicity, level-one spacing h, cutoff a, order p, levels.
@@ -70,6 +74,7 @@ class Plan:
             "R": list(I.R), "C": list(I.C), "nnbr": list(I.nnbr),
             "stencil_kind": [I.stencil_kind[l] for l in range(I.ncomp)],
             "anterp_tz": I.anterp_tz, "short_block": I.short_block, "anterp_kind": I.anterp_kind,
+            "level_method": I.level_method, "spectral_ok": bool(I.spectral_ok),
         }
 
     def debug_array(self, which, level=1):
@@ -156,11 +161,16 @@ class Plan:
         L.check(self.lib.msm_autotune(self.handle, _ptr(self.workspace), self.workspace.numel(), n, _ptr(pos), _ptr(q),
                                       _stream(self.device)))
         info = self.info()
-        return {"anterp_tz": info["anterp_tz"], "short_block": info["short_block"]}
+        return {"anterp_tz": info["anterp_tz"], "short_block": info["short_block"], "level_method": info["level_method"]}
 
     def set_tuning(self, anterp_tz=32, short_block=256):
         """anterp_tz in (16, 32, 64); short_block 128 or 256 (per-atom kernel) or SHORT_CLUSTER."""
         L.check(self.lib.msm_set_tuning(self.handle, int(anterp_tz), int(short_block)))
+
+    def set_level_method(self, method):
+        """LEVELS_BALL or LEVELS_SPECTRAL (plans with info()["spectral_ok"]); a new forward is
+        needed before the next backward."""
+        L.check(self.lib.msm_set_level_method(self.handle, int(method)))
 
     def status(self):
         st = C.c_int()

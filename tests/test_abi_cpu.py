@@ -167,3 +167,51 @@ def test_batch_systems_plan(lib, oracle):
         assert rc == 0, lib.msm_last_error()
         s = oracle.plan_summary(oracle.plan_for(w))
         assert I.nlev == s["nlev"] and list(I.M) == s["M"] and list(I.C) == s["C"]
+
+
+SPECTRAL_CASES = [
+    dict(cell=(49.6,) * 3, pbc=(1, 1, 1), h=1.5, cutoff=9.0, order=6),
+    dict(cell=(60.0, 48.0, 54.0), pbc=(1, 1, 1), h=0.0, cutoff=8.0, order=4, grid_override=(32, 32, 32)),
+    dict(cell=(39.15,) * 3, pbc=(1, 1, 1), h=1.6, cutoff=7.0, order=8),
+    dict(cell=(6.3, 6.3, 6.3), pbc=(1, 1, 1), h=2.0, cutoff=8.0, order=4),
+]
+
+
+@pytest.mark.parametrize("case", SPECTRAL_CASES)
+def test_spectra_match_fft_of_oracle_stencils(lib, oracle, case):
+    """The spectral level method's stored spectra (msm_plan_stencil which 7..13: the
+    octant k_d <= n_d/2 of the DFT of the folded K^l and dK^l, times 1/N and -1/2 (1/N))
+    against numpy's FFT of the oracle's folded stencils on each level grid. The DFT of
+    the folded stencil is real (K, dK_aa even in every axis; dK_ab odd in a and b), and
+    its imaginary part vanishes to rounding."""
+    rc, I, Pl = _describe(lib, **case)
+    assert rc == 0
+    P = oracle.make_plan(case["cell"], case["pbc"], case["h"], case["cutoff"], case["order"], case.get("levels", 0),
+                         case.get("grid_override", (0, 0, 0)), case.get("qi_mode", 0))
+    for l in range(1, I.ncomp + 1):
+        n = P.level_shape(l)
+        N = float(np.prod(n))
+        h = tuple(d // 2 + 1 for d in n)
+        refs = []
+        for which in range(7):
+            F = np.fft.fftn(oracle.stencil(P, l, which)[0])
+            refs.append(F.real[:h[0], :h[1], :h[2]] * ((1.0 if which == 0 else -0.5) / N))
+            assert np.abs(F.imag).max() <= 1e-9 * np.abs(F).max(), (l, which)
+        # tolerance: float32 rounding of the stored values, relative to the largest
+        # entry of the level's K^ (which 7) or of its six dK^ (which 8 .. 13)
+        scale_k = np.abs(refs[0]).max()
+        scale_d = max(np.abs(r).max() for r in refs[1:])
+        for which in range(7):
+            got, lo = _lib_stencil(lib, Pl, l, 7 + which)
+            assert lo == (0, 0, 0) and got.shape == h
+            scale = scale_k if which == 0 else scale_d
+            err = np.abs(got - refs[which]).max()
+            assert err <= 2e-6 * scale, (l, which, err, scale)
+
+
+def test_spectra_refused_without_spectral_method(lib):
+    for case in (CASES[0], dict(cell=(20.0, 20.0, 20.0), pbc=(1, 1, 0), h=2.0, cutoff=8.0, order=4)):
+        rc, I, Pl = _describe(lib, **case)
+        lo = (C.c_int * 3)()
+        sz = (C.c_int * 3)()
+        assert lib.msm_plan_stencil(C.byref(Pl), 1, 7, None, 0, lo, sz) == _lib.MSM_ERR_UNSUPPORTED

@@ -10,7 +10,8 @@ input: the 1,024,000-atom periodic box (p = 4, h = 2, a = 8), the
 few small systems whose energy nearly cancels); relative RMS error of
 forces, potentials, dE/dq and dE/dr <= 1e-4; virial to 1e-4 of its largest
 entry.
-The single systems run with every short-range kernel the autotuner can pick.
+The single systems run with every short-range kernel and level method the
+autotuner can pick.
 The oracle takes about a minute for the 1M-atom box.
 """
 import numpy as np
@@ -22,7 +23,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2510_05961_gb300 import SHORT_CLUSTER, Batch, Plan, build  # noqa: E402
+from paper_2510_05961_gb300 import LEVELS_BALL, LEVELS_SPECTRAL, SHORT_CLUSTER, Batch, Plan, build  # noqa: E402
 from paper_2510_05961_gb300 import workloads as W  # noqa: E402
 from msm_testutil import expected_status  # noqa: E402
 
@@ -44,9 +45,10 @@ def rel_rms(a, b):
     return float(np.sqrt(((a - b) ** 2).sum(1).mean() / max((b ** 2).sum(1).mean(), 1e-300)))
 
 
-def fwd_bwd(w, short_block=256):
+def fwd_bwd(w, short_block=256, level_method=LEVELS_BALL):
     plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, w.grid_override, max_atoms=w.n, device=DEV)
     plan.set_tuning(32, short_block)
+    plan.set_level_method(level_method)
     pos = torch.from_numpy(w.pos).to(DEV)
     q = torch.from_numpy(w.q).to(DEV)
     E, phi, F = plan.forward(pos, q, forces=True, virial=True)
@@ -91,12 +93,13 @@ def oracle_msm(w):
     pytest.param(lambda: W.rocksalt(ncell=32), id="rocksalt_32"),
 ])
 def test_full_size_parity(make):
-    # every short-range kernel the benchmark's autotuner can pick: the per-atom
-    # kernel with 256 and 128 threads per block and the cluster-pair kernel
+    # every short-range kernel and level method the benchmark's autotuner can
+    # pick: the per-atom kernel with 256 and 128 threads per block, the
+    # cluster-pair kernel, ball stencils and the spectral level method
     w = make()
     ref = oracle_msm(w)
-    for nb in (256, 128, SHORT_CLUSTER):
-        check(fwd_bwd(w, nb), ref, w.q, "short_block %d" % nb)
+    for nb, lm in ((256, LEVELS_BALL), (128, LEVELS_BALL), (SHORT_CLUSTER, LEVELS_BALL), (128, LEVELS_SPECTRAL)):
+        check(fwd_bwd(w, nb, lm), ref, w.q, "short_block %d, level method %d" % (nb, lm))
 
 
 def test_batch_512_full_size():
@@ -138,9 +141,10 @@ def test_rocksalt32_gradients_against_oracle_differences():
     rows = np.array(rows)
     idx, dEdr, dEdq = rows[:, 0].astype(int), rows[:, 1:4], rows[:, 4]
     w = W.rocksalt(ncell=32)
-    r = fwd_bwd(w)
-    assert rel_rms(r["dpos"][idx], dEdr) <= F_TOL, rel_rms(r["dpos"][idx], dEdr)
-    assert rel_rms(r["dq"][idx], dEdq) <= F_TOL, rel_rms(r["dq"][idx], dEdq)
-    Wg = r["W"]
-    W6 = np.array([Wg[0, 0], Wg[1, 1], Wg[2, 2], Wg[0, 1], Wg[0, 2], Wg[1, 2]])
-    assert np.abs(W6 - vir).max() <= F_TOL * np.abs(vir).max(), (W6, vir)
+    for lm in (LEVELS_BALL, LEVELS_SPECTRAL):
+        r = fwd_bwd(w, 256, lm)
+        assert rel_rms(r["dpos"][idx], dEdr) <= F_TOL, (lm, rel_rms(r["dpos"][idx], dEdr))
+        assert rel_rms(r["dq"][idx], dEdq) <= F_TOL, (lm, rel_rms(r["dq"][idx], dEdq))
+        Wg = r["W"]
+        W6 = np.array([Wg[0, 0], Wg[1, 1], Wg[2, 2], Wg[0, 1], Wg[0, 2], Wg[1, 2]])
+        assert np.abs(W6 - vir).max() <= F_TOL * np.abs(vir).max(), (lm, W6, vir)
