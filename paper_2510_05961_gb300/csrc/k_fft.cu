@@ -26,17 +26,23 @@
 //   y: inverse transform along y                    (k_spec_y, inverse)
 //   z: inverse transform along z, real part -> e^l  (k_spec_z_inv)
 // A block loads a tile of lines into shared memory and runs radix-2 stages
-// with a barrier between them: decimation in time on bit-reversed input for
-// forward transforms, decimation in frequency with bit-reversed output for
-// inverse ones, so no separate permutation pass is needed. Twiddles
-// exp(-2 pi i j / 256) come from a table in the stencil pool (FP64 values
-// rounded once); a level axis of n points uses every (256 / n)-th entry.
+// with a barrier between them. Forward transforms run by decimation in
+// frequency (natural input, output in bit-reversed order) and inverse ones by
+// decimation in time (bit-reversed input, natural output), so every pass reads
+// and writes its lines in place and in order: between the forward and the
+// inverse passes the work buffer holds the spectrum with each axis in
+// bit-reversed order, which the x pass undoes only to look up the spectra.
+// Twiddles exp(-2 pi i j / 256) come from a table in the stencil pool (FP64
+// values rounded once); a level axis of n points uses every (256 / n)-th entry.
+// The spectra octants are stored interleaved, eight floats per octant point
+// (K^, dK^ xx yy zz xy xz yz, zero), read with two 16-byte loads.
 #include "msm_internal.h"
 
 namespace msm {
 
 namespace {
 constexpr int kSpecThreads = 256;
+constexpr int kPer = kSpecTile / kSpecThreads;  // tile elements per thread, at most
 
 __device__ __forceinline__ int bitrev(int j, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - lg)); }
 
@@ -44,32 +50,37 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// radix-2 stages over T lines of n = 2^lg points held in shared memory, element
-// j of line t at buf[t * ts + j * js]. DIT (forward, input bit-reversed) or DIF
-// (inverse, output bit-reversed); conj selects exp(+2 pi i ...) twiddles.
-template <bool DIT>
-__device__ void fft_stages(float2* buf, int T, int lg, int ts, int js, const float2* tw, bool conj, bool tfast) {
-  const int n = 1 << lg, nb = T * (n >> 1);
+// radix-2 stages over T = 2^lgT lines of n = 2^lg points in shared memory: element
+// j of line t at buf[(j << lgT) + t] (TF: lines interleaved, t fastest) or at
+// buf[(t << lg) + j]. DIF (forward: natural input, bit-reversed output, twiddles
+// exp(-2 pi i ...)) or DIT (inverse: bit-reversed input, natural output, twiddles
+// exp(+2 pi i ...)). Index arithmetic in shifts and masks (powers of two).
+template <bool DIT, bool TF>
+__device__ __forceinline__ void fft_tile(float2* buf, int lg, int lgT, const float2* tw) {
+  const int half = (1 << lg) >> 1;
+  const int nb = half << lgT;
   for (int st = 0; st < lg; st++) {
-    const int hl = DIT ? (1 << st) : (n >> (st + 1));  // half span of this stage
-    const int sh = 8 - (DIT ? st + 1 : lg - st);        // twiddle step 256 / (2 hl) = 2^sh
+    const int s2 = DIT ? st : lg - 1 - st;  // log2 of the half span
+    const int hl = 1 << s2;
+    const int sh = 7 - s2;  // twiddle step 256 / (2 hl)
     for (int b = threadIdx.x; b < nb; b += kSpecThreads) {
       int t, i;
-      if (tfast) {
-        t = b % T;
-        i = b / T;
+      if (TF) {
+        t = b & ((1 << lgT) - 1);
+        i = b >> lgT;
       } else {
-        i = b & ((n >> 1) - 1);
+        i = b & (half - 1);
         t = b >> (lg - 1);
       }
-      const int g = i / hl, jj = i - g * hl;
-      const int j0 = g * 2 * hl + jj, j1 = j0 + hl;
+      const int jj = i & (hl - 1);
+      const int j0 = ((i >> s2) << (s2 + 1)) + jj;
+      const int j1 = j0 + hl;
       float2 w = tw[jj << sh];
-      if (conj) w.y = -w.y;
-      float2* p0 = buf + t * ts + j0 * js;
-      float2* p1 = buf + t * ts + j1 * js;
+      float2* p0 = TF ? buf + (j0 << lgT) + t : buf + (t << lg) + j0;
+      float2* p1 = TF ? buf + (j1 << lgT) + t : buf + (t << lg) + j1;
       const float2 a = *p0, c = *p1;
       if (DIT) {
+        w.y = -w.y;
         const float2 v = cmul(c, w);
         *p0 = make_float2(a.x + v.x, a.y + v.y);
         *p1 = make_float2(a.x - v.x, a.y - v.y);
@@ -88,6 +99,34 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const float* kpool, lo
 
 __device__ __forceinline__ int fold_k(int k, int n) { return min(k, n - k); }
 __device__ __forceinline__ float sgn_k(int k, int n) { return (k == 0 || 2 * k == n) ? 0.f : (2 * k < n ? 1.f : -1.f); }
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// T lines' points j at g[j * stride + t] (t < T: consecutive z) into buf[(j << lgT) + t]
+__device__ __forceinline__ void load_lines(float2* buf, const float2* __restrict__ g, long long stride, int lg, int lgT) {
+  const int cnt = 1 << (lg + lgT);
+  float2 r[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    r[k] = e < cnt ? g[(long long)(e >> lgT) * stride + (e & ((1 << lgT) - 1))] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e < cnt) buf[e] = r[k];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void store_lines(const float2* buf, float2* __restrict__ g, long long stride, int lg, int lgT) {
+  const int cnt = 1 << (lg + lgT);
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e < cnt) g[(long long)(e >> lgT) * stride + (e & ((1 << lgT) - 1))] = buf[e];
+  }
+}
 }  // namespace
 
 // z pass, forward: item (lev, x, y0, rows): rows z-lines (y0 .. y0 + rows - 1) at x
@@ -99,17 +138,28 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_fwd(const LevDev* __res
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
-  const int nz = L.n[2], lg = L.lg[2], T = it.z0;
-  const long long base = ((long long)it.x0 * L.n[1] + it.y0) * nz;
+  const long long base = ((long long)it.x0 * L.n[1] + it.y0) * L.n[2];
   const float* q = grid + L.q_off + base;
-  for (int e = threadIdx.x; e < T * nz; e += kSpecThreads) {
-    const int t = e >> lg, j = e & (nz - 1);
-    buf[t * nz + bitrev(j, lg)] = make_float2(q[e], 0.f);
+  const int lg = L.lg[2], cnt = it.z0 << lg;
+  float r[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    r[k] = e < cnt ? q[e] : 0.f;  // every load issued before the first shared-memory store
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e < cnt) buf[e] = make_float2(r[k], 0.f);
   }
   __syncthreads();
-  fft_stages<true>(buf, T, lg, nz, 1, tw, false, false);
+  fft_tile<false, false>(buf, lg, ilog2(it.z0), tw);
   float2* out = spec + L.f_off + base;
-  for (int e = threadIdx.x; e < T * nz; e += kSpecThreads) out[e] = buf[e];
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e < cnt) out[e] = buf[e];
+  }
 }
 
 // z pass, inverse: e^l = Re(inverse transform along z)
@@ -121,16 +171,27 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_inv(const LevDev* __res
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
-  const int nz = L.n[2], lg = L.lg[2], T = it.z0;
-  const long long base = ((long long)it.x0 * L.n[1] + it.y0) * nz;
+  const long long base = ((long long)it.x0 * L.n[1] + it.y0) * L.n[2];
   const float2* in = spec + L.f_off + base;
-  for (int e = threadIdx.x; e < T * nz; e += kSpecThreads) buf[e] = in[e];
+  const int lg = L.lg[2], cnt = it.z0 << lg;
+  float2 r[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    r[k] = e < cnt ? in[e] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e < cnt) buf[e] = r[k];
+  }
   __syncthreads();
-  fft_stages<false>(buf, T, lg, nz, 1, tw, true, false);
+  fft_tile<true, false>(buf, lg, ilog2(it.z0), tw);
   float* e_out = grid + L.e_off + base;
-  for (int e = threadIdx.x; e < T * nz; e += kSpecThreads) {
-    const int t = e >> lg, j = e & (nz - 1);
-    e_out[e] = buf[t * nz + bitrev(j, lg)].x;
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e < cnt) e_out[e] = buf[e].x;
   }
 }
 
@@ -143,26 +204,17 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_y(const LevDev* __restric
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
-  const int ny = L.n[1], nz = L.n[2], lg = L.lg[1], T = it.z0;
-  float2* g = spec + L.f_off + (long long)it.x0 * ny * nz + it.y0;
-  // shared layout [j][t]: t (z) fastest, matching the global order
-  for (int e = threadIdx.x; e < T * ny; e += kSpecThreads) {
-    const int t = e % T, j = e / T;
-    buf[(INV ? j : bitrev(j, lg)) * T + t] = g[(long long)j * nz + t];
-  }
-  __syncthreads();
-  if (INV) fft_stages<false>(buf, T, lg, 1, T, tw, true, true);
-  else fft_stages<true>(buf, T, lg, 1, T, tw, false, true);
-  for (int e = threadIdx.x; e < T * ny; e += kSpecThreads) {
-    const int t = e % T, j = e / T;
-    g[(long long)j * nz + t] = buf[(INV ? bitrev(j, lg) : j) * T + t];
-  }
+  float2* g = spec + L.f_off + (long long)it.x0 * L.n[1] * L.n[2] + it.y0;
+  const int lg = L.lg[1], lgT = ilog2(it.z0);
+  load_lines(buf, g, L.n[2], lg, lgT);
+  fft_tile<INV, true>(buf, lg, lgT, tw);
+  store_lines(buf, g, L.n[2], lg, lgT);
 }
 
 // x pass: item (lev, y, z0, cols): forward transform along x (the spectrum
-// Q(k_x, k_y = y, k_z = z) is then complete), the virial sums, the product
-// with K^ and the inverse transform along x; in place. part (when not null)
-// receives the block's six virial sums at 6 * blockIdx.x.
+// is then complete, every axis in bit-reversed order), the virial sums, the
+// product with K^ and the inverse transform along x; in place. part (when not
+// null) receives the block's six virial sums at 6 * blockIdx.x.
 template <bool MUL>
 __global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                          const float* __restrict__ kpool, float2* __restrict__ spec,
@@ -173,41 +225,40 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restric
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
-  const int nx = L.n[0], ny = L.n[1], nz = L.n[2], lg = L.lg[0], T = it.z0;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const int lg = L.lg[0], lgT = ilog2(it.z0);
   float2* g = spec + L.f_off + (long long)it.x0 * nz + it.y0;  // x0 holds y, y0 holds z0
   const long long xs = (long long)ny * nz;
-  for (int e = threadIdx.x; e < T * nx; e += kSpecThreads) {
-    const int t = e % T, j = e / T;
-    buf[bitrev(j, lg) * T + t] = g[(long long)j * xs + t];
-  }
-  __syncthreads();
-  fft_stages<true>(buf, T, lg, 1, T, tw, false, true);
-  // spectra octants: 7 arrays of (nx/2+1)(ny/2+1)(nz/2+1) floats: K^, then dK^ xx yy zz xy xz yz
+  load_lines(buf, g, xs, lg, lgT);
+  fft_tile<false, true>(buf, lg, lgT, tw);
+  // spectra octants, 8 floats per point: K^, dK^ xx yy zz xy xz yz, 0
   const int hy = ny / 2 + 1, hz = nz / 2 + 1;
-  const long long oct = (long long)(nx / 2 + 1) * hy * hz;
-  const float* sp = kpool + L.sp_off;
-  const int ky = it.x0;
+  const float4* sp = reinterpret_cast<const float4*>(kpool + L.sp_off);
+  const int ky = bitrev(it.x0, L.lg[1]);
   const int fy = fold_k(ky, ny);
   const float sy = sgn_k(ky, ny);
+  const int cnt = 1 << (lg + lgT);
   float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int e = threadIdx.x; e < T * nx; e += kSpecThreads) {
-    const int t = e % T, kx = e / T, kz = it.y0 + t;
+#pragma unroll
+  for (int k = 0; k < kPer; k++) {
+    const int e = threadIdx.x + k * kSpecThreads;
+    if (e >= cnt) continue;
+    const int kx = bitrev(e >> lgT, lg), kz = bitrev(it.y0 + (e & ((1 << lgT) - 1)), L.lg[2]);
     const long long o = ((long long)fold_k(kx, nx) * hy + fy) * hz + fold_k(kz, nz);
+    const float4 s0 = sp[2 * o];
     const float2 z = buf[e];
     if (part) {
+      const float4 s1 = sp[2 * o + 1];
       const float p2 = fmaf(z.x, z.x, z.y * z.y);
       const float sx = sgn_k(kx, nx), sz = sgn_k(kz, nz);
-      w[0] = fmaf(sp[oct + o], p2, w[0]);
-      w[1] = fmaf(sp[2 * oct + o], p2, w[1]);
-      w[2] = fmaf(sp[3 * oct + o], p2, w[2]);
-      w[3] = fmaf(sx * sy * sp[4 * oct + o], p2, w[3]);
-      w[4] = fmaf(sx * sz * sp[5 * oct + o], p2, w[4]);
-      w[5] = fmaf(sy * sz * sp[6 * oct + o], p2, w[5]);
+      w[0] = fmaf(s0.y, p2, w[0]);
+      w[1] = fmaf(s0.z, p2, w[1]);
+      w[2] = fmaf(s0.w, p2, w[2]);
+      w[3] = fmaf(sx * sy * s1.x, p2, w[3]);
+      w[4] = fmaf(sx * sz * s1.y, p2, w[4]);
+      w[5] = fmaf(sy * sz * s1.z, p2, w[5]);
     }
-    if (MUL) {
-      const float kk = sp[o];
-      buf[e] = make_float2(kk * z.x, kk * z.y);
-    }
+    if (MUL) buf[e] = make_float2(s0.x * z.x, s0.x * z.y);
   }
   if (part) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -225,11 +276,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restric
     part[6 * (long long)blockIdx.x + threadIdx.x] = v;
   }
   if (!MUL) return;
-  fft_stages<false>(buf, T, lg, 1, T, tw, true, true);
-  for (int e = threadIdx.x; e < T * nx; e += kSpecThreads) {
-    const int t = e % T, j = e / T;
-    g[(long long)j * xs + t] = buf[bitrev(j, lg) * T + t];
-  }
+  fft_tile<true, true>(buf, lg, lgT, tw);
+  store_lines(buf, g, xs, lg, lgT);
 }
 
 // forward: e^l of every spectral level from q~^l (and, with part, the grid virial partials)

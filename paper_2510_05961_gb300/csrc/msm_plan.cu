@@ -1026,8 +1026,12 @@ void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>&
       L.tw_off = tw;
       L.sp_off = (long long)kp.size();
       const size_t oct = (size_t)(L.n[0] / 2 + 1) * (L.n[1] / 2 + 1) * (L.n[2] / 2 + 1);
-      kp.resize(kp.size() + 7 * oct, 0.f);
-      level_spectra(S, l, L.n, kp.data() + L.sp_off);
+      std::vector<float> seven(7 * oct);
+      level_spectra(S, l, L.n, seven.data());
+      // interleaved, eight floats per octant point (two 16-byte loads in k_spec_x)
+      kp.resize(kp.size() + 8 * oct, 0.f);
+      for (size_t o = 0; o < oct; o++)
+        for (int c = 0; c < 7; c++) kp[L.sp_off + 8 * o + c] = seven[c * oct + o];
     }
   }
   if (kp.empty()) kp.push_back(0.f);
