@@ -532,22 +532,32 @@ def run_gpu(args):
         ms = float(t.item())
     value = world * n / (ms / 1e3)
 
-    # dynamic cell: msm_plan_set_cell recomputes the stencils on the device (stream-ordered);
-    # alternate a 1% larger cell and the benchmark cell, CUDA events around 20 calls
+    # dynamic cell: msm_plan_set_cell, alternating a 1% larger cell and the benchmark cell, CUDA
+    # events around 20 calls, under each level method (the ball method's stencils are recomputed on
+    # the device; the spectral method's spectra on the host, then uploaded)
     dyn = None
     if tuple(w.pbc) == (1, 1, 1) and w.p == 4 and not args.no_extras:
         import numpy as np
         base = np.array(w.cell, np.float64)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        plan.set_cell(base)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for i in range(20):
-            plan.set_cell(base * (1.01 if i % 2 == 0 else 1.0))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        dyn = {"set_cell_us": e0.elapsed_time(e1) / 20 * 1e3, "what": "msm_plan_set_cell: new cell lengths, "
-               "stencil samples, virial weights and column tables recomputed on the device"}
+        method0 = info["level_method"]
+        dyn = {}
+        for m, name in ((0, "ball"), (1, "spectral")):
+            if m == 1 and not info["spectral_ok"]:
+                continue
+            plan.set_level_method(m)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            plan.set_cell(base)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(20):
+                plan.set_cell(base * (1.01 if i % 2 == 0 else 1.0))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dyn["set_cell_us_" + name] = e0.elapsed_time(e1) / 20 * 1e3
+        plan.set_level_method(method0)
+        dyn["what"] = ("msm_plan_set_cell: new cell lengths; ball method: stencil samples, virial weights and column "
+                       "tables recomputed on the device; spectral method: the level spectra recomputed on the host "
+                       "(FP64) and uploaded")
 
     # second-order backward paths (gradients through the outputs), CUDA events, 3 repetitions each:
     # force VJP (L = sum u . F: dipole grid chain, B-spline and pair Hessians) and the potential

@@ -25,13 +25,18 @@
 //      transform along x                            (k_spec_x)
 //   y: inverse transform along y                    (k_spec_y, inverse)
 //   z: inverse transform along z, real part -> e^l  (k_spec_z_inv)
-// A block loads a tile of lines into shared memory and runs radix-2 stages
-// with a barrier between them. Forward transforms run by decimation in
-// frequency (natural input, output in bit-reversed order) and inverse ones by
-// decimation in time (bit-reversed input, natural output), so every pass reads
-// and writes its lines in place and in order: between the forward and the
-// inverse passes the work buffer holds the spectrum with each axis in
-// bit-reversed order, which the x pass undoes only to look up the spectra.
+// A block loads a tile of T lines into shared memory, lines interleaved (point j
+// of line t at j (T + 1) + t: consecutive threads take consecutive lines, and
+// the z pass's transposing copy meets at most two-way bank conflicts), and
+// runs the radix-2 stages in rounds of up to three: each thread loads 8 (4, 2)
+// points of one group into registers, applies the round's stages there with
+// the radix-2 twiddles, and stores them back, one barrier per round. Forward
+// transforms run by decimation in frequency (natural input, output in
+// bit-reversed order) and inverse ones by decimation in time (bit-reversed
+// input, natural output), so every pass reads and writes its lines in place
+// and in order: between the forward and the inverse passes the work buffer
+// holds the spectrum with each axis in bit-reversed order, which the x pass
+// undoes only to look up the spectra.
 // Twiddles exp(-2 pi i j / 256) come from a table in the stencil pool (FP64
 // values rounded once); a level axis of n points uses every (256 / n)-th entry.
 // The spectra octants are stored interleaved, eight floats per octant point
@@ -43,6 +48,7 @@ namespace msm {
 namespace {
 constexpr int kSpecThreads = 256;
 constexpr int kPer = kSpecTile / kSpecThreads;  // tile elements per thread, at most
+constexpr int kSpecBuf = kSpecTile + kSpecNmax; // interleaved tile with one padding point per line position
 
 __device__ __forceinline__ int bitrev(int j, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - lg)); }
 
@@ -50,46 +56,70 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// radix-2 stages over T = 2^lgT lines of n = 2^lg points in shared memory: element
-// j of line t at buf[(j << lgT) + t] (TF: lines interleaved, t fastest) or at
-// buf[(t << lg) + j]. DIF (forward: natural input, bit-reversed output, twiddles
-// exp(-2 pi i ...)) or DIT (inverse: bit-reversed input, natural output, twiddles
-// exp(+2 pi i ...)). Index arithmetic in shifts and masks (powers of two).
-template <bool DIT, bool TF>
-__device__ __forceinline__ void fft_tile(float2* buf, int lg, int lgT, const float2* tw) {
-  const int half = (1 << lg) >> 1;
-  const int nb = half << lgT;
-  for (int st = 0; st < lg; st++) {
-    const int s2 = DIT ? st : lg - 1 - st;  // log2 of the half span
-    const int hl = 1 << s2;
-    const int sh = 7 - s2;  // twiddle step 256 / (2 hl)
-    for (int b = threadIdx.x; b < nb; b += kSpecThreads) {
-      int t, i;
-      if (TF) {
-        t = b & ((1 << lgT) - 1);
-        i = b >> lgT;
-      } else {
-        i = b & (half - 1);
-        t = b >> (lg - 1);
-      }
-      const int jj = i & (hl - 1);
-      const int j0 = ((i >> s2) << (s2 + 1)) + jj;
-      const int j1 = j0 + hl;
-      float2 w = tw[jj << sh];
-      float2* p0 = TF ? buf + (j0 << lgT) + t : buf + (t << lg) + j0;
-      float2* p1 = TF ? buf + (j1 << lgT) + t : buf + (t << lg) + j1;
-      const float2 a = *p0, c = *p1;
-      if (DIT) {
-        w.y = -w.y;
-        const float2 v = cmul(c, w);
-        *p0 = make_float2(a.x + v.x, a.y + v.y);
-        *p1 = make_float2(a.x - v.x, a.y - v.y);
-      } else {
-        *p0 = make_float2(a.x + c.x, a.y + c.y);
-        *p1 = cmul(make_float2(a.x - c.x, a.y - c.y), w);
+// One round of R radix-2 stages over the tile (T = 2^lgT lines of 2^lg points,
+// point j of line t at buf[j * (T + 1) + t]). A group is the 2^R points j = base +
+// m 2^lq (m < 2^R) that the round's stages combine; each thread takes whole
+// groups in registers. DIF (forward, twiddles exp(-2 pi i ...)): stages with half
+// spans 2^(lq+R-1) down to 2^lq; DIT (inverse, twiddles exp(+2 pi i ...)): half
+// spans 2^lq up to 2^(lq+R-1). The stage of half span h pairs p, p + h (bit of h
+// clear in p) with the twiddle of index (p mod h) 256 / (2 h) in the table.
+template <bool DIT, int R>
+__device__ __forceinline__ void fft_round(float2* buf, int lg, int lgT, int lq, const float2* tw) {
+  constexpr int M = 1 << R;
+  const int T = 1 << lgT, P = T + 1;
+  const int ngroups = (1 << (lg - R)) << lgT;
+  for (int g = threadIdx.x; g < ngroups; g += kSpecThreads) {
+    const int t = g & (T - 1), rest = g >> lgT;
+    const int lo = rest & ((1 << lq) - 1), hi = rest >> lq;
+    const int base = (hi << (lq + R)) + lo;
+    float2 x[M];
+#pragma unroll
+    for (int m = 0; m < M; m++) x[m] = buf[(base + (m << lq)) * P + t];
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+      const int sub = DIT ? k : R - 1 - k;
+      const int h = 1 << sub, s2 = lq + sub;
+#pragma unroll
+      for (int m = 0; m < M; m++) {
+        if (m & h) continue;
+        float2 w = tw[((((m & (h - 1)) << lq) + lo) << (7 - s2))];
+        const float2 a = x[m], c = x[m + h];
+        if (DIT) {
+          w.y = -w.y;
+          const float2 v = cmul(c, w);
+          x[m] = make_float2(a.x + v.x, a.y + v.y);
+          x[m + h] = make_float2(a.x - v.x, a.y - v.y);
+        } else {
+          x[m] = make_float2(a.x + c.x, a.y + c.y);
+          x[m + h] = cmul(make_float2(a.x - c.x, a.y - c.y), w);
+        }
       }
     }
-    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < M; m++) buf[(base + (m << lq)) * P + t] = x[m];
+  }
+  __syncthreads();
+}
+
+// the whole transform of every line of the tile: rounds of three stages (the last one shorter)
+template <bool DIT>
+__device__ __forceinline__ void fft_tile(float2* buf, int lg, int lgT, const float2* tw) {
+  if (DIT) {
+    for (int k = 0; k < lg;) {
+      const int R = min(3, lg - k);
+      if (R == 3) fft_round<true, 3>(buf, lg, lgT, k, tw);
+      else if (R == 2) fft_round<true, 2>(buf, lg, lgT, k, tw);
+      else fft_round<true, 1>(buf, lg, lgT, k, tw);
+      k += R;
+    }
+  } else {
+    for (int k = lg; k > 0;) {
+      const int R = min(3, k);
+      if (R == 3) fft_round<false, 3>(buf, lg, lgT, k - 3, tw);
+      else if (R == 2) fft_round<false, 2>(buf, lg, lgT, k - 2, tw);
+      else fft_round<false, 1>(buf, lg, lgT, k - 1, tw);
+      k -= R;
+    }
   }
 }
 
@@ -102,9 +132,9 @@ __device__ __forceinline__ float sgn_k(int k, int n) { return (k == 0 || 2 * k =
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
-// T lines' points j at g[j * stride + t] (t < T: consecutive z) into buf[(j << lgT) + t]
+// T lines' points j at g[j * stride + t] (t < T: consecutive z) into the tile
 __device__ __forceinline__ void load_lines(float2* buf, const float2* __restrict__ g, long long stride, int lg, int lgT) {
-  const int cnt = 1 << (lg + lgT);
+  const int cnt = 1 << (lg + lgT), P = (1 << lgT) + 1;
   float2 r[kPer];
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
@@ -114,17 +144,17 @@ __device__ __forceinline__ void load_lines(float2* buf, const float2* __restrict
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
     const int e = threadIdx.x + k * kSpecThreads;
-    if (e < cnt) buf[e] = r[k];
+    if (e < cnt) buf[(e >> lgT) * P + (e & ((1 << lgT) - 1))] = r[k];
   }
   __syncthreads();
 }
 
 __device__ __forceinline__ void store_lines(const float2* buf, float2* __restrict__ g, long long stride, int lg, int lgT) {
-  const int cnt = 1 << (lg + lgT);
+  const int cnt = 1 << (lg + lgT), P = (1 << lgT) + 1;
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
     const int e = threadIdx.x + k * kSpecThreads;
-    if (e < cnt) g[(long long)(e >> lgT) * stride + (e & ((1 << lgT) - 1))] = buf[e];
+    if (e < cnt) g[(long long)(e >> lgT) * stride + (e & ((1 << lgT) - 1))] = buf[(e >> lgT) * P + (e & ((1 << lgT) - 1))];
   }
 }
 }  // namespace
@@ -133,14 +163,14 @@ __device__ __forceinline__ void store_lines(const float2* buf, float2* __restric
 __global__ void __launch_bounds__(kSpecThreads) k_spec_z_fwd(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                              const float* __restrict__ kpool, const float* __restrict__ grid,
                                                              float2* __restrict__ spec) {
-  __shared__ float2 buf[kSpecTile];
+  __shared__ float2 buf[kSpecBuf];
   __shared__ float2 tw[256];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
   const long long base = ((long long)it.x0 * L.n[1] + it.y0) * L.n[2];
   const float* q = grid + L.q_off + base;
-  const int lg = L.lg[2], cnt = it.z0 << lg;
+  const int lg = L.lg[2], lgT = ilog2(it.z0), cnt = it.z0 << lg, P = it.z0 + 1;
   float r[kPer];
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
@@ -149,16 +179,16 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_fwd(const LevDev* __res
   }
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
-    const int e = threadIdx.x + k * kSpecThreads;
-    if (e < cnt) buf[e] = make_float2(r[k], 0.f);
+    const int e = threadIdx.x + k * kSpecThreads;  // line e >> lg, point e & (n - 1)
+    if (e < cnt) buf[(e & ((1 << lg) - 1)) * P + (e >> lg)] = make_float2(r[k], 0.f);
   }
   __syncthreads();
-  fft_tile<false, false>(buf, lg, ilog2(it.z0), tw);
+  fft_tile<false>(buf, lg, lgT, tw);
   float2* out = spec + L.f_off + base;
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
     const int e = threadIdx.x + k * kSpecThreads;
-    if (e < cnt) out[e] = buf[e];
+    if (e < cnt) out[e] = buf[(e & ((1 << lg) - 1)) * P + (e >> lg)];
   }
 }
 
@@ -166,14 +196,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_fwd(const LevDev* __res
 __global__ void __launch_bounds__(kSpecThreads) k_spec_z_inv(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                              const float* __restrict__ kpool, float* __restrict__ grid,
                                                              const float2* __restrict__ spec) {
-  __shared__ float2 buf[kSpecTile];
+  __shared__ float2 buf[kSpecBuf];
   __shared__ float2 tw[256];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
   const long long base = ((long long)it.x0 * L.n[1] + it.y0) * L.n[2];
   const float2* in = spec + L.f_off + base;
-  const int lg = L.lg[2], cnt = it.z0 << lg;
+  const int lg = L.lg[2], lgT = ilog2(it.z0), cnt = it.z0 << lg, P = it.z0 + 1;
   float2 r[kPer];
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
@@ -183,15 +213,15 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_inv(const LevDev* __res
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
     const int e = threadIdx.x + k * kSpecThreads;
-    if (e < cnt) buf[e] = r[k];
+    if (e < cnt) buf[(e & ((1 << lg) - 1)) * P + (e >> lg)] = r[k];
   }
   __syncthreads();
-  fft_tile<true, false>(buf, lg, ilog2(it.z0), tw);
+  fft_tile<true>(buf, lg, lgT, tw);
   float* e_out = grid + L.e_off + base;
 #pragma unroll
   for (int k = 0; k < kPer; k++) {
     const int e = threadIdx.x + k * kSpecThreads;
-    if (e < cnt) e_out[e] = buf[e].x;
+    if (e < cnt) e_out[e] = buf[(e & ((1 << lg) - 1)) * P + (e >> lg)].x;
   }
 }
 
@@ -199,7 +229,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_inv(const LevDev* __res
 template <bool INV>
 __global__ void __launch_bounds__(kSpecThreads) k_spec_y(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                          const float* __restrict__ kpool, float2* __restrict__ spec) {
-  __shared__ float2 buf[kSpecTile];
+  __shared__ float2 buf[kSpecBuf];
   __shared__ float2 tw[256];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
@@ -207,7 +237,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_y(const LevDev* __restric
   float2* g = spec + L.f_off + (long long)it.x0 * L.n[1] * L.n[2] + it.y0;
   const int lg = L.lg[1], lgT = ilog2(it.z0);
   load_lines(buf, g, L.n[2], lg, lgT);
-  fft_tile<INV, true>(buf, lg, lgT, tw);
+  fft_tile<INV>(buf, lg, lgT, tw);
   store_lines(buf, g, L.n[2], lg, lgT);
 }
 
@@ -216,21 +246,21 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_y(const LevDev* __restric
 // product with K^ and the inverse transform along x; in place. part (when not
 // null) receives the block's six virial sums at 6 * blockIdx.x.
 template <bool MUL>
-__global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
+__global__ void __launch_bounds__(kSpecThreads, 4) k_spec_x(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                          const float* __restrict__ kpool, float2* __restrict__ spec,
                                                          double* __restrict__ part) {
-  __shared__ float2 buf[kSpecTile];
+  __shared__ float2 buf[kSpecBuf];
   __shared__ float2 tw[256];
   __shared__ double red[kSpecThreads / 32][6];
   const TileItem it = items[blockIdx.x];
   const LevDev& L = lev[it.lev];
   load_twiddles(tw, kpool, L.tw_off);
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const int lg = L.lg[0], lgT = ilog2(it.z0);
+  const int lg = L.lg[0], lgT = ilog2(it.z0), P = it.z0 + 1;
   float2* g = spec + L.f_off + (long long)it.x0 * nz + it.y0;  // x0 holds y, y0 holds z0
   const long long xs = (long long)ny * nz;
   load_lines(buf, g, xs, lg, lgT);
-  fft_tile<false, true>(buf, lg, lgT, tw);
+  fft_tile<false>(buf, lg, lgT, tw);
   // spectra octants, 8 floats per point: K^, dK^ xx yy zz xy xz yz, 0
   const int hy = ny / 2 + 1, hz = nz / 2 + 1;
   const float4* sp = reinterpret_cast<const float4*>(kpool + L.sp_off);
@@ -243,10 +273,12 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restric
   for (int k = 0; k < kPer; k++) {
     const int e = threadIdx.x + k * kSpecThreads;
     if (e >= cnt) continue;
-    const int kx = bitrev(e >> lgT, lg), kz = bitrev(it.y0 + (e & ((1 << lgT) - 1)), L.lg[2]);
+    const int t = e & ((1 << lgT) - 1), j = e >> lgT;
+    const int kx = bitrev(j, lg), kz = bitrev(it.y0 + t, L.lg[2]);
     const long long o = ((long long)fold_k(kx, nx) * hy + fy) * hz + fold_k(kz, nz);
     const float4 s0 = sp[2 * o];
-    const float2 z = buf[e];
+    float2* bp = buf + j * P + t;
+    const float2 z = *bp;
     if (part) {
       const float4 s1 = sp[2 * o + 1];
       const float p2 = fmaf(z.x, z.x, z.y * z.y);
@@ -258,7 +290,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restric
       w[4] = fmaf(sx * sz * s1.y, p2, w[4]);
       w[5] = fmaf(sy * sz * s1.z, p2, w[5]);
     }
-    if (MUL) buf[e] = make_float2(s0.x * z.x, s0.x * z.y);
+    if (MUL) *bp = make_float2(s0.x * z.x, s0.x * z.y);
   }
   if (part) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -276,7 +308,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_x(const LevDev* __restric
     part[6 * (long long)blockIdx.x + threadIdx.x] = v;
   }
   if (!MUL) return;
-  fft_tile<true, true>(buf, lg, lgT, tw);
+  fft_tile<true>(buf, lg, lgT, tw);
   store_lines(buf, g, xs, lg, lgT);
 }
 
