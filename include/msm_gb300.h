@@ -335,8 +335,9 @@ int msm_set_tuning(msm_plan plan, int anterp_tz, int short_block);
  *    fully periodic rectangular cell whose evaluated levels have 2 .. 256 points
  *    per axis (the planner's periodic grids are powers of two), as reported by
  *    msm_plan_info.spectral_ok. The spectra are computed on the host (FP64) at
- *    plan creation and by msm_plan_set_cell, which therefore takes its host path
- *    on a plan running this method.
+ *    plan creation; msm_plan_set_cell recomputes them with the stencils, on the
+ *    device for p = 4 plans (separable sums over the raw samples, FP32) and on
+ *    the host otherwise, whichever method the plan runs.
  * New plans run MSM_LEVELS_BALL; msm_autotune picks the faster method. */
 #define MSM_LEVELS_BALL 0
 #define MSM_LEVELS_SPECTRAL 1
@@ -344,9 +345,7 @@ int msm_set_tuning(msm_plan plan, int anterp_tz, int short_block);
 /* Selects the level method of a single-system plan (host-side; affects the next
  * calls; a following msm_backward needs a new msm_forward). MSM_ERR_INVALID_ARG
  * for an unknown method, MSM_ERR_UNSUPPORTED for MSM_LEVELS_SPECTRAL on a plan
- * that does not allow it. Switching to the spectral method after a device-path
- * msm_plan_set_cell recomputes the spectra on the host and waits for their
- * upload. */
+ * that does not allow it. */
 int msm_set_level_method(msm_plan plan, int method);
 
 /* Synchronises stream and returns the device status word (MSM_DEV_* bits)

@@ -668,8 +668,7 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
   }
   E.hsys[0] = D;
   E.have_fwd = false;  // the workspace holds results for the old cell
-  // the spectral level method's spectra are computed on the host: a plan running it takes the host path
-  bool device_path = S.pbc[0] && S.pbc[1] && S.pbc[2] && S.prefilter && E.level_method == 0;
+  bool device_path = S.pbc[0] && S.pbc[1] && S.pbc[2] && S.prefilter;
   for (const LevelHost& Lv : S.lev) device_path = device_path && Lv.kind == 0;
   cudaStream_t st = (cudaStream_t)stream;
   if (device_path) {
@@ -677,14 +676,16 @@ int msm_plan_set_cell(msm_plan plan, const double* cell, void* stream) {
     const int hz = (S.B[2] + 3) & ~3;
     launch_cell_update(E.d_sys, D, S.h1, S.a, S.p, S.B, hz, S.kball_off, S.dkh_off, S.wb_off, S.wh_off, E.d_kpool,
                        E.d_wpool, st);
-    E.spec_stale = E.spec_ok;  // the spectra follow when the plan switches to the spectral method
+    // the spectral level method's spectra, from the same raw samples (separable sums on the device)
+    if (E.spec_ok)
+      launch_spec_cell(S.h1, S.a, S.p, S.B, S.omh.data(), S.hw, (int)E.spec_n.size(), E.spec_n.data(),
+                       E.spec_sp.data(), E.d_spec_scr_a, E.d_spec_scr_b, E.d_kpool, st);
   } else {
     // omega'-convolved stencils and folded boxes: rebuilt on the host with the
     // plan's sizes, copied through pinned staging buffers (stream-ordered)
     std::string err;
     int rc = E.set_cell_host(S.L, st, &err);
     if (rc) return set_err(rc, "msm_plan_set_cell: " + err);
-    E.spec_stale = false;
     launch_set_sys(E.d_sys, D, st);
   }
   return check_launch("msm_plan_set_cell");

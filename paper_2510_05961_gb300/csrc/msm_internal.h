@@ -259,6 +259,13 @@ void launch_fvjp_final(const Work& w, const Tables& t, const AtomItem* items, in
                        float* dpos, cudaStream_t s);
 // dynamic cell (k_cell.cu): new system descriptor (alone, or with the ball stencils of a periodic p = 4 plan)
 void launch_set_sys(SysDev* d_sys, const SysDev& val, cudaStream_t s);
+// spectral level method, dynamic cell (k_cell.cu): the spectra of levels 1 .. nlev (cubic grids of n[l-1]
+// points per axis, n[0] the largest) of a periodic p = 4 plan from its raw samples, into the stencil pool
+// at sp_off[l-1], three launches for all levels; scratch_a: sum over levels of 7 (2B_x+1)(2B_y+1)(n/2+1)
+// floats, scratch_b: sum of 7 (2B_x+1)(n/2+1)^2 floats, then 7 (2B_x+1)(2B_y+1)(2B_z+1) for the samples
+void launch_spec_cell(const double h1[3], double a, int p, const int B[3], const double* om, int hw, int nlev,
+                      const int* n, const long long* sp_off, float* scratch_a, float* scratch_b, float* kpool,
+                      cudaStream_t s);
 void launch_cell_update(SysDev* d_sys, const SysDev& val, const double h1[3], double a, int p, const int B[3], int hz,
                         long long kball_off, long long dkh_off, long long wb_off, long long wh_off, float* kpool,
                         int* wpool, cudaStream_t s);

@@ -1314,6 +1314,30 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   }
   int rc = upload(kp, wp, voff, err);
   if (rc) return rc;
+  spec_n.clear();
+  spec_sp.clear();
+  if (spec_ok && sys[0].prefilter) {
+    // scratch of the device-path spectra (msm_plan_set_cell): every level's separable sums
+    const SysHost& S = sys[0];
+    for (int l = 1; l <= S.ncomp; l++) {
+      spec_n.push_back(hlev[hs[0].lev0 + l - 1].n[0]);
+      spec_sp.push_back(hlev[hs[0].lev0 + l - 1].sp_off);
+    }
+    const long long nxb = 2 * S.B[0] + 1, nyb = 2 * S.B[1] + 1;
+    long long na = 0, nb = 0;
+    for (int nl : spec_n) {
+      const long long h = nl / 2 + 1;
+      na += 7 * nxb * nyb * h;
+      nb += 7 * nxb * h * h;
+    }
+    nb += 7 * nxb * nyb * (2 * S.B[2] + 1);  // the raw samples, after the y sums
+    cudaFree(d_spec_scr_a);
+    cudaFree(d_spec_scr_b);
+    d_spec_scr_a = d_spec_scr_b = nullptr;
+    if (cudaMalloc((void**)&d_spec_scr_a, sizeof(float) * na) != cudaSuccess ||
+        cudaMalloc((void**)&d_spec_scr_b, sizeof(float) * nb) != cudaSuccess)
+      return fail(err, MSM_ERR_CUDA, "cudaMalloc of the spectra scratch failed");
+  }
   // workspace layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -1458,13 +1482,6 @@ int Engine::set_level_method(int method, std::string* err) {
     return fail(err, MSM_ERR_UNSUPPORTED,
                 "the spectral level method needs a single-system plan with a fully periodic rectangular cell and ball "
                 "levels of 2 .. 256 points per axis");
-  if (method == 1 && spec_stale) {
-    // a device-path msm_plan_set_cell updated the ball samples only: the spectra follow on the host
-    int rc = set_cell_host(sys[0].L, 0, err, true);
-    if (rc) return rc;
-    if (cudaEventSynchronize(ev_stage) != cudaSuccess) return fail(err, MSM_ERR_CUDA, "cudaEventSynchronize failed");
-    spec_stale = false;
-  }
   level_method = method;
   spec_virial_ready = false;
   have_fwd = false;
@@ -1641,6 +1658,8 @@ Engine::~Engine() {
   cudaFree(d_spec_z);
   cudaFree(d_spec_y);
   cudaFree(d_spec_x);
+  cudaFree(d_spec_scr_a);
+  cudaFree(d_spec_scr_b);
   cudaFree(d_res_items);
   cudaFree(d_pro_items);
   cudaFree(d_energy_scratch);

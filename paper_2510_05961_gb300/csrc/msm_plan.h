@@ -97,7 +97,6 @@ struct Engine {
   // The FFT items: z lines (lev, x, y0, rows), y lines (lev, x, z0, cols), x lines (lev, y, z0, cols).
   bool spec_ok = false;
   int level_method = 0;             // 0 = ball stencils, 1 = spectral (MSM_LEVELS_*)
-  bool spec_stale = false;          // a device-path msm_plan_set_cell left the spectra of the old cell
   bool spec_virial_ready = false;   // the last forward left the spectral grid-virial partials in part_wg
   long long spec_complex = 0;       // float2 entries of the levels' complex work buffers
   std::vector<TileItem> spec_z_items, spec_y_items, spec_x_items;
@@ -106,6 +105,11 @@ struct Engine {
   TileItem* d_spec_x = nullptr;
   std::vector<int> voff_spec;
   int* d_voff_spec = nullptr;       // virial partial ranges of the spectral method (x items, then boxes)
+  // device path of msm_plan_set_cell for the spectra (periodic p = 4 plans): separable-sum scratch
+  float* d_spec_scr_a = nullptr;
+  float* d_spec_scr_b = nullptr;
+  std::vector<int> spec_n;          // grid points per axis of each spectral level
+  std::vector<long long> spec_sp;   // their spectrum offsets in the stencil pool
   // device tables (owned)
   SysDev* d_sys = nullptr;
   LevDev* d_lev = nullptr;

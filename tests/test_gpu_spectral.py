@@ -143,9 +143,13 @@ def _run_cell(plan, pos, q):
                 dpos=gp.cpu().numpy(), dq=gq.cpu().numpy())
 
 
-def test_spectral_dynamic_cell():
+@pytest.mark.parametrize("make", [lambda: W.random_box(8000, seed=73),
+                                  lambda: W.random_box(3000, seed=76, p=6, h=1.5, a=6.0)], ids=["p4_device", "p6_host"])
+def test_spectral_dynamic_cell(make):
+    """Cell changes on a plan running the spectral method: periodic p = 4 plans recompute the spectra on
+    the device from the raw samples (separable sums, FP32), others on the host (FP64)."""
     import oracle as O
-    w = W.random_box(8000, seed=73)
+    w = make()
     M = [O.plan_for(w).M[d] for d in range(3)]
     base = np.array(w.cell, np.float64)
     # built for the most compressed cell it will serve (the plan keeps its stencil sizes)
@@ -156,7 +160,7 @@ def test_spectral_dynamic_cell():
         pos = (w.pos.astype(np.float64) * np.array(f)).astype(np.float32)
         plan.set_cell(cell)
         check_oracle(_run_cell(plan, pos, w.q), _oracle_for(cell, w, M, pos))
-    # a device-path cell change under the ball method, then the switch: the spectra follow
+    # a cell change under the ball method, then the switch: the spectra followed the cell
     plan.set_level_method(LEVELS_BALL)
     cell = base * 1.03
     pos = (w.pos.astype(np.float64) * 1.03).astype(np.float32)
