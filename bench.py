@@ -745,11 +745,13 @@ def run_sweep(args):
         plan.profile(False)
         ms = sum(a.elapsed_time(b) for a, b in evs) / steps
         peak = peaks(dev, None)["fp32_tflops"]
+        spectral = info["level_method"] == 1
         fl = {"short": SHORT_FLOP_PER_PAIR * short_pairs(n, 0.1, w.a),
-              "stencil": ball_sample_flops(info, w.a, w.p)[0]}
+              "stencil": (sum(2 * 5.0 * m * math.log2(m) + 2.0 * m for m in level_points(info)) if spectral
+                          else ball_sample_flops(info, w.a, w.p)[0])}
         roof = {k: (fl[k] / (phase[k] / 1e3) / 1e12 / peak if phase.get(k, 0) > 0 else None) for k in fl}
         rows.append({"atoms": n, "M": info["M"][0], "h1": round(info["h1"][0], 4), "levels": info["nlev"],
-                     "tuning": [info["anterp_tz"], info["short_block"]],
+                     "tuning": [info["anterp_tz"], info["short_block"], ["ball", "spectral"][info["level_method"]]],
                      "ms_per_forward": ms, "atoms_per_s": n / (ms / 1e3),
                      "fp32_frac": roof, "phase_ms": {k: round(v, 4) for k, v in phase.items() if v > 0}})
         del plan, pos, q, E, phi, F
@@ -757,8 +759,10 @@ def run_sweep(args):
     print(json.dumps({"sweep": rows, "unit": "atoms/s", "workload": "periodic cubes at 0.1 atoms/A^3, uniform "
                       "positions, +/-1 charges; p=4, h=2, a=8; forward only (E, phi, F)",
                       "l2": "flushed (256 MB write) before every step", "data": "synthetic",
-                      "fp32_frac_note": "algorithmic FLOP of the phase (40 per in-cutoff pair; 2 per kernel sample of "
-                                        "the ball per point, plus the prefilter) / its event time / the FP32 FMA peak from the SM count and "
+                      "fp32_frac_note": "algorithmic FLOP of the phase (40 per in-cutoff pair; ball method: 2 per kernel "
+                                        "sample of the ball per point, plus the prefilter; spectral method: 5 N log2 N "
+                                        "per forward and per inverse 3-D FFT, plus 2 N for the product) / its event "
+                                        "time / the FP32 FMA peak from the SM count and "
                                         "maximum clock; the short-range phase overlaps the grid chain, so both "
                                         "include the contention"}))
 

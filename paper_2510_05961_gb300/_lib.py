@@ -107,6 +107,11 @@ def load(path: str = None):
     L.msm_forward_noalloc.argtypes = [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]
     L.msm_profile.argtypes = [_vp, C.c_int]
     L.msm_set_level_method.argtypes = [_vp, C.c_int]
+    L.msm_autotune.argtypes = [_vp, _vp, C.c_size_t, C.c_int, _vp, _vp, _vp]
+    L.msm_batch_autotune.argtypes = [_vp, _vp, C.c_size_t, _vp, _vp, _vp]
+    L.msm_set_tuning.argtypes = [_vp, C.c_int, C.c_int]
+    L.msm_batch_set_tuning.argtypes = [_vp, C.c_int, C.c_int]
+    L.msm_batch_get_tuning.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.msm_profile_read.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int if name != "msm_last_error" else C.c_char_p

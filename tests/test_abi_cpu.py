@@ -35,6 +35,9 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(_lib.EXPORTS) == decl
     for name in decl:
         assert hasattr(lib, name), name
+        # every call has its C signature declared to ctypes (an undeclared size_t argument
+        # would be passed as a 32-bit int and wrap for workspaces above 2 GiB)
+        assert getattr(lib, name).argtypes is not None, name
 
 
 def _describe(lib, w=None, **kw):
