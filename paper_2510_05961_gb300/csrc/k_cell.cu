@@ -250,8 +250,14 @@ __global__ void __launch_bounds__(kSpecCellThreads) k_spec_cell_x(SpecCellArgs A
     const int kx = e / h, kz = e - kx * h;
     float acc = 0.f;
     for (int xi = 0; xi < nxb; xi++) acc = fmaf(slice[xi * h + kz], t[(kx * (xi - A.B[0])) & msk], acc);
-    const long long o = ((long long)kx * h + ky) * h + kz;
-    kpool[sp_off + 8 * o + c] = acc * wy * wt[kx] * wt[kz];
+    // at [|k_x|][|k_y|][z position]: the positions whose bit reversal is k_z or n - k_z
+    const float val = acc * wy * wt[kx] * wt[kz];
+    int lgn = 0;
+    while ((1 << lgn) < n) lgn++;
+    const int z0 = (int)(__brev((unsigned)kz) >> (32 - lgn)), z1 = (int)(__brev((unsigned)((n - kz) & msk)) >> (32 - lgn));
+    const long long row = ((long long)kx * h + ky) * n;
+    kpool[sp_off + 8 * (row + z0) + c] = val;
+    kpool[sp_off + 8 * (row + z1) + c] = val;
   }
 }
 

@@ -39,8 +39,10 @@
 // undoes only to look up the spectra.
 // Twiddles exp(-2 pi i j / 256) come from a table in the stencil pool (FP64
 // values rounded once); a level axis of n points uses every (256 / n)-th entry.
-// The spectra octants are stored interleaved, eight floats per octant point
-// (K^, dK^ xx yy zz xy xz yz, zero), read with two 16-byte loads.
+// The spectra are stored interleaved, eight floats per point (K^, dK^ xx yy zz
+// xy xz yz, zero; two 16-byte loads) at [|k_x|][|k_y|][z position]: along z by
+// the buffer's bit-reversed position, so the consecutive z of a tile read
+// consecutive memory.
 #include "msm_internal.h"
 
 namespace msm {
@@ -261,8 +263,8 @@ __global__ void __launch_bounds__(kSpecThreads, 4) k_spec_x(const LevDev* __rest
   const long long xs = (long long)ny * nz;
   load_lines(buf, g, xs, lg, lgT);
   fft_tile<false>(buf, lg, lgT, tw);
-  // spectra octants, 8 floats per point: K^, dK^ xx yy zz xy xz yz, 0
-  const int hy = ny / 2 + 1, hz = nz / 2 + 1;
+  // spectra, 8 floats per point (K^, dK^ xx yy zz xy xz yz, 0) at [|k_x|][|k_y|][z position]
+  const int hy = ny / 2 + 1;
   const float4* sp = reinterpret_cast<const float4*>(kpool + L.sp_off);
   const int ky = bitrev(it.x0, L.lg[1]);
   const int fy = fold_k(ky, ny);
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(kSpecThreads, 4) k_spec_x(const LevDev* __rest
     if (e >= cnt) continue;
     const int t = e & ((1 << lgT) - 1), j = e >> lgT;
     const int kx = bitrev(j, lg), kz = bitrev(it.y0 + t, L.lg[2]);
-    const long long o = ((long long)fold_k(kx, nx) * hy + fy) * hz + fold_k(kz, nz);
+    const long long o = ((long long)fold_k(kx, nx) * hy + fy) * nz + it.y0 + t;
     const float4 s0 = sp[2 * o];
     float2* bp = buf + j * P + t;
     const float2 z = *bp;

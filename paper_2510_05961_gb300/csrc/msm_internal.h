@@ -127,9 +127,9 @@ struct LevDev {
   long long p_off;          // ball: float offset of the halo-padded, omega'-prefiltered copy of q~^l
                             // (ball levels apply raw kernel samples; R is the sample radius)
   // spectral level method (fully periodic single-system plans, k_fft.cu): float2 offset of the
-  // level's complex work buffer, float offsets of its spectrum octants (eight floats per octant
-  // point: K^, dK^ xx yy zz xy xz yz, 0) and of the twiddle table in the stencil pool (-1 where
-  // the level has none), log2 of n per axis
+  // level's complex work buffer, float offsets of its spectra (eight floats per point: K^, dK^
+  // xx yy zz xy xz yz, 0; at [|k_x|][|k_y|][z position], k_z the bit reversal of the position)
+  // and of the twiddle table in the stencil pool (-1 where the level has none), log2 of n per axis
   long long f_off, sp_off, tw_off;
   int lg[3];
 };

@@ -1025,13 +1025,26 @@ void Engine::assemble_pools(const std::vector<int>& lev0_of, std::vector<float>&
       while (kp.size() % 4) kp.push_back(0.f);
       L.tw_off = tw;
       L.sp_off = (long long)kp.size();
-      const size_t oct = (size_t)(L.n[0] / 2 + 1) * (L.n[1] / 2 + 1) * (L.n[2] / 2 + 1);
+      const int hx = L.n[0] / 2 + 1, hy = L.n[1] / 2 + 1, hz = L.n[2] / 2 + 1, nz = L.n[2];
+      const size_t oct = (size_t)hx * hy * hz;
       std::vector<float> seven(7 * oct);
       level_spectra(S, l, L.n, seven.data());
-      // interleaved, eight floats per octant point (two 16-byte loads in k_spec_x)
-      kp.resize(kp.size() + 8 * oct, 0.f);
-      for (size_t o = 0; o < oct; o++)
-        for (int c = 0; c < 7; c++) kp[L.sp_off + 8 * o + c] = seven[c * oct + o];
+      // stored as k_spec_x reads them: [|k_x|][|k_y|][z position], the z position holding the
+      // frequency whose bit reversal it is (the work buffer's order), eight floats per point
+      // (two 16-byte loads); a tile's consecutive z positions are then consecutive in memory
+      kp.resize(kp.size() + (size_t)8 * hx * hy * nz, 0.f);
+      int lgz = 0;
+      while ((1 << lgz) < nz) lgz++;
+      for (int fx = 0; fx < hx; fx++)
+        for (int fy = 0; fy < hy; fy++)
+          for (int zp = 0; zp < nz; zp++) {
+            int kz = 0;
+            for (int b = 0; b < lgz; b++) kz |= ((zp >> b) & 1) << (lgz - 1 - b);
+            const int fz = std::min(kz, nz - kz);
+            const size_t o = ((size_t)fx * hy + fy) * hz + fz;
+            const size_t at = (((size_t)fx * hy + fy) * nz + zp) * 8;
+            for (int c = 0; c < 7; c++) kp[L.sp_off + at + c] = seven[c * oct + o];
+          }
     }
   }
   if (kp.empty()) kp.push_back(0.f);
