@@ -224,11 +224,12 @@ int msm_backward(msm_plan plan, void* workspace, const double* grad_energy, floa
                  double* virial, void* stream);
 
 /* End-to-end evaluation on host buffers: copies the inputs to the device (into
- * the workspace), runs msm_forward (forces, virial) and msm_backward with
- * dL/dE = 1, copies E, dE/dpos (= -F), dE/dq (= phi) and, if virial_host is
- * not NULL, W back, and waits for the copies. The per-atom gradients are
- * copied while the grid virial runs (a second stream). Unlike the other
- * calls this one returns only after the results are on the host.
+ * the workspace), evaluates forward and backward with dL/dE = 1 (the forward
+ * writes dE/dpos = -F and dE/dq = phi directly, the values msm_backward would
+ * give), copies E, dE/dpos, dE/dq and, if virial_host is not NULL, W back, and
+ * waits for the copies. The per-atom gradients are copied while the grid
+ * virial is formed (a second stream). Unlike the other calls this one returns
+ * only after the results are on the host.
  *  pos_host      host, n x 3 float32 (page-locked memory makes the copies asynchronous).
  *  q_host        host, n float32.
  *  energy_host   host, 1 double.

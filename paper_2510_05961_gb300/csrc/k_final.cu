@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
                                                      const float* __restrict__ phi_sr, const float* __restrict__ phi_lr,
                                                      const float4* __restrict__ f_sr, const float4* __restrict__ f_lr,
                                                      float* __restrict__ phi, float* __restrict__ forces,
-                                                     float2* __restrict__ part_e, float2* __restrict__ part_q) {
+                                                     float2* __restrict__ part_e, float2* __restrict__ part_q,
+                                                     float fsign) {
   __shared__ float2 red[kChunk / 32][2];
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -62,10 +63,12 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
     qa = fabsf(qk);
     if (phi) phi[g] = ph;
     if (forces) {
+      // fsign = -1 writes dE/dr = -F (the same bits as k_backward_scale with dL/dE = 1)
+      const float fq = fsign * qk;
       float4 a = f_sr[k], b = f_lr[k];
-      forces[3 * (long long)g + 0] = qk * (a.x + b.x);
-      forces[3 * (long long)g + 1] = qk * (a.y + b.y);
-      forces[3 * (long long)g + 2] = qk * (a.z + b.z);
+      forces[3 * (long long)g + 0] = fq * (a.x + b.x);
+      forces[3 * (long long)g + 1] = fq * (a.y + b.y);
+      forces[3 * (long long)g + 2] = fq * (a.z + b.z);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -235,9 +238,9 @@ __global__ void __launch_bounds__(kChunk) k_field(const SysDev* __restrict__ sys
 }
 
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
-                     float* forces, cudaStream_t s) {
+                     float* forces, cudaStream_t s, float fsign) {
   k_finalize<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, phi, forces,
-                                       w.part_e, w.part_q);
+                                       w.part_e, w.part_q, fsign);
 }
 
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s) {

@@ -71,7 +71,7 @@ static int count_forward(const Engine& E, bool) {
 
 // forward pass of an engine; n_single >= 0 sets the atom count of a single-system plan
 static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const float* pos, const float* q,
-                       double* energy, float* phi, float* forces, int flags, cudaStream_t s) {
+                       double* energy, float* phi, float* forces, int flags, cudaStream_t s, float fsign = 1.0f) {
   if (!ws || !energy) return set_err(MSM_ERR_INVALID_ARG, "workspace and energy must not be NULL");
   if (ws_bytes < E.ws_bytes) return set_err(MSM_ERR_CAPACITY, "workspace smaller than msm_workspace_bytes");
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return set_err(MSM_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -134,7 +134,7 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   if (!E.serial) cudaStreamWaitEvent(s, E.ev_join, 0);  // join
   {
     Phase ph(E, MSM_PH_FINAL, s);
-    launch_finalize(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, s);
+    launch_finalize(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, s, fsign);
     launch_energy(w, t, E.nsys, energy, s);
   }
   E.launches_fwd = count_forward(E, want_f);
@@ -189,9 +189,11 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
 }
 
 // End-to-end evaluation on host buffers (msm_evaluate_host): inputs copied into
-// the workspace's staging arrays, forward (forces, virial) and backward with
-// dL/dE = 1 on the caller's stream; E and the per-atom gradients are copied back
-// on a second stream while the grid virial runs, then the virial; waits for both.
+// the workspace's staging arrays, then the forward (forces, virial) on the
+// caller's stream writing, for dL/dE = 1, dE/dq = phi and dE/dr = -F straight
+// into the staging outputs (the same values the backward's scaling would
+// write); E and the per-atom gradients are copied back on a second stream
+// while the backward forms the virial, then the virial; waits for both.
 static int run_evaluate_host(Engine& E, void* ws, size_t ws_bytes, int n, const float* pos_h, const float* q_h,
                              double* e_h, float* dpos_h, float* dq_h, double* w_h, cudaStream_t s) {
   if (!ws || !e_h) return set_err(MSM_ERR_INVALID_ARG, "workspace and energy_host must not be NULL");
@@ -208,10 +210,9 @@ static int run_evaluate_host(Engine& E, void* ws, size_t ws_bytes, int n, const 
                 cudaMemcpyAsync(w.io_q, q_h, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess))
     return set_err(MSM_ERR_CUDA, "msm_evaluate_host: input copy failed");
   launch_fill(w.io_e + nsys, nsys, 1.0, s);  // dL/dE = 1
-  int rc = run_forward(E, ws, ws_bytes, n, w.io_pos, w.io_q, w.io_e, nullptr, nullptr,
-                       MSM_WANT_FORCES | (w_h ? MSM_WANT_VIRIAL : 0), s);
+  int rc = run_forward(E, ws, ws_bytes, n, w.io_pos, w.io_q, w.io_e, w.io_dq, w.io_dpos,
+                       MSM_WANT_FORCES | (w_h ? MSM_WANT_VIRIAL : 0), s, -1.0f);
   if (rc) return rc;
-  if ((rc = run_backward(E, ws, w.io_e + nsys, w.io_dpos, w.io_dq, nullptr, s))) return rc;
   cudaEventRecord(E.ev_grad, s);
   cudaStreamWaitEvent(E.copy, E.ev_grad, 0);
   bool ok = cudaMemcpyAsync(e_h, w.io_e, sizeof(double), cudaMemcpyDeviceToHost, E.copy) == cudaSuccess;

@@ -226,8 +226,9 @@ void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, i
 void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, int part_off,
                        cudaStream_t s);
 // outputs (k_final.cu)
+// forces are written times fsign (-1: dE/dr for dL/dE = 1)
 void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
-                     float* forces, cudaStream_t s);
+                     float* forces, cudaStream_t s, float fsign = 1.0f);
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);  // also flags non-neutral periodic systems
 // spectral level method (k_fft.cu): e^l of every spectral level (part: grid virial partials, one
 // per x item, or null), or the virial partials alone
