@@ -7,8 +7,8 @@ interpolation) before each access; a failed test sets MSM_DEV_CHECK in the
 status word and skips the access. This test builds that library and runs it,
 in a fresh process (the binding loads one library per process), on small
 cases of every boundary kind (with the per-atom and, where the plan allows
-it, the cluster-pair short-range kernel), a tilted cell, a dense cluster and
-a batch:
+them, the cluster-pair short-range kernel and the spectral level method), a
+tilted cell, a dense cluster and a batch:
 no check may fire, and the outputs must match the FP64 oracle as in the
 other parity tests.
 """
@@ -62,18 +62,19 @@ cases = [W.random_box(3000, seed=6301), W.random_box(1200, seed=6302, pbc=(1, 1,
          W.random_box(40, density=0.08, seed=6305)]
 for w in cases:
     ref = O.msm(O.plan_for(w), w.pos.astype(np.float64), w.q.astype(np.float64))
-    for sb in (256, SHORT_CLUSTER):
+    for sb, lm in ((256, 0), (SHORT_CLUSTER, 0), (256, 1)):
         plan = Plan(w.cell, w.pbc, w.h, w.a, w.p, w.levels, max_atoms=w.n, device=dev)
         try:
             plan.set_tuning(32, sb)
+            plan.set_level_method(lm)
         except Exception:
-            continue  # outside the cluster kernel's preconditions
+            continue  # outside the cluster kernel's or the spectral method's preconditions
         pos = torch.from_numpy(w.pos).to(dev); q = torch.from_numpy(w.q).to(dev)
         E, phi, F = plan.forward(pos, q, forces=True, virial=True)
         gp, gq, Wv = plan.backward(torch.ones(1, dtype=torch.float64, device=dev))
         torch.cuda.synchronize()
         st = plan.status()
-        out["cases"].append({"name": "%s/%d" % (w.name, sb), "status": st,
+        out["cases"].append({"name": "%s/%d/%d" % (w.name, sb, lm), "status": st,
                              "eE": abs(E.item() - ref["E"]) / abs(ref["E"]),
                              "eF": rel_rms(F.cpu().numpy(), ref["F"]), "ephi": rel_rms(phi.cpu().numpy(), ref["phi"]),
                              "eW": float(np.abs(Wv.cpu().numpy() - ref["W"]).max() / np.abs(ref["W"]).max())})

@@ -193,3 +193,69 @@ def test_plans_without_the_spectral_method_refuse():
         tilted.set_level_method(LEVELS_SPECTRAL)
     batch = Batch([W.random_box(500, seed=74), W.random_box(700, seed=75)], device=DEV)
     assert batch is not None  # batches keep the ball and box kernels (no level-method call)
+
+
+def test_spectral_vjps_field_and_end_to_end_match_ball_method():
+    """The calls that run the grid chain again (msm_force_vjp, msm_potential_vjp) or
+    end to end (msm_evaluate_host), and msm_field, on a spectral plan agree with the
+    ball method's to FP32 rounding."""
+    w = CASES["periodic_20001"]()
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    rng = np.random.default_rng(77)
+    u = torch.from_numpy(rng.normal(size=(w.n, 3)).astype(np.float32)).to(DEV)
+    g = torch.from_numpy(rng.normal(size=w.n).astype(np.float32)).to(DEV)
+    out = {}
+    for m in (LEVELS_BALL, LEVELS_SPECTRAL):
+        plan = make_plan(w, m)
+        plan.forward(pos, q, forces=True, virial=True)
+        fld = plan.field().cpu().numpy()
+        fq, fp = plan.force_vjp(u)
+        plan.forward(pos, q, forces=True, virial=True)
+        pq, pp = plan.potential_vjp(g)
+        torch.cuda.synchronize()
+        host = plan.evaluate_host(torch.from_numpy(w.pos), torch.from_numpy(w.q))
+        out[m] = dict(field=fld, fq=fq.cpu().numpy(), fp=fp.cpu().numpy(), pq=pq.cpu().numpy(),
+                      pp=pp.cpu().numpy(), host=host)
+    b, s = out[LEVELS_BALL], out[LEVELS_SPECTRAL]
+    for key in ("field", "fq", "fp", "pq", "pp"):
+        assert rel_rms(s[key], b[key]) <= AGREE, key
+    hb, hs = b["host"], s["host"]
+    assert abs(float(hs[0]) - float(hb[0])) <= AGREE * abs(float(hb[0]))
+    for i in (1, 2):
+        assert rel_rms(np.asarray(hs[i]), np.asarray(hb[i])) <= AGREE, i
+    assert np.abs(np.asarray(hs[3]) - np.asarray(hb[3])).max() <= AGREE * np.abs(np.asarray(hb[3])).max()
+
+
+def test_spectral_plan_in_a_cuda_graph():
+    """Forward (forces, virial) and backward of a spectral plan captured in a CUDA graph
+    and replayed twice with a new input set copied into the captured buffers: every
+    replay against the oracle on its inputs."""
+    import oracle as O
+    w = CASES["periodic_20001"]()
+    plan = make_plan(w, LEVELS_SPECTRAL)
+    pos = torch.from_numpy(w.pos).to(DEV)
+    q = torch.from_numpy(w.q).to(DEV)
+    gE = torch.ones(1, dtype=torch.float64, device=DEV)
+    side = torch.cuda.Stream(DEV)
+    side.wait_stream(torch.cuda.current_stream(DEV))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            plan.forward(pos, q, forces=True, virial=True)
+            plan.backward(gE)
+    torch.cuda.current_stream(DEV).wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        E, phi, F = plan.forward(pos, q, forces=True, virial=True)
+        gp, gq, Wv = plan.backward(gE)
+    for seed in (81, 82):
+        w2 = W.redraw(w, seed)
+        pos.copy_(torch.from_numpy(w2.pos))
+        q.copy_(torch.from_numpy(w2.q))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = O.msm(O.plan_for(w2), w2.pos.astype(np.float64), w2.q.astype(np.float64), forces=True, virial=True)
+        r = dict(E=float(E.cpu()[0]), phi=phi.cpu().numpy(), F=F.cpu().numpy(), W=Wv.cpu().numpy(),
+                 dpos=gp.cpu().numpy(), dq=gq.cpu().numpy())
+        check_oracle(r, ref)
