@@ -203,8 +203,11 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
-  int cell = cell_id[g];
+  // every load that does not depend on the bucket is issued before its scan
+  const int cell = cell_id[g];
   const int2 rg = crange[g];
+  const float qq = q[g];
+  const float px[3] = {pos[3 * (long long)g], pos[3 * (long long)g + 1], pos[3 * (long long)g + 2]};
   const int b = rg.x, e = rg.y;
   if (!MSM_CHECK(S, b >= S.atom_off && e <= S.atom_off + S.n && b <= e)) return;
   int rank = 0;
@@ -212,7 +215,6 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   int dst = b + rank;
   perm[dst] = g;
   scell[dst] = cell;
-  float qq = q[g];
   // x, y relative to the cell's lower faces, z relative to the column base
   // (the Cartesian z of the image next to the cell), formed in FP64 from the
   // FP32 input so that displacements between nearby atoms are exact to FP32
@@ -242,7 +244,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   }
   for (int d = 0; d < 3; d++) {
     float s, t;
-    const float x = pos[3 * g + d];
+    const float x = px[d];
     if (reduced_coord(S, d, x, s)) {
       loc[d] = 0.0f;
       u[d] = 0.0f;

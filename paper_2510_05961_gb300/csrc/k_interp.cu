@@ -454,11 +454,15 @@ __global__ void __launch_bounds__(kAntWarps * 32, 4) k_anterp_cols(const SysDev*
     const int zsh = kz * S.M[2] - mz0 - H + 1;  // z base relative to the segment: floor(u_z) + zsh
     int j = cs[wz], je = cs[wend + 1];
     if (!MSM_CHECK(S, j >= S.atom_off && je <= S.atom_off + S.n)) je = j;
+    // the next chunk's atoms are loaded while this chunk is added (one memory
+    // round trip per run instead of one per chunk)
+    float4 un = lane < je - j ? uq[j + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (; j < je; j += 32) {
       const int na = min(32, je - j);
+      const float4 u = un;
+      if (lane < je - j - 32) un = uq[j + 32 + lane];
       __syncwarp();  // the previous chunk's staging has been read
       if (lane < na) {
-        const float4 u = uq[j + lane];
         const float flx = floorf(u.x), fly = floorf(u.y), flz = floorf(u.z);
         const int bx = (int)flx - H + 1 - lox, by = (int)fly - H + 1 - loy, bz = (int)flz + zsh;
         float qq = u.w;
