@@ -191,7 +191,8 @@ __global__ void k_bin_scatter(const SysDev* __restrict__ sys, const AtomItem* __
 __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                            const float* __restrict__ pos, const float* __restrict__ q,
                            const int* __restrict__ cell_id, const int2* __restrict__ crange,
-                           const int* __restrict__ bucket, int* __restrict__ perm, int* __restrict__ scell,
+                           const int* __restrict__ bucket, int* __restrict__ perm, int* __restrict__ iperm,
+                           int* __restrict__ scell,
                            float4* __restrict__ xq, float4* __restrict__ uq) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -214,6 +215,7 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   for (int t = b; t < e; t++) rank += (bucket[t] < g);
   int dst = b + rank;
   perm[dst] = g;
+  iperm[g] = dst;
   scell[dst] = cell;
   // x, y relative to the cell's lower faces, z relative to the column base
   // (the Cartesian z of the image next to the cell), formed in FP64 from the
@@ -294,7 +296,7 @@ void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitem
   k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(w.cell_count, total_cells, w.cell_start, w.scan_tiles);
   k_scan_fix<<<ntiles, kScanThreads, 0, s>>>(w.cell_start, total_cells, w.scan_tiles, ntiles);
   k_bin_scatter<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_id, w.slot, w.cell_start, w.bucket, w.crange);
-  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.crange, w.bucket, w.perm, w.scell,
+  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.crange, w.bucket, w.perm, w.iperm, w.scell,
                                        w.xq, w.uq);
 }
 

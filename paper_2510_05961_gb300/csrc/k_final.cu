@@ -6,7 +6,8 @@
 //                              hi + lo pairs by error-free transformations in
 //                              a fixed order, FP64 for the final value),
 //   W = W0 + W^(1+)           (FP64, fixed-order sums of the block partials),
-// written back in the caller's atom order through the sort permutation.
+// written back in the caller's atom order by gathers through the inverse sort
+// permutation.
 #include "msm_internal.h"
 
 namespace msm {
@@ -37,14 +38,15 @@ __device__ __forceinline__ float2 shfl_down_hl(float2 v, int o) {
 // result is the exact sum up to the FP32 rounding of the lo parts, about
 // 2^-47 of sum |q phi|, with no FP64 arithmetic (slow on this GPU) before the
 // final conversion; 1/2 is applied at the end (exact).
+// The per-atom results go to res in the sorted order (coalesced); k_outputs
+// and k_backward_scale then gather them into the caller's order, so that their
+// stores are coalesced and only one 16-byte load per atom is scattered.
 __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ sys,
-                                                     const AtomItem* __restrict__ items,
-                                                     const int* __restrict__ perm, const float4* __restrict__ xq,
+                                                     const AtomItem* __restrict__ items, const float4* __restrict__ xq,
                                                      const float* __restrict__ phi_sr, const float* __restrict__ phi_lr,
                                                      const float4* __restrict__ f_sr, const float4* __restrict__ f_lr,
-                                                     float* __restrict__ phi, float* __restrict__ forces,
-                                                     float2* __restrict__ part_e, float2* __restrict__ part_q,
-                                                     float fsign) {
+                                                     bool forces, float4* __restrict__ res,
+                                                     float2* __restrict__ part_e, float2* __restrict__ part_q) {
   __shared__ float2 red[kChunk / 32][2];
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -52,24 +54,21 @@ __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ 
   float2 e = make_float2(0.f, 0.f);
   float qs = 0.f, qa = 0.f;  // sum q and sum |q| (FP32: only compared with a 1e-5 threshold)
   if ((int)threadIdx.x < it.count && local < S.n) {
-    int k = S.atom_off + local;
-    int g = perm[k];
-    if (!MSM_CHECK(S, g >= S.atom_off && g < S.atom_off + S.n)) g = S.atom_off;
+    const int k = S.atom_off + local;
     const float qk = xq[k].w;
     const float ph = phi_sr[k] + phi_lr[k];
     e.x = __fmul_rn(qk, ph);
     e.y = fmaf(qk, ph, -e.x);
     qs = qk;
     qa = fabsf(qk);
-    if (phi) phi[g] = ph;
+    float4 r = make_float4(ph, 0.f, 0.f, 0.f);
     if (forces) {
-      // fsign = -1 writes dE/dr = -F (the same bits as k_backward_scale with dL/dE = 1)
-      const float fq = fsign * qk;
-      float4 a = f_sr[k], b = f_lr[k];
-      forces[3 * (long long)g + 0] = fq * (a.x + b.x);
-      forces[3 * (long long)g + 1] = fq * (a.y + b.y);
-      forces[3 * (long long)g + 2] = fq * (a.z + b.z);
+      const float4 a = f_sr[k], b = f_lr[k];
+      r.y = qk * (a.x + b.x);
+      r.z = qk * (a.y + b.y);
+      r.w = qk * (a.z + b.z);
     }
+    res[k] = r;
   }
   for (int o = 16; o > 0; o >>= 1) {
     add_hl(e, shfl_down_hl(e, o));
@@ -193,6 +192,53 @@ __global__ void __launch_bounds__(64) k_virial_out(const double* __restrict__ sl
   }
 }
 
+// res (sorted) to the caller's order: phi_g, fsign F_g (fsign = -1 gives dE/dr =
+// -F for dL/dE = 1, the same bits as k_backward_scale_res with dL/dE = 1)
+__global__ void __launch_bounds__(kChunk) k_outputs(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                                                    const int* __restrict__ iperm, const float4* __restrict__ res,
+                                                    float* __restrict__ phi, float* __restrict__ forces, float fsign) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  const int g = S.atom_off + local;
+  int k = iperm[g];
+  if (!MSM_CHECK(S, k >= S.atom_off && k < S.atom_off + S.n)) k = S.atom_off;
+  const float4 r = res[k];
+  if (phi) phi[g] = r.x;
+  if (forces) {
+    forces[3 * (long long)g + 0] = fsign * r.y;
+    forces[3 * (long long)g + 1] = fsign * r.z;
+    forces[3 * (long long)g + 2] = fsign * r.w;
+  }
+}
+
+// dE/dq = g phi, dE/dr = -g F from the forward's res, in the caller's order
+__global__ void __launch_bounds__(kChunk) k_backward_scale_res(const SysDev* __restrict__ sys,
+                                                               const AtomItem* __restrict__ items,
+                                                               const int* __restrict__ iperm,
+                                                               const float4* __restrict__ res,
+                                                               const double* __restrict__ grad,
+                                                               float* __restrict__ dE_dpos, float* __restrict__ dE_dq) {
+  AtomItem it = items[blockIdx.x];
+  const SysDev& S = sys[it.sys];
+  const int local = it.start + threadIdx.x;
+  if ((int)threadIdx.x >= it.count || local >= S.n) return;
+  const int g = S.atom_off + local;
+  const int k = iperm[g];
+  if (!MSM_CHECK(S, k >= S.atom_off && k < S.atom_off + S.n)) return;
+  const float gr = (float)grad[it.sys];
+  const float4 r = res[k];
+  if (dE_dq) dE_dq[g] = gr * r.x;
+  if (dE_dpos) {
+    dE_dpos[3 * (long long)g + 0] = -gr * r.y;
+    dE_dpos[3 * (long long)g + 1] = -gr * r.z;
+    dE_dpos[3 * (long long)g + 2] = -gr * r.w;
+  }
+}
+
+// the same from the sorted potentials and fields (the backward recomputed the
+// fields of a forward that skipped them)
 __global__ void __launch_bounds__(kChunk) k_backward_scale(const SysDev* __restrict__ sys,
                                                            const AtomItem* __restrict__ items,
                                                            const int* __restrict__ perm,
@@ -237,10 +283,15 @@ __global__ void __launch_bounds__(kChunk) k_field(const SysDev* __restrict__ sys
   field[3 * (long long)g + 2] = a.z + b.z;
 }
 
-void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
-                     float* forces, cudaStream_t s, float fsign) {
-  k_finalize<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, phi, forces,
-                                       w.part_e, w.part_q, fsign);
+void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, cudaStream_t s) {
+  k_finalize<<<nitems, kChunk, 0, s>>>(t.sys, items, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, forces, w.res,
+                                       w.part_e, w.part_q);
+}
+
+void launch_outputs(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi, float* forces,
+                    float fsign, cudaStream_t s) {
+  if (!phi && !forces) return;
+  k_outputs<<<nitems, kChunk, 0, s>>>(t.sys, items, w.iperm, w.res, phi, forces, fsign);
 }
 
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s) {
@@ -256,9 +307,12 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
 }
 
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
-                           const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s) {
-  k_backward_scale<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, grad,
-                                             dE_dpos, dE_dq);
+                           const double* grad, float* dE_dpos, float* dE_dq, bool from_res, cudaStream_t s) {
+  if (from_res)
+    k_backward_scale_res<<<nitems, kChunk, 0, s>>>(t.sys, items, w.iperm, w.res, grad, dE_dpos, dE_dq);
+  else
+    k_backward_scale<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, grad,
+                                               dE_dpos, dE_dq);
 }
 
 // upstream vectors of the forces into the sorted order, with the charge: us[k] = (u_perm[k], q_k)

@@ -58,14 +58,14 @@ struct Phase {
 };
 
 // kernels each phase launches (for the launch count)
-static int count_forward(const Engine& E, bool) {
+static int count_forward(const Engine& E, bool outputs) {
   int n = 1 + 5 + 1;                                   // prologue, binning, short range
   n += E.anterp_items.empty() ? 0 : (E.ant_wstride > 0 ? 2 : 1);  // anterpolation (columns: partials + sums)
   for (int l = 1; l < E.maxcomp; l++) n += 2;          // restriction + prolongation per level step
   if (E.level_method == 1) n += 5;                     // spectral: z, y, x (with the product), y, z passes
   else n += E.ball_items.empty() ? 0 : 2;              // halo padding + ball stencil
   n += E.box_items.empty() ? 0 : 1;
-  n += 1 + 1 + 1;                                      // interp, finalize, energy
+  n += 1 + 1 + 1 + (outputs ? 1 : 0);                  // interp, finalize, energy, outputs
   return n;
 }
 
@@ -134,10 +134,11 @@ static int run_forward(Engine& E, void* ws, size_t ws_bytes, int n_single, const
   if (!E.serial) cudaStreamWaitEvent(s, E.ev_join, 0);  // join
   {
     Phase ph(E, MSM_PH_FINAL, s);
-    launch_finalize(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, s, fsign);
+    launch_finalize(w, t, E.d_atom_items, nai, want_f, s);
     launch_energy(w, t, E.nsys, energy, s);
+    launch_outputs(w, t, E.d_atom_items, nai, phi, want_f ? forces : nullptr, fsign, s);
   }
-  E.launches_fwd = count_forward(E, want_f);
+  E.launches_fwd = count_forward(E, phi || (want_f && forces));
   E.launches_bwd = 0;
   int rc = check_launch("msm_forward");
   if (rc) return rc;
@@ -159,6 +160,8 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   const bool had_w = (E.last_flags & MSM_WANT_VIRIAL) != 0;
   const bool need_f = dE_dpos != nullptr;
   const bool need_w = virial != nullptr;
+  // the forward's per-atom results serve unless the forces are wanted and it skipped them
+  const bool from_res = !need_f || had_f;
   int nl = 0;
   if ((need_f && !had_f) || (need_w && !had_w)) {
     // the forward skipped these parts; the short-range kernel rewrites its
@@ -181,7 +184,7 @@ static int run_backward(Engine& E, void* ws, const double* grad, float* dE_dpos,
   }
   if (dE_dpos || dE_dq) {
     Phase ph(E, MSM_PH_BSCALE, s);
-    launch_backward_scale(w, t, E.d_atom_items, nai, grad, dE_dpos, dE_dq, s);
+    launch_backward_scale(w, t, E.d_atom_items, nai, grad, dE_dpos, dE_dq, from_res, s);
     nl++;
   }
   E.launches_bwd = nl;

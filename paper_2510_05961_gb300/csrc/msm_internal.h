@@ -161,6 +161,7 @@ struct Work {
   int* slot;
   int* bucket;
   int* perm;
+  int* iperm;      // binning: sorted position of each atom, atom order
   int* scell;
   int2* crange;    // binning: each atom's cell range [b, e) in the sorted order, atom order
   float4* xq;      // Cartesian position (the periodic image next to its cell) and charge, sorted
@@ -169,6 +170,7 @@ struct Work {
   float4* f_sr;    // short-range field -grad phi0 (force / q), sorted
   float* phi_lr;   // long-range potential, sorted
   float4* f_lr;    // long-range field -grad phi^(1+) (force / q), sorted
+  float4* res;     // outputs of the last forward, sorted: phi and F = q field
   float2* part_e;  // per atom item: sum q phi as hi + lo
   float2* part_q;  // per atom item: sum q and sum |q|
   double* part_w0; // per warp of each atom item: 6 short-range virial components
@@ -226,9 +228,11 @@ void launch_virial_ball(const Work& w, const Tables& t, const TileItem* items, i
 void launch_virial_box(const Work& w, const Tables& t, const RangeItem* items, int nitems, int part_off,
                        cudaStream_t s);
 // outputs (k_final.cu)
-// forces are written times fsign (-1: dE/dr for dL/dE = 1)
-void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi,
-                     float* forces, cudaStream_t s, float fsign = 1.0f);
+// phi and F (forces: the fields were computed) per sorted atom into w.res, the energy partials
+void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int nitems, bool forces, cudaStream_t s);
+// w.res to the caller's atom order (either pointer may be null); forces times fsign (-1: dE/dr for dL/dE = 1)
+void launch_outputs(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi, float* forces,
+                    float fsign, cudaStream_t s);
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s);  // also flags non-neutral periodic systems
 // spectral level method (k_fft.cu): e^l of every spectral level (part: grid virial partials, one
 // per x item, or null), or the virial partials alone
@@ -238,8 +242,10 @@ void launch_spectral_virial(const Work& w, const Tables& t, const TileItem* zi, 
                             const TileItem* xi, int nx, double* part, cudaStream_t s);
 void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, const int* vitem_off,
                        const double* grad, double* virial, cudaStream_t s);
+// from_res: from the forward's w.res (its forces included when dE_dpos is wanted); else from the
+// sorted potentials and fields
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
-                           const double* grad, float* dE_dpos, float* dE_dq, cudaStream_t s);
+                           const double* grad, float* dE_dpos, float* dE_dq, bool from_res, cudaStream_t s);
 void launch_field(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* field, cudaStream_t s);
 void launch_fill(double* p, int n, double v, cudaStream_t s);
 // vector-Jacobian product of the forces (k_final.cu, k_short.cu, k_interp.cu)

@@ -1368,6 +1368,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_slot = take(sizeof(int) * N);
   L_bucket = take(sizeof(int) * N);
   L_perm = take(sizeof(int) * N);
+  L_iperm = take(sizeof(int) * N);
   L_scell = take(sizeof(int) * N);
   L_crange = take(sizeof(int2) * N);
   L_xq = take(sizeof(float4) * N);
@@ -1376,6 +1377,7 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_phi_lr = take(sizeof(float) * N);
   L_f_sr = take(sizeof(float4) * N);
   L_f_lr = take(sizeof(float4) * N);
+  L_res = take(sizeof(float4) * N);
   L_part_e = take(sizeof(double) * atom_items.size());
   L_part_q = take(sizeof(double) * 2 * atom_items.size());
   L_part_w0 = take(sizeof(double) * 6 * kChunkWarps * atom_items.size());
@@ -1690,6 +1692,7 @@ Work Engine::resolve(void* ws) const {
   w.slot = (int*)(b + L_slot);
   w.bucket = (int*)(b + L_bucket);
   w.perm = (int*)(b + L_perm);
+  w.iperm = (int*)(b + L_iperm);
   w.scell = (int*)(b + L_scell);
   w.crange = (int2*)(b + L_crange);
   w.xq = (float4*)(b + L_xq);
@@ -1698,6 +1701,7 @@ Work Engine::resolve(void* ws) const {
   w.phi_lr = (float*)(b + L_phi_lr);
   w.f_sr = (float4*)(b + L_f_sr);
   w.f_lr = (float4*)(b + L_f_lr);
+  w.res = (float4*)(b + L_res);
   w.part_e = (float2*)(b + L_part_e);
   w.io_pos = (float*)(b + L_io_pos);
   w.io_q = (float*)(b + L_io_q);
