@@ -170,29 +170,30 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_fix(int* __restrict__ sta
   if (blockIdx.x == (unsigned)(ntiles - 1) && threadIdx.x == 0) start[total_cells] = off + tiles[ntiles - 1];
 }
 
-// also keeps each atom's cell range [b, e) in atom order, so that the rank
-// kernel reads it with one coalesced load instead of a dependent one
+// each atom's (index, cell) at its slot of its cell's range; the rank kernel
+// then walks the sorted positions and finds each entry's stable place in the
+// same cell range
 __global__ void k_bin_scatter(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                               const int* __restrict__ cell_id, const int* __restrict__ slot,
-                              const int* __restrict__ cell_start, int* __restrict__ bucket,
-                              int2* __restrict__ crange) {
+                              const int* __restrict__ cell_start, int2* __restrict__ bucket) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
   int g = S.atom_off + local;
-  const int* cs = cell_start + S.cell_off + cell_id[g];
-  const int c0 = cs[0], c1 = cs[1];
-  crange[g] = make_int2(c0, c1);
-  const int b = c0 + slot[g];
-  if (MSM_CHECK(S, b >= S.atom_off && b < S.atom_off + S.n)) bucket[b] = g;
+  const int cell = cell_id[g];
+  const int b = cell_start[S.cell_off + cell] + slot[g];
+  if (MSM_CHECK(S, b >= S.atom_off && b < S.atom_off + S.n)) bucket[b] = make_int2(g, cell);
 }
 
+// One thread per sorted position k of the bucket: the entry (g, cell) there
+// goes to its stable place dst in the cell's range (the number of the range's
+// entries with a smaller atom index), so the stores of a warp stay within the
+// few cells its positions cover; the atom's position and charge are gathered.
 __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                            const float* __restrict__ pos, const float* __restrict__ q,
-                           const int* __restrict__ cell_id, const int2* __restrict__ crange,
-                           const int* __restrict__ bucket, int* __restrict__ perm, int* __restrict__ iperm,
-                           int* __restrict__ scell,
+                           const int* __restrict__ cell_start, const int2* __restrict__ bucket,
+                           int* __restrict__ perm, int* __restrict__ iperm, int* __restrict__ scell,
                            float4* __restrict__ xq, float4* __restrict__ uq) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
@@ -203,16 +204,15 @@ __global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __res
   __syncthreads();
   int local = it.start + threadIdx.x;
   if ((int)threadIdx.x >= it.count || local >= S.n) return;
-  int g = S.atom_off + local;
-  // every load that does not depend on the bucket is issued before its scan
-  const int cell = cell_id[g];
-  const int2 rg = crange[g];
+  const int2 bg = bucket[S.atom_off + local];
+  const int g = bg.x, cell = bg.y;
+  if (!MSM_CHECK(S, g >= S.atom_off && g < S.atom_off + S.n && cell >= 0 && cell < S.C[0] * S.C[1] * S.C[2])) return;
   const float qq = q[g];
   const float px[3] = {pos[3 * (long long)g], pos[3 * (long long)g + 1], pos[3 * (long long)g + 2]};
-  const int b = rg.x, e = rg.y;
+  const int b = cell_start[S.cell_off + cell], e = cell_start[S.cell_off + cell + 1];
   if (!MSM_CHECK(S, b >= S.atom_off && e <= S.atom_off + S.n && b <= e)) return;
   int rank = 0;
-  for (int t = b; t < e; t++) rank += (bucket[t] < g);
+  for (int t = b; t < e; t++) rank += (bucket[t].x < g);
   int dst = b + rank;
   perm[dst] = g;
   iperm[g] = dst;
@@ -295,8 +295,8 @@ void launch_bin(const Work& w, const Tables& t, const AtomItem* items, int nitem
   int ntiles = (total_cells + kScanTile - 1) / kScanTile;
   k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(w.cell_count, total_cells, w.cell_start, w.scan_tiles);
   k_scan_fix<<<ntiles, kScanThreads, 0, s>>>(w.cell_start, total_cells, w.scan_tiles, ntiles);
-  k_bin_scatter<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_id, w.slot, w.cell_start, w.bucket, w.crange);
-  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_id, w.crange, w.bucket, w.perm, w.iperm, w.scell,
+  k_bin_scatter<<<nitems, kChunk, 0, s>>>(t.sys, items, w.cell_id, w.slot, w.cell_start, w.bucket);
+  k_bin_rank<<<nitems, kChunk, 0, s>>>(t.sys, items, pos, q, w.cell_start, w.bucket, w.perm, w.iperm, w.scell,
                                        w.xq, w.uq);
 }
 

@@ -159,11 +159,10 @@ struct Work {
   int* scan_tiles;
   int* cell_id;
   int* slot;
-  int* bucket;
+  int2* bucket;    // binning: (atom, cell) at the atom's slot of its cell, before the stable rank
   int* perm;
   int* iperm;      // binning: sorted position of each atom, atom order
   int* scell;
-  int2* crange;    // binning: each atom's cell range [b, e) in the sorted order, atom order
   float4* xq;      // Cartesian position (the periodic image next to its cell) and charge, sorted
   float4* uq;      // level-1 grid coordinates and charge, sorted order
   float* phi_sr;   // short-range potential incl. self term, sorted

@@ -1366,11 +1366,10 @@ int Engine::build(const msm_params* prm, const int* counts, int nsys_, bool sing
   L_scan_tiles = take(sizeof(int) * std::max(ntiles, 1));
   L_cell_id = take(sizeof(int) * N);
   L_slot = take(sizeof(int) * N);
-  L_bucket = take(sizeof(int) * N);
+  L_bucket = take(sizeof(int2) * N);
   L_perm = take(sizeof(int) * N);
   L_iperm = take(sizeof(int) * N);
   L_scell = take(sizeof(int) * N);
-  L_crange = take(sizeof(int2) * N);
   L_xq = take(sizeof(float4) * N);
   L_uq = take(sizeof(float4) * N);
   L_phi_sr = take(sizeof(float) * N);
@@ -1690,11 +1689,10 @@ Work Engine::resolve(void* ws) const {
   w.scan_tiles = (int*)(b + L_scan_tiles);
   w.cell_id = (int*)(b + L_cell_id);
   w.slot = (int*)(b + L_slot);
-  w.bucket = (int*)(b + L_bucket);
+  w.bucket = (int2*)(b + L_bucket);
   w.perm = (int*)(b + L_perm);
   w.iperm = (int*)(b + L_iperm);
   w.scell = (int*)(b + L_scell);
-  w.crange = (int2*)(b + L_crange);
   w.xq = (float4*)(b + L_xq);
   w.uq = (float4*)(b + L_uq);
   w.phi_sr = (float*)(b + L_phi_sr);

@@ -128,7 +128,7 @@ struct Engine {
   // workspace layout (byte offsets)
   size_t L_status, L_cell_count, L_cell_start, L_scan_tiles, L_cell_id, L_slot, L_bucket, L_perm, L_iperm, L_res, L_scell, L_xq,
       L_uq, L_phi_sr, L_phi_lr, L_f_sr, L_f_lr, L_part_e, L_part_q, L_part_w0, L_part_wg, L_part_vs, L_grid, L_vjp_u,
-      L_vjp_h, L_io_pos, L_io_q, L_io_dpos, L_io_dq, L_io_e, L_apart, L_crange, L_spec;
+      L_vjp_h, L_io_pos, L_io_q, L_io_dpos, L_io_dq, L_io_e, L_apart, L_spec;
   size_t ws_bytes = 0;
   // state of the last forward pass
   bool have_fwd = false;
