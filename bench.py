@@ -282,8 +282,8 @@ def kernel_table(info, n, a, p, ph, pk, st_flops_exec, serial_note):
     add("prolong", "k_prolong (all level steps)", "hbm", 4.0 * sum(pts[l + 1] + 2 * pts[l] for l in range(len(pts) - 1)),
         "bytes: read level l+1, read and write level l (4 B per point)")
     add("interp", "k_interp", "alu", 2.0 * 4 * p ** 3 * n, "FLOP: 4 p^3 FMA per atom (potential and gradient)")
-    add("final", "k_finalize, k_energy", "hbm", 76.0 * n,
-        "bytes: read phi (2 x 4), fields (2 x 16), q (16), perm (4); write phi (4) and F (12) per atom")
+    add("final", "k_finalize, k_energy, k_outputs", "hbm", 76.0 * n,
+        "bytes: read phi (2 x 4), fields (2 x 16), q (16), permutation (4); write phi (4) and F (12) per atom")
     if spectral:
         nparts = 8 * ((n + 255) // 256) + sum(
             m[1] * -(-m[2] // min(m[2], 2048 // m[0])) for m in info["n"][:info["ncomp"]])
@@ -292,8 +292,8 @@ def kernel_table(info, n, a, p, ph, pk, st_flops_exec, serial_note):
     else:
         add("virial", "k_virial_ball, k_virial_box, k_virial_slices, k_virial_out", "alu", f_vir,
             "FLOP: 2 per unique lag (half of the %d samples) per point of the ball levels (autocorrelation)" % nnz)
-    add("bscale", "k_backward_scale", "hbm", 72.0 * n,
-        "bytes: read phi (2 x 4), fields (2 x 16), q (16), perm (4); write dE/dr (12) and dE/dq (4) per atom")
+    add("bscale", "k_backward_scale_res", "hbm", 36.0 * n,
+        "bytes: read the forward's phi and F (16) and the inverse permutation (4); write dE/dr (12) and dE/dq (4) per atom")
     return {"rows": rows, "note": serial_note}
 
 
