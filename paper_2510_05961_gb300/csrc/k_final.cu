@@ -193,47 +193,77 @@ __global__ void __launch_bounds__(64) k_virial_out(const double* __restrict__ sl
 }
 
 // res (sorted) to the caller's order: phi_g, fsign F_g (fsign = -1 gives dE/dr =
-// -F for dL/dE = 1, the same bits as k_backward_scale_res with dL/dE = 1)
-__global__ void __launch_bounds__(kChunk) k_outputs(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
-                                                    const int* __restrict__ iperm, const float4* __restrict__ res,
-                                                    float* __restrict__ phi, float* __restrict__ forces, float fsign) {
+// -F for dL/dE = 1, the same bits as k_backward_scale_res with dL/dE = 1).
+// kGatherPer atoms of an item per thread, every index load issued before the
+// first res load, so that each thread keeps kGatherPer dependent chains in
+// flight.
+constexpr int kGatherPer = 4, kGatherNT = kChunk / kGatherPer;
+
+__global__ void __launch_bounds__(kGatherNT) k_outputs(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+                                                       const int* __restrict__ iperm, const float4* __restrict__ res,
+                                                       float* __restrict__ phi, float* __restrict__ forces,
+                                                       float fsign) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  const int local = it.start + threadIdx.x;
-  if ((int)threadIdx.x >= it.count || local >= S.n) return;
-  const int g = S.atom_off + local;
-  int k = iperm[g];
-  if (!MSM_CHECK(S, k >= S.atom_off && k < S.atom_off + S.n)) k = S.atom_off;
-  const float4 r = res[k];
-  if (phi) phi[g] = r.x;
-  if (forces) {
-    forces[3 * (long long)g + 0] = fsign * r.y;
-    forces[3 * (long long)g + 1] = fsign * r.z;
-    forces[3 * (long long)g + 2] = fsign * r.w;
+  int g[kGatherPer], k[kGatherPer];
+#pragma unroll
+  for (int r = 0; r < kGatherPer; r++) {
+    const int slot = (int)threadIdx.x + r * kGatherNT, local = it.start + slot;
+    g[r] = slot < it.count && local < S.n ? S.atom_off + local : -1;
+    k[r] = g[r] >= 0 ? iperm[g[r]] : 0;
+  }
+  float4 v[kGatherPer];
+#pragma unroll
+  for (int r = 0; r < kGatherPer; r++) {
+    if (g[r] >= 0 && !MSM_CHECK(S, k[r] >= S.atom_off && k[r] < S.atom_off + S.n)) g[r] = -1;
+    v[r] = g[r] >= 0 ? res[k[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int r = 0; r < kGatherPer; r++) {
+    if (g[r] < 0) continue;
+    if (phi) phi[g[r]] = v[r].x;
+    if (forces) {
+      forces[3 * (long long)g[r] + 0] = fsign * v[r].y;
+      forces[3 * (long long)g[r] + 1] = fsign * v[r].z;
+      forces[3 * (long long)g[r] + 2] = fsign * v[r].w;
+    }
   }
 }
 
 // dE/dq = g phi, dE/dr = -g F from the forward's res, in the caller's order
-__global__ void __launch_bounds__(kChunk) k_backward_scale_res(const SysDev* __restrict__ sys,
-                                                               const AtomItem* __restrict__ items,
-                                                               const int* __restrict__ iperm,
-                                                               const float4* __restrict__ res,
-                                                               const double* __restrict__ grad,
-                                                               float* __restrict__ dE_dpos, float* __restrict__ dE_dq) {
+// (kGatherPer atoms per thread, as k_outputs)
+__global__ void __launch_bounds__(kGatherNT) k_backward_scale_res(const SysDev* __restrict__ sys,
+                                                                  const AtomItem* __restrict__ items,
+                                                                  const int* __restrict__ iperm,
+                                                                  const float4* __restrict__ res,
+                                                                  const double* __restrict__ grad,
+                                                                  float* __restrict__ dE_dpos,
+                                                                  float* __restrict__ dE_dq) {
   AtomItem it = items[blockIdx.x];
   const SysDev& S = sys[it.sys];
-  const int local = it.start + threadIdx.x;
-  if ((int)threadIdx.x >= it.count || local >= S.n) return;
-  const int g = S.atom_off + local;
-  const int k = iperm[g];
-  if (!MSM_CHECK(S, k >= S.atom_off && k < S.atom_off + S.n)) return;
   const float gr = (float)grad[it.sys];
-  const float4 r = res[k];
-  if (dE_dq) dE_dq[g] = gr * r.x;
-  if (dE_dpos) {
-    dE_dpos[3 * (long long)g + 0] = -gr * r.y;
-    dE_dpos[3 * (long long)g + 1] = -gr * r.z;
-    dE_dpos[3 * (long long)g + 2] = -gr * r.w;
+  int g[kGatherPer], k[kGatherPer];
+#pragma unroll
+  for (int r = 0; r < kGatherPer; r++) {
+    const int slot = (int)threadIdx.x + r * kGatherNT, local = it.start + slot;
+    g[r] = slot < it.count && local < S.n ? S.atom_off + local : -1;
+    k[r] = g[r] >= 0 ? iperm[g[r]] : 0;
+  }
+  float4 v[kGatherPer];
+#pragma unroll
+  for (int r = 0; r < kGatherPer; r++) {
+    if (g[r] >= 0 && !MSM_CHECK(S, k[r] >= S.atom_off && k[r] < S.atom_off + S.n)) g[r] = -1;
+    v[r] = g[r] >= 0 ? res[k[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int r = 0; r < kGatherPer; r++) {
+    if (g[r] < 0) continue;
+    if (dE_dq) dE_dq[g[r]] = gr * v[r].x;
+    if (dE_dpos) {
+      dE_dpos[3 * (long long)g[r] + 0] = -gr * v[r].y;
+      dE_dpos[3 * (long long)g[r] + 1] = -gr * v[r].z;
+      dE_dpos[3 * (long long)g[r] + 2] = -gr * v[r].w;
+    }
   }
 }
 
@@ -291,7 +321,7 @@ void launch_finalize(const Work& w, const Tables& t, const AtomItem* items, int 
 void launch_outputs(const Work& w, const Tables& t, const AtomItem* items, int nitems, float* phi, float* forces,
                     float fsign, cudaStream_t s) {
   if (!phi && !forces) return;
-  k_outputs<<<nitems, kChunk, 0, s>>>(t.sys, items, w.iperm, w.res, phi, forces, fsign);
+  k_outputs<<<nitems, kGatherNT, 0, s>>>(t.sys, items, w.iperm, w.res, phi, forces, fsign);
 }
 
 void launch_energy(const Work& w, const Tables& t, int nsys, double* energy, cudaStream_t s) {
@@ -309,7 +339,7 @@ void launch_virial_out(const Work& w, const Tables& t, int nsys, int nslice, con
 void launch_backward_scale(const Work& w, const Tables& t, const AtomItem* items, int nitems,
                            const double* grad, float* dE_dpos, float* dE_dq, bool from_res, cudaStream_t s) {
   if (from_res)
-    k_backward_scale_res<<<nitems, kChunk, 0, s>>>(t.sys, items, w.iperm, w.res, grad, dE_dpos, dE_dq);
+    k_backward_scale_res<<<nitems, kGatherNT, 0, s>>>(t.sys, items, w.iperm, w.res, grad, dE_dpos, dE_dq);
   else
     k_backward_scale<<<nitems, kChunk, 0, s>>>(t.sys, items, w.perm, w.xq, w.phi_sr, w.phi_lr, w.f_sr, w.f_lr, grad,
                                                dE_dpos, dE_dq);
