@@ -190,7 +190,7 @@ __global__ void k_bin_scatter(const SysDev* __restrict__ sys, const AtomItem* __
 // goes to its stable place dst in the cell's range (the number of the range's
 // entries with a smaller atom index), so the stores of a warp stay within the
 // few cells its positions cover; the atom's position and charge are gathered.
-__global__ void k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
+__global__ void __launch_bounds__(kChunk, 6) k_bin_rank(const SysDev* __restrict__ sys, const AtomItem* __restrict__ items,
                            const float* __restrict__ pos, const float* __restrict__ q,
                            const int* __restrict__ cell_start, const int2* __restrict__ bucket,
                            int* __restrict__ perm, int* __restrict__ iperm, int* __restrict__ scell,

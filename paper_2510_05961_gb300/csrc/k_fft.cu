@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_y(const LevDev* __restric
 // product with K^ and the inverse transform along x; in place. part (when not
 // null) receives the block's six virial sums at 6 * blockIdx.x.
 template <bool MUL>
-__global__ void __launch_bounds__(kSpecThreads, 4) k_spec_x(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
+__global__ void __launch_bounds__(kSpecThreads, 5) k_spec_x(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                          const float* __restrict__ kpool, float2* __restrict__ spec,
                                                          double* __restrict__ part) {
   __shared__ float2 buf[kSpecBuf];

@@ -595,17 +595,18 @@ __global__ void __launch_bounds__(kAntSumZ * kAntSumY, 8) k_anterp_sum(const Sys
   __syncthreads();
   const int z = it.z0 + tz;
   if (gy >= L.n[1] || z >= L.n[2]) return;
-  // eight loads in flight before their sum (in the candidates' order)
+  // sixteen loads in flight before their sum (in the candidates' order; a
+  // footprint of 5 grid columns per axis has 9 candidates, so one round trip)
   float v = 0.f;
-  for (int t0 = 0; t0 < nc; t0 += 8) {
-    float x[8];
+  for (int t0 = 0; t0 < nc; t0 += 16) {
+    float x[16];
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
+    for (int k = 0; k < 16; k++) {
       const long long o = t0 + k < nc ? off[col][t0 + k] : -1;
       x[k] = o >= 0 ? __ldg(apart + o + z) : 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 8; k++) v += x[k];
+    for (int k = 0; k < 16; k++) v += x[k];
   }
   grid[L.q_off + ((long long)gx * L.n[1] + gy) * nz + z] = v;
 }
