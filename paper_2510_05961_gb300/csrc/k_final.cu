@@ -39,7 +39,7 @@ __device__ __forceinline__ float2 shfl_down_hl(float2 v, int o) {
 // 2^-47 of sum |q phi|, with no FP64 arithmetic (slow on this GPU) before the
 // final conversion; 1/2 is applied at the end (exact).
 // The per-atom results go to res in the sorted order (coalesced); k_outputs
-// and k_backward_scale then gather them into the caller's order, so that their
+// and k_backward_scale_res then gather them into the caller's order, so that their
 // stores are coalesced and only one 16-byte load per atom is scattered.
 __global__ void __launch_bounds__(kChunk) k_finalize(const SysDev* __restrict__ sys,
                                                      const AtomItem* __restrict__ items, const float4* __restrict__ xq,
