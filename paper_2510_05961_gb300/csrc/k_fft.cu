@@ -162,7 +162,7 @@ __device__ __forceinline__ void store_lines(const float2* buf, float2* __restric
 }  // namespace
 
 // z pass, forward: item (lev, x, y0, rows): rows z-lines (y0 .. y0 + rows - 1) at x
-__global__ void __launch_bounds__(kSpecThreads) k_spec_z_fwd(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
+__global__ void __launch_bounds__(kSpecThreads, 5) k_spec_z_fwd(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                              const float* __restrict__ kpool, const float* __restrict__ grid,
                                                              float2* __restrict__ spec) {
   __shared__ float2 buf[kSpecBuf];
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_fwd(const LevDev* __res
 }
 
 // z pass, inverse: e^l = Re(inverse transform along z)
-__global__ void __launch_bounds__(kSpecThreads) k_spec_z_inv(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
+__global__ void __launch_bounds__(kSpecThreads, 5) k_spec_z_inv(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                              const float* __restrict__ kpool, float* __restrict__ grid,
                                                              const float2* __restrict__ spec) {
   __shared__ float2 buf[kSpecBuf];
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_z_inv(const LevDev* __res
 
 // y pass: item (lev, x, z0, cols): y-lines at x for z in [z0, z0 + cols); in place
 template <bool INV>
-__global__ void __launch_bounds__(kSpecThreads) k_spec_y(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
+__global__ void __launch_bounds__(kSpecThreads, 5) k_spec_y(const LevDev* __restrict__ lev, const TileItem* __restrict__ items,
                                                          const float* __restrict__ kpool, float2* __restrict__ spec) {
   __shared__ float2 buf[kSpecBuf];
   __shared__ float2 tw[256];
